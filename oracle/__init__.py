@@ -1,0 +1,47 @@
+"""Plain, slow, FP64 CPU oracle of the sketch-and-project ridge solver.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it. The
+product library (``paper_2105_05565_gb300``) never imports, calls or links it,
+and this package imports nothing from the product library.
+
+What it computes follows the paper (arXiv 2105.05565, "RidgeSketch"):
+
+* the ridge system A w = b in primal (A = X^T X + lambda I, b = X^T y) or dual
+  (A = X X^T + lambda I, b = y, w = X^T alpha) form -- Section 2.1, eqs. (2)-(4);
+* the sketch-and-project iteration -- Algorithm 1 (Section 3, update eq. (12),
+  residual recursion eq. (13)) and its momentum form Algorithm 2 (Section 6.3,
+  residual recursion eq. (53));
+* the five sketches, each built as an explicit dense m x tau matrix S from its
+  definition in Section 4 (Gaussian, Subsample, Count, SubCount, SRHT);
+* the momentum parameter rules of Sections 6.1-6.2 and 8.1 (eqs. (38), (40),
+  (49)-(50), (66), (67)).
+
+Random choices come from the counter-based generator in ``oracle.rng`` which is
+written from the published SplitMix64 definition; the GPU library implements
+the same generator separately, so that sketch indices and signs agree bit for
+bit without sharing code.
+
+Parity status of each function is stated in its docstring ("pinned by ...").
+"""
+from .rng import (  # noqa: F401
+    GAMMA,
+    mix64,
+    draw,
+    iter_key,
+    sample_keys,
+    subsample_indices,
+    signs_buckets,
+    gaussian_entries,
+)
+from .sketches import sketch_matrix, subcount_params, default_tau  # noqa: F401
+from .momentum import momentum_schedule  # noqa: F401
+from .solver import (  # noqa: F401
+    form_system,
+    direct_solution,
+    least_norm_solution,
+    sketch_and_project,
+    solve_ridge,
+    solve_matrix_free,
+    true_residual,
+)
