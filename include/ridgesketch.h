@@ -1,0 +1,219 @@
+/*
+ * ridgesketch.h -- C ABI of the GB300 sketch-and-project ridge regression solver.
+ *
+ * The library solves ridge regression (Section 2.1, eq. (1)):
+ *     min_w 1/2 ||X w - y||^2 + lambda/2 ||w||^2
+ * through the linear system A w = b of eq. (4), in primal form
+ *     A = X^T X + lambda I,  b = X^T y            (eq. (2), m = d)
+ * or dual form
+ *     A = X X^T + lambda I,  b = y,  w = X^T alpha  (eq. (3), m = n),
+ * with the sketch-and-project method with momentum (Algorithm 2, Section 6.3):
+ *     r_S   = S_k^T r^k
+ *     delta = least-norm solution of (S_k^T A S_k) delta = r_S          (eq. (14))
+ *     w^{k+1} = (1 + beta_k) w^k - beta_k w^{k-1} - gamma_k S_k delta
+ *     r^{k+1} = (1 + beta_k) r^k - beta_k r^{k-1} - gamma_k A S_k delta  (eq. (53))
+ * starting from w^{-1} = w^0 = 0, r^{-1} = r^0 = -b, and stopping once
+ * ||r^k|| / ||r^0|| <= tol (the stopping rule of Section 3).
+ *
+ * Sketches (Section 4): Gaussian, Subsample, Count, SubCount, SRHT. Momentum
+ * (Section 8.1): none, constant, theoretical ("increasing", eq. (66)), heuristic
+ * (eq. (67)). Every step of an iteration runs in this library's CUDA kernels on
+ * one GPU.
+ *
+ * Conventions for every entry point:
+ *  - Return RS_OK (0) on success, another rs_status on failure; no C++ exception
+ *    crosses the ABI. A failure message is available from rs_last_error(ctx)
+ *    (or rs_last_error(NULL) for failures without a context, e.g. in rs_create).
+ *  - Pointers flagged "on_device" are CUDA device pointers of the context's device;
+ *    all others are host pointers. Input buffers are only read during the call
+ *    (the library copies what it keeps); output buffers are caller-owned and
+ *    written during the call.
+ *  - Row-major dense layouts; sizes are element counts.
+ *  - All work of a context is issued on the context's stream (rs_opts.cuda_stream,
+ *    or a stream the library creates). Calls on one context must not overlap.
+ */
+#ifndef RIDGESKETCH_H
+#define RIDGESKETCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rs_ctx rs_ctx; /* opaque; owned by the library until rs_destroy */
+
+typedef enum {
+  RS_OK = 0,
+  RS_EINVAL = 1,     /* invalid argument (null pointer, bad size, bad enum) */
+  RS_ENOMEM = 2,     /* device or host allocation failed */
+  RS_ECUDA = 3,      /* a CUDA runtime call failed */
+  RS_ENUMERIC = 4,   /* NaN or Inf in the residual */
+  RS_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+  RS_ENOTCONV = 6,   /* max_iters reached before tol; outputs are still valid */
+  RS_EUNSUPPORTED = 7 /* combination of options this build does not implement */
+} rs_status;
+
+typedef enum { RS_PRIMAL = 0, RS_DUAL = 1 } rs_form;
+
+/* Section 4.1 (Gaussian, Subsample), 4.2 (Count, SubCount), 4.3 (SRHT). */
+typedef enum {
+  RS_GAUSSIAN = 0,
+  RS_SUBSAMPLE = 1,
+  RS_COUNT = 2,
+  RS_SUBCOUNT = 3,
+  RS_SRHT = 4
+} rs_sketch;
+
+/* Section 8.1: none (gamma = 1, beta = 0), constant (gamma_c, beta_c),
+ * theoretical increasing momentum (eq. (66) with eqs. (38), (40)), heuristic
+ * (eq. (67): gamma = 1 with the theoretical beta_k). */
+typedef enum {
+  RS_MOM_NONE = 0,
+  RS_MOM_CONST = 1,
+  RS_MOM_THEORY = 2,
+  RS_MOM_HEURISTIC = 3
+} rs_mom_kind;
+
+typedef enum { RS_F64 = 0, RS_F32 = 1 } rs_dtype;
+
+typedef enum {
+  RS_PLAIN_FP64 = 0, /* every product and update in FP64 */
+  RS_MIXED = 1       /* A, A S in FP32 (A formed with FP32 accumulation), FP64
+                        vectors, FP64 true residual through X every refresh_every
+                        iterations and before declaring convergence */
+} rs_precision;
+
+typedef struct {
+  int32_t kind;        /* rs_mom_kind */
+  int32_t uncapped;    /* heuristic only: 1 = closed form of eq. (50) for all k */
+  double eta;          /* eta of eq. (66); default 0.995 */
+  double beta_switch;  /* beta at which eta switches to 1; default 0.5 */
+  double gamma_c;      /* constant mode step size; default 1.0 */
+  double beta_c;       /* constant mode momentum; default 0.5 */
+} rs_mom;
+
+/* Dense row-major n x d design matrix X (val, dtype) or CSR (reserved). */
+typedef struct {
+  int32_t is_csr;       /* must be 0 in this build (dense X) */
+  int32_t dtype;        /* rs_dtype of val */
+  int64_t n, d;         /* rows (samples), columns (features) */
+  int64_t nnz;          /* CSR only */
+  const void* val;      /* dense: n*d values, row-major */
+  const int64_t* rowptr;/* CSR only */
+  const int32_t* colidx;/* CSR only */
+  int32_t on_device;    /* 1 if val (and rowptr/colidx) are device pointers */
+} rs_matrix;
+
+typedef struct {
+  int32_t precision;     /* rs_precision; default RS_PLAIN_FP64 */
+  int32_t refresh_every; /* RS_MIXED: true-residual period in iterations; default 50 */
+  int64_t sub_s;         /* SubCount sample size s (multiple of tau, <= m); 0 = rule of
+                            Section 4.2: k = 10 if 10 tau <= m else floor(m/tau), s = k tau */
+  void* cuda_stream;     /* cudaStream_t to issue work on; NULL = library-owned stream */
+  int32_t device;        /* CUDA device ordinal; default 0 */
+  int32_t chol_fp64;     /* RS_MIXED only: 1 = factor S^T A S in FP64 (default), 0 = FP32 */
+  int64_t chunk;         /* iterations per device-side chunk (one CUDA graph replay);
+                            0 = refresh_every (mixed) or 64 (plain) */
+} rs_opts;
+
+/* Fill *o with the defaults listed above. */
+void rs_default_opts(rs_opts* o);
+/* Fill *m with the defaults of the given momentum kind (rs_mom_kind). */
+void rs_default_mom(rs_mom* m, int32_t kind);
+
+/*
+ * Create a solver context: copies X and y to the device, forms A and b
+ * (eqs. (2)-(4)) on the device, and prepares the buffers of the iteration.
+ *   X       design matrix (see rs_matrix); X is kept on the device for the dual
+ *           recovery w = X^T alpha and for RS_MIXED true residuals.
+ *   y       n targets (FP64); device pointer if y_on_device.
+ *   lambda  regularisation, > 0.
+ *   form    rs_form.
+ *   sketch  rs_sketch.
+ *   tau     sketch size, 1 <= tau <= m (SRHT: tau <= 2^ceil(log2 m)); 0 selects
+ *           ceil(m^(2/3)) (the rule of thumb of Section 8.1).
+ *   mom     momentum parameters (NULL = no momentum).
+ *   seed    seed of the counter-based sketch generator.
+ *   opts    options (NULL = defaults).
+ *   out     receives the context; NULL on failure.
+ */
+rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, double lambda,
+                    int32_t form, int32_t sketch, int64_t tau, const rs_mom* mom,
+                    uint64_t seed, const rs_opts* opts, rs_ctx** out);
+
+/*
+ * Run the iteration from w^0 = 0 (every call restarts) until
+ * ||r^k|| / ||r^0|| <= tol or k = max_iters.
+ *   w_out      d weights (primal w, or X^T alpha for the dual), caller-owned;
+ *              device pointer if w_on_device; may be NULL.
+ *   hist_out   max_iters + 1 host doubles: hist[k] = ||r^k|| / ||r^0|| for
+ *              k = 0..iters (RS_MIXED: entries at true-residual refreshes hold the
+ *              FP64 true residual); may be NULL.
+ *   iters_out  number of iterations run; may be NULL.
+ * Returns RS_ENOTCONV if max_iters was reached first (outputs valid), RS_ENUMERIC
+ * if the residual became NaN/Inf.
+ */
+rs_status rs_solve(rs_ctx* ctx, double tol, int64_t max_iters, double* w_out,
+                   int32_t w_on_device, double* hist_out, int64_t* iters_out);
+
+/* Free every resource of the context. NULL is accepted. */
+void rs_destroy(rs_ctx* ctx);
+
+/* Message of the last failure on ctx (ctx = NULL: last failure without a context).
+ * The string is owned by the library and valid until the next call on ctx. */
+const char* rs_last_error(const rs_ctx* ctx);
+
+/* Problem sizes of a context: m (system size), tau, s (SubCount sample size, else 0),
+ * k_sum (SubCount sum size, else 0), m_pad (SRHT padded size 2^ceil(log2 m), else 0). */
+rs_status rs_get_dims(const rs_ctx* ctx, int64_t* m, int64_t* tau, int64_t* s,
+                      int64_t* k_sum, int64_t* m_pad);
+
+/*
+ * Sketch of iteration k as drawn by the device generator (parity hook), host outputs:
+ *   RS_SUBSAMPLE: idx[j] = C_j, j < tau
+ *   RS_COUNT:     bucket[i], sign[i] for i < m
+ *   RS_SUBCOUNT:  idx[p] = C_p, sign[p], bucket[p] = p / k_sum for p < s
+ *   RS_SRHT:      idx[j] = C_j in [0, m_pad), j < tau; sign[i], i < m
+ *   RS_GAUSSIAN:  RS_EINVAL (use rs_dump_gaussian)
+ * Unused outputs may be NULL.
+ */
+rs_status rs_dump_sketch(rs_ctx* ctx, int64_t k, int32_t* idx, int8_t* sign, int32_t* bucket);
+
+/* Gaussian sketch S of iteration k as an m x tau row-major host array (parity hook). */
+rs_status rs_dump_gaussian(rs_ctx* ctx, int64_t k, double* S);
+
+/*
+ * Iteration state (w^k, w^{k-1}, r^k, r^{k-1}, k), host arrays of m doubles
+ * (for the dual form these are alpha and its residual). rs_set_state replaces the
+ * state so that rs_probe_step or rs_step continue from it (checkpoint/resume).
+ */
+rs_status rs_get_state(rs_ctx* ctx, double* w, double* w_prev, double* r, double* r_prev,
+                       int64_t* k);
+rs_status rs_set_state(rs_ctx* ctx, const double* w, const double* w_prev, const double* r,
+                       const double* r_prev, int64_t k);
+
+/*
+ * Parity hook: for the current state and iteration k, compute the sketched system
+ * M = S_k^T A S_k (tau x tau, row-major), r_S = S_k^T r^k and delta (eq. (14)) on
+ * the device and copy them to the host without changing the state. Any output may
+ * be NULL.
+ */
+rs_status rs_probe_step(rs_ctx* ctx, double* M, double* r_S, double* delta);
+
+/* Run n_iters iterations from the current state (no stopping test, no refresh);
+ * hist_out (n_iters entries, may be NULL) receives ||r^{k+1}|| / ||r^0||. */
+rs_status rs_step(rs_ctx* ctx, int64_t n_iters, double* hist_out);
+
+/* FP64 true relative residual ||A v - b|| / ||b|| of v (m host doubles: w for the
+ * primal, alpha for the dual), evaluated through X without forming A. */
+rs_status rs_true_residual(rs_ctx* ctx, const double* v, double* rel_out);
+
+/* Device time of the last rs_solve (ms), split into setup (forming A, b in
+ * rs_create) and iterations. Either pointer may be NULL. */
+rs_status rs_timings(const rs_ctx* ctx, double* setup_ms, double* solve_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RIDGESKETCH_H */

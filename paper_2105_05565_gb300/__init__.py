@@ -1,0 +1,282 @@
+"""GB300-native sketch-and-project ridge regression (arXiv 2105.05565, "RidgeSketch").
+
+Thin Python binding of the C ABI declared in ``include/ridgesketch.h``. Every
+step of the iteration runs in the CUDA kernels of ``libridgesketch.so``; this
+module only marshals arguments (numpy arrays or torch tensors, host or device)
+into the ABI calls. There is no CPU fallback: importing the solver without the
+built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["Solver", "RidgeSketch", "RSError", "lib", "SKETCHES", "MOMENTA"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libridgesketch.so")
+
+RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ENUMERIC, RS_ETIMEOUT, RS_ENOTCONV, RS_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["RS_OK", "RS_EINVAL", "RS_ENOMEM", "RS_ECUDA", "RS_ENUMERIC", "RS_ETIMEOUT",
+                "RS_ENOTCONV", "RS_EUNSUPPORTED"]
+SKETCHES = {"gaussian": 0, "subsample": 1, "count": 2, "subcount": 3, "srht": 4}
+MOMENTA = {"none": 0, "const": 1, "theory": 2, "heuristic": 3}
+FORMS = {"primal": 0, "dual": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+
+
+class RSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class Mom(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("uncapped", ctypes.c_int32), ("eta", ctypes.c_double),
+                ("beta_switch", ctypes.c_double), ("gamma_c", ctypes.c_double),
+                ("beta_c", ctypes.c_double)]
+
+
+class Matrix(ctypes.Structure):
+    _fields_ = [("is_csr", ctypes.c_int32), ("dtype", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("d", ctypes.c_int64), ("nnz", ctypes.c_int64), ("val", ctypes.c_void_p),
+                ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p),
+                ("on_device", ctypes.c_int32)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("refresh_every", ctypes.c_int32),
+                ("sub_s", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
+                ("device", ctypes.c_int32), ("chol_fp64", ctypes.c_int32), ("chunk", ctypes.c_int64)]
+
+
+_LIB = None
+_P = ctypes.c_void_p
+_I32, _I64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_SIGS = {
+    "rs_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "rs_default_mom": (None, [ctypes.POINTER(Mom), _I32]),
+    "rs_create": (_I32, [ctypes.POINTER(Matrix), _P, _I32, _D, _I32, _I32, _I64,
+                         ctypes.POINTER(Mom), ctypes.c_uint64, ctypes.POINTER(Opts),
+                         ctypes.POINTER(_P)]),
+    "rs_solve": (_I32, [_P, _D, _I64, _P, _I32, _P, ctypes.POINTER(_I64)]),
+    "rs_destroy": (None, [_P]),
+    "rs_last_error": (ctypes.c_char_p, [_P]),
+    "rs_get_dims": (_I32, [_P] + [ctypes.POINTER(_I64)] * 5),
+    "rs_dump_sketch": (_I32, [_P, _I64, _P, _P, _P]),
+    "rs_dump_gaussian": (_I32, [_P, _I64, _P]),
+    "rs_get_state": (_I32, [_P, _P, _P, _P, _P, ctypes.POINTER(_I64)]),
+    "rs_set_state": (_I32, [_P, _P, _P, _P, _P, _I64]),
+    "rs_probe_step": (_I32, [_P, _P, _P, _P]),
+    "rs_step": (_I32, [_P, _I64, _P]),
+    "rs_true_residual": (_I32, [_P, _P, ctypes.POINTER(_D)]),
+    "rs_timings": (_I32, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+}
+EXPORTED = tuple(_SIGS)
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`"
+                " (the solver has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _buf(x, dtype):
+    """(pointer, on_device, keepalive) of a contiguous array of ``dtype`` (numpy dtype)."""
+    if _is_torch(x):
+        import torch
+
+        tdt = {np.float64: torch.float64, np.float32: torch.float32}[np.dtype(dtype).type]
+        t = x.detach()
+        if t.dtype != tdt:
+            t = t.to(tdt)
+        t = t.contiguous()
+        return t.data_ptr(), int(t.is_cuda), t
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, 0, a
+
+
+def _default_stream(device):
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream(device).cuda_stream
+    except Exception:  # pragma: no cover
+        pass
+    return None
+
+
+class Solver:
+    """One ridge problem on the GPU (rs_create / rs_solve / rs_destroy).
+
+    X: (n, d) float32 or float64 array or tensor (host or CUDA); y: (n,) targets.
+    """
+
+    def __init__(self, X, y, lam, form="primal", sketch="count", tau=0, momentum="none", seed=0,
+                 precision="fp64", refresh_every=50, sub_s=0, chol_fp64=True, chunk=0,
+                 eta=0.995, beta_switch=0.5, gamma_c=1.0, beta_c=0.5, uncapped=False,
+                 device=0, stream=None):
+        L = lib()
+        self._ctx = None
+        xdt = np.float32 if str(getattr(X, "dtype", "")).endswith("float32") else np.float64
+        xp, xdev, self._xkeep = _buf(X, xdt)
+        yp, ydev, self._ykeep = _buf(y, np.float64)
+        n, d = (int(s) for s in X.shape)
+        mat = Matrix(0, 1 if xdt == np.float32 else 0, n, d, 0, xp, None, None, xdev)
+        mom = Mom()
+        L.rs_default_mom(ctypes.byref(mom), MOMENTA[momentum])
+        mom.eta, mom.beta_switch, mom.gamma_c, mom.beta_c = eta, beta_switch, gamma_c, beta_c
+        mom.uncapped = int(bool(uncapped))
+        opts = Opts()
+        L.rs_default_opts(ctypes.byref(opts))
+        opts.precision = PRECISIONS[precision]
+        opts.refresh_every = int(refresh_every)
+        opts.sub_s = int(sub_s)
+        opts.device = int(device)
+        opts.chol_fp64 = int(bool(chol_fp64))
+        opts.chunk = int(chunk)
+        st = stream if stream is not None else _default_stream(device)
+        opts.cuda_stream = st
+        ctx = _P()
+        status = L.rs_create(ctypes.byref(mat), yp, ydev, float(lam), FORMS[form], SKETCHES[sketch],
+                             int(tau), ctypes.byref(mom), ctypes.c_uint64(int(seed)),
+                             ctypes.byref(opts), ctypes.byref(ctx))
+        if status != RS_OK:
+            raise RSError(status, L.rs_last_error(None).decode())
+        self._ctx = ctx
+        self.n, self.d, self.form, self.sketch = n, d, form, sketch
+        dims = [_I64() for _ in range(5)]
+        L.rs_get_dims(ctx, *[ctypes.byref(v) for v in dims])
+        self.m, self.tau, self.s, self.k_sum, self.m_pad = (v.value for v in dims)
+
+    # -- helpers --
+    def _check(self, status, allow=(RS_OK,)):
+        if status not in allow:
+            raise RSError(status, lib().rs_last_error(self._ctx).decode())
+        return status
+
+    def close(self):
+        if self._ctx is not None:
+            lib().rs_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- API --
+    def solve(self, tol=1e-6, max_iters=10000, w_out=None):
+        """Run from w = 0 to tol or max_iters. Returns (w, hist, iters, converged).
+        ``w_out`` may be a CUDA float64 tensor of d entries to receive w on the device."""
+        hist = np.empty(int(max_iters) + 1)
+        iters = _I64()
+        if w_out is not None:
+            wp, wdev, _keep = w_out.data_ptr(), int(w_out.is_cuda), w_out
+            w_ret = w_out
+        else:
+            w_ret = np.empty(self.d)
+            wp, wdev = w_ret.ctypes.data, 0
+        st = self._check(lib().rs_solve(self._ctx, float(tol), int(max_iters), wp, wdev,
+                                        hist.ctypes.data, ctypes.byref(iters)),
+                         allow=(RS_OK, RS_ENOTCONV))
+        k = iters.value
+        return w_ret, hist[: k + 1].copy(), k, st == RS_OK
+
+    def dump_sketch(self, k):
+        cap = max(self.m, self.s, self.tau, 1)
+        idx = np.zeros(cap, np.int32)
+        sign = np.zeros(cap, np.int8)
+        bucket = np.zeros(cap, np.int32)
+        self._check(lib().rs_dump_sketch(self._ctx, int(k), idx.ctypes.data, sign.ctypes.data,
+                                         bucket.ctypes.data))
+        return idx, sign, bucket
+
+    def dump_gaussian(self, k):
+        S = np.empty((self.m, self.tau))
+        self._check(lib().rs_dump_gaussian(self._ctx, int(k), S.ctypes.data))
+        return S
+
+    def get_state(self):
+        m = self.m
+        w, wp, r, rp = (np.empty(m) for _ in range(4))
+        k = _I64()
+        self._check(lib().rs_get_state(self._ctx, w.ctypes.data, wp.ctypes.data, r.ctypes.data,
+                                       rp.ctypes.data, ctypes.byref(k)))
+        return w, wp, r, rp, k.value
+
+    def set_state(self, w, w_prev, r, r_prev, k):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (w, w_prev, r, r_prev)]
+        self._check(lib().rs_set_state(self._ctx, *[a.ctypes.data for a in arrs], int(k)))
+
+    def probe_step(self):
+        t = self.tau
+        M = np.empty((t, t))
+        rS = np.empty(t)
+        delta = np.empty(t)
+        self._check(lib().rs_probe_step(self._ctx, M.ctypes.data, rS.ctypes.data, delta.ctypes.data))
+        return M, rS, delta
+
+    def step(self, n_iters):
+        hist = np.empty(max(int(n_iters), 1))
+        self._check(lib().rs_step(self._ctx, int(n_iters), hist.ctypes.data))
+        return hist[: int(n_iters)]
+
+    def true_residual(self, v):
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        out = _D()
+        self._check(lib().rs_true_residual(self._ctx, v.ctypes.data, ctypes.byref(out)))
+        return out.value
+
+    def timings(self):
+        a, b = _D(), _D()
+        self._check(lib().rs_timings(self._ctx, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+
+class RidgeSketch:
+    """Estimator with the paper's interface (Appendix B): RidgeSketch(alpha,
+    algo_mode, solver, sketch_size).fit(X, y) -> coef_."""
+
+    def __init__(self, alpha=1.0, algo_mode="mom", solver="subsample", sketch_size=0, tol=1e-6,
+                 max_iter=10000, seed=0, precision="fp64", form=None):
+        self.alpha, self.algo_mode, self.solver, self.sketch_size = alpha, algo_mode, solver, sketch_size
+        self.tol, self.max_iter, self.seed, self.precision, self.form = tol, max_iter, seed, precision, form
+
+    def fit(self, X, y):
+        n, d = X.shape
+        form = self.form or ("primal" if d <= n else "dual")  # Section 2.1
+        mom = {"mom": "heuristic", "no_mom": "none", "auto": "heuristic"}.get(self.algo_mode, self.algo_mode)
+        with Solver(X, y, self.alpha, form=form, sketch=self.solver, tau=self.sketch_size,
+                    momentum=mom, seed=self.seed, precision=self.precision) as s:
+            w, hist, iters, conv = s.solve(self.tol, self.max_iter)
+        self.coef_, self.residuals_, self.n_iter_, self.converged_ = w, hist, iters, conv
+        return self
+
+    def predict(self, X):
+        return np.asarray(X) @ self.coef_

@@ -1,0 +1,920 @@
+// C ABI of the solver (include/ridgesketch.h): context, buffers, the chunked
+// device-side iteration loop (one CUDA graph replay per chunk) and parity hooks.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ridgesketch.h"
+#include "rs_kernels.cuh"
+
+using namespace rs;
+
+namespace {
+
+std::mutex g_err_mu;
+std::string g_err;
+
+void set_global_error(const std::string& s) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_err = s;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+constexpr int64_t kLdAlign = 128;     // row length padding of m-long rows (elements)
+constexpr int64_t kMaxSample = 8192;  // largest ordered sample drawn by one CTA
+constexpr int64_t kMaxCountTau = 2048;
+
+int64_t pow2_ceil(int64_t m) {
+  int64_t p = 1;
+  while (p < m) p <<= 1;
+  return p;
+}
+
+int64_t default_tau(int64_t m) {  // smallest t with t^3 >= m^2
+  int64_t t = (int64_t)llround(std::pow((double)m, 2.0 / 3.0));
+  if (t < 1) t = 1;
+  auto ge = [&](int64_t x) { return (long double)x * x * x >= (long double)m * m; };
+  while (!ge(t)) ++t;
+  while (t > 1 && ge(t - 1)) --t;
+  return t;
+}
+
+}  // namespace
+
+struct rs_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // problem
+  int form = 0, sketch = 0, precision = 0, chol_fp64 = 1, refresh_every = 50;
+  int64_t n = 0, d = 0, m = 0, tau = 0, s = 0, kk = 0, mp = 0, ld = 0, chunk = 64;
+  double lambda = 0.0;
+  uint64_t seed = 0;
+  rs_mom mom{};
+  int xdtype = RS_F64;
+  // device data
+  void* X = nullptr;
+  double* y = nullptr;
+  void* A = nullptr;     // m x ld, double (plain) or float (mixed)
+  double* b = nullptr;
+  double *w = nullptr, *wp = nullptr, *r = nullptr, *rp = nullptr, *u = nullptr;
+  void* SA = nullptr;    // tau x ld
+  void* S = nullptr;     // gaussian m x tau
+  double *M = nullptr, *rS = nullptr, *delta = nullptr;
+  void* chol_scratch = nullptr;
+  int32_t *perm = nullptr, *boff = nullptr;
+  int64_t perm_stride = 0, boff_stride = 0;
+  int64_t nslots = 0;
+  int32_t* err_flag = nullptr;
+  int32_t* ndropped = nullptr;
+  double *gam = nullptr, *bet = nullptr;
+  int64_t sched_len = 0;
+  double* hist = nullptr;
+  int64_t hist_len = 0;
+  double* partials = nullptr;
+  int64_t npartials = 0;
+  double *vn = nullptr, *vd = nullptr, *xt_part = nullptr, *rel_dev = nullptr;
+  Ctrl* ctrl = nullptr;
+  Ctrl* ctrl_h = nullptr;  // pinned
+  double* scal_h = nullptr;  // pinned scalar
+  double r0 = 0.0;
+  // graph of one chunk
+  cudaGraphExec_t graph = nullptr;
+  bool graph_refresh = false;
+  // timing
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double setup_ms = 0.0, solve_ms = 0.0;
+  std::string err;
+
+  bool mixed() const { return precision == RS_MIXED; }
+  size_t elem() const { return mixed() ? sizeof(float) : sizeof(double); }
+};
+
+#define CKC(ctx, call)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                      \
+      return (e_ == cudaErrorMemoryAllocation) ? RS_ENOMEM : RS_ECUDA;                       \
+    }                                                                                       \
+  } while (0)
+
+#define FAILC(ctx, code, msg)   \
+  do {                          \
+    (ctx)->err = (msg);         \
+    return (code);              \
+  } while (0)
+
+namespace {
+
+template <typename T>
+rs_status dalloc(rs_ctx* c, T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  CKC(c, cudaMalloc((void**)p, n * sizeof(T)));
+  return RS_OK;
+}
+
+void free_all(rs_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  void* ptrs[] = {c->X, c->y, c->A, c->b, c->w, c->wp, c->r, c->rp, c->u, c->SA, c->S, c->M,
+                  c->rS, c->delta, c->chol_scratch, c->perm, c->boff, c->err_flag, c->ndropped,
+                  c->gam, c->bet, c->hist, c->partials, c->vn, c->vd, c->xt_part, c->rel_dev,
+                  c->ctrl};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->ctrl_h) cudaFreeHost(c->ctrl_h);
+  if (c->scal_h) cudaFreeHost(c->scal_h);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+PlanView plan_view(const rs_ctx* c) {
+  PlanView p{};
+  if (c->sketch == RS_GAUSSIAN) return p;
+  p.perm = c->perm;
+  p.boff = (c->sketch == RS_SRHT) ? nullptr : c->boff;
+  p.perm_stride = c->perm_stride;
+  p.boff_stride = c->boff_stride;
+  return p;
+}
+
+template <typename T>
+RowsView<T> rows_view(const rs_ctx* c) {
+  RowsView<T> v{};
+  v.A = static_cast<const T*>(c->A);
+  v.lda = c->ld;
+  v.SA = (c->sketch == RS_SUBSAMPLE) ? nullptr : static_cast<const T*>(c->SA);
+  v.ldsa = c->ld;
+  return v;
+}
+
+// sketch plan of `nslots` consecutive iterations starting at k0_arg (< 0: ctrl->k)
+rs_status enqueue_gen(rs_ctx* c, int64_t k0_arg, int nslots) {
+  cudaStream_t st = c->stream;
+  switch (c->sketch) {
+    case RS_SUBSAMPLE:
+      CKC(c, launch_gen_sample(st, c->ctrl, k0_arg, nslots, c->seed, c->m, c->tau, 0, 1, c->tau,
+                               c->perm, c->perm_stride, c->boff, c->boff_stride, c->err_flag));
+      break;
+    case RS_SUBCOUNT:
+      CKC(c, launch_gen_sample(st, c->ctrl, k0_arg, nslots, c->seed, c->m, c->s, 1, c->kk, c->tau,
+                               c->perm, c->perm_stride, c->boff, c->boff_stride, c->err_flag));
+      break;
+    case RS_SRHT:
+      CKC(c, launch_gen_sample(st, c->ctrl, k0_arg, nslots, c->seed, c->mp, c->tau, 2, 1, c->tau,
+                               c->perm, c->perm_stride, nullptr, 0, c->err_flag));
+      break;
+    case RS_COUNT:
+      CKC(c, launch_gen_count(st, c->ctrl, k0_arg, nslots, c->seed, c->m, c->tau, c->perm,
+                              c->perm_stride, c->boff, c->boff_stride));
+      break;
+    default:
+      break;
+  }
+  return RS_OK;
+}
+
+// sketched system of the current (force = 0) or given (force = 1, k_arg) iteration:
+// S^T A, M, r_S
+template <typename T>
+rs_status enqueue_system(rs_ctx* c, int force, int64_t k_arg) {
+  cudaStream_t st = c->stream;
+  const PlanView plan = plan_view(c);
+  const T* A = static_cast<const T*>(c->A);
+  T* SA = static_cast<T*>(c->SA);
+  switch (c->sketch) {
+    case RS_SUBSAMPLE:
+      CKC(c, launch_msys_rows<T>(st, c->ctrl, force, plan, rows_view<T>(c), c->m, c->tau, c->r,
+                                 c->M, c->rS));
+      break;
+    case RS_COUNT:
+    case RS_SUBCOUNT:
+      CKC(c, launch_sa_rows<T>(st, c->ctrl, force, plan, A, c->ld, c->m, c->tau, SA, c->ld));
+      CKC(c, launch_msys_rows<T>(st, c->ctrl, force, plan, rows_view<T>(c), c->m, c->tau, c->r,
+                                 c->M, c->rS));
+      break;
+    case RS_GAUSSIAN: {
+      T* S = static_cast<T*>(c->S);
+      CKC(c, launch_gen_gauss<T>(st, c->ctrl, force ? k_arg : -1, c->seed, c->m, c->tau, S));
+      CKC(c, launch_gauss_sa<T>(st, c->ctrl, force, S, A, c->ld, c->m, c->tau, SA, c->ld));
+      CKC(c, launch_gauss_msys<T>(st, c->ctrl, force, S, SA, c->ld, c->m, c->tau, c->r, c->M,
+                                  c->rS));
+      break;
+    }
+    case RS_SRHT:
+      CKC(c, launch_srht_sa<T>(st, c->ctrl, force, k_arg, c->seed, plan, A, c->ld, c->m, c->mp,
+                               c->tau, SA, c->ld));
+      CKC(c, launch_srht_msys<T>(st, c->ctrl, force, k_arg, c->seed, plan, SA, c->ld, c->m, c->mp,
+                                 c->tau, c->r, c->M, c->rS));
+      break;
+  }
+  return RS_OK;
+}
+
+rs_status enqueue_solve_small(rs_ctx* c, int force, int64_t k_arg) {
+  cudaStream_t st = c->stream;
+  const bool bucket_rows = (c->sketch == RS_SUBSAMPLE || c->sketch == RS_COUNT ||
+                            c->sketch == RS_SUBCOUNT);
+  PlanView plan = bucket_rows ? plan_view(c) : PlanView{};
+  const bool f64 = !c->mixed() || c->chol_fp64;
+  if (f64)
+    CKC(c, launch_chol_solve<double>(st, c->ctrl, force, c->M, c->rS, c->tau,
+                                     static_cast<double*>(c->chol_scratch), c->delta, plan, c->u,
+                                     c->ndropped));
+  else
+    CKC(c, launch_chol_solve<float>(st, c->ctrl, force, c->M, c->rS, c->tau,
+                                    static_cast<float*>(c->chol_scratch), c->delta, plan, c->u,
+                                    c->ndropped));
+  if (c->sketch == RS_GAUSSIAN) {
+    if (c->mixed())
+      CKC(c, launch_gauss_u<float>(st, c->ctrl, force, static_cast<float*>(c->S), c->m, c->tau,
+                                   c->delta, c->u));
+    else
+      CKC(c, launch_gauss_u<double>(st, c->ctrl, force, static_cast<double*>(c->S), c->m, c->tau,
+                                    c->delta, c->u));
+  } else if (c->sketch == RS_SRHT) {
+    CKC(c, launch_srht_u(st, c->ctrl, force, k_arg, c->seed, plan_view(c), c->m, c->mp, c->tau,
+                         c->delta, c->u));
+  }
+  return RS_OK;
+}
+
+template <typename T>
+rs_status enqueue_iteration_t(rs_ctx* c) {
+  rs_status s = enqueue_system<T>(c, 0, -1);
+  if (s != RS_OK) return s;
+  s = enqueue_solve_small(c, 0, -1);
+  if (s != RS_OK) return s;
+  UpdateArgs a{};
+  a.gam = c->gam; a.bet = c->bet;
+  a.w = c->w; a.wp = c->wp; a.r = c->r; a.rp = c->rp; a.u = c->u;
+  a.delta = c->delta; a.partials = c->partials; a.hist = c->hist;
+  a.mixed = c->mixed();
+  CKC(c, launch_update<T>(c->stream, c->ctrl, plan_view(c), rows_view<T>(c), c->m, c->tau, a));
+  return RS_OK;
+}
+
+rs_status enqueue_iteration(rs_ctx* c) {
+  return c->mixed() ? enqueue_iteration_t<float>(c) : enqueue_iteration_t<double>(c);
+}
+
+// true residual through X into vn / vd; v is the current iterate vector (m)
+rs_status enqueue_true_av(rs_ctx* c, const double* v, const int32_t* stop) {
+  cudaStream_t st = c->stream;
+  // primal: A w = X^T (X w) + lambda w; dual: A a = X (X^T a) + lambda a
+  if (c->xdtype == RS_F32) {
+    const float* X = static_cast<const float*>(c->X);
+    if (c->form == RS_PRIMAL) {
+      CKC(c, launch_x_v<float>(st, X, c->n, c->d, v, c->vn, stop));
+      CKC(c, launch_xt_v<float>(st, X, c->n, c->d, c->vn, c->vd, c->xt_part, stop));
+    } else {
+      CKC(c, launch_xt_v<float>(st, X, c->n, c->d, v, c->vd, c->xt_part, stop));
+      CKC(c, launch_x_v<float>(st, X, c->n, c->d, c->vd, c->vn, stop));
+    }
+  } else {
+    const double* X = static_cast<const double*>(c->X);
+    if (c->form == RS_PRIMAL) {
+      CKC(c, launch_x_v<double>(st, X, c->n, c->d, v, c->vn, stop));
+      CKC(c, launch_xt_v<double>(st, X, c->n, c->d, c->vn, c->vd, c->xt_part, stop));
+    } else {
+      CKC(c, launch_xt_v<double>(st, X, c->n, c->d, v, c->vd, c->xt_part, stop));
+      CKC(c, launch_x_v<double>(st, X, c->n, c->d, c->vd, c->vn, stop));
+    }
+  }
+  return RS_OK;
+}
+
+const double* av_out(const rs_ctx* c) { return c->form == RS_PRIMAL ? c->vd : c->vn; }
+
+rs_status enqueue_refresh(rs_ctx* c) {
+  rs_status s = enqueue_true_av(c, c->w, &c->ctrl->stop);
+  if (s != RS_OK) return s;
+  CKC(c, launch_refresh_finish(c->stream, c->ctrl, 1, c->m, av_out(c), c->w, c->b, c->lambda, c->r,
+                               c->rp, c->partials, c->hist, nullptr));
+  return RS_OK;
+}
+
+rs_status enqueue_chunk(rs_ctx* c, bool with_refresh) {
+  CKC(c, launch_chunk_begin(c->stream, c->ctrl));
+  rs_status s = enqueue_gen(c, -1, (int)c->nslots);
+  if (s != RS_OK) return s;
+  for (int64_t i = 0; i < c->chunk; ++i) {
+    s = enqueue_iteration(c);
+    if (s != RS_OK) return s;
+  }
+  if (with_refresh) return enqueue_refresh(c);
+  return RS_OK;
+}
+
+rs_status build_graph(rs_ctx* c, bool with_refresh) {
+  if (c->graph && c->graph_refresh == with_refresh) return RS_OK;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  CKC(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+  rs_status s = enqueue_chunk(c, with_refresh);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (s != RS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) FAILC(c, RS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) FAILC(c, RS_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  c->graph_refresh = with_refresh;
+  return RS_OK;
+}
+
+rs_status ensure_schedule(rs_ctx* c, int64_t K) {
+  if (K <= c->sched_len && K + 1 <= c->hist_len) return RS_OK;
+  const int64_t L = std::max<int64_t>(K, 1024);
+  if (c->gam) cudaFree(c->gam);
+  if (c->bet) cudaFree(c->bet);
+  if (c->hist) cudaFree(c->hist);
+  c->gam = c->bet = c->hist = nullptr;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  rs_status s;
+  if ((s = dalloc(c, &c->gam, L)) != RS_OK) return s;
+  if ((s = dalloc(c, &c->bet, L)) != RS_OK) return s;
+  if ((s = dalloc(c, &c->hist, L + 1)) != RS_OK) return s;
+  // momentum parameters (Section 8.1), eqs. (38), (40), (50), (66), (67)
+  std::vector<double> g(L), bt(L);
+  const rs_mom& mo = c->mom;
+  if (mo.kind == RS_MOM_NONE) {
+    for (int64_t k = 0; k < L; ++k) { g[k] = 1.0; bt[k] = 0.0; }
+  } else if (mo.kind == RS_MOM_CONST) {
+    for (int64_t k = 0; k < L; ++k) { g[k] = mo.gamma_c; bt[k] = mo.beta_c; }
+  } else if (mo.kind == RS_MOM_HEURISTIC && mo.uncapped) {
+    for (int64_t k = 0; k < L; ++k) {
+      g[k] = 1.0;
+      bt[k] = 1.0 - (2.0 - mo.eta) / (((double)k + 1.0) * (1.0 - mo.eta) + 1.0);
+    }
+  } else {
+    double acc = 0.0, eta_k = mo.eta;
+    for (int64_t k = 0; k < L; ++k) {
+      const double zeta_k = acc / eta_k;
+      const double acc_next = acc + eta_k * (1.0 - eta_k);
+      const double zeta_next = acc_next / eta_k;
+      const double gk = eta_k / (1.0 + zeta_next);
+      const double bk = zeta_k / (1.0 + zeta_next);
+      g[k] = (mo.kind == RS_MOM_THEORY) ? gk : 1.0;
+      bt[k] = bk;
+      acc = acc_next;
+      if (bk >= mo.beta_switch) eta_k = 1.0;
+    }
+  }
+  CKC(c, cudaMemcpy(c->gam, g.data(), L * sizeof(double), cudaMemcpyHostToDevice));
+  CKC(c, cudaMemcpy(c->bet, bt.data(), L * sizeof(double), cudaMemcpyHostToDevice));
+  c->sched_len = L;
+  c->hist_len = L + 1;
+  return RS_OK;
+}
+
+rs_status read_ctrl(rs_ctx* c) {
+  CKC(c, cudaMemcpyAsync(c->ctrl_h, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+  CKC(c, cudaStreamSynchronize(c->stream));
+  return RS_OK;
+}
+
+rs_status write_ctrl(rs_ctx* c) {
+  CKC(c, cudaMemcpyAsync(c->ctrl, c->ctrl_h, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
+  return RS_OK;
+}
+
+// run chunks until the device says stop; max_chunks bounds the host loop
+rs_status run_loop(rs_ctx* c, bool with_refresh, int64_t max_chunks) {
+  rs_status s = build_graph(c, with_refresh);
+  if (s != RS_OK) return s;
+  for (int64_t q = 0; q < max_chunks; ++q) {
+    CKC(c, cudaGraphLaunch(c->graph, c->stream));
+    if ((s = read_ctrl(c)) != RS_OK) return s;
+    if (c->ctrl_h->stop) return RS_OK;
+  }
+  return RS_OK;
+}
+
+rs_status copy_out_w(rs_ctx* c, double* w_out, int32_t on_device) {
+  if (!w_out) return RS_OK;
+  const double* src = c->w;
+  if (c->form == RS_DUAL) {  // w = X^T alpha (eq. (3))
+    if (c->xdtype == RS_F32)
+      CKC(c, launch_xt_v<float>(c->stream, static_cast<const float*>(c->X), c->n, c->d, c->w, c->vd,
+                                c->xt_part));
+    else
+      CKC(c, launch_xt_v<double>(c->stream, static_cast<const double*>(c->X), c->n, c->d, c->w,
+                                 c->vd, c->xt_part));
+    src = c->vd;
+  }
+  CKC(c, cudaMemcpyAsync(w_out, src, c->d * sizeof(double),
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  return RS_OK;
+}
+
+rs_status true_rel(rs_ctx* c, const double* v_dev, double* rel) {
+  rs_status s = enqueue_true_av(c, v_dev, nullptr);
+  if (s != RS_OK) return s;
+  CKC(c, launch_refresh_finish(c->stream, c->ctrl, 0, c->m, av_out(c), v_dev, c->b, c->lambda,
+                               nullptr, nullptr, c->partials, nullptr, c->rel_dev));
+  CKC(c, cudaMemcpyAsync(c->scal_h, c->rel_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CKC(c, cudaStreamSynchronize(c->stream));
+  *rel = *c->scal_h;
+  return RS_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// public API
+// ===========================================================================
+extern "C" {
+
+void rs_default_opts(rs_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = RS_PLAIN_FP64;
+  o->refresh_every = 50;
+  o->sub_s = 0;
+  o->cuda_stream = nullptr;
+  o->device = 0;
+  o->chol_fp64 = 1;
+  o->chunk = 0;
+}
+
+void rs_default_mom(rs_mom* m, int32_t kind) {
+  if (!m) return;
+  std::memset(m, 0, sizeof(*m));
+  m->kind = kind;
+  m->uncapped = 0;
+  m->eta = 0.995;
+  m->beta_switch = 0.5;
+  m->gamma_c = 1.0;
+  m->beta_c = 0.5;
+}
+
+const char* rs_last_error(const rs_ctx* ctx) {
+  if (ctx) return ctx->err.c_str();
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  return g_err.c_str();
+}
+
+rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, double lambda,
+                    int32_t form, int32_t sketch, int64_t tau, const rs_mom* mom, uint64_t seed,
+                    const rs_opts* opts, rs_ctx** out) {
+  if (out) *out = nullptr;
+  if (!X || !y || !out) { set_global_error("rs_create: null argument"); return RS_EINVAL; }
+  if (X->is_csr) { set_global_error("rs_create: CSR input is not supported by rs_create"); return RS_EUNSUPPORTED; }
+  if (X->n <= 0 || X->d <= 0 || !X->val) { set_global_error("rs_create: empty X"); return RS_EINVAL; }
+  if (X->dtype != RS_F64 && X->dtype != RS_F32) { set_global_error("rs_create: bad dtype"); return RS_EINVAL; }
+  if (!(lambda > 0.0) || !std::isfinite(lambda)) { set_global_error("rs_create: lambda must be > 0"); return RS_EINVAL; }
+  if (form != RS_PRIMAL && form != RS_DUAL) { set_global_error("rs_create: bad form"); return RS_EINVAL; }
+  if (sketch < RS_GAUSSIAN || sketch > RS_SRHT) { set_global_error("rs_create: bad sketch"); return RS_EINVAL; }
+  rs_opts o;
+  rs_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.precision != RS_PLAIN_FP64 && o.precision != RS_MIXED) { set_global_error("rs_create: bad precision"); return RS_EINVAL; }
+  rs_mom mo;
+  rs_default_mom(&mo, RS_MOM_NONE);
+  if (mom) mo = *mom;
+  if (mo.kind < RS_MOM_NONE || mo.kind > RS_MOM_HEURISTIC) { set_global_error("rs_create: bad momentum kind"); return RS_EINVAL; }
+  if ((mo.kind == RS_MOM_THEORY || mo.kind == RS_MOM_HEURISTIC) && !(mo.eta > 0.0 && mo.eta <= 1.0)) {
+    set_global_error("rs_create: eta must be in (0, 1]");
+    return RS_EINVAL;
+  }
+
+  rs_ctx* c = new (std::nothrow) rs_ctx();
+  if (!c) { set_global_error("rs_create: out of host memory"); return RS_ENOMEM; }
+  auto fail = [&](rs_status s) {
+    set_global_error(c->err);
+    free_all(c);
+    delete c;
+    return s;
+  };
+  c->device = o.device;
+  DeviceGuard dg(c->device);
+  c->form = form;
+  c->sketch = sketch;
+  c->precision = o.precision;
+  c->chol_fp64 = o.chol_fp64 ? 1 : 0;
+  c->refresh_every = o.refresh_every > 0 ? o.refresh_every : 50;
+  c->n = X->n;
+  c->d = X->d;
+  c->m = (form == RS_PRIMAL) ? X->d : X->n;
+  c->lambda = lambda;
+  c->seed = seed;
+  c->mom = mo;
+  c->xdtype = X->dtype;
+  const int64_t m = c->m;
+  c->tau = tau > 0 ? tau : default_tau(m);
+  c->ld = round_up(m, kLdAlign);
+  if (c->tau > m && sketch != RS_SRHT) { c->err = "rs_create: tau must be <= m"; return fail(RS_EINVAL); }
+  if (sketch == RS_SRHT) {
+    c->mp = pow2_ceil(m);
+    if (c->mp > srht_max_pad(8)) { c->err = "rs_create: SRHT needs 2^ceil(log2 m) <= 16384"; return fail(RS_EUNSUPPORTED); }
+    if (c->tau > c->mp) { c->err = "rs_create: SRHT needs tau <= 2^ceil(log2 m)"; return fail(RS_EINVAL); }
+  }
+  if (sketch == RS_SUBCOUNT) {
+    if (o.sub_s > 0) {
+      if (o.sub_s % c->tau != 0 || o.sub_s > m || o.sub_s < c->tau) { c->err = "rs_create: SubCount s must be a multiple of tau in [tau, m]"; return fail(RS_EINVAL); }
+      c->s = o.sub_s;
+      c->kk = o.sub_s / c->tau;
+    } else {
+      c->kk = (10 * c->tau <= m) ? 10 : m / c->tau;
+      c->s = c->kk * c->tau;
+    }
+  }
+  const int64_t sample_n = (sketch == RS_SUBCOUNT) ? c->s : c->tau;
+  if ((sketch == RS_SUBSAMPLE || sketch == RS_SUBCOUNT || sketch == RS_SRHT) && sample_n > kMaxSample) {
+    c->err = "rs_create: sample size above 8192 is not supported";
+    return fail(RS_EUNSUPPORTED);
+  }
+  if (sketch == RS_COUNT && c->tau > kMaxCountTau) { c->err = "rs_create: count sketch tau above 2048 is not supported"; return fail(RS_EUNSUPPORTED); }
+  if (c->tau > 8192) { c->err = "rs_create: tau above 8192 is not supported"; return fail(RS_EUNSUPPORTED); }
+
+  if (o.cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(o.cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { c->err = "rs_create: stream"; return fail(RS_ECUDA); }
+    c->own_stream = true;
+  }
+  c->chunk = o.chunk > 0 ? o.chunk : (c->mixed() ? c->refresh_every : 64);
+  if (c->mixed() && c->chunk != c->refresh_every) c->chunk = c->refresh_every;
+  c->nslots = c->chunk;
+  cudaStream_t st = c->stream;
+  rs_status s;
+#define TRY(expr) do { if ((s = (expr)) != RS_OK) return fail(s); } while (0)
+#define TRYC(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { c->err = std::string(#call) + ": " + cudaGetErrorString(e_); return fail(e_ == cudaErrorMemoryAllocation ? RS_ENOMEM : RS_ECUDA); } } while (0)
+  TRYC(cudaEventCreate(&c->ev0));
+  TRYC(cudaEventCreate(&c->ev1));
+  TRYC(cudaMallocHost((void**)&c->ctrl_h, sizeof(Ctrl)));
+  TRYC(cudaMallocHost((void**)&c->scal_h, sizeof(double)));
+  TRY(dalloc(c, &c->ctrl, 1));
+  std::memset(c->ctrl_h, 0, sizeof(Ctrl));
+  c->ctrl_h->r0 = 1.0;
+  TRYC(cudaMemcpyAsync(c->ctrl, c->ctrl_h, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+
+  // X, y
+  const size_t xel = X->dtype == RS_F32 ? 4 : 8;
+  const size_t xbytes = (size_t)X->n * X->d * xel;
+  TRYC(cudaMalloc(&c->X, xbytes));
+  TRYC(cudaMemcpyAsync(c->X, X->val, xbytes, X->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  TRY(dalloc(c, &c->y, c->n));
+  TRYC(cudaMemcpyAsync(c->y, y, c->n * sizeof(double), y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  // scratch of the X products
+  TRY(dalloc(c, &c->vn, c->n));
+  TRY(dalloc(c, &c->vd, c->d));
+  TRY(dalloc(c, &c->xt_part, xt_part_elems(c->n, c->d)));
+  TRY(dalloc(c, &c->rel_dev, 1));
+  // A and b (eqs. (2)-(4))
+  TRYC(cudaMalloc(&c->A, (size_t)m * c->ld * c->elem()));
+  TRYC(cudaMemsetAsync(c->A, 0, (size_t)m * c->ld * c->elem(), st));
+  TRY(dalloc(c, &c->b, m));
+  TRYC(cudaEventRecord(c->ev0, st));
+  const int dual = (form == RS_DUAL);
+  if (X->dtype == RS_F32) {
+    const float* Xf = static_cast<const float*>(c->X);
+    if (c->mixed()) TRYC((launch_form_A<float, float>(st, Xf, c->n, c->d, dual, lambda, static_cast<float*>(c->A), c->ld)));
+    else TRYC((launch_form_A<float, double>(st, Xf, c->n, c->d, dual, lambda, static_cast<double*>(c->A), c->ld)));
+    if (!dual) TRYC(launch_xt_v<float>(st, Xf, c->n, c->d, c->y, c->b, c->xt_part));
+  } else {
+    const double* Xd = static_cast<const double*>(c->X);
+    if (c->mixed()) TRYC((launch_form_A<double, float>(st, Xd, c->n, c->d, dual, lambda, static_cast<float*>(c->A), c->ld)));
+    else TRYC((launch_form_A<double, double>(st, Xd, c->n, c->d, dual, lambda, static_cast<double*>(c->A), c->ld)));
+    if (!dual) TRYC(launch_xt_v<double>(st, Xd, c->n, c->d, c->y, c->b, c->xt_part));
+  }
+  if (dual) TRYC(cudaMemcpyAsync(c->b, c->y, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  TRYC(cudaEventRecord(c->ev1, st));
+  // iteration buffers
+  TRY(dalloc(c, &c->w, m));
+  TRY(dalloc(c, &c->wp, m));
+  TRY(dalloc(c, &c->r, m));
+  TRY(dalloc(c, &c->rp, m));
+  TRY(dalloc(c, &c->u, m));
+  TRYC(cudaMemsetAsync(c->u, 0, m * sizeof(double), st));
+  TRY(dalloc(c, &c->M, (size_t)c->tau * c->tau));
+  TRY(dalloc(c, &c->rS, c->tau));
+  TRY(dalloc(c, &c->delta, c->tau));
+  TRY(dalloc(c, &c->err_flag, 1));
+  TRY(dalloc(c, &c->ndropped, 1));
+  TRYC(cudaMemsetAsync(c->err_flag, 0, sizeof(int32_t), st));
+  TRYC(cudaMemsetAsync(c->ndropped, 0, sizeof(int32_t), st));
+  {
+    const bool f64 = !c->mixed() || c->chol_fp64;
+    const size_t ne = f64 ? chol_scratch_elems<double>(c->tau) : chol_scratch_elems<float>(c->tau);
+    TRYC(cudaMalloc(&c->chol_scratch, ne * (f64 ? 8 : 4)));
+  }
+  if (sketch != RS_SUBSAMPLE) {
+    TRYC(cudaMalloc(&c->SA, (size_t)c->tau * c->ld * c->elem()));
+    TRYC(cudaMemsetAsync(c->SA, 0, (size_t)c->tau * c->ld * c->elem(), st));
+  }
+  if (sketch == RS_GAUSSIAN) TRYC(cudaMalloc(&c->S, (size_t)m * c->tau * c->elem()));
+  if (sketch != RS_GAUSSIAN) {
+    c->perm_stride = (sketch == RS_COUNT) ? m : (sketch == RS_SUBCOUNT ? c->s : c->tau);
+    c->boff_stride = c->tau + 1;
+    TRY(dalloc(c, &c->perm, (size_t)c->perm_stride * c->nslots));
+    TRY(dalloc(c, &c->boff, (size_t)c->boff_stride * c->nslots));
+  }
+  c->npartials = std::max<int64_t>(update_blocks(m), 256);
+  TRY(dalloc(c, &c->partials, c->npartials));
+  TRY(ensure_schedule(c, 1024));
+  // ||b|| = ||r^0||
+  {
+    // ||b||: evaluate v + lambda x - b with v = x = 0 (u is all zeros here), r0 = 1
+    double* zeros = c->u;
+    TRYC(launch_refresh_finish(st, c->ctrl, 0, m, zeros, zeros, c->b, 0.0, nullptr, nullptr,
+                               c->partials, nullptr, c->rel_dev));
+    TRYC(cudaMemcpyAsync(c->scal_h, c->rel_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    TRYC(cudaStreamSynchronize(st));
+    c->r0 = *c->scal_h;  // r0 was 1 in ctrl, so rel = ||b||
+  }
+  float ms = 0.f;
+  TRYC(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  c->setup_ms = ms;
+#undef TRY
+#undef TRYC
+  *out = c;
+  return RS_OK;
+}
+
+void rs_destroy(rs_ctx* ctx) {
+  if (!ctx) return;
+  {
+    DeviceGuard dg(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_all(ctx);
+  }
+  delete ctx;
+}
+
+rs_status rs_get_dims(const rs_ctx* c, int64_t* m, int64_t* tau, int64_t* s, int64_t* k_sum,
+                      int64_t* m_pad) {
+  if (!c) return RS_EINVAL;
+  if (m) *m = c->m;
+  if (tau) *tau = c->tau;
+  if (s) *s = c->s;
+  if (k_sum) *k_sum = c->kk;
+  if (m_pad) *m_pad = c->mp;
+  return RS_OK;
+}
+
+rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int32_t w_on_device,
+                   double* hist_out, int64_t* iters_out) {
+  if (!c) { set_global_error("rs_solve: null context"); return RS_EINVAL; }
+  if (max_iters < 0 || !(tol >= 0.0)) FAILC(c, RS_EINVAL, "rs_solve: bad tol or max_iters");
+  DeviceGuard dg(c->device);
+  cudaStream_t st = c->stream;
+  rs_status s;
+  if ((s = ensure_schedule(c, std::max<int64_t>(max_iters, 1))) != RS_OK) return s;
+  CKC(c, launch_init_state(st, c->m, c->b, c->w, c->wp, c->r, c->rp, c->u));
+  const double h0 = c->r0 > 0.0 ? 1.0 : 0.0;
+  CKC(c, cudaMemcpyAsync(c->hist, &h0, sizeof(double), cudaMemcpyHostToDevice, st));
+  CKC(c, cudaStreamSynchronize(st));
+  int64_t iters = 0;
+  rs_status result = RS_OK;
+  float ms = 0.f;
+  if (c->r0 == 0.0 || max_iters == 0) {
+    iters = 0;
+    if (c->r0 != 0.0 && tol < 1.0) result = RS_ENOTCONV;
+  } else {
+    Ctrl* h = c->ctrl_h;
+    std::memset(h, 0, sizeof(Ctrl));
+    h->max_iters = max_iters;
+    h->r0 = c->r0;
+    h->tol = tol;
+    if ((s = write_ctrl(c)) != RS_OK) return s;
+    CKC(c, cudaEventRecord(c->ev0, st));
+    const int64_t max_chunks = (max_iters + c->chunk - 1) / c->chunk + 2;
+    if ((s = run_loop(c, c->mixed(), max_chunks)) != RS_OK) return s;
+    CKC(c, cudaEventRecord(c->ev1, st));
+    CKC(c, cudaEventSynchronize(c->ev1));
+    CKC(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    iters = h->k;
+    int32_t gen_err = 0;
+    CKC(c, cudaMemcpy(&gen_err, c->err_flag, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (gen_err) FAILC(c, RS_ECUDA, "sketch generation: sample threshold search failed");
+    if (h->status == RS_ENUMERIC) {
+      result = RS_ENUMERIC;
+      c->err = "rs_solve: NaN or Inf in the residual";
+    } else {
+      double last = 0.0;
+      if (c->mixed()) {  // final FP64 residual check through X
+        if ((s = true_rel(c, c->w, &last)) != RS_OK) return s;
+        CKC(c, cudaMemcpy(c->hist + iters, &last, sizeof(double), cudaMemcpyHostToDevice));
+      } else {
+        CKC(c, cudaMemcpy(&last, c->hist + iters, sizeof(double), cudaMemcpyDeviceToHost));
+      }
+      if (!(last <= tol)) result = RS_ENOTCONV;
+    }
+  }
+  c->solve_ms = ms;
+  if ((s = copy_out_w(c, w_out, w_on_device)) != RS_OK) return s;
+  if (hist_out) CKC(c, cudaMemcpyAsync(hist_out, c->hist, (iters + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CKC(c, cudaStreamSynchronize(st));
+  if (iters_out) *iters_out = iters;
+  return result;
+}
+
+rs_status rs_dump_sketch(rs_ctx* c, int64_t k, int32_t* idx, int8_t* sign, int32_t* bucket) {
+  if (!c || k < 0) return RS_EINVAL;
+  if (c->sketch == RS_GAUSSIAN) FAILC(c, RS_EINVAL, "rs_dump_sketch: use rs_dump_gaussian");
+  DeviceGuard dg(c->device);
+  rs_status s = enqueue_gen(c, k, 1);
+  if (s != RS_OK) return s;
+  std::vector<int32_t> perm(c->perm_stride), boff(c->boff_stride);
+  CKC(c, cudaMemcpyAsync(perm.data(), c->perm, perm.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+  CKC(c, cudaMemcpyAsync(boff.data(), c->boff, boff.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+  CKC(c, cudaStreamSynchronize(c->stream));
+  int32_t gen_err = 0;
+  CKC(c, cudaMemcpy(&gen_err, c->err_flag, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (gen_err) FAILC(c, RS_ECUDA, "sketch generation: sample threshold search failed");
+  auto row = [](int32_t e) { return e & 0x7FFFFFFF; };
+  switch (c->sketch) {
+    case RS_SUBSAMPLE:
+      if (idx) for (int64_t j = 0; j < c->tau; ++j) idx[j] = row(perm[j]);
+      break;
+    case RS_SUBCOUNT:
+      for (int64_t p = 0; p < c->s; ++p) {
+        if (idx) idx[p] = row(perm[p]);
+        if (sign) sign[p] = perm[p] < 0 ? -1 : 1;
+        if (bucket) bucket[p] = (int32_t)(p / c->kk);
+      }
+      break;
+    case RS_SRHT:
+      if (idx) for (int64_t j = 0; j < c->tau; ++j) idx[j] = row(perm[j]);
+      if (sign)
+        for (int64_t i = 0; i < c->m; ++i)
+          sign[i] = draw_neg(draw_k(iter_key(c->seed, k), 1, (uint64_t)i)) ? -1 : 1;
+      break;
+    case RS_COUNT:
+      for (int64_t b = 0; b < c->tau; ++b)
+        for (int32_t t = boff[b]; t < boff[b + 1]; ++t) {
+          const int32_t i = row(perm[t]);
+          if (i < 0 || i >= c->m) FAILC(c, RS_ECUDA, "rs_dump_sketch: corrupt count plan");
+          if (bucket) bucket[i] = (int32_t)b;
+          if (sign) sign[i] = perm[t] < 0 ? -1 : 1;
+        }
+      if (idx) for (int64_t t = 0; t < c->m; ++t) idx[t] = row(perm[t]);
+      break;
+  }
+  return RS_OK;
+}
+
+rs_status rs_dump_gaussian(rs_ctx* c, int64_t k, double* S) {
+  if (!c || k < 0 || !S) return RS_EINVAL;
+  if (c->sketch != RS_GAUSSIAN) FAILC(c, RS_EINVAL, "rs_dump_gaussian: not a Gaussian sketch");
+  DeviceGuard dg(c->device);
+  const size_t n = (size_t)c->m * c->tau;
+  if (c->mixed()) {
+    CKC(c, launch_gen_gauss<float>(c->stream, c->ctrl, k, c->seed, c->m, c->tau, static_cast<float*>(c->S)));
+    std::vector<float> tmp(n);
+    CKC(c, cudaMemcpyAsync(tmp.data(), c->S, n * 4, cudaMemcpyDeviceToHost, c->stream));
+    CKC(c, cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i < n; ++i) S[i] = tmp[i];
+  } else {
+    CKC(c, launch_gen_gauss<double>(c->stream, c->ctrl, k, c->seed, c->m, c->tau, static_cast<double*>(c->S)));
+    CKC(c, cudaMemcpyAsync(S, c->S, n * 8, cudaMemcpyDeviceToHost, c->stream));
+    CKC(c, cudaStreamSynchronize(c->stream));
+  }
+  return RS_OK;
+}
+
+rs_status rs_get_state(rs_ctx* c, double* w, double* w_prev, double* r, double* r_prev, int64_t* k) {
+  if (!c) return RS_EINVAL;
+  DeviceGuard dg(c->device);
+  rs_status s = read_ctrl(c);
+  if (s != RS_OK) return s;
+  const size_t bytes = c->m * sizeof(double);
+  if (w) CKC(c, cudaMemcpyAsync(w, c->w, bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (w_prev) CKC(c, cudaMemcpyAsync(w_prev, c->wp, bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (r) CKC(c, cudaMemcpyAsync(r, c->r, bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (r_prev) CKC(c, cudaMemcpyAsync(r_prev, c->rp, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CKC(c, cudaStreamSynchronize(c->stream));
+  if (k) *k = c->ctrl_h->k;
+  return RS_OK;
+}
+
+rs_status rs_set_state(rs_ctx* c, const double* w, const double* w_prev, const double* r,
+                       const double* r_prev, int64_t k) {
+  if (!c || !w || !w_prev || !r || !r_prev || k < 0) return RS_EINVAL;
+  DeviceGuard dg(c->device);
+  const size_t bytes = c->m * sizeof(double);
+  CKC(c, cudaMemcpyAsync(c->w, w, bytes, cudaMemcpyHostToDevice, c->stream));
+  CKC(c, cudaMemcpyAsync(c->wp, w_prev, bytes, cudaMemcpyHostToDevice, c->stream));
+  CKC(c, cudaMemcpyAsync(c->r, r, bytes, cudaMemcpyHostToDevice, c->stream));
+  CKC(c, cudaMemcpyAsync(c->rp, r_prev, bytes, cudaMemcpyHostToDevice, c->stream));
+  CKC(c, cudaMemsetAsync(c->u, 0, bytes, c->stream));
+  std::memset(c->ctrl_h, 0, sizeof(Ctrl));
+  c->ctrl_h->k = k;
+  c->ctrl_h->k0 = k;
+  c->ctrl_h->max_iters = INT64_MAX;
+  c->ctrl_h->r0 = c->r0 > 0.0 ? c->r0 : 1.0;
+  c->ctrl_h->no_stop = 1;
+  rs_status s = write_ctrl(c);
+  if (s != RS_OK) return s;
+  CKC(c, cudaStreamSynchronize(c->stream));
+  return RS_OK;
+}
+
+rs_status rs_probe_step(rs_ctx* c, double* M, double* r_S, double* delta) {
+  if (!c) return RS_EINVAL;
+  DeviceGuard dg(c->device);
+  rs_status s = read_ctrl(c);
+  if (s != RS_OK) return s;
+  const int64_t k = c->ctrl_h->k;
+  if ((s = enqueue_gen(c, k, 1)) != RS_OK) return s;
+  s = c->mixed() ? enqueue_system<float>(c, 1, k) : enqueue_system<double>(c, 1, k);
+  if (s != RS_OK) return s;
+  if ((s = enqueue_solve_small(c, 1, k)) != RS_OK) return s;
+  const size_t t = c->tau;
+  if (M) CKC(c, cudaMemcpyAsync(M, c->M, t * t * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (r_S) CKC(c, cudaMemcpyAsync(r_S, c->rS, t * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (delta) CKC(c, cudaMemcpyAsync(delta, c->delta, t * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CKC(c, cudaMemsetAsync(c->u, 0, c->m * sizeof(double), c->stream));
+  CKC(c, cudaStreamSynchronize(c->stream));
+  return RS_OK;
+}
+
+rs_status rs_step(rs_ctx* c, int64_t n_iters, double* hist_out) {
+  if (!c || n_iters < 0) return RS_EINVAL;
+  if (n_iters == 0) return RS_OK;
+  DeviceGuard dg(c->device);
+  rs_status s = read_ctrl(c);
+  if (s != RS_OK) return s;
+  const int64_t k0 = c->ctrl_h->k;
+  if ((s = ensure_schedule(c, k0 + n_iters)) != RS_OK) return s;
+  Ctrl* h = c->ctrl_h;
+  h->stop = 0;
+  h->pending = 0;
+  h->status = 0;
+  h->ticket = 0;
+  h->no_stop = 1;
+  h->max_iters = k0 + n_iters;
+  h->r0 = c->r0 > 0.0 ? c->r0 : 1.0;
+  if ((s = write_ctrl(c)) != RS_OK) return s;
+  const int64_t chunks = (n_iters + c->chunk - 1) / c->chunk + 1;
+  for (int64_t q = 0; q < chunks; ++q) {
+    if ((s = enqueue_chunk(c, false)) != RS_OK) return s;
+    if ((s = read_ctrl(c)) != RS_OK) return s;
+    if (h->stop) break;
+  }
+  if (h->status == RS_ENUMERIC) FAILC(c, RS_ENUMERIC, "rs_step: NaN or Inf in the residual");
+  if (hist_out)
+    CKC(c, cudaMemcpy(hist_out, c->hist + k0 + 1, n_iters * sizeof(double), cudaMemcpyDeviceToHost));
+  // leave the context ready for further steps or probes
+  h->stop = 0;
+  h->max_iters = INT64_MAX;
+  if ((s = write_ctrl(c)) != RS_OK) return s;
+  CKC(c, cudaStreamSynchronize(c->stream));
+  return RS_OK;
+}
+
+rs_status rs_true_residual(rs_ctx* c, const double* v, double* rel_out) {
+  if (!c || !v || !rel_out) return RS_EINVAL;
+  DeviceGuard dg(c->device);
+  rs_status s = read_ctrl(c);
+  if (s != RS_OK) return s;
+  Ctrl saved = *c->ctrl_h;
+  c->ctrl_h->r0 = c->r0 > 0.0 ? c->r0 : 1.0;
+  c->ctrl_h->ticket = 0;
+  if ((s = write_ctrl(c)) != RS_OK) return s;
+  CKC(c, cudaMemcpyAsync(c->u, v, c->m * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  double rel = 0.0;
+  if ((s = true_rel(c, c->u, &rel)) != RS_OK) return s;
+  CKC(c, cudaMemsetAsync(c->u, 0, c->m * sizeof(double), c->stream));
+  *c->ctrl_h = saved;
+  if ((s = write_ctrl(c)) != RS_OK) return s;
+  CKC(c, cudaStreamSynchronize(c->stream));
+  *rel_out = rel;
+  return RS_OK;
+}
+
+rs_status rs_timings(const rs_ctx* c, double* setup_ms, double* solve_ms) {
+  if (!c) return RS_EINVAL;
+  if (setup_ms) *setup_ms = c->setup_ms;
+  if (solve_ms) *solve_ms = c->solve_ms;
+  return RS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Shared device helpers of the ridge sketch-and-project library (GB300, sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rs {
+
+// ---------------------------------------------------------------------------
+// Counter-based draws. Written from the SplitMix64 definition (Steele, Lea &
+// Flood, OOPSLA 2014): output function mix64 and increment GAMMA.
+//   key(seed, k)        = mix64(seed + (k+1) GAMMA)
+//   draw(seed, k, s, i) = mix64(key(seed, k) + (1 + i + s 2^40) GAMMA)
+// Streams: 0 sample keys, 1 sign + bucket, 2/3 Gaussian uniforms, 4 proposal.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t iter_key(uint64_t seed, int64_t k) {
+  return mix64(seed + (uint64_t)(k + 1) * kGamma);
+}
+__host__ __device__ __forceinline__ uint64_t draw_k(uint64_t key, uint32_t stream, uint64_t lane) {
+  return mix64(key + (1ull + lane + ((uint64_t)stream << 40)) * kGamma);
+}
+// bucket in [0, tau): multiply-shift of the low 32 bits; sign from bit 63
+__host__ __device__ __forceinline__ int32_t draw_bucket(uint64_t d, int64_t tau) {
+  return (int32_t)(((d & 0xFFFFFFFFull) * (uint64_t)tau) >> 32);
+}
+__host__ __device__ __forceinline__ bool draw_neg(uint64_t d) { return (d >> 63) != 0; }
+
+// packed sketch entry: row index in the low 31 bits, sign (1 = negative) in bit 31
+__host__ __device__ __forceinline__ int32_t pack_entry(int32_t row, bool neg) {
+  return (int32_t)((uint32_t)row | (neg ? 0x80000000u : 0u));
+}
+__host__ __device__ __forceinline__ int32_t entry_row(int32_t e) { return e & 0x7FFFFFFF; }
+__host__ __device__ __forceinline__ bool entry_neg(int32_t e) { return e < 0; }
+
+// ---------------------------------------------------------------------------
+// Device control block of one context: iteration counter, stop flags, norms.
+// ---------------------------------------------------------------------------
+struct Ctrl {
+  int64_t k;          // next iteration index
+  int64_t k0;         // first iteration of the current chunk
+  int64_t max_iters;  // iteration cap of the current solve
+  int32_t stop;       // 1: finished (converged, cap reached or error)
+  int32_t pending;    // 1 (mixed): recursive residual <= tol, awaiting the FP64 check
+  int32_t status;     // rs_status of the device side
+  uint32_t ticket;    // last-block-done counter of reductions
+  int32_t no_stop;    // 1: ignore tol (rs_step)
+  int32_t pad;
+  double r0;          // ||r^0|| = ||b||
+  double tol;
+};
+
+__device__ __forceinline__ bool halted(const Ctrl* c) {
+  return (*(volatile const int32_t*)&c->stop) | (*(volatile const int32_t*)&c->pending);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum (fixed tree over warps); result valid in every thread.
+template <typename T>
+__device__ T block_sum(T v, T* sh /* >= 32 entries */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  T t = (threadIdx.x < (unsigned)nw) ? sh[threadIdx.x] : T(0);
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) sh[0] = t;
+  __syncthreads();
+  T r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+inline int ceil_div(int64_t x, int64_t a) { return (int)((x + a - 1) / a); }
+
+}  // namespace rs

@@ -1,0 +1,172 @@
+// Forming the linear system of eq. (4) (A = X^T X + lambda I, b = X^T y for the
+// primal eq. (2); A = X X^T + lambda I, b = y for the dual eq. (3)) and evaluating
+// the true residual A v - b through X in FP64 without forming A.
+#include "rs_gemm.cuh"
+#include "rs_kernels.cuh"
+
+namespace rs {
+
+template <typename TI, typename TO>
+cudaError_t launch_form_A(cudaStream_t st, const TI* X, int64_t n, int64_t d, int dual,
+                          double lambda, TO* A, int64_t lda) {
+  using TA = TO;  // FP64 output accumulates in FP64, FP32 output in FP32
+  cudaError_t e;
+  int64_t m;
+  if (!dual) {  // A[i, j] = sum_k X[k, i] X[k, j]
+    m = d;
+    e = gemm_strided<TI, TA, TO>(st, d, d, n, X, 1, d, X, d, 1, A, lda, lambda, 1);
+  } else {      // A[i, j] = sum_k X[i, k] X[j, k]
+    m = n;
+    e = gemm_strided<TI, TA, TO>(st, n, n, d, X, d, 1, X, 1, d, A, lda, lambda, 1);
+  }
+  if (e != cudaSuccess) return e;
+  dim3 g((unsigned)((m + 31) / 32), (unsigned)((m + 31) / 32));
+  k_mirror_lower<TO><<<g, dim3(32, 32), 0, st>>>(A, m, lda);
+  return cudaGetLastError();
+}
+
+// ---- X^T v: column sums of X weighted by v, chunked over rows, FP64 ----
+constexpr int64_t kXtRows = 256;
+
+size_t xt_part_elems(int64_t n, int64_t d) { return (size_t)((n + kXtRows - 1) / kXtRows) * d; }
+
+template <typename TI>
+__global__ void __launch_bounds__(256) k_xt_v_part(const TI* __restrict__ X, int64_t n, int64_t d,
+                                                   const double* __restrict__ v,
+                                                   double* __restrict__ part,
+                                                   const int32_t* __restrict__ stop) {
+  if (stop != nullptr && *(volatile const int32_t*)stop) return;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t c = blockIdx.y;
+  if (j >= d) return;
+  const int64_t i0 = c * kXtRows, i1 = min(n, i0 + kXtRows);
+  double acc = 0.0;
+  for (int64_t i = i0; i < i1; ++i) acc += (double)X[i * d + j] * v[i];
+  part[c * d + j] = acc;
+}
+
+__global__ void k_sum_parts(const double* __restrict__ part, int64_t nchunk, int64_t d,
+                            double* __restrict__ out, const int32_t* __restrict__ stop) {
+  if (stop != nullptr && *(volatile const int32_t*)stop) return;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d) return;
+  double acc = 0.0;
+  for (int64_t c = 0; c < nchunk; ++c) acc += part[c * d + j];
+  out[j] = acc;
+}
+
+template <typename TI>
+cudaError_t launch_xt_v(cudaStream_t st, const TI* X, int64_t n, int64_t d, const double* v,
+                        double* out, double* part, const int32_t* stop) {
+  const int64_t nchunk = (n + kXtRows - 1) / kXtRows;
+  dim3 g((unsigned)((d + 255) / 256), (unsigned)nchunk);
+  k_xt_v_part<TI><<<g, 256, 0, st>>>(X, n, d, v, part, stop);
+  k_sum_parts<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(part, nchunk, d, out, stop);
+  return cudaGetLastError();
+}
+
+// ---- X v: one warp per row, FP64 ----
+template <typename TI>
+__global__ void __launch_bounds__(256) k_x_v(const TI* __restrict__ X, int64_t n, int64_t d,
+                                             const double* __restrict__ v,
+                                             double* __restrict__ out,
+                                             const int32_t* __restrict__ stop) {
+  if (stop != nullptr && *(volatile const int32_t*)stop) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int64_t j = lane; j < d; j += 32) acc += (double)X[i * d + j] * v[j];
+  acc = warp_sum(acc);
+  if (lane == 0) out[i] = acc;
+}
+
+template <typename TI>
+cudaError_t launch_x_v(cudaStream_t st, const TI* X, int64_t n, int64_t d, const double* v,
+                       double* out, const int32_t* stop) {
+  k_x_v<TI><<<(unsigned)((n + 7) / 8), 256, 0, st>>>(X, n, d, v, out, stop);
+  return cudaGetLastError();
+}
+
+// ---- true residual r = v + lambda x - b ----
+// mode 1: replace the recursive residual pair (r, r_prev) by (r_true, r_true - (r - r_prev))
+//         and decide convergence on ||r_true|| / ||r^0||; mode 0: only *rel_out.
+__global__ void __launch_bounds__(256) k_refresh_finish(Ctrl* __restrict__ ctrl, int mode, int64_t m,
+                                                        const double* __restrict__ v,
+                                                        const double* __restrict__ x,
+                                                        const double* __restrict__ b, double lambda,
+                                                        double* __restrict__ r,
+                                                        double* __restrict__ rp,
+                                                        double* __restrict__ partials,
+                                                        double* __restrict__ hist,
+                                                        double* __restrict__ rel_out) {
+  __shared__ double s_red[32];
+  __shared__ int s_last;
+  if (mode == 1 && (*(volatile int32_t*)&ctrl->stop)) return;
+  double sq = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double rt = v[i] + lambda * x[i] - b[i];
+    if (mode == 1) {
+      const double diff = r[i] - rp[i];
+      r[i] = rt;
+      rp[i] = rt - diff;
+    }
+    sq += rt * rt;
+  }
+  sq = block_sum(sq, s_red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = sq;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(&ctrl->ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double part = 0.0;
+  for (int64_t q = threadIdx.x; q < gridDim.x; q += blockDim.x) part += *((volatile double*)&partials[q]);
+  part = block_sum(part, s_red);
+  if (threadIdx.x == 0) {
+    ctrl->ticket = 0u;
+    const double rel = sqrt(part) / ctrl->r0;
+    if (mode == 1) {
+      const int64_t k = ctrl->k;
+      hist[k] = rel;
+      if (!isfinite(rel)) {
+        ctrl->status = 4;
+        ctrl->stop = 1;
+      } else if (rel <= ctrl->tol) {
+        ctrl->stop = 1;
+      }
+      ctrl->pending = 0;
+      if (k >= ctrl->max_iters) ctrl->stop = 1;
+    } else {
+      *rel_out = rel;
+    }
+    __threadfence();
+  }
+}
+
+cudaError_t launch_refresh_finish(cudaStream_t st, Ctrl* ctrl, int mode, int64_t m, const double* v,
+                                  const double* x, const double* b, double lambda, double* r,
+                                  double* rp, double* partials, double* hist, double* rel_out) {
+  int blocks = (int)std::min<int64_t>((m + 255) / 256, 152);
+  if (blocks < 1) blocks = 1;
+  k_refresh_finish<<<blocks, 256, 0, st>>>(ctrl, mode, m, v, x, b, lambda, r, rp, partials, hist,
+                                           rel_out);
+  return cudaGetLastError();
+}
+
+#define RS_INST(TI)                                                                            \
+  template cudaError_t launch_xt_v<TI>(cudaStream_t, const TI*, int64_t, int64_t, const double*, \
+                                       double*, double*, const int32_t*);                      \
+  template cudaError_t launch_x_v<TI>(cudaStream_t, const TI*, int64_t, int64_t, const double*,  \
+                                      double*, const int32_t*);                                              \
+  template cudaError_t launch_form_A<TI, double>(cudaStream_t, const TI*, int64_t, int64_t, int, \
+                                                 double, double*, int64_t);                    \
+  template cudaError_t launch_form_A<TI, float>(cudaStream_t, const TI*, int64_t, int64_t, int,  \
+                                                double, float*, int64_t);
+RS_INST(float)
+RS_INST(double)
+#undef RS_INST
+
+}  // namespace rs

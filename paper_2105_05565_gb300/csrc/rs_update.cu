@@ -1,0 +1,130 @@
+// Iterate and residual update of Algorithm 2 (Section 6.3) with the residual
+// recursion of eq. (53):
+//   w^{k+1} = (1 + beta_k) w^k - beta_k w^{k-1} - gamma_k (S delta)
+//   r^{k+1} = (1 + beta_k) r^k - beta_k r^{k-1} - gamma_k (A S delta)
+// with (A S delta)_i = sum_j (S^T A)[j, i] delta_j (A symmetric), fused with the
+// squared norm of r^{k+1}, the history entry and the stopping test.
+#include "rs_kernels.cuh"
+
+namespace rs {
+
+constexpr int kUpdCols = 32;   // elements i per block
+constexpr int kUpdWarps = 8;   // warps splitting the tau rows
+
+int update_blocks(int64_t m) { return ceil_div(m, kUpdCols); }
+
+template <typename T> struct AccT { using type = double; };
+template <> struct AccT<float> { using type = float; };
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_update(Ctrl* __restrict__ ctrl, PlanView plan,
+                                                RowsView<T> rows, int64_t m, int64_t tau,
+                                                UpdateArgs a) {
+  using TA = typename AccT<T>::type;
+  if (halted(ctrl)) return;
+  __shared__ TA red[kUpdWarps][kUpdCols + 1];
+  __shared__ double s_part[kUpdWarps];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t k = ctrl->k;
+  const int64_t i = (int64_t)blockIdx.x * kUpdCols + lane;
+  const int32_t* perm = plan.perm ? plan.perm + (k - ctrl->k0) * plan.perm_stride : nullptr;
+
+  TA acc = TA(0);
+  if (i < m) {
+    for (int64_t j = w; j < tau; j += kUpdWarps) {
+      const T* rowj = rows.SA ? rows.SA + j * rows.ldsa
+                              : rows.A + (int64_t)entry_row(perm[j]) * rows.lda;
+      acc += (TA)rowj[i] * (TA)a.delta[j];
+    }
+  }
+  red[w][lane] = acc;
+  __syncthreads();
+  if (w == 0) {
+    double sq = 0.0;
+    if (i < m) {
+      TA s = TA(0);
+#pragma unroll
+      for (int q = 0; q < kUpdWarps; ++q) s += red[q][lane];
+      const double g = a.gam[k], b = a.bet[k];
+      const double ui = a.u[i];
+      a.u[i] = 0.0;
+      const double wi = a.w[i], wpi = a.wp[i], ri = a.r[i], rpi = a.rp[i];
+      const double wn = (1.0 + b) * wi - b * wpi - g * ui;
+      const double rn = (1.0 + b) * ri - b * rpi - g * (double)s;
+      a.wp[i] = wi; a.w[i] = wn;
+      a.rp[i] = ri; a.r[i] = rn;
+      sq = rn * rn;
+    }
+    sq = warp_sum(sq);
+    if (lane == 0) a.partials[blockIdx.x] = sq;
+  }
+  // last block to finish sums the partials in block order (deterministic)
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(&ctrl->ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double part = 0.0;
+  for (int64_t b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+    part += *((volatile double*)&a.partials[b]);
+  part = warp_sum(part);
+  if (lane == 0) s_part[w] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int q = 0; q < kUpdWarps; ++q) tot += s_part[q];
+    const double rel = sqrt(tot) / ctrl->r0;
+    a.hist[k + 1] = rel;
+    const int64_t kn = k + 1;
+    ctrl->k = kn;
+    ctrl->ticket = 0u;
+    if (!isfinite(rel)) {
+      ctrl->status = 4;  // RS_ENUMERIC
+      ctrl->stop = 1;
+    } else if (!ctrl->no_stop && rel <= ctrl->tol) {
+      if (a.mixed) ctrl->pending = 1; else ctrl->stop = 1;
+    }
+    if (kn >= ctrl->max_iters) ctrl->stop = 1;
+    __threadfence();
+  }
+}
+
+template <typename T>
+cudaError_t launch_update(cudaStream_t st, Ctrl* ctrl, PlanView plan, RowsView<T> rows, int64_t m,
+                          int64_t tau, UpdateArgs a) {
+  k_update<T><<<update_blocks(m), 256, 0, st>>>(ctrl, plan, rows, m, tau, a);
+  return cudaGetLastError();
+}
+
+__global__ void k_init_state(int64_t m, const double* __restrict__ b, double* __restrict__ w,
+                             double* __restrict__ wp, double* __restrict__ r,
+                             double* __restrict__ rp, double* __restrict__ u) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    w[i] = 0.0; wp[i] = 0.0; u[i] = 0.0;
+    r[i] = -b[i]; rp[i] = -b[i];
+  }
+}
+
+cudaError_t launch_init_state(cudaStream_t st, int64_t m, const double* b, double* w, double* wp,
+                              double* r, double* rp, double* u) {
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 1024));
+  k_init_state<<<blocks, 256, 0, st>>>(m, b, w, wp, r, rp, u);
+  return cudaGetLastError();
+}
+
+__global__ void k_chunk_begin(Ctrl* ctrl) { ctrl->k0 = ctrl->k; }
+
+cudaError_t launch_chunk_begin(cudaStream_t st, Ctrl* ctrl) {
+  k_chunk_begin<<<1, 1, 0, st>>>(ctrl);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_update<float>(cudaStream_t, Ctrl*, PlanView, RowsView<float>, int64_t,
+                                          int64_t, UpdateArgs);
+template cudaError_t launch_update<double>(cudaStream_t, Ctrl*, PlanView, RowsView<double>,
+                                           int64_t, int64_t, UpdateArgs);
+
+}  // namespace rs

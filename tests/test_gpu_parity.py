@@ -1,0 +1,236 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same
+seeded inputs. Sketch indices/signs/buckets bit-exact; plain FP64 iterates within
+1e-8 relative; sketched systems and steps element by element."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import rng as orng
+from oracle.sketches import srht_pad, subcount_params
+from synth import gaussian_problem
+
+pytestmark = pytest.mark.gpu
+
+W_TOL = 1e-8  # plain FP64 path: relative error of w vs the oracle (same seed, same k)
+
+
+@pytest.fixture(scope="module")
+def rs():
+    import paper_2105_05565_gb300 as rs
+
+    rs.lib()
+    return rs
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+# ---------------------------------------------------------------- sketches ---
+@pytest.mark.parametrize("m,tau", [(50, 7), (500, 50), (4096, 256), (1000, 1000)])
+def test_subsample_indices_bitexact(rs, m, tau):
+    X, y, _ = gaussian_problem(m + 3, m, 0)
+    with rs.Solver(X, y, 1.0, sketch="subsample", tau=tau, seed=12) as s:
+        for k in [0, 1, 7, 123]:
+            idx, _, _ = s.dump_sketch(k)
+            assert np.array_equal(idx[:tau], orng.subsample_indices(12, k, m, tau))
+
+
+@pytest.mark.parametrize("m,tau", [(97, 5), (500, 50), (4096, 256), (300, 290)])
+def test_count_buckets_signs_bitexact(rs, m, tau):
+    X, y, _ = gaussian_problem(m + 1, m, 1)
+    with rs.Solver(X, y, 1.0, sketch="count", tau=tau, seed=3) as s:
+        for k in [0, 2, 55]:
+            idx, sign, bucket = s.dump_sketch(k)
+            osign, obucket = orng.signs_buckets(3, k, m, tau)
+            assert np.array_equal(bucket[:m], obucket)
+            assert np.array_equal(sign[:m], osign)
+            # rows grouped by bucket, ascending row inside a bucket
+            assert np.array_equal(idx[:m], np.lexsort((np.arange(m), obucket)))
+
+
+@pytest.mark.parametrize("m,tau,s_", [(500, 10, 0), (4096, 256, 0), (1000, 50, 400), (64, 8, 64)])
+def test_subcount_bitexact(rs, m, tau, s_):
+    X, y, _ = gaussian_problem(m + 1, m, 2)
+    with rs.Solver(X, y, 1.0, sketch="subcount", tau=tau, seed=4, sub_s=s_) as sv:
+        ss, kk = subcount_params(m, tau, s_ or None)
+        assert (sv.s, sv.k_sum) == (ss, kk)
+        for k in [0, 9]:
+            idx, sign, bucket = sv.dump_sketch(k)
+            assert np.array_equal(idx[:ss], orng.subsample_indices(4, k, m, ss))
+            assert np.array_equal(sign[:ss], orng.signs_buckets(4, k, ss, tau)[0])
+            assert np.array_equal(bucket[:ss], np.arange(ss) // kk)
+
+
+@pytest.mark.parametrize("m,tau", [(100, 20), (512, 64), (4096, 256)])
+def test_srht_bitexact(rs, m, tau):
+    X, y, _ = gaussian_problem(m + 1, m, 5)
+    with rs.Solver(X, y, 1.0, sketch="srht", tau=tau, seed=6) as s:
+        mp = srht_pad(m)
+        assert s.m_pad == mp
+        for k in [0, 3]:
+            idx, sign, _ = s.dump_sketch(k)
+            assert np.array_equal(idx[:tau], orng.subsample_indices(6, k, mp, tau))
+            assert np.array_equal(sign[:m], orng.signs_buckets(6, k, m, 1)[0])
+
+
+def test_gaussian_entries_close(rs):
+    m, tau = 200, 16
+    X, y, _ = gaussian_problem(m + 1, m, 7)
+    with rs.Solver(X, y, 1.0, sketch="gaussian", tau=tau, seed=8) as s:
+        for k in [0, 4]:
+            S = s.dump_gaussian(k)
+            ref = oracle.sketch_matrix("gaussian", m, tau, 8, k)
+            assert np.max(np.abs(S - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+# ------------------------------------------------------- plain FP64 iterates ---
+KINDS = [("subsample", 12, None), ("count", 12, None), ("subcount", 8, 48),
+         ("gaussian", 6, None), ("srht", 10, None)]
+MOMS = ["none", "const", "theory", "heuristic"]
+
+
+@pytest.mark.parametrize("kind,tau,s_", KINDS, ids=[k[0] for k in KINDS])
+@pytest.mark.parametrize("mom", MOMS)
+def test_plain_iterates_match_oracle(rs, kind, tau, s_, mom):
+    X, y, _ = gaussian_problem(160, 97, 21)  # m = 97: ragged against every tile size
+    lam, K = 0.05, 60
+    ref = oracle.solve_ridge(X, y, lam, "primal", kind, tau, seed=9, tol=0.0, max_iters=K,
+                             mom={"kind": mom}, s=s_)
+    with rs.Solver(X, y, lam, sketch=kind, tau=tau, momentum=mom, seed=9, sub_s=s_ or 0) as s:
+        w, hist, iters, _ = s.solve(tol=0.0, max_iters=K)
+    assert iters == K
+    assert rel(w, ref["w"]) <= W_TOL
+    assert np.allclose(hist, ref["hist"], rtol=1e-8, atol=1e-14)
+
+
+def test_cfg_small_to_tolerance(rs):
+    """Dense primal FP64: X 2000 x 500 iid N(0,1), lambda = 1e-3, subsample tau = 50,
+    no momentum, seed 0, relative residual 1e-6."""
+    X, y, _ = gaussian_problem(2000, 500, 0)
+    lam = 1e-3
+    ref = oracle.solve_ridge(X, y, lam, "primal", "subsample", 50, seed=0, tol=1e-6,
+                             max_iters=20000)
+    with rs.Solver(X, y, lam, sketch="subsample", tau=50, seed=0) as s:
+        w, hist, iters, conv = s.solve(tol=1e-6, max_iters=20000)
+    assert conv and iters == ref["iters"]
+    assert rel(w, ref["w"]) <= W_TOL
+    assert oracle.true_residual(X, y, lam, w) <= 1.01e-6
+    assert rel(w, oracle.direct_solution(X, y, lam)) <= 1e-4
+
+
+@pytest.mark.parametrize("kind", ["subsample", "count", "subcount", "gaussian", "srht"])
+def test_probe_sketched_system(rs, kind):
+    """M = S^T A S, r_S = S^T r and delta of one iteration, from the oracle's state."""
+    X, y, _ = gaussian_problem(150, 70, 31)
+    lam, tau = 0.3, 9
+    s_ = 27 if kind == "subcount" else None
+    ref = oracle.solve_ridge(X, y, lam, "primal", kind, tau, seed=2, tol=0.0, max_iters=6,
+                             mom={"kind": "heuristic"}, s=s_, record_first=6)
+    with rs.Solver(X, y, lam, sketch=kind, tau=tau, momentum="heuristic", seed=2,
+                   sub_s=s_ or 0) as s:
+        A, b = oracle.form_system(X, y, lam)
+        w_prev = np.zeros(70)
+        w = np.zeros(70)
+        for k in range(5):
+            r = A @ w - b
+            r_prev = A @ w_prev - b
+            s.set_state(w, w_prev, r, r_prev, k)
+            M, rS, delta = s.probe_step()
+            rec = ref["records"][k]
+            assert np.allclose(M, rec["M"], rtol=1e-12, atol=1e-12 * np.abs(rec["M"]).max())
+            assert np.allclose(rS, rec["rS"], rtol=1e-12, atol=1e-12 * np.abs(rec["rS"]).max())
+            assert rel(rec["S"] @ delta, rec["S"] @ rec["delta"]) <= 1e-10
+            w_prev, w = w, rec["w"]
+
+
+def test_step_matches_oracle_history(rs):
+    X, y, _ = gaussian_problem(300, 130, 41)
+    lam = 0.1
+    ref = oracle.solve_ridge(X, y, lam, "primal", "count", 13, seed=1, tol=0.0, max_iters=30,
+                             mom={"kind": "heuristic"})
+    with rs.Solver(X, y, lam, sketch="count", tau=13, momentum="heuristic", seed=1) as s:
+        m = 130
+        A, b = oracle.form_system(X, y, lam)
+        s.set_state(np.zeros(m), np.zeros(m), -b, -b, 0)
+        h = s.step(30)
+        w, _, _, _, k = s.get_state()
+    assert k == 30
+    assert np.allclose(h, ref["hist"][1:], rtol=1e-9)
+    assert rel(w, ref["w"]) <= W_TOL
+
+
+def test_dual_form(rs):
+    X, y, _ = gaussian_problem(60, 150, 51)  # n < d: the dual is the smaller system
+    lam = 0.5
+    ref = oracle.solve_ridge(X, y, lam, "dual", "count", 8, seed=3, tol=0.0, max_iters=50,
+                             mom={"kind": "heuristic"})
+    with rs.Solver(X, y, lam, form="dual", sketch="count", tau=8, momentum="heuristic", seed=3) as s:
+        assert s.m == 60
+        w, hist, iters, _ = s.solve(tol=0.0, max_iters=50)
+    assert rel(w, ref["w"]) <= W_TOL
+    with rs.Solver(X, y, lam, form="dual", sketch="subsample", tau=20, momentum="heuristic",
+                   seed=3) as s:
+        w, hist, iters, conv = s.solve(tol=1e-10, max_iters=20000)
+    assert conv and rel(w, oracle.direct_solution(X, y, lam)) <= 1e-8
+
+
+# ------------------------------------------------------------- edge cases ---
+def test_subsample_tau_equals_m_one_step(rs):
+    X, y, _ = gaussian_problem(90, 40, 61)
+    lam = 0.2
+    with rs.Solver(X, y, lam, sketch="subsample", tau=40, seed=0) as s:
+        w, hist, iters, conv = s.solve(tol=1e-12, max_iters=5)
+    assert iters == 1 and conv
+    assert rel(w, oracle.direct_solution(X, y, lam)) <= 1e-11
+
+
+def test_tau_one_and_empty_buckets(rs):
+    X, y, _ = gaussian_problem(80, 33, 62)
+    lam = 0.4
+    for kind, tau in [("subsample", 1), ("count", 1), ("count", 30)]:
+        ref = oracle.solve_ridge(X, y, lam, "primal", kind, tau, seed=4, tol=0.0, max_iters=40)
+        with rs.Solver(X, y, lam, sketch=kind, tau=tau, seed=4) as s:
+            w, _, _, _ = s.solve(tol=0.0, max_iters=40)
+        assert rel(w, ref["w"]) <= W_TOL, (kind, tau)
+
+
+def test_zero_rhs_returns_zero(rs):
+    X, _, _ = gaussian_problem(50, 20, 63)
+    with rs.Solver(X, np.zeros(50), 1.0, sketch="count", tau=4) as s:
+        w, hist, iters, conv = s.solve(tol=1e-6, max_iters=10)
+    assert iters == 0 and conv and np.all(w == 0)
+
+
+def test_invalid_sizes_rejected(rs):
+    X, y, _ = gaussian_problem(30, 10, 64)
+    with pytest.raises(rs.RSError):
+        rs.Solver(X, y, 1.0, sketch="subsample", tau=11)
+    with pytest.raises(rs.RSError):
+        rs.Solver(X, y, 1.0, sketch="subcount", tau=3, sub_s=7)
+    with pytest.raises(rs.RSError):
+        rs.Solver(X, y, 0.0, sketch="count", tau=3)
+
+
+def test_max_iters_reports_not_converged(rs):
+    X, y, _ = gaussian_problem(200, 60, 65)
+    with rs.Solver(X, y, 1e-3, sketch="count", tau=4, seed=1) as s:
+        w, hist, iters, conv = s.solve(tol=1e-12, max_iters=7)
+    assert iters == 7 and not conv and hist.shape == (8,)
+
+
+# ------------------------------------------------------------ mixed path ---
+@pytest.mark.parametrize("kind", ["count", "subsample", "subcount"])
+def test_mixed_reaches_tolerance(rs, kind):
+    from synth import geometric_sigma, spectrum_problem
+
+    X, y, _ = spectrum_problem(3000, 256, geometric_sigma(256), seed=7, noise=0.01, dtype=np.float32)
+    lam = 1e-2
+    with rs.Solver(X, y, lam, sketch=kind, tau=32, momentum="heuristic", seed=2,
+                   precision="mixed") as s:
+        w, hist, iters, conv = s.solve(tol=1e-6, max_iters=50000)
+    Xd = X.astype(np.float64)
+    assert conv
+    assert oracle.true_residual(Xd, y, lam, w) <= 1e-6
+    w_star = oracle.direct_solution(Xd, y, lam)
+    assert rel(w, w_star) <= 1e-4
