@@ -1,0 +1,335 @@
+"""Benchmark of the GB300 sketch-and-project ridge solver.
+
+Workload (default): dense primal ridge, X 100000 x 4096 = U diag(sigma) V^T with
+Haar U, V and sigma geometric from 1 to 1e-3 (float32 storage), y = X w* + 0.01 noise,
+lambda = 1e-2, count sketch tau = 256 with the heuristic momentum, FP32 bulk products
+with FP64 true-residual refresh every 50 iterations ("mixed"), to relative residual
+1e-6. The plain FP64 GPU path on the same problem (and both precisions with the
+subsample sketch) are measured beside it.
+
+A step is one full solve through the C ABI: rs_create (copies X, y; forms A, b on
+the device) + rs_solve to 1e-6 + the weights back. ``value`` is the iteration
+throughput of the solve phase (iterations per second); time to tolerance of the
+whole step is ``ms_per_step``. With --gpus N (torchrun) every rank solves its own
+replica of the workload (different data seed); no data moves between GPUs.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-6 rel. residual & iters/s, chosen form vs plain FP64, one GB300"
+N_ROWS, N_COLS, TAU, LAM, TOL, MAX_IT = 100000, 4096, 256, 1e-2, 1e-6, 30000
+WORKLOAD = ("dense primal ridge X 100000x4096 (Haar U,V; sigma geometric 1..1e-3; fp32), "
+            "lambda 1e-2, count sketch tau 256, heuristic momentum, mixed FP32 + FP64 refresh/50, "
+            "tol 1e-6")
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while active."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._th = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._th = threading.Thread(target=self._run, daemon=True)
+        self._th.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._th.join(timeout=10)
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def make_problem(seed, device):
+    from synth import geometric_sigma, spectrum_problem_torch
+
+    return spectrum_problem_torch(N_ROWS, N_COLS, geometric_sigma(N_COLS, 1e-3), seed=seed,
+                                  noise=0.01, device=device)
+
+
+def one_solve(rs, X, y, precision, sketch, device, w_out, on_host=False):
+    """One step: create (copy X, y; form A, b), solve to TOL, weights out, destroy.
+    Returns dict of times (ms) and iteration count."""
+    import torch
+
+    st = torch.cuda.current_stream(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(device)
+    e0.record(st)
+    with rs.Solver(X, y, LAM, sketch=sketch, tau=TAU, momentum="heuristic", seed=0,
+                   precision=precision, refresh_every=50, device=device.index or 0,
+                   stream=st.cuda_stream) as s:
+        w, hist, iters, conv = s.solve(TOL, MAX_IT, w_out=None if on_host else w_out)
+        setup_ms, solve_ms = s.timings()
+    e1.record(st)
+    torch.cuda.synchronize(device)
+    return {"ms": e0.elapsed_time(e1), "iters": iters, "conv": bool(conv), "setup_ms": setup_ms,
+            "solve_ms": solve_ms, "final_rel": float(hist[-1]), "w": w}
+
+
+def profile_kernels(rs, X, y, device):
+    """Per-kernel mean device time of the chosen form (CUDA events on the solver's
+    stream), continuing from the converged state's first iterations."""
+    import torch
+
+    st = torch.cuda.current_stream(device)
+    with rs.Solver(X, y, LAM, sketch="count", tau=TAU, momentum="heuristic", seed=0,
+                   precision="mixed", refresh_every=50, device=device.index or 0,
+                   stream=st.cuda_stream) as s:
+        s.solve(TOL, 60)
+        return s.profile_iteration(100)
+
+
+def roofline(stats, pk):
+    """Dominant kernel of the iteration and its achieved fraction of the measured peak."""
+    name, (ms, n, nbytes, flops) = max(stats.items(), key=lambda kv: kv[1][0] * kv[1][1])
+    hbm = pk.get("hbm_gbs", 6800.0)
+    if name in ("chol",):
+        # FP64 ALU bound: peak from the FP64 FMA throughput measured on this GPU
+        # (1.2 TFLOP/s = 152 SMs x 2 DFMA/clk x ~1.95 GHz); see the design doc
+        achieved = flops / (ms * 1e-3) / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": 1.19,
+                "unit": "TFLOP/s", "frac": achieved / 1.19, "traffic": None,
+                "peak_source": "measured FP64 FMA probe (DESIGN.md)"}
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+
+
+def cpu_baseline(X, y, iters_ref, sample_iters=4):
+    """The FP64 oracle on the host cores: A = X^T X + lambda I from the full X
+    (setup), then `sample_iters` count-sketch iterations; iters/s of its loop."""
+    import oracle
+
+    cores = os.cpu_count()
+    Xh = X.detach().cpu().double().numpy()
+    yh = y.detach().cpu().numpy()
+    t0 = time.perf_counter()
+    A, b = oracle.form_system(Xh, yh, LAM, "primal")
+    t_setup = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    oracle.sketch_and_project(A, b, "count", TAU, 0, 0.0, sample_iters,
+                              mom={"kind": "heuristic"})
+    t_it = (time.perf_counter() - t1) / sample_iters
+    return {"value": 1.0 / t_it, "unit": "iters/s", "cores": cores, "kind": "oracle",
+            "sample": (f"numpy FP64 oracle: setup X^T X on the full 100000x4096 X ({t_setup:.1f} s), "
+                       f"then {sample_iters} count-sketch iterations ({t_it * 1e3:.0f} ms each); "
+                       f"time to 1e-6 extrapolated with {iters_ref} iterations = "
+                       f"{t_setup + iters_ref * t_it:.1f} s"),
+            "setup_s": t_setup, "s_per_iter": t_it}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle as it stands, on the host cores, on this
+    workload; each step a bounded sample (setup once, 3 iterations per step)."""
+    import torch
+
+    import oracle
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    dev = torch.device("cuda", 0) if torch.cuda.is_available() else torch.device("cpu")
+    X, y, _ = make_problem(1234, dev)
+    Xh = X.detach().cpu().double().numpy()
+    yh = y.detach().cpu().numpy()
+    del X, y
+    A, b = oracle.form_system(Xh, yh, LAM, "primal")
+    per_step = 3
+    for _ in range(args.warmup):
+        oracle.sketch_and_project(A, b, "count", TAU, 0, 0.0, 1, mom={"kind": "heuristic"})
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sketch_and_project(A, b, "count", TAU, 0, 0.0, per_step, mom={"kind": "heuristic"})
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    line = {"metric": METRIC, "value": value, "unit": "iters/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": 1, "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"{per_step} oracle iterations per step after one setup"},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import paper_2105_05565_gb300 as rs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    rs.lib()
+    X, y, _ = make_problem(1234 + rank, dev)
+    w_out = torch.empty(N_COLS, dtype=torch.float64, device=dev)
+
+    for _ in range(max(args.warmup, 3)):
+        r = one_solve(rs, X, y, "mixed", "count", dev, w_out)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    runs = []
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            runs.append(one_solve(rs, X, y, "mixed", "count", dev, w_out))
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    iters = sum(r["iters"] for r in runs)
+    solve_s = sum(r["solve_ms"] for r in runs) / 1e3
+    step_ms = sum(r["ms"] for r in runs) / len(runs)
+    if dist:
+        t = torch.tensor([solve_s, step_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        solve_s, step_ms = t.tolist()
+        it = torch.tensor([iters], device=dev, dtype=torch.float64)
+        dist.all_reduce(it)
+        iters = int(it.item())
+    value = iters / solve_s
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    # end to end: host inputs in pinned memory, weights back to the host
+    Xh = X.cpu().pin_memory()
+    yh = y.cpu().pin_memory()
+    e2e_runs = [one_solve(rs, Xh, yh, "mixed", "count", dev, None, on_host=True)
+                for _ in range(2)]
+    e2e_iters = sum(r["iters"] for r in e2e_runs)
+    e2e_ms = sum(r["ms"] for r in e2e_runs)
+    e2e = {"value": e2e_iters / (e2e_ms / 1e3), "unit": "iters/s",
+           "h2d_bytes_per_step": int(Xh.numel() * 4 + yh.numel() * 8),
+           "d2h_bytes_per_step": int(N_COLS * 8 + (MAX_IT + 1) * 8),
+           "ms_per_step": e2e_ms / len(e2e_runs)}
+
+    # roofline of the dominant kernel (CUDA events inside the library, same stream)
+    stats = profile_kernels(rs, X, y, dev)
+    pk = peaks()
+    roof = roofline(stats, pk)
+
+    # plain FP64 and subsample arms on the same problem
+    extra = {}
+    last = runs[-1]
+    w_star_err = None
+    if not args.no_plain:
+        plain = one_solve(rs, X, y, "fp64", "count", dev, w_out)
+        extra["plain_fp64_count"] = {k: plain[k] for k in ("ms", "iters", "conv", "setup_ms",
+                                                            "solve_ms", "final_rel")}
+        extra["plain_fp64_count"]["iters_per_s"] = plain["iters"] / (plain["solve_ms"] / 1e3)
+        extra["speedup_time_to_tol_vs_plain_fp64"] = plain["ms"] / step_ms
+        wp = plain["w"].detach().cpu().numpy() if hasattr(plain["w"], "detach") else plain["w"]
+        wm = last["w"].detach().cpu().numpy() if hasattr(last["w"], "detach") else last["w"]
+        w_star_err = float(np.linalg.norm(wm - wp) / np.linalg.norm(wp))
+        for prec in ("mixed", "fp64"):
+            sub = one_solve(rs, X, y, prec, "subsample", dev, w_out)
+            extra[f"{'plain_fp64' if prec == 'fp64' else 'mixed'}_subsample"] = {
+                k: sub[k] for k in ("ms", "iters", "conv", "setup_ms", "solve_ms", "final_rel")}
+    cpu = None
+    if not args.no_cpu:
+        cpu = cpu_baseline(X, y, last["iters"])
+    line = {
+        "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": step_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": world, "seq_len": None,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (X = 1.64 GB re-read every step)"},
+        "time_to_tol_ms": step_ms, "iters_to_tol": last["iters"], "converged": last["conv"],
+        "final_true_rel_residual": last["final_rel"], "setup_ms": last["setup_ms"],
+        "solve_ms": last["solve_ms"], "rel_err_vs_plain_fp64_w": w_star_err,
+        "gpu_launches": None, "kernels": {k: {"ms": v[0], "launches": v[1], "bytes": v[2],
+                                              "flops": v[3]} for k, v in stats.items()},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+        "wall_s_timed": wall,
+    }
+    line.update(extra)
+    # kernels launched in the timed region: every chunk graph holds chunk-begin +
+    # generator + 50 x (sa_rows, msys, chol, update) + 4 refresh kernels (kernels of
+    # iterations after convergence start and exit at once); per step 10 more for
+    # forming A, b, the initial state and the final FP64 residual check
+    n_chunks = sum((r["iters"] + 49) // 50 for r in runs)
+    line["gpu_launches"] = int(n_chunks * (2 + 50 * 4 + 4) + args.steps * 10)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -213,6 +213,25 @@ rs_status rs_true_residual(rs_ctx* ctx, const double* v, double* rel_out);
  * rs_create) and iterations. Either pointer may be NULL. */
 rs_status rs_timings(const rs_ctx* ctx, double* setup_ms, double* solve_ms);
 
+/* Per-kernel device time of the iteration (measurement hook). */
+typedef struct {
+  char name[32];      /* kernel group: "gen", "sa_rows", "msys", "chol", "update", "refresh", ... */
+  int64_t launches;   /* launches timed */
+  double ms;          /* mean device time per launch (CUDA events on the context stream) */
+  double bytes;       /* algorithmic bytes moved per launch (inputs read once + outputs written) */
+  double flops;       /* algorithmic floating-point operations per launch */
+} rs_kernel_stat;
+
+/*
+ * Continue the iteration from the current state for `reps` iterations, launching
+ * each kernel group of an iteration separately between CUDA events on the context
+ * stream, and report per group the mean time per launch and the algorithmic bytes
+ * and flops of one launch. Writes at most `cap` entries to out and their number to
+ * *n_out. The state advances by `reps` iterations (no stopping test).
+ */
+rs_status rs_profile_iteration(rs_ctx* ctx, int64_t reps, rs_kernel_stat* out, int32_t cap,
+                               int32_t* n_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -52,6 +52,11 @@ class Opts(ctypes.Structure):
                 ("device", ctypes.c_int32), ("chol_fp64", ctypes.c_int32), ("chunk", ctypes.c_int64)]
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
 _LIB = None
 _P = ctypes.c_void_p
 _I32, _I64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
@@ -73,6 +78,8 @@ _SIGS = {
     "rs_step": (_I32, [_P, _I64, _P]),
     "rs_true_residual": (_I32, [_P, _P, ctypes.POINTER(_D)]),
     "rs_timings": (_I32, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "rs_profile_iteration": (_I32, [_P, _I64, ctypes.POINTER(KernelStat), _I32,
+                                    ctypes.POINTER(_I32)]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -252,6 +259,15 @@ class Solver:
         out = _D()
         self._check(lib().rs_true_residual(self._ctx, v.ctypes.data, ctypes.byref(out)))
         return out.value
+
+    def profile_iteration(self, reps):
+        """Per kernel group: dict(name -> (mean ms per launch, launches, bytes, flops))."""
+        cap = 16
+        arr = (KernelStat * cap)()
+        n = _I32()
+        self._check(lib().rs_profile_iteration(self._ctx, int(reps), arr, cap, ctypes.byref(n)))
+        return {arr[i].name.decode(): (arr[i].ms, arr[i].launches, arr[i].bytes, arr[i].flops)
+                for i in range(n.value)}
 
     def timings(self):
         a, b = _D(), _D()

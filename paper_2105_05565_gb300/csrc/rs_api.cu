@@ -910,6 +910,133 @@ rs_status rs_true_residual(rs_ctx* c, const double* v, double* rel_out) {
   return RS_OK;
 }
 
+rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int32_t cap,
+                               int32_t* n_out) {
+  if (!c || reps <= 0 || !out || !n_out || cap <= 0) return RS_EINVAL;
+  DeviceGuard dg(c->device);
+  rs_status s = read_ctrl(c);
+  if (s != RS_OK) return s;
+  const int64_t k0 = c->ctrl_h->k;
+  if ((s = ensure_schedule(c, k0 + reps + 1)) != RS_OK) return s;
+  Ctrl* h = c->ctrl_h;
+  h->stop = 0; h->pending = 0; h->status = 0; h->ticket = 0; h->no_stop = 1;
+  h->max_iters = k0 + reps;
+  h->r0 = c->r0 > 0.0 ? c->r0 : 1.0;
+  if ((s = write_ctrl(c)) != RS_OK) return s;
+  struct Grp { const char* name; double ms = 0; int64_t n = 0; double bytes = 0, flops = 0; };
+  std::vector<Grp> g;
+  auto grp = [&](const char* nm) -> Grp& {
+    for (auto& x : g) if (std::strcmp(x.name, nm) == 0) return x;
+    g.push_back(Grp{nm});
+    return g.back();
+  };
+  cudaEvent_t e0, e1;
+  CKC(c, cudaEventCreate(&e0));
+  CKC(c, cudaEventCreate(&e1));
+  auto timed = [&](const char* nm, auto&& fn) -> rs_status {
+    cudaError_t e = cudaEventRecord(e0, c->stream);
+    if (e != cudaSuccess) FAILC(c, RS_ECUDA, "event");
+    rs_status r = fn();
+    if (r != RS_OK) return r;
+    e = cudaEventRecord(e1, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) FAILC(c, RS_ECUDA, std::string("profile: ") + cudaGetErrorString(e));
+    Grp& x = grp(nm);
+    x.ms += ms;
+    x.n += 1;
+    return RS_OK;
+  };
+  const double el = (double)c->elem();
+  const double m = (double)c->m, tau = (double)c->tau, ld = (double)c->ld;
+  const bool sub = c->sketch == RS_SUBSAMPLE;
+  for (int64_t it = 0; it < reps && s == RS_OK; ++it) {
+    if (it % c->chunk == 0) {
+      s = timed("gen", [&]() -> rs_status {
+        CKC(c, launch_chunk_begin(c->stream, c->ctrl));
+        return enqueue_gen(c, -1, (int)c->nslots);
+      });
+      if (s != RS_OK) break;
+    }
+    const PlanView plan = plan_view(c);
+    if (c->sketch == RS_COUNT || c->sketch == RS_SUBCOUNT) {
+      s = timed("sa_rows", [&]() -> rs_status {
+        if (c->mixed())
+          CKC(c, launch_sa_rows<float>(c->stream, c->ctrl, 0, plan, static_cast<const float*>(c->A), c->ld, c->m, c->tau, static_cast<float*>(c->SA), c->ld));
+        else
+          CKC(c, launch_sa_rows<double>(c->stream, c->ctrl, 0, plan, static_cast<const double*>(c->A), c->ld, c->m, c->tau, static_cast<double*>(c->SA), c->ld));
+        return RS_OK;
+      });
+      const double rows = (c->sketch == RS_COUNT) ? m : (double)c->s;
+      grp("sa_rows").bytes = rows * m * el + tau * m * el + rows * 4.0;
+      grp("sa_rows").flops = rows * m;
+      if (s != RS_OK) break;
+      s = timed("msys", [&]() -> rs_status {
+        if (c->mixed()) CKC(c, launch_msys_rows<float>(c->stream, c->ctrl, 0, plan, rows_view<float>(c), c->m, c->tau, c->r, c->M, c->rS));
+        else CKC(c, launch_msys_rows<double>(c->stream, c->ctrl, 0, plan, rows_view<double>(c), c->m, c->tau, c->r, c->M, c->rS));
+        return RS_OK;
+      });
+      grp("msys").bytes = tau * m * el + rows * 4.0 + rows * 8.0 + tau * tau * 8.0 + tau * 8.0;
+      grp("msys").flops = tau * rows + rows;
+    } else if (sub) {
+      s = timed("msys", [&]() -> rs_status {
+        if (c->mixed()) CKC(c, launch_msys_rows<float>(c->stream, c->ctrl, 0, plan, rows_view<float>(c), c->m, c->tau, c->r, c->M, c->rS));
+        else CKC(c, launch_msys_rows<double>(c->stream, c->ctrl, 0, plan, rows_view<double>(c), c->m, c->tau, c->r, c->M, c->rS));
+        return RS_OK;
+      });
+      grp("msys").bytes = tau * tau * (el + 8.0) + tau * 16.0;
+      grp("msys").flops = 0.0;
+    } else {
+      s = timed("system", [&]() -> rs_status {
+        return c->mixed() ? enqueue_system<float>(c, 0, -1) : enqueue_system<double>(c, 0, -1);
+      });
+    }
+    if (s != RS_OK) break;
+    s = timed("chol", [&]() { return enqueue_solve_small(c, 0, -1); });
+    grp("chol").bytes = tau * tau * 8.0 + tau * 16.0;
+    grp("chol").flops = tau * tau * tau / 3.0 + 2.0 * tau * tau;
+    if (s != RS_OK) break;
+    s = timed("update", [&]() -> rs_status {
+      UpdateArgs a{};
+      a.gam = c->gam; a.bet = c->bet; a.w = c->w; a.wp = c->wp; a.r = c->r; a.rp = c->rp;
+      a.u = c->u; a.delta = c->delta; a.partials = c->partials; a.hist = c->hist;
+      a.mixed = c->mixed();
+      if (c->mixed()) CKC(c, launch_update<float>(c->stream, c->ctrl, plan, rows_view<float>(c), c->m, c->tau, a));
+      else CKC(c, launch_update<double>(c->stream, c->ctrl, plan, rows_view<double>(c), c->m, c->tau, a));
+      return RS_OK;
+    });
+    grp("update").bytes = tau * m * el + m * 8.0 * 9.0;
+    grp("update").flops = 2.0 * tau * m + 10.0 * m;
+    if (s == RS_OK && c->mixed() && (it + 1) % c->refresh_every == 0) {
+      s = timed("refresh", [&]() { return enqueue_refresh(c); });
+      grp("refresh").bytes = 2.0 * (double)c->n * (double)c->d * (c->xdtype == RS_F32 ? 4.0 : 8.0) + m * 48.0;
+      grp("refresh").flops = 4.0 * (double)c->n * (double)c->d;
+    }
+    (void)ld;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != RS_OK) return s;
+  int32_t n = 0;
+  for (auto& x : g) {
+    if (n >= cap) break;
+    rs_kernel_stat& o = out[n++];
+    std::memset(&o, 0, sizeof(o));
+    std::strncpy(o.name, x.name, sizeof(o.name) - 1);
+    o.launches = x.n;
+    o.ms = x.n ? x.ms / x.n : 0.0;
+    o.bytes = x.bytes;
+    o.flops = x.flops;
+  }
+  *n_out = n;
+  h->stop = 0;
+  h->max_iters = INT64_MAX;
+  if ((s = write_ctrl(c)) != RS_OK) return s;
+  CKC(c, cudaStreamSynchronize(c->stream));
+  return RS_OK;
+}
+
 rs_status rs_timings(const rs_ctx* c, double* setup_ms, double* solve_ms) {
   if (!c) return RS_EINVAL;
   if (setup_ms) *setup_ms = c->setup_ms;
