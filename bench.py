@@ -114,6 +114,7 @@ def one_solve(rs, X, y, precision, sketch, device, w_out, on_host=False):
         setup_ms, solve_ms = s.timings()
     e1.record(st)
     torch.cuda.synchronize(device)
+    w = w.detach().cpu().numpy() if hasattr(w, "detach") else np.array(w)
     return {"ms": e0.elapsed_time(e1), "iters": iters, "conv": bool(conv), "setup_ms": setup_ms,
             "solve_ms": solve_ms, "final_rel": float(hist[-1]), "w": w}
 
@@ -293,8 +294,7 @@ def main():
                                                             "solve_ms", "final_rel")}
         extra["plain_fp64_count"]["iters_per_s"] = plain["iters"] / (plain["solve_ms"] / 1e3)
         extra["speedup_time_to_tol_vs_plain_fp64"] = plain["ms"] / step_ms
-        wp = plain["w"].detach().cpu().numpy() if hasattr(plain["w"], "detach") else plain["w"]
-        wm = last["w"].detach().cpu().numpy() if hasattr(last["w"], "detach") else last["w"]
+        wp, wm = plain["w"], last["w"]
         w_star_err = float(np.linalg.norm(wm - wp) / np.linalg.norm(wp))
         for prec in ("mixed", "fp64"):
             sub = one_solve(rs, X, y, prec, "subsample", dev, w_out)

@@ -234,3 +234,40 @@ def test_mixed_reaches_tolerance(rs, kind):
     assert oracle.true_residual(Xd, y, lam, w) <= 1e-6
     w_star = oracle.direct_solution(Xd, y, lam)
     assert rel(w, w_star) <= 1e-4
+
+
+# ------------------------------------------------------- small SPD solve ---
+@pytest.mark.parametrize("tau", [1, 5, 16, 17, 33, 100, 256, 300, 512])
+def test_cholesky_solve_sizes(rs, tau):
+    """delta of the sketched system against a LAPACK solve of the same M, r_S
+    (covers the single-CTA and cluster factorisations, padding and several row
+    blocks per CTA)."""
+    m = 700
+    X, y, _ = gaussian_problem(900, m, 71)
+    with rs.Solver(X, y, 0.5, sketch="subsample", tau=tau, seed=3) as s:
+        M, rS, delta = s.probe_step()
+    ref = np.linalg.solve(M, rS)
+    assert rel(delta, ref) <= 1e-10
+
+
+@pytest.mark.parametrize("tau", [7, 64, 256, 512])
+def test_cholesky_fp32_factor(rs, tau):
+    """Mixed path with the FP32 factorisation of S^T A S."""
+    m = 700
+    X, y, _ = gaussian_problem(900, m, 72)
+    with rs.Solver(X.astype(np.float32), y, 0.5, sketch="subsample", tau=tau, seed=3,
+                   precision="mixed", chol_fp64=False) as s:
+        M, rS, delta = s.probe_step()
+    ref = np.linalg.solve(M, rS)
+    assert rel(delta, ref) <= 1e-4
+
+
+def test_mixed_fp32_factor_reaches_tolerance(rs):
+    from synth import geometric_sigma, spectrum_problem
+
+    X, y, _ = spectrum_problem(3000, 256, geometric_sigma(256), seed=7, noise=0.01, dtype=np.float32)
+    lam = 1e-2
+    with rs.Solver(X, y, lam, sketch="count", tau=32, momentum="heuristic", seed=2,
+                   precision="mixed", chol_fp64=False) as s:
+        w, hist, iters, conv = s.solve(tol=1e-6, max_iters=50000)
+    assert conv and oracle.true_residual(X.astype(np.float64), y, lam, w) <= 1e-6
