@@ -73,10 +73,13 @@ struct rs_ctx {
   void* A = nullptr;     // m x ld, double (plain) or float (mixed)
   double* b = nullptr;
   double *w = nullptr, *wp = nullptr, *r = nullptr, *rp = nullptr, *u = nullptr;
-  void* SA = nullptr;    // tau x ld
-  void* S = nullptr;     // gaussian m x tau
-  double *M = nullptr, *rS = nullptr, *delta = nullptr;
-  void* chol_scratch = nullptr;
+  void* SA = nullptr;    // per slot: tau x ld
+  void* ST = nullptr;    // gaussian, per slot: tau x ld (S transposed)
+  double* M = nullptr;   // per slot: tau x tau (FP64)
+  void* Linv = nullptr;  // per slot: tau x tau inverse Cholesky factor (factor precision)
+  void* fws = nullptr;   // factor workspace when the factor does not fit shared memory
+  double *rS = nullptr, *delta = nullptr;
+  int64_t sa_slot = 0, m_slot = 0, l_slot = 0;
   int32_t *perm = nullptr, *boff = nullptr;
   int64_t perm_stride = 0, boff_stride = 0;
   int64_t nslots = 0;
@@ -103,6 +106,7 @@ struct rs_ctx {
 
   bool mixed() const { return precision == RS_MIXED; }
   size_t elem() const { return mixed() ? sizeof(float) : sizeof(double); }
+  bool f64_factor() const { return !mixed() || chol_fp64 == 1; }
 };
 
 #define CKC(ctx, call)                                                                      \
@@ -132,8 +136,8 @@ rs_status dalloc(rs_ctx* c, T** p, size_t n) {
 
 void free_all(rs_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
-  void* ptrs[] = {c->X, c->y, c->A, c->b, c->w, c->wp, c->r, c->rp, c->u, c->SA, c->S, c->M,
-                  c->rS, c->delta, c->chol_scratch, c->perm, c->boff, c->err_flag, c->ndropped,
+  void* ptrs[] = {c->X, c->y, c->A, c->b, c->w, c->wp, c->r, c->rp, c->u, c->SA, c->ST, c->M,
+                  c->Linv, c->fws, c->rS, c->delta, c->perm, c->boff, c->err_flag, c->ndropped,
                   c->gam, c->bet, c->hist, c->partials, c->vn, c->vd, c->xt_part, c->rel_dev,
                   c->ctrl};
   for (void* p : ptrs)
@@ -162,6 +166,9 @@ RowsView<T> rows_view(const rs_ctx* c) {
   v.lda = c->ld;
   v.SA = (c->sketch == RS_SUBSAMPLE) ? nullptr : static_cast<const T*>(c->SA);
   v.ldsa = c->ld;
+  v.sa_slot = c->sa_slot;
+  v.ST = (c->sketch == RS_GAUSSIAN) ? static_cast<const T*>(c->ST) : nullptr;
+  v.st_slot = c->sa_slot;
   return v;
 }
 
@@ -191,88 +198,116 @@ rs_status enqueue_gen(rs_ctx* c, int64_t k0_arg, int nslots) {
   return RS_OK;
 }
 
-// sketched system of the current (force = 0) or given (force = 1, k_arg) iteration:
-// S^T A, M, r_S
+// Phase 1 of a chunk (independent of the iterate): sketch plans, S^T A, M = S^T A S
+// and the inverse Cholesky factor of M for `nslots` consecutive iterations. force = 1
+// (parity hooks) runs every slot starting at iteration k0_arg; force = 0 starts at
+// ctrl->k0 and skips slots the solve will not reach.
 template <typename T>
-rs_status enqueue_system(rs_ctx* c, int force, int64_t k_arg) {
+rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots) {
   cudaStream_t st = c->stream;
+  rs_status s = enqueue_gen(c, force ? k0_arg : -1, nslots);
+  if (s != RS_OK) return s;
   const PlanView plan = plan_view(c);
   const T* A = static_cast<const T*>(c->A);
   T* SA = static_cast<T*>(c->SA);
   switch (c->sketch) {
     case RS_SUBSAMPLE:
-      CKC(c, launch_msys_rows<T>(st, c->ctrl, force, plan, rows_view<T>(c), c->m, c->tau, c->r,
-                                 c->M, c->rS));
+      CKC(c, launch_msys_batched<T>(st, c->ctrl, force, nslots, plan, rows_view<T>(c), c->m, c->tau,
+                                    c->M, c->m_slot));
       break;
     case RS_COUNT:
     case RS_SUBCOUNT:
-      CKC(c, launch_sa_rows<T>(st, c->ctrl, force, plan, A, c->ld, c->m, c->tau, SA, c->ld));
-      CKC(c, launch_msys_rows<T>(st, c->ctrl, force, plan, rows_view<T>(c), c->m, c->tau, c->r,
-                                 c->M, c->rS));
+      CKC(c, launch_sa_batched<T>(st, c->ctrl, force, nslots, plan, A, c->ld, c->m, c->tau, SA,
+                                  c->ld, c->sa_slot));
+      CKC(c, launch_msys_batched<T>(st, c->ctrl, force, nslots, plan, rows_view<T>(c), c->m, c->tau,
+                                    c->M, c->m_slot));
       break;
     case RS_GAUSSIAN: {
-      T* S = static_cast<T*>(c->S);
-      CKC(c, launch_gen_gauss<T>(st, c->ctrl, force ? k_arg : -1, c->seed, c->m, c->tau, S));
-      CKC(c, launch_gauss_sa<T>(st, c->ctrl, force, S, A, c->ld, c->m, c->tau, SA, c->ld));
-      CKC(c, launch_gauss_msys<T>(st, c->ctrl, force, S, SA, c->ld, c->m, c->tau, c->r, c->M,
-                                  c->rS));
+      T* ST = static_cast<T*>(c->ST);
+      CKC(c, launch_gen_gauss<T>(st, c->ctrl, force, nslots, k0_arg, c->seed, c->m, c->tau, ST,
+                                 c->ld, c->sa_slot));
+      CKC(c, launch_gauss_system<T>(st, c->ctrl, force, nslots, ST, c->sa_slot, A, c->ld, c->m,
+                                    c->tau, SA, c->ld, c->sa_slot, c->M, c->m_slot));
       break;
     }
     case RS_SRHT:
-      CKC(c, launch_srht_sa<T>(st, c->ctrl, force, k_arg, c->seed, plan, A, c->ld, c->m, c->mp,
-                               c->tau, SA, c->ld));
-      CKC(c, launch_srht_msys<T>(st, c->ctrl, force, k_arg, c->seed, plan, SA, c->ld, c->m, c->mp,
-                                 c->tau, c->r, c->M, c->rS));
+      CKC(c, launch_srht_system<T>(st, c->ctrl, force, nslots, k0_arg, c->seed, plan, A, c->ld, c->m,
+                                   c->mp, c->tau, SA, c->ld, c->sa_slot, c->M, c->m_slot));
       break;
   }
+  if (c->f64_factor())
+    CKC(c, launch_factor_inv<double>(st, c->ctrl, force, nslots, c->M, c->m_slot, c->tau,
+                                     static_cast<double*>(c->Linv), c->l_slot,
+                                     static_cast<double*>(c->fws), c->ndropped));
+  else
+    CKC(c, launch_factor_inv<float>(st, c->ctrl, force, nslots, c->M, c->m_slot, c->tau,
+                                    static_cast<float*>(c->Linv), c->l_slot,
+                                    static_cast<float*>(c->fws), c->ndropped));
   return RS_OK;
 }
 
-rs_status enqueue_solve_small(rs_ctx* c, int force, int64_t k_arg) {
+rs_status enqueue_phase1(rs_ctx* c, int force, int64_t k0_arg, int nslots) {
+  return c->mixed() ? enqueue_phase1_t<float>(c, force, k0_arg, nslots)
+                    : enqueue_phase1_t<double>(c, force, k0_arg, nslots);
+}
+
+template <typename TF, typename T>
+DeltaArgs<TF> delta_args(rs_ctx* c) {
+  DeltaArgs<TF> g{};
+  g.kind = c->sketch == RS_GAUSSIAN ? 1 : (c->sketch == RS_SRHT ? 2 : 0);
+  g.plan = plan_view(c);
+  g.ST = nullptr;
+  g.st_slot = c->sa_slot;
+  g.ld = c->ld;
+  g.seed = c->seed;
+  g.mp = c->mp;
+  g.r = c->r;
+  g.m = c->m;
+  g.tau = c->tau;
+  g.Linv = static_cast<const TF*>(c->Linv);
+  g.l_slot = c->l_slot;
+  g.rS_out = c->rS;
+  g.delta_out = c->delta;
+  g.u = c->u;
+  return g;
+}
+
+// the sketched residual r_S = S^T r, delta = L^{-T} L^{-1} r_S and u = S delta of
+// the current (force = 0) or given (force = 1, slot 0) iteration
+rs_status enqueue_delta(rs_ctx* c, int force, int64_t k_arg) {
   cudaStream_t st = c->stream;
-  const bool bucket_rows = (c->sketch == RS_SUBSAMPLE || c->sketch == RS_COUNT ||
-                            c->sketch == RS_SUBCOUNT);
-  PlanView plan = bucket_rows ? plan_view(c) : PlanView{};
-  const bool f64 = !c->mixed() || c->chol_fp64;
-  if (f64)
-    CKC(c, launch_chol_solve<double>(st, c->ctrl, force, c->M, c->rS, c->tau,
-                                     static_cast<double*>(c->chol_scratch), c->delta, plan, c->u,
-                                     c->ndropped));
-  else
-    CKC(c, launch_chol_solve<float>(st, c->ctrl, force, c->M, c->rS, c->tau,
-                                    static_cast<float*>(c->chol_scratch), c->delta, plan, c->u,
-                                    c->ndropped));
-  if (c->sketch == RS_GAUSSIAN) {
-    if (c->mixed())
-      CKC(c, launch_gauss_u<float>(st, c->ctrl, force, static_cast<float*>(c->S), c->m, c->tau,
-                                   c->delta, c->u));
-    else
-      CKC(c, launch_gauss_u<double>(st, c->ctrl, force, static_cast<double*>(c->S), c->m, c->tau,
-                                    c->delta, c->u));
-  } else if (c->sketch == RS_SRHT) {
-    CKC(c, launch_srht_u(st, c->ctrl, force, k_arg, c->seed, plan_view(c), c->m, c->mp, c->tau,
-                         c->delta, c->u));
+  if (c->f64_factor()) {
+    DeltaArgs<double> g = delta_args<double, double>(c);
+    if (c->sketch == RS_GAUSSIAN) {
+      if (c->mixed()) return (c->err = "rs: Gaussian sketch with an FP64 factor needs FP64 S in the mixed form", RS_EUNSUPPORTED);
+      g.ST = static_cast<const double*>(c->ST);
+    }
+    CKC(c, launch_delta<double>(st, c->ctrl, force, k_arg, g));
+  } else {
+    DeltaArgs<float> g = delta_args<float, float>(c);
+    if (c->sketch == RS_GAUSSIAN) g.ST = static_cast<const float*>(c->ST);
+    CKC(c, launch_delta<float>(st, c->ctrl, force, k_arg, g));
   }
   return RS_OK;
 }
 
-template <typename T>
-rs_status enqueue_iteration_t(rs_ctx* c) {
-  rs_status s = enqueue_system<T>(c, 0, -1);
-  if (s != RS_OK) return s;
-  s = enqueue_solve_small(c, 0, -1);
-  if (s != RS_OK) return s;
+rs_status enqueue_update(rs_ctx* c) {
   UpdateArgs a{};
   a.gam = c->gam; a.bet = c->bet;
   a.w = c->w; a.wp = c->wp; a.r = c->r; a.rp = c->rp; a.u = c->u;
   a.delta = c->delta; a.partials = c->partials; a.hist = c->hist;
   a.mixed = c->mixed();
-  CKC(c, launch_update<T>(c->stream, c->ctrl, plan_view(c), rows_view<T>(c), c->m, c->tau, a));
+  if (c->mixed())
+    CKC(c, launch_update<float>(c->stream, c->ctrl, plan_view(c), rows_view<float>(c), c->m, c->tau, a));
+  else
+    CKC(c, launch_update<double>(c->stream, c->ctrl, plan_view(c), rows_view<double>(c), c->m, c->tau, a));
   return RS_OK;
 }
 
 rs_status enqueue_iteration(rs_ctx* c) {
-  return c->mixed() ? enqueue_iteration_t<float>(c) : enqueue_iteration_t<double>(c);
+  rs_status s = enqueue_delta(c, 0, -1);
+  if (s != RS_OK) return s;
+  return enqueue_update(c);
 }
 
 // true residual through X into vn / vd; v is the current iterate vector (m)
@@ -313,7 +348,7 @@ rs_status enqueue_refresh(rs_ctx* c) {
 
 rs_status enqueue_chunk(rs_ctx* c, bool with_refresh) {
   CKC(c, launch_chunk_begin(c->stream, c->ctrl));
-  rs_status s = enqueue_gen(c, -1, (int)c->nslots);
+  rs_status s = enqueue_phase1(c, 0, -1, (int)c->nslots);
   if (s != RS_OK) return s;
   for (int64_t i = 0; i < c->chunk; ++i) {
     s = enqueue_iteration(c);
@@ -459,7 +494,7 @@ void rs_default_opts(rs_opts* o) {
   o->sub_s = 0;
   o->cuda_stream = nullptr;
   o->device = 0;
-  o->chol_fp64 = 1;
+  o->chol_fp64 = 0;
   o->chunk = 0;
 }
 
@@ -518,6 +553,11 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   c->sketch = sketch;
   c->precision = o.precision;
   c->chol_fp64 = o.chol_fp64 ? 1 : 0;
+  if (c->mixed() && c->chol_fp64 && sketch == RS_GAUSSIAN) {
+    set_global_error("rs_create: the mixed Gaussian sketch factors in FP32 (chol_fp64 = 0)");
+    delete c;
+    return RS_EUNSUPPORTED;
+  }
   c->refresh_every = o.refresh_every > 0 ? o.refresh_every : 50;
   c->n = X->n;
   c->d = X->d;
@@ -532,7 +572,7 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   if (c->tau > m && sketch != RS_SRHT) { c->err = "rs_create: tau must be <= m"; return fail(RS_EINVAL); }
   if (sketch == RS_SRHT) {
     c->mp = pow2_ceil(m);
-    if (c->mp > srht_max_pad(8)) { c->err = "rs_create: SRHT needs 2^ceil(log2 m) <= 16384"; return fail(RS_EUNSUPPORTED); }
+    if (c->mp > srht_max_pad()) { c->err = "rs_create: SRHT needs 2^ceil(log2 m) <= 16384"; return fail(RS_EUNSUPPORTED); }
     if (c->tau > c->mp) { c->err = "rs_create: SRHT needs tau <= 2^ceil(log2 m)"; return fail(RS_EINVAL); }
   }
   if (sketch == RS_SUBCOUNT) {
@@ -559,8 +599,19 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { c->err = "rs_create: stream"; return fail(RS_ECUDA); }
     c->own_stream = true;
   }
-  c->chunk = o.chunk > 0 ? o.chunk : (c->mixed() ? c->refresh_every : 64);
+  c->chunk = o.chunk > 0 ? o.chunk : (c->mixed() ? c->refresh_every : 128);
   if (c->mixed() && c->chunk != c->refresh_every) c->chunk = c->refresh_every;
+  {
+    // keep the per-slot buffers of one chunk under 4 GB
+    const int64_t per_slot = (sketch == RS_SUBSAMPLE ? 0 : c->tau * c->ld * (int64_t)c->elem()) *
+                                 (sketch == RS_GAUSSIAN ? 2 : 1) +
+                             c->tau * c->tau * 16 + m * 4;
+    const int64_t cap = std::max<int64_t>(1, (int64_t)4e9 / std::max<int64_t>(per_slot, 1));
+    if (c->chunk > cap) {
+      if (c->mixed()) { c->err = "rs_create: refresh_every too large for the per-iteration buffers"; return fail(RS_EINVAL); }
+      c->chunk = cap;
+    }
+  }
   c->nslots = c->chunk;
   cudaStream_t st = c->stream;
   rs_status s;
@@ -613,7 +664,6 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   TRY(dalloc(c, &c->rp, m));
   TRY(dalloc(c, &c->u, m));
   TRYC(cudaMemsetAsync(c->u, 0, m * sizeof(double), st));
-  TRY(dalloc(c, &c->M, (size_t)c->tau * c->tau));
   TRY(dalloc(c, &c->rS, c->tau));
   TRY(dalloc(c, &c->delta, c->tau));
   TRY(dalloc(c, &c->err_flag, 1));
@@ -621,15 +671,25 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   TRYC(cudaMemsetAsync(c->err_flag, 0, sizeof(int32_t), st));
   TRYC(cudaMemsetAsync(c->ndropped, 0, sizeof(int32_t), st));
   {
-    const bool f64 = !c->mixed() || c->chol_fp64;
-    const size_t ne = f64 ? chol_scratch_elems<double>(c->tau) : chol_scratch_elems<float>(c->tau);
-    TRYC(cudaMalloc(&c->chol_scratch, ne * (f64 ? 8 : 4)));
+    // per-slot buffers of phase 1 (sketched rows, M, inverse factor)
+    const size_t fel = c->f64_factor() ? 8 : 4;
+    c->sa_slot = (sketch == RS_SUBSAMPLE) ? 0 : c->tau * c->ld;
+    c->m_slot = c->tau * c->tau;
+    c->l_slot = c->tau * c->tau;
+    const size_t nsl = (size_t)c->nslots;
+    TRY(dalloc(c, &c->M, nsl * c->m_slot));
+    TRYC(cudaMalloc(&c->Linv, nsl * c->l_slot * fel));
+    const size_t need_smem = (size_t)factor_ws_elems(c->tau) * fel + c->tau + 64;
+    if (need_smem > 200 * 1024) TRYC(cudaMalloc(&c->fws, nsl * factor_ws_elems(c->tau) * fel));
+    if (sketch != RS_SUBSAMPLE) {
+      TRYC(cudaMalloc(&c->SA, nsl * c->sa_slot * c->elem()));
+      TRYC(cudaMemsetAsync(c->SA, 0, nsl * c->sa_slot * c->elem(), st));
+    }
+    if (sketch == RS_GAUSSIAN) {
+      TRYC(cudaMalloc(&c->ST, nsl * c->sa_slot * c->elem()));
+      TRYC(cudaMemsetAsync(c->ST, 0, nsl * c->sa_slot * c->elem(), st));
+    }
   }
-  if (sketch != RS_SUBSAMPLE) {
-    TRYC(cudaMalloc(&c->SA, (size_t)c->tau * c->ld * c->elem()));
-    TRYC(cudaMemsetAsync(c->SA, 0, (size_t)c->tau * c->ld * c->elem(), st));
-  }
-  if (sketch == RS_GAUSSIAN) TRYC(cudaMalloc(&c->S, (size_t)m * c->tau * c->elem()));
   if (sketch != RS_GAUSSIAN) {
     c->perm_stride = (sketch == RS_COUNT) ? m : (sketch == RS_SUBCOUNT ? c->s : c->tau);
     c->boff_stride = c->tau + 1;
@@ -785,18 +845,23 @@ rs_status rs_dump_gaussian(rs_ctx* c, int64_t k, double* S) {
   if (!c || k < 0 || !S) return RS_EINVAL;
   if (c->sketch != RS_GAUSSIAN) FAILC(c, RS_EINVAL, "rs_dump_gaussian: not a Gaussian sketch");
   DeviceGuard dg(c->device);
-  const size_t n = (size_t)c->m * c->tau;
+  const size_t n = (size_t)c->tau * c->ld;
+  std::vector<double> st(n);
   if (c->mixed()) {
-    CKC(c, launch_gen_gauss<float>(c->stream, c->ctrl, k, c->seed, c->m, c->tau, static_cast<float*>(c->S)));
+    CKC(c, launch_gen_gauss<float>(c->stream, c->ctrl, 1, 1, k, c->seed, c->m, c->tau,
+                                   static_cast<float*>(c->ST), c->ld, c->sa_slot));
     std::vector<float> tmp(n);
-    CKC(c, cudaMemcpyAsync(tmp.data(), c->S, n * 4, cudaMemcpyDeviceToHost, c->stream));
+    CKC(c, cudaMemcpyAsync(tmp.data(), c->ST, n * 4, cudaMemcpyDeviceToHost, c->stream));
     CKC(c, cudaStreamSynchronize(c->stream));
-    for (size_t i = 0; i < n; ++i) S[i] = tmp[i];
+    for (size_t i = 0; i < n; ++i) st[i] = tmp[i];
   } else {
-    CKC(c, launch_gen_gauss<double>(c->stream, c->ctrl, k, c->seed, c->m, c->tau, static_cast<double*>(c->S)));
-    CKC(c, cudaMemcpyAsync(S, c->S, n * 8, cudaMemcpyDeviceToHost, c->stream));
+    CKC(c, launch_gen_gauss<double>(c->stream, c->ctrl, 1, 1, k, c->seed, c->m, c->tau,
+                                    static_cast<double*>(c->ST), c->ld, c->sa_slot));
+    CKC(c, cudaMemcpyAsync(st.data(), c->ST, n * 8, cudaMemcpyDeviceToHost, c->stream));
     CKC(c, cudaStreamSynchronize(c->stream));
   }
+  for (int64_t i = 0; i < c->m; ++i)
+    for (int64_t j = 0; j < c->tau; ++j) S[i * c->tau + j] = st[j * c->ld + i];
   return RS_OK;
 }
 
@@ -843,10 +908,8 @@ rs_status rs_probe_step(rs_ctx* c, double* M, double* r_S, double* delta) {
   rs_status s = read_ctrl(c);
   if (s != RS_OK) return s;
   const int64_t k = c->ctrl_h->k;
-  if ((s = enqueue_gen(c, k, 1)) != RS_OK) return s;
-  s = c->mixed() ? enqueue_system<float>(c, 1, k) : enqueue_system<double>(c, 1, k);
-  if (s != RS_OK) return s;
-  if ((s = enqueue_solve_small(c, 1, k)) != RS_OK) return s;
+  if ((s = enqueue_phase1(c, 1, k, 1)) != RS_OK) return s;
+  if ((s = enqueue_delta(c, 1, k)) != RS_OK) return s;
   const size_t t = c->tau;
   if (M) CKC(c, cudaMemcpyAsync(M, c->M, t * t * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   if (r_S) CKC(c, cudaMemcpyAsync(r_S, c->rS, t * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -949,71 +1012,71 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
     return RS_OK;
   };
   const double el = (double)c->elem();
-  const double m = (double)c->m, tau = (double)c->tau, ld = (double)c->ld;
-  const bool sub = c->sketch == RS_SUBSAMPLE;
+  const double fel = c->f64_factor() ? 8.0 : 4.0;
+  const double m = (double)c->m, tau = (double)c->tau;
+  const int ns = (int)c->nslots;
+  const double rows = c->sketch == RS_COUNT ? m : (c->sketch == RS_SUBCOUNT ? (double)c->s : tau);
   for (int64_t it = 0; it < reps && s == RS_OK; ++it) {
     if (it % c->chunk == 0) {
-      s = timed("gen", [&]() -> rs_status {
-        CKC(c, launch_chunk_begin(c->stream, c->ctrl));
-        return enqueue_gen(c, -1, (int)c->nslots);
-      });
-      if (s != RS_OK) break;
+      const double nsl = (double)std::min<int64_t>(ns, reps - it);
+      const PlanView plan = plan_view(c);
+      if (c->sketch == RS_GAUSSIAN || c->sketch == RS_SRHT) {
+        // one group for the whole phase 1 of these sketches
+        s = timed("phase1", [&]() -> rs_status {
+          CKC(c, launch_chunk_begin(c->stream, c->ctrl));
+          return enqueue_phase1(c, 0, -1, ns);
+        });
+        if (s != RS_OK) break;
+      } else {
+        s = timed("gen", [&]() -> rs_status {
+          CKC(c, launch_chunk_begin(c->stream, c->ctrl));
+          return enqueue_gen(c, -1, ns);
+        });
+        if (s != RS_OK) break;
+        if (c->sketch == RS_COUNT || c->sketch == RS_SUBCOUNT) {
+          s = timed("sa", [&]() -> rs_status {
+            if (c->mixed())
+              CKC(c, launch_sa_batched<float>(c->stream, c->ctrl, 0, ns, plan, static_cast<const float*>(c->A), c->ld, c->m, c->tau, static_cast<float*>(c->SA), c->ld, c->sa_slot));
+            else
+              CKC(c, launch_sa_batched<double>(c->stream, c->ctrl, 0, ns, plan, static_cast<const double*>(c->A), c->ld, c->m, c->tau, static_cast<double*>(c->SA), c->ld, c->sa_slot));
+            return RS_OK;
+          });
+          grp("sa").bytes = nsl * (rows * m * el + tau * m * el + rows * 4.0);
+          grp("sa").flops = nsl * rows * m;
+          if (s != RS_OK) break;
+        }
+        s = timed("msys", [&]() -> rs_status {
+          if (c->mixed()) CKC(c, launch_msys_batched<float>(c->stream, c->ctrl, 0, ns, plan, rows_view<float>(c), c->m, c->tau, c->M, c->m_slot));
+          else CKC(c, launch_msys_batched<double>(c->stream, c->ctrl, 0, ns, plan, rows_view<double>(c), c->m, c->tau, c->M, c->m_slot));
+          return RS_OK;
+        });
+        grp("msys").bytes = nsl * ((c->sketch == RS_SUBSAMPLE ? tau * tau * el : tau * m * el + rows * 4.0) + tau * tau * 8.0);
+        grp("msys").flops = nsl * (c->sketch == RS_SUBSAMPLE ? 0.0 : tau * rows);
+        if (s != RS_OK) break;
+        s = timed("factor", [&]() -> rs_status {
+          if (c->f64_factor())
+            CKC(c, launch_factor_inv<double>(c->stream, c->ctrl, 0, ns, c->M, c->m_slot, c->tau, static_cast<double*>(c->Linv), c->l_slot, static_cast<double*>(c->fws), c->ndropped));
+          else
+            CKC(c, launch_factor_inv<float>(c->stream, c->ctrl, 0, ns, c->M, c->m_slot, c->tau, static_cast<float*>(c->Linv), c->l_slot, static_cast<float*>(c->fws), c->ndropped));
+          return RS_OK;
+        });
+        grp("factor").bytes = nsl * (tau * tau * (8.0 + fel));
+        grp("factor").flops = nsl * (2.0 * tau * tau * tau / 3.0);
+        if (s != RS_OK) break;
+      }
     }
-    const PlanView plan = plan_view(c);
-    if (c->sketch == RS_COUNT || c->sketch == RS_SUBCOUNT) {
-      s = timed("sa_rows", [&]() -> rs_status {
-        if (c->mixed())
-          CKC(c, launch_sa_rows<float>(c->stream, c->ctrl, 0, plan, static_cast<const float*>(c->A), c->ld, c->m, c->tau, static_cast<float*>(c->SA), c->ld));
-        else
-          CKC(c, launch_sa_rows<double>(c->stream, c->ctrl, 0, plan, static_cast<const double*>(c->A), c->ld, c->m, c->tau, static_cast<double*>(c->SA), c->ld));
-        return RS_OK;
-      });
-      const double rows = (c->sketch == RS_COUNT) ? m : (double)c->s;
-      grp("sa_rows").bytes = rows * m * el + tau * m * el + rows * 4.0;
-      grp("sa_rows").flops = rows * m;
-      if (s != RS_OK) break;
-      s = timed("msys", [&]() -> rs_status {
-        if (c->mixed()) CKC(c, launch_msys_rows<float>(c->stream, c->ctrl, 0, plan, rows_view<float>(c), c->m, c->tau, c->r, c->M, c->rS));
-        else CKC(c, launch_msys_rows<double>(c->stream, c->ctrl, 0, plan, rows_view<double>(c), c->m, c->tau, c->r, c->M, c->rS));
-        return RS_OK;
-      });
-      grp("msys").bytes = tau * m * el + rows * 4.0 + rows * 8.0 + tau * tau * 8.0 + tau * 8.0;
-      grp("msys").flops = tau * rows + rows;
-    } else if (sub) {
-      s = timed("msys", [&]() -> rs_status {
-        if (c->mixed()) CKC(c, launch_msys_rows<float>(c->stream, c->ctrl, 0, plan, rows_view<float>(c), c->m, c->tau, c->r, c->M, c->rS));
-        else CKC(c, launch_msys_rows<double>(c->stream, c->ctrl, 0, plan, rows_view<double>(c), c->m, c->tau, c->r, c->M, c->rS));
-        return RS_OK;
-      });
-      grp("msys").bytes = tau * tau * (el + 8.0) + tau * 16.0;
-      grp("msys").flops = 0.0;
-    } else {
-      s = timed("system", [&]() -> rs_status {
-        return c->mixed() ? enqueue_system<float>(c, 0, -1) : enqueue_system<double>(c, 0, -1);
-      });
-    }
+    s = timed("delta", [&]() { return enqueue_delta(c, 0, -1); });
+    grp("delta").bytes = tau * tau * fel / 2.0 + rows * 12.0 + m * 8.0;
+    grp("delta").flops = 2.0 * tau * tau;
     if (s != RS_OK) break;
-    s = timed("chol", [&]() { return enqueue_solve_small(c, 0, -1); });
-    grp("chol").bytes = tau * tau * 8.0 + tau * 16.0;
-    grp("chol").flops = tau * tau * tau / 3.0 + 2.0 * tau * tau;
-    if (s != RS_OK) break;
-    s = timed("update", [&]() -> rs_status {
-      UpdateArgs a{};
-      a.gam = c->gam; a.bet = c->bet; a.w = c->w; a.wp = c->wp; a.r = c->r; a.rp = c->rp;
-      a.u = c->u; a.delta = c->delta; a.partials = c->partials; a.hist = c->hist;
-      a.mixed = c->mixed();
-      if (c->mixed()) CKC(c, launch_update<float>(c->stream, c->ctrl, plan, rows_view<float>(c), c->m, c->tau, a));
-      else CKC(c, launch_update<double>(c->stream, c->ctrl, plan, rows_view<double>(c), c->m, c->tau, a));
-      return RS_OK;
-    });
-    grp("update").bytes = tau * m * el + m * 8.0 * 9.0;
+    s = timed("update", [&]() { return enqueue_update(c); });
+    grp("update").bytes = (c->sketch == RS_SUBSAMPLE ? tau * m * el : tau * m * el) + m * 8.0 * 9.0;
     grp("update").flops = 2.0 * tau * m + 10.0 * m;
     if (s == RS_OK && c->mixed() && (it + 1) % c->refresh_every == 0) {
       s = timed("refresh", [&]() { return enqueue_refresh(c); });
       grp("refresh").bytes = 2.0 * (double)c->n * (double)c->d * (c->xdtype == RS_F32 ? 4.0 : 8.0) + m * 48.0;
       grp("refresh").flops = 4.0 * (double)c->n * (double)c->d;
     }
-    (void)ld;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -59,6 +59,15 @@ __device__ __forceinline__ bool halted(const Ctrl* c) {
   return (*(volatile const int32_t*)&c->stop) | (*(volatile const int32_t*)&c->pending);
 }
 
+// number of slots of the current chunk that run: all of them for a forced (probe)
+// launch, none once the solve has stopped, else those below max_iters
+__device__ __forceinline__ int64_t active_slots(const Ctrl* c, int force, int nslots) {
+  if (force) return nslots;
+  if (halted(c)) return 0;
+  const int64_t left = c->max_iters - c->k0;
+  return left < 0 ? 0 : (left < nslots ? left : (int64_t)nslots);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -81,6 +90,23 @@ __device__ T block_sum(T v, T* sh /* >= 32 entries */) {
   T r = sh[0];
   __syncthreads();
   return r;
+}
+
+// In-place fast Walsh-Hadamard transform of length n (a power of two) in shared
+// memory, Sylvester order (entry (i, c) of H is (-1)^popcount(i & c)). Called by
+// every thread of the block.
+template <typename T>
+__device__ void fwht_smem(T* buf, int64_t n) {
+  for (int64_t h = 1; h < n; h <<= 1) {
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < (n >> 1); t += blockDim.x) {
+      const int64_t i = (t / h) * 2 * h + (t % h);
+      const T a = buf[i], b = buf[i + h];
+      buf[i] = a + b;
+      buf[i + h] = a - b;
+    }
+  }
+  __syncthreads();
 }
 
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }

@@ -12,11 +12,16 @@ namespace rs {
 
 template <typename TI, typename TA, typename TO>
 __global__ void __launch_bounds__(256)
-k_gemm_strided(int64_t M, int64_t N, int64_t K, const TI* __restrict__ P, int64_t p0, int64_t p1,
-               const TI* __restrict__ Q, int64_t q0, int64_t q1, TO* __restrict__ C, int64_t ldc,
-               double diag, int lower_only, const Ctrl* __restrict__ ctrl) {
+k_gemm_strided(int64_t M, int64_t N, int64_t K, const TI* P, int64_t p0, int64_t p1,
+               const TI* Q, int64_t q0, int64_t q1, TO* C, int64_t ldc,
+               double diag, int lower_only, const Ctrl* __restrict__ ctrl, int64_t bP,
+               int64_t bQ, int64_t bC) {
   constexpr int BM = 64, BN = 64, BK = 16;
-  if (ctrl != nullptr && halted(ctrl)) return;
+  // batched use (blockIdx.z = slot of a chunk): skip slots the solve will not reach
+  if (ctrl != nullptr && (int64_t)blockIdx.z >= active_slots(ctrl, 0, gridDim.z)) return;
+  P += (int64_t)blockIdx.z * bP;
+  Q += (int64_t)blockIdx.z * bQ;
+  C += (int64_t)blockIdx.z * bC;
   __shared__ TA sP[BK][BM + 4];
   __shared__ TA sQ[BK][BN + 4];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -84,10 +89,11 @@ template <typename TI, typename TA, typename TO>
 inline cudaError_t gemm_strided(cudaStream_t st, int64_t M, int64_t N, int64_t K, const TI* P,
                                 int64_t p0, int64_t p1, const TI* Q, int64_t q0, int64_t q1, TO* C,
                                 int64_t ldc, double diag, int lower_only = 0,
-                                const Ctrl* ctrl = nullptr) {
-  dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
+                                const Ctrl* ctrl = nullptr, int nbatch = 1, int64_t bP = 0,
+                                int64_t bQ = 0, int64_t bC = 0) {
+  dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64), (unsigned)nbatch);
   k_gemm_strided<TI, TA, TO><<<grid, 256, 0, st>>>(M, N, K, P, p0, p1, Q, q0, q1, C, ldc, diag,
-                                                  lower_only, ctrl);
+                                                  lower_only, ctrl, bP, bQ, bC);
   return cudaGetLastError();
 }
 

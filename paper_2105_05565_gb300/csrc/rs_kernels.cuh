@@ -18,76 +18,78 @@ cudaError_t launch_gen_sample(cudaStream_t st, const Ctrl* ctrl, int64_t k0_arg,
 cudaError_t launch_gen_count(cudaStream_t st, const Ctrl* ctrl, int64_t k0_arg, int nslots,
                              uint64_t seed, int64_t m, int64_t tau, int32_t* perm,
                              int64_t perm_stride, int32_t* boff, int64_t boff_stride);
+// Gaussian S of every slot, stored transposed: ST_s[j * ld + i] = S[i, j]
 template <typename T>
-cudaError_t launch_gen_gauss(cudaStream_t st, const Ctrl* ctrl, int64_t k_arg, uint64_t seed,
-                             int64_t m, int64_t tau, T* S);
+cudaError_t launch_gen_gauss(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
+                             int64_t k0_arg, uint64_t seed, int64_t m, int64_t tau, T* ST,
+                             int64_t ld, int64_t st_slot);
 
-// ---- applying the sketch (rs_apply.cu) ----
-// Where the tau "sketched rows" S^T A live: rows of A picked by the sample
-// (subsample, no copy) or a materialised tau x ld buffer.
-template <typename T>
-struct RowsView {
-  const T* A;        // A, row-major, leading dimension lda
-  int64_t lda;
-  const T* SA;       // materialised S^T A (tau x ldsa) or nullptr (subsample)
-  int64_t ldsa;
-};
-struct PlanView {    // bucket-row representation of subsample / count / subcount
+// ---- applying the sketch, phase 1 (rs_apply.cu) ----
+struct PlanView {    // bucket-row representation of subsample / count / subcount (and SRHT's C)
   const int32_t* perm;  // packed (row | sign bit), grouped by bucket
   const int32_t* boff;  // tau + 1 bucket offsets
   int64_t perm_stride, boff_stride;  // per slot
 };
-// SA[j, :] = sum_{t in bucket j} sign_t A[row_t, :]   (count, subcount)
+// Where the tau "sketched rows" S^T A of a slot live: rows of A picked by the
+// sample (subsample, no copy) or a materialised tau x ldsa buffer per slot;
+// ST: transposed Gaussian sketch per slot (Gaussian only).
 template <typename T>
-cudaError_t launch_sa_rows(cudaStream_t st, const Ctrl* ctrl, int force, PlanView plan,
-                           const T* A, int64_t lda, int64_t m, int64_t tau, T* SA, int64_t ldsa);
-// M = S^T A S (tau x tau, FP64 out) and r_S = S^T r for the bucket-row sketches
+struct RowsView {
+  const T* A;
+  int64_t lda;
+  const T* SA;       // nullptr for subsample
+  int64_t ldsa, sa_slot;
+  const T* ST;       // Gaussian: tau x lda per slot, else nullptr
+  int64_t st_slot;
+};
 template <typename T>
-cudaError_t launch_msys_rows(cudaStream_t st, const Ctrl* ctrl, int force, PlanView plan,
-                             RowsView<T> rows, int64_t m, int64_t tau, const double* r,
-                             double* M, double* rS);
-// Gaussian: SA = S^T A, M = SA S, r_S = S^T r; u = S delta
+cudaError_t launch_sa_batched(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
+                              PlanView plan, const T* A, int64_t lda, int64_t m, int64_t tau, T* SA,
+                              int64_t ldsa, int64_t sa_slot);
 template <typename T>
-cudaError_t launch_gauss_sa(cudaStream_t st, const Ctrl* ctrl, int force, const T* S, const T* A,
-                            int64_t lda, int64_t m, int64_t tau, T* SA, int64_t ldsa);
+cudaError_t launch_msys_batched(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
+                                PlanView plan, RowsView<T> rows, int64_t m, int64_t tau,
+                                double* M, int64_t m_slot);
 template <typename T>
-cudaError_t launch_gauss_msys(cudaStream_t st, const Ctrl* ctrl, int force, const T* S,
-                              const T* SA, int64_t ldsa, int64_t m, int64_t tau, const double* r,
-                              double* M, double* rS);
+cudaError_t launch_gauss_system(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
+                                const T* ST, int64_t st_slot, const T* A, int64_t lda, int64_t m,
+                                int64_t tau, T* SA, int64_t ldsa, int64_t sa_slot, double* M,
+                                int64_t m_slot);
 template <typename T>
-cudaError_t launch_gauss_u(cudaStream_t st, const Ctrl* ctrl, int force, const T* S, int64_t m,
-                           int64_t tau, const double* delta, double* u);
-// SRHT (m' = 2^ceil(log2 m)): SA, M, r_S, u through fast Walsh-Hadamard transforms
-template <typename T>
-cudaError_t launch_srht_sa(cudaStream_t st, const Ctrl* ctrl, int force, int64_t k_arg,
-                           uint64_t seed, PlanView C, const T* A, int64_t lda, int64_t m,
-                           int64_t mp, int64_t tau, T* SA, int64_t ldsa);
-template <typename T>
-cudaError_t launch_srht_msys(cudaStream_t st, const Ctrl* ctrl, int force, int64_t k_arg,
-                             uint64_t seed, PlanView C, const T* SA, int64_t ldsa, int64_t m,
-                             int64_t mp, int64_t tau, const double* r, double* M, double* rS);
-cudaError_t launch_srht_u(cudaStream_t st, const Ctrl* ctrl, int force, int64_t k_arg,
-                          uint64_t seed, PlanView C, int64_t m, int64_t mp, int64_t tau,
-                          const double* delta, double* u);
-int64_t srht_max_pad(int elem_bytes);
+cudaError_t launch_srht_system(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
+                               int64_t k0_arg, uint64_t seed, PlanView plan, const T* A,
+                               int64_t lda, int64_t m, int64_t mp, int64_t tau, T* SA, int64_t ldsa,
+                               int64_t sa_slot, double* M, int64_t m_slot);
+int64_t srht_max_pad();
 
-// ---- small SPD solve (rs_chol.cu) ----
-// delta = least-norm solution of M delta = r_S by Cholesky with the pivot rule:
-// a pivot below tau * eps * max_i M_ii drops its index (delta_j = 0). When perm /
-// boff are given, also scatters u[row_t] = sign_t delta_j over bucket j.
+// ---- small SPD system (rs_chol.cu) ----
+size_t factor_ws_elems(int64_t tau);
 template <typename T>
-cudaError_t launch_chol_solve(cudaStream_t st, const Ctrl* ctrl, int force, const double* M,
-                              const double* rS, int64_t tau, T* gscratch, double* delta,
-                              PlanView plan, double* u, int32_t* ndropped);
+cudaError_t launch_factor_inv(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
+                              const double* M, int64_t m_slot, int64_t tau, T* Linv, int64_t l_slot,
+                              T* ws, int32_t* ndropped);
 template <typename T>
-size_t chol_scratch_elems(int64_t tau);
+struct DeltaArgs {
+  int kind;            // 0 bucket rows (subsample, count, subcount), 1 Gaussian, 2 SRHT
+  PlanView plan;
+  const T* ST; int64_t st_slot, ld;
+  uint64_t seed; int64_t mp;
+  const double* r; int64_t m, tau;
+  const T* Linv; int64_t l_slot;
+  double* rS_out;      // may be nullptr
+  double* delta_out;
+  double* u;           // dense S delta (bucket rows, SRHT)
+};
+template <typename T>
+cudaError_t launch_delta(cudaStream_t st, const Ctrl* ctrl, int force, int64_t k_arg,
+                         DeltaArgs<T> g);
 
 // ---- iterate / residual update (rs_update.cu) ----
 struct UpdateArgs {
   const double* gam;  // gamma_k table
   const double* bet;  // beta_k table
   double* w; double* wp; double* r; double* rp;
-  double* u;          // dense S delta (reset to 0 after use)
+  double* u;          // dense S delta (reset to 0 after use); unused with rows.ST
   const double* delta;
   double* partials;   // per-block partial ||r||^2
   double* hist;       // hist[k + 1] written by the last block
@@ -97,7 +99,7 @@ template <typename T>
 cudaError_t launch_update(cudaStream_t st, Ctrl* ctrl, PlanView plan, RowsView<T> rows,
                           int64_t m, int64_t tau, UpdateArgs a);
 int update_blocks(int64_t m);
-// w = w_prev = u = 0, r = r_prev = -b, hist[0] = (||b|| > 0)
+// w = w_prev = u = 0, r = r_prev = -b
 cudaError_t launch_init_state(cudaStream_t st, int64_t m, const double* b, double* w, double* wp,
                               double* r, double* rp, double* u);
 // ctrl->k0 = ctrl->k (first iteration of a chunk)

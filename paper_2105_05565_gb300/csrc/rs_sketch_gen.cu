@@ -207,19 +207,25 @@ __global__ void __launch_bounds__(1024) k_gen_count(const Ctrl* __restrict__ ctr
   }
 }
 
-// Gaussian sketch entries S[i * tau + j] (Box-Muller on draws of streams 2, 3).
+// Gaussian sketch entries (Box-Muller on draws of streams 2, 3), stored
+// transposed per slot: ST_s[j * ld + i] = S_k[i, j] with lane i * tau + j, k = k0 + s.
 template <typename T>
-__global__ void k_gen_gauss(const Ctrl* __restrict__ ctrl, int64_t k_arg, uint64_t seed, int64_t m,
-                            int64_t tau, T* __restrict__ S) {
-  if (k_arg < 0 && halted(ctrl)) return;
-  const int64_t k = k_arg >= 0 ? k_arg : ctrl->k;
+__global__ void k_gen_gauss(const Ctrl* __restrict__ ctrl, int force, int nslots, int64_t k0_arg,
+                            uint64_t seed, int64_t m, int64_t tau, T* __restrict__ ST, int64_t ld,
+                            int64_t st_slot) {
+  const int64_t nact = active_slots(ctrl, force, nslots);
+  const int64_t s = blockIdx.y;
+  if (s >= nact) return;
+  const int64_t k = (force ? k0_arg : ctrl->k0) + s;
   const uint64_t key = iter_key(seed, k);
   const int64_t total = m * tau;
+  T* out = ST + s * st_slot;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < total;
        l += (int64_t)gridDim.x * blockDim.x) {
     const double u1 = ((double)(draw_k(key, 2, l) >> 11) + 1.0) * 0x1.0p-53;
     const double u2 = (double)(draw_k(key, 3, l) >> 11) * 0x1.0p-53;
-    S[l] = (T)(sqrt(-2.0 * log(u1)) * cospi(2.0 * u2));
+    const int64_t i = l / tau, j = l - i * tau;
+    out[j * ld + i] = (T)(sqrt(-2.0 * log(u1)) * cospi(2.0 * u2));
   }
 }
 
@@ -261,17 +267,19 @@ cudaError_t launch_gen_count(cudaStream_t st, const Ctrl* ctrl, int64_t k0_arg, 
 }
 
 template <typename T>
-cudaError_t launch_gen_gauss(cudaStream_t st, const Ctrl* ctrl, int64_t k_arg, uint64_t seed,
-                             int64_t m, int64_t tau, T* S) {
+cudaError_t launch_gen_gauss(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
+                             int64_t k0_arg, uint64_t seed, int64_t m, int64_t tau, T* ST,
+                             int64_t ld, int64_t st_slot) {
   const int64_t total = m * tau;
-  int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  int blocks = (int)std::min<int64_t>((total + 255) / 256, 1024);
   if (blocks < 1) blocks = 1;
-  k_gen_gauss<T><<<blocks, 256, 0, st>>>(ctrl, k_arg, seed, m, tau, S);
+  k_gen_gauss<T><<<dim3(blocks, nslots), 256, 0, st>>>(ctrl, force, nslots, k0_arg, seed, m, tau,
+                                                        ST, ld, st_slot);
   return cudaGetLastError();
 }
-template cudaError_t launch_gen_gauss<double>(cudaStream_t, const Ctrl*, int64_t, uint64_t, int64_t,
-                                              int64_t, double*);
-template cudaError_t launch_gen_gauss<float>(cudaStream_t, const Ctrl*, int64_t, uint64_t, int64_t,
-                                             int64_t, float*);
+template cudaError_t launch_gen_gauss<double>(cudaStream_t, const Ctrl*, int, int, int64_t, uint64_t,
+                                              int64_t, int64_t, double*, int64_t, int64_t);
+template cudaError_t launch_gen_gauss<float>(cudaStream_t, const Ctrl*, int, int, int64_t, uint64_t,
+                                             int64_t, int64_t, float*, int64_t, int64_t);
 
 }  // namespace rs

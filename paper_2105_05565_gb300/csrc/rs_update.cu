@@ -9,7 +9,7 @@
 namespace rs {
 
 constexpr int kUpdCols = 32;   // elements i per block
-constexpr int kUpdWarps = 8;   // warps splitting the tau rows
+constexpr int kUpdWarps = 16;  // warps splitting the tau rows (4 row loads in flight each)
 
 int update_blocks(int64_t m) { return ceil_div(m, kUpdCols); }
 
@@ -17,28 +17,44 @@ template <typename T> struct AccT { using type = double; };
 template <> struct AccT<float> { using type = float; };
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_update(Ctrl* __restrict__ ctrl, PlanView plan,
+__global__ void __launch_bounds__(512) k_update(Ctrl* __restrict__ ctrl, PlanView plan,
                                                 RowsView<T> rows, int64_t m, int64_t tau,
                                                 UpdateArgs a) {
   using TA = typename AccT<T>::type;
   if (halted(ctrl)) return;
   __shared__ TA red[kUpdWarps][kUpdCols + 1];
+  __shared__ TA ured[kUpdWarps][kUpdCols + 1];
   __shared__ double s_part[kUpdWarps];
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t k = ctrl->k;
   const int64_t i = (int64_t)blockIdx.x * kUpdCols + lane;
-  const int32_t* perm = plan.perm ? plan.perm + (k - ctrl->k0) * plan.perm_stride : nullptr;
+  const int64_t slot = k - ctrl->k0;
+  const int32_t* perm = plan.perm ? plan.perm + slot * plan.perm_stride : nullptr;
+  const T* SA = rows.SA ? rows.SA + slot * rows.sa_slot : nullptr;
+  const T* ST = rows.ST ? rows.ST + slot * rows.st_slot : nullptr;
 
-  TA acc = TA(0);
+  TA acc = TA(0), uacc = TA(0);
   if (i < m) {
-    for (int64_t j = w; j < tau; j += kUpdWarps) {
-      const T* rowj = rows.SA ? rows.SA + j * rows.ldsa
-                              : rows.A + (int64_t)entry_row(perm[j]) * rows.lda;
-      acc += (TA)rowj[i] * (TA)a.delta[j];
+    auto rowp = [&](int64_t j) -> const T* {
+      return SA ? SA + j * rows.ldsa : rows.A + (int64_t)entry_row(perm[j]) * rows.lda;
+    };
+    if (ST)  // Gaussian: (S delta)_i = sum_j ST[j, i] delta_j
+      for (int64_t j = w; j < tau; j += kUpdWarps) uacc += (TA)ST[j * rows.lda + i] * (TA)a.delta[j];
+    int64_t j = w;
+    // four independent row loads in flight per warp; the sum keeps the j order
+    for (; j + 3 * kUpdWarps < tau; j += 4 * kUpdWarps) {
+      const T v0 = rowp(j)[i], v1 = rowp(j + kUpdWarps)[i];
+      const T v2 = rowp(j + 2 * kUpdWarps)[i], v3 = rowp(j + 3 * kUpdWarps)[i];
+      acc += (TA)v0 * (TA)a.delta[j];
+      acc += (TA)v1 * (TA)a.delta[j + kUpdWarps];
+      acc += (TA)v2 * (TA)a.delta[j + 2 * kUpdWarps];
+      acc += (TA)v3 * (TA)a.delta[j + 3 * kUpdWarps];
     }
+    for (; j < tau; j += kUpdWarps) acc += (TA)rowp(j)[i] * (TA)a.delta[j];
   }
   red[w][lane] = acc;
+  ured[w][lane] = uacc;
   __syncthreads();
   if (w == 0) {
     double sq = 0.0;
@@ -47,8 +63,16 @@ __global__ void __launch_bounds__(256) k_update(Ctrl* __restrict__ ctrl, PlanVie
 #pragma unroll
       for (int q = 0; q < kUpdWarps; ++q) s += red[q][lane];
       const double g = a.gam[k], b = a.bet[k];
-      const double ui = a.u[i];
-      a.u[i] = 0.0;
+      double ui;
+      if (ST) {
+        TA us = TA(0);
+#pragma unroll
+        for (int q = 0; q < kUpdWarps; ++q) us += ured[q][lane];
+        ui = (double)us;
+      } else {
+        ui = a.u[i];
+        a.u[i] = 0.0;
+      }
       const double wi = a.w[i], wpi = a.wp[i], ri = a.r[i], rpi = a.rp[i];
       const double wn = (1.0 + b) * wi - b * wpi - g * ui;
       const double rn = (1.0 + b) * ri - b * rpi - g * (double)s;
@@ -94,7 +118,7 @@ __global__ void __launch_bounds__(256) k_update(Ctrl* __restrict__ ctrl, PlanVie
 template <typename T>
 cudaError_t launch_update(cudaStream_t st, Ctrl* ctrl, PlanView plan, RowsView<T> rows, int64_t m,
                           int64_t tau, UpdateArgs a) {
-  k_update<T><<<update_blocks(m), 256, 0, st>>>(ctrl, plan, rows, m, tau, a);
+  k_update<T><<<update_blocks(m), 32 * kUpdWarps, 0, st>>>(ctrl, plan, rows, m, tau, a);
   return cudaGetLastError();
 }
 
