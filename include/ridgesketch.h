@@ -112,9 +112,13 @@ typedef struct {
                             Section 4.2: k = 10 if 10 tau <= m else floor(m/tau), s = k tau */
   void* cuda_stream;     /* cudaStream_t to issue work on; NULL = library-owned stream */
   int32_t device;        /* CUDA device ordinal; default 0 */
-  int32_t chol_fp64;     /* RS_MIXED only: 1 = factor S^T A S in FP64 (default), 0 = FP32 */
-  int64_t chunk;         /* iterations per device-side chunk (one CUDA graph replay);
-                            0 = refresh_every (mixed) or 64 (plain) */
+  int32_t chol_fp64;     /* RS_MIXED only: 1 = factor S^T A S in FP64, 0 = FP32 (default;
+                            S^T A S is formed from the FP32 A there). RS_PLAIN_FP64 always
+                            factors in FP64. The Gaussian sketch in RS_MIXED needs 0. */
+  int64_t chunk;         /* iterations per device-side chunk (one CUDA graph replay); the
+                            sketched systems of a chunk are formed and factored ahead in
+                            batched launches. 0 = refresh_every (mixed) or 128 (plain),
+                            reduced so that the chunk's buffers stay under 4 GB */
 } rs_opts;
 
 /* Fill *o with the defaults listed above. */

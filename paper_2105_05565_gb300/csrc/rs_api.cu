@@ -679,8 +679,9 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     const size_t nsl = (size_t)c->nslots;
     TRY(dalloc(c, &c->M, nsl * c->m_slot));
     TRYC(cudaMalloc(&c->Linv, nsl * c->l_slot * fel));
-    const size_t need_smem = (size_t)factor_ws_elems(c->tau) * fel + c->tau + 64;
-    if (need_smem > 200 * 1024) TRYC(cudaMalloc(&c->fws, nsl * factor_ws_elems(c->tau) * fel));
+    const size_t need_smem = (size_t)factor_ws_elems(c->tau) * fel + 4096;
+    if (need_smem > 220 * 1024 || c->tau > 4096)
+      TRYC(cudaMalloc(&c->fws, nsl * factor_ws_elems(c->tau) * fel));
     if (sketch != RS_SUBSAMPLE) {
       TRYC(cudaMalloc(&c->SA, nsl * c->sa_slot * c->elem()));
       TRYC(cudaMemsetAsync(c->SA, 0, nsl * c->sa_slot * c->elem(), st));

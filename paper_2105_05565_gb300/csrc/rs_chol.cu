@@ -1,10 +1,10 @@
 // The small SPD system of eq. (14): delta = (S^T A S)^dagger r_S.
 //
-// Phase 1 (k_factor_inv, batched over the slots of a chunk, one CTA per slot):
-// Cholesky factorisation M = L L^T, right-looking, with the pivot rule of the
+// Phase 1 (k_factor_blk, batched over the slots of a chunk, one CTA per slot):
+// blocked Cholesky factorisation M = L L^T, right-looking, with the pivot rule of the
 // least-norm case: a pivot at most tau * eps * max_i M_ii drops its index j (row
 // and column j of L become e_j). The triangular factor is then inverted in place
-// (right-looking triangular solve against the identity) and the dropped rows and
+// (block row by block row) and the dropped rows and
 // columns of L^{-1} are zeroed, so that
 //     delta = L^{-T} (L^{-1} r_S)
 // is the solution of the reduced system with delta_j = 0 at dropped indices.
@@ -26,17 +26,72 @@ template <typename T> struct Eps;
 template <> struct Eps<float> { static constexpr double v = 1.1920928955078125e-07; };
 template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
 
-template <typename T>
-size_t factor_smem_bytes(int64_t tau) {
-  return (size_t)pk(tau, 0) * sizeof(T) + (size_t)tau + 64;
-}
-size_t factor_ws_elems(int64_t tau) { return (size_t)pk(tau, 0); }
+// ---------------------------------------------------------------------------
+// phase 1: blocked factor and inverse, one CTA (512 threads = 16 warps) per slot.
+// The lower triangle is held as NB x NB tiles (row stride NB + 1, so that rows of
+// a tile fall in distinct shared-memory banks); tile ops run one warp per tile,
+// each lane accumulating an 8 x 4 block of the output in registers.
+// ---------------------------------------------------------------------------
+constexpr int NBK = 32;        // tile size
+constexpr int TSK = NBK + 1;   // row stride of a tile
+constexpr int TILE = NBK * TSK;
 
-// ---------------------------------------------------------------------------
-// phase 1: factor and invert, one CTA (1024 threads) per slot
-// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int64_t ntiles_lower(int64_t P) { return P * (P + 1) / 2; }
+// tiles of the lower triangle + one temporary tile per row block
+__host__ __device__ size_t factor_ws_elems(int64_t tau) {
+  const int64_t P = (tau + NBK - 1) / NBK;
+  return (size_t)(ntiles_lower(P) + P) * TILE;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(1024) k_factor_inv(const Ctrl* __restrict__ ctrl, int force,
+__device__ __forceinline__ T* tile_at(T* base, int64_t I, int64_t J) {
+  return base + (I * (I + 1) / 2 + J) * TILE;
+}
+
+// acc (8 rows x 4 cols of the lane) += SGN * A op(B), op(B) = B^T (TB) or B
+template <typename T, bool TB, int SGN>
+__device__ __forceinline__ void wtile_mma(T (&acc)[8][4], const T* __restrict__ A,
+                                          const T* __restrict__ B, int ly, int lx) {
+#pragma unroll 2
+  for (int l = 0; l < NBK; ++l) {
+    T a[8], b[4];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) a[r] = A[(ly * 8 + r) * TSK + l];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) b[c] = TB ? B[(lx * 4 + c) * TSK + l] : B[l * TSK + lx * 4 + c];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (SGN > 0) acc[r][c] += a[r] * b[c];
+        else acc[r][c] -= a[r] * b[c];
+      }
+  }
+}
+template <typename T>
+__device__ __forceinline__ void wtile_zero(T (&acc)[8][4]) {
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = T(0);
+}
+template <typename T>
+__device__ __forceinline__ void wtile_load(T (&acc)[8][4], const T* C, int ly, int lx) {
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = C[(ly * 8 + r) * TSK + lx * 4 + c];
+}
+template <typename T>
+__device__ __forceinline__ void wtile_store(T* C, const T (&acc)[8][4], int ly, int lx) {
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) C[(ly * 8 + r) * TSK + lx * 4 + c] = acc[r][c];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_factor_blk(const Ctrl* __restrict__ ctrl, int force,
                                                      int nslots, const double* __restrict__ M,
                                                      int64_t m_slot, int64_t tau,
                                                      T* __restrict__ Linv, int64_t l_slot,
@@ -45,108 +100,184 @@ __global__ void __launch_bounds__(1024) k_factor_inv(const Ctrl* __restrict__ ct
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t s = blockIdx.x;
   if (s >= active_slots(ctrl, force, nslots)) return;
-  unsigned char* dropped = smem_raw;
-  T* a = use_smem ? reinterpret_cast<T*>(smem_raw + ((tau + 15) / 16) * 16) : ws + s * pk(tau, 0);
+  const int64_t P = (tau + NBK - 1) / NBK;
+  const int64_t tp = P * NBK;
+  unsigned char* dropped = smem_raw;  // tp flags (tau <= 4096)
+  T* tiles = use_smem ? reinterpret_cast<T*>(smem_raw + 4096)
+                      : ws + s * (int64_t)factor_ws_elems(tau);
+  T* temps = tiles + ntiles_lower(P) * TILE;
   const double* Ms = M + s * m_slot;
   T* out = Linv + s * l_slot;
   __shared__ double s_red[32];
-  __shared__ T s_piv;
-  __shared__ int s_drop;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int ly = lane >> 3, lx = lane & 7;
+  const unsigned full = 0xffffffffu;
 
+  // load the lower triangle into tiles (identity padding), max of the diagonal
   double dmax = 0.0;
-  for (int64_t i = tid; i < tau; i += blockDim.x) {
-    dropped[i] = 0;
-    dmax = fmax(dmax, Ms[i * tau + i]);
+  for (int64_t i = tid; i < tau; i += blockDim.x) dmax = fmax(dmax, Ms[i * tau + i]);
+  for (int64_t i = tid; i < tp; i += blockDim.x) dropped[i] = 0;
+  for (int64_t t = wid; t < ntiles_lower(P) * NBK; t += nw) {  // one tile row per warp step
+    const int64_t tile = t / NBK, rr = t - tile * NBK;
+    int64_t I = 0;
+    while ((I + 1) * (I + 2) / 2 <= tile) ++I;
+    const int64_t J = tile - I * (I + 1) / 2;
+    const int64_t R = I * NBK + rr, Cc = J * NBK + lane;
+    double v = 0.0;
+    if (R < tau && Cc < tau) v = Ms[R * tau + Cc];
+    else if (R == Cc) v = 1.0;
+    tiles[tile * TILE + rr * TSK + lane] = (T)v;
   }
-  for (int64_t i = wid; i < tau; i += nw)
-    for (int64_t j = lane; j <= i; j += 32) a[pk(i, j)] = (T)Ms[i * tau + j];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(full, dmax, o));
   if (lane == 0) s_red[wid] = dmax;
   __syncthreads();
   if (wid == 0) {
     double v = lane < nw ? s_red[lane] : 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(full, v, o));
     if (lane == 0) s_red[0] = v;
   }
   __syncthreads();
   const T thr = (T)((double)tau * Eps<T>::v * s_red[0]);
 
-  // Cholesky, column by column
-  int drops = 0;
-  for (int64_t k = 0; k < tau; ++k) {
-    if (tid == 0) {
-      const T d = a[pk(k, k)];
-      const int dr = !(d > thr);
-      s_drop = dr;
-      s_piv = dr ? T(1) : (T)sqrt((double)d);
-      a[pk(k, k)] = s_piv;
-      dropped[k] = (unsigned char)dr;
-      drops += dr;
-    }
-    __syncthreads();
-    const int dr = s_drop;
-    const T inv = dr ? T(0) : T(1) / s_piv;
-    for (int64_t i = k + 1 + tid; i < tau; i += blockDim.x) a[pk(i, k)] *= inv;
-    if (dr)
-      for (int64_t j = tid; j < k; j += blockDim.x) a[pk(k, j)] = T(0);
-    __syncthreads();
-    for (int64_t i = k + 1 + wid; i < tau; i += nw) {
-      const T lik = a[pk(i, k)];
-      if (lik != T(0)) {
-        T* rowi = a + pk(i, 0);
-        for (int64_t j = k + 1 + lane; j <= i; j += 32) rowi[j] -= lik * a[pk(j, k)];
-      }
-    }
-    __syncthreads();
-  }
-  // in-place inverse: solve L X = I right-looking; row k of X replaces row k of L
-  // once every update from rows above has been applied
-  for (int64_t k = 0; k < tau; ++k) {
-    const T inv = T(1) / a[pk(k, k)];
-    for (int64_t c = tid; c < k; c += blockDim.x) a[pk(k, c)] *= inv;
-    __syncthreads();
-    if (tid == 0) a[pk(k, k)] = inv;
-    __syncthreads();
-    const T* xk = a + pk(k, 0);
-    for (int64_t i = k + 1 + wid; i < tau; i += nw) {
-      T* rowi = a + pk(i, 0);
-      const T lik = rowi[k];
-      __syncwarp();
-      if (lik != T(0)) {
-        for (int64_t c = lane; c <= k; c += 32) {
-          if (c == k) rowi[k] = -lik * xk[k];
-          else rowi[c] -= lik * xk[c];
+  for (int64_t p = 0; p < P; ++p) {
+    const int64_t c0 = p * NBK;
+    T* D = tile_at(tiles, p, p);
+    if (wid == 0) {
+      // factor the diagonal tile: lane i holds row i
+      T r[NBK];
+#pragma unroll
+      for (int j = 0; j < NBK; ++j) r[j] = D[lane * TSK + j];
+#pragma unroll
+      for (int kk = 0; kk < NBK; ++kk) {
+        const T d = __shfl_sync(full, r[kk], kk);
+        const bool dr = !(d > thr);
+        const T piv = dr ? T(1) : (T)sqrt((double)d);
+        const T inv = dr ? T(0) : T(1) / piv;
+        if (lane == kk) {
+          r[kk] = piv;
+          if (dr) {
+#pragma unroll
+            for (int j = 0; j < kk; ++j) r[j] = T(0);
+          }
+        } else if (lane > kk) {
+          r[kk] *= inv;
         }
+#pragma unroll
+        for (int j = kk + 1; j < NBK; ++j) {
+          const T ljk = __shfl_sync(full, r[kk], j);
+          if (lane >= j) r[j] -= r[kk] * ljk;
+        }
+        if (lane == 0) dropped[c0 + kk] = dr;
       }
+      // store L_pp, then invert it: lane c holds column c of L_pp^{-1}
+#pragma unroll
+      for (int j = 0; j < NBK; ++j) D[lane * TSK + j] = (j <= lane) ? r[j] : T(0);
+      __syncwarp();
+      T x[NBK];
+#pragma unroll
+      for (int i = 0; i < NBK; ++i) {
+        T acc = (i == lane) ? T(1) : T(0);
+#pragma unroll
+        for (int k = 0; k < i; ++k) acc -= D[i * TSK + k] * x[k];
+        x[i] = (i < lane) ? T(0) : acc / D[i * TSK + i];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < NBK; ++i) D[i * TSK + lane] = x[i];
+    }
+    __syncthreads();
+    // a dropped index q becomes e_q in L: clear its row in the tiles left of the panel
+    for (int64_t e = tid; e < p * NBK * NBK; e += blockDim.x) {
+      const int64_t J = e / (NBK * NBK), rem = e - J * NBK * NBK;
+      const int rr = (int)(rem / NBK), cc = (int)(rem - (rem / NBK) * NBK);
+      if (dropped[c0 + rr]) tile_at(tiles, p, J)[rr * TSK + cc] = T(0);
+    }
+    // panel tiles below: L_Ip = M_Ip L_pp^{-T} (dropped columns stay zero)
+    for (int64_t I = p + 1 + wid; I < P; I += nw) {
+      T acc[8][4];
+      wtile_zero(acc);
+      T* C = tile_at(tiles, I, p);
+      wtile_mma<T, true, 1>(acc, C, D, ly, lx);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (dropped[c0 + lx * 4 + c])
+#pragma unroll
+          for (int r = 0; r < 8; ++r) acc[r][c] = T(0);
+      __syncwarp();
+      wtile_store(C, acc, ly, lx);
+    }
+    __syncthreads();
+    // trailing update M_IJ -= L_Ip L_Jp^T, p < J <= I
+    const int64_t q = P - p - 1;
+    for (int64_t t = wid; t < q * (q + 1) / 2; t += nw) {
+      int64_t a = 0;
+      while ((a + 1) * (a + 2) / 2 <= t) ++a;
+      const int64_t I = p + 1 + a, J = p + 1 + (t - a * (a + 1) / 2);
+      T acc[8][4];
+      T* C = tile_at(tiles, I, J);
+      wtile_load(acc, C, ly, lx);
+      wtile_mma<T, true, -1>(acc, tile_at(tiles, I, p), tile_at(tiles, J, p), ly, lx);
+      wtile_store(C, acc, ly, lx);
     }
     __syncthreads();
   }
-  // zero dropped rows and columns, write L^{-1} (tau x tau, zero above the diagonal)
+  // inverse of L, row block by row block, in place (diagonal tiles hold L_II^{-1}):
+  // X_IJ = -L_II^{-1} sum_{K=J}^{I-1} L_IK X_KJ
+  for (int64_t I = 1; I < P; ++I) {
+    for (int64_t J = wid; J < I; J += nw) {
+      T acc[8][4];
+      wtile_zero(acc);
+      for (int64_t K = J; K < I; ++K)
+        wtile_mma<T, false, 1>(acc, tile_at(tiles, I, K), tile_at(tiles, K, J), ly, lx);
+      T* tmp = temps + J * TILE;
+      wtile_store(tmp, acc, ly, lx);
+      __syncwarp();
+      wtile_zero(acc);
+      wtile_mma<T, false, -1>(acc, tile_at(tiles, I, I), tmp, ly, lx);
+      __syncwarp();
+      wtile_store(tmp, acc, ly, lx);
+    }
+    __syncthreads();
+    for (int64_t e = tid; e < I * TILE; e += blockDim.x) {
+      const int64_t J = e / TILE, off = e - J * TILE;
+      tile_at(tiles, I, J)[off] = temps[J * TILE + off];
+    }
+    __syncthreads();
+  }
+  // write L^{-1} with the dropped rows and columns zeroed (tau x tau, zero above)
   for (int64_t i = wid; i < tau; i += nw) {
     const bool di = dropped[i];
+    const int64_t I = i / NBK, rr = i - I * NBK;
     for (int64_t j = lane; j < tau; j += 32) {
       T v = T(0);
-      if (j <= i && !di && !dropped[j]) v = a[pk(i, j)];
+      if (j <= i && !di && !dropped[j]) {
+        const int64_t J = j / NBK;
+        v = tile_at(tiles, I, J)[rr * TSK + (j - J * NBK)];
+      }
       out[i * tau + j] = v;
     }
   }
-  if (tid == 0 && ndropped != nullptr && drops > 0) atomicAdd(ndropped, drops);
+  if (tid == 0 && ndropped != nullptr) {
+    int cnt = 0;
+    for (int64_t i = 0; i < tau; ++i) cnt += dropped[i];
+    if (cnt) atomicAdd(ndropped, cnt);
+  }
 }
 
 template <typename T>
 cudaError_t launch_factor_inv(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
                               const double* M, int64_t m_slot, int64_t tau, T* Linv, int64_t l_slot,
                               T* ws, int32_t* ndropped) {
-  const size_t need = factor_smem_bytes<T>(tau);
-  const int use_smem = need <= 200 * 1024;
-  const size_t smem = use_smem ? need : (size_t)tau + 64;
-  cudaError_t e = cudaFuncSetAttribute(k_factor_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t need = factor_ws_elems(tau) * sizeof(T) + 4096;
+  const int use_smem = need <= 220 * 1024 && tau <= 4096;
+  const size_t smem = use_smem ? need : 4096;
+  if (!use_smem && ws == nullptr) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_factor_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_factor_inv<T><<<nslots, 1024, smem, st>>>(ctrl, force, nslots, M, m_slot, tau, Linv, l_slot, ws,
+  k_factor_blk<T><<<nslots, 512, smem, st>>>(ctrl, force, nslots, M, m_slot, tau, Linv, l_slot, ws,
                                               use_smem, ndropped);
   return cudaGetLastError();
 }

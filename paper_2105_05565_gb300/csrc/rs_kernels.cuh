@@ -63,7 +63,7 @@ cudaError_t launch_srht_system(cudaStream_t st, const Ctrl* ctrl, int force, int
 int64_t srht_max_pad();
 
 // ---- small SPD system (rs_chol.cu) ----
-size_t factor_ws_elems(int64_t tau);
+__host__ __device__ size_t factor_ws_elems(int64_t tau);
 template <typename T>
 cudaError_t launch_factor_inv(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
                               const double* M, int64_t m_slot, int64_t tau, T* Linv, int64_t l_slot,

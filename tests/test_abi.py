@@ -74,7 +74,7 @@ def test_default_options(L):
 
     o = rs.Opts()
     L.rs_default_opts(ctypes.byref(o))
-    assert o.precision == 0 and o.refresh_every == 50 and o.chol_fp64 == 1
+    assert o.precision == 0 and o.refresh_every == 50 and o.chol_fp64 == 0
     m = rs.Mom()
     L.rs_default_mom(ctypes.byref(m), 3)
     assert m.kind == 3 and m.eta == 0.995 and m.beta_switch == 0.5
