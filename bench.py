@@ -98,7 +98,7 @@ def make_problem(seed, device):
                                   noise=0.01, device=device)
 
 
-def one_solve(rs, X, y, precision, sketch, device, w_out, on_host=False):
+def one_solve(rs, X, y, precision, sketch, device, w_out, on_host=False, chol_fp64=False):
     """One step: create (copy X, y; form A, b), solve to TOL, weights out, destroy.
     Returns dict of times (ms) and iteration count."""
     import torch
@@ -109,7 +109,7 @@ def one_solve(rs, X, y, precision, sketch, device, w_out, on_host=False):
     e0.record(st)
     with rs.Solver(X, y, LAM, sketch=sketch, tau=TAU, momentum="heuristic", seed=0,
                    precision=precision, refresh_every=50, device=device.index or 0,
-                   stream=st.cuda_stream) as s:
+                   stream=st.cuda_stream, chol_fp64=chol_fp64) as s:
         w, hist, iters, conv = s.solve(TOL, MAX_IT, w_out=None if on_host else w_out)
         setup_ms, solve_ms = s.timings()
     e1.record(st)
@@ -296,6 +296,9 @@ def main():
         extra["speedup_time_to_tol_vs_plain_fp64"] = plain["ms"] / step_ms
         wp, wm = plain["w"], last["w"]
         w_star_err = float(np.linalg.norm(wm - wp) / np.linalg.norm(wp))
+        f64f = one_solve(rs, X, y, "mixed", "count", dev, w_out, chol_fp64=True)
+        extra["mixed_count_fp64_factor"] = {k: f64f[k] for k in ("ms", "iters", "conv", "setup_ms",
+                                                                  "solve_ms", "final_rel")}
         for prec in ("mixed", "fp64"):
             sub = one_solve(rs, X, y, prec, "subsample", dev, w_out)
             extra[f"{'plain_fp64' if prec == 'fp64' else 'mixed'}_subsample"] = {

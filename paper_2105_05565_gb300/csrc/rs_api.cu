@@ -81,6 +81,7 @@ struct rs_ctx {
   double *rS = nullptr, *delta = nullptr;
   int64_t sa_slot = 0, m_slot = 0, l_slot = 0;
   int32_t *perm = nullptr, *boff = nullptr;
+  int32_t* inv = nullptr;  // per slot: row -> bucket | sign (bucket-row sketches)
   int64_t perm_stride = 0, boff_stride = 0;
   int64_t nslots = 0;
   int32_t* err_flag = nullptr;
@@ -137,7 +138,8 @@ rs_status dalloc(rs_ctx* c, T** p, size_t n) {
 void free_all(rs_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   void* ptrs[] = {c->X, c->y, c->A, c->b, c->w, c->wp, c->r, c->rp, c->u, c->SA, c->ST, c->M,
-                  c->Linv, c->fws, c->rS, c->delta, c->perm, c->boff, c->err_flag, c->ndropped,
+                  c->Linv, c->fws, c->rS, c->delta, c->perm, c->boff, c->inv, c->err_flag,
+                  c->ndropped,
                   c->gam, c->bet, c->hist, c->partials, c->vn, c->vd, c->xt_part, c->rel_dev,
                   c->ctrl};
   for (void* p : ptrs)
@@ -208,6 +210,9 @@ rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots) {
   rs_status s = enqueue_gen(c, force ? k0_arg : -1, nslots);
   if (s != RS_OK) return s;
   const PlanView plan = plan_view(c);
+  if (c->inv != nullptr)
+    CKC(c, launch_inv_map(st, c->ctrl, force, nslots, plan, c->m, c->tau,
+                          c->sketch == RS_COUNT ? 1 : 0, c->inv, c->m));
   const T* A = static_cast<const T*>(c->A);
   T* SA = static_cast<T*>(c->SA);
   switch (c->sketch) {
@@ -304,6 +309,35 @@ rs_status enqueue_update(rs_ctx* c) {
   return RS_OK;
 }
 
+template <typename T, typename TF>
+rs_status enqueue_iterate_t(rs_ctx* c) {
+  IterArgs<T, TF> g{};
+  g.kind = c->sketch == RS_GAUSSIAN ? 1 : 0;
+  g.mixed = c->mixed();
+  g.A = static_cast<const T*>(c->A);
+  g.lda = c->ld;
+  g.SA = c->sketch == RS_SUBSAMPLE ? nullptr : static_cast<const T*>(c->SA);
+  g.sa_slot = c->sa_slot;
+  g.ST = c->sketch == RS_GAUSSIAN ? static_cast<const T*>(c->ST) : nullptr;
+  g.plan = plan_view(c);
+  g.inv = c->inv;
+  g.inv_slot = c->m;
+  g.Linv = static_cast<const TF*>(c->Linv);
+  g.l_slot = c->l_slot;
+  g.gam = c->gam; g.bet = c->bet;
+  g.w = c->w; g.wp = c->wp; g.r = c->r; g.rp = c->rp;
+  g.hist = c->hist; g.delta_out = c->delta; g.rS_out = c->rS;
+  g.m = c->m; g.tau = c->tau; g.chunk = c->chunk;
+  CKC(c, (launch_iterate<T, TF>(c->stream, c->ctrl, g)));
+  return RS_OK;
+}
+
+// every iteration of the chunk in one cluster launch (all sketches but SRHT)
+rs_status enqueue_iterate(rs_ctx* c) {
+  if (!c->mixed()) return enqueue_iterate_t<double, double>(c);
+  return c->f64_factor() ? enqueue_iterate_t<float, double>(c) : enqueue_iterate_t<float, float>(c);
+}
+
 rs_status enqueue_iteration(rs_ctx* c) {
   rs_status s = enqueue_delta(c, 0, -1);
   if (s != RS_OK) return s;
@@ -350,9 +384,14 @@ rs_status enqueue_chunk(rs_ctx* c, bool with_refresh) {
   CKC(c, launch_chunk_begin(c->stream, c->ctrl));
   rs_status s = enqueue_phase1(c, 0, -1, (int)c->nslots);
   if (s != RS_OK) return s;
-  for (int64_t i = 0; i < c->chunk; ++i) {
-    s = enqueue_iteration(c);
+  if (c->sketch != RS_SRHT) {
+    s = enqueue_iterate(c);
     if (s != RS_OK) return s;
+  } else {
+    for (int64_t i = 0; i < c->chunk; ++i) {
+      s = enqueue_iteration(c);
+      if (s != RS_OK) return s;
+    }
   }
   if (with_refresh) return enqueue_refresh(c);
   return RS_OK;
@@ -696,6 +735,7 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     c->boff_stride = c->tau + 1;
     TRY(dalloc(c, &c->perm, (size_t)c->perm_stride * c->nslots));
     TRY(dalloc(c, &c->boff, (size_t)c->boff_stride * c->nslots));
+    if (sketch != RS_SRHT) TRY(dalloc(c, &c->inv, (size_t)m * c->nslots));
   }
   c->npartials = std::max<int64_t>(update_blocks(m), 256);
   TRY(dalloc(c, &c->partials, c->npartials));

@@ -84,6 +84,29 @@ template <typename T>
 cudaError_t launch_delta(cudaStream_t st, const Ctrl* ctrl, int force, int64_t k_arg,
                          DeltaArgs<T> g);
 
+// ---- fused iterations of a chunk on a thread-block cluster (rs_iterate.cu) ----
+template <typename T, typename TF>
+struct IterArgs {
+  int kind;            // 0 bucket rows (subsample, count, subcount), 1 Gaussian
+  int mixed;           // 1: convergence sets `pending` (FP64 check follows)
+  const T* A; int64_t lda;
+  const T* SA; int64_t sa_slot;   // sketched rows per slot (nullptr for subsample)
+  const T* ST;                    // Gaussian: S^T per slot (stride sa_slot)
+  PlanView plan;
+  const int32_t* inv; int64_t inv_slot;  // row -> bucket | sign (bucket-row sketches)
+  const TF* Linv; int64_t l_slot;
+  const double* gam; const double* bet;
+  double* w; double* wp; double* r; double* rp;
+  double* hist; double* delta_out; double* rS_out;
+  int64_t m, tau, chunk;
+};
+template <typename T, typename TF>
+cudaError_t launch_iterate(cudaStream_t st, Ctrl* ctrl, IterArgs<T, TF> g);
+// inverse map of the sketch plans: inv[i] = bucket | sign bit, or 0x7FFFFFFF when row i
+// is not in the sketch (all_rows = 1: every row is, as in the count sketch)
+cudaError_t launch_inv_map(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, PlanView plan,
+                           int64_t m, int64_t tau, int all_rows, int32_t* inv, int64_t inv_slot);
+
 // ---- iterate / residual update (rs_update.cu) ----
 struct UpdateArgs {
   const double* gam;  // gamma_k table

@@ -271,3 +271,18 @@ def test_mixed_fp32_factor_reaches_tolerance(rs):
                    precision="mixed", chol_fp64=False) as s:
         w, hist, iters, conv = s.solve(tol=1e-6, max_iters=50000)
     assert conv and oracle.true_residual(X.astype(np.float64), y, lam, w) <= 1e-6
+
+
+@pytest.mark.parametrize("kind", ["count", "subsample", "gaussian"])
+def test_mixed_fp64_factor_and_kinds(rs, kind):
+    """Mixed path: FP64 factor of S^T A S (count, subsample) and the Gaussian sketch
+    with the FP32 factor, both to the FP64-checked tolerance."""
+    from synth import geometric_sigma, spectrum_problem
+
+    X, y, _ = spectrum_problem(2000, 192, geometric_sigma(192), seed=9, noise=0.01, dtype=np.float32)
+    lam = 1e-2
+    f64 = kind != "gaussian"
+    with rs.Solver(X, y, lam, sketch=kind, tau=24, momentum="heuristic", seed=4,
+                   precision="mixed", chol_fp64=f64) as s:
+        w, hist, iters, conv = s.solve(tol=1e-6, max_iters=50000)
+    assert conv and oracle.true_residual(X.astype(np.float64), y, lam, w) <= 1e-6
