@@ -134,7 +134,7 @@ def profile_kernels(rs, X, y, device):
 
 def roofline(stats, pk):
     """Dominant kernel of the iteration and its achieved fraction of the measured peak."""
-    name, (ms, n, nbytes, flops) = max(stats.items(), key=lambda kv: kv[1][0] * kv[1][1])
+    name, (ms, n, nbytes, flops, _its) = max(stats.items(), key=lambda kv: kv[1][0] * kv[1][1])
     hbm = pk.get("hbm_gbs", 6800.0)
     if name in ("chol",):
         # FP64 ALU bound: peak from the FP64 FMA throughput measured on this GPU
@@ -318,17 +318,18 @@ def main():
         "final_true_rel_residual": last["final_rel"], "setup_ms": last["setup_ms"],
         "solve_ms": last["solve_ms"], "rel_err_vs_plain_fp64_w": w_star_err,
         "gpu_launches": None, "kernels": {k: {"ms": v[0], "launches": v[1], "bytes": v[2],
-                                              "flops": v[3]} for k, v in stats.items()},
+                                              "flops": v[3], "iters": v[4]}
+                                          for k, v in stats.items()},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
         "wall_s_timed": wall,
     }
     line.update(extra)
-    # kernels launched in the timed region: every chunk graph holds chunk-begin +
-    # generator + 50 x (sa_rows, msys, chol, update) + 4 refresh kernels (kernels of
-    # iterations after convergence start and exit at once); per step 10 more for
-    # forming A, b, the initial state and the final FP64 residual check
+    # kernels launched in the timed region, per chunk of 50 iterations: chunk begin,
+    # sketch plans, inverse plan map, S^T A, S^T A S, factor + inverse, the fused
+    # iteration kernel, and the FP64 refresh (float-pair X^T X v, sum, finish);
+    # per step 10 more (forming A and b, ||b||, initial state, final FP64 check)
     n_chunks = sum((r["iters"] + 49) // 50 for r in runs)
-    line["gpu_launches"] = int(n_chunks * (2 + 50 * 4 + 4) + args.steps * 10)
+    line["gpu_launches"] = int(n_chunks * 10 + args.steps * 10)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -224,6 +224,7 @@ typedef struct {
   double ms;          /* mean device time per launch (CUDA events on the context stream) */
   double bytes;       /* algorithmic bytes moved per launch (inputs read once + outputs written) */
   double flops;       /* algorithmic floating-point operations per launch */
+  int64_t iters;      /* iterations covered by the launches (fused chunk kernel), else launches */
 } rs_kernel_stat;
 
 /*

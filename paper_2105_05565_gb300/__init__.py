@@ -54,7 +54,7 @@ class Opts(ctypes.Structure):
 
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
-                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double), ("iters", ctypes.c_int64)]
 
 
 _LIB = None
@@ -266,7 +266,8 @@ class Solver:
         arr = (KernelStat * cap)()
         n = _I32()
         self._check(lib().rs_profile_iteration(self._ctx, int(reps), arr, cap, ctypes.byref(n)))
-        return {arr[i].name.decode(): (arr[i].ms, arr[i].launches, arr[i].bytes, arr[i].flops)
+        return {arr[i].name.decode(): (arr[i].ms, arr[i].launches, arr[i].bytes, arr[i].flops,
+                                       arr[i].iters)
                 for i in range(n.value)}
 
     def timings(self):

@@ -67,6 +67,7 @@ struct rs_ctx {
   uint64_t seed = 0;
   rs_mom mom{};
   int xdtype = RS_F64;
+  bool xtx_df = true;      // one-pass float-pair X^T X v for FP32 X (primal)
   // device data
   void* X = nullptr;
   double* y = nullptr;
@@ -350,7 +351,9 @@ rs_status enqueue_true_av(rs_ctx* c, const double* v, const int32_t* stop) {
   // primal: A w = X^T (X w) + lambda w; dual: A a = X (X^T a) + lambda a
   if (c->xdtype == RS_F32) {
     const float* X = static_cast<const float*>(c->X);
-    if (c->form == RS_PRIMAL) {
+    if (c->form == RS_PRIMAL && c->d <= 4096 && c->xtx_df) {
+      CKC(c, launch_xtx_v_df(st, X, c->n, c->d, v, c->vd, c->xt_part, stop));
+    } else if (c->form == RS_PRIMAL) {
       CKC(c, launch_x_v<float>(st, X, c->n, c->d, v, c->vn, stop));
       CKC(c, launch_xt_v<float>(st, X, c->n, c->d, c->vn, c->vd, c->xt_part, stop));
     } else {
@@ -675,7 +678,8 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   // scratch of the X products
   TRY(dalloc(c, &c->vn, c->n));
   TRY(dalloc(c, &c->vd, c->d));
-  TRY(dalloc(c, &c->xt_part, xt_part_elems(c->n, c->d)));
+  TRY(dalloc(c, &c->xt_part, std::max<size_t>(xt_part_elems(c->n, c->d),
+                                               (size_t)xtx_df_blocks() * c->d)));
   TRY(dalloc(c, &c->rel_dev, 1));
   // A and b (eqs. (2)-(4))
   TRYC(cudaMalloc(&c->A, (size_t)m * c->ld * c->elem()));
@@ -1027,7 +1031,7 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
   h->max_iters = k0 + reps;
   h->r0 = c->r0 > 0.0 ? c->r0 : 1.0;
   if ((s = write_ctrl(c)) != RS_OK) return s;
-  struct Grp { const char* name; double ms = 0; int64_t n = 0; double bytes = 0, flops = 0; };
+  struct Grp { const char* name; double ms = 0; int64_t n = 0; double bytes = 0, flops = 0; int64_t iters = 0; };
   std::vector<Grp> g;
   auto grp = [&](const char* nm) -> Grp& {
     for (auto& x : g) if (std::strcmp(x.name, nm) == 0) return x;
@@ -1106,6 +1110,21 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
         if (s != RS_OK) break;
       }
     }
+    if (c->sketch != RS_SRHT) {
+      // fused: the whole chunk's iterations in one launch
+      const int64_t nit = std::min<int64_t>(c->chunk, reps - it);
+      s = timed("iterate", [&]() { return enqueue_iterate(c); });
+      grp("iterate").bytes = (double)nit * (tau * m * el + tau * tau * fel + 80.0 * m);
+      grp("iterate").flops = (double)nit * (2.0 * tau * m + 2.0 * tau * tau + 10.0 * m);
+      grp("iterate").iters += nit;
+      if (s == RS_OK && c->mixed() && (it + nit) % c->refresh_every == 0) {
+        s = timed("refresh", [&]() { return enqueue_refresh(c); });
+        grp("refresh").bytes = (double)c->n * (double)c->d * (c->xdtype == RS_F32 ? 4.0 : 8.0) + m * 48.0;
+        grp("refresh").flops = 4.0 * (double)c->n * (double)c->d;
+      }
+      it += nit - 1;
+      continue;
+    }
     s = timed("delta", [&]() { return enqueue_delta(c, 0, -1); });
     grp("delta").bytes = tau * tau * fel / 2.0 + rows * 12.0 + m * 8.0;
     grp("delta").flops = 2.0 * tau * tau;
@@ -1132,6 +1151,7 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
     o.ms = x.n ? x.ms / x.n : 0.0;
     o.bytes = x.bytes;
     o.flops = x.flops;
+    o.iters = x.iters > 0 ? x.iters : x.n;
   }
   *n_out = n;
   h->stop = 0;

@@ -88,6 +88,128 @@ cudaError_t launch_x_v(cudaStream_t st, const TI* X, int64_t n, int64_t d, const
   return cudaGetLastError();
 }
 
+// ---- A v = X^T (X v) in one pass over FP32 X, FP64-accurate through float pairs ----
+// X holds exact FP32 data; v is FP64. Products x * v_hi are split exactly with a fused
+// multiply-add (x * v = p + e, e = fma(x, v_hi, -p)), sums are carried as unevaluated
+// float pairs with the error-free two-sum (Knuth); v_lo = fp32(v - v_hi) adds its small
+// product directly. Each block takes a range of rows: for every row i it forms
+// u_i = x_i . v (block reduction of pairs), then adds u_i x_i to its per-column
+// pairs; per-block column sums go to `part` (blocks x d) and are added in block order.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (ah, al) + (bh, bl), renormalised
+__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(al, bl));
+  ah = __fadd_rn(s, e);
+  al = __fsub_rn(e, __fsub_rn(ah, s));
+}
+
+template <int NC, int R>
+__global__ void __launch_bounds__(256) k_xtx_v_df(const float* __restrict__ X, int64_t n, int64_t d,
+                                                  const double* __restrict__ v,
+                                                  double* __restrict__ part,
+                                                  const int32_t* __restrict__ stop) {
+  if (stop != nullptr && *(volatile const int32_t*)stop) return;
+  __shared__ float s_h[8][R], s_l[8][R];
+  __shared__ float u_h[R], u_l[R];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  float vh[NC], vl[NC], ah[NC], al[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int64_t col = tid + 256 * c;
+    const double vv = col < d ? v[col] : 0.0;
+    vh[c] = (float)vv;
+    vl[c] = (float)(vv - (double)vh[c]);
+    ah[c] = 0.f;
+    al[c] = 0.f;
+  }
+  const int64_t rows_per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * rows_per, i1 = min(n, i0 + rows_per);
+  for (int64_t ib = i0; ib < i1; ib += R) {
+    float x[R][NC];
+    float dh[R], dl[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      dh[r] = 0.f;
+      dl[r] = 0.f;
+      const int64_t i = ib + r;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int64_t col = tid + 256 * c;
+        x[r][c] = (i < i1 && col < d) ? __ldg(X + i * d + col) : 0.f;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float p = __fmul_rn(x[r][c], vh[c]);
+        const float e = __fmaf_rn(x[r][c], vh[c], -p);
+        float s, er;
+        two_sum(dh[r], p, s, er);
+        dh[r] = s;
+        dl[r] = __fmaf_rn(x[r][c], vl[c], __fadd_rn(dl[r], __fadd_rn(er, e)));
+      }
+    // block reduction of the R row dots (fixed tree)
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, dh[r], o);
+        const float ol = __shfl_xor_sync(0xffffffffu, dl[r], o);
+        df_add(dh[r], dl[r], oh, ol);
+      }
+      if (lane == 0) { s_h[wid][r] = dh[r]; s_l[wid][r] = dl[r]; }
+    }
+    __syncthreads();
+    if (tid < R) {
+      float h = s_h[0][tid], l = s_l[0][tid];
+      for (int q = 1; q < 8; ++q) df_add(h, l, s_h[q][tid], s_l[q][tid]);
+      u_h[tid] = h;
+      u_l[tid] = l;
+    }
+    __syncthreads();
+    // column pairs += u_i x_i
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float uh = u_h[r], ul = u_l[r];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const float p = __fmul_rn(x[r][c], uh);
+        const float e = __fmaf_rn(x[r][c], uh, -p);
+        float s, er;
+        two_sum(ah[c], p, s, er);
+        ah[c] = s;
+        al[c] = __fmaf_rn(x[r][c], ul, __fadd_rn(al[c], __fadd_rn(er, e)));
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int64_t col = tid + 256 * c;
+    if (col < d) part[blockIdx.x * d + col] = (double)ah[c] + (double)al[c];
+  }
+}
+
+int xtx_df_blocks() { return 152; }
+
+cudaError_t launch_xtx_v_df(cudaStream_t st, const float* X, int64_t n, int64_t d, const double* v,
+                            double* out, double* part, const int32_t* stop) {
+  const int G = xtx_df_blocks();
+  if (d <= 1024) k_xtx_v_df<4, 4><<<G, 256, 0, st>>>(X, n, d, v, part, stop);
+  else if (d <= 2048) k_xtx_v_df<8, 4><<<G, 256, 0, st>>>(X, n, d, v, part, stop);
+  else if (d <= 4096) k_xtx_v_df<16, 4><<<G, 256, 0, st>>>(X, n, d, v, part, stop);
+  else return cudaErrorInvalidValue;
+  k_sum_parts<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(part, G, d, out, stop);
+  return cudaGetLastError();
+}
+
 // ---- true residual r = v + lambda x - b ----
 // mode 1: replace the recursive residual pair (r, r_prev) by (r_true, r_true - (r - r_prev))
 //         and decide convergence on ||r_true|| / ||r^0||; mode 0: only *rel_out.

@@ -103,7 +103,9 @@ __global__ void __launch_bounds__(256) k_iterate(Ctrl* __restrict__ ctrl, IterAr
   TF* part = yv + rper;                                 // tau
   double* dfull = reinterpret_cast<double*>(smem_raw + (((2 * tau + rper) * sizeof(TF) + 15) / 16) * 16);
   double* nrm = dfull + tau;                            // 1 (+ pad)
-  TA* red = reinterpret_cast<TA*>(nrm + 2);             // 256 * VN
+  TA* red = reinterpret_cast<TA*>(nrm + 2);             // 2 * 256 * VN
+  double* stg_r = reinterpret_cast<double*>(red + 2 * 256 * VN);   // m (g.stage)
+  int32_t* stg_p = reinterpret_cast<int32_t*>(stg_r + (g.stage ? m : 0));  // plan
   __shared__ double s_w[8];
 
   int outcome = 0;  // 0 chunk done, 1 converged, 2 numeric failure
@@ -113,21 +115,45 @@ __global__ void __launch_bounds__(256) k_iterate(Ctrl* __restrict__ ctrl, IterAr
     const int32_t* boff = g.plan.boff ? g.plan.boff + slot * g.plan.boff_stride : nullptr;
     const TF* Li = g.Linv + slot * g.l_slot;
     const T* ST = g.ST ? g.ST + slot * g.sa_slot : nullptr;
-    // r_S = S^T r (every CTA, all tau entries)
+    // r_S = S^T r (every CTA, all tau entries). r and the slot's plan are first
+    // copied to shared memory with coalesced loads; the gathers then hit shared memory.
     if (g.kind == 0) {
-      for (int64_t l = tid; l < tau; l += blockDim.x) {
-        double acc = 0.0;
-        const int32_t t1 = boff[l + 1];
-        for (int32_t t = boff[l]; t < t1; ++t) {
-          const int32_t e = perm[t];
-          const double v = g.r[entry_row(e)];
-          acc += entry_neg(e) ? -v : v;
+      if (g.stage) {
+        double* sr = stg_r;
+        int32_t* sp = stg_p;
+        int32_t* sb = stg_p + g.plan.perm_stride;
+#pragma unroll 8
+        for (int64_t i = tid; i < m; i += blockDim.x) sr[i] = g.r[i];
+#pragma unroll 8
+        for (int64_t t = tid; t < g.plan.perm_stride; t += blockDim.x) sp[t] = perm[t];
+        for (int64_t t = tid; t <= tau; t += blockDim.x) sb[t] = boff[t];
+        __syncthreads();
+        for (int64_t l = tid; l < tau; l += blockDim.x) {
+          double acc = 0.0;
+          const int32_t t1 = sb[l + 1];
+          for (int32_t t = sb[l]; t < t1; ++t) {
+            const int32_t e = sp[t];
+            const double v = sr[entry_row(e)];
+            acc += entry_neg(e) ? -v : v;
+          }
+          rsf[l] = (TF)acc;
         }
-        rsf[l] = (TF)acc;
+      } else {
+        for (int64_t l = tid; l < tau; l += blockDim.x) {
+          double acc = 0.0;
+          const int32_t t1 = boff[l + 1];
+          for (int32_t t = boff[l]; t < t1; ++t) {
+            const int32_t e = perm[t];
+            const double v = g.r[entry_row(e)];
+            acc += entry_neg(e) ? -v : v;
+          }
+          rsf[l] = (TF)acc;
+        }
       }
     } else {
       for (int64_t l = wid; l < tau; l += 8) {
         double acc = 0.0;
+#pragma unroll 8
         for (int64_t i = lane; i < m; i += 32) acc += (double)ST[l * g.lda + i] * g.r[i];
         acc = warp_sum(acc);
         if (lane == 0) rsf[l] = (TF)acc;
@@ -138,7 +164,8 @@ __global__ void __launch_bounds__(256) k_iterate(Ctrl* __restrict__ ctrl, IterAr
     for (int64_t i = lo + wid; i < hi; i += 8) {
       TF acc = TF(0);
       const TF* row = Li + i * tau;
-      for (int64_t j = lane; j <= i; j += 32) acc += row[j] * rsf[j];
+#pragma unroll 8
+      for (int64_t j = lane; j <= i; j += 32) acc += __ldg(row + j) * rsf[j];
       acc = warp_sum(acc);
       if (lane == 0) yv[i - lo] = acc;
     }
@@ -146,7 +173,8 @@ __global__ void __launch_bounds__(256) k_iterate(Ctrl* __restrict__ ctrl, IterAr
     // partial of delta = L^{-T} y from the own rows
     for (int64_t j = tid; j < tau; j += blockDim.x) {
       TF acc = TF(0);
-      for (int64_t i = (j > lo ? j : lo); i < hi; ++i) acc += Li[i * tau + j] * yv[i - lo];
+#pragma unroll 8
+      for (int64_t i = (j > lo ? j : lo); i < hi; ++i) acc += __ldg(Li + i * tau + j) * yv[i - lo];
       part[j] = acc;
     }
     cluster.sync();
@@ -174,12 +202,35 @@ __global__ void __launch_bounds__(256) k_iterate(Ctrl* __restrict__ ctrl, IterAr
       for (int q = 0; q < VN; ++q) { acc[q] = TA(0); uacc[q] = TA(0); }
       if (vi < nvec && jp < jparts) {
         const int64_t i = ilo + vi * VN;
-        for (int64_t j = jp; j < tau; j += jparts) {
-          const T* rowj = (g.SA != nullptr) ? g.SA + slot * g.sa_slot + j * g.lda
-                                            : g.A + (int64_t)entry_row(perm[j]) * g.lda;
-          const TV v = __ldg(reinterpret_cast<const TV*>(rowj + i));
-          vfma(acc, v, (TA)dfull[j]);
-          if (ST) vfma(uacc, __ldg(reinterpret_cast<const TV*>(ST + j * g.lda + i)), (TA)dfull[j]);
+        constexpr int UNR = 8;  // row loads in flight per thread
+        for (int64_t j0 = jp; j0 < tau; j0 += UNR * jparts) {
+          TV v[UNR];
+#pragma unroll
+          for (int q = 0; q < UNR; ++q) {
+            const int64_t j = j0 + q * jparts;
+            if (j < tau) {
+              const T* rowj = (g.SA != nullptr) ? g.SA + slot * g.sa_slot + j * g.lda
+                                                : g.A + (int64_t)entry_row(perm[j]) * g.lda;
+              v[q] = __ldg(reinterpret_cast<const TV*>(rowj + i));
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < UNR; ++q) {
+            const int64_t j = j0 + q * jparts;
+            if (j < tau) vfma(acc, v[q], (TA)dfull[j]);
+          }
+          if (ST) {
+#pragma unroll
+            for (int q = 0; q < UNR; ++q) {
+              const int64_t j = j0 + q * jparts;
+              if (j < tau) v[q] = __ldg(reinterpret_cast<const TV*>(ST + j * g.lda + i));
+            }
+#pragma unroll
+            for (int q = 0; q < UNR; ++q) {
+              const int64_t j = j0 + q * jparts;
+              if (j < tau) vfma(uacc, v[q], (TA)dfull[j]);
+            }
+          }
         }
       }
       // reduce the row parts (fixed order)
@@ -273,22 +324,27 @@ __global__ void __launch_bounds__(256) k_iterate(Ctrl* __restrict__ ctrl, IterAr
 }
 
 template <typename T, typename TF>
-size_t iterate_smem(int64_t tau, int cs) {
+size_t iterate_smem(int64_t tau, int cs, int64_t stage_bytes) {
   const int64_t rper = (tau + cs - 1) / cs;
   return (((2 * tau + rper) * sizeof(TF) + 15) / 16) * 16 + (tau + 2) * sizeof(double) +
-         2 * 256 * V2<T>::n * sizeof(T) + 64;
+         2 * 256 * V2<T>::n * sizeof(T) + stage_bytes + 64;
 }
 
 template <typename T, typename TF>
 cudaError_t launch_iterate(cudaStream_t st, Ctrl* ctrl, IterArgs<T, TF> g) {
-  static thread_local int64_t last_tau = -1;
+  static thread_local int64_t last_tau = -1, last_stage = -1;
   static thread_local int cs = 16;
   auto kern = k_iterate<T, TF>;
-  if (last_tau != g.tau) {
+  // stage r and the plan in shared memory when they fit next to the other buffers
+  const int64_t stage_bytes = (g.kind == 0) ? g.m * 8 + (g.plan.perm_stride + g.tau + 1) * 4 : 0;
+  g.stage = (g.kind == 0 && stage_bytes <= 160 * 1024) ? 1 : 0;
+  const int64_t sb = g.stage ? stage_bytes : 0;
+  if (last_tau != g.tau || last_stage != sb) {
     last_tau = g.tau;
+    last_stage = sb;
     cs = 16;
     for (;;) {
-      const size_t smem = iterate_smem<T, TF>(g.tau, cs);
+      const size_t smem = iterate_smem<T, TF>(g.tau, cs, sb);
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (cs > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       cudaLaunchConfig_t cfg = {};
@@ -309,7 +365,7 @@ cudaError_t launch_iterate(cudaStream_t st, Ctrl* ctrl, IterArgs<T, TF> g) {
       cs >>= 1;
     }
   }
-  const size_t smem = iterate_smem<T, TF>(g.tau, cs);
+  const size_t smem = iterate_smem<T, TF>(g.tau, cs, sb);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)cs);
   cfg.blockDim = dim3(256);

@@ -99,6 +99,7 @@ struct IterArgs {
   double* w; double* wp; double* r; double* rp;
   double* hist; double* delta_out; double* rS_out;
   int64_t m, tau, chunk;
+  int stage;           // set by the launcher: r and the plan staged in shared memory
 };
 template <typename T, typename TF>
 cudaError_t launch_iterate(cudaStream_t st, Ctrl* ctrl, IterArgs<T, TF> g);
@@ -144,6 +145,11 @@ size_t xt_part_elems(int64_t n, int64_t d);
 template <typename TI>
 cudaError_t launch_x_v(cudaStream_t st, const TI* X, int64_t n, int64_t d, const double* v,
                        double* out, const int32_t* stop = nullptr);
+// out = X^T (X v) for FP32 X in one pass, FP64-accurate (float pairs); d <= 4096;
+// part: xtx_df_blocks() * d doubles
+cudaError_t launch_xtx_v_df(cudaStream_t st, const float* X, int64_t n, int64_t d, const double* v,
+                            double* out, double* part, const int32_t* stop = nullptr);
+int xtx_df_blocks();
 // r_true = v + lambda x - b; replaces (r, rp) keeping r - rp, writes hist[k] and the
 // convergence decision (mode 1) or only the relative residual (mode 0 -> *rel_out)
 cudaError_t launch_refresh_finish(cudaStream_t st, Ctrl* ctrl, int mode, int64_t m,

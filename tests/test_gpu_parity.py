@@ -286,3 +286,25 @@ def test_mixed_fp64_factor_and_kinds(rs, kind):
                    precision="mixed", chol_fp64=f64) as s:
         w, hist, iters, conv = s.solve(tol=1e-6, max_iters=50000)
     assert conv and oracle.true_residual(X.astype(np.float64), y, lam, w) <= 1e-6
+
+
+@pytest.mark.parametrize("d", [700, 2048, 4096])
+def test_true_residual_fp32_x(rs, d):
+    """A v - b through FP32 X in one pass with float pairs vs the FP64 oracle."""
+    n = 3000
+    g = np.random.default_rng(d)
+    X = g.standard_normal((n, d)).astype(np.float32)
+    y = g.standard_normal(n)
+    lam = 0.3
+    v = g.standard_normal(d)
+    with rs.Solver(X, y, lam, sketch="count", tau=16, seed=1, precision="mixed") as s:
+        got = s.true_residual(v)
+    ref = oracle.true_residual(X.astype(np.float64), y, lam, v)
+    assert abs(got - ref) <= 1e-12 * ref
+    # near a solution the residual is a small difference of large terms
+    w_star = oracle.direct_solution(X.astype(np.float64), y, lam)
+    w_near = w_star * (1.0 + 1e-7 * g.standard_normal(d))
+    with rs.Solver(X, y, lam, sketch="count", tau=16, seed=1, precision="mixed") as s:
+        got = s.true_residual(w_near)
+    ref = oracle.true_residual(X.astype(np.float64), y, lam, w_near)
+    assert abs(got - ref) <= 1e-6 * ref
