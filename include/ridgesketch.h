@@ -119,6 +119,8 @@ typedef struct {
                             sketched systems of a chunk are formed and factored ahead in
                             batched launches. 0 = refresh_every (mixed) or 128 (plain),
                             reduced so that the chunk's buffers stay under 4 GB */
+  int32_t setup_tc;      /* RS_MIXED, primal, FP32 X: 1 = form X^T X on the tensor cores
+                            (TF32 inputs, FP32 accumulation; default), 0 = FP32 CUDA cores */
 } rs_opts;
 
 /* Fill *o with the defaults listed above. */

@@ -49,7 +49,8 @@ class Matrix(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("refresh_every", ctypes.c_int32),
                 ("sub_s", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
-                ("device", ctypes.c_int32), ("chol_fp64", ctypes.c_int32), ("chunk", ctypes.c_int64)]
+                ("device", ctypes.c_int32), ("chol_fp64", ctypes.c_int32), ("chunk", ctypes.c_int64),
+                ("setup_tc", ctypes.c_int32)]
 
 
 class KernelStat(ctypes.Structure):
@@ -140,7 +141,7 @@ class Solver:
     def __init__(self, X, y, lam, form="primal", sketch="count", tau=0, momentum="none", seed=0,
                  precision="fp64", refresh_every=50, sub_s=0, chol_fp64=False, chunk=0,
                  eta=0.995, beta_switch=0.5, gamma_c=1.0, beta_c=0.5, uncapped=False,
-                 device=0, stream=None):
+                 device=0, stream=None, setup_tc=True):
         L = lib()
         self._ctx = None
         xdt = np.float32 if str(getattr(X, "dtype", "")).endswith("float32") else np.float64
@@ -160,6 +161,7 @@ class Solver:
         opts.device = int(device)
         opts.chol_fp64 = int(bool(chol_fp64))
         opts.chunk = int(chunk)
+        opts.setup_tc = int(bool(setup_tc))
         st = stream if stream is not None else _default_stream(device)
         opts.cuda_stream = st
         ctx = _P()

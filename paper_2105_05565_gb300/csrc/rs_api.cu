@@ -538,6 +538,7 @@ void rs_default_opts(rs_opts* o) {
   o->device = 0;
   o->chol_fp64 = 0;
   o->chunk = 0;
+  o->setup_tc = 1;
 }
 
 void rs_default_mom(rs_mom* m, int32_t kind) {
@@ -689,7 +690,18 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   const int dual = (form == RS_DUAL);
   if (X->dtype == RS_F32) {
     const float* Xf = static_cast<const float*>(c->X);
-    if (c->mixed()) TRYC((launch_form_A<float, float>(st, Xf, c->n, c->d, dual, lambda, static_cast<float*>(c->A), c->ld)));
+    if (c->mixed() && !dual && o.setup_tc) {
+      // X^T X on the tensor cores through a transposed, padded copy of X
+      float* Xt = nullptr;
+      TRYC(cudaMalloc(&Xt, gram_tc_ws_floats(c->n, c->d) * sizeof(float)));
+      cudaError_t e1 = launch_gram_tc(st, Xf, c->n, c->d, lambda, static_cast<float*>(c->A), c->ld,
+                                      Xt, c->err_flag);
+      if (e1 == cudaSuccess) e1 = launch_mirror_lower<float>(st, static_cast<float*>(c->A), c->d, c->ld);
+      cudaError_t e2 = cudaStreamSynchronize(st);
+      cudaFree(Xt);
+      TRYC(e1);
+      TRYC(e2);
+    } else if (c->mixed()) TRYC((launch_form_A<float, float>(st, Xf, c->n, c->d, dual, lambda, static_cast<float*>(c->A), c->ld)));
     else TRYC((launch_form_A<float, double>(st, Xf, c->n, c->d, dual, lambda, static_cast<double*>(c->A), c->ld)));
     if (!dual) TRYC(launch_xt_v<float>(st, Xf, c->n, c->d, c->y, c->b, c->xt_part));
   } else {

@@ -25,6 +25,15 @@ cudaError_t launch_form_A(cudaStream_t st, const TI* X, int64_t n, int64_t d, in
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_mirror_lower(cudaStream_t st, T* A, int64_t m, int64_t lda) {
+  dim3 g((unsigned)((m + 31) / 32), (unsigned)((m + 31) / 32));
+  k_mirror_lower<T><<<g, dim3(32, 32), 0, st>>>(A, m, lda);
+  return cudaGetLastError();
+}
+template cudaError_t launch_mirror_lower<float>(cudaStream_t, float*, int64_t, int64_t);
+template cudaError_t launch_mirror_lower<double>(cudaStream_t, double*, int64_t, int64_t);
+
 // ---- X^T v: column sums of X weighted by v, chunked over rows, FP64 ----
 constexpr int64_t kXtRows = 256;
 

@@ -129,6 +129,15 @@ cudaError_t launch_init_state(cudaStream_t st, int64_t m, const double* b, doubl
 // ctrl->k0 = ctrl->k (first iteration of a chunk)
 cudaError_t launch_chunk_begin(cudaStream_t st, Ctrl* ctrl);
 
+// ---- X^T X on the tensor cores (rs_tc_gemm.cu) ----
+// A (lower triangle and diagonal, d x lda FP32) = X^T X + lambda I, TF32 inputs, FP32
+// accumulation; Xt_ws: gram_tc_ws_floats(n, d) floats; err set on a device timeout
+size_t gram_tc_ws_floats(int64_t n, int64_t d);
+cudaError_t launch_gram_tc(cudaStream_t st, const float* X, int64_t n, int64_t d, double lambda,
+                           float* A, int64_t lda, float* Xt_ws, int32_t* err);
+template <typename T>
+cudaError_t launch_mirror_lower(cudaStream_t st, T* A, int64_t m, int64_t lda);
+
 // ---- forming A, b; true residuals through X (rs_form.cu) ----
 // C (m x ldc) = op(X) op(X)^T + lambda I, primal op(X) = X^T (m = d), dual X (m = n)
 template <typename TI, typename TO>

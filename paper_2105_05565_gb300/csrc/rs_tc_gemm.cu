@@ -1,0 +1,271 @@
+// A = X^T X + lambda I on the 5th-generation tensor cores (mixed form, eq. (2)).
+//
+// TF32 operands, FP32 accumulation in tensor memory. X is first copied transposed
+// (Xt = X^T, d x ldk, K = n contiguous and zero padded) so that both operands of
+// C = Xt Xt^T are K-major. One CTA per 128 x 128 tile of the lower triangle:
+//   warp 0 (one lane)  TMA producer: 128 x 32 fp32 boxes of Xt (128B swizzle) into a
+//                      ring of kStages shared-memory stages, completion on mbarriers;
+//   warp 1 (one lane)  MMA issuer: 4 x tcgen05.mma (M 128, N 128, K 8) per stage,
+//                      tcgen05.commit frees the stage when those MMAs retire;
+//   warps 0-3          epilogue: tcgen05.ld of the 128 x 128 FP32 accumulator (each
+//                      warp its 32 TMEM lanes), + lambda on the diagonal, to global.
+// The upper triangle is mirrored afterwards. Every mbarrier wait is bounded; on
+// timeout the CTA records an error, stops issuing, drains its own MMAs (bounded)
+// and releases its tensor memory.
+#include <cuda.h>
+
+#include "rs_kernels.cuh"
+
+namespace rs {
+
+namespace {
+
+constexpr int kBM = 128, kBN = 128, kBK = 32;  // tile; kBK fp32 = 128 bytes
+constexpr int kStages = 6;
+constexpr int kStageBytes = (kBM + kBN) * kBK * 4;  // 32 KB
+constexpr uint32_t kTmemCols = 128;
+constexpr long long kSpinLimit = 1LL << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// bounded wait on phase `parity`; returns false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// UMMA shared-memory descriptor, K-major operand in the 128-byte swizzled layout
+// written by TMA: 8-row groups of 128-byte rows, 1024 bytes apart.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: kind::tf32, D f32, A/B tf32, both K-major, M = 128, N = 128
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                            ((uint32_t)(kBM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUtensorMap tmap,
+                                                   int64_t d, int64_t nk, double lambda,
+                                                   float* __restrict__ A, int64_t lda,
+                                                   int32_t* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte alignment for the swizzled stages
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+
+  // tile (ti >= tj) of the lower triangle
+  int64_t t = blockIdx.x, ti = 0;
+  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+  const int64_t tj = t - ti * (ti + 1) / 2;
+  const int row0 = (int)(ti * kBM), col0 = (int)(tj * kBN);
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (wid == 0) {  // tensor memory for the 128 x 128 accumulator
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+
+  if (wid == 0 && lane == 0) {
+    // producer
+    for (int64_t kb = 0; kb < nk; ++kb) {
+      const int s = (int)(kb % kStages);
+      const uint32_t ph = (uint32_t)((kb / kStages) & 1);
+      if (!mbar_wait(&empty_bar[s], ph ^ 1)) { s_abort = 1; atomicExch(err, 1); break; }
+      if (*(volatile int*)&s_abort) break;
+      unsigned char* st = base + s * kStageBytes;
+      mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
+      tma_load_2d(st, &tmap, &full_bar[s], (int)(kb * kBK), row0);
+      tma_load_2d(st + kBM * kBK * 4, &tmap, &full_bar[s], (int)(kb * kBK), col0);
+    }
+  } else if (wid == 1 && lane == 0) {
+    // MMA issuer
+    int64_t kb = 0;
+    for (; kb < nk; ++kb) {
+      const int s = (int)(kb % kStages);
+      const uint32_t ph = (uint32_t)((kb / kStages) & 1);
+      if (!mbar_wait(&full_bar[s], ph)) { s_abort = 1; atomicExch(err, 1); break; }
+      if (*(volatile int*)&s_abort) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(base + s * kStageBytes);
+      const uint32_t sb = sa + kBM * kBK * 4;
+#pragma unroll
+      for (int ks = 0; ks < kBK / 8; ++ks)  // K = 8 tf32 = 32 bytes per MMA
+        mma_tf32(tmem, umma_desc_sw128(sa + ks * 32), umma_desc_sw128(sb + ks * 32),
+                 (kb > 0 || ks > 0) ? 1u : 0u);
+      mma_commit(&empty_bar[s]);
+    }
+    mma_commit(&done_bar);  // arrives once every MMA issued above has retired
+  }
+  __syncwarp();
+  // epilogue: all 128 threads, warp w reads TMEM lanes 32w..32w+31
+  const bool ok = mbar_wait(&done_bar, 0);
+  if (!ok && lane == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok && !*(volatile int*)&s_abort) {
+    const int64_t r = row0 + wid * 32 + lane;
+    for (int c0 = 0; c0 < kBN; c0 += 16) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(wid * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+          "%11, %12, %13, %14, %15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (r < d) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int64_t cidx = col0 + c0 + q;
+          if (cidx < d && cidx <= r) {
+            float f = __uint_as_float(v[q]);
+            if (cidx == r) f = (float)((double)f + lambda);
+            A[r * lda + cidx] = f;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (wid == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+}
+
+// Xt[i * ldk + k] = X[k * d + i] (zero for k >= n): 32 x 32 tiles through shared memory
+__global__ void k_transpose_pad(const float* __restrict__ X, int64_t n, int64_t d,
+                                float* __restrict__ Xt, int64_t ldk) {
+  __shared__ float tile[32][33];
+  const int64_t k0 = (int64_t)blockIdx.x * 32, i0 = (int64_t)blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t k = k0 + r, i = i0 + threadIdx.x;
+    tile[r][threadIdx.x] = (k < n && i < d) ? X[k * d + i] : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t i = i0 + r, k = k0 + threadIdx.x;
+    if (i < d && k < ldk) Xt[i * ldk + k] = tile[threadIdx.x][r];
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+size_t gram_tc_ws_floats(int64_t n, int64_t d) { return (size_t)d * (size_t)round_up(n, 32); }
+
+// A (d x lda, lower triangle and diagonal; the caller mirrors) = X^T X + lambda I
+cudaError_t launch_gram_tc(cudaStream_t st, const float* X, int64_t n, int64_t d, double lambda,
+                           float* A, int64_t lda, float* Xt_ws, int32_t* err) {
+  const int64_t ldk = round_up(n, 32);
+  dim3 tb(32, 8), tg((unsigned)(ldk / 32), (unsigned)((d + 31) / 32));
+  k_transpose_pad<<<tg, tb, 0, st>>>(X, n, d, Xt_ws, ldk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)d};
+  const cuuint64_t strides[1] = {(cuuint64_t)ldk * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, Xt_ws, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const int64_t T = (d + kBM - 1) / kBM;
+  const int64_t tiles = T * (T + 1) / 2;
+  const size_t smem = (size_t)kStages * kStageBytes + 1024;
+  e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_gram_tc<<<(unsigned)tiles, 128, smem, st>>>(map, d, ldk / kBK, lambda, A, lda, err);
+  return cudaGetLastError();
+}
+
+}  // namespace rs

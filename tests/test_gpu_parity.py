@@ -308,3 +308,24 @@ def test_true_residual_fp32_x(rs, d):
         got = s.true_residual(w_near)
     ref = oracle.true_residual(X.astype(np.float64), y, lam, w_near)
     assert abs(got - ref) <= 1e-6 * ref
+
+
+@pytest.mark.parametrize("n,d", [(2000, 300), (1000, 256), (5000, 130)])
+def test_gram_tensor_cores(rs, n, d):
+    """X^T X + lambda I formed by the tensor-core kernel (TF32 inputs, FP32
+    accumulation): M = S^T A S with S = I_C, tau = m, equals the FP64 A[C, C] within
+    the TF32 rounding of both inputs, and the CUDA-core path within FP32 rounding."""
+    g = np.random.default_rng(n + d)
+    X = g.standard_normal((n, d)).astype(np.float32)
+    y = g.standard_normal(n)
+    lam = 0.7
+    C = orng.subsample_indices(5, 0, d, d)
+    A64, _ = oracle.form_system(X.astype(np.float64), y, lam)
+    ref = A64[np.ix_(C, C)]
+    bound = 2.0 ** -9 * (np.abs(X.astype(np.float64)).T @ np.abs(X.astype(np.float64)))[np.ix_(C, C)]
+    for tc in (True, False):
+        with rs.Solver(X, y, lam, sketch="subsample", tau=d, seed=5, precision="mixed",
+                       setup_tc=tc) as s:
+            M, _, _ = s.probe_step()
+        assert np.all(np.abs(M - ref) <= bound + 1e-6), tc
+        assert np.allclose(M, M.T, rtol=0, atol=0)
