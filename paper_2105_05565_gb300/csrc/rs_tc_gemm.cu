@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
   }
   __syncwarp();
   // epilogue: all 128 threads, warp w reads TMEM lanes 32w..32w+31
-  const bool ok = mbar_wait(&done_bar, 0);
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0));
   if (!ok && lane == 0) atomicExch(err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok && !*(volatile int*)&s_abort) {
