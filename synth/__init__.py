@@ -66,6 +66,22 @@ def spectrum_problem(n: int, d: int, sigma: np.ndarray, seed: int, noise: float 
     return X, y, w_true
 
 
+def _preload_torch_linalg():
+    """Load torch's lazily opened CUDA linear-algebra library by full path, so that
+    the QR below also works under tools that change the library search path."""
+    import ctypes
+    import os
+
+    import torch
+
+    p = os.path.join(os.path.dirname(torch.__file__), "lib", "libtorch_cuda_linalg.so")
+    if os.path.exists(p):
+        try:
+            ctypes.CDLL(p, mode=ctypes.RTLD_GLOBAL)
+        except OSError:
+            pass
+
+
 def spectrum_problem_torch(n: int, d: int, sigma, seed: int, noise: float = 0.01,
                            device="cuda"):
     """Large-size version of ``spectrum_problem`` drawn with torch on ``device``.
@@ -75,6 +91,7 @@ def spectrum_problem_torch(n: int, d: int, sigma, seed: int, noise: float = 0.01
     """
     import torch
 
+    _preload_torch_linalg()
     gen = torch.Generator(device=device)
     gen.manual_seed(int(seed))
     sig = torch.as_tensor(np.asarray(sigma), dtype=torch.float32, device=device)
