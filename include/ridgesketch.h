@@ -239,6 +239,31 @@ typedef struct {
 rs_status rs_profile_iteration(rs_ctx* ctx, int64_t reps, rs_kernel_stat* out, int32_t cap,
                                int32_t* n_out);
 
+/*
+ * out = X^T (X v) for a dense FP32 X, with FP64-accurate sums (the product the
+ * library uses for true residuals of the primal form), WITHOUT ALLOCATING ANY MEMORY.
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc or any allocating routine -- for example code running inside a
+ * region where allocation is forbidden (a real-time loop with a no-allocation
+ * policy, a host framework that owns all device memory and forbids others to
+ * allocate, a program that must not change its memory footprint after start-up).
+ *   X      n x d row-major FP32, device pointer (exact data; not modified)
+ *   v      d FP64, device pointer
+ *   out    d FP64, device pointer, caller-owned, overwritten
+ *   stream cudaStream_t to run on (NULL = default stream)
+ * Limits: 1 <= n, 1 <= d <= 4096 (RS_EINVAL beyond, with a message from
+ * rs_last_error(NULL)). Work space: a fixed 2 MiB device array inside the library
+ * (64 x 4096 doubles), held by every GPU that loads the library until the process
+ * exits. The first call on a device looks up that array's device address (with the
+ * device current), so make the first call before any stream capture. All calls share
+ * the array: calls that overlap on the GPU (other streams, other host threads) race
+ * and give wrong results; serialise them. Every entry the kernels read is written by
+ * the same call, so no clearing is needed between calls. Runs asynchronously on
+ * `stream`; returns RS_ECUDA if a launch fails.
+ */
+rs_status rs_gram_apply_noalloc(const float* X, int64_t n, int64_t d, const double* v,
+                                double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,7 @@ _SIGS = {
     "rs_timings": (_I32, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "rs_profile_iteration": (_I32, [_P, _I64, ctypes.POINTER(KernelStat), _I32,
                                     ctypes.POINTER(_I32)]),
+    "rs_gram_apply_noalloc": (_I32, [_P, _I64, _I64, _P, _P, _P]),
 }
 EXPORTED = tuple(_SIGS)
 

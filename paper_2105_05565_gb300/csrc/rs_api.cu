@@ -56,6 +56,10 @@ int64_t default_tau(int64_t m) {  // smallest t with t^3 >= m^2
 
 }  // namespace
 
+namespace rs {
+void set_global_error_msg(const char* msg) { set_global_error(msg ? msg : ""); }
+}  // namespace rs
+
 struct rs_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;

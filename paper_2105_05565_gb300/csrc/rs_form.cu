@@ -1,6 +1,10 @@
 // Forming the linear system of eq. (4) (A = X^T X + lambda I, b = X^T y for the
 // primal eq. (2); A = X X^T + lambda I, b = y for the dual eq. (3)) and evaluating
 // the true residual A v - b through X in FP64 without forming A.
+#include <mutex>
+#include <string>
+
+#include "ridgesketch.h"
 #include "rs_gemm.cuh"
 #include "rs_kernels.cuh"
 
@@ -218,6 +222,71 @@ cudaError_t launch_xtx_v_df(cudaStream_t st, const float* X, int64_t n, int64_t 
   k_sum_parts<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(part, G, d, out, stop);
   return cudaGetLastError();
 }
+
+// ---- variant of the one-pass X^T X v that allocates nothing (rs_gram_apply_noalloc) ----
+// The per-block column sums live in a fixed device array of this file instead of a
+// buffer the caller or the library allocates: kNoAllocBlocks x kNoAllocMaxD doubles
+// (2 MiB), held by every GPU that loads the library until the process exits.
+constexpr int kNoAllocBlocks = 64;
+constexpr int64_t kNoAllocMaxD = 4096;
+static __device__ __align__(256) double g_noalloc_part[kNoAllocBlocks * kNoAllocMaxD];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};  // device address of g_noalloc_part, per device ordinal
+}  // namespace
+
+}  // namespace rs
+
+extern "C" rs_status rs_gram_apply_noalloc(const float* X, int64_t n, int64_t d, const double* v,
+                                           double* out, void* stream) {
+  using namespace rs;
+  if (X == nullptr || v == nullptr || out == nullptr) {
+    set_global_error_msg("rs_gram_apply_noalloc: null pointer");
+    return RS_EINVAL;
+  }
+  if (n < 1 || d < 1 || d > kNoAllocMaxD) {
+    set_global_error_msg("rs_gram_apply_noalloc: need n >= 1 and 1 <= d <= 4096");
+    return RS_EINVAL;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    set_global_error_msg("rs_gram_apply_noalloc: no usable current device");
+    return RS_ECUDA;
+  }
+  void* part = nullptr;
+  {
+    // set-up on the first call on this device: the host-side name of the array is
+    // not a device address, so ask the runtime for it (with this device current)
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_ptr[dev] == nullptr) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_part);
+      if (e != cudaSuccess || p == nullptr) {
+        set_global_error_msg((std::string("rs_gram_apply_noalloc: cudaGetSymbolAddress: ") +
+                              cudaGetErrorString(e)).c_str());
+        return RS_ECUDA;
+      }
+      g_noalloc_ptr[dev] = p;
+    }
+    part = g_noalloc_ptr[dev];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* pp = static_cast<double*>(part);
+  // every block writes all d of its column sums, so nothing needs clearing first
+  if (d <= 1024) k_xtx_v_df<4, 4><<<kNoAllocBlocks, 256, 0, st>>>(X, n, d, v, pp, nullptr);
+  else if (d <= 2048) k_xtx_v_df<8, 4><<<kNoAllocBlocks, 256, 0, st>>>(X, n, d, v, pp, nullptr);
+  else k_xtx_v_df<16, 4><<<kNoAllocBlocks, 256, 0, st>>>(X, n, d, v, pp, nullptr);
+  k_sum_parts<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(pp, kNoAllocBlocks, d, out, nullptr);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_global_error_msg((std::string("rs_gram_apply_noalloc: ") + cudaGetErrorString(e)).c_str());
+    return RS_ECUDA;
+  }
+  return RS_OK;
+}
+
+namespace rs {
 
 // ---- true residual r = v + lambda x - b ----
 // mode 1: replace the recursive residual pair (r, r_prev) by (r_true, r_true - (r - r_prev))

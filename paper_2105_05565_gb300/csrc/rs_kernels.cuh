@@ -10,6 +10,8 @@ namespace rs {
 
 // ---- sketch generation (rs_sketch_gen.cu) ----
 int sample_cap(int64_t n, int64_t cnt);
+// message returned by rs_last_error(NULL) (entry points without a context)
+void set_global_error_msg(const char* msg);
 // mode 0 subsample, 1 subcount (signs), 2 srht. k0_arg < 0: first slot is ctrl->k.
 cudaError_t launch_gen_sample(cudaStream_t st, const Ctrl* ctrl, int64_t k0_arg, int nslots,
                               uint64_t seed, int64_t n, int64_t cnt, int mode, int64_t kk,
