@@ -121,6 +121,10 @@ typedef struct {
                             reduced so that the chunk's buffers stay under 4 GB */
   int32_t setup_tc;      /* RS_MIXED, primal, FP32 X: 1 = form X^T X on the tensor cores
                             (TF32 inputs, FP32 accumulation; default), 0 = FP32 CUDA cores */
+  int32_t iter_ctas;     /* subsample / count / subcount: CTAs of the persistent iteration
+                            kernel that spreads the rows of w and r over the GPU (rounded
+                            down to a multiple of 8); 0 = every SM (default); -1 = use the
+                            single-cluster iteration kernel instead */
 } rs_opts;
 
 /* Fill *o with the defaults listed above. */
@@ -174,6 +178,12 @@ const char* rs_last_error(const rs_ctx* ctx);
  * k_sum (SubCount sum size, else 0), m_pad (SRHT padded size 2^ceil(log2 m), else 0). */
 rs_status rs_get_dims(const rs_ctx* ctx, int64_t* m, int64_t* tau, int64_t* s,
                       int64_t* k_sum, int64_t* m_pad);
+
+/* Launch shape of the fused iteration kernel of a context: ctas CTAs owning q rows
+ * each of w and r (persistent kernel over the GPU), or ctas = q = 0 when the chunk's
+ * iterations run on one thread-block cluster (Gaussian; or the slices do not fit
+ * shared memory; or rs_opts.iter_ctas = -1). Outputs may be NULL. */
+rs_status rs_iter_plan(const rs_ctx* ctx, int32_t* ctas, int64_t* q);
 
 /*
  * Sketch of iteration k as drawn by the device generator (parity hook), host outputs:

@@ -50,7 +50,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("refresh_every", ctypes.c_int32),
                 ("sub_s", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
                 ("device", ctypes.c_int32), ("chol_fp64", ctypes.c_int32), ("chunk", ctypes.c_int64),
-                ("setup_tc", ctypes.c_int32)]
+                ("setup_tc", ctypes.c_int32), ("iter_ctas", ctypes.c_int32)]
 
 
 class KernelStat(ctypes.Structure):
@@ -71,6 +71,7 @@ _SIGS = {
     "rs_destroy": (None, [_P]),
     "rs_last_error": (ctypes.c_char_p, [_P]),
     "rs_get_dims": (_I32, [_P] + [ctypes.POINTER(_I64)] * 5),
+    "rs_iter_plan": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
     "rs_dump_sketch": (_I32, [_P, _I64, _P, _P, _P]),
     "rs_dump_gaussian": (_I32, [_P, _I64, _P]),
     "rs_get_state": (_I32, [_P, _P, _P, _P, _P, ctypes.POINTER(_I64)]),
@@ -142,7 +143,7 @@ class Solver:
     def __init__(self, X, y, lam, form="primal", sketch="count", tau=0, momentum="none", seed=0,
                  precision="fp64", refresh_every=50, sub_s=0, chol_fp64=False, chunk=0,
                  eta=0.995, beta_switch=0.5, gamma_c=1.0, beta_c=0.5, uncapped=False,
-                 device=0, stream=None, setup_tc=True):
+                 device=0, stream=None, setup_tc=True, iter_ctas=0):
         L = lib()
         self._ctx = None
         xdt = np.float32 if str(getattr(X, "dtype", "")).endswith("float32") else np.float64
@@ -163,6 +164,7 @@ class Solver:
         opts.chol_fp64 = int(bool(chol_fp64))
         opts.chunk = int(chunk)
         opts.setup_tc = int(bool(setup_tc))
+        opts.iter_ctas = int(iter_ctas)
         st = stream if stream is not None else _default_stream(device)
         opts.cuda_stream = st
         ctx = _P()
@@ -176,6 +178,9 @@ class Solver:
         dims = [_I64() for _ in range(5)]
         L.rs_get_dims(ctx, *[ctypes.byref(v) for v in dims])
         self.m, self.tau, self.s, self.k_sum, self.m_pad = (v.value for v in dims)
+        ctas, q = _I32(), _I64()
+        L.rs_iter_plan(ctx, ctypes.byref(ctas), ctypes.byref(q))
+        self.iter_ctas, self.iter_rows = ctas.value, q.value
 
     # -- helpers --
     def _check(self, status, allow=(RS_OK,)):

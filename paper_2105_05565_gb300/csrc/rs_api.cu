@@ -86,7 +86,15 @@ struct rs_ctx {
   double *rS = nullptr, *delta = nullptr;
   int64_t sa_slot = 0, m_slot = 0, l_slot = 0;
   int32_t *perm = nullptr, *boff = nullptr;
-  int32_t* inv = nullptr;  // per slot: row -> bucket | sign (bucket-row sketches)
+  int32_t* inv = nullptr;  // per slot (stride ld): row -> bucket | sign (bucket-row sketches)
+  // persistent iteration kernel over the whole GPU (bucket-row sketches)
+  bool use_wide = false;
+  WidePlan wide{};
+  void* Pm = nullptr;       // per slot: M^+ = L^{-T} L^{-1}, tau x pld (factor precision)
+  int64_t pld = 0, p_slot = 0;
+  uint64_t* xpart = nullptr;   // all-reduce partials, 2 x nblk x (tau + 1) x 2 tagged words
+  uint64_t* xflags = nullptr;  // launch counter of the tags
+  int32_t* xabort = nullptr;
   int64_t perm_stride = 0, boff_stride = 0;
   int64_t nslots = 0;
   int32_t* err_flag = nullptr;
@@ -146,7 +154,7 @@ void free_all(rs_ctx* c) {
                   c->Linv, c->fws, c->rS, c->delta, c->perm, c->boff, c->inv, c->err_flag,
                   c->ndropped,
                   c->gam, c->bet, c->hist, c->partials, c->vn, c->vd, c->xt_part, c->rel_dev,
-                  c->ctrl};
+                  c->ctrl, c->Pm, c->xpart, c->xflags, c->xabort};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->ctrl_h) cudaFreeHost(c->ctrl_h);
@@ -171,11 +179,12 @@ RowsView<T> rows_view(const rs_ctx* c) {
   RowsView<T> v{};
   v.A = static_cast<const T*>(c->A);
   v.lda = c->ld;
-  v.SA = (c->sketch == RS_SUBSAMPLE) ? nullptr : static_cast<const T*>(c->SA);
+  v.SA = (c->sketch == RS_SUBSAMPLE && !c->use_wide) ? nullptr : static_cast<const T*>(c->SA);
   v.ldsa = c->ld;
   v.sa_slot = c->sa_slot;
   v.ST = (c->sketch == RS_GAUSSIAN) ? static_cast<const T*>(c->ST) : nullptr;
   v.st_slot = c->sa_slot;
+  v.bq = c->use_wide ? c->wide.q : 0;
   return v;
 }
 
@@ -210,25 +219,32 @@ rs_status enqueue_gen(rs_ctx* c, int64_t k0_arg, int nslots) {
 // (parity hooks) runs every slot starting at iteration k0_arg; force = 0 starts at
 // ctrl->k0 and skips slots the solve will not reach.
 template <typename T>
-rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots) {
+rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots, bool want_p) {
   cudaStream_t st = c->stream;
   rs_status s = enqueue_gen(c, force ? k0_arg : -1, nslots);
   if (s != RS_OK) return s;
   const PlanView plan = plan_view(c);
   if (c->inv != nullptr)
     CKC(c, launch_inv_map(st, c->ctrl, force, nslots, plan, c->m, c->tau,
-                          c->sketch == RS_COUNT ? 1 : 0, c->inv, c->m));
+                          c->sketch == RS_COUNT ? 1 : 0, c->inv, c->ld));
   const T* A = static_cast<const T*>(c->A);
   T* SA = static_cast<T*>(c->SA);
   switch (c->sketch) {
     case RS_SUBSAMPLE:
-      CKC(c, launch_msys_batched<T>(st, c->ctrl, force, nslots, plan, rows_view<T>(c), c->m, c->tau,
-                                    c->M, c->m_slot));
-      break;
     case RS_COUNT:
     case RS_SUBCOUNT:
+      if (c->sketch == RS_SUBSAMPLE && !c->use_wide) {  // M = A[C, C] gathered, no S^T A
+        CKC(c, launch_msys_batched<T>(st, c->ctrl, force, nslots, plan, rows_view<T>(c), c->m,
+                                      c->tau, c->M, c->m_slot));
+        break;
+      }
+      if (sa_msys_fits<T>(c->m, c->tau, c->perm_stride)) {  // S^T A and M in one pass
+        CKC(c, launch_sa_msys<T>(st, c->ctrl, force, nslots, plan, A, c->ld, c->m, c->tau, SA, c->ld,
+                                 c->sa_slot, c->use_wide ? c->wide.q : 0, c->M, c->m_slot));
+        break;
+      }
       CKC(c, launch_sa_batched<T>(st, c->ctrl, force, nslots, plan, A, c->ld, c->m, c->tau, SA,
-                                  c->ld, c->sa_slot));
+                                  c->ld, c->sa_slot, c->use_wide ? c->wide.q : 0));
       CKC(c, launch_msys_batched<T>(st, c->ctrl, force, nslots, plan, rows_view<T>(c), c->m, c->tau,
                                     c->M, c->m_slot));
       break;
@@ -245,6 +261,12 @@ rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots) {
                                    c->mp, c->tau, SA, c->ld, c->sa_slot, c->M, c->m_slot));
       break;
   }
+  if (want_p && !c->f64_factor() && c->tau <= kSweepMaxTau) {
+    // FP32 M^+ directly (symmetric sweeps), no triangular factor
+    CKC(c, launch_sweep_inv(st, c->ctrl, force, nslots, c->M, c->m_slot, c->tau,
+                            static_cast<float*>(c->Pm), c->pld, c->p_slot, c->ndropped));
+    return RS_OK;
+  }
   if (c->f64_factor())
     CKC(c, launch_factor_inv<double>(st, c->ctrl, force, nslots, c->M, c->m_slot, c->tau,
                                      static_cast<double*>(c->Linv), c->l_slot,
@@ -253,12 +275,21 @@ rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots) {
     CKC(c, launch_factor_inv<float>(st, c->ctrl, force, nslots, c->M, c->m_slot, c->tau,
                                     static_cast<float*>(c->Linv), c->l_slot,
                                     static_cast<float*>(c->fws), c->ndropped));
+  if (want_p) {
+    if (c->f64_factor())
+      CKC(c, launch_pinv<double>(st, c->ctrl, force, nslots, static_cast<const double*>(c->Linv),
+                                 c->l_slot, c->tau, static_cast<double*>(c->Pm), c->pld, c->p_slot));
+    else
+      CKC(c, launch_pinv<float>(st, c->ctrl, force, nslots, static_cast<const float*>(c->Linv),
+                                c->l_slot, c->tau, static_cast<float*>(c->Pm), c->pld, c->p_slot));
+  }
   return RS_OK;
 }
 
-rs_status enqueue_phase1(rs_ctx* c, int force, int64_t k0_arg, int nslots) {
-  return c->mixed() ? enqueue_phase1_t<float>(c, force, k0_arg, nslots)
-                    : enqueue_phase1_t<double>(c, force, k0_arg, nslots);
+// want_p: also M^+ per slot, for the persistent iteration kernel
+rs_status enqueue_phase1(rs_ctx* c, int force, int64_t k0_arg, int nslots, bool want_p = false) {
+  return c->mixed() ? enqueue_phase1_t<float>(c, force, k0_arg, nslots, want_p)
+                    : enqueue_phase1_t<double>(c, force, k0_arg, nslots, want_p);
 }
 
 template <typename TF, typename T>
@@ -326,7 +357,7 @@ rs_status enqueue_iterate_t(rs_ctx* c) {
   g.ST = c->sketch == RS_GAUSSIAN ? static_cast<const T*>(c->ST) : nullptr;
   g.plan = plan_view(c);
   g.inv = c->inv;
-  g.inv_slot = c->m;
+  g.inv_slot = c->ld;
   g.Linv = static_cast<const TF*>(c->Linv);
   g.l_slot = c->l_slot;
   g.gam = c->gam; g.bet = c->bet;
@@ -337,8 +368,37 @@ rs_status enqueue_iterate_t(rs_ctx* c) {
   return RS_OK;
 }
 
-// every iteration of the chunk in one cluster launch (all sketches but SRHT)
+template <typename T, typename TF>
+rs_status enqueue_wide_t(rs_ctx* c) {
+  WideArgs<T, TF> g{};
+  g.mixed = c->mixed();
+  g.rows = static_cast<const T*>(c->SA);
+  g.sa_slot = c->sa_slot;
+  g.inv = c->inv;
+  g.inv_slot = c->ld;
+  g.P = static_cast<const TF*>(c->Pm);
+  g.pld = c->pld;
+  g.p_slot = c->p_slot;
+  g.gam = c->gam; g.bet = c->bet;
+  g.w = c->w; g.wp = c->wp; g.r = c->r; g.rp = c->rp;
+  g.hist = c->hist; g.delta_out = c->delta;
+  g.part = c->xpart;
+  g.epoch = c->xflags;
+  g.abort_word = c->xabort;
+  g.m = c->m; g.tau = c->tau; g.chunk = c->chunk; g.q = c->wide.q;
+  g.nblk = c->wide.nblk;
+  g.nsab = c->wide.nsab;
+  CKC(c, (launch_iterate_wide<T, TF>(c->stream, c->ctrl, g, c->wide.smem)));
+  return RS_OK;
+}
+
+// every iteration of the chunk in one launch (all sketches but SRHT): over the
+// whole GPU for the bucket-row sketches, else on one thread-block cluster
 rs_status enqueue_iterate(rs_ctx* c) {
+  if (c->use_wide) {
+    if (!c->mixed()) return enqueue_wide_t<double, double>(c);
+    return c->f64_factor() ? enqueue_wide_t<float, double>(c) : enqueue_wide_t<float, float>(c);
+  }
   if (!c->mixed()) return enqueue_iterate_t<double, double>(c);
   return c->f64_factor() ? enqueue_iterate_t<float, double>(c) : enqueue_iterate_t<float, float>(c);
 }
@@ -389,7 +449,7 @@ rs_status enqueue_refresh(rs_ctx* c) {
 
 rs_status enqueue_chunk(rs_ctx* c, bool with_refresh) {
   CKC(c, launch_chunk_begin(c->stream, c->ctrl));
-  rs_status s = enqueue_phase1(c, 0, -1, (int)c->nslots);
+  rs_status s = enqueue_phase1(c, 0, -1, (int)c->nslots, c->use_wide);
   if (s != RS_OK) return s;
   if (c->sketch != RS_SRHT) {
     s = enqueue_iterate(c);
@@ -650,9 +710,9 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   if (c->mixed() && c->chunk != c->refresh_every) c->chunk = c->refresh_every;
   {
     // keep the per-slot buffers of one chunk under 4 GB
-    const int64_t per_slot = (sketch == RS_SUBSAMPLE ? 0 : c->tau * c->ld * (int64_t)c->elem()) *
-                                 (sketch == RS_GAUSSIAN ? 2 : 1) +
-                             c->tau * c->tau * 16 + m * 4;
+    // (S^T A is materialised for every sketch once the persistent kernel runs it)
+    const int64_t per_slot = c->tau * c->ld * (int64_t)c->elem() * (sketch == RS_GAUSSIAN ? 2 : 1) +
+                             c->tau * c->tau * 24 + c->ld * 4;
     const int64_t cap = std::max<int64_t>(1, (int64_t)4e9 / std::max<int64_t>(per_slot, 1));
     if (c->chunk > cap) {
       if (c->mixed()) { c->err = "rs_create: refresh_every too large for the per-iteration buffers"; return fail(RS_EINVAL); }
@@ -729,10 +789,37 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   TRY(dalloc(c, &c->ndropped, 1));
   TRYC(cudaMemsetAsync(c->err_flag, 0, sizeof(int32_t), st));
   TRYC(cudaMemsetAsync(c->ndropped, 0, sizeof(int32_t), st));
+  if ((sketch == RS_SUBSAMPLE || sketch == RS_COUNT || sketch == RS_SUBCOUNT) && o.iter_ctas >= 0) {
+    // persistent iteration kernel over the whole GPU: S^T A blocked by CTA, M^+ per
+    // slot and the all-reduce buffers
+    bool fits = false;
+    if (!c->mixed()) fits = wide_plan<double, double>(m, c->tau, o.iter_ctas, c->chunk, &c->wide);
+    else if (c->f64_factor()) fits = wide_plan<float, double>(m, c->tau, o.iter_ctas, c->chunk, &c->wide);
+    else fits = wide_plan<float, float>(m, c->tau, o.iter_ctas, c->chunk, &c->wide);
+    if (fits) {
+      const size_t fel = c->f64_factor() ? 8 : 4;
+      c->pld = round_up(c->tau, 4);
+      c->p_slot = c->tau * c->pld;
+      TRYC(cudaMalloc(&c->Pm, (size_t)c->nslots * c->p_slot * fel));
+      const size_t nwords = (size_t)2 * c->wide.nblk * (c->tau + 1) * 2;
+      TRY(dalloc(c, &c->xpart, nwords));
+      TRY(dalloc(c, &c->xflags, 1));
+      TRY(dalloc(c, &c->xabort, 1));
+      TRYC(cudaMemsetAsync(c->xpart, 0, nwords * sizeof(uint64_t), st));
+      TRYC(cudaMemsetAsync(c->xflags, 0, sizeof(uint64_t), st));
+      TRYC(cudaMemsetAsync(c->xabort, 0, sizeof(int32_t), st));
+      c->use_wide = true;
+    } else {
+      cudaGetLastError();
+    }
+  }
   {
     // per-slot buffers of phase 1 (sketched rows, M, inverse factor)
     const size_t fel = c->f64_factor() ? 8 : 4;
-    c->sa_slot = (sketch == RS_SUBSAMPLE) ? 0 : c->tau * c->ld;
+    if (c->use_wide)
+      c->sa_slot = (m + c->wide.q - 1) / c->wide.q * c->tau * round_up(c->wide.q, 4);
+    else
+      c->sa_slot = (sketch == RS_SUBSAMPLE) ? 0 : c->tau * c->ld;
     c->m_slot = c->tau * c->tau;
     c->l_slot = c->tau * c->tau;
     const size_t nsl = (size_t)c->nslots;
@@ -741,7 +828,7 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     const size_t need_smem = (size_t)factor_ws_elems(c->tau) * fel + 4096;
     if (need_smem > 220 * 1024 || c->tau > 4096)
       TRYC(cudaMalloc(&c->fws, nsl * factor_ws_elems(c->tau) * fel));
-    if (sketch != RS_SUBSAMPLE) {
+    if (c->sa_slot > 0) {
       TRYC(cudaMalloc(&c->SA, nsl * c->sa_slot * c->elem()));
       TRYC(cudaMemsetAsync(c->SA, 0, nsl * c->sa_slot * c->elem(), st));
     }
@@ -751,11 +838,11 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     }
   }
   if (sketch != RS_GAUSSIAN) {
-    c->perm_stride = (sketch == RS_COUNT) ? m : (sketch == RS_SUBCOUNT ? c->s : c->tau);
+    c->perm_stride = round_up((sketch == RS_COUNT) ? m : (sketch == RS_SUBCOUNT ? c->s : c->tau), 4);
     c->boff_stride = c->tau + 1;
     TRY(dalloc(c, &c->perm, (size_t)c->perm_stride * c->nslots));
     TRY(dalloc(c, &c->boff, (size_t)c->boff_stride * c->nslots));
-    if (sketch != RS_SRHT) TRY(dalloc(c, &c->inv, (size_t)m * c->nslots));
+    if (sketch != RS_SRHT) TRY(dalloc(c, &c->inv, (size_t)c->ld * c->nslots));
   }
   c->npartials = std::max<int64_t>(update_blocks(m), 256);
   TRY(dalloc(c, &c->partials, c->npartials));
@@ -835,7 +922,9 @@ rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int3
     int32_t gen_err = 0;
     CKC(c, cudaMemcpy(&gen_err, c->err_flag, sizeof(int32_t), cudaMemcpyDeviceToHost));
     if (gen_err) FAILC(c, RS_ECUDA, "sketch generation: sample threshold search failed");
-    if (h->status == RS_ENUMERIC) {
+    if (h->status == RS_ETIMEOUT) {
+      FAILC(c, RS_ETIMEOUT, "rs_solve: a bounded device-side wait of the iteration kernel gave up");
+    } else if (h->status == RS_ENUMERIC) {
       result = RS_ENUMERIC;
       c->err = "rs_solve: NaN or Inf in the residual";
     } else {
@@ -855,6 +944,13 @@ rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int3
   CKC(c, cudaStreamSynchronize(st));
   if (iters_out) *iters_out = iters;
   return result;
+}
+
+rs_status rs_iter_plan(const rs_ctx* c, int32_t* ctas, int64_t* q) {
+  if (!c) return RS_EINVAL;
+  if (ctas) *ctas = c->use_wide ? c->wide.nblk : 0;
+  if (q) *q = c->use_wide ? c->wide.q : 0;
+  return RS_OK;
 }
 
 rs_status rs_dump_sketch(rs_ctx* c, int64_t k, int32_t* idx, int8_t* sign, int32_t* bucket) {
@@ -1003,6 +1099,7 @@ rs_status rs_step(rs_ctx* c, int64_t n_iters, double* hist_out) {
     if ((s = read_ctrl(c)) != RS_OK) return s;
     if (h->stop) break;
   }
+  if (h->status == RS_ETIMEOUT) FAILC(c, RS_ETIMEOUT, "rs_step: a bounded device-side wait gave up");
   if (h->status == RS_ENUMERIC) FAILC(c, RS_ENUMERIC, "rs_step: NaN or Inf in the residual");
   if (hist_out)
     CKC(c, cudaMemcpy(hist_out, c->hist + k0 + 1, n_iters * sizeof(double), cudaMemcpyDeviceToHost));
@@ -1094,43 +1191,90 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
           return enqueue_gen(c, -1, ns);
         });
         if (s != RS_OK) break;
-        if (c->sketch == RS_COUNT || c->sketch == RS_SUBCOUNT) {
-          s = timed("sa", [&]() -> rs_status {
+        const bool has_sa = c->sketch == RS_COUNT || c->sketch == RS_SUBCOUNT || c->use_wide;
+        const int64_t bq = c->use_wide ? c->wide.q : 0;
+        const bool fused = has_sa && (c->mixed() ? sa_msys_fits<float>(c->m, c->tau, c->perm_stride)
+                                                 : sa_msys_fits<double>(c->m, c->tau, c->perm_stride));
+        if (fused) {
+          // S^T A and M in one pass: A rows read once per slot, S^T A written once
+          s = timed("sa_msys", [&]() -> rs_status {
             if (c->mixed())
-              CKC(c, launch_sa_batched<float>(c->stream, c->ctrl, 0, ns, plan, static_cast<const float*>(c->A), c->ld, c->m, c->tau, static_cast<float*>(c->SA), c->ld, c->sa_slot));
+              CKC(c, launch_sa_msys<float>(c->stream, c->ctrl, 0, ns, plan, static_cast<const float*>(c->A), c->ld, c->m, c->tau, static_cast<float*>(c->SA), c->ld, c->sa_slot, bq, c->M, c->m_slot));
             else
-              CKC(c, launch_sa_batched<double>(c->stream, c->ctrl, 0, ns, plan, static_cast<const double*>(c->A), c->ld, c->m, c->tau, static_cast<double*>(c->SA), c->ld, c->sa_slot));
+              CKC(c, launch_sa_msys<double>(c->stream, c->ctrl, 0, ns, plan, static_cast<const double*>(c->A), c->ld, c->m, c->tau, static_cast<double*>(c->SA), c->ld, c->sa_slot, bq, c->M, c->m_slot));
             return RS_OK;
           });
-          grp("sa").bytes = nsl * (rows * m * el + tau * m * el + rows * 4.0);
-          grp("sa").flops = nsl * rows * m;
+          grp("sa_msys").bytes = nsl * (rows * m * el + tau * m * el + rows * 4.0 + tau * tau * 8.0);
+          grp("sa_msys").flops = nsl * (rows * m + tau * rows);
+          if (s != RS_OK) break;
+        } else {
+          if (has_sa) {
+            s = timed("sa", [&]() -> rs_status {
+              if (c->mixed())
+                CKC(c, launch_sa_batched<float>(c->stream, c->ctrl, 0, ns, plan, static_cast<const float*>(c->A), c->ld, c->m, c->tau, static_cast<float*>(c->SA), c->ld, c->sa_slot, bq));
+              else
+                CKC(c, launch_sa_batched<double>(c->stream, c->ctrl, 0, ns, plan, static_cast<const double*>(c->A), c->ld, c->m, c->tau, static_cast<double*>(c->SA), c->ld, c->sa_slot, bq));
+              return RS_OK;
+            });
+            grp("sa").bytes = nsl * (rows * m * el + tau * m * el + rows * 4.0);
+            grp("sa").flops = nsl * rows * m;
+            if (s != RS_OK) break;
+          }
+          s = timed("msys", [&]() -> rs_status {
+            if (c->mixed()) CKC(c, launch_msys_batched<float>(c->stream, c->ctrl, 0, ns, plan, rows_view<float>(c), c->m, c->tau, c->M, c->m_slot));
+            else CKC(c, launch_msys_batched<double>(c->stream, c->ctrl, 0, ns, plan, rows_view<double>(c), c->m, c->tau, c->M, c->m_slot));
+            return RS_OK;
+          });
+          grp("msys").bytes = nsl * ((c->sketch == RS_SUBSAMPLE ? tau * tau * el : tau * m * el + rows * 4.0) + tau * tau * 8.0);
+          grp("msys").flops = nsl * (c->sketch == RS_SUBSAMPLE ? 0.0 : tau * rows);
           if (s != RS_OK) break;
         }
-        s = timed("msys", [&]() -> rs_status {
-          if (c->mixed()) CKC(c, launch_msys_batched<float>(c->stream, c->ctrl, 0, ns, plan, rows_view<float>(c), c->m, c->tau, c->M, c->m_slot));
-          else CKC(c, launch_msys_batched<double>(c->stream, c->ctrl, 0, ns, plan, rows_view<double>(c), c->m, c->tau, c->M, c->m_slot));
-          return RS_OK;
-        });
-        grp("msys").bytes = nsl * ((c->sketch == RS_SUBSAMPLE ? tau * tau * el : tau * m * el + rows * 4.0) + tau * tau * 8.0);
-        grp("msys").flops = nsl * (c->sketch == RS_SUBSAMPLE ? 0.0 : tau * rows);
-        if (s != RS_OK) break;
-        s = timed("factor", [&]() -> rs_status {
+        const bool sweep = c->use_wide && !c->f64_factor() && c->tau <= kSweepMaxTau;
+        if (sweep) {
+          s = timed("sweep", [&]() -> rs_status {
+            CKC(c, launch_sweep_inv(c->stream, c->ctrl, 0, ns, c->M, c->m_slot, c->tau, static_cast<float*>(c->Pm), c->pld, c->p_slot, c->ndropped));
+            return RS_OK;
+          });
+          grp("sweep").bytes = nsl * tau * tau * (8.0 + 4.0);
+          grp("sweep").flops = nsl * tau * tau * tau;
+          if (s != RS_OK) break;
+        }
+        if (!sweep) s = timed("factor", [&]() -> rs_status {
           if (c->f64_factor())
             CKC(c, launch_factor_inv<double>(c->stream, c->ctrl, 0, ns, c->M, c->m_slot, c->tau, static_cast<double*>(c->Linv), c->l_slot, static_cast<double*>(c->fws), c->ndropped));
           else
             CKC(c, launch_factor_inv<float>(c->stream, c->ctrl, 0, ns, c->M, c->m_slot, c->tau, static_cast<float*>(c->Linv), c->l_slot, static_cast<float*>(c->fws), c->ndropped));
           return RS_OK;
         });
-        grp("factor").bytes = nsl * (tau * tau * (8.0 + fel));
-        grp("factor").flops = nsl * (2.0 * tau * tau * tau / 3.0);
+        if (!sweep) {
+          grp("factor").bytes = nsl * (tau * tau * (8.0 + fel));
+          grp("factor").flops = nsl * (2.0 * tau * tau * tau / 3.0);
+        }
         if (s != RS_OK) break;
+        if (c->use_wide && !sweep) {
+          s = timed("pinv", [&]() -> rs_status {
+            if (c->f64_factor())
+              CKC(c, launch_pinv<double>(c->stream, c->ctrl, 0, ns, static_cast<const double*>(c->Linv), c->l_slot, c->tau, static_cast<double*>(c->Pm), c->pld, c->p_slot));
+            else
+              CKC(c, launch_pinv<float>(c->stream, c->ctrl, 0, ns, static_cast<const float*>(c->Linv), c->l_slot, c->tau, static_cast<float*>(c->Pm), c->pld, c->p_slot));
+            return RS_OK;
+          });
+          grp("pinv").bytes = nsl * (tau * tau * 2.0 * fel);
+          grp("pinv").flops = nsl * (2.0 * tau * tau * tau);
+          if (s != RS_OK) break;
+        }
       }
     }
     if (c->sketch != RS_SRHT) {
       // fused: the whole chunk's iterations in one launch
       const int64_t nit = std::min<int64_t>(c->chunk, reps - it);
       s = timed("iterate", [&]() { return enqueue_iterate(c); });
-      grp("iterate").bytes = (double)nit * (tau * m * el + tau * tau * fel + 80.0 * m);
+      // algorithmic HBM bytes: S^T A (or the sampled rows of A) and the small system
+      // of every iteration; the persistent kernel reads and writes w, w_prev, r,
+      // r_prev once per launch, the cluster kernel every iteration
+      grp("iterate").bytes = c->use_wide
+          ? (double)nit * (tau * m * el + tau * tau * fel + 4.0 * m) + 64.0 * m
+          : (double)nit * (tau * m * el + tau * tau * fel + 80.0 * m);
       grp("iterate").flops = (double)nit * (2.0 * tau * m + 2.0 * tau * tau + 10.0 * m);
       grp("iterate").iters += nit;
       if (s == RS_OK && c->mixed() && (it + nit) % c->refresh_every == 0) {

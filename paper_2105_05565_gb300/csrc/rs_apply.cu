@@ -21,6 +21,18 @@ __device__ __forceinline__ void vadd(double2& a, const double2& b, bool neg) {
   if (neg) { a.x -= b.x; a.y -= b.y; } else { a.x += b.x; a.y += b.y; }
 }
 
+// offset of entry (j, i) of a slot's S^T A: row-major with row stride ld (bq = 0),
+// or blocked by slices of bq rows of the iterate: the tau x round_up(bq, 4) block
+// of slice i / bq is contiguous (the persistent iteration kernel copies one block
+// per CTA and iteration)
+__host__ __device__ __forceinline__ int64_t sa_off(int64_t j, int64_t i, int64_t ld, int64_t bq,
+                                                   int64_t tau) {
+  if (bq == 0) return j * ld + i;
+  const int64_t bqs = (bq + 3) / 4 * 4;
+  const int64_t c = i / bq;
+  return c * tau * bqs + j * bqs + (i - c * bq);
+}
+
 // ---------------------------------------------------------------------------
 // Count / SubCount (Section 4.2): SA_s[j, :] = sum over bucket j of sign * A[row, :]
 // for every slot s of the chunk. One warp per (slot, bucket, column slab of 32
@@ -33,7 +45,7 @@ __global__ void __launch_bounds__(256) k_sa_batched(const Ctrl* __restrict__ ctr
                                                     int nslots, PlanView plan,
                                                     const T* __restrict__ A, int64_t lda,
                                                     int64_t m, int64_t tau, T* __restrict__ SA,
-                                                    int64_t ldsa, int64_t sa_slot) {
+                                                    int64_t ldsa, int64_t sa_slot, int64_t bq) {
   using V = typename Vec<T>::type;
   constexpr int VN = Vec<T>::n;
   const int64_t nact = active_slots(ctrl, force, nslots);
@@ -69,20 +81,22 @@ __global__ void __launch_bounds__(256) k_sa_batched(const Ctrl* __restrict__ ctr
       const int32_t e = perm[t];
       vadd(acc, __ldg(reinterpret_cast<const V*>(A + (int64_t)entry_row(e) * lda + c)), entry_neg(e));
     }
-    if (c < ldsa) *reinterpret_cast<V*>(SA + s * sa_slot + j * ldsa + c) = acc;
+    if (bq == 0 ? c < ldsa : c < m)
+      *reinterpret_cast<V*>(SA + s * sa_slot + sa_off(j, c, ldsa, bq, tau)) = acc;
   }
 }
 
 template <typename T>
 cudaError_t launch_sa_batched(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
                               PlanView plan, const T* A, int64_t lda, int64_t m, int64_t tau, T* SA,
-                              int64_t ldsa, int64_t sa_slot) {
+                              int64_t ldsa, int64_t sa_slot, int64_t bq) {
   constexpr int VN = Vec<T>::n;
   const int64_t units = (int64_t)nslots * tau * ((m + 32 * VN - 1) / (32 * VN));
   int blocks = (int)std::min<int64_t>((units + 7) / 8, 152 * 8);
   if (blocks < 1) blocks = 1;
+  if (bq % 4 != 0) return cudaErrorInvalidValue;  // a vector never straddles two blocks
   k_sa_batched<T><<<blocks, 256, 0, st>>>(ctrl, force, nslots, plan, A, lda, m, tau, SA, ldsa,
-                                          sa_slot);
+                                          sa_slot, bq);
   return cudaGetLastError();
 }
 
@@ -112,26 +126,28 @@ __global__ void __launch_bounds__(512) k_msys_batched(const Ctrl* __restrict__ c
       Ms[j * tau + l] = (double)rowj[entry_row(perm[l])];
     return;
   }
-  const T* rowj = rows.SA + s * rows.sa_slot + j * rows.ldsa;
+  const T* Ss = rows.SA + s * rows.sa_slot;
   const int32_t* sp = perm;
   const int32_t* sb = boff;
-  const T* sr = rowj;
+  const T* sr = Ss + j * rows.ldsa;  // row j when row-major
   if (staged) {
     int32_t* sperm = reinterpret_cast<int32_t*>(smem_raw);
     int32_t* sboff = sperm + nperm;
     T* srow = reinterpret_cast<T*>(smem_raw + ((size_t)(nperm + tau + 1) * 4 + 15) / 16 * 16);
     for (int64_t t = threadIdx.x; t < nperm; t += blockDim.x) sperm[t] = perm[t];
     for (int64_t t = threadIdx.x; t <= tau; t += blockDim.x) sboff[t] = boff[t];
-    for (int64_t t = threadIdx.x; t < m; t += blockDim.x) srow[t] = rowj[t];
+    for (int64_t t = threadIdx.x; t < m; t += blockDim.x)
+      srow[t] = Ss[sa_off(j, t, rows.ldsa, rows.bq, tau)];
     __syncthreads();
     sp = sperm; sb = sboff; sr = srow;
   }
+  const bool flat = staged || rows.bq == 0;
   for (int64_t l = threadIdx.x; l < tau; l += blockDim.x) {
     T acc = T(0);
     const int32_t t1 = sb[l + 1];
     for (int32_t t = sb[l]; t < t1; ++t) {
       const int32_t e = sp[t];
-      const T v = sr[entry_row(e)];
+      const T v = flat ? sr[entry_row(e)] : Ss[sa_off(j, entry_row(e), rows.ldsa, rows.bq, tau)];
       acc += entry_neg(e) ? -v : v;
     }
     Ms[j * tau + l] = (double)acc;
@@ -157,6 +173,145 @@ cudaError_t launch_msys_batched(cudaStream_t st, const Ctrl* ctrl, int force, in
   }
   k_msys_batched<T><<<(unsigned)(nslots * tau), 512, smem, st>>>(ctrl, force, nslots, plan, rows, m,
                                                                   tau, nperm, staged, M, m_slot);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// S^T A and M = S^T A S of the bucket-row sketches in one pass: a block owns kJB
+// buckets j of one slot; it stages the slot's plan, forms the rows SA_s[j, :] (sum
+// over bucket j of sign * A[row, :], rows in bucket order) in shared memory, writes
+// them out, and then M_s[j, l] = sum over bucket l of sign * SA_s[j, row] from
+// shared memory, so S^T A is not read back.
+// ---------------------------------------------------------------------------
+constexpr int kJB = 2;  // buckets per block
+
+template <typename T>
+size_t sa_msys_smem(int64_t m, int64_t tau, int64_t nperm) {
+  return ((size_t)(nperm + tau + 1) * 4 + 15) / 16 * 16 + (size_t)kJB * round_up(m, 4) * sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sa_msys(const Ctrl* __restrict__ ctrl, int force, int nslots,
+                                                 PlanView plan, const T* __restrict__ A, int64_t lda,
+                                                 int64_t m, int64_t tau, int64_t nperm,
+                                                 T* __restrict__ SA, int64_t ldsa, int64_t sa_slot,
+                                                 int64_t bq, double* __restrict__ M, int64_t m_slot) {
+  using V = typename Vec<T>::type;
+  constexpr int VN = Vec<T>::n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t nact = active_slots(ctrl, force, nslots);
+  const int64_t nj = (tau + kJB - 1) / kJB;
+  const int64_t s = blockIdx.x / nj;
+  const int64_t jb = (blockIdx.x - s * nj) * kJB;
+  if (s >= nact) return;
+  const int tid = threadIdx.x;
+  int32_t* sperm = reinterpret_cast<int32_t*>(smem_raw);
+  int32_t* sboff = sperm + nperm;
+  const int64_t mr = round_up(m, 4);
+  T* srow = reinterpret_cast<T*>(smem_raw + ((size_t)(nperm + tau + 1) * 4 + 15) / 16 * 16);
+  const int32_t* perm = plan.perm + s * plan.perm_stride;
+  const int32_t* boff = plan.boff + s * plan.boff_stride;
+  for (int64_t t = tid; t < nperm; t += blockDim.x) sperm[t] = perm[t];
+  for (int64_t t = tid; t <= tau; t += blockDim.x) sboff[t] = boff[t];
+  __syncthreads();
+  const int nrow = (int)(jb + kJB <= tau ? kJB : tau - jb);
+  T* SAs = SA + s * sa_slot;
+  // rows SA[j, :], j = jb .. jb + nrow - 1: each thread kVU vectors of VN columns at
+  // once (kVU x 2 row loads in flight), rows summed in bucket order
+  const int64_t nvec = (m + VN - 1) / VN;
+  constexpr int kVU = 4;
+  for (int r = 0; r < nrow; ++r) {
+    const int64_t j = jb + r;
+    const int32_t t0 = sboff[j], t1 = sboff[j + 1];
+    for (int64_t v0 = tid; v0 < nvec; v0 += (int64_t)blockDim.x * kVU) {
+      V acc[kVU];
+#pragma unroll
+      for (int u = 0; u < kVU; ++u) {
+        if constexpr (VN == 4) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f); else acc[u] = make_double2(0.0, 0.0);
+      }
+      int32_t t = t0;
+      for (; t + 2 <= t1; t += 2) {
+        const int32_t ea = sperm[t], eb = sperm[t + 1];
+        const T* ra = A + (int64_t)entry_row(ea) * lda;
+        const T* rb = A + (int64_t)entry_row(eb) * lda;
+        V va[kVU], vb[kVU];
+#pragma unroll
+        for (int u = 0; u < kVU; ++u) {
+          const int64_t v = v0 + (int64_t)u * blockDim.x;
+          if (v < nvec) {
+            va[u] = __ldg(reinterpret_cast<const V*>(ra + v * VN));
+            vb[u] = __ldg(reinterpret_cast<const V*>(rb + v * VN));
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kVU; ++u) {
+          if (v0 + (int64_t)u * blockDim.x < nvec) {
+            vadd(acc[u], va[u], entry_neg(ea));
+            vadd(acc[u], vb[u], entry_neg(eb));
+          }
+        }
+      }
+      if (t < t1) {
+        const int32_t e = sperm[t];
+        const T* ra = A + (int64_t)entry_row(e) * lda;
+#pragma unroll
+        for (int u = 0; u < kVU; ++u) {
+          const int64_t v = v0 + (int64_t)u * blockDim.x;
+          if (v < nvec) vadd(acc[u], __ldg(reinterpret_cast<const V*>(ra + v * VN)), entry_neg(e));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kVU; ++u) {
+        const int64_t v = v0 + (int64_t)u * blockDim.x;
+        if (v >= nvec) continue;
+        const int64_t c = v * VN;
+        *reinterpret_cast<V*>(srow + r * mr + c) = acc[u];
+        if (bq == 0 ? c < ldsa : c < m)
+          *reinterpret_cast<V*>(SAs + sa_off(j, c, ldsa, bq, tau)) = acc[u];
+      }
+    }
+  }
+  __syncthreads();
+  // M[j, l] for the block's rows, bucket l traversed once for all of them
+  double* Ms = M + s * m_slot;
+  for (int64_t l = tid; l < tau; l += blockDim.x) {
+    T acc[kJB];
+#pragma unroll
+    for (int r = 0; r < kJB; ++r) acc[r] = T(0);
+    const int32_t t1 = sboff[l + 1];
+    for (int32_t t = sboff[l]; t < t1; ++t) {
+      const int32_t e = sperm[t];
+      const int64_t i = entry_row(e);
+      const bool ng = entry_neg(e);
+#pragma unroll
+      for (int r = 0; r < kJB; ++r) {
+        const T v = srow[r * mr + i];
+        acc[r] += ng ? -v : v;
+      }
+    }
+    for (int r = 0; r < nrow; ++r) Ms[(jb + r) * tau + l] = (double)acc[r];
+  }
+}
+
+// false when the block's buffers do not fit shared memory (two-kernel path)
+template <typename T>
+bool sa_msys_fits(int64_t m, int64_t tau, int64_t nperm) {
+  return sa_msys_smem<T>(m, tau, nperm) <= 200 * 1024;
+}
+
+template <typename T>
+cudaError_t launch_sa_msys(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, PlanView plan,
+                           const T* A, int64_t lda, int64_t m, int64_t tau, T* SA, int64_t ldsa,
+                           int64_t sa_slot, int64_t bq, double* M, int64_t m_slot) {
+  const int64_t nperm = plan.perm_stride;
+  const size_t smem = sa_msys_smem<T>(m, tau, nperm);
+  if (smem > 200 * 1024 || bq % 4 != 0) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_sa_msys<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t nj = (tau + kJB - 1) / kJB;
+  k_sa_msys<T><<<(unsigned)(nslots * nj), 256, smem, st>>>(ctrl, force, nslots, plan, A, lda, m, tau,
+                                                           nperm, SA, ldsa, sa_slot, bq, M, m_slot);
   return cudaGetLastError();
 }
 
@@ -263,9 +418,13 @@ cudaError_t launch_srht_system(cudaStream_t st, const Ctrl* ctrl, int force, int
 }
 
 #define RS_INST(T)                                                                                \
+  template bool sa_msys_fits<T>(int64_t, int64_t, int64_t);                                        \
+  template cudaError_t launch_sa_msys<T>(cudaStream_t, const Ctrl*, int, int, PlanView, const T*,  \
+                                         int64_t, int64_t, int64_t, T*, int64_t, int64_t, int64_t, \
+                                         double*, int64_t);                                        \
   template cudaError_t launch_sa_batched<T>(cudaStream_t, const Ctrl*, int, int, PlanView,         \
                                             const T*, int64_t, int64_t, int64_t, T*, int64_t,      \
-                                            int64_t);                                              \
+                                            int64_t, int64_t);                                     \
   template cudaError_t launch_msys_batched<T>(cudaStream_t, const Ctrl*, int, int, PlanView,       \
                                               RowsView<T>, int64_t, int64_t, double*, int64_t);    \
   template cudaError_t launch_gauss_system<T>(cudaStream_t, const Ctrl*, int, int, const T*,       \

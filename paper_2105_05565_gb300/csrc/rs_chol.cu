@@ -16,6 +16,7 @@
 // iteration sits in phase 1, off the sequential chain of iterations.
 #include <cooperative_groups.h>
 
+#include "rs_gemm.cuh"
 #include "rs_kernels.cuh"
 
 namespace rs {
@@ -478,7 +479,253 @@ cudaError_t launch_delta(cudaStream_t st, const Ctrl* ctrl, int force, int64_t k
   return cudaLaunchKernelEx(&cfg, kern, ctrl, force, k_arg, g);
 }
 
+// ---------------------------------------------------------------------------
+// M^+ in FP32 by symmetric sweeps (Gauss-Jordan elimination without pivoting on a
+// symmetric matrix, Goodnight 1979): sweeping index p maps
+//   a_pp -> -1 / a_pp,  a_ip -> a_ip / a_pp,  a_il -> a_il - a_ip a_pl / a_pp  (i, l != p)
+// and sweeping every index turns M into -M^{-1}. The pivot a_pp at the moment of
+// its sweep is the Schur complement pivot of the Cholesky factorisation, so the drop
+// rule is the factor's: a pivot at most tau * eps * max_i M_ii is not swept and its
+// row and column are zeroed at the end, which gives the inverse of the kept
+// principal submatrix, padded with zeros (the same least-norm reading as the
+// factor kernel).
+//
+// Eight indices P are swept at once (a block sweep): with X = A[:, P] and
+// Z = A_PP^+ (the 8 x 8 sweep of the diagonal block, drop rule included),
+//   A_RR -> A_RR - X_R Z X_R^T,  A_RP -> X_R Z,  A_PP -> -Z,
+// i.e. with Y = X Z one rank-8 update A_IJ -= X_I Y_J^T of every other block.
+// The sweep runs on the unit-diagonal matrix M' = D^{-1/2} M D^{-1/2} (D = diag M),
+// and M^+ = D^{-1/2} M'^+ D^{-1/2}.
+//
+// One CTA per slot; the lower triangle of 8 x 8 blocks lives in registers, one block
+// per thread (tau = 256: 528 blocks, 17 warps; 96 registers keep 5 warps of one
+// scheduler within its register file; all register indexing is static). The owner
+// of the next diagonal block sweeps it (8 x 8, in registers) as soon as its last
+// update is done, overlapping the other blocks' updates; X, Z and Y go through
+// shared memory; two barriers per block of eight indices.
+// ---------------------------------------------------------------------------
+constexpr int kSwB = 8;         // register block edge = indices swept at once
+constexpr int kSwMaxTau = 256;
+
+__host__ __device__ inline int sweep_threads(int64_t tau) {
+  const int nb = (int)((tau + kSwB - 1) / kSwB);
+  return (nb * (nb + 1) / 2 + 31) / 32 * 32;
+}
+
+// Sweep of a diagonal 8 x 8 block held in registers (both triangles) by its owner
+// thread, with the drop rule (pivot <= thrs[p], the threshold in the scaled matrix):
+// a becomes -Z on the kept indices (0 on dropped rows and columns); Z goes to Zo.
+__device__ __forceinline__ void diag_sweep(float (&a)[kSwB][kSwB], int Pb, const float* thrs,
+                                           unsigned char* dropped, float (*Zo)[kSwB + 1]) {
+  unsigned dmask = 0;
+#pragma unroll
+  for (int kk = 0; kk < kSwB; ++kk) {
+    const int p = Pb * kSwB + kk;
+    const float d = a[kk][kk];
+    if (dropped[p] || !(d > thrs[p])) {
+      dmask |= 1u << kk;
+      continue;
+    }
+    const float id = __frcp_rn(d);
+#pragma unroll
+    for (int r = 0; r < kSwB; ++r)
+#pragma unroll
+      for (int c = 0; c < kSwB; ++c)
+        if (r != kk && c != kk) a[r][c] = fmaf(-a[r][kk] * id, a[kk][c], a[r][c]);
+#pragma unroll
+    for (int c = 0; c < kSwB; ++c)
+      if (c != kk) {
+        a[kk][c] *= id;
+        a[c][kk] *= id;
+      }
+    a[kk][kk] = -id;
+  }
+#pragma unroll
+  for (int r = 0; r < kSwB; ++r)
+#pragma unroll
+    for (int c = 0; c < kSwB; ++c) {
+      const bool keep = !((dmask >> r) & 1u) && !((dmask >> c) & 1u);
+      a[r][c] = keep ? a[r][c] : 0.f;
+      Zo[r][c] = -a[r][c];
+    }
+#pragma unroll
+  for (int kk = 0; kk < kSwB; ++kk)
+    if ((dmask >> kk) & 1u) dropped[Pb * kSwB + kk] = 1;
+}
+
+__global__ void __maxnreg__(96) k_sweep_inv(const Ctrl* __restrict__ ctrl, int force, int nslots,
+                                            const double* __restrict__ M, int64_t m_slot, int tau,
+                                            float* __restrict__ P, int64_t pld, int64_t p_slot,
+                                            int32_t* __restrict__ ndropped) {
+  const int64_t slot = blockIdx.x;
+  if (slot >= active_slots(ctrl, force, nslots)) return;
+  // X = A[:, P] and Y = X Z column by column, rows padded to 9 per block of 8 so
+  // that lanes reading different blocks hit different banks: X[i][kk] at
+  // Xs[kk][(i / 8) * 9 + i % 8]
+  constexpr int kRow9 = kSwMaxTau / kSwB * (kSwB + 1);
+  __shared__ float Xs[2][kSwB][kRow9];      // by panel parity
+  __shared__ float Ys[kSwB][kRow9];
+  __shared__ float Zs[2][kSwB][kSwB + 1];   // Z of the panel, by panel parity
+  __shared__ float thrs[kSwMaxTau];         // pivot threshold in the scaled matrix
+  __shared__ double dg[kSwMaxTau];          // M_ii
+  __shared__ float sc[kSwMaxTau];           // M_ii^{-1/2}, 0 for an index dropped at the start
+  __shared__ unsigned char dropped[kSwMaxTau];
+  __shared__ double s_red[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nb = (tau + kSwB - 1) / kSwB;
+  const int tp = nb * kSwB;
+  const int nblocks = nb * (nb + 1) / 2;
+  const bool own = tid < nblocks;
+  int I = 0;
+  while ((I + 1) * (I + 2) / 2 <= tid) ++I;
+  const int J = tid - I * (I + 1) / 2;  // block (I, J), I >= J
+  const double* Ms = M + slot * m_slot;
+  double dmax = 0.0;
+  for (int i = tid; i < tau; i += blockDim.x) {
+    const double d = Ms[(int64_t)i * tau + i];
+    dg[i] = d;
+    dmax = fmax(dmax, d);
+  }
+  {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if (lane == 0) s_red[wid] = dmax;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t = fmax(t, s_red[w]);
+      s_red[0] = t;
+    }
+    __syncthreads();
+  }
+  const double thr = (double)tau * 1.1920928955078125e-07 * s_red[0];
+  for (int i = tid; i < tp; i += blockDim.x) {
+    const bool dr = (i >= tau) || !(dg[i] > thr);  // padding counts as dropped
+    dropped[i] = dr;
+    sc[i] = dr ? 0.f : (float)(1.0 / sqrt(dg[i]));
+    thrs[i] = dr ? 0.f : (float)(thr / dg[i]);
+  }
+  __syncthreads();
+  float a[kSwB][kSwB];
+#pragma unroll
+  for (int r = 0; r < kSwB; ++r) {
+#pragma unroll
+    for (int c = 0; c < kSwB; ++c) {
+      const int i = I * kSwB + r, l = J * kSwB + c;
+      float x = 0.f;
+      if (own && i < tau && l < tau)
+        x = (float)(Ms[(int64_t)i * tau + l] * (double)sc[i] * (double)sc[l]);
+      a[r][c] = x;
+    }
+    asm volatile("" ::: "memory");  // one row of loads in flight: keeps registers for a
+  }
+  if (own && I == 0 && J == 0) diag_sweep(a, 0, thrs, dropped, Zs[0]);
+
+  for (int Pb = 0; Pb < nb; ++Pb) {
+    float(*X)[kRow9] = Xs[Pb & 1];
+    // X = column block Pb (blocks (I > Pb, Pb) and, transposed, (Pb, J < Pb)); Z of
+    // the panel is in Zs already (swept by the owner of the diagonal block)
+    if (own) {
+      if (J == Pb && I > Pb) {
+#pragma unroll
+        for (int r = 0; r < kSwB; ++r)
+#pragma unroll
+          for (int c = 0; c < kSwB; ++c) X[c][I * (kSwB + 1) + r] = a[r][c];
+      } else if (I == Pb && J < Pb) {
+#pragma unroll
+        for (int r = 0; r < kSwB; ++r)
+#pragma unroll
+          for (int c = 0; c < kSwB; ++c) X[r][J * (kSwB + 1) + c] = a[r][c];
+      }
+    }
+    __syncthreads();
+    // Y = X Z, one entry per thread and step
+    for (int e = tid; e < tp * kSwB; e += blockDim.x) {
+      const int c = e / tp, t = e - c * tp;
+      const int t9 = (t >> 3) * (kSwB + 1) + (t & 7);
+      float y = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < kSwB; ++kk) y = fmaf(X[kk][t9], Zs[Pb & 1][kk][c], y);
+      Ys[c][t9] = y;
+    }
+    __syncthreads();
+    // A_IJ -= X_I Y_J^T; A_IP = Y_I, A_PJ = Y_J^T, A_PP = -Z
+    if (own) {
+      if (I == Pb && J == Pb) {
+        // already -Z: swept by this thread after the previous panel's update
+      } else if (J == Pb) {
+#pragma unroll
+        for (int r = 0; r < kSwB; ++r)
+#pragma unroll
+          for (int c = 0; c < kSwB; ++c) a[r][c] = Ys[c][I * (kSwB + 1) + r];
+      } else if (I == Pb) {
+#pragma unroll
+        for (int r = 0; r < kSwB; ++r)
+#pragma unroll
+          for (int c = 0; c < kSwB; ++c) a[r][c] = Ys[r][J * (kSwB + 1) + c];
+      } else {
+#pragma unroll 1
+        for (int kk = 0; kk < kSwB; ++kk) {  // rolled: one rank-1 step of loads live
+          float y[kSwB];
+#pragma unroll
+          for (int c = 0; c < kSwB; ++c) y[c] = Ys[kk][J * (kSwB + 1) + c];
+#pragma unroll
+          for (int r = 0; r < kSwB; ++r) {
+            const float x = X[kk][I * (kSwB + 1) + r];
+#pragma unroll
+            for (int c = 0; c < kSwB; ++c) a[r][c] = fmaf(-x, y[c], a[r][c]);
+          }
+        }
+        // the next panel's diagonal block is final now: sweep it while the other
+        // blocks are still being updated
+        if (I == Pb + 1 && J == Pb + 1) diag_sweep(a, Pb + 1, thrs, dropped, Zs[(Pb + 1) & 1]);
+      }
+    }
+  }
+  __syncthreads();
+  // P = -D^{-1/2} (swept M') D^{-1/2} on the kept indices, both triangles
+  if (own) {
+    float* Ps = P + slot * p_slot;
+#pragma unroll
+    for (int r = 0; r < kSwB; ++r)
+#pragma unroll
+      for (int c = 0; c < kSwB; ++c) {
+        const int i = I * kSwB + r, l = J * kSwB + c;
+        if (i < tau && l < tau && (I != J || c <= r)) {
+          const float x = (dropped[i] || dropped[l]) ? 0.f : -a[r][c] * sc[i] * sc[l];
+          Ps[(int64_t)i * pld + l] = x;
+          Ps[(int64_t)l * pld + i] = x;
+        }
+      }
+  }
+  if (tid == 0 && ndropped != nullptr) {
+    int cnt = 0;
+    for (int i = 0; i < tau; ++i) cnt += dropped[i];
+    if (cnt) atomicAdd(ndropped, cnt);
+  }
+}
+
+cudaError_t launch_sweep_inv(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
+                             const double* M, int64_t m_slot, int64_t tau, float* P, int64_t pld,
+                             int64_t p_slot, int32_t* ndropped) {
+  if (tau < 1 || tau > kSwMaxTau) return cudaErrorInvalidValue;
+  k_sweep_inv<<<nslots, sweep_threads(tau), 0, st>>>(ctrl, force, nslots, M, m_slot, (int)tau, P,
+                                                     pld, p_slot, ndropped);
+  return cudaGetLastError();
+}
+
+// P_s = L_s^{-T} L_s^{-1}: P(i, j) = sum_k Linv[k, i] Linv[k, j], every slot in one launch
+template <typename TF>
+cudaError_t launch_pinv(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, const TF* Linv,
+                        int64_t l_slot, int64_t tau, TF* P, int64_t pld, int64_t p_slot) {
+  return gemm_strided<TF, TF, TF>(st, tau, tau, tau, Linv, 1, tau, Linv, tau, 1, P, pld, 0.0, 0,
+                                  force ? nullptr : ctrl, nslots, l_slot, l_slot, p_slot);
+}
+
 #define RS_INST(T)                                                                             \
+  template cudaError_t launch_pinv<T>(cudaStream_t, const Ctrl*, int, int, const T*, int64_t,  \
+                                      int64_t, T*, int64_t, int64_t);                          \
   template cudaError_t launch_factor_inv<T>(cudaStream_t, const Ctrl*, int, int, const double*, \
                                             int64_t, int64_t, T*, int64_t, T*, int32_t*);       \
   template cudaError_t launch_delta<T>(cudaStream_t, const Ctrl*, int, int64_t, DeltaArgs<T>);

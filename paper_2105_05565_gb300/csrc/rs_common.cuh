@@ -38,6 +38,10 @@ __host__ __device__ __forceinline__ int32_t pack_entry(int32_t row, bool neg) {
 __host__ __device__ __forceinline__ int32_t entry_row(int32_t e) { return e & 0x7FFFFFFF; }
 __host__ __device__ __forceinline__ bool entry_neg(int32_t e) { return e < 0; }
 
+// inverse map of a sketch plan: inv[i] = bucket | sign bit for rows in the sketch,
+// kNotSketched otherwise
+constexpr int32_t kNotSketched = 0x7FFFFFFF;
+
 // ---------------------------------------------------------------------------
 // Device control block of one context: iteration counter, stop flags, norms.
 // ---------------------------------------------------------------------------
@@ -109,7 +113,7 @@ __device__ void fwht_smem(T* buf, int64_t n) {
   __syncthreads();
 }
 
-inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+__host__ __device__ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline int ceil_div(int64_t x, int64_t a) { return (int)((x + a - 1) / a); }
 
 }  // namespace rs

@@ -34,9 +34,6 @@ __device__ __forceinline__ void vfma(double (&acc)[2], const double2& v, double 
   acc[0] += v.x * d; acc[1] += v.y * d;
 }
 
-// inverse map of the sketch plan per slot: inv[i] = bucket | sign bit for rows in the
-// sketch, kNotSketched otherwise
-constexpr int32_t kNotSketched = 0x7FFFFFFF;
 
 __global__ void k_inv_reset(const Ctrl* __restrict__ ctrl, int force, int nslots, int64_t m,
                             int32_t* __restrict__ inv, int64_t inv_slot) {

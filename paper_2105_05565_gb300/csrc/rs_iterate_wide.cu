@@ -1,0 +1,721 @@
+// Phase 2 of a chunk on the whole GPU: every iteration of Algorithm 2 (Section 6.3,
+// update of eq. (53)) of the chunk runs inside one launch of nblk CTAs (clusters of
+// kWideCluster), for the bucket-row sketches (subsample, count, subcount).
+//
+// CTA c owns the rows [c q, (c + 1) q) of w, w_prev, r, r_prev and keeps them in
+// shared memory for the whole launch. With P_k = M_k^+ formed in phase 1 and the
+// sketch written as S_k = sum_i sigma_i e_i e_{b_i}^T,
+//   delta_k = P_k S_k^T r_k = sum_c sum_{i in c, sketched} sigma_i r_i P_k[b_i, :],
+// so every CTA contributes a partial of delta_k from its own rows alone. One
+// all-reduce per iteration (tau partial entries plus the partial ||r_k||^2) gives
+// every CTA the same delta_k and ||r_k||; each then updates its own rows:
+//   (A S_k delta_k)_i = sum_j (S_k^T A)[j, i] delta_j   from its block of S_k^T A,
+//   (S_k delta_k)_i   = sigma_i delta_{b_i},
+//   w_i, r_i          by the momentum step (1 + beta) x - beta x_prev - gamma (...).
+// Phase 1 writes S_k^T A blocked by CTA (the tau x q block of CTA c is contiguous),
+// so one bulk copy per iteration stages it in shared memory; the rows P_k[b_i, :]
+// and the slot's inverse map are bulk-copied too, all one or two iterations ahead
+// and issued after the CTA has published its partials, so that they overlap the
+// all-reduce.
+//
+// All-reduce, deterministic: (1) each CTA stores its tau + 1 partials to global
+// memory and publishes a flag with release semantics; (2) CTA rank r of a cluster
+// waits for every flag (acquire) and sums the entries [r E, (r + 1) E) over all
+// CTAs in a fixed order; (3) it stores those sums into the shared memory of every
+// CTA of its cluster with st.async, whose bytes complete on the destination's
+// mbarrier. Every wait is bounded (global timer); a CTA that gives up raises the
+// abort word, which ends the others' waits.
+#include "rs_kernels.cuh"
+#include "rs_ptx.cuh"
+
+namespace rs {
+
+namespace {
+
+constexpr int kWThreads = 256;
+constexpr int kWWarps = kWThreads / 32;
+constexpr int kIssueWarp = kWWarps - 1;        // issues the bulk copies
+constexpr int kSumLoads = 20;                   // partials in flight per thread
+constexpr int kRowsPerLane = 2;                 // rows of a lane in the A S delta product
+constexpr uint64_t kWaitNs = 2000000000ull;     // 2 s bound of every wait
+
+struct WideLayout {
+  int64_t qs, E, G;
+  size_t sa, pb, iv, mine, tot, dT, red, st, coef, prow, pinv, hn2, bars, gb, total;
+};
+
+__host__ __device__ inline size_t wl_take(size_t& o, size_t bytes) {
+  const size_t at = o;
+  o += (bytes + 127) / 128 * 128;
+  return at;
+}
+
+// shared-memory layout of one CTA (host and device agree on it)
+__host__ __device__ inline WideLayout wide_layout(int64_t q, int64_t tau, int64_t pld, int se,
+                                                  int sf, int64_t chunk, int nsab) {
+  WideLayout L;
+  L.qs = (q + 3) / 4 * 4;
+  L.E = (tau + 1 + kWideCluster - 1) / kWideCluster;  // all-reduce entries per cluster rank
+  L.G = kWThreads / L.E > 0 ? kWThreads / L.E : 1;     // thread groups of the sums
+  size_t o = 0;
+  L.sa = wl_take(o, (size_t)nsab * tau * L.qs * se);  // S^T A block, 1 or 2 buffers
+  L.pb = wl_take(o, (size_t)L.qs * pld * sf);       // rows of P for the own rows
+  L.iv = wl_take(o, (size_t)3 * L.qs * 4);          // inverse map slices, 3 slots
+  L.mine = wl_take(o, (size_t)tau * 8);             // own partials of delta
+  L.tot = wl_take(o, (size_t)(tau + 1) * 8);        // all-reduced totals
+  L.dT = wl_take(o, (size_t)tau * se);              // delta in the product type
+  const int64_t rw = kWWarps * L.qs > L.G * L.E ? kWWarps * L.qs : L.G * L.E;
+  L.red = wl_take(o, (size_t)rw * 8);               // cross-warp / cross-group partial sums
+  L.st = wl_take(o, (size_t)4 * L.qs * 8);          // r, r_prev, w, w_prev
+  L.coef = wl_take(o, (size_t)L.qs * 8);            // sigma_i r_i of the staged rows
+  L.prow = wl_take(o, (size_t)L.qs * 4);            // staged row -> own row | sign
+  L.pinv = wl_take(o, (size_t)L.qs * 4);            // own row -> staged row, or -1
+  L.hn2 = wl_take(o, (size_t)(chunk + 1) * 8);      // ||r_k||^2 of the tested iterations
+  L.bars = wl_take(o, 8 * 8);                       // mbarriers
+  L.gb = wl_take(o, (size_t)2 * chunk * 8);         // gamma_k, beta_k of the chunk
+  L.total = o;
+  return L;
+}
+
+// bounded wait on an mbarrier phase; false on timeout or (abort_word != nullptr)
+// when another CTA has raised the abort word
+__device__ bool wait_bar(uint64_t* bar, uint32_t parity, const int32_t* abort_word) {
+  if (ptx::mbar_test(bar, parity)) return true;
+  const uint64_t t0 = ptx::now_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (ptx::mbar_test(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (abort_word != nullptr && ptx::ld_relaxed_s32(abort_word) != 0) return false;
+      if (ptx::now_ns() - t0 > kWaitNs) return false;
+    }
+  }
+}
+
+struct Xch {
+  uint64_t* part;   // 2 (parity) x nblk x nw words
+  int32_t* abort_word;
+  int nblk, cta;
+  uint32_t crank;
+  int64_t tau, ne, E, G, nw;
+  void* mine;       // PT[tau]: own partials of delta
+  double* mine_nrm; // own partial of ||r||^2
+  double* tot;      // ne all-reduced totals (delta, then ||r||^2)
+  void* red;        // per-group sums of the reducer
+  uint64_t* xbar;
+};
+
+// The partials travel as self-validating words: a 32-bit payload and the exchange's
+// 32-bit tag in one 8-byte word (single-copy atomic), so a reader that sees the tag
+// has the payload and no separate flag, fence or release is needed. Tags increase
+// from exchange to exchange and from launch to launch and the buffer alternates by
+// parity, so a stale word never carries the current tag. Payloads: PT = float,
+// one word per delta entry and the norm as a float pair (hi, lo); PT = double, two
+// words (low and high halves) per entry.
+__device__ __forceinline__ uint64_t ll_word(uint32_t payload, uint32_t tag) {
+  return (uint64_t)payload | ((uint64_t)tag << 32);
+}
+template <typename PT>
+__host__ __device__ constexpr int64_t ll_words(int64_t tau) {
+  return sizeof(PT) == 4 ? tau + 2 : 2 * tau + 2;
+}
+
+// error-free sum of two floats (Knuth): s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float t = s - a;
+  e = (a - (s - t)) + (b - t);
+}
+
+// All-reduce of the partials over every CTA into `tot`, first half: arm the own
+// mbarrier for the ne * 8 bytes the cluster will store, then publish the partials.
+// `n` counts this launch's exchanges.
+template <typename PT>
+__device__ void xch_begin(const Xch& x, uint32_t tag, uint32_t n) {
+  const int tid = threadIdx.x;
+  uint64_t* pb = x.part + ((size_t)(n & 1) * x.nblk + x.cta) * x.nw;
+  __syncthreads();  // the partials written; `tot` of the previous exchange read
+  if (tid == 0) ptx::mbar_arrive_expect_tx(x.xbar, (uint32_t)(x.ne * 8));
+  const PT* mine = static_cast<const PT*>(x.mine);
+  if constexpr (sizeof(PT) == 4) {
+    for (int64_t e = tid; e < x.tau; e += kWThreads)
+      ptx::st_relaxed_u64(pb + e, ll_word(__float_as_uint(mine[e]), tag));
+    if (tid == 0) {
+      const double v = *x.mine_nrm;
+      const float hi = (float)v, lo = (float)(v - (double)hi);
+      ptx::st_relaxed_u64(pb + x.tau, ll_word(__float_as_uint(hi), tag));
+      ptx::st_relaxed_u64(pb + x.tau + 1, ll_word(__float_as_uint(lo), tag));
+    }
+  } else {
+    for (int64_t e = tid; e < x.ne; e += kWThreads) {
+      const uint64_t b = (uint64_t)__double_as_longlong(e < x.tau ? (double)mine[e] : *x.mine_nrm);
+      ptx::st_relaxed_u64(pb + 2 * e, ll_word((uint32_t)b, tag));
+      ptx::st_relaxed_u64(pb + 2 * e + 1, ll_word((uint32_t)(b >> 32), tag));
+    }
+  }
+}
+
+// word(s) of entry e in a CTA's block
+template <typename PT>
+__device__ __forceinline__ void ll_pos(int64_t e, int64_t tau, int64_t& w0, int& nwords) {
+  if constexpr (sizeof(PT) == 4) {
+    w0 = e;
+    nwords = (e < tau) ? 1 : 2;
+  } else {
+    w0 = 2 * e;
+    nwords = 2;
+  }
+}
+
+// second half: gather the own entries of every CTA (re-reading words whose tag is
+// not current yet), sum them in a fixed order (float pairs for PT = float, so the
+// sum is as accurate as in FP64 without FP64 arithmetic), scatter the sums to the
+// cluster and wait for the cluster's sums; false on abort or timeout
+template <typename PT>
+__device__ bool xch_end(const Xch& x, uint32_t tag, uint32_t n) {
+  constexpr bool F = sizeof(PT) == 4;
+  const int tid = threadIdx.x;
+  const uint64_t* pb = x.part + (size_t)(n & 1) * x.nblk * x.nw;
+  // own entries [e0, e1): thread (g, el) adds CTAs g, g + G, ... in that order,
+  // then the G group sums are added in group order (fixed order, deterministic)
+  const int64_t e0 = (int64_t)x.crank * x.E;
+  const int64_t e1 = (e0 + x.E < x.ne) ? e0 + x.E : x.ne;
+  int bad = 0;
+  for (int64_t idx = tid; idx < x.G * x.E; idx += kWThreads) {
+    const int64_t g = idx / x.E, el = idx - g * x.E, e = e0 + el;
+    float S = 0.f, C = 0.f;   // PT = float
+    double acc = 0.0;         // PT = double
+    if (e < e1) {
+      int64_t w0;
+      int nwd;
+      ll_pos<PT>(e, x.tau, w0, nwd);
+      for (int c0 = (int)g; c0 < x.nblk && !bad; c0 += (int)x.G * kSumLoads) {
+        uint64_t a[kSumLoads], b[kSumLoads];
+        // every pass re-reads, all at once, the words whose tag is not current yet;
+        // the first pass reads them all
+        uint32_t pend = 0;
+#pragma unroll
+        for (int u = 0; u < kSumLoads; ++u)
+          if (c0 + u * (int)x.G < x.nblk) pend |= 1u << u;
+        const uint64_t t0 = ptx::now_ns();
+        for (uint32_t pass = 0; pend != 0; ++pass) {
+#pragma unroll
+          for (int u = 0; u < kSumLoads; ++u) {
+            if (pend & (1u << u)) {
+              const uint64_t* w = pb + (size_t)(c0 + u * (int)x.G) * x.nw + w0;
+              a[u] = ptx::ld_relaxed_u64(w);
+              b[u] = nwd > 1 ? ptx::ld_relaxed_u64(w + 1) : ll_word(0u, tag);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kSumLoads; ++u)
+            if ((pend & (1u << u)) && (uint32_t)(a[u] >> 32) == tag && (uint32_t)(b[u] >> 32) == tag)
+              pend &= ~(1u << u);
+          if (pend != 0 && (pass & 15) == 15 &&
+              (ptx::ld_relaxed_s32(x.abort_word) != 0 || ptx::now_ns() - t0 > kWaitNs)) {
+            bad = 1;
+            break;
+          }
+        }
+        if (bad) break;
+#pragma unroll
+        for (int u = 0; u < kSumLoads; ++u) {
+          if (c0 + u * (int)x.G >= x.nblk) continue;
+          if constexpr (F) {
+            float t, err;
+            two_sum(S, __uint_as_float((uint32_t)a[u]), t, err);
+            S = t;
+            C += err + __uint_as_float((uint32_t)b[u]);  // lo of the norm, else 0
+          } else {
+            acc += __longlong_as_double((long long)((a[u] & 0xFFFFFFFFull) | (b[u] << 32)));
+          }
+        }
+      }
+    }
+    if constexpr (F) static_cast<float2*>(x.red)[idx] = make_float2(S, C);
+    else static_cast<double*>(x.red)[idx] = acc;
+  }
+  if (__syncthreads_or(bad)) {
+    if (tid == 0) atomicExch(x.abort_word, 1);
+    return false;
+  }
+  for (int64_t e = e0 + tid; e < e1; e += kWThreads) {
+    double v;
+    if constexpr (F) {
+      const float2* r = static_cast<const float2*>(x.red);
+      float S = 0.f, C = 0.f;
+      for (int64_t g = 0; g < x.G; ++g) {
+        const float2 p = r[g * x.E + (e - e0)];
+        float t, err;
+        two_sum(S, p.x, t, err);
+        S = t;
+        C += err + p.y;
+      }
+      v = (double)S + (double)C;
+    } else {
+      const double* r = static_cast<const double*>(x.red);
+      v = 0.0;
+      for (int64_t g = 0; g < x.G; ++g) v += r[g * x.E + (e - e0)];
+    }
+#pragma unroll
+    for (uint32_t rk = 0; rk < (uint32_t)kWideCluster; ++rk)
+      ptx::st_async_f64(ptx::map_rank(x.tot + e, rk), v, ptx::map_rank(x.xbar, rk));
+  }
+  const bool ok = wait_bar(x.xbar, n & 1, x.abort_word);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicExch(x.abort_word, 1);
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+template <typename T, typename TF>
+__global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict__ ctrl,
+                                                              WideArgs<T, TF> g) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  // ctrl is read once; no CTA writes it before every CTA has passed its first
+  // exchange, so all CTAs take the same branches
+  if (halted(ctrl)) return;
+  const int64_t k0 = ctrl->k0, kstart = ctrl->k;
+  const int64_t kend = min(k0 + g.chunk, ctrl->max_iters);
+  if (kstart >= kend) return;
+  const double tol = ctrl->tol, r0 = ctrl->r0;
+  const double thr2 = (tol * r0) * (tol * r0);
+  const double thr2_lo = thr2 * (1.0 - 1e-9), thr2_hi = thr2 * (1.0 + 1e-9);
+  const int no_stop = ctrl->no_stop;
+  const uint64_t tag0 = (*g.epoch) << 24;
+
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int cta = blockIdx.x;
+  uint32_t crank;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
+  const int64_t tau = g.tau, m = g.m;
+  const int nsab = g.nsab;
+  const WideLayout L =
+      wide_layout(g.q, tau, g.pld, (int)sizeof(T), (int)sizeof(TF), g.chunk, nsab);
+  const int64_t qs = L.qs;
+  const int64_t ilo = (int64_t)cta * g.q;
+  const int64_t qc = ilo < m ? (m - ilo < g.q ? m - ilo : g.q) : 0;  // own rows
+  const int64_t qcp = (qc + 3) / 4 * 4;                                // copied width
+  const bool has_rows = qc > 0;
+
+  T* sab = reinterpret_cast<T*>(smem + L.sa);
+  TF* pbuf = reinterpret_cast<TF*>(smem + L.pb);
+  int32_t* ivb = reinterpret_cast<int32_t*>(smem + L.iv);
+  TF* mine = reinterpret_cast<TF*>(smem + L.mine);
+  double* tot = reinterpret_cast<double*>(smem + L.tot);
+  T* dT = reinterpret_cast<T*>(smem + L.dT);
+  T* red = reinterpret_cast<T*>(smem + L.red);
+  TF* coef = reinterpret_cast<TF*>(smem + L.coef);
+  double* sr = reinterpret_cast<double*>(smem + L.st);
+  double* srp = sr + qs;
+  double* sw = srp + qs;
+  double* swp = sw + qs;
+  int32_t* prow = reinterpret_cast<int32_t*>(smem + L.prow);
+  int32_t* pinv = reinterpret_cast<int32_t*>(smem + L.pinv);
+  double* hn2 = reinterpret_cast<double*>(smem + L.hn2);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bars);
+  uint64_t* sa_full = bars;        // 2
+  uint64_t* iv_full = bars + 2;    // 3
+  uint64_t* p_full = bars + 5;     // 1
+  uint64_t* xbar = bars + 6;       // 1
+  double* sgam = reinterpret_cast<double*>(smem + L.gb);
+  double* sbet = sgam + g.chunk;
+  __shared__ int s_nrows;
+  __shared__ double s_red[32];
+  __shared__ double s_nrm;  // own partial of ||r||^2
+  __shared__ int s_dec;     // stopping decision of the current iteration
+
+  if (tid == 0) {
+    for (int b = 0; b < 7; ++b) ptx::mbar_init(bars + b, 1);
+    ptx::fence_mbar_init();
+  }
+  for (int64_t k = kstart + tid; k < kend; k += kWThreads) {
+    sgam[k - k0] = g.gam[k];
+    sbet[k - k0] = g.bet[k];
+  }
+  for (int64_t i = tid; i < qc; i += kWThreads) {
+    sr[i] = g.r[ilo + i];
+    srp[i] = g.rp[ilo + i];
+    sw[i] = g.w[ilo + i];
+    swp[i] = g.wp[ilo + i];
+  }
+  __syncthreads();
+  ptx::cluster_sync_all();  // peers' mbarriers are initialised before any remote store
+
+  Xch x;
+  x.part = g.part; x.abort_word = g.abort_word;
+  x.nblk = g.nblk; x.cta = cta; x.crank = crank;
+  x.tau = tau; x.ne = tau + 1; x.E = L.E; x.G = L.G; x.nw = ll_words<TF>(tau);
+  x.mine = mine; x.mine_nrm = &s_nrm; x.tot = tot; x.red = red; x.xbar = xbar;
+
+  // copy bookkeeping, identical in every thread: issued / consumed phases per buffer
+  uint32_t sa_iss[2] = {0, 0}, sa_use[2] = {0, 0};
+  uint32_t iv_iss[3] = {0, 0, 0}, iv_use[3] = {0, 0, 0};
+  uint32_t p_iss = 0, p_use = 0;
+  bool ok = true;
+
+  auto slot_of = [&](int64_t k) { return k - k0; };
+  // (issue warp) inverse-map slice of slot s
+  auto issue_iv = [&](int64_t s) {
+    const int b = (int)(s % 3);
+    if (wid == kIssueWarp && lane == 0) {
+      ptx::mbar_arrive_expect_tx(iv_full + b, (uint32_t)(qcp * 4));
+      ptx::bulk_g2s(ivb + b * qs, g.inv + s * g.inv_slot + ilo, (uint32_t)(qcp * 4), iv_full + b);
+    }
+    iv_iss[b]++;
+  };
+  // (every thread) the inverse map of slot s is in place
+  auto wait_iv = [&](int64_t s) -> bool {
+    const int b = (int)(s % 3);
+    const bool r = wait_bar(iv_full + b, iv_use[b] & 1, g.abort_word);
+    iv_use[b]++;
+    return !__syncthreads_or(!r);
+  };
+  // (issue warp) the CTA's tau x qs block of S^T A of slot s: one bulk copy
+  auto issue_sa = [&](int64_t s) {
+    const int b = (int)(s % nsab);
+    if (wid == kIssueWarp && lane == 0) {
+      const uint32_t bytes = (uint32_t)(tau * qs * sizeof(T));
+      ptx::mbar_arrive_expect_tx(sa_full + b, bytes);
+      ptx::bulk_g2s(sab + (size_t)b * tau * qs, g.rows + s * g.sa_slot + (int64_t)cta * tau * qs,
+                    bytes, sa_full + b);
+    }
+    sa_iss[b]++;
+  };
+  // (issue warp) rows P_s[b_i, :] for the sketched own rows; the inverse map of s
+  // must be in place (waited by the issue warp itself: `iv_ready`)
+  auto issue_p = [&](int64_t s, bool iv_ready) {
+    if (wid == kIssueWarp) {
+      const int bi = (int)(s % 3);
+      bool okw = iv_ready || wait_bar(iv_full + bi, iv_use[bi] & 1, g.abort_word);
+      if (!okw) {
+        if (lane == 0) atomicExch(g.abort_word, 1);
+      }
+      const int32_t* iv = ivb + bi * qs;
+      int nrows = 0;
+      for (int64_t i0 = 0; i0 < qc; i0 += 32) {
+        const int64_t i = i0 + lane;
+        const int32_t e = (okw && i < qc) ? iv[i] : kNotSketched;
+        const bool sk = (e != kNotSketched);
+        const unsigned bal = __ballot_sync(0xffffffffu, sk);
+        const int t = nrows + __popc(bal & ((1u << lane) - 1u));
+        if (sk) prow[t] = (int32_t)((uint32_t)i | ((uint32_t)e & 0x80000000u));
+        if (i < qc) pinv[i] = sk ? t : -1;
+        nrows += __popc(bal);
+      }
+      __syncwarp();
+      const uint32_t rb = (uint32_t)(g.pld * sizeof(TF));
+      if (lane == 0) {
+        s_nrows = nrows;
+        ptx::mbar_arrive_expect_tx(p_full, rb * (uint32_t)nrows);
+      }
+      __syncwarp();
+      const TF* Ps = g.P + s * g.p_slot;
+      for (int t = lane; t < nrows; t += 32) {
+        const int32_t e = iv[prow[t] & 0x7FFFFFFF];
+        ptx::bulk_g2s(pbuf + (size_t)t * g.pld, Ps + (int64_t)(e & 0x7FFFFFFF) * g.pld, rb, p_full);
+      }
+    }
+    p_iss++;
+  };
+  // own partials of delta_k (with_delta) and of ||r_k||^2: the squares are summed
+  // per warp into s_red by whoever last wrote the rows (the update, or `fresh`)
+  auto partial = [&](bool with_delta, bool fresh) -> bool {
+    const bool use_p = with_delta && has_rows;
+    if (fresh) {
+      double sq = 0.0;
+      for (int64_t i = tid; i < qc; i += kWThreads) sq += sr[i] * sr[i];
+      if (wid * 32 < qc) sq = warp_sum(sq);
+      if (lane == 0) s_red[wid] = sq;
+    }
+    if (use_p) {
+      const bool r = wait_bar(p_full, p_use & 1, g.abort_word);
+      p_use++;
+      if (__syncthreads_or(!r)) return false;
+    } else {
+      __syncthreads();
+    }
+    // sigma_i r_i of the staged rows, once each in the partial's precision (FP64
+    // arithmetic is scarce on this GPU: nothing of it in the loop below)
+    const int nrows = use_p ? s_nrows : 0;
+    if (fresh) {  // else the row update has written them
+      for (int t = tid; t < nrows; t += kWThreads) {
+        const int32_t pr = prow[t];
+        const double v = sr[pr & 0x7FFFFFFF];
+        coef[t] = (TF)(pr < 0 ? -v : v);
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      double t = 0.0;
+      if (has_rows)
+        for (int w = 0; w < kWWarps; ++w) t += s_red[w];
+      s_nrm = t;
+    }
+    for (int64_t j = tid; j < tau; j += kWThreads) {
+      TF acc = TF(0);
+#pragma unroll 4
+      for (int t = 0; t < nrows; ++t) acc += coef[t] * pbuf[(size_t)t * g.pld + j];
+      mine[j] = acc;
+    }
+    return true;
+  };
+
+  int64_t k = kstart;
+  uint32_t nx = 0;   // exchanges so far
+  int outcome = 0;   // 0 chunk done, 1 converged, 2 numeric failure, 3 timed out
+  if (has_rows) {
+    const int64_t s0 = slot_of(k);
+    issue_iv(s0);
+    if (k + 1 < kend) issue_iv(s0 + 1);
+    issue_sa(s0);
+    ok = wait_iv(s0);
+    if (ok) issue_p(s0, true);
+  }
+  if (ok) ok = partial(true, true);
+  while (ok) {
+    const uint32_t tag = (uint32_t)(tag0 + nx + 1);
+    xch_begin<TF>(x, tag, nx);
+    // prefetch, after the partials are out: S^T A and P rows of the next slot,
+    // the inverse map of the one after
+    if (has_rows && k + 1 < kend) {
+      const int64_t s1 = slot_of(k + 1);
+      if (nsab == 2) issue_sa(s1);  // one buffer: issued once iteration k has read it
+      issue_p(s1, false);
+      if (k + 2 < kend) issue_iv(s1 + 1);
+    }
+    ok = xch_end<TF>(x, tag, nx);
+    ++nx;
+    if (!ok) break;
+    // stopping test on ||r_k|| (k = kstart was tested before this launch), taken by
+    // one thread (the FP64 square root and division are slow here) and broadcast
+    if (tid == 0) {
+      int dec = 0;
+      if (k > kstart) {
+        const double n2 = tot[tau];
+        hn2[k - k0] = n2;
+        if (!isfinite(n2)) {
+          dec = 2;
+        } else if (!no_stop) {
+          // rel = sqrt(n2) / r0 <= tol, decided on n2 away from the boundary
+          if (n2 <= thr2_lo) dec = 1;
+          else if (n2 <= thr2_hi) dec = (sqrt(n2) / r0 <= tol) ? 1 : 0;
+        }
+      }
+      s_dec = dec;
+    }
+    if (k >= kend) {
+      __syncthreads();
+      outcome = s_dec;
+      break;
+    }
+    // iteration k on the own rows
+    const int64_t s = slot_of(k);
+    for (int64_t j = tid; j < tau; j += kWThreads) dT[j] = (T)tot[j];
+    const int b = (int)(s % nsab);
+    bool r = true;
+    if (has_rows) {
+      r = (k == kstart) || wait_bar(iv_full + (s % 3), iv_use[s % 3] & 1, g.abort_word);
+      if (k > kstart) iv_use[s % 3]++;
+      r = r && wait_bar(sa_full + b, sa_use[b] & 1, g.abort_word);
+      sa_use[b]++;
+    }
+    if (__syncthreads_or(!r)) { ok = false; break; }
+    if (s_dec != 0) { outcome = s_dec; break; }
+    if (has_rows) {
+      // (A S delta)_i: warp w takes the columns [w jc, (w + 1) jc), lane the rows
+      // lane + 32 u, kRowsPerLane at a time
+      const T* sb = sab + (size_t)b * tau * qs;
+      const int64_t jc = (tau + kWWarps - 1) / kWWarps;
+      const int64_t j0 = wid * jc, j1 = (j0 + jc < tau) ? j0 + jc : tau;
+      for (int64_t i0 = 0; i0 < qc; i0 += 32 * kRowsPerLane) {
+        T acc[kRowsPerLane][4];  // 4 independent chains over j
+#pragma unroll
+        for (int u = 0; u < kRowsPerLane; ++u)
+#pragma unroll
+          for (int q4 = 0; q4 < 4; ++q4) acc[u][q4] = T(0);
+        int64_t j = j0;
+        for (; j + 4 <= j1; j += 4) {
+#pragma unroll
+          for (int q4 = 0; q4 < 4; ++q4) {
+            const T d = dT[j + q4];
+#pragma unroll
+            for (int u = 0; u < kRowsPerLane; ++u) {
+              const int64_t i = i0 + lane + 32 * u;
+              if (i < qs) acc[u][q4] += sb[(j + q4) * qs + i] * d;
+            }
+          }
+        }
+        for (; j < j1; ++j) {
+          const T d = dT[j];
+#pragma unroll
+          for (int u = 0; u < kRowsPerLane; ++u) {
+            const int64_t i = i0 + lane + 32 * u;
+            if (i < qs) acc[u][0] += sb[j * qs + i] * d;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kRowsPerLane; ++u) {
+          const int64_t i = i0 + lane + 32 * u;
+          if (i < qs) red[wid * qs + i] = (acc[u][0] + acc[u][1]) + (acc[u][2] + acc[u][3]);
+        }
+      }
+      __syncthreads();
+      if (nsab == 1 && k + 1 < kend) issue_sa(s + 1);
+      const double gk = sgam[k - k0], bk = sbet[k - k0];
+      const int32_t* iv = ivb + (s % 3) * qs;
+      double sq = 0.0;
+      for (int64_t i = tid; i < qc; i += kWThreads) {
+        T asum = T(0);
+#pragma unroll
+        for (int w = 0; w < kWWarps; ++w) asum += red[w * qs + i];
+        const double asd = (double)asum;
+        const int32_t e = iv[i];
+        const double ui = (e == kNotSketched) ? 0.0
+                          : (entry_neg(e) ? -tot[e & 0x7FFFFFFF] : tot[e & 0x7FFFFFFF]);
+        const double ri = sr[i], rpi = srp[i], wi = sw[i], wpi = swp[i];
+        const double rn = (1.0 + bk) * ri - bk * rpi - gk * asd;
+        sr[i] = rn;
+        const int32_t t = pinv[i];  // staged row of slot k + 1
+        if (t >= 0) coef[t] = (TF)(prow[t] < 0 ? -rn : rn);
+        srp[i] = ri;
+        sw[i] = (1.0 + bk) * wi - bk * wpi - gk * ui;
+        swp[i] = wi;
+        sq += rn * rn;
+      }
+      if (wid * 32 < qc) sq = warp_sum(sq);
+      if (lane == 0) s_red[wid] = sq;
+    }
+    if (cta == 0 && k + 1 == kend)
+      for (int64_t j = tid; j < tau; j += kWThreads) g.delta_out[j] = tot[j];
+    ++k;
+    ok = partial(k < kend, false);
+  }
+  if (!ok) {
+    outcome = 3;
+    // let the stores of the cluster's sums of the last exchange land (bounded)
+    if (nx > 0) wait_bar(xbar, (nx - 1) & 1, nullptr);
+  }
+  // no bulk copy may still be writing this CTA's shared memory when it exits
+  if (has_rows) {
+    for (int b = 0; b < nsab; ++b)
+      for (; sa_use[b] < sa_iss[b]; ++sa_use[b]) wait_bar(sa_full + b, sa_use[b] & 1, nullptr);
+    for (int b = 0; b < 3; ++b)
+      for (; iv_use[b] < iv_iss[b]; ++iv_use[b]) wait_bar(iv_full + b, iv_use[b] & 1, nullptr);
+    for (; p_use < p_iss; ++p_use) wait_bar(p_full, p_use & 1, nullptr);
+  }
+  __syncthreads();
+  for (int64_t i = tid; i < qc; i += kWThreads) {
+    g.r[ilo + i] = sr[i];
+    g.rp[ilo + i] = srp[i];
+    g.w[ilo + i] = sw[i];
+    g.wp[ilo + i] = swp[i];
+  }
+  // relative residuals of the tested iterations (kstart was tested before)
+  if (cta == 0) {
+    const int64_t klast = (outcome == 3) ? kstart : k;
+    for (int64_t kk = kstart + 1 + tid; kk <= klast; kk += kWThreads) g.hist[kk] = sqrt(hn2[kk - k0]) / r0;
+  }
+  if (cta == 0 && tid == 0) {
+    ctrl->k = k;
+    if (outcome == 3) { ctrl->status = 5; ctrl->stop = 1; }
+    if (outcome == 2) { ctrl->status = 4; ctrl->stop = 1; }
+    if (outcome == 1) { if (g.mixed) ctrl->pending = 1; else ctrl->stop = 1; }
+    if (k >= ctrl->max_iters) ctrl->stop = 1;
+    *g.epoch = (tag0 >> 24) + 1;
+    __threadfence();
+  }
+  // no CTA leaves while a peer may still store into its shared memory
+  ptx::cluster_sync_all();
+}
+
+template <typename T, typename TF>
+bool wide_plan(int64_t m, int64_t tau, int max_ctas, int64_t chunk, WidePlan* out) {
+  int dev = 0, nsm = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (nsm <= 0 || optin <= 0) return false;
+  const int64_t pld = (tau + 3) / 4 * 4;
+  int nsab = 2;
+  auto smem_of = [&](int64_t q) {
+    return wide_layout(q, tau, pld, (int)sizeof(T), (int)sizeof(TF), chunk, nsab).total;
+  };
+  auto kern = k_iterate_wide<T, TF>;
+  int64_t cap_ctas = (int64_t)nsm / kWideCluster * kWideCluster;
+  if (max_ctas > 0)
+    cap_ctas = std::min<int64_t>(cap_ctas, std::max(kWideCluster, max_ctas / kWideCluster * kWideCluster));
+  int64_t q = std::max<int64_t>(4, round_up((m + cap_ctas - 1) / cap_ctas, 4));
+  for (;;) {
+    if (smem_of(q) > (size_t)optin) nsab = 1;  // S^T A single buffered
+    const size_t smem = smem_of(q);
+    // the staged block must fit one bulk copy's transaction count as well
+    if (smem > (size_t)optin || (size_t)tau * round_up(q, 4) * sizeof(T) >= (1u << 20)) return false;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    const int64_t nblk = round_up((m + q - 1) / q, kWideCluster);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nblk);
+    cfg.blockDim = dim3(kWThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kWideCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (ncl <= 0) return false;
+    if ((int64_t)ncl * kWideCluster >= nblk) {
+      out->nblk = (int)nblk;
+      out->q = q;
+      out->smem = smem;
+      out->nsab = nsab;
+      return true;
+    }
+    // fewer clusters are resident than the slices need: widen the slices
+    q = std::max<int64_t>(q + 4, round_up((m + (int64_t)ncl * kWideCluster - 1) /
+                                              ((int64_t)ncl * kWideCluster), 4));
+  }
+}
+
+template <typename T, typename TF>
+cudaError_t launch_iterate_wide(cudaStream_t st, Ctrl* ctrl, const WideArgs<T, TF>& g, size_t smem) {
+  auto kern = k_iterate_wide<T, TF>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)g.nblk);
+  cfg.blockDim = dim3(kWThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kWideCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, ctrl, g);
+}
+
+#define RS_WIDE_INST(T, TF)                                                                     \
+  template bool wide_plan<T, TF>(int64_t, int64_t, int, int64_t, WidePlan*);                   \
+  template cudaError_t launch_iterate_wide<T, TF>(cudaStream_t, Ctrl*, const WideArgs<T, TF>&, \
+                                                  size_t);
+RS_WIDE_INST(float, float)
+RS_WIDE_INST(float, double)
+RS_WIDE_INST(double, double)
+#undef RS_WIDE_INST
+
+}  // namespace rs

@@ -43,11 +43,20 @@ struct RowsView {
   int64_t ldsa, sa_slot;
   const T* ST;       // Gaussian: tau x lda per slot, else nullptr
   int64_t st_slot;
+  int64_t bq;        // 0: SA row-major (row stride ldsa); else blocked by bq-row slices
 };
 template <typename T>
 cudaError_t launch_sa_batched(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
                               PlanView plan, const T* A, int64_t lda, int64_t m, int64_t tau, T* SA,
-                              int64_t ldsa, int64_t sa_slot);
+                              int64_t ldsa, int64_t sa_slot, int64_t bq = 0);
+// S^T A and M = S^T A S of the bucket-row sketches in one launch (plan and kJB rows
+// of S^T A in shared memory); sa_msys_fits says whether they fit
+template <typename T>
+bool sa_msys_fits(int64_t m, int64_t tau, int64_t nperm);
+template <typename T>
+cudaError_t launch_sa_msys(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, PlanView plan,
+                           const T* A, int64_t lda, int64_t m, int64_t tau, T* SA, int64_t ldsa,
+                           int64_t sa_slot, int64_t bq, double* M, int64_t m_slot);
 template <typename T>
 cudaError_t launch_msys_batched(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
                                 PlanView plan, RowsView<T> rows, int64_t m, int64_t tau,
@@ -109,6 +118,51 @@ cudaError_t launch_iterate(cudaStream_t st, Ctrl* ctrl, IterArgs<T, TF> g);
 // is not in the sketch (all_rows = 1: every row is, as in the count sketch)
 cudaError_t launch_inv_map(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, PlanView plan,
                            int64_t m, int64_t tau, int all_rows, int32_t* inv, int64_t inv_slot);
+
+// ---- persistent iterations of a chunk over the whole GPU (rs_iterate_wide.cu) ----
+// Bucket-row sketches (subsample, count, subcount). Each CTA owns a slice of q rows
+// of the m-vectors; delta = M^+ S^T r is assembled from per-CTA partials through a
+// deterministic all-reduce (tagged partial words in global memory, then the
+// cluster's shared memory).
+template <typename T, typename TF>
+struct WideArgs {
+  int mixed;                       // 1: convergence sets `pending` (FP64 check follows)
+  const T* rows;                   // S^T A of slot 0, blocked: CTA c's tau x round_up(q, 4)
+                                   // block at c * tau * round_up(q, 4)
+  int64_t sa_slot;                 // slot stride of S^T A
+  const int32_t* inv; int64_t inv_slot;      // row -> bucket | sign, kNotSketched
+  const TF* P; int64_t pld, p_slot;          // M^+ per slot, tau x pld
+  const double* gam; const double* bet;
+  double* w; double* wp; double* r; double* rp;
+  double* hist; double* delta_out;
+  uint64_t* part;                  // 2 x nblk x (tau + 1) x 2 tagged words of partials
+  uint64_t* epoch;                 // launch counter of the tags
+  int32_t* abort_word;             // set by a CTA whose bounded wait ran out
+  int64_t m, tau, chunk, q;
+  int nblk;
+  int nsab;                        // buffers of the staged S^T A block (2, or 1 when tight)
+};
+struct WidePlan {
+  int nblk;       // CTAs (a multiple of the cluster size)
+  int64_t q;      // rows per CTA (a multiple of 4)
+  size_t smem;    // dynamic shared memory per CTA
+  int nsab;       // S^T A staging buffers
+};
+// false when the slice buffers do not fit shared memory (the cluster kernel is used)
+template <typename T, typename TF>
+bool wide_plan(int64_t m, int64_t tau, int max_ctas, int64_t chunk, WidePlan* out);
+template <typename T, typename TF>
+cudaError_t launch_iterate_wide(cudaStream_t st, Ctrl* ctrl, const WideArgs<T, TF>& g, size_t smem);
+constexpr int kWideCluster = 8;
+// P_s = M_s^+ in FP32 by symmetric sweeps, without the triangular factor (tau <= 256)
+cudaError_t launch_sweep_inv(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
+                             const double* M, int64_t m_slot, int64_t tau, float* P, int64_t pld,
+                             int64_t p_slot, int32_t* ndropped);
+constexpr int64_t kSweepMaxTau = 256;
+// P_s = L_s^{-T} L_s^{-1} (full, row stride pld) for every active slot
+template <typename TF>
+cudaError_t launch_pinv(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, const TF* Linv,
+                        int64_t l_slot, int64_t tau, TF* P, int64_t pld, int64_t p_slot);
 
 // ---- iterate / residual update (rs_update.cu) ----
 struct UpdateArgs {

@@ -50,6 +50,7 @@ def test_null_arguments_are_rejected_without_a_device(L):
     assert b"null" in L.rs_last_error(None)
     st = L.rs_solve(None, 1e-6, 10, None, 0, None, None)
     assert st == rs.RS_EINVAL
+    assert L.rs_iter_plan(None, None, None) == rs.RS_EINVAL
     L.rs_destroy(None)
 
 
@@ -75,6 +76,7 @@ def test_default_options(L):
     o = rs.Opts()
     L.rs_default_opts(ctypes.byref(o))
     assert o.precision == 0 and o.refresh_every == 50 and o.chol_fp64 == 0
+    assert o.iter_ctas == 0 and o.setup_tc == 1
     m = rs.Mom()
     L.rs_default_mom(ctypes.byref(m), 3)
     assert m.kind == 3 and m.eta == 0.995 and m.beta_switch == 0.5

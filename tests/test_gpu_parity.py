@@ -104,6 +104,42 @@ def test_plain_iterates_match_oracle(rs, kind, tau, s_, mom):
     assert np.allclose(hist, ref["hist"], rtol=1e-8, atol=1e-14)
 
 
+@pytest.mark.parametrize("kind,tau,s_", KINDS[:3], ids=[k[0] for k in KINDS[:3]])
+def test_plain_iterates_one_cluster_of_ctas(rs, kind, tau, s_):
+    """The persistent iteration kernel with 8 CTAs of 16 rows (one cluster; the
+    last CTA idle) against the oracle."""
+    X, y, _ = gaussian_problem(160, 97, 21)
+    lam, K = 0.05, 40
+    ref = oracle.solve_ridge(X, y, lam, "primal", kind, tau, seed=9, tol=0.0, max_iters=K,
+                             mom={"kind": "heuristic"}, s=s_)
+    with rs.Solver(X, y, lam, sketch=kind, tau=tau, momentum="heuristic", seed=9,
+                   sub_s=s_ or 0, iter_ctas=8) as s:
+        assert (s.iter_ctas, s.iter_rows) == (8, 16)
+        w, hist, iters, _ = s.solve(tol=0.0, max_iters=K)
+    assert iters == K
+    assert rel(w, ref["w"]) <= W_TOL
+    assert np.allclose(hist, ref["hist"], rtol=1e-8, atol=1e-14)
+
+
+@pytest.mark.parametrize("kind,tau,s_", [("subsample", 64, 0), ("count", 64, 0),
+                                         ("subcount", 64, 640)], ids=["subsample", "count", "subcount"])
+def test_persistent_kernel_matches_cluster_kernel(rs, kind, tau, s_):
+    """Plain FP64 iterates of the two iteration kernels (CTAs spread over the GPU vs
+    one cluster) agree to rounding; m = 1999 is ragged against the 4-row slices;
+    chunk 128 with 300 iterations spans several launches."""
+    X, y, _ = gaussian_problem(2600, 1999, 31)
+    lam, K = 0.1, 300
+    out = []
+    for ctas in (0, -1):
+        with rs.Solver(X, y, lam, sketch=kind, tau=tau, momentum="heuristic", seed=5,
+                       sub_s=s_, iter_ctas=ctas) as s:
+            assert (s.iter_ctas > 0) == (ctas == 0)
+            w, hist, iters, _ = s.solve(tol=0.0, max_iters=K)
+            out.append((w, hist))
+    assert rel(out[0][0], out[1][0]) <= 1e-10
+    assert np.allclose(out[0][1], out[1][1], rtol=1e-9, atol=0)
+
+
 def test_cfg_small_to_tolerance(rs):
     """Dense primal FP64: X 2000 x 500 iid N(0,1), lambda = 1e-3, subsample tau = 50,
     no momentum, seed 0, relative residual 1e-6."""
@@ -234,6 +270,45 @@ def test_mixed_reaches_tolerance(rs, kind):
     assert oracle.true_residual(Xd, y, lam, w) <= 1e-6
     w_star = oracle.direct_solution(Xd, y, lam)
     assert rel(w, w_star) <= 1e-4
+
+
+@pytest.mark.parametrize("kind,tau,s_", [("count", 32, 0), ("subsample", 32, 0),
+                                         ("subcount", 32, 160)], ids=["count", "subsample", "subcount"])
+def test_mixed_iterates_close_to_oracle(rs, kind, tau, s_):
+    """Mixed path (FP32 A formed on the CUDA cores, S^T A and M^+ by FP32 sweeps;
+    FP64 vectors) against the FP64 oracle on the same FP32 data for 12 iterations:
+    the difference is FP32 rounding of the products."""
+    from synth import geometric_sigma, spectrum_problem
+
+    X, y, _ = spectrum_problem(1500, 256, geometric_sigma(256, 1e-1), seed=8, noise=0.01,
+                               dtype=np.float32)
+    lam, K = 1e-1, 12
+    Xd = X.astype(np.float64)
+    ref = oracle.solve_ridge(Xd, y, lam, "primal", kind, tau, seed=6, tol=0.0, max_iters=K,
+                             mom={"kind": "heuristic"}, s=s_)
+    with rs.Solver(X, y, lam, sketch=kind, tau=tau, momentum="heuristic", seed=6, sub_s=s_,
+                   precision="mixed", setup_tc=False) as s:
+        assert s.iter_ctas > 0
+        w, hist, iters, _ = s.solve(tol=0.0, max_iters=K)
+    assert iters == K
+    assert rel(w, ref["w"]) <= 2e-5
+    assert np.allclose(hist[:K], ref["hist"][:K], rtol=2e-5, atol=0)
+
+
+def test_mixed_sweep_empty_buckets(rs):
+    """Count sketch with tau close to m: empty buckets make S^T A S singular; the
+    sweep drops those indices and the solve still reaches the FP64-checked tolerance."""
+    from synth import geometric_sigma, spectrum_problem
+
+    X, y, _ = spectrum_problem(1200, 256, geometric_sigma(256, 1e-2), seed=3, noise=0.01,
+                               dtype=np.float32)
+    lam = 1e-2
+    with rs.Solver(X, y, lam, sketch="count", tau=230, momentum="none", seed=1,
+                   precision="mixed") as s:
+        w, hist, iters, conv = s.solve(tol=1e-6, max_iters=5000)
+    Xd = X.astype(np.float64)
+    assert conv and oracle.true_residual(Xd, y, lam, w) <= 1e-6
+    assert rel(w, oracle.direct_solution(Xd, y, lam)) <= 1e-4
 
 
 # ------------------------------------------------------- small SPD solve ---
