@@ -91,10 +91,10 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def make_problem(seed, device):
+def make_problem(seed, device, n_rows=N_ROWS):
     from synth import geometric_sigma, spectrum_problem_torch
 
-    return spectrum_problem_torch(N_ROWS, N_COLS, geometric_sigma(N_COLS, 1e-3), seed=seed,
+    return spectrum_problem_torch(n_rows, N_COLS, geometric_sigma(N_COLS, 1e-3), seed=seed,
                                   noise=0.01, device=device)
 
 
@@ -216,6 +216,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--small", action="store_true",
+                    help="profiling case: X 20000 x 4096 (328 MB, larger than L2), same sketch and "
+                         "schedule; prints the line of that case (not the benchmark workload)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -235,7 +238,7 @@ def main():
 
         dist.init_process_group("nccl", device_id=dev)
     rs.lib()
-    X, y, _ = make_problem(1234 + rank, dev)
+    X, y, _ = make_problem(1234 + rank, dev, 20000 if args.small else N_ROWS)
     w_out = torch.empty(N_COLS, dtype=torch.float64, device=dev)
 
     for _ in range(max(args.warmup, 3)):
@@ -311,7 +314,8 @@ def main():
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": step_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "global_batch": world, "seq_len": None,
+        "config": {"workload": WORKLOAD.replace("100000x4096", "20000x4096") if args.small else WORKLOAD,
+                   "global_batch": world, "seq_len": None,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (X = 1.64 GB re-read every step)"},
         "time_to_tol_ms": step_ms, "iters_to_tol": last["iters"], "converged": last["conv"],

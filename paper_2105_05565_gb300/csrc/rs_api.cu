@@ -36,6 +36,7 @@ struct DeviceGuard {
 };
 
 constexpr int64_t kLdAlign = 128;     // row length padding of m-long rows (elements)
+constexpr int kChunksPerGraph = 4;    // chunks of iterations captured in one CUDA graph
 constexpr int64_t kMaxSample = 8192;  // largest ordered sample drawn by one CTA
 constexpr int64_t kMaxCountTau = 2048;
 
@@ -91,6 +92,8 @@ struct rs_ctx {
   bool use_wide = false;
   WidePlan wide{};
   void* Pm = nullptr;       // per slot: M^+ = L^{-T} L^{-1}, tau x pld (factor precision)
+  bool sweep_p = false;     // M^+ by FP32 sweeps from an FP32 M (mixed, FP32 factor)
+  float* Mf = nullptr;      // per slot: M in FP32 for the sweeps
   int64_t pld = 0, p_slot = 0;
   uint64_t* xpart = nullptr;   // all-reduce partials, 2 x nblk x (tau + 1) x 2 tagged words
   uint64_t* xflags = nullptr;  // launch counter of the tags
@@ -154,7 +157,7 @@ void free_all(rs_ctx* c) {
                   c->Linv, c->fws, c->rS, c->delta, c->perm, c->boff, c->inv, c->err_flag,
                   c->ndropped,
                   c->gam, c->bet, c->hist, c->partials, c->vn, c->vd, c->xt_part, c->rel_dev,
-                  c->ctrl, c->Pm, c->xpart, c->xflags, c->xabort};
+                  c->ctrl, c->Pm, c->xpart, c->xflags, c->xabort, c->Mf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->ctrl_h) cudaFreeHost(c->ctrl_h);
@@ -240,7 +243,8 @@ rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots, boo
       }
       if (sa_msys_fits<T>(c->m, c->tau, c->perm_stride)) {  // S^T A and M in one pass
         CKC(c, launch_sa_msys<T>(st, c->ctrl, force, nslots, plan, A, c->ld, c->m, c->tau, SA, c->ld,
-                                 c->sa_slot, c->use_wide ? c->wide.q : 0, c->M, c->m_slot));
+                                 c->sa_slot, c->use_wide ? c->wide.q : 0, c->M, c->m_slot,
+                                 (want_p && c->sweep_p) ? c->Mf : nullptr));
         break;
       }
       CKC(c, launch_sa_batched<T>(st, c->ctrl, force, nslots, plan, A, c->ld, c->m, c->tau, SA,
@@ -261,9 +265,9 @@ rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots, boo
                                    c->mp, c->tau, SA, c->ld, c->sa_slot, c->M, c->m_slot));
       break;
   }
-  if (want_p && !c->f64_factor() && c->tau <= kSweepMaxTau) {
+  if (want_p && c->sweep_p) {
     // FP32 M^+ directly (symmetric sweeps), no triangular factor
-    CKC(c, launch_sweep_inv(st, c->ctrl, force, nslots, c->M, c->m_slot, c->tau,
+    CKC(c, launch_sweep_inv(st, c->ctrl, force, nslots, c->Mf, c->m_slot, c->tau,
                             static_cast<float*>(c->Pm), c->pld, c->p_slot, c->ndropped));
     return RS_OK;
   }
@@ -471,7 +475,10 @@ rs_status build_graph(rs_ctx* c, bool with_refresh) {
     c->graph = nullptr;
   }
   CKC(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
-  rs_status s = enqueue_chunk(c, with_refresh);
+  // several chunks per replay: the host reads the control block once per replay;
+  // chunks after the solve has stopped return at once (every kernel checks ctrl)
+  rs_status s = RS_OK;
+  for (int i = 0; i < kChunksPerGraph && s == RS_OK; ++i) s = enqueue_chunk(c, with_refresh);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->stream, &g);
   if (s != RS_OK) {
@@ -549,7 +556,7 @@ rs_status write_ctrl(rs_ctx* c) {
 rs_status run_loop(rs_ctx* c, bool with_refresh, int64_t max_chunks) {
   rs_status s = build_graph(c, with_refresh);
   if (s != RS_OK) return s;
-  for (int64_t q = 0; q < max_chunks; ++q) {
+  for (int64_t q = 0; q < (max_chunks + kChunksPerGraph - 1) / kChunksPerGraph; ++q) {
     CKC(c, cudaGraphLaunch(c->graph, c->stream));
     if ((s = read_ctrl(c)) != RS_OK) return s;
     if (c->ctrl_h->stop) return RS_OK;
@@ -809,6 +816,10 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
       TRYC(cudaMemsetAsync(c->xflags, 0, sizeof(uint64_t), st));
       TRYC(cudaMemsetAsync(c->xabort, 0, sizeof(int32_t), st));
       c->use_wide = true;
+      // FP32 M^+ by sweeps where S^T A and M are formed in one pass
+      c->sweep_p = c->mixed() && !c->f64_factor() && c->tau <= kSweepMaxTau &&
+                   sa_msys_fits<float>(m, c->tau, round_up((sketch == RS_COUNT) ? m : (sketch == RS_SUBCOUNT ? c->s : c->tau), 4));
+      if (c->sweep_p) TRY(dalloc(c, &c->Mf, (size_t)c->nslots * c->tau * c->tau));
     } else {
       cudaGetLastError();
     }
@@ -1199,7 +1210,7 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
           // S^T A and M in one pass: A rows read once per slot, S^T A written once
           s = timed("sa_msys", [&]() -> rs_status {
             if (c->mixed())
-              CKC(c, launch_sa_msys<float>(c->stream, c->ctrl, 0, ns, plan, static_cast<const float*>(c->A), c->ld, c->m, c->tau, static_cast<float*>(c->SA), c->ld, c->sa_slot, bq, c->M, c->m_slot));
+              CKC(c, launch_sa_msys<float>(c->stream, c->ctrl, 0, ns, plan, static_cast<const float*>(c->A), c->ld, c->m, c->tau, static_cast<float*>(c->SA), c->ld, c->sa_slot, bq, c->M, c->m_slot, c->sweep_p ? c->Mf : nullptr));
             else
               CKC(c, launch_sa_msys<double>(c->stream, c->ctrl, 0, ns, plan, static_cast<const double*>(c->A), c->ld, c->m, c->tau, static_cast<double*>(c->SA), c->ld, c->sa_slot, bq, c->M, c->m_slot));
             return RS_OK;
@@ -1229,10 +1240,10 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
           grp("msys").flops = nsl * (c->sketch == RS_SUBSAMPLE ? 0.0 : tau * rows);
           if (s != RS_OK) break;
         }
-        const bool sweep = c->use_wide && !c->f64_factor() && c->tau <= kSweepMaxTau;
+        const bool sweep = c->sweep_p;
         if (sweep) {
           s = timed("sweep", [&]() -> rs_status {
-            CKC(c, launch_sweep_inv(c->stream, c->ctrl, 0, ns, c->M, c->m_slot, c->tau, static_cast<float*>(c->Pm), c->pld, c->p_slot, c->ndropped));
+            CKC(c, launch_sweep_inv(c->stream, c->ctrl, 0, ns, c->Mf, c->m_slot, c->tau, static_cast<float*>(c->Pm), c->pld, c->p_slot, c->ndropped));
             return RS_OK;
           });
           grp("sweep").bytes = nsl * tau * tau * (8.0 + 4.0);

@@ -195,7 +195,8 @@ __global__ void __launch_bounds__(256) k_sa_msys(const Ctrl* __restrict__ ctrl, 
                                                  PlanView plan, const T* __restrict__ A, int64_t lda,
                                                  int64_t m, int64_t tau, int64_t nperm,
                                                  T* __restrict__ SA, int64_t ldsa, int64_t sa_slot,
-                                                 int64_t bq, double* __restrict__ M, int64_t m_slot) {
+                                                 int64_t bq, double* __restrict__ M, int64_t m_slot,
+                                                 float* __restrict__ Mf) {
   using V = typename Vec<T>::type;
   constexpr int VN = Vec<T>::n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -289,7 +290,10 @@ __global__ void __launch_bounds__(256) k_sa_msys(const Ctrl* __restrict__ ctrl, 
         acc[r] += ng ? -v : v;
       }
     }
-    for (int r = 0; r < nrow; ++r) Ms[(jb + r) * tau + l] = (double)acc[r];
+    if (Mf != nullptr)
+      for (int r = 0; r < nrow; ++r) Mf[s * m_slot + (jb + r) * tau + l] = (float)acc[r];
+    else
+      for (int r = 0; r < nrow; ++r) Ms[(jb + r) * tau + l] = (double)acc[r];
   }
 }
 
@@ -302,7 +306,7 @@ bool sa_msys_fits(int64_t m, int64_t tau, int64_t nperm) {
 template <typename T>
 cudaError_t launch_sa_msys(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, PlanView plan,
                            const T* A, int64_t lda, int64_t m, int64_t tau, T* SA, int64_t ldsa,
-                           int64_t sa_slot, int64_t bq, double* M, int64_t m_slot) {
+                           int64_t sa_slot, int64_t bq, double* M, int64_t m_slot, float* Mf) {
   const int64_t nperm = plan.perm_stride;
   const size_t smem = sa_msys_smem<T>(m, tau, nperm);
   if (smem > 200 * 1024 || bq % 4 != 0) return cudaErrorInvalidValue;
@@ -311,7 +315,8 @@ cudaError_t launch_sa_msys(cudaStream_t st, const Ctrl* ctrl, int force, int nsl
   if (e != cudaSuccess) return e;
   const int64_t nj = (tau + kJB - 1) / kJB;
   k_sa_msys<T><<<(unsigned)(nslots * nj), 256, smem, st>>>(ctrl, force, nslots, plan, A, lda, m, tau,
-                                                           nperm, SA, ldsa, sa_slot, bq, M, m_slot);
+                                                           nperm, SA, ldsa, sa_slot, bq, M, m_slot,
+                                                           Mf);
   return cudaGetLastError();
 }
 
@@ -421,7 +426,7 @@ cudaError_t launch_srht_system(cudaStream_t st, const Ctrl* ctrl, int force, int
   template bool sa_msys_fits<T>(int64_t, int64_t, int64_t);                                        \
   template cudaError_t launch_sa_msys<T>(cudaStream_t, const Ctrl*, int, int, PlanView, const T*,  \
                                          int64_t, int64_t, int64_t, T*, int64_t, int64_t, int64_t, \
-                                         double*, int64_t);                                        \
+                                         double*, int64_t, float*);                                \
   template cudaError_t launch_sa_batched<T>(cudaStream_t, const Ctrl*, int, int, PlanView,         \
                                             const T*, int64_t, int64_t, int64_t, T*, int64_t,      \
                                             int64_t, int64_t);                                     \

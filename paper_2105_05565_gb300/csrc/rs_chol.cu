@@ -554,7 +554,7 @@ __device__ __forceinline__ void diag_sweep(float (&a)[kSwB][kSwB], int Pb, const
 }
 
 __global__ void __maxnreg__(96) k_sweep_inv(const Ctrl* __restrict__ ctrl, int force, int nslots,
-                                            const double* __restrict__ M, int64_t m_slot, int tau,
+                                            const float* __restrict__ M, int64_t m_slot, int tau,
                                             float* __restrict__ P, int64_t pld, int64_t p_slot,
                                             int32_t* __restrict__ ndropped) {
   const int64_t slot = blockIdx.x;
@@ -563,14 +563,13 @@ __global__ void __maxnreg__(96) k_sweep_inv(const Ctrl* __restrict__ ctrl, int f
   // that lanes reading different blocks hit different banks: X[i][kk] at
   // Xs[kk][(i / 8) * 9 + i % 8]
   constexpr int kRow9 = kSwMaxTau / kSwB * (kSwB + 1);
-  __shared__ float Xs[2][kSwB][kRow9];      // by panel parity
+  __shared__ float Xs[kSwB][kRow9];
   __shared__ float Ys[kSwB][kRow9];
-  __shared__ float Zs[2][kSwB][kSwB + 1];   // Z of the panel, by panel parity
+  __shared__ float Zs[kSwB][kSwB + 1];      // Z of the current panel
   __shared__ float thrs[kSwMaxTau];         // pivot threshold in the scaled matrix
-  __shared__ double dg[kSwMaxTau];          // M_ii
   __shared__ float sc[kSwMaxTau];           // M_ii^{-1/2}, 0 for an index dropped at the start
   __shared__ unsigned char dropped[kSwMaxTau];
-  __shared__ double s_red[32];
+  __shared__ float s_red[32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nb = (tau + kSwB - 1) / kSwB;
   const int tp = nb * kSwB;
@@ -579,81 +578,90 @@ __global__ void __maxnreg__(96) k_sweep_inv(const Ctrl* __restrict__ ctrl, int f
   int I = 0;
   while ((I + 1) * (I + 2) / 2 <= tid) ++I;
   const int J = tid - I * (I + 1) / 2;  // block (I, J), I >= J
-  const double* Ms = M + slot * m_slot;
-  double dmax = 0.0;
-  for (int i = tid; i < tau; i += blockDim.x) {
-    const double d = Ms[(int64_t)i * tau + i];
-    dg[i] = d;
-    dmax = fmax(dmax, d);
-  }
+  const float* Ms = M + slot * m_slot;
+  float dmax = 0.f;
+  for (int i = tid; i < tau; i += blockDim.x) dmax = fmaxf(dmax, Ms[(int64_t)i * tau + i]);
   {
     const int nw = blockDim.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
     if (lane == 0) s_red[wid] = dmax;
     __syncthreads();
     if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < nw; ++w) t = fmax(t, s_red[w]);
+      float t = 0.f;
+      for (int w = 0; w < nw; ++w) t = fmaxf(t, s_red[w]);
       s_red[0] = t;
     }
     __syncthreads();
   }
-  const double thr = (double)tau * 1.1920928955078125e-07 * s_red[0];
+  const float thr = (float)tau * 1.1920928955078125e-07f * s_red[0];
   for (int i = tid; i < tp; i += blockDim.x) {
-    const bool dr = (i >= tau) || !(dg[i] > thr);  // padding counts as dropped
+    const float d = (i < tau) ? Ms[(int64_t)i * tau + i] : 0.f;
+    const bool dr = (i >= tau) || !(d > thr);  // padding counts as dropped
     dropped[i] = dr;
-    sc[i] = dr ? 0.f : (float)(1.0 / sqrt(dg[i]));
-    thrs[i] = dr ? 0.f : (float)(thr / dg[i]);
+    sc[i] = dr ? 0.f : rsqrtf(d);
+    thrs[i] = dr ? 0.f : thr / d;
   }
   __syncthreads();
   float a[kSwB][kSwB];
 #pragma unroll
   for (int r = 0; r < kSwB; ++r) {
+    const int i = I * kSwB + r;
+    const float si = (own && i < tau) ? sc[i] : 0.f;
 #pragma unroll
     for (int c = 0; c < kSwB; ++c) {
-      const int i = I * kSwB + r, l = J * kSwB + c;
-      float x = 0.f;
-      if (own && i < tau && l < tau)
-        x = (float)(Ms[(int64_t)i * tau + l] * (double)sc[i] * (double)sc[l]);
-      a[r][c] = x;
+      const int l = J * kSwB + c;
+      a[r][c] = (own && i < tau && l < tau) ? Ms[(int64_t)i * tau + l] * si * sc[l] : 0.f;
     }
-    asm volatile("" ::: "memory");  // one row of loads in flight: keeps registers for a
   }
-  if (own && I == 0 && J == 0) diag_sweep(a, 0, thrs, dropped, Zs[0]);
+  if (own && I == 0 && J == 0) diag_sweep(a, 0, thrs, dropped, Zs);
 
   for (int Pb = 0; Pb < nb; ++Pb) {
-    float(*X)[kRow9] = Xs[Pb & 1];
-    // X = column block Pb (blocks (I > Pb, Pb) and, transposed, (Pb, J < Pb)); Z of
-    // the panel is in Zs already (swept by the owner of the diagonal block)
-    if (own) {
-      if (J == Pb && I > Pb) {
+    __syncthreads();  // Z of the panel in Zs; X, Y of the previous panel consumed
+    // the panel blocks publish X and Y = X Z: (I > Pb, Pb) holds X_I, (Pb, J < Pb)
+    // holds X_J^T
+    if (own && J == Pb && I > Pb) {
 #pragma unroll
-        for (int r = 0; r < kSwB; ++r)
+      for (int r = 0; r < kSwB; ++r)
 #pragma unroll
-          for (int c = 0; c < kSwB; ++c) X[c][I * (kSwB + 1) + r] = a[r][c];
-      } else if (I == Pb && J < Pb) {
+        for (int kk = 0; kk < kSwB; ++kk) Xs[kk][I * (kSwB + 1) + r] = a[r][kk];
 #pragma unroll
-        for (int r = 0; r < kSwB; ++r)
+      for (int c = 0; c < kSwB; ++c) {
+        float z[kSwB];
 #pragma unroll
-          for (int c = 0; c < kSwB; ++c) X[r][J * (kSwB + 1) + c] = a[r][c];
+        for (int kk = 0; kk < kSwB; ++kk) z[kk] = Zs[kk][c];
+#pragma unroll
+        for (int r = 0; r < kSwB; ++r) {
+          float y = 0.f;
+#pragma unroll
+          for (int kk = 0; kk < kSwB; ++kk) y = fmaf(a[r][kk], z[kk], y);
+          Ys[c][I * (kSwB + 1) + r] = y;
+        }
+      }
+    } else if (own && I == Pb && J < Pb) {
+#pragma unroll
+      for (int kk = 0; kk < kSwB; ++kk)
+#pragma unroll
+        for (int c = 0; c < kSwB; ++c) Xs[kk][J * (kSwB + 1) + c] = a[kk][c];
+#pragma unroll
+      for (int cc = 0; cc < kSwB; ++cc) {
+        float z[kSwB];
+#pragma unroll
+        for (int kk = 0; kk < kSwB; ++kk) z[kk] = Zs[kk][cc];
+#pragma unroll
+        for (int c = 0; c < kSwB; ++c) {
+          float y = 0.f;
+#pragma unroll
+          for (int kk = 0; kk < kSwB; ++kk) y = fmaf(a[kk][c], z[kk], y);
+          Ys[cc][J * (kSwB + 1) + c] = y;
+        }
       }
     }
     __syncthreads();
-    // Y = X Z, one entry per thread and step
-    for (int e = tid; e < tp * kSwB; e += blockDim.x) {
-      const int c = e / tp, t = e - c * tp;
-      const int t9 = (t >> 3) * (kSwB + 1) + (t & 7);
-      float y = 0.f;
-#pragma unroll
-      for (int kk = 0; kk < kSwB; ++kk) y = fmaf(X[kk][t9], Zs[Pb & 1][kk][c], y);
-      Ys[c][t9] = y;
-    }
-    __syncthreads();
-    // A_IJ -= X_I Y_J^T; A_IP = Y_I, A_PJ = Y_J^T, A_PP = -Z
+    // A_IJ -= X_I Y_J^T; A_IP = Y_I, A_PJ = Y_J^T; A_PP = -Z already
     if (own) {
       if (I == Pb && J == Pb) {
-        // already -Z: swept by this thread after the previous panel's update
+        // swept by this thread after the previous panel's update
       } else if (J == Pb) {
 #pragma unroll
         for (int r = 0; r < kSwB; ++r)
@@ -672,14 +680,14 @@ __global__ void __maxnreg__(96) k_sweep_inv(const Ctrl* __restrict__ ctrl, int f
           for (int c = 0; c < kSwB; ++c) y[c] = Ys[kk][J * (kSwB + 1) + c];
 #pragma unroll
           for (int r = 0; r < kSwB; ++r) {
-            const float x = X[kk][I * (kSwB + 1) + r];
+            const float x = Xs[kk][I * (kSwB + 1) + r];
 #pragma unroll
             for (int c = 0; c < kSwB; ++c) a[r][c] = fmaf(-x, y[c], a[r][c]);
           }
         }
         // the next panel's diagonal block is final now: sweep it while the other
-        // blocks are still being updated
-        if (I == Pb + 1 && J == Pb + 1) diag_sweep(a, Pb + 1, thrs, dropped, Zs[(Pb + 1) & 1]);
+        // blocks are still being updated (Z is read again only after the barrier)
+        if (I == Pb + 1 && J == Pb + 1) diag_sweep(a, Pb + 1, thrs, dropped, Zs);
       }
     }
   }
@@ -688,16 +696,52 @@ __global__ void __maxnreg__(96) k_sweep_inv(const Ctrl* __restrict__ ctrl, int f
   if (own) {
     float* Ps = P + slot * p_slot;
 #pragma unroll
-    for (int r = 0; r < kSwB; ++r)
+    for (int r = 0; r < kSwB; ++r) {
+      const int i = I * kSwB + r;
+      const float si = (i < tp && !dropped[i]) ? -sc[i] : 0.f;
 #pragma unroll
       for (int c = 0; c < kSwB; ++c) {
-        const int i = I * kSwB + r, l = J * kSwB + c;
-        if (i < tau && l < tau && (I != J || c <= r)) {
-          const float x = (dropped[i] || dropped[l]) ? 0.f : -a[r][c] * sc[i] * sc[l];
-          Ps[(int64_t)i * pld + l] = x;
-          Ps[(int64_t)l * pld + i] = x;
+        const int l = J * kSwB + c;
+        a[r][c] *= (!dropped[l]) ? si * sc[l] : 0.f;
+      }
+    }
+    if ((I + 1) * kSwB <= tau) {  // full blocks: rows of 8 as two float4 stores
+#pragma unroll
+      for (int r = 0; r < kSwB; ++r) {
+        float* row = Ps + (int64_t)(I * kSwB + r) * pld + J * kSwB;
+        if (I != J) {
+          *reinterpret_cast<float4*>(row) = make_float4(a[r][0], a[r][1], a[r][2], a[r][3]);
+          *reinterpret_cast<float4*>(row + 4) = make_float4(a[r][4], a[r][5], a[r][6], a[r][7]);
+        } else {
+#pragma unroll
+          for (int c = 0; c <= r; ++c) row[c] = a[r][c];
         }
       }
+      if (I != J) {
+#pragma unroll
+        for (int c = 0; c < kSwB; ++c) {
+          float* row = Ps + (int64_t)(J * kSwB + c) * pld + I * kSwB;
+          *reinterpret_cast<float4*>(row) = make_float4(a[0][c], a[1][c], a[2][c], a[3][c]);
+          *reinterpret_cast<float4*>(row + 4) = make_float4(a[4][c], a[5][c], a[6][c], a[7][c]);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < kSwB; ++r)
+#pragma unroll
+          for (int c = 0; c < r; ++c) Ps[(int64_t)(J * kSwB + c) * pld + I * kSwB + r] = a[r][c];
+      }
+    } else {  // the ragged last block row
+#pragma unroll
+      for (int r = 0; r < kSwB; ++r)
+#pragma unroll
+        for (int c = 0; c < kSwB; ++c) {
+          const int i = I * kSwB + r, l = J * kSwB + c;
+          if (i < tau && l < tau && (I != J || c <= r)) {
+            Ps[(int64_t)i * pld + l] = a[r][c];
+            Ps[(int64_t)l * pld + i] = a[r][c];
+          }
+        }
+    }
   }
   if (tid == 0 && ndropped != nullptr) {
     int cnt = 0;
@@ -707,7 +751,7 @@ __global__ void __maxnreg__(96) k_sweep_inv(const Ctrl* __restrict__ ctrl, int f
 }
 
 cudaError_t launch_sweep_inv(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
-                             const double* M, int64_t m_slot, int64_t tau, float* P, int64_t pld,
+                             const float* M, int64_t m_slot, int64_t tau, float* P, int64_t pld,
                              int64_t p_slot, int32_t* ndropped) {
   if (tau < 1 || tau > kSwMaxTau) return cudaErrorInvalidValue;
   k_sweep_inv<<<nslots, sweep_threads(tau), 0, st>>>(ctrl, force, nslots, M, m_slot, (int)tau, P,

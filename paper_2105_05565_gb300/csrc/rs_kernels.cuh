@@ -56,7 +56,8 @@ bool sa_msys_fits(int64_t m, int64_t tau, int64_t nperm);
 template <typename T>
 cudaError_t launch_sa_msys(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, PlanView plan,
                            const T* A, int64_t lda, int64_t m, int64_t tau, T* SA, int64_t ldsa,
-                           int64_t sa_slot, int64_t bq, double* M, int64_t m_slot);
+                           int64_t sa_slot, int64_t bq, double* M, int64_t m_slot,
+                           float* Mf = nullptr);
 template <typename T>
 cudaError_t launch_msys_batched(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
                                 PlanView plan, RowsView<T> rows, int64_t m, int64_t tau,
@@ -156,7 +157,7 @@ cudaError_t launch_iterate_wide(cudaStream_t st, Ctrl* ctrl, const WideArgs<T, T
 constexpr int kWideCluster = 8;
 // P_s = M_s^+ in FP32 by symmetric sweeps, without the triangular factor (tau <= 256)
 cudaError_t launch_sweep_inv(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
-                             const double* M, int64_t m_slot, int64_t tau, float* P, int64_t pld,
+                             const float* M, int64_t m_slot, int64_t tau, float* P, int64_t pld,
                              int64_t p_slot, int32_t* ndropped);
 constexpr int64_t kSweepMaxTau = 256;
 // P_s = L_s^{-T} L_s^{-1} (full, row stride pld) for every active slot
