@@ -75,7 +75,11 @@ typedef enum {
   RS_MOM_HEURISTIC = 3
 } rs_mom_kind;
 
-typedef enum { RS_F64 = 0, RS_F32 = 1 } rs_dtype;
+typedef enum {
+  RS_F64 = 0,
+  RS_F32 = 1,
+  RS_BF16 = 2 /* CSR values only (bfloat16, 2 bytes); products widen them exactly */
+} rs_dtype;
 
 typedef enum {
   RS_PLAIN_FP64 = 0, /* every product and update in FP64 */
@@ -93,15 +97,24 @@ typedef struct {
   double beta_c;       /* constant mode momentum; default 0.5 */
 } rs_mom;
 
-/* Dense row-major n x d design matrix X (val, dtype) or CSR (reserved). */
+/*
+ * Design matrix X, n x d: dense row-major (is_csr = 0: val holds n*d values of
+ * dtype RS_F64 or RS_F32) or CSR (is_csr = 1: rowptr[n + 1] with rowptr[0] = 0 and
+ * rowptr[n] = nnz, colidx[nnz] in [0, d), val[nnz] of dtype RS_F64, RS_F32 or
+ * RS_BF16; column indices need not be sorted within a row, duplicates add up).
+ * A CSR X runs matrix-free (A = X^T X + lambda I is never formed; A V =
+ * X^T (X V) + lambda V, Section 2), primal form, subsample / count / subcount
+ * sketches; inconsistent CSR arrays give RS_EINVAL (checked on the device before
+ * any use). The arrays are copied; n, d < 2^31.
+ */
 typedef struct {
-  int32_t is_csr;       /* must be 0 in this build (dense X) */
+  int32_t is_csr;       /* 0 dense, 1 CSR */
   int32_t dtype;        /* rs_dtype of val */
   int64_t n, d;         /* rows (samples), columns (features) */
-  int64_t nnz;          /* CSR only */
-  const void* val;      /* dense: n*d values, row-major */
-  const int64_t* rowptr;/* CSR only */
-  const int32_t* colidx;/* CSR only */
+  int64_t nnz;          /* CSR: stored entries */
+  const void* val;      /* dense: n*d values, row-major; CSR: nnz values */
+  const int64_t* rowptr;/* CSR: n + 1 row offsets */
+  const int32_t* colidx;/* CSR: nnz column indices */
   int32_t on_device;    /* 1 if val (and rowptr/colidx) are device pointers */
 } rs_matrix;
 

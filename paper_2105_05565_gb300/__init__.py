@@ -123,6 +123,35 @@ def _buf(x, dtype):
     return a.ctypes.data, 0, a
 
 
+class CSR:
+    """Sparse X in compressed rows for the matrix-free path: rowptr (n + 1, int64),
+    colidx (nnz, int32), vals (nnz; float64, float32, or bfloat16 given as the
+    float values, which must be representable in bfloat16, with ``bf16=True``)."""
+
+    def __init__(self, rowptr, colidx, vals, shape, bf16=False):
+        self.n, self.d = (int(v) for v in shape)
+        self.rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        self.colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+        v = np.ascontiguousarray(vals)
+        if bf16:
+            bits = v.astype(np.float32).view(np.uint32)
+            if np.any(bits & 0xFFFF):
+                raise ValueError("CSR values are not representable in bfloat16")
+            self.vals = np.ascontiguousarray((bits >> 16).astype(np.uint16))
+            self.dtype = 2
+        elif v.dtype == np.float32:
+            self.vals, self.dtype = v, 1
+        else:
+            self.vals, self.dtype = np.ascontiguousarray(v, dtype=np.float64), 0
+        self.nnz = int(self.colidx.shape[0])
+        self.shape = (self.n, self.d)
+
+    @classmethod
+    def from_scipy(cls, A, bf16=False):
+        A = A.tocsr()
+        return cls(A.indptr, A.indices, A.data, A.shape, bf16=bf16)
+
+
 def _default_stream(device):
     try:
         import torch
@@ -146,11 +175,17 @@ class Solver:
                  device=0, stream=None, setup_tc=True, iter_ctas=0):
         L = lib()
         self._ctx = None
-        xdt = np.float32 if str(getattr(X, "dtype", "")).endswith("float32") else np.float64
-        xp, xdev, self._xkeep = _buf(X, xdt)
         yp, ydev, self._ykeep = _buf(y, np.float64)
-        n, d = (int(s) for s in X.shape)
-        mat = Matrix(0, 1 if xdt == np.float32 else 0, n, d, 0, xp, None, None, xdev)
+        if isinstance(X, CSR):
+            self._xkeep = X
+            n, d = X.n, X.d
+            mat = Matrix(1, X.dtype, n, d, X.nnz, X.vals.ctypes.data, X.rowptr.ctypes.data,
+                         X.colidx.ctypes.data, 0)
+        else:
+            xdt = np.float32 if str(getattr(X, "dtype", "")).endswith("float32") else np.float64
+            xp, xdev, self._xkeep = _buf(X, xdt)
+            n, d = (int(s) for s in X.shape)
+            mat = Matrix(0, 1 if xdt == np.float32 else 0, n, d, 0, xp, None, None, xdev)
         mom = Mom()
         L.rs_default_mom(ctypes.byref(mom), MOMENTA[momentum])
         mom.eta, mom.beta_switch, mom.gamma_c, mom.beta_c = eta, beta_switch, gamma_c, beta_c

@@ -8,6 +8,11 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <type_traits>
+
 #include "ridgesketch.h"
 #include "rs_kernels.cuh"
 
@@ -98,6 +103,21 @@ struct rs_ctx {
   uint64_t* xpart = nullptr;   // all-reduce partials, 2 x nblk x (tau + 1) x 2 tagged words
   uint64_t* xflags = nullptr;  // launch counter of the tags
   int32_t* xabort = nullptr;
+  // matrix-free sparse X (CSR input)
+  bool sparse = false;
+  int64_t nnz = 0;
+  int64_t* sx_rowptr = nullptr; int32_t* sx_colidx = nullptr; void* sx_val = nullptr;
+  int64_t* sx_colptr = nullptr; int32_t* sx_rowidx = nullptr; void* sx_cval = nullptr;
+  int32_t* sx_pcol = nullptr; int64_t* sx_pstart = nullptr; int32_t* sx_cpiece = nullptr;
+  int64_t sx_npieces = 0;
+  int32_t *mf_bsum = nullptr, *mf_boffs = nullptr, *mf_tot = nullptr, *mf_crow = nullptr,
+          *mf_cptr = nullptr, *mf_ebuck = nullptr;
+  void* mf_eval = nullptr;   // per slot: ecap entries (FP32 mixed, FP64 plain)
+  void* mf_v = nullptr;      // n: (XS) delta (FP32 mixed, FP64 plain)
+  void* mf_pu = nullptr;     // pieces of X^T v, same type
+  double* mf_pud = nullptr;  // pieces of the FP64 products
+  double* mf_z = nullptr;    // n: X w for the FP64 refresh
+  int64_t mf_nrb = 0, mf_rcap = 0, mf_ecap = 0;
   int64_t perm_stride = 0, boff_stride = 0;
   int64_t nslots = 0;
   int32_t* err_flag = nullptr;
@@ -157,7 +177,11 @@ void free_all(rs_ctx* c) {
                   c->Linv, c->fws, c->rS, c->delta, c->perm, c->boff, c->inv, c->err_flag,
                   c->ndropped,
                   c->gam, c->bet, c->hist, c->partials, c->vn, c->vd, c->xt_part, c->rel_dev,
-                  c->ctrl, c->Pm, c->xpart, c->xflags, c->xabort, c->Mf};
+                  c->ctrl, c->Pm, c->xpart, c->xflags, c->xabort, c->Mf,
+                  c->sx_rowptr, c->sx_colidx, c->sx_val, c->sx_colptr, c->sx_rowidx, c->sx_cval,
+                  c->sx_pcol, c->sx_pstart, c->sx_cpiece, c->mf_bsum, c->mf_boffs, c->mf_tot,
+                  c->mf_crow, c->mf_cptr, c->mf_ebuck, c->mf_eval, c->mf_v, c->mf_pu, c->mf_pud,
+                  c->mf_z};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->ctrl_h) cudaFreeHost(c->ctrl_h);
@@ -189,6 +213,38 @@ RowsView<T> rows_view(const rs_ctx* c) {
   v.st_slot = c->sa_slot;
   v.bq = c->use_wide ? c->wide.q : 0;
   return v;
+}
+
+// ---- matrix-free sparse X ----
+template <typename VT>
+SparseX<VT> sparse_view(const rs_ctx* c) {
+  SparseX<VT> X{};
+  X.n = c->n; X.d = c->d; X.nnz = c->nnz;
+  X.rowptr = c->sx_rowptr; X.colidx = c->sx_colidx; X.val = static_cast<const VT*>(c->sx_val);
+  X.colptr = c->sx_colptr; X.rowidx = c->sx_rowidx; X.cval = static_cast<const VT*>(c->sx_cval);
+  X.pcol = c->sx_pcol; X.pstart = c->sx_pstart; X.npieces = c->sx_npieces;
+  X.cpiece = c->sx_cpiece;
+  return X;
+}
+
+MfArgs mf_args(const rs_ctx* c) {
+  MfArgs a{};
+  a.n = c->n; a.d = c->d; a.tau = c->tau;
+  a.rowptr = c->sx_rowptr; a.colidx = c->sx_colidx;
+  a.inv = c->inv; a.inv_slot = c->ld;
+  a.bsum = c->mf_bsum; a.boffs = c->mf_boffs; a.tot = c->mf_tot;
+  a.crow = c->mf_crow; a.cptr = c->mf_cptr; a.ebuck = c->mf_ebuck;
+  a.nrb = c->mf_nrb; a.rcap = c->mf_rcap; a.ecap = c->mf_ecap;
+  a.lambda = c->lambda;
+  return a;
+}
+
+// calls f(tag) with a null pointer of the sparse value type
+template <typename F>
+rs_status with_vt(const rs_ctx* c, F&& f) {
+  if (c->xdtype == RS_F64) return f(static_cast<double*>(nullptr));
+  if (c->xdtype == RS_F32) return f(static_cast<float*>(nullptr));
+  return f(static_cast<__nv_bfloat16*>(nullptr));
 }
 
 // sketch plan of `nslots` consecutive iterations starting at k0_arg (< 0: ctrl->k)
@@ -232,6 +288,16 @@ rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots, boo
                           c->sketch == RS_COUNT ? 1 : 0, c->inv, c->ld));
   const T* A = static_cast<const T*>(c->A);
   T* SA = static_cast<T*>(c->SA);
+  if (c->sparse) {  // XS and M = S^T X^T X S + lambda S^T S without A
+    s = with_vt(c, [&](auto tag) -> rs_status {
+      using VT = std::remove_pointer_t<decltype(tag)>;
+      CKC(c, (launch_mf_phase1<VT, T>(st, c->ctrl, force, nslots, mf_args(c),
+                                      static_cast<const VT*>(c->sx_val), static_cast<T*>(c->mf_eval),
+                                      plan, c->M, c->m_slot)));
+      return RS_OK;
+    });
+    if (s != RS_OK) return s;
+  } else
   switch (c->sketch) {
     case RS_SUBSAMPLE:
     case RS_COUNT:
@@ -407,6 +473,32 @@ rs_status enqueue_iterate(rs_ctx* c) {
   return c->f64_factor() ? enqueue_iterate_t<float, double>(c) : enqueue_iterate_t<float, float>(c);
 }
 
+// one matrix-free iteration: delta, (XS) delta, X^T v by column pieces, update
+rs_status enqueue_mf_iteration(rs_ctx* c) {
+  UpdateArgs a{};
+  a.gam = c->gam; a.bet = c->bet;
+  a.w = c->w; a.wp = c->wp; a.r = c->r; a.rp = c->rp; a.u = c->u;
+  a.delta = c->delta; a.partials = c->partials; a.hist = c->hist;
+  a.mixed = c->mixed();
+  return with_vt(c, [&](auto tag) -> rs_status {
+    using VT = std::remove_pointer_t<decltype(tag)>;
+    const SparseX<VT> X = sparse_view<VT>(c);
+    if (c->mixed())
+      CKC(c, (launch_mf_iteration<VT, float>(c->stream, c->ctrl, mf_args(c), X,
+                                             static_cast<const float*>(c->mf_eval), plan_view(c),
+                                             static_cast<const float*>(c->Pm), c->pld, c->p_slot,
+                                             static_cast<float*>(c->mf_v),
+                                             static_cast<float*>(c->mf_pu), a, c->rS)));
+    else
+      CKC(c, (launch_mf_iteration<VT, double>(c->stream, c->ctrl, mf_args(c), X,
+                                              static_cast<const double*>(c->mf_eval), plan_view(c),
+                                              static_cast<const double*>(c->Pm), c->pld, c->p_slot,
+                                              static_cast<double*>(c->mf_v),
+                                              static_cast<double*>(c->mf_pu), a, c->rS)));
+    return RS_OK;
+  });
+}
+
 rs_status enqueue_iteration(rs_ctx* c) {
   rs_status s = enqueue_delta(c, 0, -1);
   if (s != RS_OK) return s;
@@ -416,6 +508,14 @@ rs_status enqueue_iteration(rs_ctx* c) {
 // true residual through X into vn / vd; v is the current iterate vector (m)
 rs_status enqueue_true_av(rs_ctx* c, const double* v, const int32_t* stop) {
   cudaStream_t st = c->stream;
+  if (c->sparse)  // primal: X^T (X w) + lambda w, FP64 through the stored values
+    return with_vt(c, [&](auto tag) -> rs_status {
+      using VT = std::remove_pointer_t<decltype(tag)>;
+      const SparseX<VT> X = sparse_view<VT>(c);
+      CKC(c, sparse_xv_d<VT>(st, X, v, c->mf_z, stop));
+      CKC(c, sparse_xtv_d<VT>(st, X, c->mf_z, c->vd, c->mf_pud, stop));
+      return RS_OK;
+    });
   // primal: A w = X^T (X w) + lambda w; dual: A a = X (X^T a) + lambda a
   if (c->xdtype == RS_F32) {
     const float* X = static_cast<const float*>(c->X);
@@ -453,9 +553,12 @@ rs_status enqueue_refresh(rs_ctx* c) {
 
 rs_status enqueue_chunk(rs_ctx* c, bool with_refresh) {
   CKC(c, launch_chunk_begin(c->stream, c->ctrl));
-  rs_status s = enqueue_phase1(c, 0, -1, (int)c->nslots, c->use_wide);
+  rs_status s = enqueue_phase1(c, 0, -1, (int)c->nslots, c->use_wide || c->sparse);
   if (s != RS_OK) return s;
-  if (c->sketch != RS_SRHT) {
+  if (c->sparse) {
+    for (int64_t i = 0; i < c->chunk && s == RS_OK; ++i) s = enqueue_mf_iteration(c);
+    if (s != RS_OK) return s;
+  } else if (c->sketch != RS_SRHT) {
     s = enqueue_iterate(c);
     if (s != RS_OK) return s;
   } else {
@@ -592,6 +695,86 @@ rs_status true_rel(rs_ctx* c, const double* v_dev, double* rel) {
   return RS_OK;
 }
 
+// CSR input: device copies, CSC by a stable counting sort, the column pieces of
+// X^T v, b = X^T y, and the capacities of the per-slot XS buffers
+template <typename VT>
+rs_status sparse_setup_t(rs_ctx* c, const rs_matrix* X, const double* y, int32_t y_on_device) {
+  cudaStream_t st = c->stream;
+  const int64_t n = c->n, d = c->d, nnz = c->nnz;
+  const cudaMemcpyKind kind = X->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  rs_status s;
+  if ((s = dalloc(c, &c->sx_rowptr, n + 1)) != RS_OK) return s;
+  if ((s = dalloc(c, &c->sx_colidx, nnz)) != RS_OK) return s;
+  CKC(c, cudaMalloc(&c->sx_val, std::max<int64_t>(nnz, 1) * sizeof(VT)));
+  CKC(c, cudaMemcpyAsync(c->sx_rowptr, X->rowptr, (n + 1) * sizeof(int64_t), kind, st));
+  CKC(c, cudaMemcpyAsync(c->sx_colidx, X->colidx, nnz * sizeof(int32_t), kind, st));
+  CKC(c, cudaMemcpyAsync(c->sx_val, X->val, nnz * sizeof(VT), kind, st));
+  CKC(c, cudaMemsetAsync(c->err_flag, 0, sizeof(int32_t), st));
+  CKC(c, launch_csr_check(st, c->sx_rowptr, n, c->sx_colidx, nnz, d, c->err_flag));
+  int32_t bad = 0;
+  CKC(c, cudaMemcpyAsync(&bad, c->err_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CKC(c, cudaStreamSynchronize(st));
+  if (bad) FAILC(c, RS_EINVAL, "rs_create: inconsistent CSR arrays (rowptr or column indices)");
+  // CSC (rows ascending in every column)
+  const int nb = 152;
+  int32_t* table = nullptr;
+  int64_t* colcnt = nullptr;
+  if ((s = dalloc(c, &table, (size_t)nb * d)) != RS_OK) return s;
+  if ((s = dalloc(c, &colcnt, d)) != RS_OK) { cudaFree(table); return s; }
+  if ((s = dalloc(c, &c->sx_colptr, d + 1)) != RS_OK) return s;
+  if ((s = dalloc(c, &c->sx_rowidx, nnz)) != RS_OK) return s;
+  CKC(c, cudaMalloc(&c->sx_cval, std::max<int64_t>(nnz, 1) * sizeof(VT)));
+  cudaError_t e = build_csc<VT>(st, c->sx_rowptr, n, c->sx_colidx, static_cast<const VT*>(c->sx_val),
+                                nnz, d, table, nb, colcnt, c->sx_colptr, c->sx_rowidx,
+                                static_cast<VT*>(c->sx_cval));
+  std::vector<int64_t> colptr(d + 1);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(colptr.data(), c->sx_colptr, (d + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(table);
+  cudaFree(colcnt);
+  CKC(c, e);
+  // pieces of at most kPiece entries per column, in column order
+  std::vector<int32_t> pcol, cpiece(d + 1);
+  std::vector<int64_t> pstart;
+  for (int64_t col = 0; col < d; ++col) {
+    cpiece[col] = (int32_t)pcol.size();
+    for (int64_t q = colptr[col]; q < colptr[col + 1]; q += kPiece) {
+      pcol.push_back((int32_t)col);
+      pstart.push_back(q);
+    }
+  }
+  cpiece[d] = (int32_t)pcol.size();
+  c->sx_npieces = (int64_t)pcol.size();
+  if ((s = dalloc(c, &c->sx_pcol, pcol.size())) != RS_OK) return s;
+  if ((s = dalloc(c, &c->sx_pstart, pstart.size())) != RS_OK) return s;
+  if ((s = dalloc(c, &c->sx_cpiece, d + 1)) != RS_OK) return s;
+  if (!pcol.empty()) {
+    CKC(c, cudaMemcpy(c->sx_pcol, pcol.data(), pcol.size() * 4, cudaMemcpyHostToDevice));
+    CKC(c, cudaMemcpy(c->sx_pstart, pstart.data(), pstart.size() * 8, cudaMemcpyHostToDevice));
+  }
+  CKC(c, cudaMemcpy(c->sx_cpiece, cpiece.data(), (d + 1) * 4, cudaMemcpyHostToDevice));
+  // y, b = X^T y (FP64)
+  if ((s = dalloc(c, &c->y, n)) != RS_OK) return s;
+  CKC(c, cudaMemcpyAsync(c->y, y, n * sizeof(double), y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  if ((s = dalloc(c, &c->mf_pud, std::max<int64_t>(c->sx_npieces, 1))) != RS_OK) return s;
+  if ((s = dalloc(c, &c->mf_z, n)) != RS_OK) return s;
+  if ((s = dalloc(c, &c->vd, d)) != RS_OK) return s;
+  if ((s = dalloc(c, &c->b, d)) != RS_OK) return s;
+  CKC(c, sparse_xtv_d<VT>(st, sparse_view<VT>(c), c->y, c->b, c->mf_pud, nullptr));
+  // capacity of one slot's XS: the entries of the heaviest sampled columns
+  std::vector<int64_t> cnt(d);
+  for (int64_t col = 0; col < d; ++col) cnt[col] = colptr[col + 1] - colptr[col];
+  const int64_t ns = (c->sketch == RS_COUNT) ? d : (c->sketch == RS_SUBCOUNT ? c->s : c->tau);
+  std::nth_element(cnt.begin(), cnt.begin() + std::min<int64_t>(ns, d) - 1, cnt.end(), std::greater<int64_t>());
+  int64_t ecap = 0;
+  for (int64_t q = 0; q < std::min<int64_t>(ns, d); ++q) ecap += cnt[q];
+  c->mf_ecap = std::max<int64_t>(ecap, 1);
+  c->mf_rcap = std::max<int64_t>(1, std::min<int64_t>(n, ecap));
+  c->mf_nrb = mf_row_blocks(n);
+  return RS_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -634,12 +817,23 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
                     const rs_opts* opts, rs_ctx** out) {
   if (out) *out = nullptr;
   if (!X || !y || !out) { set_global_error("rs_create: null argument"); return RS_EINVAL; }
-  if (X->is_csr) { set_global_error("rs_create: CSR input is not supported by rs_create"); return RS_EUNSUPPORTED; }
-  if (X->n <= 0 || X->d <= 0 || !X->val) { set_global_error("rs_create: empty X"); return RS_EINVAL; }
-  if (X->dtype != RS_F64 && X->dtype != RS_F32) { set_global_error("rs_create: bad dtype"); return RS_EINVAL; }
+  if (X->n <= 0 || X->d <= 0) { set_global_error("rs_create: empty X"); return RS_EINVAL; }
+  if (X->is_csr) {
+    if (!X->rowptr || !X->colidx || X->nnz < 0 || (X->nnz > 0 && !X->val)) { set_global_error("rs_create: null or bad CSR arrays"); return RS_EINVAL; }
+    if (X->dtype != RS_F64 && X->dtype != RS_F32 && X->dtype != RS_BF16) { set_global_error("rs_create: bad dtype"); return RS_EINVAL; }
+    if (X->d > INT32_MAX || X->n > INT32_MAX) { set_global_error("rs_create: sparse X needs n, d < 2^31"); return RS_EINVAL; }
+  } else {
+    if (!X->val) { set_global_error("rs_create: empty X"); return RS_EINVAL; }
+    if (X->dtype != RS_F64 && X->dtype != RS_F32) { set_global_error("rs_create: bad dtype"); return RS_EINVAL; }
+  }
   if (!(lambda > 0.0) || !std::isfinite(lambda)) { set_global_error("rs_create: lambda must be > 0"); return RS_EINVAL; }
   if (form != RS_PRIMAL && form != RS_DUAL) { set_global_error("rs_create: bad form"); return RS_EINVAL; }
   if (sketch < RS_GAUSSIAN || sketch > RS_SRHT) { set_global_error("rs_create: bad sketch"); return RS_EINVAL; }
+  if (X->is_csr && form != RS_PRIMAL) { set_global_error("rs_create: a sparse X runs matrix-free in the primal form only"); return RS_EUNSUPPORTED; }
+  if (X->is_csr && sketch != RS_SUBSAMPLE && sketch != RS_COUNT && sketch != RS_SUBCOUNT) {
+    set_global_error("rs_create: a sparse X takes the subsample, count or subcount sketch");
+    return RS_EUNSUPPORTED;
+  }
   rs_opts o;
   rs_default_opts(&o);
   if (opts) o = *opts;
@@ -680,6 +874,8 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   c->seed = seed;
   c->mom = mo;
   c->xdtype = X->dtype;
+  c->sparse = X->is_csr != 0;
+  c->nnz = X->is_csr ? X->nnz : 0;
   const int64_t m = c->m;
   c->tau = tau > 0 ? tau : default_tau(m);
   c->ld = round_up(m, kLdAlign);
@@ -715,7 +911,7 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   }
   c->chunk = o.chunk > 0 ? o.chunk : (c->mixed() ? c->refresh_every : 128);
   if (c->mixed() && c->chunk != c->refresh_every) c->chunk = c->refresh_every;
-  {
+  if (!c->sparse) {
     // keep the per-slot buffers of one chunk under 4 GB
     // (S^T A is materialised for every sketch once the persistent kernel runs it)
     const int64_t per_slot = c->tau * c->ld * (int64_t)c->elem() * (sketch == RS_GAUSSIAN ? 2 : 1) +
@@ -740,6 +936,30 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   c->ctrl_h->r0 = 1.0;
   TRYC(cudaMemcpyAsync(c->ctrl, c->ctrl_h, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
 
+  TRY(dalloc(c, &c->err_flag, 1));
+  TRY(dalloc(c, &c->ndropped, 1));
+  TRYC(cudaMemsetAsync(c->err_flag, 0, sizeof(int32_t), st));
+  TRYC(cudaMemsetAsync(c->ndropped, 0, sizeof(int32_t), st));
+  TRY(dalloc(c, &c->rel_dev, 1));
+  if (c->sparse) {
+    // matrix-free: CSR + CSC of X on the device, b = X^T y; A is never formed
+    TRYC(cudaEventRecord(c->ev0, st));
+    s = with_vt(c, [&](auto tag) -> rs_status {
+      using VT = std::remove_pointer_t<decltype(tag)>;
+      return sparse_setup_t<VT>(c, X, y, y_on_device);
+    });
+    if (s != RS_OK) return fail(s);
+    TRYC(cudaEventRecord(c->ev1, st));
+    // the per-slot XS buffers of a chunk stay under 4 GB
+    const int64_t per_slot = c->mf_rcap * 8 + c->mf_ecap * (4 + (int64_t)c->elem()) +
+                             c->tau * c->tau * 24 + c->ld * 4 + c->mf_nrb * 16;
+    const int64_t cap = std::max<int64_t>(1, (int64_t)4e9 / std::max<int64_t>(per_slot, 1));
+    if (c->chunk > cap) {
+      if (c->mixed()) { c->err = "rs_create: refresh_every too large for the per-iteration buffers"; return fail(RS_EINVAL); }
+      c->chunk = cap;
+      c->nslots = cap;
+    }
+  } else {
   // X, y
   const size_t xel = X->dtype == RS_F32 ? 4 : 8;
   const size_t xbytes = (size_t)X->n * X->d * xel;
@@ -752,7 +972,6 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   TRY(dalloc(c, &c->vd, c->d));
   TRY(dalloc(c, &c->xt_part, std::max<size_t>(xt_part_elems(c->n, c->d),
                                                (size_t)xtx_df_blocks() * c->d)));
-  TRY(dalloc(c, &c->rel_dev, 1));
   // A and b (eqs. (2)-(4))
   TRYC(cudaMalloc(&c->A, (size_t)m * c->ld * c->elem()));
   TRYC(cudaMemsetAsync(c->A, 0, (size_t)m * c->ld * c->elem(), st));
@@ -783,6 +1002,7 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   }
   if (dual) TRYC(cudaMemcpyAsync(c->b, c->y, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
   TRYC(cudaEventRecord(c->ev1, st));
+  }
   // iteration buffers
   TRY(dalloc(c, &c->w, m));
   TRY(dalloc(c, &c->wp, m));
@@ -792,11 +1012,26 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   TRYC(cudaMemsetAsync(c->u, 0, m * sizeof(double), st));
   TRY(dalloc(c, &c->rS, c->tau));
   TRY(dalloc(c, &c->delta, c->tau));
-  TRY(dalloc(c, &c->err_flag, 1));
-  TRY(dalloc(c, &c->ndropped, 1));
-  TRYC(cudaMemsetAsync(c->err_flag, 0, sizeof(int32_t), st));
-  TRYC(cudaMemsetAsync(c->ndropped, 0, sizeof(int32_t), st));
-  if ((sketch == RS_SUBSAMPLE || sketch == RS_COUNT || sketch == RS_SUBCOUNT) && o.iter_ctas >= 0) {
+  if (c->sparse) {
+    // M^+ per slot and the per-slot XS of the chunk
+    const size_t fel = c->f64_factor() ? 8 : 4;
+    const size_t nsl = (size_t)c->nslots;
+    c->pld = round_up(c->tau, 4);
+    c->p_slot = c->tau * c->pld;
+    TRYC(cudaMalloc(&c->Pm, nsl * c->p_slot * fel));
+    TRY(dalloc(c, &c->mf_bsum, nsl * c->mf_nrb * 2));
+    TRY(dalloc(c, &c->mf_boffs, nsl * c->mf_nrb * 2));
+    TRY(dalloc(c, &c->mf_tot, nsl * 2));
+    TRYC(cudaMemsetAsync(c->mf_tot, 0, nsl * 2 * sizeof(int32_t), st));
+    TRY(dalloc(c, &c->mf_crow, nsl * c->mf_rcap));
+    TRY(dalloc(c, &c->mf_cptr, nsl * (c->mf_rcap + 1)));
+    TRY(dalloc(c, &c->mf_ebuck, nsl * c->mf_ecap));
+    TRYC(cudaMalloc(&c->mf_eval, nsl * c->mf_ecap * c->elem()));
+    TRYC(cudaMalloc(&c->mf_v, (size_t)c->n * c->elem()));
+    TRYC(cudaMemsetAsync(c->mf_v, 0, (size_t)c->n * c->elem(), st));
+    TRYC(cudaMalloc(&c->mf_pu, std::max<int64_t>(c->sx_npieces, 1) * c->elem()));
+  }
+  if (!c->sparse && (sketch == RS_SUBSAMPLE || sketch == RS_COUNT || sketch == RS_SUBCOUNT) && o.iter_ctas >= 0) {
     // persistent iteration kernel over the whole GPU: S^T A blocked by CTA, M^+ per
     // slot and the all-reduce buffers
     bool fits = false;
@@ -1186,6 +1421,23 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
   const int ns = (int)c->nslots;
   const double rows = c->sketch == RS_COUNT ? m : (c->sketch == RS_SUBCOUNT ? (double)c->s : tau);
   for (int64_t it = 0; it < reps && s == RS_OK; ++it) {
+    if (c->sparse) {  // matrix-free: phase 1 of the chunk, then one group per iteration
+      if (it % c->chunk == 0) {
+        s = timed("phase1", [&]() -> rs_status {
+          CKC(c, launch_chunk_begin(c->stream, c->ctrl));
+          return enqueue_phase1(c, 0, -1, ns, true);
+        });
+        if (s != RS_OK) break;
+      }
+      s = timed("mf_iter", [&]() { return enqueue_mf_iteration(c); });
+      // per iteration: X restricted to the sampled columns' rows is touched through
+      // the compact rows; X^T v reads every stored entry once
+      grp("mf_iter").bytes = (double)c->nnz * (4.0 + (c->xdtype == RS_BF16 ? 2.0 : (c->xdtype == RS_F32 ? 4.0 : 8.0))) + m * 48.0;
+      grp("mf_iter").iters += 1;
+      if (s == RS_OK && c->mixed() && (it + 1) % c->refresh_every == 0)
+        s = timed("refresh", [&]() { return enqueue_refresh(c); });
+      continue;
+    }
     if (it % c->chunk == 0) {
       const double nsl = (double)std::min<int64_t>(ns, reps - it);
       const PlanView plan = plan_view(c);

@@ -165,6 +165,51 @@ template <typename TF>
 cudaError_t launch_pinv(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, const TF* Linv,
                         int64_t l_slot, int64_t tau, TF* P, int64_t pld, int64_t p_slot);
 
+// ---- matrix-free sparse X (rs_sparse.cu) ----
+constexpr int kPiece = 1024;  // column entries summed by one warp in X^T v
+template <typename VT>
+struct SparseX {
+  int64_t n, d, nnz;
+  const int64_t* rowptr; const int32_t* colidx; const VT* val;  // CSR (rows ascending)
+  const int64_t* colptr; const int32_t* rowidx; const VT* cval; // CSC (rows ascending)
+  const int32_t* pcol; const int64_t* pstart; int64_t npieces;  // pieces of <= kPiece entries
+  const int32_t* cpiece;                                        // d + 1: pieces of column c
+};
+// per-slot XS of a chunk (compact rows that meet the sampled columns) and its scans
+struct MfArgs {
+  int64_t n, d, tau;
+  const int64_t* rowptr; const int32_t* colidx;
+  const int32_t* inv; int64_t inv_slot;        // column -> bucket | sign per slot
+  int32_t* bsum; int32_t* boffs;               // per slot: nrb x 2 block counts / offsets
+  int32_t* tot;                                // per slot: entries E, compact rows R
+  int32_t* crow; int32_t* cptr; int32_t* ebuck;  // rows (rcap), offsets (rcap + 1), buckets (ecap)
+  int64_t nrb, rcap, ecap;
+  double lambda;
+};
+int64_t mf_row_blocks(int64_t n);
+// *err = 1 when the CSR arrays are inconsistent (read-only bounds check)
+cudaError_t launch_csr_check(cudaStream_t st, const int64_t* rowptr, int64_t n,
+                             const int32_t* colidx, int64_t nnz, int64_t d, int32_t* err);
+template <typename VT>
+cudaError_t build_csc(cudaStream_t st, const int64_t* rowptr, int64_t n, const int32_t* colidx,
+                      const VT* val, int64_t nnz, int64_t d, int32_t* table, int nb,
+                      int64_t* colcnt, int64_t* colptr, int32_t* rowidx, VT* cval);
+// out = X^T v (FP64, column pieces; pu: npieces doubles); z = X x (FP64)
+template <typename VT>
+cudaError_t sparse_xtv_d(cudaStream_t st, const SparseX<VT>& X, const double* v, double* out,
+                         double* pu, const int32_t* stop);
+template <typename VT>
+cudaError_t sparse_xv_d(cudaStream_t st, const SparseX<VT>& X, const double* x, double* z,
+                        const int32_t* stop);
+template <typename VT, typename AT>
+cudaError_t launch_mf_phase1(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, MfArgs a,
+                             const VT* val, AT* eval, PlanView plan, double* M, int64_t m_slot);
+struct UpdateArgs;
+template <typename VT, typename AT>
+cudaError_t launch_mf_iteration(cudaStream_t st, Ctrl* ctrl, MfArgs a, const SparseX<VT>& X,
+                                const AT* eval, PlanView plan, const AT* P, int64_t pld,
+                                int64_t p_slot, AT* v, AT* pu, UpdateArgs u, double* rS_out);
+
 // ---- iterate / residual update (rs_update.cu) ----
 struct UpdateArgs {
   const double* gam;  // gamma_k table

@@ -173,3 +173,32 @@ def batched_problem(n: int, d: int, nrhs: int, seed: int, noise: float = 0.1,
     W = g.standard_normal((nrhs, d))
     Y = (X.astype(np.float64) @ W.T).T + noise * g.standard_normal((nrhs, n))
     return X, Y
+
+
+def bf16_round(x) -> np.ndarray:
+    """Values of x rounded to the nearest bfloat16 (ties to even), as float64: the
+    stored data of a bfloat16 design matrix."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def sparse_problem(n: int, d: int, nnz_target: int, seed: int, noise: float = 0.1,
+                   alpha: float = 1.1, bf16: bool = True):
+    """Zipf-sparse design (``zipf_csr``), values rounded to bfloat16 when ``bf16``;
+    w* ~ N(0,1), y = X w* + noise * N(0,1) from the stored values.
+    Returns (rowptr, colidx, vals, y, w_true)."""
+    import scipy.sparse as sp
+
+    rowptr, colidx, vals = zipf_csr(n, d, nnz_target, seed, alpha)
+    if bf16:
+        vals = bf16_round(vals)
+    g = _rng(seed + 7919)
+    w_true = g.standard_normal(d)
+    X = sp.csr_matrix((vals, colidx, rowptr), shape=(n, d))
+    y = X @ w_true + noise * g.standard_normal(n)
+    return rowptr, colidx, vals, y, w_true
+
+
+__all__ += ["bf16_round", "sparse_problem"]
