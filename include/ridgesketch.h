@@ -287,6 +287,52 @@ rs_status rs_profile_iteration(rs_ctx* ctx, int64_t reps, rs_kernel_stat* out, i
 rs_status rs_gram_apply_noalloc(const float* X, int64_t n, int64_t d, const double* v,
                                 double* out, void* stream);
 
+/*
+ * Batch of P independent primal ridge problems with nrhs right-hand sides each,
+ * solved together: the iterations of every problem and right-hand side of a chunk
+ * run in one persistent launch (one CTA per problem), the right-hand sides of a
+ * problem sharing its sketches, S^T A and the small system's pseudo-inverse
+ * (Algorithm 2, eq. (53), applied to A_p W = B_p column by column).
+ *   P        number of problems, >= 1
+ *   Xs       P dense matrices (rs_matrix, is_csr = 0; FP32 for RS_MIXED), copied
+ *   Ys       P pointers; Ys[p] holds nrhs x n_p targets, right-hand side major
+ *            (Ys[p][r * n_p + i]), FP64; device pointers if y_on_device
+ *   nrhs     right-hand sides per problem, 1 <= nrhs <= 8
+ *   lambdas  P regularisers, > 0
+ *   sketch   RS_SUBSAMPLE, RS_COUNT or RS_SUBCOUNT
+ *   taus     P sketch sizes (0 = the rule of rs_create), or NULL for all 0
+ *   mom, opts as for rs_create (opts.cuda_stream: the stream of the whole batch);
+ *            problem p draws its sketches with seed + p
+ *   out      receives the batch; NULL on failure
+ * On failure the message is rs_batch_last_error(NULL).
+ */
+typedef struct rs_batch rs_batch; /* opaque; owned by the library until rs_destroy_batch */
+rs_status rs_create_batch(int32_t P, const rs_matrix* Xs, const double* const* Ys,
+                          int32_t y_on_device, int32_t nrhs, const double* lambdas,
+                          int32_t sketch, const int64_t* taus, const rs_mom* mom, uint64_t seed,
+                          const rs_opts* opts, rs_batch** out);
+/*
+ * Solve every (problem, right-hand side) pair to relative residual tol (each
+ * relative to its own ||b||), at most max_iters iterations per problem.
+ *   W_out      P host pointers; W_out[p] receives nrhs x d_p weights (right-hand side
+ *              major), or NULL to skip
+ *   iters_out  P * nrhs iterations done per pair (pair p * nrhs + r), or NULL
+ *   resid_out  P * nrhs final relative residuals (RS_MIXED: FP64 through X), or NULL
+ * Returns RS_ENOTCONV if some pair did not reach tol (outputs valid), RS_ENUMERIC if
+ * some pair produced NaN/Inf.
+ */
+rs_status rs_solve_batch(rs_batch* b, double tol, int64_t max_iters, double* const* W_out,
+                         int64_t* iters_out, double* resid_out);
+void rs_destroy_batch(rs_batch* b);
+const char* rs_batch_last_error(const rs_batch* b);
+/* setup (all problems' A, B), last solve and autotuner time in ms (the autotuner
+ * runs once, in the first rs_solve_batch, outside its solve time), the CTA size of
+ * the batch's iteration kernel and the number of streams its phase 1 (sketches,
+ * S^T A, M^+ of every problem) is spread over, both chosen by the autotuner. Any
+ * output pointer may be NULL. */
+rs_status rs_batch_info(const rs_batch* b, double* setup_ms, double* solve_ms, double* tune_ms,
+                        int32_t* iter_threads, int32_t* phase1_streams);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,7 +13,7 @@ import os
 
 import numpy as np
 
-__all__ = ["Solver", "RidgeSketch", "RSError", "lib", "SKETCHES", "MOMENTA"]
+__all__ = ["Solver", "Batch", "CSR", "RidgeSketch", "RSError", "lib", "SKETCHES", "MOMENTA"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libridgesketch.so")
@@ -83,6 +83,14 @@ _SIGS = {
     "rs_profile_iteration": (_I32, [_P, _I64, ctypes.POINTER(KernelStat), _I32,
                                     ctypes.POINTER(_I32)]),
     "rs_gram_apply_noalloc": (_I32, [_P, _I64, _I64, _P, _P, _P]),
+    "rs_create_batch": (_I32, [_I32, ctypes.POINTER(Matrix), ctypes.POINTER(_P), _I32, _I32,
+                               ctypes.POINTER(_D), _I32, ctypes.POINTER(_I64), ctypes.POINTER(Mom),
+                               ctypes.c_uint64, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
+    "rs_solve_batch": (_I32, [_P, _D, _I64, ctypes.POINTER(_P), _P, _P]),
+    "rs_destroy_batch": (None, [_P]),
+    "rs_batch_last_error": (ctypes.c_char_p, [_P]),
+    "rs_batch_info": (_I32, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D),
+                             ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -317,6 +325,115 @@ class Solver:
         a, b = _D(), _D()
         self._check(lib().rs_timings(self._ctx, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+
+class Batch:
+    """P independent primal ridge problems, nrhs right-hand sides each, solved together
+    (rs_create_batch / rs_solve_batch / rs_destroy_batch).
+
+    Xs: P dense (n_p, d_p) arrays (float32 for ``precision="mixed"``); Ys: P arrays of
+    shape (nrhs, n_p); lams: P regularisers; taus: P sketch sizes (0 = default rule)
+    or None. Problem p draws its sketches with seed + p.
+    """
+
+    def __init__(self, Xs, Ys, lams, sketch="count", taus=None, momentum="none", seed=0,
+                 precision="fp64", refresh_every=50, sub_s=0, chunk=0, eta=0.995,
+                 beta_switch=0.5, gamma_c=1.0, beta_c=0.5, uncapped=False, device=0, stream=None,
+                 setup_tc=True):
+        L = lib()
+        self._b = None
+        P = len(Xs)
+        if not (len(Ys) == P and len(lams) == P):
+            raise ValueError("Xs, Ys and lams must have one entry per problem")
+        xdt = np.float32 if precision == "mixed" else np.float64
+        mats = (Matrix * P)()
+        self._keep = []
+        yptrs = (_P * P)()
+        nrhs = None
+        self.dims = []
+        for p in range(P):
+            xp, xdev, xk = _buf(Xs[p], xdt)
+            n, d = (int(v) for v in Xs[p].shape)
+            mats[p] = Matrix(0, 1 if xdt == np.float32 else 0, n, d, 0, xp, None, None, xdev)
+            Y = np.ascontiguousarray(Ys[p], dtype=np.float64)
+            if Y.ndim == 1:
+                Y = Y[None, :]
+            if Y.shape[1] != n:
+                raise ValueError(f"Ys[{p}] must have shape (nrhs, {n})")
+            if nrhs is None:
+                nrhs = Y.shape[0]
+            elif Y.shape[0] != nrhs:
+                raise ValueError("every problem needs the same number of right-hand sides")
+            yptrs[p] = Y.ctypes.data
+            self._keep += [xk, Y]
+            self.dims.append(d)
+        lam_a = (_D * P)(*[float(v) for v in lams])
+        tau_a = (_I64 * P)(*[int(v) for v in (taus if taus is not None else [0] * P)])
+        mom = Mom()
+        L.rs_default_mom(ctypes.byref(mom), MOMENTA[momentum])
+        mom.eta, mom.beta_switch, mom.gamma_c, mom.beta_c = eta, beta_switch, gamma_c, beta_c
+        mom.uncapped = int(bool(uncapped))
+        opts = Opts()
+        L.rs_default_opts(ctypes.byref(opts))
+        opts.precision = PRECISIONS[precision]
+        opts.refresh_every = int(refresh_every)
+        opts.sub_s = int(sub_s)
+        opts.device = int(device)
+        opts.chunk = int(chunk)
+        opts.setup_tc = int(bool(setup_tc))
+        opts.cuda_stream = stream if stream is not None else _default_stream(device)
+        b = _P()
+        status = L.rs_create_batch(P, mats, yptrs, 0, int(nrhs), lam_a, SKETCHES[sketch], tau_a,
+                                   ctypes.byref(mom), ctypes.c_uint64(int(seed)), ctypes.byref(opts),
+                                   ctypes.byref(b))
+        if status != RS_OK:
+            raise RSError(status, L.rs_batch_last_error(None).decode())
+        self._b = b
+        self.P, self.nrhs = P, int(nrhs)
+
+    def _check(self, status, allow=(RS_OK,)):
+        if status not in allow:
+            raise RSError(status, lib().rs_batch_last_error(self._b).decode())
+        return status
+
+    def close(self):
+        if self._b is not None:
+            lib().rs_destroy_batch(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, tol=1e-6, max_iters=10000):
+        """Returns (W, iters, resid, converged): W[p] of shape (nrhs, d_p); iters and resid
+        of shape (P, nrhs); converged is True when every pair reached tol."""
+        W = [np.empty((self.nrhs, d)) for d in self.dims]
+        wptr = (_P * self.P)(*[w.ctypes.data for w in W])
+        iters = np.empty(self.P * self.nrhs, np.int64)
+        resid = np.empty(self.P * self.nrhs)
+        st = self._check(lib().rs_solve_batch(self._b, float(tol), int(max_iters), wptr,
+                                              iters.ctypes.data, resid.ctypes.data),
+                         allow=(RS_OK, RS_ENOTCONV))
+        return (W, iters.reshape(self.P, self.nrhs), resid.reshape(self.P, self.nrhs),
+                st == RS_OK)
+
+    def info(self):
+        """dict: setup_ms, solve_ms, tune_ms, iter_threads, phase1_streams."""
+        a, b, c = _D(), _D(), _D()
+        t, ns = _I32(), _I32()
+        self._check(lib().rs_batch_info(self._b, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                        ctypes.byref(t), ctypes.byref(ns)))
+        return {"setup_ms": a.value, "solve_ms": b.value, "tune_ms": c.value,
+                "iter_threads": t.value, "phase1_streams": ns.value}
 
 
 class RidgeSketch:

@@ -66,6 +66,12 @@ namespace rs {
 void set_global_error_msg(const char* msg) { set_global_error(msg ? msg : ""); }
 }  // namespace rs
 
+namespace {
+// set while rs_create_batch creates its member contexts: M^+ per slot is kept for the
+// batch's iteration kernel (the persistent single-problem kernel is not used)
+thread_local bool t_batch_member = false;
+}  // namespace
+
 struct rs_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -98,6 +104,7 @@ struct rs_ctx {
   WidePlan wide{};
   void* Pm = nullptr;       // per slot: M^+ = L^{-T} L^{-1}, tau x pld (factor precision)
   bool sweep_p = false;     // M^+ by FP32 sweeps from an FP32 M (mixed, FP32 factor)
+  bool batch_member = false;  // a problem of an rs_batch (S^T A and M^+ kept per slot)
   float* Mf = nullptr;      // per slot: M in FP32 for the sweeps
   int64_t pld = 0, p_slot = 0;
   uint64_t* xpart = nullptr;   // all-reduce partials, 2 x nblk x (tau + 1) x 2 tagged words
@@ -206,7 +213,7 @@ RowsView<T> rows_view(const rs_ctx* c) {
   RowsView<T> v{};
   v.A = static_cast<const T*>(c->A);
   v.lda = c->ld;
-  v.SA = (c->sketch == RS_SUBSAMPLE && !c->use_wide) ? nullptr : static_cast<const T*>(c->SA);
+  v.SA = (c->sketch == RS_SUBSAMPLE && !c->use_wide && !c->batch_member) ? nullptr : static_cast<const T*>(c->SA);
   v.ldsa = c->ld;
   v.sa_slot = c->sa_slot;
   v.ST = (c->sketch == RS_GAUSSIAN) ? static_cast<const T*>(c->ST) : nullptr;
@@ -302,7 +309,7 @@ rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots, boo
     case RS_SUBSAMPLE:
     case RS_COUNT:
     case RS_SUBCOUNT:
-      if (c->sketch == RS_SUBSAMPLE && !c->use_wide) {  // M = A[C, C] gathered, no S^T A
+      if (c->sketch == RS_SUBSAMPLE && !c->use_wide && !c->batch_member) {  // M = A[C, C] gathered
         CKC(c, launch_msys_batched<T>(st, c->ctrl, force, nslots, plan, rows_view<T>(c), c->m,
                                       c->tau, c->M, c->m_slot));
         break;
@@ -875,6 +882,7 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   c->mom = mo;
   c->xdtype = X->dtype;
   c->sparse = X->is_csr != 0;
+  c->batch_member = t_batch_member;
   c->nnz = X->is_csr ? X->nnz : 0;
   const int64_t m = c->m;
   c->tau = tau > 0 ? tau : default_tau(m);
@@ -1031,7 +1039,16 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     TRYC(cudaMemsetAsync(c->mf_v, 0, (size_t)c->n * c->elem(), st));
     TRYC(cudaMalloc(&c->mf_pu, std::max<int64_t>(c->sx_npieces, 1) * c->elem()));
   }
-  if (!c->sparse && (sketch == RS_SUBSAMPLE || sketch == RS_COUNT || sketch == RS_SUBCOUNT) && o.iter_ctas >= 0) {
+  if (t_batch_member && !c->sparse) {
+    const size_t fel = c->f64_factor() ? 8 : 4;
+    c->pld = round_up(c->tau, 4);
+    c->p_slot = c->tau * c->pld;
+    TRYC(cudaMalloc(&c->Pm, (size_t)c->nslots * c->p_slot * fel));
+    c->sweep_p = c->mixed() && !c->f64_factor() && c->tau <= kSweepMaxTau &&
+                 sa_msys_fits<float>(m, c->tau, round_up((sketch == RS_COUNT) ? m : (sketch == RS_SUBCOUNT ? c->s : c->tau), 4));
+    if (c->sweep_p) TRY(dalloc(c, &c->Mf, (size_t)c->nslots * c->tau * c->tau));
+  }
+  if (!t_batch_member && !c->sparse && (sketch == RS_SUBSAMPLE || sketch == RS_COUNT || sketch == RS_SUBCOUNT) && o.iter_ctas >= 0) {
     // persistent iteration kernel over the whole GPU: S^T A blocked by CTA, M^+ per
     // slot and the all-reduce buffers
     bool fits = false;
@@ -1065,7 +1082,7 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     if (c->use_wide)
       c->sa_slot = (m + c->wide.q - 1) / c->wide.q * c->tau * round_up(c->wide.q, 4);
     else
-      c->sa_slot = (sketch == RS_SUBSAMPLE) ? 0 : c->tau * c->ld;
+      c->sa_slot = (sketch == RS_SUBSAMPLE && !c->batch_member) ? 0 : c->tau * c->ld;
     c->m_slot = c->tau * c->tau;
     c->l_slot = c->tau * c->tau;
     const size_t nsl = (size_t)c->nslots;
@@ -1588,6 +1605,566 @@ rs_status rs_timings(const rs_ctx* c, double* setup_ms, double* solve_ms) {
   if (!c) return RS_EINVAL;
   if (setup_ms) *setup_ms = c->setup_ms;
   if (solve_ms) *solve_ms = c->solve_ms;
+  return RS_OK;
+}
+
+}  // extern "C"
+
+
+// ===========================================================================
+// batches of problems (rs_create_batch / rs_solve_batch)
+//
+// Problem p is a member context (A_p, b_p of its first right-hand side, its sketch
+// sequence seed + p, per-slot S^T A and M^+); its right-hand sides share them. One
+// chunk of the batch, captured once as a CUDA graph:
+//   phase 1 of every member (chunk_begin, plans, S^T A and M, M^+), spread over
+//   side streams by balanced d^2 (longest first);
+//   the batch's persistent iteration kernel (CTA per problem);
+//   mixed: w in FP64, X^T X w per pair through X on the member's stream, the FP64
+//   refresh of every pair;
+//   the finish kernel (problems whose pairs are all done stop; counts for the host).
+// The autotuner times whole chunks for each (iteration CTA size, side streams)
+// candidate on the first solve and keeps the fastest.
+// ===========================================================================
+struct rs_batch {
+  int P = 0, nrhs = 0;
+  int precision = 0;
+  int64_t chunk = 50, tau_max = 1;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<rs_ctx*> mem;            // one member context per problem
+  std::vector<unsigned char*> state;   // per problem: 48 bytes per (right-hand side, coordinate)
+  void* probs = nullptr;               // device BatchProb (plain) or BatchProbM (mixed) array
+  void* refs = nullptr;                // device BatchRef or BatchRefM array, P * nrhs
+  rs::Ctrl** ctrls = nullptr;          // device: the members' control blocks
+  int32_t *flag = nullptr, *skip = nullptr;
+  int64_t* iters = nullptr;
+  double *r0 = nullptr, *resid = nullptr;
+  double* tol = nullptr;               // device: tolerance of the current solve
+  int32_t* fin = nullptr;              // device: problems running, failed pairs
+  int32_t* fin_h = nullptr;            // pinned copy
+  std::vector<cudaStream_t> side;      // phase-1 fan-out streams
+  std::vector<cudaEvent_t> evs;        // fork / join events (timing disabled)
+  cudaGraphExec_t graph = nullptr;
+  const double* graph_gam = nullptr;   // momentum table the graph was captured with
+  int graph_threads = 0, graph_streams = 0;
+  bool tuned = false;
+  int threads = 256;                   // CTA size of the iteration kernel (tuned)
+  int nstreams = 1;                    // side streams of phase 1 (tuned)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double setup_ms = 0.0, solve_ms = 0.0, tune_ms = 0.0;
+  std::string err;
+  bool mixed() const { return precision == RS_MIXED; }
+};
+
+namespace {
+
+std::string g_batch_err;
+constexpr int kBatchMaxStreams = 4;
+
+rs::BatchPairs batch_pairs(const rs_batch* b) {
+  rs::BatchPairs p{};
+  p.flag = b->flag; p.skip = b->skip; p.iters = b->iters; p.r0 = b->r0; p.resid = b->resid;
+  return p;
+}
+
+void batch_free(rs_batch* b) {
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (rs_ctx* c : b->mem) rs_destroy(c);
+  for (unsigned char* p : b->state) if (p) cudaFree(p);
+  void* ptrs[] = {b->probs, b->refs, b->ctrls, b->flag, b->skip, b->iters, b->r0, b->resid, b->tol, b->fin};
+  for (void* p : ptrs) if (p) cudaFree(p);
+  if (b->fin_h) cudaFreeHost(b->fin_h);
+  for (cudaStream_t s : b->side) if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->evs) if (e) cudaEventDestroy(e);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+#define BKC(call)                                                                 \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      b->err = std::string(#call) + ": " + cudaGetErrorString(e_);                \
+      return (e_ == cudaErrorMemoryAllocation) ? RS_ENOMEM : RS_ECUDA;             \
+    }                                                                             \
+  } while (0)
+
+// byte offsets of the per-problem state (v = nrhs * d entries per array):
+//   plain  w, w_prev, r, r_prev, b (FP64 each; the sixth array unused)
+//   mixed  w (float pair), r (float pair), Delta_w, Delta_r (FP32), w (FP64), b, X^T X w
+rs_status batch_upload(rs_batch* b) {
+  const size_t np = (size_t)b->P * b->nrhs;
+  std::vector<rs::Ctrl*> ctrls(b->P);
+  for (int p = 0; p < b->P; ++p) ctrls[p] = b->mem[p]->ctrl;
+  BKC(cudaMalloc(&b->ctrls, b->P * sizeof(rs::Ctrl*)));
+  BKC(cudaMemcpy(b->ctrls, ctrls.data(), b->P * sizeof(rs::Ctrl*), cudaMemcpyHostToDevice));
+  auto fill_common = [&](auto& q, const rs_ctx* c) {
+    q.d = c->m; q.tau = c->tau; q.ld = c->ld; q.sa_slot = c->sa_slot; q.pld = c->pld;
+    q.p_slot = c->p_slot; q.perm_stride = c->perm_stride; q.boff_stride = c->boff_stride;
+    q.inv_slot = c->ld;
+    q.perm = c->perm; q.boff = c->boff; q.inv = c->inv;
+    q.ctrl = c->ctrl;
+  };
+  if (b->mixed()) {
+    std::vector<rs::BatchProbM> h(b->P);
+    std::vector<rs::BatchRefM> f(np);
+    for (int p = 0; p < b->P; ++p) {
+      const rs_ctx* c = b->mem[p];
+      const size_t v = (size_t)b->nrhs * c->m;
+      unsigned char* base = b->state[p];
+      rs::BatchProbM& q = h[p];
+      fill_common(q, c);
+      q.SA = static_cast<const float*>(c->SA); q.P = static_cast<const float*>(c->Pm);
+      q.w = reinterpret_cast<float2*>(base);
+      q.r = reinterpret_cast<float2*>(base + 8 * v);
+      q.dw = reinterpret_cast<float*>(base + 16 * v);
+      q.dr = reinterpret_cast<float*>(base + 20 * v);
+      for (int r = 0; r < b->nrhs; ++r) {
+        rs::BatchRefM& g = f[(size_t)p * b->nrhs + r];
+        const size_t o = (size_t)r * c->m;
+        g.d = c->m; g.pair = p * b->nrhs + r; g.lambda = c->lambda;
+        g.w2 = q.w + o; g.r2 = q.r + o; g.dw = q.dw + o; g.dr = q.dr + o;
+        g.wd = reinterpret_cast<double*>(base + 24 * v) + o;
+        g.b = reinterpret_cast<const double*>(base + 32 * v) + o;
+        g.v = reinterpret_cast<const double*>(base + 40 * v) + o;
+      }
+    }
+    BKC(cudaMalloc(&b->probs, h.size() * sizeof(h[0])));
+    BKC(cudaMemcpy(b->probs, h.data(), h.size() * sizeof(h[0]), cudaMemcpyHostToDevice));
+    BKC(cudaMalloc(&b->refs, f.size() * sizeof(f[0])));
+    BKC(cudaMemcpy(b->refs, f.data(), f.size() * sizeof(f[0]), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<rs::BatchProb<double, double>> h(b->P);
+    std::vector<rs::BatchRef> f(np);
+    for (int p = 0; p < b->P; ++p) {
+      const rs_ctx* c = b->mem[p];
+      const size_t v = (size_t)b->nrhs * c->m;
+      double* base = reinterpret_cast<double*>(b->state[p]);
+      rs::BatchProb<double, double>& q = h[p];
+      fill_common(q, c);
+      q.SA = static_cast<const double*>(c->SA); q.P = static_cast<const double*>(c->Pm);
+      q.w = base; q.wp = base + v; q.r = base + 2 * v; q.rp = base + 3 * v;
+      for (int r = 0; r < b->nrhs; ++r) {
+        rs::BatchRef& g = f[(size_t)p * b->nrhs + r];
+        const size_t o = (size_t)r * c->m;
+        g.d = c->m; g.pair = p * b->nrhs + r; g.lambda = c->lambda;
+        g.w = q.w + o; g.wp = q.wp + o; g.r = q.r + o; g.rp = q.rp + o; g.b = base + 4 * v + o;
+      }
+    }
+    BKC(cudaMalloc(&b->probs, h.size() * sizeof(h[0])));
+    BKC(cudaMemcpy(b->probs, h.data(), h.size() * sizeof(h[0]), cudaMemcpyHostToDevice));
+    BKC(cudaMalloc(&b->refs, f.size() * sizeof(f[0])));
+    BKC(cudaMemcpy(b->refs, f.data(), f.size() * sizeof(f[0]), cudaMemcpyHostToDevice));
+  }
+  return RS_OK;
+}
+
+// fresh state of every pair and every member's control block (k = 0)
+rs_status batch_reset(rs_batch* b, double tol, int64_t max_iters) {
+  const rs::BatchPairs pr = batch_pairs(b);
+  const int np = b->P * b->nrhs;
+  if (b->mixed())
+    BKC(rs::launch_batch_mixed_aux(b->stream, 0, static_cast<const rs::BatchRefM*>(b->refs), np, pr, b->tol));
+  else
+    BKC(rs::launch_batch_init(b->stream, static_cast<const rs::BatchRef*>(b->refs), np, pr));
+  BKC(cudaMemcpyAsync(b->tol, &tol, sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  for (rs_ctx* c : b->mem) {
+    std::memset(c->ctrl_h, 0, sizeof(rs::Ctrl));
+    c->ctrl_h->max_iters = max_iters;
+    c->ctrl_h->r0 = 1.0;
+    c->ctrl_h->tol = tol;
+    BKC(cudaMemcpyAsync(c->ctrl, c->ctrl_h, sizeof(rs::Ctrl), cudaMemcpyHostToDevice, b->stream));
+  }
+  BKC(cudaStreamSynchronize(b->stream));
+  return RS_OK;
+}
+
+// problem p's phase-1 stream: longest processing time first over d_p^2
+std::vector<int> batch_owners(const rs_batch* b, int ns) {
+  std::vector<int> order(b->P), owner(b->P, 0);
+  for (int p = 0; p < b->P; ++p) order[p] = p;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return b->mem[x]->m > b->mem[y]->m; });
+  std::vector<double> load(ns, 0.0);
+  for (int p : order) {
+    int best = 0;
+    for (int i = 1; i < ns; ++i) if (load[i] < load[best]) best = i;
+    owner[p] = best;
+    load[best] += (double)b->mem[p]->m * (double)b->mem[p]->m;
+  }
+  return owner;
+}
+
+rs_status batch_fork(rs_batch* b, int ns, int ev) {
+  if (ns <= 1) return RS_OK;
+  BKC(cudaEventRecord(b->evs[ev], b->stream));
+  for (int i = 1; i < ns; ++i) BKC(cudaStreamWaitEvent(b->side[i - 1], b->evs[ev], 0));
+  return RS_OK;
+}
+
+rs_status batch_join(rs_batch* b, int ns, int ev) {
+  for (int i = 1; i < ns; ++i) {
+    BKC(cudaEventRecord(b->evs[ev + i], b->side[i - 1]));
+    BKC(cudaStreamWaitEvent(b->stream, b->evs[ev + i], 0));
+  }
+  return RS_OK;
+}
+
+// one chunk of the whole batch (enqueued on b->stream, or captured from it)
+rs_status batch_enqueue_chunk(rs_batch* b, int threads, int ns) {
+  const std::vector<int> owner = batch_owners(b, ns);
+  auto stream_of = [&](int p) { return owner[p] == 0 ? b->stream : b->side[owner[p] - 1]; };
+  const rs::BatchPairs pr = batch_pairs(b);
+  const int np = b->P * b->nrhs;
+  rs_status s;
+  if ((s = batch_fork(b, ns, 0)) != RS_OK) return s;
+  for (int p = 0; p < b->P; ++p) {
+    rs_ctx* c = b->mem[p];
+    cudaStream_t st = stream_of(p);
+    BKC(launch_chunk_begin(st, c->ctrl));
+    c->stream = st;
+    s = enqueue_phase1(c, 0, -1, (int)c->nslots, true);
+    c->stream = b->stream;
+    if (s != RS_OK) { b->err = c->err; return s; }
+  }
+  if ((s = batch_join(b, ns, 0)) != RS_OK) return s;
+  const double* gam = b->mem[0]->gam;
+  const double* bet = b->mem[0]->bet;
+  if (b->mixed()) {
+    const rs::BatchRefM* refs = static_cast<const rs::BatchRefM*>(b->refs);
+    BKC(rs::launch_batch_iterate_mixed(b->stream, static_cast<const rs::BatchProbM*>(b->probs), b->P,
+                                       b->nrhs, pr, gam, bet, b->chunk, b->tol, b->tau_max, threads));
+    // FP64 refresh: w in FP64, X^T X w per pair through X, r = X^T X w + lambda w - b
+    BKC(rs::launch_batch_mixed_aux(b->stream, 1, refs, np, pr, b->tol));
+    if ((s = batch_fork(b, ns, kBatchMaxStreams)) != RS_OK) return s;
+    for (int p = 0; p < b->P; ++p) {
+      rs_ctx* c = b->mem[p];
+      const size_t v = (size_t)b->nrhs * c->m;
+      const double* wd = reinterpret_cast<const double*>(b->state[p] + 24 * v);
+      double* xv = reinterpret_cast<double*>(b->state[p] + 40 * v);
+      for (int r = 0; r < b->nrhs; ++r)
+        BKC(launch_xtx_v_df(stream_of(p), static_cast<const float*>(c->X), c->n, c->d,
+                            wd + (size_t)r * c->m, xv + (size_t)r * c->m, c->xt_part,
+                            b->skip + p * b->nrhs + r));
+    }
+    if ((s = batch_join(b, ns, kBatchMaxStreams)) != RS_OK) return s;
+    BKC(rs::launch_batch_mixed_aux(b->stream, 3, refs, np, pr, b->tol));
+  } else {
+    BKC(rs::launch_batch_iterate(b->stream, static_cast<const rs::BatchProb<double, double>*>(b->probs),
+                                 b->P, b->nrhs, pr, gam, bet, b->chunk, b->tol, b->tau_max, threads));
+  }
+  BKC(rs::launch_batch_finish(b->stream, b->ctrls, b->P, b->nrhs, pr, b->fin));
+  return RS_OK;
+}
+
+rs_status batch_build_graph(rs_batch* b, int threads, int ns) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  BKC(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
+  const rs_status s = batch_enqueue_chunk(b, threads, ns);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  if (s != RS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    b->err = std::string("batch graph capture: ") + cudaGetErrorString(e);
+    return RS_ECUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    b->graph = nullptr;
+    b->err = std::string("batch graph instantiate: ") + cudaGetErrorString(ei);
+    return RS_ECUDA;
+  }
+  b->graph_gam = b->mem[0]->gam;
+  b->graph_threads = threads;
+  b->graph_streams = ns;
+  return RS_OK;
+}
+
+// replay chunks until every problem has stopped (at most max_replays)
+rs_status batch_run(rs_batch* b, int64_t max_replays) {
+  for (int64_t q = 0; q < max_replays; ++q) {
+    BKC(cudaGraphLaunch(b->graph, b->stream));
+    BKC(cudaMemcpyAsync(b->fin_h, b->fin, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream));
+    BKC(cudaStreamSynchronize(b->stream));
+    if (b->fin_h[0] == 0) return RS_OK;
+  }
+  return RS_OK;
+}
+
+// autotuner: one steady-state chunk (tol = 0, no pair stops) per candidate CTA size
+// of the iteration kernel and number of phase-1 streams; keeps the fastest
+rs_status batch_tune(rs_batch* b) {
+  const int thr[] = {128, 256, 512};
+  const int nss[] = {1, 2, kBatchMaxStreams};
+  float best = -1.f;
+  int bt = 256, bs = 1;
+  rs_status s;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  BKC(cudaEventCreate(&e0));
+  BKC(cudaEventCreate(&e1));
+  auto done = [&](rs_status r) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return r;
+  };
+  for (int ns : nss) {
+    if (ns > 1 && ns > b->P) continue;
+    for (int t : thr) {
+      if ((s = batch_reset(b, 0.0, 2 * b->chunk)) != RS_OK) return done(s);
+      if ((s = batch_build_graph(b, t, ns)) != RS_OK) return done(s);
+      cudaError_t e = cudaGraphLaunch(b->graph, b->stream);  // first replay: uploads the graph
+      if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+      if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, b->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        b->err = std::string("batch autotuner: ") + cudaGetErrorString(e);
+        return done(RS_ECUDA);
+      }
+      if (best < 0.f || ms < best) { best = ms; bt = t; bs = ns; }
+    }
+  }
+  b->threads = bt;
+  b->nstreams = bs;
+  b->tuned = true;
+  return done(RS_OK);
+}
+
+}  // namespace
+
+namespace {
+
+// members, state, B of every right-hand side, device pair arrays
+rs_status batch_init(rs_batch* b, const rs_matrix* Xs, const double* const* Ys,
+                     int32_t y_on_device, const double* lambdas, int32_t sketch,
+                     const int64_t* taus, const rs_mom* mom, uint64_t seed, rs_opts o) {
+  const int P = b->P, nrhs = b->nrhs;
+  if (o.cuda_stream) {
+    b->stream = static_cast<cudaStream_t>(o.cuda_stream);
+  } else {
+    BKC(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    b->own_stream = true;
+  }
+  BKC(cudaEventCreate(&b->ev0));
+  BKC(cudaEventCreate(&b->ev1));
+  b->side.assign(kBatchMaxStreams - 1, nullptr);
+  for (cudaStream_t& s : b->side) BKC(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  b->evs.assign(2 * kBatchMaxStreams, nullptr);
+  for (cudaEvent_t& e : b->evs) BKC(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  o.cuda_stream = b->stream;
+  o.iter_ctas = -1;
+  BKC(cudaEventRecord(b->ev0, b->stream));
+  // member contexts: A_p, b_p of the first right-hand side, per-slot buffers with M^+.
+  // The members share one chunk length: where the memory cap shortened some
+  // members' chunks, all are made again with the shortest.
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    for (rs_ctx* c : b->mem) rs_destroy(c);
+    b->mem.assign(P, nullptr);
+    for (int p = 0; p < P; ++p) {
+      rs_ctx* c = nullptr;
+      t_batch_member = true;
+      const rs_status s = rs_create(&Xs[p], Ys[p], y_on_device, lambdas[p], RS_PRIMAL, sketch,
+                                    taus ? taus[p] : 0, mom, seed + (uint64_t)p, &o, &c);
+      t_batch_member = false;
+      if (s != RS_OK) {
+        b->err = std::string("problem ") + std::to_string(p) + ": " + rs_last_error(nullptr);
+        return s;
+      }
+      b->mem[p] = c;
+    }
+    int64_t lo = b->mem[0]->chunk, hi = lo;
+    for (rs_ctx* c : b->mem) {
+      lo = std::min<int64_t>(lo, c->chunk);
+      hi = std::max<int64_t>(hi, c->chunk);
+    }
+    if (lo == hi) break;
+    if (attempt == 1) { b->err = "rs_create_batch: members with different chunks"; return RS_EINVAL; }
+    o.chunk = lo;
+  }
+  b->chunk = b->mem[0]->chunk;
+  for (rs_ctx* c : b->mem) b->tau_max = std::max<int64_t>(b->tau_max, c->tau);
+  // per-problem state; B = X^T Y of every right-hand side (FP64)
+  b->state.assign(P, nullptr);
+  int64_t nmax = 0;
+  for (rs_ctx* c : b->mem) nmax = std::max<int64_t>(nmax, c->n);
+  double* ytmp = nullptr;
+  BKC(cudaMalloc(&ytmp, (size_t)nmax * sizeof(double)));
+  rs_status s = RS_OK;
+  for (int p = 0; p < P && s == RS_OK; ++p) {
+    rs_ctx* c = b->mem[p];
+    const size_t v = (size_t)nrhs * c->m;
+    cudaError_t e = cudaMalloc(&b->state[p], 48 * v);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->state[p], 0, 48 * v, b->stream);
+    double* bp = reinterpret_cast<double*>(b->state[p] + 32 * v);
+    for (int r = 0; r < nrhs && e == cudaSuccess; ++r) {
+      e = cudaMemcpyAsync(ytmp, Ys[p] + (size_t)r * c->n, (size_t)c->n * sizeof(double),
+                          y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream);
+      if (e != cudaSuccess) break;
+      if (c->xdtype == RS_F32)
+        e = launch_xt_v<float>(b->stream, static_cast<const float*>(c->X), c->n, c->d, ytmp,
+                               bp + (size_t)r * c->m, c->xt_part);
+      else
+        e = launch_xt_v<double>(b->stream, static_cast<const double*>(c->X), c->n, c->d, ytmp,
+                                bp + (size_t)r * c->m, c->xt_part);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // ytmp reused
+    if (e != cudaSuccess) {
+      b->err = std::string("rs_create_batch: B of problem ") + std::to_string(p) + ": " + cudaGetErrorString(e);
+      s = (e == cudaErrorMemoryAllocation) ? RS_ENOMEM : RS_ECUDA;
+    }
+  }
+  cudaFree(ytmp);
+  if (s != RS_OK) return s;
+  const size_t np = (size_t)P * nrhs;
+  BKC(cudaMalloc(&b->flag, np * sizeof(int32_t)));
+  BKC(cudaMalloc(&b->skip, np * sizeof(int32_t)));
+  BKC(cudaMalloc(&b->iters, np * sizeof(int64_t)));
+  BKC(cudaMalloc(&b->r0, np * sizeof(double)));
+  BKC(cudaMalloc(&b->resid, np * sizeof(double)));
+  BKC(cudaMalloc(&b->tol, sizeof(double)));
+  BKC(cudaMalloc(&b->fin, 2 * sizeof(int32_t)));
+  BKC(cudaMallocHost(&b->fin_h, 2 * sizeof(int32_t)));
+  if ((s = batch_upload(b)) != RS_OK) return s;
+  BKC(cudaEventRecord(b->ev1, b->stream));
+  BKC(cudaEventSynchronize(b->ev1));
+  float ms = 0.f;
+  BKC(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+  b->setup_ms = ms;
+  return RS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rs_status rs_create_batch(int32_t P, const rs_matrix* Xs, const double* const* Ys,
+                          int32_t y_on_device, int32_t nrhs, const double* lambdas,
+                          int32_t sketch, const int64_t* taus, const rs_mom* mom, uint64_t seed,
+                          const rs_opts* opts, rs_batch** out) {
+  if (out) *out = nullptr;
+  if (P < 1 || !Xs || !Ys || !lambdas || !out) { g_batch_err = "rs_create_batch: null argument or P < 1"; return RS_EINVAL; }
+  if (nrhs < 1 || nrhs > 8) { g_batch_err = "rs_create_batch: nrhs must be in [1, 8]"; return RS_EINVAL; }
+  if (sketch != RS_SUBSAMPLE && sketch != RS_COUNT && sketch != RS_SUBCOUNT) {
+    g_batch_err = "rs_create_batch: the batch takes the subsample, count or subcount sketch";
+    return RS_EUNSUPPORTED;
+  }
+  rs_opts o;
+  rs_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.precision == RS_MIXED) o.chol_fp64 = 0;
+  for (int p = 0; p < P; ++p) {
+    if (Xs[p].is_csr) { g_batch_err = "rs_create_batch: dense X only"; return RS_EUNSUPPORTED; }
+    if (o.precision == RS_MIXED && Xs[p].dtype != RS_F32) { g_batch_err = "rs_create_batch: RS_MIXED takes FP32 X"; return RS_EINVAL; }
+    if (!Ys[p]) { g_batch_err = "rs_create_batch: null targets"; return RS_EINVAL; }
+  }
+  rs_batch* b = new (std::nothrow) rs_batch();
+  if (!b) { g_batch_err = "rs_create_batch: out of host memory"; return RS_ENOMEM; }
+  DeviceGuard dg(o.device);
+  b->P = P;
+  b->nrhs = nrhs;
+  b->precision = o.precision;
+  const rs_status s = batch_init(b, Xs, Ys, y_on_device, lambdas, sketch, taus, mom, seed, o);
+  if (s != RS_OK) {
+    g_batch_err = b->err;
+    batch_free(b);
+    delete b;
+    return s;
+  }
+  g_batch_err.clear();
+  *out = b;
+  return RS_OK;
+}
+
+rs_status rs_solve_batch(rs_batch* b, double tol, int64_t max_iters, double* const* W_out,
+                         int64_t* iters_out, double* resid_out) {
+  if (!b) { g_batch_err = "rs_solve_batch: null batch"; return RS_EINVAL; }
+  if (max_iters < 0 || !(tol >= 0.0)) { b->err = "rs_solve_batch: bad tol or max_iters"; return RS_EINVAL; }
+  DeviceGuard dg(b->mem[0]->device);
+  rs_status s;
+  rs_ctx* c0 = b->mem[0];
+  if ((s = ensure_schedule(c0, std::max<int64_t>(max_iters, 2 * b->chunk))) != RS_OK) { b->err = c0->err; return s; }
+  if (!b->tuned) {
+    BKC(cudaEventRecord(b->ev0, b->stream));
+    if ((s = batch_tune(b)) != RS_OK) return s;
+    BKC(cudaEventRecord(b->ev1, b->stream));
+    BKC(cudaEventSynchronize(b->ev1));
+    float ms = 0.f;
+    BKC(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+    b->tune_ms = ms;
+  }
+  if (!b->graph || b->graph_gam != c0->gam || b->graph_threads != b->threads ||
+      b->graph_streams != b->nstreams)
+    if ((s = batch_build_graph(b, b->threads, b->nstreams)) != RS_OK) return s;
+  if ((s = batch_reset(b, tol, max_iters)) != RS_OK) return s;
+  BKC(cudaEventRecord(b->ev0, b->stream));
+  if (max_iters > 0 && (s = batch_run(b, max_iters + 2)) != RS_OK) return s;
+  BKC(cudaEventRecord(b->ev1, b->stream));
+  BKC(cudaEventSynchronize(b->ev1));
+  float ms = 0.f;
+  BKC(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+  b->solve_ms = ms;
+  const int np = b->P * b->nrhs;
+  if (b->mixed())
+    BKC(rs::launch_batch_mixed_aux(b->stream, 2, static_cast<const rs::BatchRefM*>(b->refs), np,
+                                   batch_pairs(b), b->tol));
+  for (int p = 0; p < b->P; ++p) {
+    const rs_ctx* c = b->mem[p];
+    int32_t gen_err = 0;
+    BKC(cudaMemcpy(&gen_err, c->err_flag, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (gen_err) { b->err = "sketch generation: sample threshold search failed"; return RS_ECUDA; }
+    if (!W_out || !W_out[p]) continue;
+    const size_t v = (size_t)b->nrhs * c->m;
+    const unsigned char* src = b->state[p] + (b->mixed() ? 24 * v : 0);
+    BKC(cudaMemcpyAsync(W_out[p], src, v * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  }
+  std::vector<int32_t> flag(np);
+  BKC(cudaMemcpyAsync(flag.data(), b->flag, np * sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream));
+  if (iters_out) BKC(cudaMemcpyAsync(iters_out, b->iters, np * sizeof(int64_t), cudaMemcpyDeviceToHost, b->stream));
+  if (resid_out) BKC(cudaMemcpyAsync(resid_out, b->resid, np * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  BKC(cudaStreamSynchronize(b->stream));
+  bool nan = false, open = false;
+  for (int32_t f : flag) {
+    nan |= (f == 3);
+    open |= (f < 2);
+  }
+  if (nan) { b->err = "rs_solve_batch: NaN or Inf in a residual"; return RS_ENUMERIC; }
+  return open ? RS_ENOTCONV : RS_OK;
+}
+
+void rs_destroy_batch(rs_batch* b) {
+  if (!b) return;
+  {
+    DeviceGuard dg(b->mem.empty() || !b->mem[0] ? 0 : b->mem[0]->device);
+    batch_free(b);
+  }
+  delete b;
+}
+
+const char* rs_batch_last_error(const rs_batch* b) {
+  return b ? b->err.c_str() : g_batch_err.c_str();
+}
+
+rs_status rs_batch_info(const rs_batch* b, double* setup_ms, double* solve_ms, double* tune_ms,
+                        int32_t* iter_threads, int32_t* phase1_streams) {
+  if (!b) return RS_EINVAL;
+  if (setup_ms) *setup_ms = b->setup_ms;
+  if (solve_ms) *solve_ms = b->solve_ms;
+  if (tune_ms) *tune_ms = b->tune_ms;
+  if (iter_threads) *iter_threads = b->threads;
+  if (phase1_streams) *phase1_streams = b->nstreams;
   return RS_OK;
 }
 

@@ -210,6 +210,56 @@ cudaError_t launch_mf_iteration(cudaStream_t st, Ctrl* ctrl, MfArgs a, const Spa
                                 const AT* eval, PlanView plan, const AT* P, int64_t pld,
                                 int64_t p_slot, AT* v, AT* pu, UpdateArgs u, double* rS_out);
 
+// ---- many problems, several right-hand sides each (rs_batch.cu) ----
+template <typename T, typename TF>
+struct BatchProb {
+  int64_t d, tau, ld, sa_slot, pld, p_slot, perm_stride, boff_stride, inv_slot;
+  const T* SA; const TF* P;                       // per slot: S^T A (tau x ld), M^+ (tau x pld)
+  const int32_t* perm; const int32_t* boff; const int32_t* inv;  // per slot: plan, row map
+  double *w, *wp, *r, *rp;                        // nrhs x d each (right-hand side major)
+  Ctrl* ctrl;                                     // the problem's control block (k, k0, stop)
+};
+struct BatchPairs {        // per (problem, right-hand side)
+  int32_t* flag;           // 0 active, 1 pending (FP64 check due), 2 converged, 3 failed
+  int32_t* skip;           // 1: no refresh (converged or failed)
+  int64_t* iters;          // iterations done
+  double* r0;              // ||b||
+  double* resid;           // last relative residual
+};
+struct BatchRef {          // state of one pair (plain FP64)
+  int64_t d; int pair; double lambda;
+  double* w; double* wp; const double* b; double* r; double* rp;
+};
+struct BatchProbM {        // mixed precision: float-pair state, FP32 increments
+  int64_t d, tau, ld, sa_slot, pld, p_slot, perm_stride, boff_stride, inv_slot;
+  const float* SA; const float* P;
+  const int32_t* perm; const int32_t* boff; const int32_t* inv;
+  float2 *w, *r;                                  // nrhs x d each: hi, lo
+  float *dw, *dr;                                 // nrhs x d each: last increments
+  Ctrl* ctrl;
+};
+struct BatchRefM {        // state of one pair (mixed)
+  int64_t d; int pair; double lambda;
+  float2* w2; float2* r2; float* dw; float* dr;   // the pair's state
+  double* wd; const double* v; const double* b;   // w in FP64, X^T X w, b
+};
+cudaError_t launch_batch_iterate_mixed(cudaStream_t st, const BatchProbM* probs, int P, int nrhs,
+                                       BatchPairs pairs, const double* gam, const double* bet,
+                                       int64_t chunk, const double* tol, int64_t tau_max,
+                                       int threads);
+// what: 0 init state and r0, 1 w -> FP64 (active pairs), 2 w -> FP64 (all), 3 refresh
+cudaError_t launch_batch_mixed_aux(cudaStream_t st, int what, const BatchRefM* refs, int npairs,
+                                   BatchPairs pairs, const double* tol);
+// plain FP64: FP64 state, S^T A and M^+ in FP64
+size_t batch_iterate_smem(int64_t tau_max, int nrhs);
+cudaError_t launch_batch_iterate(cudaStream_t st, const BatchProb<double, double>* probs, int P,
+                                 int nrhs, BatchPairs pairs, const double* gam, const double* bet,
+                                 int64_t chunk, const double* tol, int64_t tau_max, int threads);
+cudaError_t launch_batch_init(cudaStream_t st, const BatchRef* refs, int npairs, BatchPairs pairs);
+
+cudaError_t launch_batch_finish(cudaStream_t st, Ctrl* const* ctrls, int P, int nrhs,
+                                BatchPairs pairs, int32_t* out);
+
 // ---- iterate / residual update (rs_update.cu) ----
 struct UpdateArgs {
   const double* gam;  // gamma_k table
