@@ -332,6 +332,18 @@ const char* rs_batch_last_error(const rs_batch* b);
  * output pointer may be NULL. */
 rs_status rs_batch_info(const rs_batch* b, double* setup_ms, double* solve_ms, double* tune_ms,
                         int32_t* iter_threads, int32_t* phase1_streams);
+/* Fix the launch shape instead of running the autotuner: iter_threads in {128, 256,
+ * 512}, phase1_streams in {1, 2, 4}; (0, 0) hands the choice back to the autotuner,
+ * which then runs in the next rs_solve_batch. RS_EINVAL for other values or when the
+ * iteration kernel does not fit with that CTA size. */
+rs_status rs_batch_set_launch(rs_batch* b, int32_t iter_threads, int32_t phase1_streams);
+/* Time the parts of a chunk: from a fresh state (tolerance 0, so that no pair
+ * stops), `chunks` chunks of every problem, each part captured as its own CUDA graph
+ * and timed with events: phase 1 (sketches, S^T A, M and M^+ of every slot), the
+ * iterations, and the FP64 refresh with the end-of-chunk bookkeeping. Outputs are
+ * mean ms per chunk (any may be NULL). The solution state is overwritten. */
+rs_status rs_batch_profile(rs_batch* b, int32_t chunks, double* ms_phase1, double* ms_iterate,
+                           double* ms_refresh);
 
 #ifdef __cplusplus
 }

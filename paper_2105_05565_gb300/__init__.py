@@ -91,6 +91,9 @@ _SIGS = {
     "rs_batch_last_error": (ctypes.c_char_p, [_P]),
     "rs_batch_info": (_I32, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D),
                              ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "rs_batch_set_launch": (_I32, [_P, _I32, _I32]),
+    "rs_batch_profile": (_I32, [_P, _I32, ctypes.POINTER(_D), ctypes.POINTER(_D),
+                                ctypes.POINTER(_D)]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -351,21 +354,27 @@ class Batch:
         yptrs = (_P * P)()
         nrhs = None
         self.dims = []
+        ydev = None
         for p in range(P):
             xp, xdev, xk = _buf(Xs[p], xdt)
             n, d = (int(v) for v in Xs[p].shape)
             mats[p] = Matrix(0, 1 if xdt == np.float32 else 0, n, d, 0, xp, None, None, xdev)
-            Y = np.ascontiguousarray(Ys[p], dtype=np.float64)
+            Y = Ys[p]
             if Y.ndim == 1:
                 Y = Y[None, :]
-            if Y.shape[1] != n:
+            if tuple(Y.shape)[1] != n:
                 raise ValueError(f"Ys[{p}] must have shape (nrhs, {n})")
+            yp, ydv, yk = _buf(Y, np.float64)
+            if ydev is None:
+                ydev = ydv
+            elif ydv != ydev:
+                raise ValueError("Ys must be all host arrays or all CUDA tensors")
             if nrhs is None:
-                nrhs = Y.shape[0]
-            elif Y.shape[0] != nrhs:
+                nrhs = int(Y.shape[0])
+            elif int(Y.shape[0]) != nrhs:
                 raise ValueError("every problem needs the same number of right-hand sides")
-            yptrs[p] = Y.ctypes.data
-            self._keep += [xk, Y]
+            yptrs[p] = yp
+            self._keep += [xk, yk]
             self.dims.append(d)
         lam_a = (_D * P)(*[float(v) for v in lams])
         tau_a = (_I64 * P)(*[int(v) for v in (taus if taus is not None else [0] * P)])
@@ -383,7 +392,7 @@ class Batch:
         opts.setup_tc = int(bool(setup_tc))
         opts.cuda_stream = stream if stream is not None else _default_stream(device)
         b = _P()
-        status = L.rs_create_batch(P, mats, yptrs, 0, int(nrhs), lam_a, SKETCHES[sketch], tau_a,
+        status = L.rs_create_batch(P, mats, yptrs, int(ydev), int(nrhs), lam_a, SKETCHES[sketch], tau_a,
                                    ctypes.byref(mom), ctypes.c_uint64(int(seed)), ctypes.byref(opts),
                                    ctypes.byref(b))
         if status != RS_OK:
@@ -425,6 +434,17 @@ class Batch:
                          allow=(RS_OK, RS_ENOTCONV))
         return (W, iters.reshape(self.P, self.nrhs), resid.reshape(self.P, self.nrhs),
                 st == RS_OK)
+
+    def set_launch(self, iter_threads=0, phase1_streams=0):
+        """Fix the iteration kernel's CTA size and the phase-1 streams (0, 0: autotune)."""
+        self._check(lib().rs_batch_set_launch(self._b, int(iter_threads), int(phase1_streams)))
+
+    def profile(self, chunks=2):
+        """Mean ms per chunk of (phase 1, iterations, refresh); overwrites the state."""
+        a, b, c = _D(), _D(), _D()
+        self._check(lib().rs_batch_profile(self._b, int(chunks), ctypes.byref(a), ctypes.byref(b),
+                                           ctypes.byref(c)))
+        return {"phase1_ms": a.value, "iterate_ms": b.value, "refresh_ms": c.value}
 
     def info(self):
         """dict: setup_ms, solve_ms, tune_ms, iter_threads, phase1_streams."""

@@ -97,6 +97,7 @@ struct rs_ctx {
   void* fws = nullptr;   // factor workspace when the factor does not fit shared memory
   double *rS = nullptr, *delta = nullptr;
   int64_t sa_slot = 0, m_slot = 0, l_slot = 0;
+  int64_t bq = 0;             // S^T A blocked by slices of bq rows of the iterate (0: row-major)
   int32_t *perm = nullptr, *boff = nullptr;
   int32_t* inv = nullptr;  // per slot (stride ld): row -> bucket | sign (bucket-row sketches)
   // persistent iteration kernel over the whole GPU (bucket-row sketches)
@@ -218,7 +219,7 @@ RowsView<T> rows_view(const rs_ctx* c) {
   v.sa_slot = c->sa_slot;
   v.ST = (c->sketch == RS_GAUSSIAN) ? static_cast<const T*>(c->ST) : nullptr;
   v.st_slot = c->sa_slot;
-  v.bq = c->use_wide ? c->wide.q : 0;
+  v.bq = c->bq;
   return v;
 }
 
@@ -316,12 +317,12 @@ rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots, boo
       }
       if (sa_msys_fits<T>(c->m, c->tau, c->perm_stride)) {  // S^T A and M in one pass
         CKC(c, launch_sa_msys<T>(st, c->ctrl, force, nslots, plan, A, c->ld, c->m, c->tau, SA, c->ld,
-                                 c->sa_slot, c->use_wide ? c->wide.q : 0, c->M, c->m_slot,
+                                 c->sa_slot, c->bq, c->M, c->m_slot,
                                  (want_p && c->sweep_p) ? c->Mf : nullptr));
         break;
       }
       CKC(c, launch_sa_batched<T>(st, c->ctrl, force, nslots, plan, A, c->ld, c->m, c->tau, SA,
-                                  c->ld, c->sa_slot, c->use_wide ? c->wide.q : 0));
+                                  c->ld, c->sa_slot, c->bq));
       CKC(c, launch_msys_batched<T>(st, c->ctrl, force, nslots, plan, rows_view<T>(c), c->m, c->tau,
                                     c->M, c->m_slot));
       break;
@@ -1079,8 +1080,11 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   {
     // per-slot buffers of phase 1 (sketched rows, M, inverse factor)
     const size_t fel = c->f64_factor() ? 8 : 4;
-    if (c->use_wide)
-      c->sa_slot = (m + c->wide.q - 1) / c->wide.q * c->tau * round_up(c->wide.q, 4);
+    if (c->use_wide) c->bq = c->wide.q;
+    // batch members: one slice per CTA of the problem's cluster
+    if (c->batch_member) c->bq = round_up((m + kBatchCluster - 1) / kBatchCluster, 4);
+    if (c->bq > 0)
+      c->sa_slot = (m + c->bq - 1) / c->bq * c->tau * round_up(c->bq, 4);
     else
       c->sa_slot = (sketch == RS_SUBSAMPLE && !c->batch_member) ? 0 : c->tau * c->ld;
     c->m_slot = c->tau * c->tau;
@@ -1102,7 +1106,7 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   }
   if (sketch != RS_GAUSSIAN) {
     c->perm_stride = round_up((sketch == RS_COUNT) ? m : (sketch == RS_SUBCOUNT ? c->s : c->tau), 4);
-    c->boff_stride = c->tau + 1;
+    c->boff_stride = round_up(c->tau + 1, 4);  // 16-byte aligned slots (bulk copies)
     TRY(dalloc(c, &c->perm, (size_t)c->perm_stride * c->nslots));
     TRY(dalloc(c, &c->boff, (size_t)c->boff_stride * c->nslots));
     if (sketch != RS_SRHT) TRY(dalloc(c, &c->inv, (size_t)c->ld * c->nslots));
@@ -1212,7 +1216,7 @@ rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int3
 rs_status rs_iter_plan(const rs_ctx* c, int32_t* ctas, int64_t* q) {
   if (!c) return RS_EINVAL;
   if (ctas) *ctas = c->use_wide ? c->wide.nblk : 0;
-  if (q) *q = c->use_wide ? c->wide.q : 0;
+  if (q) *q = c->bq;
   return RS_OK;
 }
 
@@ -1472,7 +1476,7 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
         });
         if (s != RS_OK) break;
         const bool has_sa = c->sketch == RS_COUNT || c->sketch == RS_SUBCOUNT || c->use_wide;
-        const int64_t bq = c->use_wide ? c->wide.q : 0;
+        const int64_t bq = c->bq;
         const bool fused = has_sa && (c->mixed() ? sa_msys_fits<float>(c->m, c->tau, c->perm_stride)
                                                  : sa_msys_fits<double>(c->m, c->tau, c->perm_stride));
         if (fused) {
@@ -1641,13 +1645,21 @@ struct rs_batch {
   int64_t* iters = nullptr;
   double *r0 = nullptr, *resid = nullptr;
   double* tol = nullptr;               // device: tolerance of the current solve
-  int32_t* fin = nullptr;              // device: problems running, failed pairs
+  int32_t* fin = nullptr;              // device: problems running, failed pairs, timeouts
   int32_t* fin_h = nullptr;            // pinned copy
+  int32_t* alive = nullptr;            // device: 1 while problem p runs
+  int32_t* order = nullptr;            // device: problems of the captured chunk, largest first
+  std::vector<int32_t> order_h;        // host copy; its first nrun entries are captured
+  int nrun = 0;
+  int32_t* err_word = nullptr;         // device: an iteration kernel gave up a bounded wait
+  std::vector<double*> xpart;          // per phase-1 stream: X^T X W partial sums (mixed)
+  std::vector<float2*> xu;             // per phase-1 stream: X W as float pairs (mixed)
+  int64_t bq_max = 0, d_max = 0, perm_max = 0, pld_max = 0;
   std::vector<cudaStream_t> side;      // phase-1 fan-out streams
   std::vector<cudaEvent_t> evs;        // fork / join events (timing disabled)
   cudaGraphExec_t graph = nullptr;
   const double* graph_gam = nullptr;   // momentum table the graph was captured with
-  int graph_threads = 0, graph_streams = 0;
+  int graph_threads = 0, graph_streams = 0, graph_nrun = 0;
   bool tuned = false;
   int threads = 256;                   // CTA size of the iteration kernel (tuned)
   int nstreams = 1;                    // side streams of phase 1 (tuned)
@@ -1673,8 +1685,11 @@ void batch_free(rs_batch* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (rs_ctx* c : b->mem) rs_destroy(c);
   for (unsigned char* p : b->state) if (p) cudaFree(p);
-  void* ptrs[] = {b->probs, b->refs, b->ctrls, b->flag, b->skip, b->iters, b->r0, b->resid, b->tol, b->fin};
+  void* ptrs[] = {b->probs, b->refs, b->ctrls, b->flag, b->skip, b->iters, b->r0, b->resid,
+                  b->tol, b->fin, b->alive, b->order, b->err_word};
   for (void* p : ptrs) if (p) cudaFree(p);
+  for (double* p : b->xpart) if (p) cudaFree(p);
+  for (float2* p : b->xu) if (p) cudaFree(p);
   if (b->fin_h) cudaFreeHost(b->fin_h);
   for (cudaStream_t s : b->side) if (s) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->evs) if (e) cudaEventDestroy(e);
@@ -1701,32 +1716,33 @@ rs_status batch_upload(rs_batch* b) {
   for (int p = 0; p < b->P; ++p) ctrls[p] = b->mem[p]->ctrl;
   BKC(cudaMalloc(&b->ctrls, b->P * sizeof(rs::Ctrl*)));
   BKC(cudaMemcpy(b->ctrls, ctrls.data(), b->P * sizeof(rs::Ctrl*), cudaMemcpyHostToDevice));
-  auto fill_common = [&](auto& q, const rs_ctx* c) {
-    q.d = c->m; q.tau = c->tau; q.ld = c->ld; q.sa_slot = c->sa_slot; q.pld = c->pld;
+  auto fill = [&](auto& q, const rs_ctx* c) {
+    q.d = c->m; q.tau = c->tau; q.bq = c->bq; q.sa_slot = c->sa_slot; q.pld = c->pld;
     q.p_slot = c->p_slot; q.perm_stride = c->perm_stride; q.boff_stride = c->boff_stride;
     q.inv_slot = c->ld;
     q.perm = c->perm; q.boff = c->boff; q.inv = c->inv;
     q.ctrl = c->ctrl;
   };
   if (b->mixed()) {
-    std::vector<rs::BatchProbM> h(b->P);
+    std::vector<rs::BatchProbC<float>> h(b->P);
     std::vector<rs::BatchRefM> f(np);
     for (int p = 0; p < b->P; ++p) {
       const rs_ctx* c = b->mem[p];
       const size_t v = (size_t)b->nrhs * c->m;
       unsigned char* base = b->state[p];
-      rs::BatchProbM& q = h[p];
-      fill_common(q, c);
+      rs::BatchProbC<float>& q = h[p];
+      q = {};
+      fill(q, c);
       q.SA = static_cast<const float*>(c->SA); q.P = static_cast<const float*>(c->Pm);
-      q.w = reinterpret_cast<float2*>(base);
-      q.r = reinterpret_cast<float2*>(base + 8 * v);
+      q.w2 = reinterpret_cast<float2*>(base);
+      q.r2 = reinterpret_cast<float2*>(base + 8 * v);
       q.dw = reinterpret_cast<float*>(base + 16 * v);
       q.dr = reinterpret_cast<float*>(base + 20 * v);
       for (int r = 0; r < b->nrhs; ++r) {
         rs::BatchRefM& g = f[(size_t)p * b->nrhs + r];
         const size_t o = (size_t)r * c->m;
         g.d = c->m; g.pair = p * b->nrhs + r; g.lambda = c->lambda;
-        g.w2 = q.w + o; g.r2 = q.r + o; g.dw = q.dw + o; g.dr = q.dr + o;
+        g.w2 = q.w2 + o; g.r2 = q.r2 + o; g.dw = q.dw + o; g.dr = q.dr + o;
         g.wd = reinterpret_cast<double*>(base + 24 * v) + o;
         g.b = reinterpret_cast<const double*>(base + 32 * v) + o;
         g.v = reinterpret_cast<const double*>(base + 40 * v) + o;
@@ -1737,14 +1753,15 @@ rs_status batch_upload(rs_batch* b) {
     BKC(cudaMalloc(&b->refs, f.size() * sizeof(f[0])));
     BKC(cudaMemcpy(b->refs, f.data(), f.size() * sizeof(f[0]), cudaMemcpyHostToDevice));
   } else {
-    std::vector<rs::BatchProb<double, double>> h(b->P);
+    std::vector<rs::BatchProbC<double>> h(b->P);
     std::vector<rs::BatchRef> f(np);
     for (int p = 0; p < b->P; ++p) {
       const rs_ctx* c = b->mem[p];
       const size_t v = (size_t)b->nrhs * c->m;
       double* base = reinterpret_cast<double*>(b->state[p]);
-      rs::BatchProb<double, double>& q = h[p];
-      fill_common(q, c);
+      rs::BatchProbC<double>& q = h[p];
+      q = {};
+      fill(q, c);
       q.SA = static_cast<const double*>(c->SA); q.P = static_cast<const double*>(c->Pm);
       q.w = base; q.wp = base + v; q.r = base + 2 * v; q.rp = base + 3 * v;
       for (int r = 0; r < b->nrhs; ++r) {
@@ -1762,6 +1779,19 @@ rs_status batch_upload(rs_batch* b) {
   return RS_OK;
 }
 
+// the problems a chunk graph covers: those of `alive` (all when null), largest first
+rs_status batch_set_order(rs_batch* b, const int32_t* alive) {
+  b->order_h.clear();
+  for (int p = 0; p < b->P; ++p)
+    if (!alive || alive[p]) b->order_h.push_back(p);
+  std::stable_sort(b->order_h.begin(), b->order_h.end(),
+                   [&](int x, int y) { return b->mem[x]->m > b->mem[y]->m; });
+  b->nrun = (int)b->order_h.size();
+  if (b->nrun > 0)
+    BKC(cudaMemcpy(b->order, b->order_h.data(), b->nrun * sizeof(int32_t), cudaMemcpyHostToDevice));
+  return RS_OK;
+}
+
 // fresh state of every pair and every member's control block (k = 0)
 rs_status batch_reset(rs_batch* b, double tol, int64_t max_iters) {
   const rs::BatchPairs pr = batch_pairs(b);
@@ -1771,6 +1801,7 @@ rs_status batch_reset(rs_batch* b, double tol, int64_t max_iters) {
   else
     BKC(rs::launch_batch_init(b->stream, static_cast<const rs::BatchRef*>(b->refs), np, pr));
   BKC(cudaMemcpyAsync(b->tol, &tol, sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  BKC(cudaMemsetAsync(b->err_word, 0, sizeof(int32_t), b->stream));
   for (rs_ctx* c : b->mem) {
     std::memset(c->ctrl_h, 0, sizeof(rs::Ctrl));
     c->ctrl_h->max_iters = max_iters;
@@ -1782,14 +1813,13 @@ rs_status batch_reset(rs_batch* b, double tol, int64_t max_iters) {
   return RS_OK;
 }
 
-// problem p's phase-1 stream: longest processing time first over d_p^2
+// phase-1 stream of each captured problem: longest processing time first over d_p^2
+// (order_h is sorted by d, largest first)
 std::vector<int> batch_owners(const rs_batch* b, int ns) {
-  std::vector<int> order(b->P), owner(b->P, 0);
-  for (int p = 0; p < b->P; ++p) order[p] = p;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int x, int y) { return b->mem[x]->m > b->mem[y]->m; });
+  std::vector<int> owner(b->P, 0);
   std::vector<double> load(ns, 0.0);
-  for (int p : order) {
+  for (int t = 0; t < b->nrun; ++t) {
+    const int p = b->order_h[t];
     int best = 0;
     for (int i = 1; i < ns; ++i) if (load[i] < load[best]) best = i;
     owner[p] = best;
@@ -1813,15 +1843,22 @@ rs_status batch_join(rs_batch* b, int ns, int ev) {
   return RS_OK;
 }
 
-// one chunk of the whole batch (enqueued on b->stream, or captured from it)
-rs_status batch_enqueue_chunk(rs_batch* b, int threads, int ns) {
+// parts of a chunk (batch_enqueue_chunk)
+constexpr int kPartPhase1 = 1, kPartIterate = 2, kPartRefresh = 4, kPartAll = 7;
+
+// one chunk of the captured problems (enqueued on b->stream, or captured from it);
+// `parts` selects phase 1, the iterations and the refresh with the end-of-chunk
+// bookkeeping
+rs_status batch_enqueue_chunk(rs_batch* b, int threads, int ns, int parts = kPartAll) {
   const std::vector<int> owner = batch_owners(b, ns);
   auto stream_of = [&](int p) { return owner[p] == 0 ? b->stream : b->side[owner[p] - 1]; };
   const rs::BatchPairs pr = batch_pairs(b);
   const int np = b->P * b->nrhs;
   rs_status s;
+  if (parts & kPartPhase1) {
   if ((s = batch_fork(b, ns, 0)) != RS_OK) return s;
-  for (int p = 0; p < b->P; ++p) {
+  for (int t = 0; t < b->nrun; ++t) {
+    const int p = b->order_h[t];
     rs_ctx* c = b->mem[p];
     cudaStream_t st = stream_of(p);
     BKC(launch_chunk_begin(st, c->ctrl));
@@ -1831,42 +1868,49 @@ rs_status batch_enqueue_chunk(rs_batch* b, int threads, int ns) {
     if (s != RS_OK) { b->err = c->err; return s; }
   }
   if ((s = batch_join(b, ns, 0)) != RS_OK) return s;
+  }
   const double* gam = b->mem[0]->gam;
   const double* bet = b->mem[0]->bet;
+  if ((parts & kPartIterate) && b->mixed())
+    BKC((rs::launch_batch_cluster<float, true>(
+        b->stream, static_cast<const rs::BatchProbC<float>*>(b->probs), b->order, b->nrun, b->nrhs,
+        pr, gam, bet, b->chunk, b->tol, b->tau_max, b->bq_max, b->perm_max, b->pld_max, threads,
+        b->err_word)));
+  if ((parts & kPartIterate) && !b->mixed())
+    BKC((rs::launch_batch_cluster<double, false>(
+        b->stream, static_cast<const rs::BatchProbC<double>*>(b->probs), b->order, b->nrun,
+        b->nrhs, pr, gam, bet, b->chunk, b->tol, b->tau_max, b->bq_max, b->perm_max, b->pld_max,
+        threads, b->err_word)));
+  if (!(parts & kPartRefresh)) return RS_OK;
   if (b->mixed()) {
     const rs::BatchRefM* refs = static_cast<const rs::BatchRefM*>(b->refs);
-    BKC(rs::launch_batch_iterate_mixed(b->stream, static_cast<const rs::BatchProbM*>(b->probs), b->P,
-                                       b->nrhs, pr, gam, bet, b->chunk, b->tol, b->tau_max, threads));
-    // FP64 refresh: w in FP64, X^T X w per pair through X, r = X^T X w + lambda w - b
+    // FP64 refresh: w in FP64, X^T X W of each problem in one pass over X (four
+    // right-hand sides at a time), r = X^T X w + lambda w - b
     BKC(rs::launch_batch_mixed_aux(b->stream, 1, refs, np, pr, b->tol));
     if ((s = batch_fork(b, ns, kBatchMaxStreams)) != RS_OK) return s;
-    for (int p = 0; p < b->P; ++p) {
+    for (int t = 0; t < b->nrun; ++t) {
+      const int p = b->order_h[t];
       rs_ctx* c = b->mem[p];
       const size_t v = (size_t)b->nrhs * c->m;
       const double* wd = reinterpret_cast<const double*>(b->state[p] + 24 * v);
       double* xv = reinterpret_cast<double*>(b->state[p] + 40 * v);
-      for (int r = 0; r < b->nrhs; ++r)
-        BKC(launch_xtx_v_df(stream_of(p), static_cast<const float*>(c->X), c->n, c->d,
-                            wd + (size_t)r * c->m, xv + (size_t)r * c->m, c->xt_part,
-                            b->skip + p * b->nrhs + r));
+      for (int q0 = 0; q0 < b->nrhs; q0 += 4)
+        BKC(launch_xtx_two_pass(stream_of(p), static_cast<const float*>(c->X), c->n, c->d,
+                                std::min(4, b->nrhs - q0), wd + (size_t)q0 * c->m,
+                                xv + (size_t)q0 * c->m, b->xu[owner[p]], b->xpart[owner[p]],
+                                b->skip + p * b->nrhs + q0));
     }
     if ((s = batch_join(b, ns, kBatchMaxStreams)) != RS_OK) return s;
     BKC(rs::launch_batch_mixed_aux(b->stream, 3, refs, np, pr, b->tol));
-  } else {
-    BKC(rs::launch_batch_iterate(b->stream, static_cast<const rs::BatchProb<double, double>*>(b->probs),
-                                 b->P, b->nrhs, pr, gam, bet, b->chunk, b->tol, b->tau_max, threads));
   }
-  BKC(rs::launch_batch_finish(b->stream, b->ctrls, b->P, b->nrhs, pr, b->fin));
+  BKC(rs::launch_batch_finish(b->stream, b->ctrls, b->P, b->nrhs, pr, b->alive, b->fin));
   return RS_OK;
 }
 
-rs_status batch_build_graph(rs_batch* b, int threads, int ns) {
-  if (b->graph) {
-    cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
-  }
+// capture `parts` of one chunk into *out
+rs_status batch_capture(rs_batch* b, int threads, int ns, int parts, cudaGraphExec_t* out) {
   BKC(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
-  const rs_status s = batch_enqueue_chunk(b, threads, ns);
+  const rs_status s = batch_enqueue_chunk(b, threads, ns, parts);
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
   if (s != RS_OK) {
@@ -1878,28 +1922,60 @@ rs_status batch_build_graph(rs_batch* b, int threads, int ns) {
     b->err = std::string("batch graph capture: ") + cudaGetErrorString(e);
     return RS_ECUDA;
   }
-  const cudaError_t ei = cudaGraphInstantiate(&b->graph, g, 0);
+  const cudaError_t ei = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (ei != cudaSuccess) {
-    b->graph = nullptr;
+    *out = nullptr;
     b->err = std::string("batch graph instantiate: ") + cudaGetErrorString(ei);
     return RS_ECUDA;
   }
-  b->graph_gam = b->mem[0]->gam;
-  b->graph_threads = threads;
-  b->graph_streams = ns;
   return RS_OK;
 }
 
-// replay chunks until every problem has stopped (at most max_replays)
+rs_status batch_build_graph(rs_batch* b, int threads, int ns) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  const rs_status s = batch_capture(b, threads, ns, kPartAll, &b->graph);
+  if (s != RS_OK) return s;
+  b->graph_gam = b->mem[0]->gam;
+  b->graph_threads = threads;
+  b->graph_streams = ns;
+  b->graph_nrun = b->nrun;
+  return RS_OK;
+}
+
+// replay chunks until every problem has stopped (at most max_replays); when the
+// problems still running are half of those the graph covers or fewer, the graph
+// is captured again over them only
 rs_status batch_run(rs_batch* b, int64_t max_replays) {
+  std::vector<int32_t> alive(b->P);
   for (int64_t q = 0; q < max_replays; ++q) {
     BKC(cudaGraphLaunch(b->graph, b->stream));
-    BKC(cudaMemcpyAsync(b->fin_h, b->fin, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream));
+    BKC(cudaMemcpyAsync(b->fin_h, b->fin, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream));
     BKC(cudaStreamSynchronize(b->stream));
-    if (b->fin_h[0] == 0) return RS_OK;
+    if (b->fin_h[2] > 0) {
+      b->err = "rs_solve_batch: a bounded device-side wait of the iteration kernel gave up";
+      return RS_ETIMEOUT;
+    }
+    const int run = b->fin_h[0];
+    if (run == 0) return RS_OK;
+    if (2 * run <= b->nrun) {
+      BKC(cudaMemcpy(alive.data(), b->alive, b->P * sizeof(int32_t), cudaMemcpyDeviceToHost));
+      rs_status s = batch_set_order(b, alive.data());
+      if (s == RS_OK) s = batch_build_graph(b, b->threads, b->nstreams);
+      if (s != RS_OK) return s;
+    }
   }
   return RS_OK;
+}
+
+bool batch_fits(const rs_batch* b, int threads) {
+  return (b->mixed() ? rs::batch_cluster_fit<float, true>(b->nrhs, b->tau_max, b->bq_max,
+                                                          b->perm_max, b->pld_max, threads)
+                     : rs::batch_cluster_fit<double, false>(b->nrhs, b->tau_max, b->bq_max,
+                                                            b->perm_max, b->pld_max, threads)) > 0;
 }
 
 // autotuner: one steady-state chunk (tol = 0, no pair stops) per candidate CTA size
@@ -1921,6 +1997,7 @@ rs_status batch_tune(rs_batch* b) {
   for (int ns : nss) {
     if (ns > 1 && ns > b->P) continue;
     for (int t : thr) {
+      if (b->bq_max > 4 * t || !batch_fits(b, t)) continue;
       if ((s = batch_reset(b, 0.0, 2 * b->chunk)) != RS_OK) return done(s);
       if ((s = batch_build_graph(b, t, ns)) != RS_OK) return done(s);
       cudaError_t e = cudaGraphLaunch(b->graph, b->stream);  // first replay: uploads the graph
@@ -1936,6 +2013,10 @@ rs_status batch_tune(rs_batch* b) {
       }
       if (best < 0.f || ms < best) { best = ms; bt = t; bs = ns; }
     }
+  }
+  if (best < 0.f) {
+    b->err = "batch autotuner: no launch shape of the iteration kernel fits";
+    return done(RS_EUNSUPPORTED);
   }
   b->threads = bt;
   b->nstreams = bs;
@@ -1995,7 +2076,21 @@ rs_status batch_init(rs_batch* b, const rs_matrix* Xs, const double* const* Ys,
     o.chunk = lo;
   }
   b->chunk = b->mem[0]->chunk;
-  for (rs_ctx* c : b->mem) b->tau_max = std::max<int64_t>(b->tau_max, c->tau);
+  for (rs_ctx* c : b->mem) {
+    b->tau_max = std::max<int64_t>(b->tau_max, c->tau);
+    b->bq_max = std::max<int64_t>(b->bq_max, c->bq);
+    b->d_max = std::max<int64_t>(b->d_max, c->m);
+    b->perm_max = std::max<int64_t>(b->perm_max, c->perm_stride);
+    b->pld_max = std::max<int64_t>(b->pld_max, c->pld);
+  }
+  if (b->mixed() && b->d_max > 4096) {
+    b->err = "rs_create_batch: RS_MIXED takes problems with d <= 4096";
+    return RS_EUNSUPPORTED;
+  }
+  if (b->bq_max > 4 * 512 || !(batch_fits(b, 512) || batch_fits(b, 256) || batch_fits(b, 128))) {
+    b->err = "rs_create_batch: the problems are too large for the batch's iteration kernel";
+    return RS_EUNSUPPORTED;
+  }
   // per-problem state; B = X^T Y of every right-hand side (FP64)
   b->state.assign(P, nullptr);
   int64_t nmax = 0;
@@ -2035,8 +2130,21 @@ rs_status batch_init(rs_batch* b, const rs_matrix* Xs, const double* const* Ys,
   BKC(cudaMalloc(&b->r0, np * sizeof(double)));
   BKC(cudaMalloc(&b->resid, np * sizeof(double)));
   BKC(cudaMalloc(&b->tol, sizeof(double)));
-  BKC(cudaMalloc(&b->fin, 2 * sizeof(int32_t)));
-  BKC(cudaMallocHost(&b->fin_h, 2 * sizeof(int32_t)));
+  BKC(cudaMalloc(&b->fin, 3 * sizeof(int32_t)));
+  BKC(cudaMallocHost(&b->fin_h, 3 * sizeof(int32_t)));
+  BKC(cudaMalloc(&b->alive, P * sizeof(int32_t)));
+  BKC(cudaMalloc(&b->order, P * sizeof(int32_t)));
+  BKC(cudaMalloc(&b->err_word, sizeof(int32_t)));
+  BKC(cudaMemset(b->err_word, 0, sizeof(int32_t)));
+  if (b->mixed()) {
+    int64_t n_max = 0;
+    for (rs_ctx* c : b->mem) n_max = std::max<int64_t>(n_max, c->n);
+    b->xpart.assign(kBatchMaxStreams, nullptr);
+    b->xu.assign(kBatchMaxStreams, nullptr);
+    const size_t words = (size_t)xtx_two_pass_part(n_max, b->d_max, 4);
+    for (double*& x : b->xpart) BKC(cudaMalloc(&x, words * sizeof(double)));
+    for (float2*& x : b->xu) BKC(cudaMalloc(&x, (size_t)n_max * 4 * sizeof(float2)));
+  }
   if ((s = batch_upload(b)) != RS_OK) return s;
   BKC(cudaEventRecord(b->ev1, b->stream));
   BKC(cudaEventSynchronize(b->ev1));
@@ -2096,6 +2204,7 @@ rs_status rs_solve_batch(rs_batch* b, double tol, int64_t max_iters, double* con
   rs_status s;
   rs_ctx* c0 = b->mem[0];
   if ((s = ensure_schedule(c0, std::max<int64_t>(max_iters, 2 * b->chunk))) != RS_OK) { b->err = c0->err; return s; }
+  if ((s = batch_set_order(b, nullptr)) != RS_OK) return s;  // every problem, largest first
   if (!b->tuned) {
     BKC(cudaEventRecord(b->ev0, b->stream));
     if ((s = batch_tune(b)) != RS_OK) return s;
@@ -2106,7 +2215,7 @@ rs_status rs_solve_batch(rs_batch* b, double tol, int64_t max_iters, double* con
     b->tune_ms = ms;
   }
   if (!b->graph || b->graph_gam != c0->gam || b->graph_threads != b->threads ||
-      b->graph_streams != b->nstreams)
+      b->graph_streams != b->nstreams || b->graph_nrun != b->nrun)
     if ((s = batch_build_graph(b, b->threads, b->nstreams)) != RS_OK) return s;
   if ((s = batch_reset(b, tol, max_iters)) != RS_OK) return s;
   BKC(cudaEventRecord(b->ev0, b->stream));
@@ -2142,6 +2251,75 @@ rs_status rs_solve_batch(rs_batch* b, double tol, int64_t max_iters, double* con
   }
   if (nan) { b->err = "rs_solve_batch: NaN or Inf in a residual"; return RS_ENUMERIC; }
   return open ? RS_ENOTCONV : RS_OK;
+}
+
+rs_status rs_batch_profile(rs_batch* b, int32_t chunks, double* ms_phase1, double* ms_iterate,
+                           double* ms_refresh) {
+  if (!b || chunks < 1) { g_batch_err = "rs_batch_profile: null batch or chunks < 1"; return RS_EINVAL; }
+  DeviceGuard dg(b->mem[0]->device);
+  rs_status s;
+  rs_ctx* c0 = b->mem[0];
+  const int64_t K = (int64_t)chunks * b->chunk;
+  if ((s = ensure_schedule(c0, std::max<int64_t>(K, 2 * b->chunk))) != RS_OK) { b->err = c0->err; return s; }
+  if ((s = batch_set_order(b, nullptr)) != RS_OK) return s;
+  if (!b->tuned && (s = batch_tune(b)) != RS_OK) return s;
+  cudaGraphExec_t g[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  auto done = [&](rs_status r) {
+    for (cudaGraphExec_t x : g) if (x) cudaGraphExecDestroy(x);
+    for (cudaEvent_t e : ev) if (e) cudaEventDestroy(e);
+    return r;
+  };
+  const int parts[3] = {kPartPhase1, kPartIterate, kPartRefresh};
+  for (int i = 0; i < 3; ++i)
+    if ((s = batch_capture(b, b->threads, b->nstreams, parts[i], &g[i])) != RS_OK) return done(s);
+  for (cudaEvent_t& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) { b->err = "rs_batch_profile: events"; return done(RS_ECUDA); }
+  if ((s = batch_reset(b, 0.0, K)) != RS_OK) return done(s);
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int q = 0; q < chunks; ++q) {
+    cudaError_t e = cudaEventRecord(ev[0], b->stream);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+      e = cudaGraphLaunch(g[i], b->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[i + 1], b->stream);
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      acc[i] += ms;
+    }
+    if (e != cudaSuccess) {
+      b->err = std::string("rs_batch_profile: ") + cudaGetErrorString(e);
+      return done(RS_ECUDA);
+    }
+  }
+  if (ms_phase1) *ms_phase1 = acc[0] / chunks;
+  if (ms_iterate) *ms_iterate = acc[1] / chunks;
+  if (ms_refresh) *ms_refresh = acc[2] / chunks;
+  return done(RS_OK);
+}
+
+rs_status rs_batch_set_launch(rs_batch* b, int32_t iter_threads, int32_t phase1_streams) {
+  if (!b) { g_batch_err = "rs_batch_set_launch: null batch"; return RS_EINVAL; }
+  if (iter_threads == 0 && phase1_streams == 0) {
+    b->tuned = false;
+    return RS_OK;
+  }
+  if ((iter_threads != 128 && iter_threads != 256 && iter_threads != 512) ||
+      (phase1_streams != 1 && phase1_streams != 2 && phase1_streams != kBatchMaxStreams)) {
+    b->err = "rs_batch_set_launch: iter_threads in {128, 256, 512}, phase1_streams in {1, 2, 4}";
+    return RS_EINVAL;
+  }
+  DeviceGuard dg(b->mem[0]->device);
+  if (b->bq_max > 4 * iter_threads || !batch_fits(b, iter_threads)) {
+    b->err = "rs_batch_set_launch: the iteration kernel does not fit with that CTA size";
+    return RS_EINVAL;
+  }
+  b->threads = iter_threads;
+  b->nstreams = phase1_streams;
+  b->tuned = true;
+  return RS_OK;
 }
 
 void rs_destroy_batch(rs_batch* b) {

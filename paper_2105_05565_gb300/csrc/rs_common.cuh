@@ -45,6 +45,10 @@ constexpr int32_t kNotSketched = 0x7FFFFFFF;
 // ---------------------------------------------------------------------------
 // Device control block of one context: iteration counter, stop flags, norms.
 // ---------------------------------------------------------------------------
+// device-side status codes of Ctrl::status (the values of RS_ENUMERIC, RS_ETIMEOUT)
+constexpr int32_t kStatusNumeric = 4;
+constexpr int32_t kStatusTimeout = 5;
+
 struct Ctrl {
   int64_t k;          // next iteration index
   int64_t k0;         // first iteration of the current chunk

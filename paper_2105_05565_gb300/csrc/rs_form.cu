@@ -1,6 +1,7 @@
 // Forming the linear system of eq. (4) (A = X^T X + lambda I, b = X^T y for the
 // primal eq. (2); A = X X^T + lambda I, b = y for the dual eq. (3)) and evaluating
 // the true residual A v - b through X in FP64 without forming A.
+#include <algorithm>
 #include <mutex>
 #include <string>
 
@@ -220,6 +221,303 @@ cudaError_t launch_xtx_v_df(cudaStream_t st, const float* X, int64_t n, int64_t 
   else if (d <= 4096) k_xtx_v_df<16, 4><<<G, 256, 0, st>>>(X, n, d, v, part, stop);
   else return cudaErrorInvalidValue;
   k_sum_parts<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(part, G, d, out, stop);
+  return cudaGetLastError();
+}
+
+// ---- X^T X V for up to four vectors in one pass over FP32 X (same arithmetic) ----
+// The vectors' float pairs sit in shared memory (nv x d); every row of X is loaded
+// once and serves all nv row dots and all nv column updates. The kernel returns at
+// once when every vector is flagged in `skip`.
+template <int NC, int R>
+__global__ void __launch_bounds__(512, 1) k_xtx_multi_df(const float* __restrict__ X, int64_t n,
+                                                         int64_t d, int nv,
+                                                         const double* __restrict__ V,
+                                                         double* __restrict__ part,
+                                                         const int32_t* __restrict__ skip) {
+  constexpr int NVM = 4, NWM = 16;
+  if (skip != nullptr) {
+    int all = 1;
+    for (int q = 0; q < nv; ++q) all &= (skip[q] != 0);
+    if (all) return;
+  }
+  extern __shared__ float2 sv[];  // nv x d: (hi, lo) of the vectors
+  __shared__ float s_h[NWM][R][NVM], s_l[NWM][R][NVM];
+  __shared__ float u_h[R][NVM], u_l[R][NVM];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int NT = blockDim.x;
+  for (int64_t e = tid; e < (int64_t)nv * d; e += NT) {
+    const double vv = V[e];
+    const float h = (float)vv;
+    sv[e] = make_float2(h, (float)(vv - (double)h));
+  }
+  __syncthreads();
+  float ah[NVM][NC], al[NVM][NC];
+#pragma unroll
+  for (int q = 0; q < NVM; ++q)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) { ah[q][c] = 0.f; al[q][c] = 0.f; }
+  const int64_t rows_per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * rows_per, i1 = min(n, i0 + rows_per);
+  for (int64_t ib = i0; ib < i1; ib += R) {
+    float x[R][NC];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int64_t col = tid + (int64_t)NT * c;
+        x[r][c] = (ib + r < i1 && col < d) ? __ldg(X + (ib + r) * d + col) : 0.f;
+      }
+    float dh[R][NVM], dlo[R][NVM];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int q = 0; q < NVM; ++q) { dh[r][q] = 0.f; dlo[r][q] = 0.f; }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int64_t col = tid + (int64_t)NT * c;
+      if (col >= d) break;
+#pragma unroll
+      for (int q = 0; q < NVM; ++q) {
+        if (q >= nv) break;
+        const float2 v = sv[(int64_t)q * d + col];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float p = __fmul_rn(x[r][c], v.x);
+          const float e = __fmaf_rn(x[r][c], v.x, -p);
+          float s, er;
+          two_sum(dh[r][q], p, s, er);
+          dh[r][q] = s;
+          dlo[r][q] = __fmaf_rn(x[r][c], v.y, __fadd_rn(dlo[r][q], __fadd_rn(er, e)));
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int q = 0; q < NVM; ++q) {
+        if (q >= nv) break;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float oh = __shfl_xor_sync(0xffffffffu, dh[r][q], o);
+          const float ol = __shfl_xor_sync(0xffffffffu, dlo[r][q], o);
+          df_add(dh[r][q], dlo[r][q], oh, ol);
+        }
+        if (lane == 0) { s_h[wid][r][q] = dh[r][q]; s_l[wid][r][q] = dlo[r][q]; }
+      }
+    __syncthreads();
+    if (tid < R * NVM) {
+      const int r = tid / NVM, q = tid % NVM;
+      if (q < nv) {
+        float h = s_h[0][r][q], l = s_l[0][r][q];
+        for (int w = 1; w < nw; ++w) df_add(h, l, s_h[w][r][q], s_l[w][r][q]);
+        u_h[r][q] = h;
+        u_l[r][q] = l;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int q = 0; q < NVM; ++q) {
+        if (q >= nv) break;
+        const float uh = u_h[r][q], ul = u_l[r][q];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const float p = __fmul_rn(x[r][c], uh);
+          const float e = __fmaf_rn(x[r][c], uh, -p);
+          float s, er;
+          two_sum(ah[q][c], p, s, er);
+          ah[q][c] = s;
+          al[q][c] = __fmaf_rn(x[r][c], ul, __fadd_rn(al[q][c], __fadd_rn(er, e)));
+        }
+      }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < NVM; ++q) {
+    if (q >= nv) break;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int64_t col = tid + (int64_t)NT * c;
+      if (col < d) part[((int64_t)blockIdx.x * nv + q) * d + col] = (double)ah[q][c] + (double)al[q][c];
+    }
+  }
+}
+
+// out[q] = sum over blocks of part[block][q] in block order
+__global__ void k_sum_parts_multi(const double* __restrict__ part, int nblk, int nv, int64_t d,
+                                  double* __restrict__ out, const int32_t* __restrict__ skip) {
+  const int q = blockIdx.y;
+  if (skip != nullptr && skip[q]) return;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d) return;
+  double acc = 0.0;
+  for (int b = 0; b < nblk; ++b) acc += part[((int64_t)b * nv + q) * d + j];
+  out[(int64_t)q * d + j] = acc;
+}
+
+int xtx_multi_blocks() { return 152; }
+
+cudaError_t launch_xtx_multi_df(cudaStream_t st, const float* X, int64_t n, int64_t d, int nv,
+                                const double* V, double* out, double* part, const int32_t* skip) {
+  if (nv < 1 || nv > 4 || d > 4096) return cudaErrorInvalidValue;
+  const int G = xtx_multi_blocks();
+  const size_t smem = (size_t)nv * d * sizeof(float2);
+  cudaError_t e = cudaSuccess;
+  auto go = [&](auto kern) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) kern<<<G, 512, smem, st>>>(X, n, d, nv, V, part, skip);
+  };
+  if (d <= 1024) go(k_xtx_multi_df<2, 2>);
+  else if (d <= 2048) go(k_xtx_multi_df<4, 2>);
+  else go(k_xtx_multi_df<8, 1>);
+  if (e != cudaSuccess) return e;
+  k_sum_parts_multi<<<dim3((unsigned)((d + 255) / 256), (unsigned)nv), 256, 0, st>>>(part, G, nv, d,
+                                                                                      out, skip);
+  return cudaGetLastError();
+}
+
+// ---- X^T X W for up to four vectors in two passes (same float-pair arithmetic) ----
+// Pass 1: U = X W, a warp per row of X (lanes over the columns, the vectors' float
+// pairs in shared memory), the row dots reduced across the warp as float pairs; no
+// block-wide synchronisation. Pass 2: V = X^T U, a thread per column over a range
+// of rows (the range's U in shared memory), per-range sums added in range order.
+template <int NV>
+__global__ void __launch_bounds__(1024) k_xw_df(const float* __restrict__ X, int64_t n, int64_t d,
+                                               int nv, const double* __restrict__ W,
+                                               float2* __restrict__ U,
+                                               const int32_t* __restrict__ skip) {
+  if (skip != nullptr) {
+    int all = 1;
+    for (int q = 0; q < nv; ++q) all &= (skip[q] != 0);
+    if (all) return;
+  }
+  extern __shared__ float2 sw[];  // d x NV: (hi, lo) of the vectors, column-major in q
+  for (int64_t e = threadIdx.x; e < d * NV; e += blockDim.x) {
+    const int64_t c = e / NV;
+    const int q = (int)(e - c * NV);
+    const double v = q < nv ? W[(int64_t)q * d + c] : 0.0;
+    const float h = (float)v;
+    sw[e] = make_float2(h, (float)(v - (double)h));
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwg = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = wg; i < n; i += nwg) {
+    float dh[NV], dlo[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) { dh[q] = 0.f; dlo[q] = 0.f; }
+    const float* xr = X + i * d;
+    for (int64_t c0 = lane; c0 < d; c0 += 128) {  // four columns in flight per lane
+      float xs[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xs[u] = (c0 + 32 * u < d) ? __ldg(xr + c0 + 32 * u) : 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t c = c0 + 32 * u;
+        if (c >= d) break;
+        const float x = xs[u];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          const float2 v = sw[c * NV + q];
+          const float p = __fmul_rn(x, v.x);
+          const float e = __fmaf_rn(x, v.x, -p);
+          float s, er;
+          two_sum(dh[q], p, s, er);
+          dh[q] = s;
+          dlo[q] = __fmaf_rn(x, v.y, __fadd_rn(dlo[q], __fadd_rn(er, e)));
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, dh[q], o);
+        const float ol = __shfl_xor_sync(0xffffffffu, dlo[q], o);
+        df_add(dh[q], dlo[q], oh, ol);
+      }
+    }
+    if (lane < NV) {
+      float h = dh[0], l = dlo[0];
+#pragma unroll
+      for (int q = 1; q < NV; ++q)
+        if (lane == q) { h = dh[q]; l = dlo[q]; }
+      U[i * NV + lane] = make_float2(h, l);
+    }
+  }
+}
+
+constexpr int kXtuCols = 256;  // columns per block of pass 2
+constexpr int kXtuRows = 512;  // rows per block of pass 2
+
+template <int NV>
+__global__ void __launch_bounds__(kXtuCols) k_xtu_df(const float* __restrict__ X, int64_t n,
+                                                     int64_t d, int nv,
+                                                     const float2* __restrict__ U,
+                                                     double* __restrict__ part,
+                                                     const int32_t* __restrict__ skip) {
+  if (skip != nullptr) {
+    int all = 1;
+    for (int q = 0; q < nv; ++q) all &= (skip[q] != 0);
+    if (all) return;
+  }
+  __shared__ float2 su[kXtuRows * NV];
+  const int64_t r0 = (int64_t)blockIdx.y * kXtuRows;
+  const int64_t r1 = min(n, r0 + kXtuRows);
+  for (int64_t e = threadIdx.x; e < (r1 - r0) * NV; e += blockDim.x) su[e] = U[r0 * NV + e];
+  __syncthreads();
+  const int64_t c = (int64_t)blockIdx.x * kXtuCols + threadIdx.x;
+  if (c >= d) return;
+  float ah[NV], al[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) { ah[q] = 0.f; al[q] = 0.f; }
+  for (int64_t i = r0; i < r1; ++i) {
+    const float x = __ldg(X + i * d + c);
+    const float2* u = su + (i - r0) * NV;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const float2 uq = u[q];
+      const float p = __fmul_rn(x, uq.x);
+      const float e = __fmaf_rn(x, uq.x, -p);
+      float s, er;
+      two_sum(ah[q], p, s, er);
+      ah[q] = s;
+      al[q] = __fmaf_rn(x, uq.y, __fadd_rn(al[q], __fadd_rn(er, e)));
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+    if (q < nv) part[((int64_t)blockIdx.y * nv + q) * d + c] = (double)ah[q] + (double)al[q];
+}
+
+int64_t xtx_two_pass_part(int64_t n, int64_t d, int nv) {
+  return ((n + kXtuRows - 1) / kXtuRows) * nv * d;
+}
+
+cudaError_t launch_xtx_two_pass(cudaStream_t st, const float* X, int64_t n, int64_t d, int nv,
+                                const double* W, double* out, float2* U, double* part,
+                                const int32_t* skip) {
+  if (nv < 1 || nv > 4) return cudaErrorInvalidValue;
+  const int NV = nv <= 1 ? 1 : (nv <= 2 ? 2 : 4);
+  const size_t smem = (size_t)d * NV * sizeof(float2);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  const unsigned g1 = (unsigned)std::min<int64_t>((n + 31) / 32, 152);
+  const dim3 g2((unsigned)((d + kXtuCols - 1) / kXtuCols), (unsigned)((n + kXtuRows - 1) / kXtuRows));
+  cudaError_t e = cudaSuccess;
+  auto go = [&](auto k1, auto k2) {
+    e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return;
+    k1<<<g1, 1024, smem, st>>>(X, n, d, nv, W, U, skip);
+    k2<<<g2, kXtuCols, 0, st>>>(X, n, d, nv, U, part, skip);
+  };
+  if (NV == 1) go(k_xw_df<1>, k_xtu_df<1>);
+  else if (NV == 2) go(k_xw_df<2>, k_xtu_df<2>);
+  else go(k_xw_df<4>, k_xtu_df<4>);
+  if (e != cudaSuccess) return e;
+  k_sum_parts_multi<<<dim3((unsigned)((d + 255) / 256), (unsigned)nv), 256, 0, st>>>(
+      part, (int)g2.y, nv, d, out, skip);
   return cudaGetLastError();
 }
 

@@ -620,8 +620,8 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   }
   if (cta == 0 && tid == 0) {
     ctrl->k = k;
-    if (outcome == 3) { ctrl->status = 5; ctrl->stop = 1; }
-    if (outcome == 2) { ctrl->status = 4; ctrl->stop = 1; }
+    if (outcome == 3) { ctrl->status = kStatusTimeout; ctrl->stop = 1; }
+    if (outcome == 2) { ctrl->status = kStatusNumeric; ctrl->stop = 1; }
     if (outcome == 1) { if (g.mixed) ctrl->pending = 1; else ctrl->stop = 1; }
     if (k >= ctrl->max_iters) ctrl->stop = 1;
     *g.epoch = (tag0 >> 24) + 1;

@@ -211,14 +211,6 @@ cudaError_t launch_mf_iteration(cudaStream_t st, Ctrl* ctrl, MfArgs a, const Spa
                                 int64_t p_slot, AT* v, AT* pu, UpdateArgs u, double* rS_out);
 
 // ---- many problems, several right-hand sides each (rs_batch.cu) ----
-template <typename T, typename TF>
-struct BatchProb {
-  int64_t d, tau, ld, sa_slot, pld, p_slot, perm_stride, boff_stride, inv_slot;
-  const T* SA; const TF* P;                       // per slot: S^T A (tau x ld), M^+ (tau x pld)
-  const int32_t* perm; const int32_t* boff; const int32_t* inv;  // per slot: plan, row map
-  double *w, *wp, *r, *rp;                        // nrhs x d each (right-hand side major)
-  Ctrl* ctrl;                                     // the problem's control block (k, k0, stop)
-};
 struct BatchPairs {        // per (problem, right-hand side)
   int32_t* flag;           // 0 active, 1 pending (FP64 check due), 2 converged, 3 failed
   int32_t* skip;           // 1: no refresh (converged or failed)
@@ -230,35 +222,43 @@ struct BatchRef {          // state of one pair (plain FP64)
   int64_t d; int pair; double lambda;
   double* w; double* wp; const double* b; double* r; double* rp;
 };
-struct BatchProbM {        // mixed precision: float-pair state, FP32 increments
-  int64_t d, tau, ld, sa_slot, pld, p_slot, perm_stride, boff_stride, inv_slot;
-  const float* SA; const float* P;
-  const int32_t* perm; const int32_t* boff; const int32_t* inv;
-  float2 *w, *r;                                  // nrhs x d each: hi, lo
-  float *dw, *dr;                                 // nrhs x d each: last increments
-  Ctrl* ctrl;
-};
 struct BatchRefM {        // state of one pair (mixed)
   int64_t d; int pair; double lambda;
   float2* w2; float2* r2; float* dw; float* dr;   // the pair's state
   double* wd; const double* v; const double* b;   // w in FP64, X^T X w, b
 };
-cudaError_t launch_batch_iterate_mixed(cudaStream_t st, const BatchProbM* probs, int P, int nrhs,
-                                       BatchPairs pairs, const double* gam, const double* bet,
-                                       int64_t chunk, const double* tol, int64_t tau_max,
-                                       int threads);
 // what: 0 init state and r0, 1 w -> FP64 (active pairs), 2 w -> FP64 (all), 3 refresh
 cudaError_t launch_batch_mixed_aux(cudaStream_t st, int what, const BatchRefM* refs, int npairs,
                                    BatchPairs pairs, const double* tol);
-// plain FP64: FP64 state, S^T A and M^+ in FP64
-size_t batch_iterate_smem(int64_t tau_max, int nrhs);
-cudaError_t launch_batch_iterate(cudaStream_t st, const BatchProb<double, double>* probs, int P,
-                                 int nrhs, BatchPairs pairs, const double* gam, const double* bet,
-                                 int64_t chunk, const double* tol, int64_t tau_max, int threads);
 cudaError_t launch_batch_init(cudaStream_t st, const BatchRef* refs, int npairs, BatchPairs pairs);
 
+// one cluster of kBatchCluster CTAs per problem (rs_batch_cluster.cu)
+constexpr int kBatchCluster = 8;
+template <typename T>
+struct BatchProbC {
+  int64_t d, tau, bq, sa_slot, pld, p_slot, perm_stride, boff_stride, inv_slot;
+  const T* SA;                                    // per slot: tau x bq slices, one per CTA
+  const T* P;                                     // per slot: M^+ (tau x pld)
+  const int32_t* perm; const int32_t* boff; const int32_t* inv;  // per slot: plan, row map
+  T *w, *wp, *r, *rp;                             // plain: nrhs x d each
+  float2 *w2, *r2;                                // mixed: nrhs x d float pairs
+  float *dw, *dr;                                 // mixed: last increments
+  Ctrl* ctrl;
+};
+// tau_max, bq_max, perm_max, pld_max: maxima over the problems of tau, bq, the plan's
+// perm_stride and the row stride of M^+ (they size the shared memory)
+template <typename T, bool kMixed>
+cudaError_t launch_batch_cluster(cudaStream_t st, const BatchProbC<T>* probs, const int32_t* order,
+                                 int nprob, int nrhs, BatchPairs pairs, const double* gam,
+                                 const double* bet, int64_t chunk, const double* tol,
+                                 int64_t tau_max, int64_t bq_max, int64_t perm_max, int64_t pld_max,
+                                 int threads, int32_t* err_word);
+template <typename T, bool kMixed>
+int batch_cluster_fit(int nrhs, int64_t tau_max, int64_t bq_max, int64_t perm_max, int64_t pld_max,
+                      int threads);
+
 cudaError_t launch_batch_finish(cudaStream_t st, Ctrl* const* ctrls, int P, int nrhs,
-                                BatchPairs pairs, int32_t* out);
+                                BatchPairs pairs, int32_t* alive, int32_t* out);
 
 // ---- iterate / residual update (rs_update.cu) ----
 struct UpdateArgs {
@@ -311,6 +311,18 @@ cudaError_t launch_x_v(cudaStream_t st, const TI* X, int64_t n, int64_t d, const
 cudaError_t launch_xtx_v_df(cudaStream_t st, const float* X, int64_t n, int64_t d, const double* v,
                             double* out, double* part, const int32_t* stop = nullptr);
 int xtx_df_blocks();
+// out[q] = X^T X V[q] for nv <= 4 vectors (nv x d, vector-major) in one pass over X,
+// d <= 4096; part holds xtx_multi_blocks() x nv x d doubles; vectors flagged in skip
+// (nv entries) are not written, and nothing runs when all are flagged
+cudaError_t launch_xtx_multi_df(cudaStream_t st, const float* X, int64_t n, int64_t d, int nv,
+                                const double* V, double* out, double* part, const int32_t* skip);
+int xtx_multi_blocks();
+// the same product in two passes (U = X W with a warp per row, then X^T U with a thread
+// per column): U holds n x 4 float pairs, part xtx_two_pass_part(n, d, nv) doubles
+cudaError_t launch_xtx_two_pass(cudaStream_t st, const float* X, int64_t n, int64_t d, int nv,
+                                const double* W, double* out, float2* U, double* part,
+                                const int32_t* skip);
+int64_t xtx_two_pass_part(int64_t n, int64_t d, int nv);
 // r_true = v + lambda x - b; replaces (r, rp) keeping r - rp, writes hist[k] and the
 // convergence decision (mode 1) or only the relative residual (mode 0 -> *rel_out)
 cudaError_t launch_refresh_finish(cudaStream_t st, Ctrl* ctrl, int mode, int64_t m,

@@ -175,6 +175,25 @@ def batched_problem(n: int, d: int, nrhs: int, seed: int, noise: float = 0.1,
     return X, Y
 
 
+def batched_problem_torch(n: int, d: int, nrhs: int, seed: int, noise: float = 0.1,
+                          device="cuda"):
+    """Large-batch version of ``batched_problem`` drawn with torch on ``device``:
+    X float32 (n x d, row-major, the stored data), Y float64 (nrhs x n) computed from
+    that stored X. Returns torch tensors (X, Y)."""
+    import torch
+
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    u = torch.rand(d, generator=gen, device=device, dtype=torch.float64)
+    c = torch.exp(math.log(1e-2) * (1.0 - u))
+    X = (torch.randn(n, d, generator=gen, device=device, dtype=torch.float32)
+         * c.float()[None, :]).contiguous()
+    W = torch.randn(nrhs, d, generator=gen, device=device, dtype=torch.float64)
+    eps = torch.randn(nrhs, n, generator=gen, device=device, dtype=torch.float64)
+    Y = (X.double() @ W.T).T + noise * eps
+    return X, Y.contiguous()
+
+
 def bf16_round(x) -> np.ndarray:
     """Values of x rounded to the nearest bfloat16 (ties to even), as float64: the
     stored data of a bfloat16 design matrix."""
