@@ -339,11 +339,11 @@ rs_status rs_batch_info(const rs_batch* b, double* setup_ms, double* solve_ms, d
 rs_status rs_batch_set_launch(rs_batch* b, int32_t iter_threads, int32_t phase1_streams);
 /* Time the parts of a chunk: from a fresh state (tolerance 0, so that no pair
  * stops), `chunks` chunks of every problem, each part captured as its own CUDA graph
- * and timed with events: phase 1 (sketches, S^T A, M and M^+ of every slot), the
- * iterations, and the FP64 refresh with the end-of-chunk bookkeeping. Outputs are
- * mean ms per chunk (any may be NULL). The solution state is overwritten. */
-rs_status rs_batch_profile(rs_batch* b, int32_t chunks, double* ms_phase1, double* ms_iterate,
-                           double* ms_refresh);
+ * and timed with events. ms_parts (6 entries) receives the mean ms per chunk of:
+ * the sketch plans, the sketched rows S^T A, M = S^T A S, the inverses M^+ (the four
+ * parts of phase 1), the iterations, and the FP64 refresh with the end-of-chunk
+ * bookkeeping. The solution state is overwritten. */
+rs_status rs_batch_profile(rs_batch* b, int32_t chunks, double* ms_parts);
 
 #ifdef __cplusplus
 }

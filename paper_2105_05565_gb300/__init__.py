@@ -92,8 +92,7 @@ _SIGS = {
     "rs_batch_info": (_I32, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D),
                              ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "rs_batch_set_launch": (_I32, [_P, _I32, _I32]),
-    "rs_batch_profile": (_I32, [_P, _I32, ctypes.POINTER(_D), ctypes.POINTER(_D),
-                                ctypes.POINTER(_D)]),
+    "rs_batch_profile": (_I32, [_P, _I32, _P]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -440,11 +439,14 @@ class Batch:
         self._check(lib().rs_batch_set_launch(self._b, int(iter_threads), int(phase1_streams)))
 
     def profile(self, chunks=2):
-        """Mean ms per chunk of (phase 1, iterations, refresh); overwrites the state."""
-        a, b, c = _D(), _D(), _D()
-        self._check(lib().rs_batch_profile(self._b, int(chunks), ctypes.byref(a), ctypes.byref(b),
-                                           ctypes.byref(c)))
-        return {"phase1_ms": a.value, "iterate_ms": b.value, "refresh_ms": c.value}
+        """Mean ms per chunk of each part (plans, rows, msys, inverse: phase 1; iterate;
+        refresh); overwrites the state."""
+        out = np.zeros(6)
+        self._check(lib().rs_batch_profile(self._b, int(chunks), out.ctypes.data))
+        names = ["plan_ms", "rows_ms", "msys_ms", "inverse_ms", "iterate_ms", "refresh_ms"]
+        r = dict(zip(names, out.tolist()))
+        r["phase1_ms"] = float(out[:4].sum())
+        return r
 
     def info(self):
         """dict: setup_ms, solve_ms, tune_ms, iter_threads, phase1_streams."""

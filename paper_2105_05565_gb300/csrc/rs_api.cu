@@ -285,18 +285,27 @@ rs_status enqueue_gen(rs_ctx* c, int64_t k0_arg, int nslots) {
 // and the inverse Cholesky factor of M for `nslots` consecutive iterations. force = 1
 // (parity hooks) runs every slot starting at iteration k0_arg; force = 0 starts at
 // ctrl->k0 and skips slots the solve will not reach.
+// stages of phase 1 (a chunk's profile times them apart): the sketch plans, the
+// sketched rows (with M where one pass forms both), M from the sketched rows, and
+// the small systems' inverses
+constexpr int kP1Plan = 1, kP1Rows = 2, kP1Msys = 4, kP1Inv = 8, kP1All = 15;
+
 template <typename T>
-rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots, bool want_p) {
+rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots, bool want_p,
+                           int stages = kP1All) {
   cudaStream_t st = c->stream;
-  rs_status s = enqueue_gen(c, force ? k0_arg : -1, nslots);
-  if (s != RS_OK) return s;
+  rs_status s;
   const PlanView plan = plan_view(c);
-  if (c->inv != nullptr)
-    CKC(c, launch_inv_map(st, c->ctrl, force, nslots, plan, c->m, c->tau,
-                          c->sketch == RS_COUNT ? 1 : 0, c->inv, c->ld));
+  if (stages & kP1Plan) {
+    if ((s = enqueue_gen(c, force ? k0_arg : -1, nslots)) != RS_OK) return s;
+    if (c->inv != nullptr)
+      CKC(c, launch_inv_map(st, c->ctrl, force, nslots, plan, c->m, c->tau,
+                            c->sketch == RS_COUNT ? 1 : 0, c->inv, c->ld));
+  }
   const T* A = static_cast<const T*>(c->A);
   T* SA = static_cast<T*>(c->SA);
-  if (c->sparse) {  // XS and M = S^T X^T X S + lambda S^T S without A
+  if (!(stages & (kP1Rows | kP1Msys))) {
+  } else if (c->sparse) {  // XS and M = S^T X^T X S + lambda S^T S without A
     s = with_vt(c, [&](auto tag) -> rs_status {
       using VT = std::remove_pointer_t<decltype(tag)>;
       CKC(c, (launch_mf_phase1<VT, T>(st, c->ctrl, force, nslots, mf_args(c),
@@ -315,6 +324,7 @@ rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots, boo
                                       c->tau, c->M, c->m_slot));
         break;
       }
+      if (!(stages & kP1Rows)) break;  // (here M is formed with S^T A)
       if (sa_msys_fits<T>(c->m, c->tau, c->perm_stride)) {  // S^T A and M in one pass
         CKC(c, launch_sa_msys<T>(st, c->ctrl, force, nslots, plan, A, c->ld, c->m, c->tau, SA, c->ld,
                                  c->sa_slot, c->bq, c->M, c->m_slot,
@@ -324,7 +334,7 @@ rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots, boo
       CKC(c, launch_sa_batched<T>(st, c->ctrl, force, nslots, plan, A, c->ld, c->m, c->tau, SA,
                                   c->ld, c->sa_slot, c->bq));
       CKC(c, launch_msys_batched<T>(st, c->ctrl, force, nslots, plan, rows_view<T>(c), c->m, c->tau,
-                                    c->M, c->m_slot));
+                                    c->M, c->m_slot, (want_p && c->sweep_p) ? c->Mf : nullptr));
       break;
     case RS_GAUSSIAN: {
       T* ST = static_cast<T*>(c->ST);
@@ -339,6 +349,7 @@ rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots, boo
                                    c->mp, c->tau, SA, c->ld, c->sa_slot, c->M, c->m_slot));
       break;
   }
+  if (!(stages & kP1Inv)) return RS_OK;
   if (want_p && c->sweep_p) {
     // FP32 M^+ directly (symmetric sweeps), no triangular factor
     CKC(c, launch_sweep_inv(st, c->ctrl, force, nslots, c->Mf, c->m_slot, c->tau,
@@ -365,9 +376,10 @@ rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots, boo
 }
 
 // want_p: also M^+ per slot, for the persistent iteration kernel
-rs_status enqueue_phase1(rs_ctx* c, int force, int64_t k0_arg, int nslots, bool want_p = false) {
-  return c->mixed() ? enqueue_phase1_t<float>(c, force, k0_arg, nslots, want_p)
-                    : enqueue_phase1_t<double>(c, force, k0_arg, nslots, want_p);
+rs_status enqueue_phase1(rs_ctx* c, int force, int64_t k0_arg, int nslots, bool want_p = false,
+                         int stages = kP1All) {
+  return c->mixed() ? enqueue_phase1_t<float>(c, force, k0_arg, nslots, want_p, stages)
+                    : enqueue_phase1_t<double>(c, force, k0_arg, nslots, want_p, stages);
 }
 
 template <typename TF, typename T>
@@ -1045,8 +1057,8 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     c->pld = round_up(c->tau, 4);
     c->p_slot = c->tau * c->pld;
     TRYC(cudaMalloc(&c->Pm, (size_t)c->nslots * c->p_slot * fel));
-    c->sweep_p = c->mixed() && !c->f64_factor() && c->tau <= kSweepMaxTau &&
-                 sa_msys_fits<float>(m, c->tau, round_up((sketch == RS_COUNT) ? m : (sketch == RS_SUBCOUNT ? c->s : c->tau), 4));
+    // FP32 M^+ by sweeps (every phase-1 path of a member writes the FP32 M they read)
+    c->sweep_p = c->mixed() && !c->f64_factor() && c->tau <= kSweepMaxTau;
     if (c->sweep_p) TRY(dalloc(c, &c->Mf, (size_t)c->nslots * c->tau * c->tau));
   }
   if (!t_batch_member && !c->sparse && (sketch == RS_SUBSAMPLE || sketch == RS_COUNT || sketch == RS_SUBCOUNT) && o.iter_ctas >= 0) {
@@ -1849,7 +1861,8 @@ constexpr int kPartPhase1 = 1, kPartIterate = 2, kPartRefresh = 4, kPartAll = 7;
 // one chunk of the captured problems (enqueued on b->stream, or captured from it);
 // `parts` selects phase 1, the iterations and the refresh with the end-of-chunk
 // bookkeeping
-rs_status batch_enqueue_chunk(rs_batch* b, int threads, int ns, int parts = kPartAll) {
+rs_status batch_enqueue_chunk(rs_batch* b, int threads, int ns, int parts = kPartAll,
+                              int p1_stages = kP1All) {
   const std::vector<int> owner = batch_owners(b, ns);
   auto stream_of = [&](int p) { return owner[p] == 0 ? b->stream : b->side[owner[p] - 1]; };
   const rs::BatchPairs pr = batch_pairs(b);
@@ -1861,9 +1874,9 @@ rs_status batch_enqueue_chunk(rs_batch* b, int threads, int ns, int parts = kPar
     const int p = b->order_h[t];
     rs_ctx* c = b->mem[p];
     cudaStream_t st = stream_of(p);
-    BKC(launch_chunk_begin(st, c->ctrl));
+    if (p1_stages & kP1Plan) BKC(launch_chunk_begin(st, c->ctrl));
     c->stream = st;
-    s = enqueue_phase1(c, 0, -1, (int)c->nslots, true);
+    s = enqueue_phase1(c, 0, -1, (int)c->nslots, true, p1_stages);
     c->stream = b->stream;
     if (s != RS_OK) { b->err = c->err; return s; }
   }
@@ -1908,9 +1921,10 @@ rs_status batch_enqueue_chunk(rs_batch* b, int threads, int ns, int parts = kPar
 }
 
 // capture `parts` of one chunk into *out
-rs_status batch_capture(rs_batch* b, int threads, int ns, int parts, cudaGraphExec_t* out) {
+rs_status batch_capture(rs_batch* b, int threads, int ns, int parts, cudaGraphExec_t* out,
+                        int p1_stages = kP1All) {
   BKC(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
-  const rs_status s = batch_enqueue_chunk(b, threads, ns, parts);
+  const rs_status s = batch_enqueue_chunk(b, threads, ns, parts, p1_stages);
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
   if (s != RS_OK) {
@@ -2253,8 +2267,7 @@ rs_status rs_solve_batch(rs_batch* b, double tol, int64_t max_iters, double* con
   return open ? RS_ENOTCONV : RS_OK;
 }
 
-rs_status rs_batch_profile(rs_batch* b, int32_t chunks, double* ms_phase1, double* ms_iterate,
-                           double* ms_refresh) {
+rs_status rs_batch_profile(rs_batch* b, int32_t chunks, double* ms_parts) {
   if (!b || chunks < 1) { g_batch_err = "rs_batch_profile: null batch or chunks < 1"; return RS_EINVAL; }
   DeviceGuard dg(b->mem[0]->device);
   rs_status s;
@@ -2263,28 +2276,30 @@ rs_status rs_batch_profile(rs_batch* b, int32_t chunks, double* ms_phase1, doubl
   if ((s = ensure_schedule(c0, std::max<int64_t>(K, 2 * b->chunk))) != RS_OK) { b->err = c0->err; return s; }
   if ((s = batch_set_order(b, nullptr)) != RS_OK) return s;
   if (!b->tuned && (s = batch_tune(b)) != RS_OK) return s;
-  cudaGraphExec_t g[3] = {nullptr, nullptr, nullptr};
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  constexpr int NP = 6;
+  cudaGraphExec_t g[NP] = {};
+  cudaEvent_t ev[NP + 1] = {};
   auto done = [&](rs_status r) {
     for (cudaGraphExec_t x : g) if (x) cudaGraphExecDestroy(x);
     for (cudaEvent_t e : ev) if (e) cudaEventDestroy(e);
     return r;
   };
-  const int parts[3] = {kPartPhase1, kPartIterate, kPartRefresh};
-  for (int i = 0; i < 3; ++i)
-    if ((s = batch_capture(b, b->threads, b->nstreams, parts[i], &g[i])) != RS_OK) return done(s);
+  const int parts[NP] = {kPartPhase1, kPartPhase1, kPartPhase1, kPartPhase1, kPartIterate, kPartRefresh};
+  const int p1[NP] = {kP1Plan, kP1Rows, kP1Msys, kP1Inv, kP1All, kP1All};
+  for (int i = 0; i < NP; ++i)
+    if ((s = batch_capture(b, b->threads, b->nstreams, parts[i], &g[i], p1[i])) != RS_OK) return done(s);
   for (cudaEvent_t& e : ev)
     if (cudaEventCreate(&e) != cudaSuccess) { b->err = "rs_batch_profile: events"; return done(RS_ECUDA); }
   if ((s = batch_reset(b, 0.0, K)) != RS_OK) return done(s);
-  double acc[3] = {0.0, 0.0, 0.0};
+  double acc[NP] = {};
   for (int q = 0; q < chunks; ++q) {
     cudaError_t e = cudaEventRecord(ev[0], b->stream);
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    for (int i = 0; i < NP && e == cudaSuccess; ++i) {
       e = cudaGraphLaunch(g[i], b->stream);
       if (e == cudaSuccess) e = cudaEventRecord(ev[i + 1], b->stream);
     }
-    if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[NP]);
+    for (int i = 0; i < NP && e == cudaSuccess; ++i) {
       float ms = 0.f;
       e = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
       acc[i] += ms;
@@ -2294,9 +2309,8 @@ rs_status rs_batch_profile(rs_batch* b, int32_t chunks, double* ms_phase1, doubl
       return done(RS_ECUDA);
     }
   }
-  if (ms_phase1) *ms_phase1 = acc[0] / chunks;
-  if (ms_iterate) *ms_iterate = acc[1] / chunks;
-  if (ms_refresh) *ms_refresh = acc[2] / chunks;
+  if (ms_parts)
+    for (int i = 0; i < NP; ++i) ms_parts[i] = acc[i] / chunks;
   return done(RS_OK);
 }
 

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(512) k_msys_batched(const Ctrl* __restrict__ c
                                                       int nslots, PlanView plan, RowsView<T> rows,
                                                       int64_t m, int64_t tau, int64_t nperm,
                                                       int staged, double* __restrict__ M,
-                                                      int64_t m_slot) {
+                                                      int64_t m_slot, float* __restrict__ Mf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t nact = active_slots(ctrl, force, nslots);
   const int64_t s = blockIdx.x / tau;
@@ -122,8 +122,10 @@ __global__ void __launch_bounds__(512) k_msys_batched(const Ctrl* __restrict__ c
   double* Ms = M + s * m_slot;
   if (rows.SA == nullptr) {  // subsample: M[j, l] = A[C_j, C_l]
     const T* rowj = rows.A + (int64_t)entry_row(perm[j]) * rows.lda;
-    for (int64_t l = threadIdx.x; l < tau; l += blockDim.x)
+    for (int64_t l = threadIdx.x; l < tau; l += blockDim.x) {
       Ms[j * tau + l] = (double)rowj[entry_row(perm[l])];
+      if (Mf != nullptr) Mf[s * tau * tau + j * tau + l] = (float)rowj[entry_row(perm[l])];
+    }
     return;
   }
   const T* Ss = rows.SA + s * rows.sa_slot;
@@ -151,13 +153,14 @@ __global__ void __launch_bounds__(512) k_msys_batched(const Ctrl* __restrict__ c
       acc += entry_neg(e) ? -v : v;
     }
     Ms[j * tau + l] = (double)acc;
+    if (Mf != nullptr) Mf[s * tau * tau + j * tau + l] = (float)acc;
   }
 }
 
 template <typename T>
 cudaError_t launch_msys_batched(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
                                 PlanView plan, RowsView<T> rows, int64_t m, int64_t tau,
-                                double* M, int64_t m_slot) {
+                                double* M, int64_t m_slot, float* Mf) {
   const int64_t nperm = plan.perm_stride;
   size_t smem = 0;
   int staged = 0;
@@ -172,7 +175,7 @@ cudaError_t launch_msys_batched(cudaStream_t st, const Ctrl* ctrl, int force, in
     if (e != cudaSuccess) return e;
   }
   k_msys_batched<T><<<(unsigned)(nslots * tau), 512, smem, st>>>(ctrl, force, nslots, plan, rows, m,
-                                                                  tau, nperm, staged, M, m_slot);
+                                                                  tau, nperm, staged, M, m_slot, Mf);
   return cudaGetLastError();
 }
 
@@ -431,7 +434,8 @@ cudaError_t launch_srht_system(cudaStream_t st, const Ctrl* ctrl, int force, int
                                             const T*, int64_t, int64_t, int64_t, T*, int64_t,      \
                                             int64_t, int64_t);                                     \
   template cudaError_t launch_msys_batched<T>(cudaStream_t, const Ctrl*, int, int, PlanView,       \
-                                              RowsView<T>, int64_t, int64_t, double*, int64_t);    \
+                                              RowsView<T>, int64_t, int64_t, double*, int64_t,     \
+                                              float*);                                             \
   template cudaError_t launch_gauss_system<T>(cudaStream_t, const Ctrl*, int, int, const T*,       \
                                               int64_t, const T*, int64_t, int64_t, int64_t, T*,    \
                                               int64_t, int64_t, double*, int64_t);                 \

@@ -61,7 +61,8 @@ cudaError_t launch_sa_msys(cudaStream_t st, const Ctrl* ctrl, int force, int nsl
 template <typename T>
 cudaError_t launch_msys_batched(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
                                 PlanView plan, RowsView<T> rows, int64_t m, int64_t tau,
-                                double* M, int64_t m_slot);
+                                double* M, int64_t m_slot, float* Mf = nullptr);
+
 template <typename T>
 cudaError_t launch_gauss_system(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
                                 const T* ST, int64_t st_slot, const T* A, int64_t lda, int64_t m,
