@@ -144,8 +144,12 @@ def roofline(stats, pk):
                 "unit": "TFLOP/s", "frac": achieved / 1.19, "traffic": None,
                 "peak_source": "measured FP64 FMA probe (DESIGN.md)"}
     achieved = nbytes / (ms * 1e-3) / 1e9
+    traffic = None
+    if name in PROFILED_TRAFFIC and n > 0:
+        t_bytes, t_iters = PROFILED_TRAFFIC[name]
+        traffic = t_bytes * (_its / n) / t_iters  # per launch, scaled to its iterations
     return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+            "frac": achieved / hbm, "traffic": traffic, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
 
 
 def cpu_baseline(X, y, iters_ref, sample_iters=4):
@@ -208,6 +212,87 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ncu DRAM traffic per launch of the iteration kernel (read + write), taken on the
+# X 20000 x 4096 profiling case; the kernel does not touch X, so one launch (50
+# iterations on m = 4096, tau = 256) moves the same bytes at n = 100000
+PROFILED_TRAFFIC = {"iterate": (227.9e6, 50)}
+
+
+def bench_batched(args, rs, dev):
+    """256 uneven problems (d log-uniform in [256, 4096], n = 4 d, lambda log-uniform in
+    [1e-4, 1]), 4 right-hand sides each, count sketch tau = min(128, d / 8), heuristic
+    momentum, mixed precision to 1e-6 per pair; the plain FP64 batch timed over a
+    bounded number of iterations beside it."""
+    import torch
+
+    from synth import batched_problem_torch, batched_specs
+
+    P = 256
+    d, n, lam = batched_specs(P, 4)
+    taus = [min(128, int(v) // 8) for v in d]
+
+    def make(prec):
+        Xs, Ys = [], []
+        for p in range(P):
+            X, Y = batched_problem_torch(int(n[p]), int(d[p]), 4, 10000 + p, device=dev)
+            Xs.append(X if prec == "mixed" else X.double())
+            Ys.append(Y)
+        return Xs, Ys
+
+    Xs, Ys = make("mixed")
+    torch.cuda.synchronize(dev)
+    with ClockSampler(dev.index or 0) as clk:
+        with rs.Batch(Xs, Ys, list(lam), sketch="count", taus=taus, momentum="heuristic", seed=0,
+                      precision="mixed") as b:
+            W, iters, resid, conv = b.solve(tol=TOL, max_iters=400000)
+            info = b.info()
+            parts = b.profile(2)
+    solve_s = info["solve_ms"] / 1e3
+    it_p = iters.max(axis=1).astype(np.float64)
+    a_bytes = float(np.sum(it_p * d.astype(np.float64) ** 2 * 4))
+    out = {"workload": "batched", "converged": bool(conv), "time_to_tol_ms": info["solve_ms"],
+           "setup_ms": info["setup_ms"], "tune_ms": info["tune_ms"],
+           "iter_threads": info["iter_threads"], "phase1_streams": info["phase1_streams"],
+           "problem_iters_per_s": float(it_p.sum() / solve_s), "max_iters": int(iters.max()),
+           "mean_iters": float(iters.mean()), "max_resid": float(resid.max()),
+           "a_bytes_per_s_gbs": a_bytes / solve_s / 1e9, "chunk_profile_all_running_ms": parts,
+           "clocks": clk.summary()}
+    del Xs
+    Xd, Yd = make("fp64")
+    with rs.Batch(Xd, Yd, list(lam), sketch="count", taus=taus, momentum="heuristic", seed=0,
+                  precision="fp64") as b:
+        K = 2000
+        _, pit, _, _ = b.solve(tol=0.0, max_iters=K)
+        pinfo = b.info()
+    out["plain_fp64_problem_iters_per_s"] = float(pit.max(axis=1).sum() / (pinfo["solve_ms"] / 1e3))
+    out["plain_fp64_time_to_tol_ms_extrapolated"] = pinfo["solve_ms"] / K * int(iters.max())
+    out["speedup_vs_plain_fp64"] = out["plain_fp64_time_to_tol_ms_extrapolated"] / info["solve_ms"]
+    print(json.dumps(out), flush=True)
+
+
+def bench_sparse(args, rs, dev):
+    """Zipf-sparse X 1e6 x 5e4 (about 5e6 entries, bfloat16 values), lambda 0.1, SubCount
+    s = 4096 -> tau = 512, heuristic momentum, matrix-free; mixed and plain FP64 over
+    the same bounded number of iterations."""
+    from synth import sparse_problem
+
+    n, d = 1_000_000, 50_000
+    rowptr, colidx, vals, y, _ = sparse_problem(n, d, 5_000_000, 3000, bf16=True)
+    K = 2000
+    out = {"workload": "sparse", "n": n, "d": d, "nnz": int(len(vals)), "iters": K}
+    for prec, bf in (("mixed", True), ("fp64", False)):
+        X = rs.CSR(rowptr, colidx, vals, (n, d), bf16=bf)
+        with rs.Solver(X, y, 0.1, sketch="subcount", tau=512, momentum="heuristic", seed=0,
+                       precision=prec, sub_s=4096) as s:
+            w, hist, iters, conv = s.solve(tol=TOL, max_iters=K)
+            setup_ms, solve_ms = s.timings()
+            out[prec] = {"iters_per_s": iters / (solve_ms / 1e3), "setup_ms": setup_ms,
+                         "solve_ms": solve_ms, "iters": iters, "final_rel": float(hist[-1]),
+                         "true_rel": s.true_residual(w)}
+    out["speedup_vs_plain_fp64"] = out["mixed"]["iters_per_s"] / out["fp64"]["iters_per_s"]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -219,9 +304,21 @@ def main():
     ap.add_argument("--small", action="store_true",
                     help="profiling case: X 20000 x 4096 (328 MB, larger than L2), same sketch and "
                          "schedule; prints the line of that case (not the benchmark workload)")
+    ap.add_argument("--workload", default="dense", choices=["dense", "batched", "sparse"],
+                    help="dense: the benchmark line; batched / sparse: measurement lines of the "
+                         "256-problem batch and the Zipf-sparse matrix-free solve")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "dense":
+        import torch
+
+        import paper_2105_05565_gb300 as rs
+
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        rs.lib()
+        return (bench_batched if args.workload == "batched" else bench_sparse)(args, rs, dev)
 
     import torch
 

@@ -15,7 +15,10 @@ What it computes follows the paper (arXiv 2105.05565, "RidgeSketch"):
 * the five sketches, each built as an explicit dense m x tau matrix S from its
   definition in Section 4 (Gaussian, Subsample, Count, SubCount, SRHT);
 * the momentum parameter rules of Sections 6.1-6.2 and 8.1 (eqs. (38), (40),
-  (49)-(50), (66), (67)).
+  (49)-(50), (66), (67));
+* the learned sketch proposal (``oracle.learned``): features, the scoring
+  network and its gradient, the proposal, Gumbel-top-tau selection, the
+  per-coordinate labels from the projection identity of Section 3, and Adam.
 
 Random choices come from the counter-based generator in ``oracle.rng`` which is
 written from the published SplitMix64 definition; the GPU library implements
@@ -45,3 +48,4 @@ from .solver import (  # noqa: F401
     solve_matrix_free,
     true_residual,
 )
+from . import learned  # noqa: F401,E402

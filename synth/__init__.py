@@ -221,3 +221,17 @@ def sparse_problem(n: int, d: int, nnz_target: int, seed: int, noise: float = 0.
 
 
 __all__ += ["bf16_round", "sparse_problem"]
+
+
+def mlp_init(seed: int) -> np.ndarray:
+    """Initial parameters of the 4 -> 64 -> 64 -> 1 scoring network (flat, 4545
+    entries: W1 64 x 4, b1, W2 64 x 64, b2, w3, b3): He-normal weights
+    (std sqrt(2 / fan_in); sqrt(1 / 64) for the output layer), zero biases."""
+    g = _rng(seed)
+    W1 = g.standard_normal((64, 4)) * np.sqrt(2.0 / 4)
+    W2 = g.standard_normal((64, 64)) * np.sqrt(2.0 / 64)
+    w3 = g.standard_normal(64) * np.sqrt(1.0 / 64)
+    return np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), w3, [0.0]])
+
+
+__all__ += ["mlp_init"]
