@@ -345,6 +345,56 @@ rs_status rs_batch_set_launch(rs_batch* b, int32_t iter_threads, int32_t phase1_
  * bookkeeping. The solution state is overwritten. */
 rs_status rs_batch_profile(rs_batch* b, int32_t chunks, double* ms_parts);
 
+/*
+ * Learned sketch proposal (subsample sketch of a dense context). The rows of each
+ * iteration's sample are drawn without replacement from
+ *   p_j = (1 - eps) softmax(s)_j + eps / m,
+ * s_j the score of a 4 -> 64 -> 64 -> 1 network (ReLU; bfloat16 weights and
+ * activations, FP32 accumulation) on the standardised features of row j at the
+ * chunk's first iteration k0: ln A_jj, ln(1 + |r_j| / rms(r)), ln ||A[:, j]||_2,
+ * ln(1 + age_j) (age_j = k0 - the last iteration whose sample held j, k0 + 1 if
+ * none). The draw for iteration k: the tau rows with the largest
+ * ln p_j - ln(-ln u_j), u_j = (hi32(draw(seed, k, 4, j)) + 1/2) 2^-32 (stream 4
+ * of the counter-based generator; Gumbel-top-k), in increasing row order. The
+ * proposal is evaluated once per chunk (opts.chunk iterations), so that the
+ * chunk's sketched systems are still formed and inverted together. This replaces
+ * the paper's fixed sampling probabilities (uniform, or proportional to A_jj in
+ * Section 6) by predicted ones; uniform sampling stays available.
+ *   w_bf16  4545 bfloat16 weights, host pointer, copied: W1 (64 x 4, row-major),
+ *           b1 (64), W2 (64 x 64, row-major, W2[o, i]), b2 (64), w3 (64), b3; NULL =
+ *           uniform proposal (p_j = 1 / m) drawn the same way
+ *   eps     uniform share in [0, 1]; eps < 0 switches back to the plain sampler
+ * RS_EUNSUPPORTED for other sketches, matrix-free contexts or m > 16384.
+ */
+rs_status rs_set_proposal(rs_ctx* c, const uint16_t* w_bf16, double eps);
+/* The m x 4 standardised feature rows (FP32, row-major, host pointer) at the
+ * context's current state, as the proposal would see them at a chunk start. */
+rs_status rs_proposal_features(rs_ctx* c, float* Z_out);
+
+/*
+ * Training the proposal's network: FP32 master weights, Adam (beta1 0.9, beta2
+ * 0.999, eps 1e-8, bias-corrected), and the bfloat16 copy that the forward uses.
+ * The loss is mean((s - y)^2) / 2 over the rows; the forward rounds weights and
+ * hidden activations to bfloat16 and the gradient passes those roundings
+ * straight through. Z (n x 4 FP32, row-major) and y (n FP32) are device
+ * pointers; everything runs on `stream` (NULL = default stream).
+ */
+typedef struct rs_mlp rs_mlp; /* opaque; owned by the library until rs_mlp_destroy */
+rs_status rs_mlp_create(const float* theta0 /* host, 4545 */, int32_t device, void* stream,
+                        rs_mlp** out);
+/* gradient (host, 4545; NULL to skip) and loss at the current weights */
+rs_status rs_mlp_grad(rs_mlp* h, const float* Z, const float* y, int64_t n, float* grad_out,
+                      double* loss_out);
+/* one Adam step on the rows; the loss before the step (NULL to skip) */
+rs_status rs_mlp_step(rs_mlp* h, const float* Z, const float* y, int64_t n, double lr,
+                      double* loss_out);
+/* scores of n feature rows into s_out (device, n FP32), asynchronous */
+rs_status rs_mlp_scores(rs_mlp* h, const float* Z, int64_t n, float* s_out);
+/* FP32 master weights and/or their bfloat16 copy (host pointers, 4545 each) */
+rs_status rs_mlp_get(rs_mlp* h, float* theta_out, uint16_t* bf16_out);
+void rs_mlp_destroy(rs_mlp* h);
+const char* rs_mlp_last_error(const rs_mlp* h);
+
 #ifdef __cplusplus
 }
 #endif

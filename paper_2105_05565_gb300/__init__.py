@@ -13,7 +13,7 @@ import os
 
 import numpy as np
 
-__all__ = ["Solver", "Batch", "CSR", "RidgeSketch", "RSError", "lib", "SKETCHES", "MOMENTA"]
+__all__ = ["Solver", "Batch", "CSR", "MLP", "RidgeSketch", "RSError", "lib", "SKETCHES", "MOMENTA"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libridgesketch.so")
@@ -93,6 +93,15 @@ _SIGS = {
                              ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "rs_batch_set_launch": (_I32, [_P, _I32, _I32]),
     "rs_batch_profile": (_I32, [_P, _I32, _P]),
+    "rs_set_proposal": (_I32, [_P, _P, _D]),
+    "rs_proposal_features": (_I32, [_P, _P]),
+    "rs_mlp_create": (_I32, [_P, _I32, _P, ctypes.POINTER(_P)]),
+    "rs_mlp_grad": (_I32, [_P, _P, _P, _I64, _P, ctypes.POINTER(_D)]),
+    "rs_mlp_step": (_I32, [_P, _P, _P, _I64, _D, ctypes.POINTER(_D)]),
+    "rs_mlp_scores": (_I32, [_P, _P, _I64, _P]),
+    "rs_mlp_get": (_I32, [_P, _P, _P]),
+    "rs_mlp_destroy": (None, [_P]),
+    "rs_mlp_last_error": (ctypes.c_char_p, [_P]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -323,10 +332,121 @@ class Solver:
                                        arr[i].iters)
                 for i in range(n.value)}
 
+    def set_proposal(self, weights_bf16=None, eps=0.1):
+        """Draw the subsample rows from the learned proposal: ``weights_bf16`` (4545
+        uint16 bfloat16 bit patterns) or None for the uniform proposal; eps < 0
+        switches back to the plain sampler."""
+        if weights_bf16 is None:
+            ptr = None
+        else:
+            self._wkeep = np.ascontiguousarray(weights_bf16, dtype=np.uint16)
+            if self._wkeep.size != MLP_PARAMS:
+                raise ValueError(f"weights_bf16 must hold {MLP_PARAMS} values")
+            ptr = self._wkeep.ctypes.data
+        self._check(lib().rs_set_proposal(self._ctx, ptr, float(eps)))
+
+    def proposal_features(self):
+        """(m, 4) float32 standardised features at the current state."""
+        Z = np.empty((self.m, 4), np.float32)
+        self._check(lib().rs_proposal_features(self._ctx, Z.ctypes.data))
+        return Z
+
     def timings(self):
         a, b = _D(), _D()
         self._check(lib().rs_timings(self._ctx, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+
+MLP_PARAMS = 4545
+
+
+class MLP:
+    """The proposal's 4 -> 64 -> 64 -> 1 network on the GPU for training: FP32
+    master weights, Adam, and the bfloat16 copy the proposal reads
+    (rs_mlp_create / rs_mlp_grad / rs_mlp_step / rs_mlp_get)."""
+
+    def __init__(self, theta0, device=0, stream=None):
+        L = lib()
+        self._h = None
+        th = np.ascontiguousarray(theta0, dtype=np.float32)
+        if th.size != MLP_PARAMS:
+            raise ValueError(f"theta0 must hold {MLP_PARAMS} values")
+        h = _P()
+        st = stream if stream is not None else _default_stream(device)
+        status = L.rs_mlp_create(th.ctypes.data, int(device), st, ctypes.byref(h))
+        if status != RS_OK:
+            raise RSError(status, L.rs_mlp_last_error(None).decode())
+        self._h = h
+        self.device = device
+
+    def _check(self, status):
+        if status != RS_OK:
+            raise RSError(status, lib().rs_mlp_last_error(self._h).decode())
+
+    @staticmethod
+    def _dev(x, dtype):
+        import torch
+
+        t = torch.as_tensor(x)
+        return t.to(device="cuda", dtype=dtype).contiguous()
+
+    def grad(self, Z, y):
+        """(loss, gradient (4545,) float32) of mean((s - y)^2) / 2."""
+        import torch
+
+        Zd, yd = self._dev(Z, torch.float32), self._dev(y, torch.float32)
+        g = np.empty(MLP_PARAMS, np.float32)
+        loss = _D()
+        self._check(lib().rs_mlp_grad(self._h, Zd.data_ptr(), yd.data_ptr(), int(yd.numel()),
+                                      g.ctypes.data, ctypes.byref(loss)))
+        return loss.value, g
+
+    def step(self, Z, y, lr=1e-3):
+        """One Adam step; returns the loss before it."""
+        import torch
+
+        Zd, yd = self._dev(Z, torch.float32), self._dev(y, torch.float32)
+        loss = _D()
+        self._check(lib().rs_mlp_step(self._h, Zd.data_ptr(), yd.data_ptr(), int(yd.numel()),
+                                      float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def scores(self, Z):
+        import torch
+
+        Zd = self._dev(Z, torch.float32)
+        n = Zd.shape[0]
+        out = torch.empty(n, dtype=torch.float32, device="cuda")
+        self._check(lib().rs_mlp_scores(self._h, Zd.data_ptr(), int(n), out.data_ptr()))
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    def params(self):
+        th = np.empty(MLP_PARAMS, np.float32)
+        self._check(lib().rs_mlp_get(self._h, th.ctypes.data, None))
+        return th
+
+    def weights_bf16(self):
+        w = np.empty(MLP_PARAMS, np.uint16)
+        self._check(lib().rs_mlp_get(self._h, None, w.ctypes.data))
+        return w
+
+    def close(self):
+        if self._h is not None:
+            lib().rs_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Batch:

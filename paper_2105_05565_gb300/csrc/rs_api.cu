@@ -98,6 +98,17 @@ struct rs_ctx {
   double *rS = nullptr, *delta = nullptr;
   int64_t sa_slot = 0, m_slot = 0, l_slot = 0;
   int64_t bq = 0;             // S^T A blocked by slices of bq rows of the iterate (0: row-major)
+  // learned proposal of the subsample rows (rs_set_proposal)
+  bool learned = false;
+  bool lp_uniform = false;     // no network: p_j = 1 / m
+  float lp_eps = 0.1f;
+  uint16_t* lp_w = nullptr;    // network weights, bfloat16
+  float* lp_raw = nullptr;     // 2 m work space
+  float* lp_zstat = nullptr;   // 2 m standardised static features
+  double* lp_stats = nullptr;  // 8
+  float* lp_score = nullptr;   // m scores
+  float* lp_feat = nullptr;    // m x 4 features (rs_proposal_features)
+  int32_t* lp_last = nullptr;  // last iteration whose sample held the row (-1: never)
   int32_t *perm = nullptr, *boff = nullptr;
   int32_t* inv = nullptr;  // per slot (stride ld): row -> bucket | sign (bucket-row sketches)
   // persistent iteration kernel over the whole GPU (bucket-row sketches)
@@ -189,7 +200,8 @@ void free_all(rs_ctx* c) {
                   c->sx_rowptr, c->sx_colidx, c->sx_val, c->sx_colptr, c->sx_rowidx, c->sx_cval,
                   c->sx_pcol, c->sx_pstart, c->sx_cpiece, c->mf_bsum, c->mf_boffs, c->mf_tot,
                   c->mf_crow, c->mf_cptr, c->mf_ebuck, c->mf_eval, c->mf_v, c->mf_pu, c->mf_pud,
-                  c->mf_z};
+                  c->mf_z, c->lp_w, c->lp_raw, c->lp_zstat, c->lp_stats, c->lp_score, c->lp_feat,
+                  c->lp_last};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->ctrl_h) cudaFreeHost(c->ctrl_h);
@@ -258,6 +270,13 @@ rs_status with_vt(const rs_ctx* c, F&& f) {
 // sketch plan of `nslots` consecutive iterations starting at k0_arg (< 0: ctrl->k)
 rs_status enqueue_gen(rs_ctx* c, int64_t k0_arg, int nslots) {
   cudaStream_t st = c->stream;
+  if (c->learned) {  // rows drawn from the learned proposal (the chunk's plans at once)
+    CKC(c, launch_lp_plans(st, c->ctrl, k0_arg >= 0 ? 1 : 0, nslots, k0_arg, c->seed,
+                           c->lp_uniform ? nullptr : c->lp_w, c->lp_eps, c->lp_zstat, c->lp_stats,
+                           c->r, c->lp_last, c->m, c->tau, c->lp_score, c->perm, c->perm_stride,
+                           c->boff, c->boff_stride, k0_arg < 0));
+    return RS_OK;
+  }
   switch (c->sketch) {
     case RS_SUBSAMPLE:
       CKC(c, launch_gen_sample(st, c->ctrl, k0_arg, nslots, c->seed, c->m, c->tau, 0, 1, c->tau,
@@ -1175,6 +1194,7 @@ rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int3
   rs_status s;
   if ((s = ensure_schedule(c, std::max<int64_t>(max_iters, 1))) != RS_OK) return s;
   CKC(c, launch_init_state(st, c->m, c->b, c->w, c->wp, c->r, c->rp, c->u));
+  if (c->learned) CKC(c, cudaMemsetAsync(c->lp_last, 0xFF, c->m * sizeof(int32_t), st));
   const double h0 = c->r0 > 0.0 ? 1.0 : 0.0;
   CKC(c, cudaMemcpyAsync(c->hist, &h0, sizeof(double), cudaMemcpyHostToDevice, st));
   CKC(c, cudaStreamSynchronize(st));
@@ -1326,6 +1346,7 @@ rs_status rs_set_state(rs_ctx* c, const double* w, const double* w_prev, const d
   CKC(c, cudaMemcpyAsync(c->r, r, bytes, cudaMemcpyHostToDevice, c->stream));
   CKC(c, cudaMemcpyAsync(c->rp, r_prev, bytes, cudaMemcpyHostToDevice, c->stream));
   CKC(c, cudaMemsetAsync(c->u, 0, bytes, c->stream));
+  if (c->learned) CKC(c, cudaMemsetAsync(c->lp_last, 0xFF, c->m * sizeof(int32_t), c->stream));
   std::memset(c->ctrl_h, 0, sizeof(Ctrl));
   c->ctrl_h->k = k;
   c->ctrl_h->k0 = k;
@@ -1613,6 +1634,60 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
   h->stop = 0;
   h->max_iters = INT64_MAX;
   if ((s = write_ctrl(c)) != RS_OK) return s;
+  CKC(c, cudaStreamSynchronize(c->stream));
+  return RS_OK;
+}
+
+rs_status rs_set_proposal(rs_ctx* c, const uint16_t* w_bf16, double eps) {
+  if (!c) { set_global_error("rs_set_proposal: null context"); return RS_EINVAL; }
+  DeviceGuard dg(c->device);
+  if (eps < 0.0) {  // back to the plain sampler
+    c->learned = false;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    return RS_OK;
+  }
+  if (c->sketch != RS_SUBSAMPLE || c->sparse)
+    FAILC(c, RS_EUNSUPPORTED, "rs_set_proposal: the learned proposal draws subsample sketches of dense A");
+  if (!(eps <= 1.0)) FAILC(c, RS_EINVAL, "rs_set_proposal: eps must be in [0, 1]");
+  int64_t np2 = 1;
+  while (np2 < c->m) np2 <<= 1;
+  if (np2 * 8 > 200 * 1024) FAILC(c, RS_EUNSUPPORTED, "rs_set_proposal: m > 16384");
+  cudaStream_t st = c->stream;
+  const size_t m = (size_t)c->m;
+  if (!c->lp_w) {
+    CKC(c, cudaMalloc(&c->lp_w, kMlpParams * sizeof(uint16_t)));
+    CKC(c, cudaMalloc(&c->lp_raw, 2 * m * sizeof(float)));
+    CKC(c, cudaMalloc(&c->lp_zstat, 2 * m * sizeof(float)));
+    CKC(c, cudaMalloc(&c->lp_stats, 8 * sizeof(double)));
+    CKC(c, cudaMalloc(&c->lp_score, m * sizeof(float)));
+    CKC(c, cudaMalloc(&c->lp_feat, m * 4 * sizeof(float)));
+    CKC(c, cudaMalloc(&c->lp_last, m * sizeof(int32_t)));
+    CKC(c, cudaMemsetAsync(c->lp_last, 0xFF, m * sizeof(int32_t), st));
+    if (c->mixed())
+      CKC(c, launch_lp_static<float>(st, static_cast<const float*>(c->A), c->ld, c->m, c->lp_raw,
+                                     c->lp_zstat));
+    else
+      CKC(c, launch_lp_static<double>(st, static_cast<const double*>(c->A), c->ld, c->m, c->lp_raw,
+                                      c->lp_zstat));
+  }
+  c->lp_uniform = (w_bf16 == nullptr);
+  if (w_bf16) CKC(c, cudaMemcpyAsync(c->lp_w, w_bf16, kMlpParams * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
+  c->lp_eps = (float)eps;
+  c->learned = true;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  CKC(c, cudaStreamSynchronize(st));
+  return RS_OK;
+}
+
+rs_status rs_proposal_features(rs_ctx* c, float* Z_out) {
+  if (!c || !Z_out) return RS_EINVAL;
+  if (!c->learned) FAILC(c, RS_EINVAL, "rs_proposal_features: no proposal set");
+  DeviceGuard dg(c->device);
+  rs_status s = read_ctrl(c);
+  if (s != RS_OK) return s;
+  CKC(c, launch_lp_features(c->stream, c->ctrl, c->ctrl_h->k, c->lp_zstat, c->lp_stats, c->r,
+                            c->lp_last, c->m, c->lp_score, c->lp_feat));
+  CKC(c, cudaMemcpyAsync(Z_out, c->lp_feat, c->m * 4 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   CKC(c, cudaStreamSynchronize(c->stream));
   return RS_OK;
 }
@@ -2359,5 +2434,148 @@ rs_status rs_batch_info(const rs_batch* b, double* setup_ms, double* solve_ms, d
   if (phase1_streams) *phase1_streams = b->nstreams;
   return RS_OK;
 }
+
+}  // extern "C"
+
+// ===========================================================================
+// training the proposal's network (rs_mlp_*): FP32 master weights, Adam moments,
+// the bfloat16 copy the proposal reads, gradient work space
+// ===========================================================================
+struct rs_mlp {
+  float *theta = nullptr, *mom = nullptr, *vel = nullptr, *grad = nullptr;
+  uint16_t* wbf = nullptr;
+  float *part = nullptr, *loss_part = nullptr;
+  double* loss = nullptr;
+  int64_t cap_blocks = 0;
+  int64_t step = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+};
+
+namespace {
+std::string g_mlp_err;
+
+#define MKC(call)                                                                 \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                \
+      return (e_ == cudaErrorMemoryAllocation) ? RS_ENOMEM : RS_ECUDA;             \
+    }                                                                             \
+  } while (0)
+
+void mlp_free(rs_mlp* h) {
+  void* ptrs[] = {h->theta, h->mom, h->vel, h->grad, h->wbf, h->part, h->loss_part, h->loss};
+  for (void* p : ptrs) if (p) cudaFree(p);
+}
+
+rs_status mlp_grad(rs_mlp* h, const float* Z, const float* y, int64_t n) {
+  const int64_t nb = mlp_grad_blocks(n);
+  if (nb > h->cap_blocks) {
+    if (h->part) cudaFree(h->part);
+    if (h->loss_part) cudaFree(h->loss_part);
+    h->part = nullptr;
+    h->loss_part = nullptr;
+    MKC(cudaMalloc(&h->part, (size_t)nb * kMlpParams * sizeof(float)));
+    MKC(cudaMalloc(&h->loss_part, (size_t)nb * sizeof(float)));
+    h->cap_blocks = nb;
+  }
+  MKC(launch_mlp_grad(h->stream, h->theta, Z, y, n, h->part, h->loss_part, h->grad, h->loss));
+  return RS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+rs_status rs_mlp_create(const float* theta0, int32_t device, void* stream, rs_mlp** out) {
+  if (out) *out = nullptr;
+  if (!theta0 || !out) { g_mlp_err = "rs_mlp_create: null argument"; return RS_EINVAL; }
+  rs_mlp* h = new (std::nothrow) rs_mlp();
+  if (!h) { g_mlp_err = "rs_mlp_create: out of host memory"; return RS_ENOMEM; }
+  DeviceGuard dg(device);
+  h->device = device;
+  h->stream = static_cast<cudaStream_t>(stream);
+  auto fail = [&](rs_status s) {
+    g_mlp_err = h->err;
+    mlp_free(h);
+    delete h;
+    return s;
+  };
+  const size_t pb = kMlpParams * sizeof(float);
+  if (cudaMalloc(&h->theta, pb) != cudaSuccess || cudaMalloc(&h->mom, pb) != cudaSuccess ||
+      cudaMalloc(&h->vel, pb) != cudaSuccess || cudaMalloc(&h->grad, pb) != cudaSuccess ||
+      cudaMalloc(&h->wbf, kMlpParams * sizeof(uint16_t)) != cudaSuccess ||
+      cudaMalloc(&h->loss, sizeof(double)) != cudaSuccess) {
+    h->err = "rs_mlp_create: device allocation";
+    return fail(RS_ENOMEM);
+  }
+  if (cudaMemcpyAsync(h->theta, theta0, pb, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->mom, 0, pb, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->vel, 0, pb, h->stream) != cudaSuccess ||
+      launch_f32_to_bf16(h->stream, h->theta, kMlpParams, h->wbf) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    h->err = "rs_mlp_create: upload";
+    return fail(RS_ECUDA);
+  }
+  *out = h;
+  return RS_OK;
+}
+
+rs_status rs_mlp_grad(rs_mlp* h, const float* Z, const float* y, int64_t n, float* grad_out,
+                      double* loss_out) {
+  if (!h || !Z || !y || n < 1) { g_mlp_err = "rs_mlp_grad: bad arguments"; return RS_EINVAL; }
+  DeviceGuard dg(h->device);
+  rs_status s = mlp_grad(h, Z, y, n);
+  if (s != RS_OK) return s;
+  if (grad_out) MKC(cudaMemcpyAsync(grad_out, h->grad, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  if (loss_out) MKC(cudaMemcpyAsync(loss_out, h->loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  MKC(cudaStreamSynchronize(h->stream));
+  return RS_OK;
+}
+
+rs_status rs_mlp_step(rs_mlp* h, const float* Z, const float* y, int64_t n, double lr,
+                      double* loss_out) {
+  if (!h || !Z || !y || n < 1 || !(lr > 0.0)) { g_mlp_err = "rs_mlp_step: bad arguments"; return RS_EINVAL; }
+  DeviceGuard dg(h->device);
+  rs_status s = mlp_grad(h, Z, y, n);
+  if (s != RS_OK) return s;
+  h->step += 1;
+  MKC(launch_mlp_adam(h->stream, h->theta, h->mom, h->vel, h->grad, h->step, (float)lr, 0.9f,
+                      0.999f, 1e-8f, h->wbf));
+  if (loss_out) {
+    MKC(cudaMemcpyAsync(loss_out, h->loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    MKC(cudaStreamSynchronize(h->stream));
+  }
+  return RS_OK;
+}
+
+rs_status rs_mlp_scores(rs_mlp* h, const float* Z, int64_t n, float* s_out) {
+  if (!h || !Z || !s_out || n < 0) { g_mlp_err = "rs_mlp_scores: bad arguments"; return RS_EINVAL; }
+  DeviceGuard dg(h->device);
+  MKC(launch_mlp_forward(h->stream, h->wbf, Z, n, s_out));
+  return RS_OK;
+}
+
+rs_status rs_mlp_get(rs_mlp* h, float* theta_out, uint16_t* bf16_out) {
+  if (!h) { g_mlp_err = "rs_mlp_get: null handle"; return RS_EINVAL; }
+  DeviceGuard dg(h->device);
+  if (theta_out) MKC(cudaMemcpyAsync(theta_out, h->theta, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  if (bf16_out) MKC(cudaMemcpyAsync(bf16_out, h->wbf, kMlpParams * sizeof(uint16_t), cudaMemcpyDeviceToHost, h->stream));
+  MKC(cudaStreamSynchronize(h->stream));
+  return RS_OK;
+}
+
+void rs_mlp_destroy(rs_mlp* h) {
+  if (!h) return;
+  {
+    DeviceGuard dg(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    mlp_free(h);
+  }
+  delete h;
+}
+
+const char* rs_mlp_last_error(const rs_mlp* h) { return h ? h->err.c_str() : g_mlp_err.c_str(); }
 
 }  // extern "C"

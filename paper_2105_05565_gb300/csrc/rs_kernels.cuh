@@ -261,6 +261,34 @@ int batch_cluster_fit(int nrhs, int64_t tau_max, int64_t bq_max, int64_t perm_ma
 cudaError_t launch_batch_finish(cudaStream_t st, Ctrl* const* ctrls, int P, int nrhs,
                                 BatchPairs pairs, int32_t* alive, int32_t* out);
 
+// ---- learned sketch proposal (rs_learned.cu) ----
+constexpr int kMlpParams = 4545;  // W1 64x4, b1, W2 64x64, b2, w3, b3
+// raw: 2 m floats of work space; zstat: 2 m standardised static features
+template <typename T>
+cudaError_t launch_lp_static(cudaStream_t st, const T* A, int64_t lda, int64_t m, float* raw,
+                             float* zstat);
+// plans of the chunk's slots drawn from the proposal (w null: uniform); stats: 5
+// doubles, score: m floats of work space; last: last visit per row (updated when
+// update_age)
+cudaError_t launch_lp_plans(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, int64_t k0_arg,
+                            uint64_t seed, const uint16_t* w, float eps, const float* zstat,
+                            double* stats, const double* r, int32_t* last, int64_t m, int64_t tau,
+                            float* score, int32_t* perm, int64_t perm_stride, int32_t* boff,
+                            int64_t boff_stride, bool update_age);
+// the m x 4 feature rows at iteration k0 (the network's inputs)
+cudaError_t launch_lp_features(cudaStream_t st, const Ctrl* ctrl, int64_t k0, const float* zstat,
+                               double* stats, const double* r, const int32_t* last, int64_t m,
+                               float* score, float* feat_out);
+cudaError_t launch_mlp_forward(cudaStream_t st, const uint16_t* w, const float* Z, int64_t n,
+                               float* s_out);
+int mlp_grad_blocks(int64_t n);
+// part: mlp_grad_blocks(n) x kMlpParams floats, loss_part: mlp_grad_blocks(n) floats
+cudaError_t launch_mlp_grad(cudaStream_t st, const float* theta, const float* Z, const float* y,
+                            int64_t n, float* part, float* loss_part, float* grad, double* loss);
+cudaError_t launch_mlp_adam(cudaStream_t st, float* theta, float* mom, float* vel, const float* grad,
+                            int64_t step, float lr, float b1, float b2, float eps, uint16_t* w_bf16);
+cudaError_t launch_f32_to_bf16(cudaStream_t st, const float* x, int64_t n, uint16_t* out);
+
 // ---- iterate / residual update (rs_update.cu) ----
 struct UpdateArgs {
   const double* gam;  // gamma_k table

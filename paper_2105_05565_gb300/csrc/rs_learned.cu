@@ -1,0 +1,558 @@
+// Learned sketch proposal: per-coordinate features, the 4 -> 64 -> 64 -> 1 scoring
+// network (bfloat16 weights and activations, FP32 accumulation), the eps-mixed
+// softmax proposal and Gumbel-top-tau selection of the subsample sketch's rows;
+// the network's gradient and Adam for training it on solver trajectories.
+//
+// The proposal is evaluated once per chunk, from the residual and the visit ages
+// at the chunk's first iteration k0; iteration k0 + t of the chunk draws its own
+// sample with the Gumbel noise of stream 4 of the counter-based generator:
+//   z_j   = standardised (ln A_jj, ln(1 + |r_j| / rms(r)), ln ||A[:, j]||, ln(1 + age_j))
+//   s_j   = w3 . relu(W2 relu(W1 z_j + b1) + b2) + b3
+//   p_j   = (1 - eps) softmax(s)_j + eps / m
+//   key_j = ln p_j - ln(-ln u_j),  u_j = (hi32(draw(seed, k, 4, j)) + 1/2) 2^-32
+//   C_k   = the tau largest keys (ties: smaller index), rows in increasing order.
+// Sorting the keys descending and keeping the first tau is a draw of tau rows
+// without replacement from p (Gumbel-top-k).
+#include <algorithm>
+
+#include "rs_kernels.cuh"
+
+namespace rs {
+
+namespace {
+constexpr int kH = 64;
+constexpr int kNF = 4;
+constexpr int kOffB1 = kH * kNF;
+constexpr int kOffW2 = kOffB1 + kH;
+constexpr int kOffB2 = kOffW2 + kH * kH;
+constexpr int kOffW3 = kOffB2 + kH;
+constexpr int kOffB3 = kOffW3 + kH;
+static_assert(kOffB3 + 1 == kMlpParams, "parameter layout");
+
+__device__ __forceinline__ float bf16_to_f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+// round to the nearest bfloat16 (ties to even) and back to FP32
+__device__ __forceinline__ float round_bf16(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t r = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ uint16_t to_bf16(float x) {
+  return (uint16_t)(__float_as_uint(round_bf16(x)) >> 16);
+}
+
+// network weights (bfloat16 values as FP32) in shared memory
+struct MlpSmem {
+  float p[kMlpParams + 3];
+};
+
+__device__ __forceinline__ void load_weights_bf16(MlpSmem& s, const uint16_t* w) {
+  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) s.p[i] = bf16_to_f(w[i]);
+}
+
+// forward of one feature row; h1 rounded to bfloat16 on the way
+__device__ __forceinline__ float mlp_forward(const MlpSmem& s, const float z[kNF]) {
+  float h1[kH];
+#pragma unroll
+  for (int o = 0; o < kH; ++o) {
+    float a = s.p[kOffB1 + o];
+#pragma unroll
+    for (int i = 0; i < kNF; ++i) a = fmaf(s.p[o * kNF + i], z[i], a);
+    h1[o] = round_bf16(fmaxf(a, 0.f));
+  }
+  float out = s.p[kOffB3];
+  for (int o = 0; o < kH; ++o) {
+    const float4* w2 = reinterpret_cast<const float4*>(s.p + kOffW2 + o * kH);
+    float a = s.p[kOffB2 + o];
+#pragma unroll
+    for (int i4 = 0; i4 < kH / 4; ++i4) {
+      const float4 w = w2[i4];
+      a = fmaf(w.x, h1[4 * i4], a);
+      a = fmaf(w.y, h1[4 * i4 + 1], a);
+      a = fmaf(w.z, h1[4 * i4 + 2], a);
+      a = fmaf(w.w, h1[4 * i4 + 3], a);
+    }
+    out = fmaf(s.p[kOffW3 + o], round_bf16(fmaxf(a, 0.f)), out);
+  }
+  return out;
+}
+}  // namespace
+
+// ---- static features: standardised ln A_jj and ln ||A[:, j]|| (A symmetric) ----
+template <typename T>
+__global__ void __launch_bounds__(256) k_lp_rownorm(const T* __restrict__ A, int64_t lda, int64_t m,
+                                                    float* __restrict__ raw) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= m) return;
+  double sq = 0.0;
+  for (int64_t c = lane; c < m; c += 32) {
+    const double v = (double)A[row * lda + c];
+    sq += v * v;
+  }
+  sq = warp_sum(sq);
+  if (lane == 0) {
+    raw[row] = (float)log((double)A[row * lda + row]);
+    raw[m + row] = (float)(0.5 * log(sq));
+  }
+}
+
+// z = (x - mean) / (std + 1e-6) of `count` arrays of length m (one block each)
+__global__ void __launch_bounds__(1024) k_lp_standardise(const float* __restrict__ raw, int64_t m,
+                                                         float* __restrict__ z) {
+  __shared__ double sh[32];
+  const float* x = raw + (int64_t)blockIdx.x * m;
+  double s = 0.0;
+  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) s += x[j];
+  const double mean = block_sum(s, sh) / (double)m;
+  __syncthreads();
+  double v = 0.0;
+  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
+    const double dd = x[j] - mean;
+    v += dd * dd;
+  }
+  const double sd = sqrt(block_sum(v, sh) / (double)m);
+  const double inv = 1.0 / (sd + 1e-6);
+  for (int64_t j = threadIdx.x; j < m; j += blockDim.x)
+    z[(int64_t)blockIdx.x * m + j] = (float)((x[j] - mean) * inv);
+}
+
+template <typename T>
+cudaError_t launch_lp_static(cudaStream_t st, const T* A, int64_t lda, int64_t m, float* raw,
+                             float* zstat) {
+  k_lp_rownorm<T><<<(unsigned)((m * 32 + 255) / 256), 256, 0, st>>>(A, lda, m, raw);
+  k_lp_standardise<<<2, 1024, 0, st>>>(raw, m, zstat);
+  return cudaGetLastError();
+}
+
+// ---- per chunk: the dynamic features' statistics (one block) ----
+// stats: rms(r), mean and 1 / (std + 1e-6) of x1 = ln(1 + |r| / rms) and of
+// x3 = ln(1 + age), age_j = k0 - last_j
+__global__ void __launch_bounds__(1024) k_lp_stats(const Ctrl* __restrict__ ctrl, int64_t k0_arg,
+                                                   const double* __restrict__ r, int64_t m,
+                                                   const int32_t* __restrict__ last,
+                                                   double* __restrict__ stats) {
+  __shared__ double sh[32];
+  const int64_t k0 = k0_arg >= 0 ? k0_arg : ctrl->k0;
+  double q = 0.0;
+  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) q += r[j] * r[j];
+  const double rms = sqrt(block_sum(q, sh) / (double)m);
+  __syncthreads();
+  const double ir = rms > 0.0 ? 1.0 / rms : 0.0;
+  double s1 = 0.0, s3 = 0.0;
+  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
+    s1 += log1p(fabs(r[j]) * ir);
+    s3 += log1p((double)(k0 - last[j]));
+  }
+  const double m1 = block_sum(s1, sh) / (double)m;
+  __syncthreads();
+  const double m3 = block_sum(s3, sh) / (double)m;
+  __syncthreads();
+  double v1 = 0.0, v3 = 0.0;
+  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
+    const double a = log1p(fabs(r[j]) * ir) - m1;
+    const double b = log1p((double)(k0 - last[j])) - m3;
+    v1 += a * a;
+    v3 += b * b;
+  }
+  const double sd1 = sqrt(block_sum(v1, sh) / (double)m);
+  __syncthreads();
+  const double sd3 = sqrt(block_sum(v3, sh) / (double)m);
+  if (threadIdx.x == 0) {
+    stats[0] = ir;
+    stats[1] = m1;
+    stats[2] = 1.0 / (sd1 + 1e-6);
+    stats[3] = m3;
+    stats[4] = 1.0 / (sd3 + 1e-6);
+  }
+}
+
+__device__ __forceinline__ void lp_feature_row(const float* zstat, const double* stats,
+                                               const double* r, const int32_t* last, int64_t k0,
+                                               int64_t m, int64_t j, float z[kNF]) {
+  z[0] = zstat[j];
+  z[1] = (float)((log1p(fabs(r[j]) * stats[0]) - stats[1]) * stats[2]);
+  z[2] = zstat[m + j];
+  z[3] = (float)((log1p((double)(k0 - last[j])) - stats[3]) * stats[4]);
+}
+
+// ---- per chunk: scores s_j (uniform proposal: s = 0) ----
+__global__ void __launch_bounds__(256) k_lp_score(const Ctrl* __restrict__ ctrl, int64_t k0_arg,
+                                                  const uint16_t* __restrict__ w, const float* zstat,
+                                                  const double* stats, const double* __restrict__ r,
+                                                  const int32_t* __restrict__ last, int64_t m,
+                                                  float* __restrict__ score, float* feat_out) {
+  __shared__ __align__(16) MlpSmem s;
+  if (w != nullptr) load_weights_bf16(s, w);
+  __syncthreads();
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const int64_t k0 = k0_arg >= 0 ? k0_arg : ctrl->k0;
+  float z[kNF];
+  lp_feature_row(zstat, stats, r, last, k0, m, j, z);
+  if (feat_out != nullptr)
+#pragma unroll
+    for (int i = 0; i < kNF; ++i) feat_out[j * kNF + i] = z[i];
+  score[j] = w != nullptr ? mlp_forward(s, z) : 0.f;
+}
+
+// ---- per slot: proposal, Gumbel keys, top tau (one block per slot) ----
+// keys and row indices sorted in shared memory (bitonic, descending by key, ties by
+// ascending row); the first tau rows are then sorted ascending into the plan
+__global__ void __launch_bounds__(1024) k_lp_select(const Ctrl* __restrict__ ctrl, int force,
+                                                    int nslots, int64_t k0_arg, uint64_t seed,
+                                                    const float* __restrict__ score, int64_t m,
+                                                    int64_t tau, float eps, int64_t npow2,
+                                                    int32_t* __restrict__ perm, int64_t perm_stride,
+                                                    int32_t* __restrict__ boff, int64_t boff_stride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* key = reinterpret_cast<float*>(smem_raw);
+  int32_t* idx = reinterpret_cast<int32_t*>(key + npow2);
+  __shared__ float s_red[32];
+  __shared__ float s_bc[2];
+  const int64_t nact = active_slots(ctrl, force, nslots);
+  const int64_t t = blockIdx.x;
+  if (t >= nact) return;
+  const int64_t k = (k0_arg >= 0 ? k0_arg : ctrl->k0) + t;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  // softmax normaliser: max and sum of exp(s - max)
+  float mx = -INFINITY;
+  for (int64_t j = tid; j < m; j += blockDim.x) mx = fmaxf(mx, score[j]);
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) s_red[wid] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    float v = s_red[0];
+    for (int i = 1; i < nw; ++i) v = fmaxf(v, s_red[i]);
+    s_bc[0] = v;
+  }
+  __syncthreads();
+  mx = s_bc[0];
+  float se = 0.f;
+  for (int64_t j = tid; j < m; j += blockDim.x) se += expf(score[j] - mx);
+  se = warp_sum(se);
+  __syncthreads();
+  if (lane == 0) s_red[wid] = se;
+  __syncthreads();
+  if (tid == 0) {
+    float v = 0.f;
+    for (int i = 0; i < nw; ++i) v += s_red[i];
+    s_bc[1] = v;
+  }
+  __syncthreads();
+  const float c1 = (1.f - eps) / s_bc[1], c0 = eps / (float)m;
+  const uint64_t kk = iter_key(seed, k);
+  for (int64_t j = tid; j < npow2; j += blockDim.x) {
+    if (j < m) {
+      const float lp = logf(c1 * expf(score[j] - mx) + c0);
+      const uint32_t hi = (uint32_t)(draw_k(kk, 4, (uint64_t)j) >> 32);
+      const float u = ((float)hi + 0.5f) * 2.3283064365386963e-10f;
+      key[j] = lp - logf(-logf(u));
+      idx[j] = (int32_t)j;
+    } else {
+      key[j] = -INFINITY;
+      idx[j] = 0x7FFFFFFF;
+    }
+  }
+  __syncthreads();
+  // bitonic sort: "a before b" when key_a > key_b or (equal and idx_a < idx_b)
+  for (int64_t size = 2; size <= npow2; size <<= 1) {
+    for (int64_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int64_t i = tid; i < npow2 / 2; i += blockDim.x) {
+        const int64_t lo = 2 * i - (i & (stride - 1));
+        const int64_t hi2 = lo + stride;
+        const bool desc = ((lo & size) == 0);
+        const float ka = key[lo], kb = key[hi2];
+        const int32_t ia = idx[lo], ib = idx[hi2];
+        const bool a_first = (ka > kb) || (ka == kb && ia < ib);
+        if (a_first != desc) {
+          key[lo] = kb; key[hi2] = ka;
+          idx[lo] = ib; idx[hi2] = ia;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // the tau selected rows in increasing order (bitonic on tau padded to a power of two)
+  int64_t tp = 1;
+  while (tp < tau) tp <<= 1;
+  int32_t* sel = reinterpret_cast<int32_t*>(key);  // keys no longer needed
+  for (int64_t i = tid; i < tp; i += blockDim.x) sel[i] = i < tau ? idx[i] : 0x7FFFFFFF;
+  __syncthreads();
+  for (int64_t size = 2; size <= tp; size <<= 1) {
+    for (int64_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int64_t i = tid; i < tp / 2; i += blockDim.x) {
+        const int64_t lo = 2 * i - (i & (stride - 1));
+        const int64_t hi2 = lo + stride;
+        const bool asc = ((lo & size) == 0);
+        const int32_t a = sel[lo], b = sel[hi2];
+        if ((a > b) == asc) { sel[lo] = b; sel[hi2] = a; }
+      }
+      __syncthreads();
+    }
+  }
+  int32_t* ps = perm + t * perm_stride;
+  int32_t* bs = boff + t * boff_stride;
+  for (int64_t p = tid; p < tau; p += blockDim.x) ps[p] = sel[p];
+  for (int64_t p = tid; p <= tau; p += blockDim.x) bs[p] = (int32_t)p;
+}
+
+// ---- after the plans: last visit of every drawn row ----
+__global__ void k_lp_age(const Ctrl* __restrict__ ctrl, int force, int nslots, int64_t k0_arg,
+                         const int32_t* __restrict__ perm, int64_t perm_stride, int64_t tau,
+                         int32_t* __restrict__ last) {
+  const int64_t nact = active_slots(ctrl, force, nslots);
+  const int64_t k0 = k0_arg >= 0 ? k0_arg : ctrl->k0;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nact * tau) return;
+  const int64_t t = e / tau, p = e - t * tau;
+  atomicMax(last + entry_row(perm[t * perm_stride + p]), (int32_t)(k0 + t));
+}
+
+cudaError_t launch_lp_plans(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, int64_t k0_arg,
+                            uint64_t seed, const uint16_t* w, float eps, const float* zstat,
+                            double* stats, const double* r, int32_t* last, int64_t m, int64_t tau,
+                            float* score, int32_t* perm, int64_t perm_stride, int32_t* boff,
+                            int64_t boff_stride, bool update_age) {
+  int64_t npow2 = 1;
+  while (npow2 < m) npow2 <<= 1;
+  const size_t smem = (size_t)npow2 * 8;
+  if (smem > 200 * 1024 || tau > m) return cudaErrorInvalidValue;
+  k_lp_stats<<<1, 1024, 0, st>>>(ctrl, k0_arg, r, m, last, stats);
+  k_lp_score<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(ctrl, k0_arg, w, zstat, stats, r, last, m,
+                                                          score, nullptr);
+  cudaError_t e = cudaFuncSetAttribute(k_lp_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_lp_select<<<(unsigned)nslots, 1024, smem, st>>>(ctrl, force, nslots, k0_arg, seed, score, m, tau,
+                                                    eps, npow2, perm, perm_stride, boff, boff_stride);
+  if (update_age)
+    k_lp_age<<<(unsigned)((nslots * tau + 255) / 256), 256, 0, st>>>(ctrl, force, nslots, k0_arg,
+                                                                      perm, perm_stride, tau, last);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lp_features(cudaStream_t st, const Ctrl* ctrl, int64_t k0, const float* zstat,
+                               double* stats, const double* r, const int32_t* last, int64_t m,
+                               float* score, float* feat_out) {
+  k_lp_stats<<<1, 1024, 0, st>>>(ctrl, k0, r, m, last, stats);
+  k_lp_score<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(ctrl, k0, nullptr, zstat, stats, r, last,
+                                                          m, score, feat_out);
+  return cudaGetLastError();
+}
+
+// ---- network scores of given feature rows (inference / parity) ----
+__global__ void __launch_bounds__(256) k_mlp_forward(const uint16_t* __restrict__ w,
+                                                     const float* __restrict__ Z, int64_t n,
+                                                     float* __restrict__ s_out) {
+  __shared__ __align__(16) MlpSmem s;
+  load_weights_bf16(s, w);
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float z[kNF];
+#pragma unroll
+  for (int f = 0; f < kNF; ++f) z[f] = Z[i * kNF + f];
+  s_out[i] = mlp_forward(s, z);
+}
+
+cudaError_t launch_mlp_forward(cudaStream_t st, const uint16_t* w, const float* Z, int64_t n,
+                               float* s_out) {
+  if (n <= 0) return cudaSuccess;
+  k_mlp_forward<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w, Z, n, s_out);
+  return cudaGetLastError();
+}
+
+// ---- training: gradient of the mean loss (s - y)^2 / 2 over n rows ----
+// A block takes kGB rows (a thread per row): the forward with bfloat16-rounded
+// weights and activations (kept in shared memory column-major by row), the
+// backward in FP32 (the roundings pass gradients straight through), then the
+// block's weight gradients as sums over its rows in row order; per-block sums go
+// to part (blocks x kMlpParams) and are added in block order.
+namespace {
+constexpr int kGB = 128;
+
+struct GradSmem {
+  float w[kMlpParams + 3];
+  float z[kNF][kGB];
+  float h1[kH][kGB];
+  float h2[kH][kGB];
+  float d2[kH][kGB];   // dL / da2
+  float d1[kH][kGB];   // dL / da1
+  float ds[kGB];
+  float loss[kGB];
+};
+}  // namespace
+
+__global__ void __launch_bounds__(kGB, 1) k_mlp_grad(const float* __restrict__ theta,
+                                                     const float* __restrict__ Z,
+                                                     const float* __restrict__ y, int64_t n,
+                                                     float* __restrict__ part,
+                                                     float* __restrict__ loss_part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  GradSmem& s = *reinterpret_cast<GradSmem*>(smem_raw);
+  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) s.w[i] = round_bf16(theta[i]);
+  const int tid = threadIdx.x;
+  const int64_t row = (int64_t)blockIdx.x * kGB + tid;
+  const bool live = row < n;
+  float z[kNF];
+#pragma unroll
+  for (int f = 0; f < kNF; ++f) {
+    z[f] = live ? Z[row * kNF + f] : 0.f;
+    s.z[f][tid] = z[f];
+  }
+  __syncthreads();
+  // forward
+  float h1[kH];
+#pragma unroll
+  for (int o = 0; o < kH; ++o) {
+    float a = s.w[kOffB1 + o];
+#pragma unroll
+    for (int i = 0; i < kNF; ++i) a = fmaf(s.w[o * kNF + i], z[i], a);
+    h1[o] = round_bf16(fmaxf(a, 0.f));
+    s.h1[o][tid] = h1[o];
+  }
+  float out = s.w[kOffB3];
+  for (int o = 0; o < kH; ++o) {
+    const float4* w2 = reinterpret_cast<const float4*>(s.w + kOffW2 + o * kH);
+    float a = s.w[kOffB2 + o];
+#pragma unroll
+    for (int i4 = 0; i4 < kH / 4; ++i4) {
+      const float4 w = w2[i4];
+      a = fmaf(w.x, h1[4 * i4], a);
+      a = fmaf(w.y, h1[4 * i4 + 1], a);
+      a = fmaf(w.z, h1[4 * i4 + 2], a);
+      a = fmaf(w.w, h1[4 * i4 + 3], a);
+    }
+    const float h2 = round_bf16(fmaxf(a, 0.f));
+    s.h2[o][tid] = h2;
+    s.d2[o][tid] = a > 0.f ? 1.f : 0.f;  // relu mask for now
+    out = fmaf(s.w[kOffW3 + o], h2, out);
+  }
+  const float err = live ? out - y[row] : 0.f;
+  const float ds = err / (float)n;
+  s.ds[tid] = ds;
+  s.loss[tid] = 0.5f * err * err;
+  // backward through the rows of this thread
+  float g1[kH];
+#pragma unroll
+  for (int i = 0; i < kH; ++i) g1[i] = 0.f;
+  for (int o = 0; o < kH; ++o) {
+    const float d = ds * s.w[kOffW3 + o] * s.d2[o][tid];
+    s.d2[o][tid] = d;
+    const float4* w2 = reinterpret_cast<const float4*>(s.w + kOffW2 + o * kH);
+#pragma unroll
+    for (int i4 = 0; i4 < kH / 4; ++i4) {
+      const float4 w = w2[i4];
+      g1[4 * i4] = fmaf(d, w.x, g1[4 * i4]);
+      g1[4 * i4 + 1] = fmaf(d, w.y, g1[4 * i4 + 1]);
+      g1[4 * i4 + 2] = fmaf(d, w.z, g1[4 * i4 + 2]);
+      g1[4 * i4 + 3] = fmaf(d, w.w, g1[4 * i4 + 3]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kH; ++i) s.d1[i][tid] = h1[i] > 0.f ? g1[i] : 0.f;
+  __syncthreads();
+  // the block's parameter gradients (sums over its rows in row order)
+  float* pb = part + (int64_t)blockIdx.x * kMlpParams;
+  for (int e = tid; e < kMlpParams; e += blockDim.x) {
+    float acc = 0.f;
+    if (e < kOffB1) {                      // W1[o][i]
+      const int o = e / kNF, i = e % kNF;
+      for (int r = 0; r < kGB; ++r) acc = fmaf(s.d1[o][r], s.z[i][r], acc);
+    } else if (e < kOffW2) {               // b1[o]
+      const int o = e - kOffB1;
+      for (int r = 0; r < kGB; ++r) acc += s.d1[o][r];
+    } else if (e < kOffB2) {               // W2[o][i]
+      const int o = (e - kOffW2) / kH, i = (e - kOffW2) % kH;
+      for (int r = 0; r < kGB; ++r) acc = fmaf(s.d2[o][r], s.h1[i][r], acc);
+    } else if (e < kOffW3) {               // b2[o]
+      const int o = e - kOffB2;
+      for (int r = 0; r < kGB; ++r) acc += s.d2[o][r];
+    } else if (e < kOffB3) {               // w3[o]
+      const int o = e - kOffW3;
+      for (int r = 0; r < kGB; ++r) acc = fmaf(s.ds[r], s.h2[o][r], acc);
+    } else {                               // b3
+      for (int r = 0; r < kGB; ++r) acc += s.ds[r];
+    }
+    pb[e] = acc;
+  }
+  if (tid == 0) {
+    float l = 0.f;
+    for (int r = 0; r < kGB; ++r) l += s.loss[r];
+    loss_part[blockIdx.x] = l;
+  }
+}
+
+// grad = sum of the block parts in block order; loss = their row-loss sums / n
+__global__ void k_mlp_sum(const float* __restrict__ part, const float* __restrict__ loss_part,
+                          int nblk, int64_t n, float* __restrict__ grad, double* __restrict__ loss) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < kMlpParams) {
+    float acc = 0.f;
+    for (int b = 0; b < nblk; ++b) acc += part[(int64_t)b * kMlpParams + e];
+    grad[e] = acc;
+  }
+  if (e == 0 && loss != nullptr) {
+    double l = 0.0;
+    for (int b = 0; b < nblk; ++b) l += loss_part[b];
+    *loss = l / (double)n;
+  }
+}
+
+int mlp_grad_blocks(int64_t n) { return (int)((n + kGB - 1) / kGB); }
+
+cudaError_t launch_mlp_grad(cudaStream_t st, const float* theta, const float* Z, const float* y,
+                            int64_t n, float* part, float* loss_part, float* grad, double* loss) {
+  if (n <= 0) return cudaErrorInvalidValue;
+  const int nblk = mlp_grad_blocks(n);
+  const size_t smem = sizeof(GradSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_mlp_grad<<<nblk, kGB, smem, st>>>(theta, Z, y, n, part, loss_part);
+  k_mlp_sum<<<(kMlpParams + 255) / 256, 256, 0, st>>>(part, loss_part, nblk, n, grad, loss);
+  return cudaGetLastError();
+}
+
+// ---- Adam (Kingma and Ba, 2015) on the FP32 master weights; bfloat16 copy ----
+__global__ void k_mlp_adam(float* __restrict__ theta, float* __restrict__ mom,
+                           float* __restrict__ vel, const float* __restrict__ grad, float lr,
+                           float b1, float b2, float eps, float c1, float c2,
+                           uint16_t* __restrict__ w_bf16) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kMlpParams) return;
+  const float g = grad[e];
+  const float m = b1 * mom[e] + (1.f - b1) * g;
+  const float v = b2 * vel[e] + (1.f - b2) * g * g;
+  mom[e] = m;
+  vel[e] = v;
+  const float t = theta[e] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+  theta[e] = t;
+  if (w_bf16 != nullptr) w_bf16[e] = to_bf16(t);
+}
+
+cudaError_t launch_mlp_adam(cudaStream_t st, float* theta, float* mom, float* vel, const float* grad,
+                            int64_t step, float lr, float b1, float b2, float eps, uint16_t* w_bf16) {
+  const float c1 = (float)(1.0 - pow((double)b1, (double)step));
+  const float c2 = (float)(1.0 - pow((double)b2, (double)step));
+  k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, st>>>(theta, mom, vel, grad, lr, b1, b2, eps, c1,
+                                                       c2, w_bf16);
+  return cudaGetLastError();
+}
+
+__global__ void k_f32_to_bf16(const float* __restrict__ x, int64_t n, uint16_t* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = to_bf16(x[e]);
+}
+
+cudaError_t launch_f32_to_bf16(cudaStream_t st, const float* x, int64_t n, uint16_t* out) {
+  k_f32_to_bf16<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, n, out);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_lp_static<float>(cudaStream_t, const float*, int64_t, int64_t, float*,
+                                             float*);
+template cudaError_t launch_lp_static<double>(cudaStream_t, const double*, int64_t, int64_t,
+                                              float*, float*);
+
+}  // namespace rs
