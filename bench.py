@@ -293,6 +293,61 @@ def bench_sparse(args, rs, dev):
     print(json.dumps(out), flush=True)
 
 
+def bench_learned(args, rs, dev):
+    """X 65536 x 8192 = U diag(i^-0.8) V^T (Haar U, V), lambda 1e-3, subsample tau 256,
+    no momentum, to 1e-6: uniform draws against the learned proposal (the network
+    trained with the library's kernels on trajectories of two 16384 x 2048 problems
+    of the same recipe), plain FP64 and mixed."""
+    import torch
+
+    from paper_2105_05565_gb300 import learned
+    from synth import power_sigma, spectrum_problem_torch
+
+    tau, lam, chunk = 256, 1e-3, 20
+    out = {"workload": "learned", "tau": tau, "chunk": chunk}
+    t0 = time.perf_counter()
+    Zs, Ys = [], []
+    for sd in range(2):
+        X, y, _ = spectrum_problem_torch(16384, 2048, power_sigma(2048, 0.8), 700 + sd, device=dev)
+        X64 = X.double()
+        A = X64.T @ X64 + lam * torch.eye(2048, dtype=torch.float64, device=dev)
+        w_star = torch.linalg.solve(A, X64.T @ y).cpu().numpy()
+        del A, X64
+        with rs.Solver(X.double(), y, lam, sketch="subsample", tau=64, momentum="none", seed=sd,
+                       chunk=1) as s:
+            s.set_proposal(None, 0.1)
+            s.set_state(np.zeros(2048), np.zeros(2048), *(2 * [-(X.double().T @ y).cpu().numpy()]), 0)
+            Z, t = learned.collect(s, w_star, 1500, tol=1e-6)
+        Zs.append(Z)
+        Ys.append(t)
+    wb, _, losses = learned.train(np.concatenate(Zs), np.concatenate(Ys), steps=2000, batch=1024,
+                                  lr=3e-3, seed=0)
+    out["train_s"] = time.perf_counter() - t0
+    out["train_rows"] = int(sum(len(t) for t in Ys))
+    out["train_loss_first_last"] = [float(losses[:50].mean()), float(losses[-200:].mean())]
+    X, y, _ = spectrum_problem_torch(65536, 8192, power_sigma(8192, 0.8), 999, device=dev)
+    for prec in ("fp64", "mixed"):
+        Xp = X.double() if prec == "fp64" else X
+        for name, w8 in (("uniform", None), ("learned", wb)):
+            if prec == "mixed" and name == "uniform":
+                continue
+            with rs.Solver(Xp, y, lam, sketch="subsample", tau=tau, momentum="none", seed=5,
+                           precision=prec, chunk=chunk, refresh_every=chunk) as s:
+                s.set_proposal(w8, 0.1)
+                w, hist, iters, conv = s.solve(tol=TOL, max_iters=100000)
+                setup_ms, solve_ms = s.timings()
+                out[f"{prec}_{name}"] = {"iters": iters, "converged": bool(conv),
+                                         "solve_ms": solve_ms, "setup_ms": setup_ms,
+                                         "iters_per_s": iters / (solve_ms / 1e3),
+                                         "final_rel": float(hist[-1])}
+        del Xp
+    u = out["fp64_uniform"]
+    out["learned_iters_ratio_vs_uniform"] = out["fp64_learned"]["iters"] / u["iters"]
+    out["speedup_time_to_tol_fp64_learned_vs_uniform"] = u["solve_ms"] / out["fp64_learned"]["solve_ms"]
+    out["speedup_time_to_tol_mixed_learned_vs_plain_fp64_uniform"] = u["solve_ms"] / out["mixed_learned"]["solve_ms"]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,7 +359,7 @@ def main():
     ap.add_argument("--small", action="store_true",
                     help="profiling case: X 20000 x 4096 (328 MB, larger than L2), same sketch and "
                          "schedule; prints the line of that case (not the benchmark workload)")
-    ap.add_argument("--workload", default="dense", choices=["dense", "batched", "sparse"],
+    ap.add_argument("--workload", default="dense", choices=["dense", "batched", "sparse", "learned"],
                     help="dense: the benchmark line; batched / sparse: measurement lines of the "
                          "256-problem batch and the Zipf-sparse matrix-free solve")
     args = ap.parse_args()
@@ -318,7 +373,8 @@ def main():
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
         rs.lib()
-        return (bench_batched if args.workload == "batched" else bench_sparse)(args, rs, dev)
+        fn = {"batched": bench_batched, "sparse": bench_sparse, "learned": bench_learned}[args.workload]
+        return fn(args, rs, dev)
 
     import torch
 
