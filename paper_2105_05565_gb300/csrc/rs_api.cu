@@ -103,7 +103,7 @@ struct rs_ctx {
   bool lp_uniform = false;     // no network: p_j = 1 / m
   float lp_eps = 0.1f;
   uint16_t* lp_w = nullptr;    // network weights, bfloat16
-  float* lp_raw = nullptr;     // 2 m work space
+  float* lp_raw = nullptr;     // 2 m work space (raw static, then the dynamic features)
   float* lp_zstat = nullptr;   // 2 m standardised static features
   double* lp_stats = nullptr;  // 8
   float* lp_score = nullptr;   // m scores
@@ -272,9 +272,9 @@ rs_status enqueue_gen(rs_ctx* c, int64_t k0_arg, int nslots) {
   cudaStream_t st = c->stream;
   if (c->learned) {  // rows drawn from the learned proposal (the chunk's plans at once)
     CKC(c, launch_lp_plans(st, c->ctrl, k0_arg >= 0 ? 1 : 0, nslots, k0_arg, c->seed,
-                           c->lp_uniform ? nullptr : c->lp_w, c->lp_eps, c->lp_zstat, c->lp_stats,
-                           c->r, c->lp_last, c->m, c->tau, c->lp_score, c->perm, c->perm_stride,
-                           c->boff, c->boff_stride, k0_arg < 0));
+                           c->lp_uniform ? nullptr : c->lp_w, c->lp_eps, c->lp_zstat, c->lp_raw,
+                           c->lp_stats, c->r, c->lp_last, c->m, c->tau, c->lp_score, c->perm,
+                           c->perm_stride, c->boff, c->boff_stride, k0_arg < 0));
     return RS_OK;
   }
   switch (c->sketch) {
@@ -560,6 +560,10 @@ rs_status enqueue_true_av(rs_ctx* c, const double* v, const int32_t* stop) {
     const float* X = static_cast<const float*>(c->X);
     if (c->form == RS_PRIMAL && c->d <= 4096 && c->xtx_df) {
       CKC(c, launch_xtx_v_df(st, X, c->n, c->d, v, c->vd, c->xt_part, stop));
+    } else if (c->form == RS_PRIMAL && c->xtx_df && c->d <= 24576) {
+      // wider d: the same float-pair product in two passes (X w into vn as pairs)
+      CKC(c, launch_xtx_two_pass(st, X, c->n, c->d, 1, v, c->vd, reinterpret_cast<float2*>(c->vn),
+                                 c->xt_part, stop));
     } else if (c->form == RS_PRIMAL) {
       CKC(c, launch_x_v<float>(st, X, c->n, c->d, v, c->vn, stop));
       CKC(c, launch_xt_v<float>(st, X, c->n, c->d, c->vn, c->vd, c->xt_part, stop));
@@ -1685,8 +1689,8 @@ rs_status rs_proposal_features(rs_ctx* c, float* Z_out) {
   DeviceGuard dg(c->device);
   rs_status s = read_ctrl(c);
   if (s != RS_OK) return s;
-  CKC(c, launch_lp_features(c->stream, c->ctrl, c->ctrl_h->k, c->lp_zstat, c->lp_stats, c->r,
-                            c->lp_last, c->m, c->lp_score, c->lp_feat));
+  CKC(c, launch_lp_features(c->stream, c->ctrl, c->ctrl_h->k, c->lp_zstat, c->lp_raw, c->lp_stats,
+                            c->r, c->lp_last, c->m, c->lp_score, c->lp_feat));
   CKC(c, cudaMemcpyAsync(Z_out, c->lp_feat, c->m * 4 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   CKC(c, cudaStreamSynchronize(c->stream));
   return RS_OK;

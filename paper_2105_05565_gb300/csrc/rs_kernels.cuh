@@ -272,13 +272,13 @@ cudaError_t launch_lp_static(cudaStream_t st, const T* A, int64_t lda, int64_t m
 // update_age)
 cudaError_t launch_lp_plans(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, int64_t k0_arg,
                             uint64_t seed, const uint16_t* w, float eps, const float* zstat,
-                            double* stats, const double* r, int32_t* last, int64_t m, int64_t tau,
-                            float* score, int32_t* perm, int64_t perm_stride, int32_t* boff,
-                            int64_t boff_stride, bool update_age);
-// the m x 4 feature rows at iteration k0 (the network's inputs)
+                            float* dyn, double* stats, const double* r, int32_t* last, int64_t m,
+                            int64_t tau, float* score, int32_t* perm, int64_t perm_stride,
+                            int32_t* boff, int64_t boff_stride, bool update_age);
+// the m x 4 feature rows at iteration k0 (the network's inputs); dyn: 2 m floats
 cudaError_t launch_lp_features(cudaStream_t st, const Ctrl* ctrl, int64_t k0, const float* zstat,
-                               double* stats, const double* r, const int32_t* last, int64_t m,
-                               float* score, float* feat_out);
+                               float* dyn, double* stats, const double* r, const int32_t* last,
+                               int64_t m, float* score, float* feat_out);
 cudaError_t launch_mlp_forward(cudaStream_t st, const uint16_t* w, const float* Z, int64_t n,
                                float* s_out);
 int mlp_grad_blocks(int64_t n);

@@ -124,12 +124,14 @@ cudaError_t launch_lp_static(cudaStream_t st, const T* A, int64_t lda, int64_t m
   return cudaGetLastError();
 }
 
-// ---- per chunk: the dynamic features' statistics (one block) ----
-// stats: rms(r), mean and 1 / (std + 1e-6) of x1 = ln(1 + |r| / rms) and of
-// x3 = ln(1 + age), age_j = k0 - last_j
+// ---- per chunk: the dynamic features and their statistics (one block) ----
+// dyn: x1_j = ln(1 + |r_j| / rms(r)) and x3_j = ln(1 + age_j), age_j = k0 - last_j,
+// in FP32 (2 m floats); stats: 1 / rms(r), mean and 1 / (std + 1e-6) of x1 and x3
+// (sums in FP64)
 __global__ void __launch_bounds__(1024) k_lp_stats(const Ctrl* __restrict__ ctrl, int64_t k0_arg,
                                                    const double* __restrict__ r, int64_t m,
                                                    const int32_t* __restrict__ last,
+                                                   float* __restrict__ dyn,
                                                    double* __restrict__ stats) {
   __shared__ double sh[32];
   const int64_t k0 = k0_arg >= 0 ? k0_arg : ctrl->k0;
@@ -137,11 +139,15 @@ __global__ void __launch_bounds__(1024) k_lp_stats(const Ctrl* __restrict__ ctrl
   for (int64_t j = threadIdx.x; j < m; j += blockDim.x) q += r[j] * r[j];
   const double rms = sqrt(block_sum(q, sh) / (double)m);
   __syncthreads();
-  const double ir = rms > 0.0 ? 1.0 / rms : 0.0;
+  const float ir = rms > 0.0 ? (float)(1.0 / rms) : 0.f;
   double s1 = 0.0, s3 = 0.0;
   for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
-    s1 += log1p(fabs(r[j]) * ir);
-    s3 += log1p((double)(k0 - last[j]));
+    const float x1 = log1pf(fabsf((float)r[j]) * ir);
+    const float x3 = log1pf((float)(k0 - last[j]));
+    dyn[j] = x1;
+    dyn[m + j] = x3;
+    s1 += x1;
+    s3 += x3;
   }
   const double m1 = block_sum(s1, sh) / (double)m;
   __syncthreads();
@@ -149,8 +155,8 @@ __global__ void __launch_bounds__(1024) k_lp_stats(const Ctrl* __restrict__ ctrl
   __syncthreads();
   double v1 = 0.0, v3 = 0.0;
   for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
-    const double a = log1p(fabs(r[j]) * ir) - m1;
-    const double b = log1p((double)(k0 - last[j])) - m3;
+    const double a = (double)dyn[j] - m1;
+    const double b = (double)dyn[m + j] - m3;
     v1 += a * a;
     v3 += b * b;
   }
@@ -167,28 +173,26 @@ __global__ void __launch_bounds__(1024) k_lp_stats(const Ctrl* __restrict__ ctrl
 }
 
 __device__ __forceinline__ void lp_feature_row(const float* zstat, const double* stats,
-                                               const double* r, const int32_t* last, int64_t k0,
-                                               int64_t m, int64_t j, float z[kNF]) {
+                                               const float* dyn, int64_t m, int64_t j,
+                                               float z[kNF]) {
   z[0] = zstat[j];
-  z[1] = (float)((log1p(fabs(r[j]) * stats[0]) - stats[1]) * stats[2]);
+  z[1] = (float)(((double)dyn[j] - stats[1]) * stats[2]);
   z[2] = zstat[m + j];
-  z[3] = (float)((log1p((double)(k0 - last[j])) - stats[3]) * stats[4]);
+  z[3] = (float)(((double)dyn[m + j] - stats[3]) * stats[4]);
 }
 
 // ---- per chunk: scores s_j (uniform proposal: s = 0) ----
-__global__ void __launch_bounds__(256) k_lp_score(const Ctrl* __restrict__ ctrl, int64_t k0_arg,
-                                                  const uint16_t* __restrict__ w, const float* zstat,
-                                                  const double* stats, const double* __restrict__ r,
-                                                  const int32_t* __restrict__ last, int64_t m,
-                                                  float* __restrict__ score, float* feat_out) {
+__global__ void __launch_bounds__(256) k_lp_score(const uint16_t* __restrict__ w, const float* zstat,
+                                                  const double* stats, const float* __restrict__ dyn,
+                                                  int64_t m, float* __restrict__ score,
+                                                  float* feat_out) {
   __shared__ __align__(16) MlpSmem s;
   if (w != nullptr) load_weights_bf16(s, w);
   __syncthreads();
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
-  const int64_t k0 = k0_arg >= 0 ? k0_arg : ctrl->k0;
   float z[kNF];
-  lp_feature_row(zstat, stats, r, last, k0, m, j, z);
+  lp_feature_row(zstat, stats, dyn, m, j, z);
   if (feat_out != nullptr)
 #pragma unroll
     for (int i = 0; i < kNF; ++i) feat_out[j * kNF + i] = z[i];
@@ -310,16 +314,15 @@ __global__ void k_lp_age(const Ctrl* __restrict__ ctrl, int force, int nslots, i
 
 cudaError_t launch_lp_plans(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, int64_t k0_arg,
                             uint64_t seed, const uint16_t* w, float eps, const float* zstat,
-                            double* stats, const double* r, int32_t* last, int64_t m, int64_t tau,
-                            float* score, int32_t* perm, int64_t perm_stride, int32_t* boff,
-                            int64_t boff_stride, bool update_age) {
+                            float* dyn, double* stats, const double* r, int32_t* last, int64_t m,
+                            int64_t tau, float* score, int32_t* perm, int64_t perm_stride,
+                            int32_t* boff, int64_t boff_stride, bool update_age) {
   int64_t npow2 = 1;
   while (npow2 < m) npow2 <<= 1;
   const size_t smem = (size_t)npow2 * 8;
   if (smem > 200 * 1024 || tau > m) return cudaErrorInvalidValue;
-  k_lp_stats<<<1, 1024, 0, st>>>(ctrl, k0_arg, r, m, last, stats);
-  k_lp_score<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(ctrl, k0_arg, w, zstat, stats, r, last, m,
-                                                          score, nullptr);
+  k_lp_stats<<<1, 1024, 0, st>>>(ctrl, k0_arg, r, m, last, dyn, stats);
+  k_lp_score<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(w, zstat, stats, dyn, m, score, nullptr);
   cudaError_t e = cudaFuncSetAttribute(k_lp_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -332,11 +335,11 @@ cudaError_t launch_lp_plans(cudaStream_t st, const Ctrl* ctrl, int force, int ns
 }
 
 cudaError_t launch_lp_features(cudaStream_t st, const Ctrl* ctrl, int64_t k0, const float* zstat,
-                               double* stats, const double* r, const int32_t* last, int64_t m,
-                               float* score, float* feat_out) {
-  k_lp_stats<<<1, 1024, 0, st>>>(ctrl, k0, r, m, last, stats);
-  k_lp_score<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(ctrl, k0, nullptr, zstat, stats, r, last,
-                                                          m, score, feat_out);
+                               float* dyn, double* stats, const double* r, const int32_t* last,
+                               int64_t m, float* score, float* feat_out) {
+  k_lp_stats<<<1, 1024, 0, st>>>(ctrl, k0, r, m, last, dyn, stats);
+  k_lp_score<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(nullptr, zstat, stats, dyn, m, score,
+                                                          feat_out);
   return cudaGetLastError();
 }
 

@@ -404,3 +404,23 @@ def test_gram_tensor_cores(rs, n, d):
             M, _, _ = s.probe_step()
         assert np.all(np.abs(M - ref) <= bound + 1e-6), tc
         assert np.allclose(M, M.T, rtol=0, atol=0)
+
+
+def test_mixed_refresh_beyond_4096_columns(rs):
+    """d = 4500 (past the one-pass refresh kernel): the FP64 true residual through X in
+    two passes equals the oracle's, and the mixed solve reaches 1e-6 by it."""
+    from synth import geometric_sigma, spectrum_problem
+
+    X, y, _ = spectrum_problem(5000, 4500, geometric_sigma(4500, 1e-1), 44, noise=0.01)
+    X = X.astype(np.float32)
+    X64 = X.astype(np.float64)
+    lam = 1e-1
+    with rs.Solver(X, y, lam, sketch="count", tau=256, momentum="heuristic", seed=2,
+                   precision="mixed") as s:
+        w, hist, iters, conv = s.solve(tol=1e-6, max_iters=20000)
+        assert conv
+        got = s.true_residual(w)
+    ref = oracle.true_residual(X64, y, lam, w)
+    # float-pair products carry about 48 bits: the residual relative to ||b|| to ~1e-14
+    assert abs(got - ref) <= 1e-12
+    assert ref <= 1e-6 * (1 + 1e-6)
