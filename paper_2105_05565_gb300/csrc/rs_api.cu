@@ -1442,10 +1442,12 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
   rs_status s = read_ctrl(c);
   if (s != RS_OK) return s;
   const int64_t k0 = c->ctrl_h->k;
-  if ((s = ensure_schedule(c, k0 + reps + 1)) != RS_OK) return s;
+  if ((s = ensure_schedule(c, k0 + reps + c->chunk + 2)) != RS_OK) return s;
   Ctrl* h = c->ctrl_h;
   h->stop = 0; h->pending = 0; h->status = 0; h->ticket = 0; h->no_stop = 1;
-  h->max_iters = k0 + reps;
+  // past the profiled iterations, so that no kernel of the last chunk sees the cap
+  // (the refresh after it would return at once)
+  h->max_iters = k0 + reps + c->chunk + 1;
   h->r0 = c->r0 > 0.0 ? c->r0 : 1.0;
   if ((s = write_ctrl(c)) != RS_OK) return s;
   struct Grp { const char* name; double ms = 0; int64_t n = 0; double bytes = 0, flops = 0; int64_t iters = 0; };

@@ -67,11 +67,17 @@ __device__ __forceinline__ bool halted(const Ctrl* c) {
   return (*(volatile const int32_t*)&c->stop) | (*(volatile const int32_t*)&c->pending);
 }
 
+__device__ __forceinline__ bool stopped(const Ctrl* c) {
+  return *(volatile const int32_t*)&c->stop;
+}
+
 // number of slots of the current chunk that run: all of them for a forced (probe)
-// launch, none once the solve has stopped, else those below max_iters
+// launch, none once the solve has stopped, else those below max_iters. Phase 1
+// does not depend on the iterate, so a pending FP64 check (which may resume the
+// solve) does not stop it: it may run beside that check.
 __device__ __forceinline__ int64_t active_slots(const Ctrl* c, int force, int nslots) {
   if (force) return nslots;
-  if (halted(c)) return 0;
+  if (stopped(c)) return 0;
   const int64_t left = c->max_iters - c->k0;
   return left < 0 ? 0 : (left < nslots ? left : (int64_t)nslots);
 }

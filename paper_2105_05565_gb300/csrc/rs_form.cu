@@ -109,6 +109,8 @@ cudaError_t launch_x_v(cudaStream_t st, const TI* X, int64_t n, int64_t d, const
 // product directly. Each block takes a range of rows: for every row i it forms
 // u_i = x_i . v (block reduction of pairs), then adds u_i x_i to its per-column
 // pairs; per-block column sums go to `part` (blocks x d) and are added in block order.
+// X is read with evict-first loads so that its stream does not push A (read again
+// by the next chunk's phase 1) out of L2.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);
@@ -123,19 +125,20 @@ __device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl)
   al = __fsub_rn(e, __fsub_rn(ah, s));
 }
 
-template <int NC, int R>
-__global__ void __launch_bounds__(256) k_xtx_v_df(const float* __restrict__ X, int64_t n, int64_t d,
+template <int NC, int R, int NT = 256>
+__global__ void __launch_bounds__(NT) k_xtx_v_df(const float* __restrict__ X, int64_t n, int64_t d,
                                                   const double* __restrict__ v,
                                                   double* __restrict__ part,
                                                   const int32_t* __restrict__ stop) {
   if (stop != nullptr && *(volatile const int32_t*)stop) return;
-  __shared__ float s_h[8][R], s_l[8][R];
+  constexpr int NW = NT / 32;
+  __shared__ float s_h[NW][R], s_l[NW][R];
   __shared__ float u_h[R], u_l[R];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   float vh[NC], vl[NC], ah[NC], al[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    const int64_t col = tid + 256 * c;
+    const int64_t col = tid + NT * c;
     const double vv = col < d ? v[col] : 0.0;
     vh[c] = (float)vv;
     vl[c] = (float)(vv - (double)vh[c]);
@@ -154,8 +157,8 @@ __global__ void __launch_bounds__(256) k_xtx_v_df(const float* __restrict__ X, i
       const int64_t i = ib + r;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        const int64_t col = tid + 256 * c;
-        x[r][c] = (i < i1 && col < d) ? __ldg(X + i * d + col) : 0.f;
+        const int64_t col = tid + NT * c;
+        x[r][c] = (i < i1 && col < d) ? __ldcs(X + i * d + col) : 0.f;
       }
     }
 #pragma unroll
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(256) k_xtx_v_df(const float* __restrict__ X, i
     __syncthreads();
     if (tid < R) {
       float h = s_h[0][tid], l = s_l[0][tid];
-      for (int q = 1; q < 8; ++q) df_add(h, l, s_h[q][tid], s_l[q][tid]);
+      for (int q = 1; q < NW; ++q) df_add(h, l, s_h[q][tid], s_l[q][tid]);
       u_h[tid] = h;
       u_l[tid] = l;
     }
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(256) k_xtx_v_df(const float* __restrict__ X, i
   }
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    const int64_t col = tid + 256 * c;
+    const int64_t col = tid + NT * c;
     if (col < d) part[blockIdx.x * d + col] = (double)ah[c] + (double)al[c];
   }
 }

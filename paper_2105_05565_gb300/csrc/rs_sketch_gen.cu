@@ -28,7 +28,7 @@ __global__ void k_gen_sample(const Ctrl* __restrict__ ctrl, int64_t k0_arg, uint
 
   const int64_t k0 = k0_arg >= 0 ? k0_arg : ctrl->k;
   const int64_t k = k0 + blockIdx.x;
-  if (k0_arg < 0 && (halted(ctrl) || k >= ctrl->max_iters)) return;
+  if (k0_arg < 0 && (stopped(ctrl) || k >= ctrl->max_iters)) return;
   const uint64_t key = iter_key(seed, k);
   int32_t* out = perm + (int64_t)blockIdx.x * perm_stride;
 
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(1024) k_gen_count(const Ctrl* __restrict__ ctr
 
   const int64_t k0 = k0_arg >= 0 ? k0_arg : ctrl->k;
   const int64_t k = k0 + blockIdx.x;
-  if (k0_arg < 0 && (halted(ctrl) || k >= ctrl->max_iters)) return;
+  if (k0_arg < 0 && (stopped(ctrl) || k >= ctrl->max_iters)) return;
   const uint64_t key = iter_key(seed, k);
   int32_t* out = perm + (int64_t)blockIdx.x * perm_stride;
   int32_t* bo = boff + (int64_t)blockIdx.x * boff_stride;
