@@ -3,7 +3,7 @@
 Workload (default): dense primal ridge, X 100000 x 4096 = U diag(sigma) V^T with
 Haar U, V and sigma geometric from 1 to 1e-3 (float32 storage), y = X w* + 0.01 noise,
 lambda = 1e-2, count sketch tau = 256 with the heuristic momentum, FP32 bulk products
-with FP64 true-residual refresh every 50 iterations ("mixed"), to relative residual
+with FP64 true-residual refresh every 150 iterations ("mixed"), to relative residual
 1e-6. The plain FP64 GPU path on the same problem (and both precisions with the
 subsample sketch) are measured beside it.
 
@@ -31,8 +31,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time-to-1e-6 rel. residual & iters/s, chosen form vs plain FP64, one GB300"
 N_ROWS, N_COLS, TAU, LAM, TOL, MAX_IT = 100000, 4096, 256, 1e-2, 1e-6, 30000
+REFRESH = 150
 WORKLOAD = ("dense primal ridge X 100000x4096 (Haar U,V; sigma geometric 1..1e-3; fp32), "
-            "lambda 1e-2, count sketch tau 256, heuristic momentum, mixed FP32 + FP64 refresh/50, "
+            "lambda 1e-2, count sketch tau 256, heuristic momentum, mixed FP32 + FP64 refresh/150, "
             "tol 1e-6")
 
 
@@ -108,7 +109,7 @@ def one_solve(rs, X, y, precision, sketch, device, w_out, on_host=False, chol_fp
     torch.cuda.synchronize(device)
     e0.record(st)
     with rs.Solver(X, y, LAM, sketch=sketch, tau=TAU, momentum="heuristic", seed=0,
-                   precision=precision, refresh_every=50, device=device.index or 0,
+                   precision=precision, refresh_every=REFRESH, device=device.index or 0,
                    stream=st.cuda_stream, chol_fp64=chol_fp64) as s:
         w, hist, iters, conv = s.solve(TOL, MAX_IT, w_out=None if on_host else w_out)
         setup_ms, solve_ms = s.timings()
@@ -126,10 +127,10 @@ def profile_kernels(rs, X, y, device):
 
     st = torch.cuda.current_stream(device)
     with rs.Solver(X, y, LAM, sketch="count", tau=TAU, momentum="heuristic", seed=0,
-                   precision="mixed", refresh_every=50, device=device.index or 0,
+                   precision="mixed", refresh_every=REFRESH, device=device.index or 0,
                    stream=st.cuda_stream) as s:
         s.solve(TOL, 60)
-        return s.profile_iteration(100)
+        return s.profile_iteration(2 * REFRESH)
 
 
 def roofline(stats, pk):
@@ -146,8 +147,7 @@ def roofline(stats, pk):
     achieved = nbytes / (ms * 1e-3) / 1e9
     traffic = None
     if name in PROFILED_TRAFFIC and n > 0:
-        t_bytes, t_iters = PROFILED_TRAFFIC[name]
-        traffic = t_bytes * (_its / n) / t_iters  # per launch, scaled to its iterations
+        traffic = PROFILED_TRAFFIC[name](_its / n)  # per launch
     return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
 
@@ -212,10 +212,13 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-# ncu DRAM traffic per launch of the iteration kernel (read + write), taken on the
-# X 20000 x 4096 profiling case; the kernel does not touch X, so one launch (50
-# iterations on m = 4096, tau = 256) moves the same bytes at n = 100000
-PROFILED_TRAFFIC = {"iterate": (227.9e6, 50)}
+# ncu DRAM traffic (read + write) per launch, taken on the X 20000 x 4096 profiling
+# case (profiles/): the iteration kernel does not touch X, so a launch of 50
+# iterations moves the same bytes at n = 100000 (scaled to the launch's
+# iterations); the refresh product reads X once, so its traffic scales with n
+# (327.8 MB read + 2.9 MB written at n = 20000, times 5)
+PROFILED_TRAFFIC = {"iterate": lambda its_per_launch: 227.9e6 * its_per_launch / 50.0,
+                    "refresh": lambda its_per_launch: 330.7e6 * N_ROWS / 20000.0}
 
 
 def bench_batched(args, rs, dev):
@@ -481,11 +484,11 @@ def main():
         "wall_s_timed": wall,
     }
     line.update(extra)
-    # kernels launched in the timed region, per chunk of 50 iterations: chunk begin,
+    # kernels launched in the timed region, per chunk of REFRESH iterations: chunk begin,
     # sketch plans, inverse plan map, S^T A, S^T A S, factor + inverse, the fused
     # iteration kernel, and the FP64 refresh (float-pair X^T X v, sum, finish);
     # per step 10 more (forming A and b, ||b||, initial state, final FP64 check)
-    n_chunks = sum((r["iters"] + 49) // 50 for r in runs)
+    n_chunks = sum((r["iters"] + REFRESH - 1) // REFRESH for r in runs)
     line["gpu_launches"] = int(n_chunks * 10 + args.steps * 10)
     print(json.dumps(line), flush=True)
     if dist:

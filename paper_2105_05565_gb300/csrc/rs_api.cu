@@ -77,7 +77,7 @@ struct rs_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   // problem
-  int form = 0, sketch = 0, precision = 0, chol_fp64 = 1, refresh_every = 50;
+  int form = 0, sketch = 0, precision = 0, chol_fp64 = 1, refresh_every = 150;
   int64_t n = 0, d = 0, m = 0, tau = 0, s = 0, kk = 0, mp = 0, ld = 0, chunk = 64;
   double lambda = 0.0;
   uint64_t seed = 0;
@@ -829,7 +829,7 @@ void rs_default_opts(rs_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
   o->precision = RS_PLAIN_FP64;
-  o->refresh_every = 50;
+  o->refresh_every = 150;
   o->sub_s = 0;
   o->cuda_stream = nullptr;
   o->device = 0;
@@ -909,7 +909,7 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     delete c;
     return RS_EUNSUPPORTED;
   }
-  c->refresh_every = o.refresh_every > 0 ? o.refresh_every : 50;
+  c->refresh_every = o.refresh_every > 0 ? o.refresh_every : 150;
   c->n = X->n;
   c->d = X->d;
   c->m = (form == RS_PRIMAL) ? X->d : X->n;
@@ -961,9 +961,9 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     const int64_t per_slot = c->tau * c->ld * (int64_t)c->elem() * (sketch == RS_GAUSSIAN ? 2 : 1) +
                              c->tau * c->tau * 24 + c->ld * 4;
     const int64_t cap = std::max<int64_t>(1, (int64_t)4e9 / std::max<int64_t>(per_slot, 1));
-    if (c->chunk > cap) {
-      if (c->mixed()) { c->err = "rs_create: refresh_every too large for the per-iteration buffers"; return fail(RS_EINVAL); }
+    if (c->chunk > cap) {  // (mixed: the refresh period shortens with the chunk)
       c->chunk = cap;
+      if (c->mixed()) c->refresh_every = (int)cap;
     }
   }
   c->nslots = c->chunk;
@@ -999,9 +999,9 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
                              c->tau * c->tau * 24 + c->ld * 4 + c->mf_nrb * 16;
     const int64_t cap = std::max<int64_t>(1, (int64_t)4e9 / std::max<int64_t>(per_slot, 1));
     if (c->chunk > cap) {
-      if (c->mixed()) { c->err = "rs_create: refresh_every too large for the per-iteration buffers"; return fail(RS_EINVAL); }
       c->chunk = cap;
       c->nslots = cap;
+      if (c->mixed()) c->refresh_every = (int)cap;
     }
   } else {
   // X, y
