@@ -25,6 +25,15 @@
 // CTA of its cluster with st.async, whose bytes complete on the destination's
 // mbarrier. Every wait is bounded (global timer); a CTA that gives up raises the
 // abort word, which ends the others' waits.
+//
+// Precision of the mixed form (T = TF = float): FP64 instructions take 64 cycles
+// (add, FMA) to about 100 (conversions) on this GPU, and every one of them on the
+// path from one all-reduce to the next adds to the iteration's latency. So w,
+// w_prev, r, r_prev are float pairs (hi + lo) in shared memory, each update adds
+// an FP32 increment to them exactly (error-free sums), the all-reduced delta
+// arrives as float pairs, and ||r_k||^2 / ||r_0||^2 is summed in FP32 for the
+// stopping test (a convergence it signals is confirmed by the FP64 refresh). FP64
+// arithmetic remains only at the launch's start and end.
 #include "rs_kernels.cuh"
 #include "rs_ptx.cuh"
 
@@ -98,7 +107,7 @@ struct Xch {
   uint32_t crank;
   int64_t tau, ne, E, G, nw;
   void* mine;       // PT[tau]: own partials of delta
-  double* mine_nrm; // own partial of ||r||^2
+  const void* mine_nrm;  // own partial of ||r||^2 (float for PT = float, else double)
   double* tot;      // ne all-reduced totals (delta, then ||r||^2)
   void* red;        // per-group sums of the reducer
   uint64_t* xbar;
@@ -109,8 +118,8 @@ struct Xch {
 // has the payload and no separate flag, fence or release is needed. Tags increase
 // from exchange to exchange and from launch to launch and the buffer alternates by
 // parity, so a stale word never carries the current tag. Payloads: PT = float,
-// one word per delta entry and the norm as a float pair (hi, lo); PT = double, two
-// words (low and high halves) per entry.
+// one word per delta entry and two for the norm (the value, then zero); PT =
+// double, two words (low and high halves) per entry.
 __device__ __forceinline__ uint64_t ll_word(uint32_t payload, uint32_t tag) {
   return (uint64_t)payload | ((uint64_t)tag << 32);
 }
@@ -140,14 +149,14 @@ __device__ void xch_begin(const Xch& x, uint32_t tag, uint32_t n) {
     for (int64_t e = tid; e < x.tau; e += kWThreads)
       ptx::st_relaxed_u64(pb + e, ll_word(__float_as_uint(mine[e]), tag));
     if (tid == 0) {
-      const double v = *x.mine_nrm;
-      const float hi = (float)v, lo = (float)(v - (double)hi);
-      ptx::st_relaxed_u64(pb + x.tau, ll_word(__float_as_uint(hi), tag));
-      ptx::st_relaxed_u64(pb + x.tau + 1, ll_word(__float_as_uint(lo), tag));
+      const float v = *static_cast<const float*>(x.mine_nrm);
+      ptx::st_relaxed_u64(pb + x.tau, ll_word(__float_as_uint(v), tag));
+      ptx::st_relaxed_u64(pb + x.tau + 1, ll_word(0u, tag));
     }
   } else {
     for (int64_t e = tid; e < x.ne; e += kWThreads) {
-      const uint64_t b = (uint64_t)__double_as_longlong(e < x.tau ? (double)mine[e] : *x.mine_nrm);
+      const uint64_t b = (uint64_t)__double_as_longlong(
+          e < x.tau ? (double)mine[e] : *static_cast<const double*>(x.mine_nrm));
       ptx::st_relaxed_u64(pb + 2 * e, ll_word((uint32_t)b, tag));
       ptx::st_relaxed_u64(pb + 2 * e + 1, ll_word((uint32_t)(b >> 32), tag));
     }
@@ -169,7 +178,9 @@ __device__ __forceinline__ void ll_pos(int64_t e, int64_t tau, int64_t& w0, int&
 // second half: gather the own entries of every CTA (re-reading words whose tag is
 // not current yet), sum them in a fixed order (float pairs for PT = float, so the
 // sum is as accurate as in FP64 without FP64 arithmetic), scatter the sums to the
-// cluster and wait for the cluster's sums; false on abort or timeout
+// cluster (PT = float: each total as a normalised float pair (hi, lo) in the 8
+// bytes of its `tot` entry) and wait for the cluster's sums; false on abort or
+// timeout
 template <typename PT>
 __device__ bool xch_end(const Xch& x, uint32_t tag, uint32_t n) {
   constexpr bool F = sizeof(PT) == 4;
@@ -239,7 +250,6 @@ __device__ bool xch_end(const Xch& x, uint32_t tag, uint32_t n) {
     return false;
   }
   for (int64_t e = e0 + tid; e < e1; e += kWThreads) {
-    double v;
     if constexpr (F) {
       const float2* r = static_cast<const float2*>(x.red);
       float S = 0.f, C = 0.f;
@@ -250,15 +260,20 @@ __device__ bool xch_end(const Xch& x, uint32_t tag, uint32_t n) {
         S = t;
         C += err + p.y;
       }
-      v = (double)S + (double)C;
+      float hi, lo;
+      two_sum(S, C, hi, lo);
+      const uint64_t v = (uint64_t)__float_as_uint(hi) | ((uint64_t)__float_as_uint(lo) << 32);
+#pragma unroll
+      for (uint32_t rk = 0; rk < (uint32_t)kWideCluster; ++rk)
+        ptx::st_async_b64(ptx::map_rank(x.tot + e, rk), v, ptx::map_rank(x.xbar, rk));
     } else {
       const double* r = static_cast<const double*>(x.red);
-      v = 0.0;
+      double v = 0.0;
       for (int64_t g = 0; g < x.G; ++g) v += r[g * x.E + (e - e0)];
-    }
 #pragma unroll
-    for (uint32_t rk = 0; rk < (uint32_t)kWideCluster; ++rk)
-      ptx::st_async_f64(ptx::map_rank(x.tot + e, rk), v, ptx::map_rank(x.xbar, rk));
+      for (uint32_t rk = 0; rk < (uint32_t)kWideCluster; ++rk)
+        ptx::st_async_f64(ptx::map_rank(x.tot + e, rk), v, ptx::map_rank(x.xbar, rk));
+    }
   }
   const bool ok = wait_bar(x.xbar, n & 1, x.abort_word);
   if (__syncthreads_or(!ok)) {
@@ -266,6 +281,23 @@ __device__ bool xch_end(const Xch& x, uint32_t tag, uint32_t n) {
     return false;
   }
   return true;
+}
+
+// float pair (hi, lo) of a double, and back
+__device__ __forceinline__ float2 split2(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+__device__ __forceinline__ double join2(float2 a) { return (double)a.x + (double)a.y; }
+
+// a + b for a float pair a and a float b, error-free up to the final rounding of lo
+__device__ __forceinline__ float2 add_pf(float2 a, float b) {
+  float s, e;
+  two_sum(a.x, b, s, e);
+  e += a.y;
+  float h, l;
+  two_sum(s, e, h, l);
+  return make_float2(h, l);
 }
 
 }  // namespace
@@ -283,6 +315,10 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   const double tol = ctrl->tol, r0 = ctrl->r0;
   const double thr2 = (tol * r0) * (tol * r0);
   const double thr2_lo = thr2 * (1.0 - 1e-9), thr2_hi = thr2 * (1.0 + 1e-9);
+  // float-pair state (mixed form): norms relative to ||r_0||, thresholds in FP32
+  constexpr bool kFP = sizeof(T) == 4 && sizeof(TF) == 4;
+  const float inv_r0f = r0 > 0.0 ? (float)(1.0 / r0) : 0.f;
+  const float thr2f = (float)(tol * tol);
   const int no_stop = ctrl->no_stop;
   const uint64_t tag0 = (*g.epoch) << 24;
 
@@ -312,6 +348,12 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   double* srp = sr + qs;
   double* sw = srp + qs;
   double* swp = sw + qs;
+  // the same buffers as float pairs (kFP)
+  float2* fr = reinterpret_cast<float2*>(sr);
+  float2* frp = fr + qs;
+  float2* fw = frp + qs;
+  float2* fwp = fw + qs;
+  const float2* tot2 = reinterpret_cast<const float2*>(tot);
   int32_t* prow = reinterpret_cast<int32_t*>(smem + L.prow);
   int32_t* pinv = reinterpret_cast<int32_t*>(smem + L.pinv);
   double* hn2 = reinterpret_cast<double*>(smem + L.hn2);
@@ -322,9 +364,14 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   uint64_t* xbar = bars + 6;       // 1
   double* sgam = reinterpret_cast<double*>(smem + L.gb);
   double* sbet = sgam + g.chunk;
+  float* sgamf = reinterpret_cast<float*>(sgam);  // kFP: gamma_k, beta_k in FP32
+  float* sbetf = sgamf + g.chunk;
+  float2* hn2f = reinterpret_cast<float2*>(hn2);  // kFP: ||r_k||^2 / ||r_0||^2 as float pairs
   __shared__ int s_nrows;
   __shared__ double s_red[32];
   __shared__ double s_nrm;  // own partial of ||r||^2
+  __shared__ float s_redf[32];
+  __shared__ float s_nrmf;  // kFP: own partial of ||r||^2 / ||r_0||^2
   __shared__ int s_dec;     // stopping decision of the current iteration
 
   if (tid == 0) {
@@ -332,14 +379,26 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
     ptx::fence_mbar_init();
   }
   for (int64_t k = kstart + tid; k < kend; k += kWThreads) {
-    sgam[k - k0] = g.gam[k];
-    sbet[k - k0] = g.bet[k];
+    if constexpr (kFP) {
+      sgamf[k - k0] = (float)g.gam[k];
+      sbetf[k - k0] = (float)g.bet[k];
+    } else {
+      sgam[k - k0] = g.gam[k];
+      sbet[k - k0] = g.bet[k];
+    }
   }
   for (int64_t i = tid; i < qc; i += kWThreads) {
-    sr[i] = g.r[ilo + i];
-    srp[i] = g.rp[ilo + i];
-    sw[i] = g.w[ilo + i];
-    swp[i] = g.wp[ilo + i];
+    if constexpr (kFP) {
+      fr[i] = split2(g.r[ilo + i]);
+      frp[i] = split2(g.rp[ilo + i]);
+      fw[i] = split2(g.w[ilo + i]);
+      fwp[i] = split2(g.wp[ilo + i]);
+    } else {
+      sr[i] = g.r[ilo + i];
+      srp[i] = g.rp[ilo + i];
+      sw[i] = g.w[ilo + i];
+      swp[i] = g.wp[ilo + i];
+    }
   }
   __syncthreads();
   ptx::cluster_sync_all();  // peers' mbarriers are initialised before any remote store
@@ -348,7 +407,8 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   x.part = g.part; x.abort_word = g.abort_word;
   x.nblk = g.nblk; x.cta = cta; x.crank = crank;
   x.tau = tau; x.ne = tau + 1; x.E = L.E; x.G = L.G; x.nw = ll_words<TF>(tau);
-  x.mine = mine; x.mine_nrm = &s_nrm; x.tot = tot; x.red = red; x.xbar = xbar;
+  x.mine = mine; x.tot = tot; x.red = red; x.xbar = xbar;
+  if constexpr (kFP) x.mine_nrm = &s_nrmf; else x.mine_nrm = &s_nrm;
 
   // copy bookkeeping, identical in every thread: issued / consumed phases per buffer
   uint32_t sa_iss[2] = {0, 0}, sa_use[2] = {0, 0};
@@ -425,10 +485,20 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   auto partial = [&](bool with_delta, bool fresh) -> bool {
     const bool use_p = with_delta && has_rows;
     if (fresh) {
-      double sq = 0.0;
-      for (int64_t i = tid; i < qc; i += kWThreads) sq += sr[i] * sr[i];
-      if (wid * 32 < qc) sq = warp_sum(sq);
-      if (lane == 0) s_red[wid] = sq;
+      if constexpr (kFP) {
+        float sq = 0.f;
+        for (int64_t i = tid; i < qc; i += kWThreads) {
+          const float v = fr[i].x * inv_r0f;
+          sq = fmaf(v, v, sq);
+        }
+        if (wid * 32 < qc) sq = warp_sum(sq);
+        if (lane == 0) s_redf[wid] = sq;
+      } else {
+        double sq = 0.0;
+        for (int64_t i = tid; i < qc; i += kWThreads) sq += sr[i] * sr[i];
+        if (wid * 32 < qc) sq = warp_sum(sq);
+        if (lane == 0) s_red[wid] = sq;
+      }
     }
     if (use_p) {
       const bool r = wait_bar(p_full, p_use & 1, g.abort_word);
@@ -443,22 +513,43 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
     if (fresh) {  // else the row update has written them
       for (int t = tid; t < nrows; t += kWThreads) {
         const int32_t pr = prow[t];
-        const double v = sr[pr & 0x7FFFFFFF];
-        coef[t] = (TF)(pr < 0 ? -v : v);
+        if constexpr (kFP) {
+          const float v = fr[pr & 0x7FFFFFFF].x;
+          coef[t] = pr < 0 ? -v : v;
+        } else {
+          const double v = sr[pr & 0x7FFFFFFF];
+          coef[t] = (TF)(pr < 0 ? -v : v);
+        }
       }
       __syncthreads();
     }
     if (tid == 0) {
-      double t = 0.0;
-      if (has_rows)
-        for (int w = 0; w < kWWarps; ++w) t += s_red[w];
-      s_nrm = t;
+      if constexpr (kFP) {
+        float t = 0.f;
+        if (has_rows)
+          for (int w = 0; w < kWWarps; ++w) t += s_redf[w];
+        s_nrmf = t;
+      } else {
+        double t = 0.0;
+        if (has_rows)
+          for (int w = 0; w < kWWarps; ++w) t += s_red[w];
+        s_nrm = t;
+      }
     }
+    // four independent chains over the staged rows, added in a fixed order
+    const int64_t pld = g.pld;
     for (int64_t j = tid; j < tau; j += kWThreads) {
-      TF acc = TF(0);
-#pragma unroll 4
-      for (int t = 0; t < nrows; ++t) acc += coef[t] * pbuf[(size_t)t * g.pld + j];
-      mine[j] = acc;
+      const TF* pj = pbuf + j;
+      TF a0 = TF(0), a1 = TF(0), a2 = TF(0), a3 = TF(0);
+      int t = 0;
+      for (; t + 4 <= nrows; t += 4) {
+        a0 += coef[t] * pj[(int64_t)t * pld];
+        a1 += coef[t + 1] * pj[(int64_t)(t + 1) * pld];
+        a2 += coef[t + 2] * pj[(int64_t)(t + 2) * pld];
+        a3 += coef[t + 3] * pj[(int64_t)(t + 3) * pld];
+      }
+      for (; t < nrows; ++t) a0 += coef[t] * pj[(int64_t)t * pld];
+      mine[j] = (a0 + a1) + (a2 + a3);
     }
     return true;
   };
@@ -494,14 +585,23 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
     if (tid == 0) {
       int dec = 0;
       if (k > kstart) {
-        const double n2 = tot[tau];
-        hn2[k - k0] = n2;
-        if (!isfinite(n2)) {
-          dec = 2;
-        } else if (!no_stop) {
-          // rel = sqrt(n2) / r0 <= tol, decided on n2 away from the boundary
-          if (n2 <= thr2_lo) dec = 1;
-          else if (n2 <= thr2_hi) dec = (sqrt(n2) / r0 <= tol) ? 1 : 0;
+        if constexpr (kFP) {
+          // relative ||r_k||^2 in FP32; the FP64 refresh confirms a convergence
+          const float2 n2 = tot2[tau];
+          hn2f[k - k0] = n2;
+          const float nf = n2.x + n2.y;
+          if (!isfinite(nf)) dec = 2;
+          else if (!no_stop && nf <= thr2f) dec = 1;
+        } else {
+          const double n2 = tot[tau];
+          hn2[k - k0] = n2;
+          if (!isfinite(n2)) {
+            dec = 2;
+          } else if (!no_stop) {
+            // rel = sqrt(n2) / r0 <= tol, decided on n2 away from the boundary
+            if (n2 <= thr2_lo) dec = 1;
+            else if (n2 <= thr2_hi) dec = (sqrt(n2) / r0 <= tol) ? 1 : 0;
+          }
         }
       }
       s_dec = dec;
@@ -513,7 +613,10 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
     }
     // iteration k on the own rows
     const int64_t s = slot_of(k);
-    for (int64_t j = tid; j < tau; j += kWThreads) dT[j] = (T)tot[j];
+    for (int64_t j = tid; j < tau; j += kWThreads) {
+      if constexpr (kFP) dT[j] = tot2[j].x + tot2[j].y;
+      else dT[j] = (T)tot[j];
+    }
     const int b = (int)(s % nsab);
     bool r = true;
     if (has_rows) {
@@ -564,32 +667,68 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
       }
       __syncthreads();
       if (nsab == 1 && k + 1 < kend) issue_sa(s + 1);
-      const double gk = sgam[k - k0], bk = sbet[k - k0];
       const int32_t* iv = ivb + (s % 3) * qs;
-      double sq = 0.0;
-      for (int64_t i = tid; i < qc; i += kWThreads) {
-        T asum = T(0);
+      if constexpr (kFP) {
+        // x_{k+1} = x_k + beta (x_k - x_{k-1}) - gamma (...): the increment in FP32,
+        // added to the float pair exactly
+        const float gk = sgamf[k - k0], bk = sbetf[k - k0];
+        float sq = 0.f;
+        for (int64_t i = tid; i < qc; i += kWThreads) {
+          float asum = 0.f;
 #pragma unroll
-        for (int w = 0; w < kWWarps; ++w) asum += red[w * qs + i];
-        const double asd = (double)asum;
-        const int32_t e = iv[i];
-        const double ui = (e == kNotSketched) ? 0.0
-                          : (entry_neg(e) ? -tot[e & 0x7FFFFFFF] : tot[e & 0x7FFFFFFF]);
-        const double ri = sr[i], rpi = srp[i], wi = sw[i], wpi = swp[i];
-        const double rn = (1.0 + bk) * ri - bk * rpi - gk * asd;
-        sr[i] = rn;
-        const int32_t t = pinv[i];  // staged row of slot k + 1
-        if (t >= 0) coef[t] = (TF)(prow[t] < 0 ? -rn : rn);
-        srp[i] = ri;
-        sw[i] = (1.0 + bk) * wi - bk * wpi - gk * ui;
-        swp[i] = wi;
-        sq += rn * rn;
+          for (int w = 0; w < kWWarps; ++w) asum += red[w * qs + i];
+          const int32_t e = iv[i];
+          float ui = 0.f;
+          if (e != kNotSketched) {
+            const float2 dv = tot2[e & 0x7FFFFFFF];
+            ui = entry_neg(e) ? -(dv.x + dv.y) : (dv.x + dv.y);
+          }
+          const float2 ri = fr[i], rpi = frp[i], wi = fw[i], wpi = fwp[i];
+          const float dr = (ri.x - rpi.x) + (ri.y - rpi.y);
+          const float dw = (wi.x - wpi.x) + (wi.y - wpi.y);
+          const float2 rn = add_pf(ri, fmaf(bk, dr, -gk * (float)asum));
+          fr[i] = rn;
+          frp[i] = ri;
+          fw[i] = add_pf(wi, fmaf(bk, dw, -gk * ui));
+          fwp[i] = wi;
+          const int32_t t = pinv[i];  // staged row of slot k + 1
+          if (t >= 0) coef[t] = prow[t] < 0 ? -rn.x : rn.x;
+          const float v = rn.x * inv_r0f;
+          sq = fmaf(v, v, sq);
+        }
+        if (wid * 32 < qc) sq = warp_sum(sq);
+        if (lane == 0) s_redf[wid] = sq;
+      } else {
+        const double gk = sgam[k - k0], bk = sbet[k - k0];
+        double sq = 0.0;
+        for (int64_t i = tid; i < qc; i += kWThreads) {
+          T asum = T(0);
+#pragma unroll
+          for (int w = 0; w < kWWarps; ++w) asum += red[w * qs + i];
+          const double asd = (double)asum;
+          const int32_t e = iv[i];
+          const double ui = (e == kNotSketched) ? 0.0
+                            : (entry_neg(e) ? -tot[e & 0x7FFFFFFF] : tot[e & 0x7FFFFFFF]);
+          const double ri = sr[i], rpi = srp[i], wi = sw[i], wpi = swp[i];
+          const double rn = (1.0 + bk) * ri - bk * rpi - gk * asd;
+          sr[i] = rn;
+          const int32_t t = pinv[i];  // staged row of slot k + 1
+          if (t >= 0) coef[t] = (TF)(prow[t] < 0 ? -rn : rn);
+          srp[i] = ri;
+          sw[i] = (1.0 + bk) * wi - bk * wpi - gk * ui;
+          swp[i] = wi;
+          sq += rn * rn;
+        }
+        if (wid * 32 < qc) sq = warp_sum(sq);
+        if (lane == 0) s_red[wid] = sq;
       }
-      if (wid * 32 < qc) sq = warp_sum(sq);
-      if (lane == 0) s_red[wid] = sq;
     }
-    if (cta == 0 && k + 1 == kend)
-      for (int64_t j = tid; j < tau; j += kWThreads) g.delta_out[j] = tot[j];
+    if (cta == 0 && k + 1 == kend) {
+      for (int64_t j = tid; j < tau; j += kWThreads) {
+        if constexpr (kFP) g.delta_out[j] = join2(tot2[j]);
+        else g.delta_out[j] = tot[j];
+      }
+    }
     ++k;
     ok = partial(k < kend, false);
   }
@@ -608,15 +747,25 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   }
   __syncthreads();
   for (int64_t i = tid; i < qc; i += kWThreads) {
-    g.r[ilo + i] = sr[i];
-    g.rp[ilo + i] = srp[i];
-    g.w[ilo + i] = sw[i];
-    g.wp[ilo + i] = swp[i];
+    if constexpr (kFP) {
+      g.r[ilo + i] = join2(fr[i]);
+      g.rp[ilo + i] = join2(frp[i]);
+      g.w[ilo + i] = join2(fw[i]);
+      g.wp[ilo + i] = join2(fwp[i]);
+    } else {
+      g.r[ilo + i] = sr[i];
+      g.rp[ilo + i] = srp[i];
+      g.w[ilo + i] = sw[i];
+      g.wp[ilo + i] = swp[i];
+    }
   }
   // relative residuals of the tested iterations (kstart was tested before)
   if (cta == 0) {
     const int64_t klast = (outcome == 3) ? kstart : k;
-    for (int64_t kk = kstart + 1 + tid; kk <= klast; kk += kWThreads) g.hist[kk] = sqrt(hn2[kk - k0]) / r0;
+    for (int64_t kk = kstart + 1 + tid; kk <= klast; kk += kWThreads) {
+      if constexpr (kFP) g.hist[kk] = sqrt(join2(hn2f[kk - k0]));
+      else g.hist[kk] = sqrt(hn2[kk - k0]) / r0;
+    }
   }
   if (cta == 0 && tid == 0) {
     ctrl->k = k;

@@ -75,6 +75,14 @@ __device__ __forceinline__ void st_async_f64(uint32_t cluster_addr, double v, ui
       "l"(__double_as_longlong(v)), "r"(cluster_bar)
       : "memory");
 }
+// the same for 8 raw bytes (a packed pair of floats)
+__device__ __forceinline__ void st_async_b64(uint32_t cluster_addr, uint64_t v, uint32_t cluster_bar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(
+          cluster_addr),
+      "l"(v), "r"(cluster_bar)
+      : "memory");
+}
 __device__ __forceinline__ void fence_cluster() {
   asm volatile("fence.acq_rel.cluster;" ::: "memory");
 }
