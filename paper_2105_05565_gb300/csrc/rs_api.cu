@@ -1037,7 +1037,8 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
       TRYC(e2);
     } else if (c->mixed()) TRYC((launch_form_A<float, float>(st, Xf, c->n, c->d, dual, lambda, static_cast<float*>(c->A), c->ld)));
     else TRYC((launch_form_A<float, double>(st, Xf, c->n, c->d, dual, lambda, static_cast<double*>(c->A), c->ld)));
-    if (!dual) TRYC(launch_xt_v<float>(st, Xf, c->n, c->d, c->y, c->b, c->xt_part));
+    if (!dual && c->mixed()) TRYC(launch_xt_v_pairs(st, Xf, c->n, c->d, c->y, c->b, c->xt_part));
+    else if (!dual) TRYC(launch_xt_v<float>(st, Xf, c->n, c->d, c->y, c->b, c->xt_part));
   } else {
     const double* Xd = static_cast<const double*>(c->X);
     if (c->mixed()) TRYC((launch_form_A<double, float>(st, Xd, c->n, c->d, dual, lambda, static_cast<float*>(c->A), c->ld)));
@@ -2203,7 +2204,10 @@ rs_status batch_init(rs_batch* b, const rs_matrix* Xs, const double* const* Ys,
       e = cudaMemcpyAsync(ytmp, Ys[p] + (size_t)r * c->n, (size_t)c->n * sizeof(double),
                           y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream);
       if (e != cudaSuccess) break;
-      if (c->xdtype == RS_F32)
+      if (c->xdtype == RS_F32 && c->mixed())
+        e = launch_xt_v_pairs(b->stream, static_cast<const float*>(c->X), c->n, c->d, ytmp,
+                              bp + (size_t)r * c->m, c->xt_part);
+      else if (c->xdtype == RS_F32)
         e = launch_xt_v<float>(b->stream, static_cast<const float*>(c->X), c->n, c->d, ytmp,
                                bp + (size_t)r * c->m, c->xt_part);
       else

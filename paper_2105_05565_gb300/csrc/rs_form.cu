@@ -42,7 +42,10 @@ template cudaError_t launch_mirror_lower<double>(cudaStream_t, double*, int64_t,
 // ---- X^T v: column sums of X weighted by v, chunked over rows, FP64 ----
 constexpr int64_t kXtRows = 256;
 
-size_t xt_part_elems(int64_t n, int64_t d) { return (size_t)((n + kXtRows - 1) / kXtRows) * d; }
+// (n more for the float pairs of v of launch_xt_v_pairs)
+size_t xt_part_elems(int64_t n, int64_t d) {
+  return (size_t)((n + kXtRows - 1) / kXtRows) * d + (size_t)n;
+}
 
 template <typename TI>
 __global__ void __launch_bounds__(256) k_xt_v_part(const TI* __restrict__ X, int64_t n, int64_t d,
@@ -493,6 +496,31 @@ __global__ void __launch_bounds__(kXtuCols) k_xtu_df(const float* __restrict__ X
 #pragma unroll
   for (int q = 0; q < NV; ++q)
     if (q < nv) part[((int64_t)blockIdx.y * nv + q) * d + c] = (double)ah[q] + (double)al[q];
+}
+
+// U[i] = (hi, lo) float pair of v[i]
+__global__ void k_split_pairs(const double* __restrict__ v, int64_t n, float2* __restrict__ U,
+                              const int32_t* __restrict__ stop) {
+  if (stop != nullptr && *(volatile const int32_t*)stop) return;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x = v[i];
+  const float h = (float)x;
+  U[i] = make_float2(h, (float)(x - (double)h));
+}
+
+// X^T v for FP32 X in float-pair arithmetic (the FP64 pipe is too narrow on this GPU
+// for one FP64 FMA per entry of X): v split into float pairs, then the column sums
+// of pass 2 of the two-pass product, then the FP64 sum of the row blocks' sums.
+cudaError_t launch_xt_v_pairs(cudaStream_t st, const float* X, int64_t n, int64_t d,
+                              const double* v, double* out, double* part, const int32_t* stop) {
+  const int64_t nblk = (n + kXtuRows - 1) / kXtuRows;
+  float2* U = reinterpret_cast<float2*>(part + nblk * d);  // after the row blocks' sums
+  k_split_pairs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, n, U, stop);
+  const dim3 g2((unsigned)((d + kXtuCols - 1) / kXtuCols), (unsigned)nblk);
+  k_xtu_df<1><<<g2, kXtuCols, 0, st>>>(X, n, d, 1, U, part, stop);
+  k_sum_parts<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(part, nblk, d, out, stop);
+  return cudaGetLastError();
 }
 
 int64_t xtx_two_pass_part(int64_t n, int64_t d, int nv) {

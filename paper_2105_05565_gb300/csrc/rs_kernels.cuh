@@ -331,6 +331,11 @@ template <typename TI>
 cudaError_t launch_xt_v(cudaStream_t st, const TI* X, int64_t n, int64_t d, const double* v,
                         double* out, double* part, const int32_t* stop = nullptr);
 size_t xt_part_elems(int64_t n, int64_t d);
+// the same for FP32 X in float-pair arithmetic (relative error about 1e-12; part as
+// for launch_xt_v)
+cudaError_t launch_xt_v_pairs(cudaStream_t st, const float* X, int64_t n, int64_t d,
+                              const double* v, double* out, double* part,
+                              const int32_t* stop = nullptr);
 // out[i] = sum_j X[i, j] v[j] (i < n), FP64 accumulate
 template <typename TI>
 cudaError_t launch_x_v(cudaStream_t st, const TI* X, int64_t n, int64_t d, const double* v,

@@ -2,16 +2,22 @@
 //
 // TF32 operands, FP32 accumulation in tensor memory. X is first copied transposed
 // (Xt = X^T, d x ldk, K = n contiguous and zero padded) so that both operands of
-// C = Xt Xt^T are K-major. One CTA per 128 x 128 tile of the lower triangle:
-//   warp 0 (one lane)  TMA producer: 128 x 32 fp32 boxes of Xt (128B swizzle) into a
-//                      ring of kStages shared-memory stages, completion on mbarriers;
-//   warp 1 (one lane)  MMA issuer: 4 x tcgen05.mma (M 128, N 128, K 8) per stage,
-//                      tcgen05.commit frees the stage when those MMAs retire;
-//   warps 0-3          epilogue: tcgen05.ld of the 128 x 128 FP32 accumulator (each
+// C = Xt Xt^T are K-major. The lower triangle is cut into 128 x 256 tiles (128 rows
+// ti, 256 columns tj, tj <= ti / 2); the two tiles of the row blocks 2a and 2a + 1
+// with the same column block form a cluster of two CTAs, which share that column
+// block: each CTA loads one 128-row half of it and multicasts the half into both
+// CTAs' shared memory, so a CTA reads 16 KB of A rows and 16 KB of B rows from L2
+// per 128 x 256 x 32 step (the operand stream from L2 bounds this kernel).
+//   warp 0 (one lane)  TMA producer: its A box and its multicast B half into a ring
+//                      of kStages stages; a stage is refilled once the MMAs of both
+//                      CTAs have released it (two arrivals on its `empty` barrier);
+//   warp 1 (one lane)  MMA issuer: 4 x tcgen05.mma (M 128, N 256, K 8) per stage,
+//                      tcgen05.commit (multicast to both CTAs) frees the stage;
+//   warps 0-3          epilogue: tcgen05.ld of the 128 x 256 FP32 accumulator (each
 //                      warp its 32 TMEM lanes), + lambda on the diagonal, to global.
-// The upper triangle is mirrored afterwards. Every mbarrier wait is bounded; on
-// timeout the CTA records an error, stops issuing, drains its own MMAs (bounded)
-// and releases its tensor memory.
+// The upper triangle is mirrored afterwards. Every mbarrier wait is bounded; on a
+// timeout the CTA records an error and stops issuing; both CTAs meet at a cluster
+// barrier before either releases its shared memory.
 #include <cuda.h>
 
 #include "rs_kernels.cuh"
@@ -20,11 +26,15 @@ namespace rs {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 128, kBK = 32;  // tile; kBK fp32 = 128 bytes
-constexpr int kStages = 6;
-constexpr int kStageBytes = (kBM + kBN) * kBK * 4;  // 32 KB
-constexpr uint32_t kTmemCols = 128;
-constexpr long long kSpinLimit = 1LL << 26;
+constexpr int kBM = 128;                            // rows of a CTA's tile
+constexpr int kBN = 256;                            // columns (the pair's B block)
+constexpr int kBK = 32;                             // K step: 32 fp32 = one 128-byte row
+constexpr int kStages = 4;
+constexpr int kABytes = kBM * kBK * 4;              // 16 KB
+constexpr int kBHalfBytes = (kBN / 2) * kBK * 4;    // 16 KB, one CTA's half of B
+constexpr int kStageBytes = kABytes + 2 * kBHalfBytes;  // 48 KB
+constexpr uint32_t kTmemCols = 256;
+constexpr uint64_t kWaitNs = 4000000000ull;  // 4 s bound of every wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -38,20 +48,32 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                "r"(bytes)
                : "memory");
 }
-// bounded wait on phase `parity`; returns false on timeout
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// wait on phase `parity` (acquire at cluster scope: the peer's multicast bytes and
+// commits arrive on these barriers), bounded by kWaitNs of the global timer; false
+// on timeout
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < kSpinLimit; ++it) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((it & 255) == 255) {
+      const uint64_t t = now_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > kWaitNs) return false;
+    }
   }
-  return false;
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
@@ -60,6 +82,16 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
       "%4}], [%2];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+// the same box written at the same offset into the shared memory of every CTA of
+// `mask`, completing on the mbarrier at the same offset in each
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                               int x, int y, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::"
+      "cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
       : "memory");
 }
 
@@ -75,7 +107,7 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor: kind::tf32, D f32, A/B tf32, both K-major, M = 128, N = 128
+// instruction descriptor: kind::tf32, D f32, A/B tf32, both K-major, M = 128, N = 256
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kBN >> 3) << 17) |
                             ((uint32_t)(kBM >> 4) << 24);
 
@@ -86,11 +118,24 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b
       "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
       : "memory");
 }
+// arrive once on `bar` when the MMAs issued so far retire
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
       : "memory");
+}
+// the same on the barrier at this offset in every CTA of `mask`
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+      "[%0], %1;" ::"r"(smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
 }
 
 }  // namespace
@@ -100,30 +145,34 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
                                                    float* __restrict__ A, int64_t lda,
                                                    int32_t* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte alignment for the swizzled stages
+  // 1024-byte alignment for the swizzled stages (the same offset in both CTAs)
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  uint32_t crank;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
+  constexpr uint16_t kBoth = 0x3;
 
-  // tile (ti >= tj) of the lower triangle
-  int64_t t = blockIdx.x, ti = 0;
-  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-  const int64_t tj = t - ti * (ti + 1) / 2;
-  const int row0 = (int)(ti * kBM), col0 = (int)(tj * kBN);
+  // cluster p: row blocks 2a + crank, column block tj <= a
+  const int64_t p = blockIdx.x / 2;
+  int64_t a = 0;
+  while ((a + 1) * (a + 2) / 2 <= p) ++a;
+  const int64_t tj = p - a * (a + 1) / 2;
+  const int row0 = (int)((2 * a + (int64_t)crank) * kBM), col0 = (int)(tj * kBN);
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 1);
+      mbar_init(&empty_bar[s], 2);  // released by the MMAs of both CTAs
     }
     mbar_init(&done_bar, 1);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (wid == 0) {  // tensor memory for the 128 x 128 accumulator
+  if (wid == 0) {  // tensor memory for the 128 x 256 accumulator
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&s_tmem)),
                  "r"(kTmemCols)
@@ -132,36 +181,47 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  cluster_sync();  // the peer's barriers are initialised before anything reaches them
   const uint32_t tmem = s_tmem;
 
   if (wid == 0 && lane == 0) {
-    // producer
-    for (int64_t kb = 0; kb < nk; ++kb) {
+    // producer: the own A box, and the own half of the shared B block into both CTAs
+    int64_t kb = 0;
+    for (; kb < nk; ++kb) {
       const int s = (int)(kb % kStages);
       const uint32_t ph = (uint32_t)((kb / kStages) & 1);
       if (!mbar_wait(&empty_bar[s], ph ^ 1)) { s_abort = 1; atomicExch(err, 1); break; }
       if (*(volatile int*)&s_abort) break;
       unsigned char* st = base + s * kStageBytes;
-      mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
+      mbar_arrive_expect_tx(&full_bar[s], kStageBytes);  // own A + both halves of B
       tma_load_2d(st, &tmap, &full_bar[s], (int)(kb * kBK), row0);
-      tma_load_2d(st + kBM * kBK * 4, &tmap, &full_bar[s], (int)(kb * kBK), col0);
+      tma_load_2d_mc(st + kABytes + crank * kBHalfBytes, &tmap, &full_bar[s], (int)(kb * kBK),
+                     col0 + (int)crank * (kBN / 2), kBoth);
+    }
+    // tail: every stage filled here has been released by both CTAs' MMAs, so no
+    // commit of the peer is still on its way to these barriers
+    if (kb == nk) {
+      for (int64_t t = nk; t < nk + kStages; ++t) {
+        const int s = (int)(t % kStages);
+        const uint32_t ph = (uint32_t)((t / kStages) & 1);
+        if (!mbar_wait(&empty_bar[s], ph ^ 1)) { s_abort = 1; atomicExch(err, 1); break; }
+      }
     }
   } else if (wid == 1 && lane == 0) {
     // MMA issuer
-    int64_t kb = 0;
-    for (; kb < nk; ++kb) {
+    for (int64_t kb = 0; kb < nk; ++kb) {
       const int s = (int)(kb % kStages);
       const uint32_t ph = (uint32_t)((kb / kStages) & 1);
       if (!mbar_wait(&full_bar[s], ph)) { s_abort = 1; atomicExch(err, 1); break; }
       if (*(volatile int*)&s_abort) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sa = smem_u32(base + s * kStageBytes);
-      const uint32_t sb = sa + kBM * kBK * 4;
+      const uint32_t sb = sa + kABytes;
 #pragma unroll
       for (int ks = 0; ks < kBK / 8; ++ks)  // K = 8 tf32 = 32 bytes per MMA
         mma_tf32(tmem, umma_desc_sw128(sa + ks * 32), umma_desc_sw128(sb + ks * 32),
                  (kb > 0 || ks > 0) ? 1u : 0u);
-      mma_commit(&empty_bar[s]);
+      mma_commit_mc(&empty_bar[s], kBoth);  // the stage is free in both CTAs' rings
     }
     mma_commit(&done_bar);  // arrives once every MMA issued above has retired
   }
@@ -173,6 +233,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
   if (ok && !*(volatile int*)&s_abort) {
     const int64_t r = row0 + wid * 32 + lane;
     for (int c0 = 0; c0 < kBN; c0 += 16) {
+      if (col0 + c0 > row0 + kBM - 1) break;  // above every row of the tile (uniform)
       uint32_t v[16];
       const uint32_t taddr = tmem + ((uint32_t)(wid * 32) << 16) + (uint32_t)c0;
       asm volatile(
@@ -202,6 +263,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(kTmemCols)
                  : "memory");
+  cluster_sync();  // neither CTA leaves while the other may still reach its shared memory
 }
 
 // Xt[i * ldk + k] = X[k * d + i] (zero for k >= n): 32 x 32 tiles through shared memory
@@ -253,19 +315,31 @@ cudaError_t launch_gram_tc(cudaStream_t st, const float* X, int64_t n, int64_t d
   CUtensorMap map;
   const cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)d};
   const cuuint64_t strides[1] = {(cuuint64_t)ldk * 4};
-  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};  // also one half of B
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, Xt_ws, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  const int64_t T = (d + kBM - 1) / kBM;
-  const int64_t tiles = T * (T + 1) / 2;
+  const int64_t T = (d + kBM - 1) / kBM;  // row blocks
+  const int64_t Tp = (T + 1) / 2;         // row-block pairs
+  const int64_t clusters = Tp * (Tp + 1) / 2;
   const size_t smem = (size_t)kStages * kStageBytes + 1024;
   e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gram_tc<<<(unsigned)tiles, 128, smem, st>>>(map, d, ldk / kBK, lambda, A, lda, err);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * clusters));
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_gram_tc, map, d, ldk / kBK, lambda, A, lda, err);
 }
 
 }  // namespace rs

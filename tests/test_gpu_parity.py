@@ -385,7 +385,7 @@ def test_true_residual_fp32_x(rs, d):
     assert abs(got - ref) <= 1e-6 * ref
 
 
-@pytest.mark.parametrize("n,d", [(2000, 300), (1000, 256), (5000, 130)])
+@pytest.mark.parametrize("n,d", [(2000, 300), (1000, 256), (5000, 130), (1001, 500)])
 def test_gram_tensor_cores(rs, n, d):
     """X^T X + lambda I formed by the tensor-core kernel (TF32 inputs, FP32
     accumulation): M = S^T A S with S = I_C, tau = m, equals the FP64 A[C, C] within
