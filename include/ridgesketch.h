@@ -181,8 +181,14 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
 rs_status rs_solve(rs_ctx* ctx, double tol, int64_t max_iters, double* w_out,
                    int32_t w_on_device, double* hist_out, int64_t* iters_out);
 
-/* Free every resource of the context. NULL is accepted. */
+/* Free every resource of the context. NULL is accepted. The device memory of the
+ * contexts comes from one stream-ordered pool per device that keeps freed blocks
+ * for the next context (no cudaMalloc / cudaFree per context once warm). */
 void rs_destroy(rs_ctx* ctx);
+
+/* Return the pool's unused device memory on `device` to the driver (memory of live
+ * contexts stays). RS_EINVAL for a device ordinal outside [0, 64). */
+rs_status rs_trim_memory(int32_t device);
 
 /* Message of the last failure on ctx (ctx = NULL: last failure without a context).
  * The string is owned by the library and valid until the next call on ctx. */

@@ -69,6 +69,7 @@ _SIGS = {
                          ctypes.POINTER(_P)]),
     "rs_solve": (_I32, [_P, _D, _I64, _P, _I32, _P, ctypes.POINTER(_I64)]),
     "rs_destroy": (None, [_P]),
+    "rs_trim_memory": (_I32, [_I32]),
     "rs_last_error": (ctypes.c_char_p, [_P]),
     "rs_get_dims": (_I32, [_P] + [ctypes.POINTER(_I64)] * 5),
     "rs_iter_plan": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
@@ -140,6 +141,14 @@ def _buf(x, dtype):
         return t.data_ptr(), int(t.is_cuda), t
     a = np.ascontiguousarray(x, dtype=dtype)
     return a.ctypes.data, 0, a
+
+
+def trim_memory(device: int = 0) -> None:
+    """Return the unused device memory the library's pool keeps after destroyed
+    contexts (rs_trim_memory)."""
+    st = lib().rs_trim_memory(int(device))
+    if st != RS_OK:
+        raise RSError(st, lib().rs_last_error(None).decode())
 
 
 class CSR:

@@ -182,11 +182,59 @@ struct rs_ctx {
 
 namespace {
 
+// ---- device memory of the contexts ----
+// One stream-ordered pool per device that keeps the blocks its contexts free
+// (release threshold: unlimited), so creating and destroying a context costs no
+// cudaMalloc / cudaFree (and no device-wide synchronisation) once the pool holds
+// the sizes; rs_trim_memory returns the unused blocks to the driver. Every access
+// to a context's memory is ordered on the context's stream.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+
+cudaError_t ctx_pool(int dev, cudaMemPool_t* out) {
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (g_pool[dev] == nullptr) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    g_pool[dev] = pool;
+  }
+  *out = g_pool[dev];
+  return cudaSuccess;
+}
+
+cudaError_t pmalloc(rs_ctx* c, void** p, size_t bytes) {
+  cudaMemPool_t pool = nullptr;
+  const cudaError_t e = ctx_pool(c->device, &pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(p, bytes, pool, c->stream);
+}
+void pfree(rs_ctx* c, void* p) {
+  if (p) cudaFreeAsync(p, c->stream);
+}
+// a blocking copy ordered after the work already on the context's stream
+cudaError_t copy_sync(rs_ctx* c, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e;
+}
+
 template <typename T>
 rs_status dalloc(rs_ctx* c, T** p, size_t n) {
   *p = nullptr;
   if (n == 0) n = 1;
-  CKC(c, cudaMalloc((void**)p, n * sizeof(T)));
+  CKC(c, pmalloc(c, (void**)p, n * sizeof(T)));
   return RS_OK;
 }
 
@@ -202,9 +250,11 @@ void free_all(rs_ctx* c) {
                   c->mf_crow, c->mf_cptr, c->mf_ebuck, c->mf_eval, c->mf_v, c->mf_pu, c->mf_pud,
                   c->mf_z, c->lp_w, c->lp_raw, c->lp_zstat, c->lp_stats, c->lp_score, c->lp_feat,
                   c->lp_last};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
-  if (c->ctrl_h) cudaFreeHost(c->ctrl_h);
+  for (void* p : ptrs) pfree(c, p);
+  if (c->ctrl_h) {  // the stream may still read the pinned control block
+    cudaStreamSynchronize(c->stream);
+    cudaFreeHost(c->ctrl_h);
+  }
   if (c->scal_h) cudaFreeHost(c->scal_h);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -642,9 +692,9 @@ rs_status build_graph(rs_ctx* c, bool with_refresh) {
 rs_status ensure_schedule(rs_ctx* c, int64_t K) {
   if (K <= c->sched_len && K + 1 <= c->hist_len) return RS_OK;
   const int64_t L = std::max<int64_t>(K, 1024);
-  if (c->gam) cudaFree(c->gam);
-  if (c->bet) cudaFree(c->bet);
-  if (c->hist) cudaFree(c->hist);
+  pfree(c, c->gam);
+  pfree(c, c->bet);
+  pfree(c, c->hist);
   c->gam = c->bet = c->hist = nullptr;
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
@@ -680,8 +730,8 @@ rs_status ensure_schedule(rs_ctx* c, int64_t K) {
       if (bk >= mo.beta_switch) eta_k = 1.0;
     }
   }
-  CKC(c, cudaMemcpy(c->gam, g.data(), L * sizeof(double), cudaMemcpyHostToDevice));
-  CKC(c, cudaMemcpy(c->bet, bt.data(), L * sizeof(double), cudaMemcpyHostToDevice));
+  CKC(c, copy_sync(c, c->gam, g.data(), L * sizeof(double), cudaMemcpyHostToDevice));
+  CKC(c, copy_sync(c, c->bet, bt.data(), L * sizeof(double), cudaMemcpyHostToDevice));
   c->sched_len = L;
   c->hist_len = L + 1;
   return RS_OK;
@@ -748,7 +798,7 @@ rs_status sparse_setup_t(rs_ctx* c, const rs_matrix* X, const double* y, int32_t
   rs_status s;
   if ((s = dalloc(c, &c->sx_rowptr, n + 1)) != RS_OK) return s;
   if ((s = dalloc(c, &c->sx_colidx, nnz)) != RS_OK) return s;
-  CKC(c, cudaMalloc(&c->sx_val, std::max<int64_t>(nnz, 1) * sizeof(VT)));
+  CKC(c, pmalloc(c, (void**)&c->sx_val, std::max<int64_t>(nnz, 1) * sizeof(VT)));
   CKC(c, cudaMemcpyAsync(c->sx_rowptr, X->rowptr, (n + 1) * sizeof(int64_t), kind, st));
   CKC(c, cudaMemcpyAsync(c->sx_colidx, X->colidx, nnz * sizeof(int32_t), kind, st));
   CKC(c, cudaMemcpyAsync(c->sx_val, X->val, nnz * sizeof(VT), kind, st));
@@ -763,10 +813,10 @@ rs_status sparse_setup_t(rs_ctx* c, const rs_matrix* X, const double* y, int32_t
   int32_t* table = nullptr;
   int64_t* colcnt = nullptr;
   if ((s = dalloc(c, &table, (size_t)nb * d)) != RS_OK) return s;
-  if ((s = dalloc(c, &colcnt, d)) != RS_OK) { cudaFree(table); return s; }
+  if ((s = dalloc(c, &colcnt, d)) != RS_OK) { pfree(c, table); return s; }
   if ((s = dalloc(c, &c->sx_colptr, d + 1)) != RS_OK) return s;
   if ((s = dalloc(c, &c->sx_rowidx, nnz)) != RS_OK) return s;
-  CKC(c, cudaMalloc(&c->sx_cval, std::max<int64_t>(nnz, 1) * sizeof(VT)));
+  CKC(c, pmalloc(c, (void**)&c->sx_cval, std::max<int64_t>(nnz, 1) * sizeof(VT)));
   cudaError_t e = build_csc<VT>(st, c->sx_rowptr, n, c->sx_colidx, static_cast<const VT*>(c->sx_val),
                                 nnz, d, table, nb, colcnt, c->sx_colptr, c->sx_rowidx,
                                 static_cast<VT*>(c->sx_cval));
@@ -774,8 +824,8 @@ rs_status sparse_setup_t(rs_ctx* c, const rs_matrix* X, const double* y, int32_t
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(colptr.data(), c->sx_colptr, (d + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(table);
-  cudaFree(colcnt);
+  pfree(c, table);
+  pfree(c, colcnt);
   CKC(c, e);
   // pieces of at most kPiece entries per column, in column order
   std::vector<int32_t> pcol, cpiece(d + 1);
@@ -793,10 +843,10 @@ rs_status sparse_setup_t(rs_ctx* c, const rs_matrix* X, const double* y, int32_t
   if ((s = dalloc(c, &c->sx_pstart, pstart.size())) != RS_OK) return s;
   if ((s = dalloc(c, &c->sx_cpiece, d + 1)) != RS_OK) return s;
   if (!pcol.empty()) {
-    CKC(c, cudaMemcpy(c->sx_pcol, pcol.data(), pcol.size() * 4, cudaMemcpyHostToDevice));
-    CKC(c, cudaMemcpy(c->sx_pstart, pstart.data(), pstart.size() * 8, cudaMemcpyHostToDevice));
+    CKC(c, copy_sync(c, c->sx_pcol, pcol.data(), pcol.size() * 4, cudaMemcpyHostToDevice));
+    CKC(c, copy_sync(c, c->sx_pstart, pstart.data(), pstart.size() * 8, cudaMemcpyHostToDevice));
   }
-  CKC(c, cudaMemcpy(c->sx_cpiece, cpiece.data(), (d + 1) * 4, cudaMemcpyHostToDevice));
+  CKC(c, copy_sync(c, c->sx_cpiece, cpiece.data(), (d + 1) * 4, cudaMemcpyHostToDevice));
   // y, b = X^T y (FP64)
   if ((s = dalloc(c, &c->y, n)) != RS_OK) return s;
   CKC(c, cudaMemcpyAsync(c->y, y, n * sizeof(double), y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
@@ -1007,7 +1057,7 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   // X, y
   const size_t xel = X->dtype == RS_F32 ? 4 : 8;
   const size_t xbytes = (size_t)X->n * X->d * xel;
-  TRYC(cudaMalloc(&c->X, xbytes));
+  TRYC(pmalloc(c, (void**)&c->X, xbytes));
   TRYC(cudaMemcpyAsync(c->X, X->val, xbytes, X->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   TRY(dalloc(c, &c->y, c->n));
   TRYC(cudaMemcpyAsync(c->y, y, c->n * sizeof(double), y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
@@ -1017,7 +1067,7 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   TRY(dalloc(c, &c->xt_part, std::max<size_t>(xt_part_elems(c->n, c->d),
                                                (size_t)xtx_df_blocks() * c->d)));
   // A and b (eqs. (2)-(4))
-  TRYC(cudaMalloc(&c->A, (size_t)m * c->ld * c->elem()));
+  TRYC(pmalloc(c, (void**)&c->A, (size_t)m * c->ld * c->elem()));
   TRYC(cudaMemsetAsync(c->A, 0, (size_t)m * c->ld * c->elem(), st));
   TRY(dalloc(c, &c->b, m));
   TRYC(cudaEventRecord(c->ev0, st));
@@ -1027,14 +1077,12 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     if (c->mixed() && !dual && o.setup_tc) {
       // X^T X on the tensor cores through a transposed, padded copy of X
       float* Xt = nullptr;
-      TRYC(cudaMalloc(&Xt, gram_tc_ws_floats(c->n, c->d) * sizeof(float)));
+      TRYC(pmalloc(c, (void**)&Xt, gram_tc_ws_floats(c->n, c->d) * sizeof(float)));
       cudaError_t e1 = launch_gram_tc(st, Xf, c->n, c->d, lambda, static_cast<float*>(c->A), c->ld,
                                       Xt, c->err_flag);
       if (e1 == cudaSuccess) e1 = launch_mirror_lower<float>(st, static_cast<float*>(c->A), c->d, c->ld);
-      cudaError_t e2 = cudaStreamSynchronize(st);
-      cudaFree(Xt);
+      pfree(c, Xt);  // in stream order, after the product
       TRYC(e1);
-      TRYC(e2);
     } else if (c->mixed()) TRYC((launch_form_A<float, float>(st, Xf, c->n, c->d, dual, lambda, static_cast<float*>(c->A), c->ld)));
     else TRYC((launch_form_A<float, double>(st, Xf, c->n, c->d, dual, lambda, static_cast<double*>(c->A), c->ld)));
     if (!dual && c->mixed()) TRYC(launch_xt_v_pairs(st, Xf, c->n, c->d, c->y, c->b, c->xt_part));
@@ -1063,7 +1111,7 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     const size_t nsl = (size_t)c->nslots;
     c->pld = round_up(c->tau, 4);
     c->p_slot = c->tau * c->pld;
-    TRYC(cudaMalloc(&c->Pm, nsl * c->p_slot * fel));
+    TRYC(pmalloc(c, (void**)&c->Pm, nsl * c->p_slot * fel));
     TRY(dalloc(c, &c->mf_bsum, nsl * c->mf_nrb * 2));
     TRY(dalloc(c, &c->mf_boffs, nsl * c->mf_nrb * 2));
     TRY(dalloc(c, &c->mf_tot, nsl * 2));
@@ -1071,16 +1119,16 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     TRY(dalloc(c, &c->mf_crow, nsl * c->mf_rcap));
     TRY(dalloc(c, &c->mf_cptr, nsl * (c->mf_rcap + 1)));
     TRY(dalloc(c, &c->mf_ebuck, nsl * c->mf_ecap));
-    TRYC(cudaMalloc(&c->mf_eval, nsl * c->mf_ecap * c->elem()));
-    TRYC(cudaMalloc(&c->mf_v, (size_t)c->n * c->elem()));
+    TRYC(pmalloc(c, (void**)&c->mf_eval, nsl * c->mf_ecap * c->elem()));
+    TRYC(pmalloc(c, (void**)&c->mf_v, (size_t)c->n * c->elem()));
     TRYC(cudaMemsetAsync(c->mf_v, 0, (size_t)c->n * c->elem(), st));
-    TRYC(cudaMalloc(&c->mf_pu, std::max<int64_t>(c->sx_npieces, 1) * c->elem()));
+    TRYC(pmalloc(c, (void**)&c->mf_pu, std::max<int64_t>(c->sx_npieces, 1) * c->elem()));
   }
   if (t_batch_member && !c->sparse) {
     const size_t fel = c->f64_factor() ? 8 : 4;
     c->pld = round_up(c->tau, 4);
     c->p_slot = c->tau * c->pld;
-    TRYC(cudaMalloc(&c->Pm, (size_t)c->nslots * c->p_slot * fel));
+    TRYC(pmalloc(c, (void**)&c->Pm, (size_t)c->nslots * c->p_slot * fel));
     // FP32 M^+ by sweeps (every phase-1 path of a member writes the FP32 M they read)
     c->sweep_p = c->mixed() && !c->f64_factor() && c->tau <= kSweepMaxTau;
     if (c->sweep_p) TRY(dalloc(c, &c->Mf, (size_t)c->nslots * c->tau * c->tau));
@@ -1096,7 +1144,7 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
       const size_t fel = c->f64_factor() ? 8 : 4;
       c->pld = round_up(c->tau, 4);
       c->p_slot = c->tau * c->pld;
-      TRYC(cudaMalloc(&c->Pm, (size_t)c->nslots * c->p_slot * fel));
+      TRYC(pmalloc(c, (void**)&c->Pm, (size_t)c->nslots * c->p_slot * fel));
       const size_t nwords = (size_t)2 * c->wide.nblk * (c->tau + 1) * 2;
       TRY(dalloc(c, &c->xpart, nwords));
       TRY(dalloc(c, &c->xflags, 1));
@@ -1127,16 +1175,16 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     c->l_slot = c->tau * c->tau;
     const size_t nsl = (size_t)c->nslots;
     TRY(dalloc(c, &c->M, nsl * c->m_slot));
-    TRYC(cudaMalloc(&c->Linv, nsl * c->l_slot * fel));
+    TRYC(pmalloc(c, (void**)&c->Linv, nsl * c->l_slot * fel));
     const size_t need_smem = (size_t)factor_ws_elems(c->tau) * fel + 4096;
     if (need_smem > 220 * 1024 || c->tau > 4096)
-      TRYC(cudaMalloc(&c->fws, nsl * factor_ws_elems(c->tau) * fel));
+      TRYC(pmalloc(c, (void**)&c->fws, nsl * factor_ws_elems(c->tau) * fel));
     if (c->sa_slot > 0) {
-      TRYC(cudaMalloc(&c->SA, nsl * c->sa_slot * c->elem()));
+      TRYC(pmalloc(c, (void**)&c->SA, nsl * c->sa_slot * c->elem()));
       TRYC(cudaMemsetAsync(c->SA, 0, nsl * c->sa_slot * c->elem(), st));
     }
     if (sketch == RS_GAUSSIAN) {
-      TRYC(cudaMalloc(&c->ST, nsl * c->sa_slot * c->elem()));
+      TRYC(pmalloc(c, (void**)&c->ST, nsl * c->sa_slot * c->elem()));
       TRYC(cudaMemsetAsync(c->ST, 0, nsl * c->sa_slot * c->elem(), st));
     }
   }
@@ -1145,7 +1193,15 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     c->boff_stride = round_up(c->tau + 1, 4);  // 16-byte aligned slots (bulk copies)
     TRY(dalloc(c, &c->perm, (size_t)c->perm_stride * c->nslots));
     TRY(dalloc(c, &c->boff, (size_t)c->boff_stride * c->nslots));
-    if (sketch != RS_SRHT) TRY(dalloc(c, &c->inv, (size_t)c->ld * c->nslots));
+    // pool memory holds whatever a previous context left: the plans start as valid
+    // (all-zero) indices, so that no read of a slot that was not drawn yet can
+    // leave its buffers
+    TRYC(cudaMemsetAsync(c->perm, 0, (size_t)c->perm_stride * c->nslots * sizeof(int32_t), st));
+    TRYC(cudaMemsetAsync(c->boff, 0, (size_t)c->boff_stride * c->nslots * sizeof(int32_t), st));
+    if (sketch != RS_SRHT) {
+      TRY(dalloc(c, &c->inv, (size_t)c->ld * c->nslots));
+      TRYC(cudaMemsetAsync(c->inv, 0, (size_t)c->ld * c->nslots * sizeof(int32_t), st));
+    }
   }
   c->npartials = std::max<int64_t>(update_blocks(m), 256);
   TRY(dalloc(c, &c->partials, c->npartials));
@@ -1177,6 +1233,22 @@ void rs_destroy(rs_ctx* ctx) {
     free_all(ctx);
   }
   delete ctx;
+}
+
+rs_status rs_trim_memory(int32_t device) {
+  if (device < 0 || device >= 64) return RS_EINVAL;
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    pool = g_pool[device];
+  }
+  if (pool == nullptr) return RS_OK;
+  DeviceGuard dg(device);
+  if (cudaMemPoolTrimTo(pool, 0) != cudaSuccess) {
+    set_global_error("rs_trim_memory: cudaMemPoolTrimTo failed");
+    return RS_ECUDA;
+  }
+  return RS_OK;
 }
 
 rs_status rs_get_dims(const rs_ctx* c, int64_t* m, int64_t* tau, int64_t* s, int64_t* k_sum,
@@ -1224,7 +1296,7 @@ rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int3
     CKC(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     iters = h->k;
     int32_t gen_err = 0;
-    CKC(c, cudaMemcpy(&gen_err, c->err_flag, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CKC(c, copy_sync(c, &gen_err, c->err_flag, sizeof(int32_t), cudaMemcpyDeviceToHost));
     if (gen_err) FAILC(c, RS_ECUDA, "sketch generation: sample threshold search failed");
     if (h->status == RS_ETIMEOUT) {
       FAILC(c, RS_ETIMEOUT, "rs_solve: a bounded device-side wait of the iteration kernel gave up");
@@ -1235,9 +1307,9 @@ rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int3
       double last = 0.0;
       if (c->mixed()) {  // final FP64 residual check through X
         if ((s = true_rel(c, c->w, &last)) != RS_OK) return s;
-        CKC(c, cudaMemcpy(c->hist + iters, &last, sizeof(double), cudaMemcpyHostToDevice));
+        CKC(c, copy_sync(c, c->hist + iters, &last, sizeof(double), cudaMemcpyHostToDevice));
       } else {
-        CKC(c, cudaMemcpy(&last, c->hist + iters, sizeof(double), cudaMemcpyDeviceToHost));
+        CKC(c, copy_sync(c, &last, c->hist + iters, sizeof(double), cudaMemcpyDeviceToHost));
       }
       if (!(last <= tol)) result = RS_ENOTCONV;
     }
@@ -1268,7 +1340,7 @@ rs_status rs_dump_sketch(rs_ctx* c, int64_t k, int32_t* idx, int8_t* sign, int32
   CKC(c, cudaMemcpyAsync(boff.data(), c->boff, boff.size() * 4, cudaMemcpyDeviceToHost, c->stream));
   CKC(c, cudaStreamSynchronize(c->stream));
   int32_t gen_err = 0;
-  CKC(c, cudaMemcpy(&gen_err, c->err_flag, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  CKC(c, copy_sync(c, &gen_err, c->err_flag, sizeof(int32_t), cudaMemcpyDeviceToHost));
   if (gen_err) FAILC(c, RS_ECUDA, "sketch generation: sample threshold search failed");
   auto row = [](int32_t e) { return e & 0x7FFFFFFF; };
   switch (c->sketch) {
@@ -1407,7 +1479,7 @@ rs_status rs_step(rs_ctx* c, int64_t n_iters, double* hist_out) {
   if (h->status == RS_ETIMEOUT) FAILC(c, RS_ETIMEOUT, "rs_step: a bounded device-side wait gave up");
   if (h->status == RS_ENUMERIC) FAILC(c, RS_ENUMERIC, "rs_step: NaN or Inf in the residual");
   if (hist_out)
-    CKC(c, cudaMemcpy(hist_out, c->hist + k0 + 1, n_iters * sizeof(double), cudaMemcpyDeviceToHost));
+    CKC(c, copy_sync(c, hist_out, c->hist + k0 + 1, n_iters * sizeof(double), cudaMemcpyDeviceToHost));
   // leave the context ready for further steps or probes
   h->stop = 0;
   h->max_iters = INT64_MAX;
@@ -1512,7 +1584,13 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
       } else {
         s = timed("gen", [&]() -> rs_status {
           CKC(c, launch_chunk_begin(c->stream, c->ctrl));
-          return enqueue_gen(c, -1, ns);
+          const rs_status r = enqueue_gen(c, -1, ns);
+          if (r != RS_OK) return r;
+          // the row -> bucket map of the new plans, as in the chunk's phase 1
+          if (c->inv != nullptr)
+            CKC(c, launch_inv_map(c->stream, c->ctrl, 0, ns, plan, c->m, c->tau,
+                                  c->sketch == RS_COUNT ? 1 : 0, c->inv, c->ld));
+          return RS_OK;
         });
         if (s != RS_OK) break;
         const bool has_sa = c->sketch == RS_COUNT || c->sketch == RS_SUBCOUNT || c->use_wide;
@@ -1662,13 +1740,13 @@ rs_status rs_set_proposal(rs_ctx* c, const uint16_t* w_bf16, double eps) {
   cudaStream_t st = c->stream;
   const size_t m = (size_t)c->m;
   if (!c->lp_w) {
-    CKC(c, cudaMalloc(&c->lp_w, kMlpParams * sizeof(uint16_t)));
-    CKC(c, cudaMalloc(&c->lp_raw, 2 * m * sizeof(float)));
-    CKC(c, cudaMalloc(&c->lp_zstat, 2 * m * sizeof(float)));
-    CKC(c, cudaMalloc(&c->lp_stats, 8 * sizeof(double)));
-    CKC(c, cudaMalloc(&c->lp_score, m * sizeof(float)));
-    CKC(c, cudaMalloc(&c->lp_feat, m * 4 * sizeof(float)));
-    CKC(c, cudaMalloc(&c->lp_last, m * sizeof(int32_t)));
+    CKC(c, pmalloc(c, (void**)&c->lp_w, kMlpParams * sizeof(uint16_t)));
+    CKC(c, pmalloc(c, (void**)&c->lp_raw, 2 * m * sizeof(float)));
+    CKC(c, pmalloc(c, (void**)&c->lp_zstat, 2 * m * sizeof(float)));
+    CKC(c, pmalloc(c, (void**)&c->lp_stats, 8 * sizeof(double)));
+    CKC(c, pmalloc(c, (void**)&c->lp_score, m * sizeof(float)));
+    CKC(c, pmalloc(c, (void**)&c->lp_feat, m * 4 * sizeof(float)));
+    CKC(c, pmalloc(c, (void**)&c->lp_last, m * sizeof(int32_t)));
     CKC(c, cudaMemsetAsync(c->lp_last, 0xFF, m * sizeof(int32_t), st));
     if (c->mixed())
       CKC(c, launch_lp_static<float>(st, static_cast<const float*>(c->A), c->ld, c->m, c->lp_raw,
@@ -2329,9 +2407,9 @@ rs_status rs_solve_batch(rs_batch* b, double tol, int64_t max_iters, double* con
     BKC(rs::launch_batch_mixed_aux(b->stream, 2, static_cast<const rs::BatchRefM*>(b->refs), np,
                                    batch_pairs(b), b->tol));
   for (int p = 0; p < b->P; ++p) {
-    const rs_ctx* c = b->mem[p];
+    rs_ctx* c = b->mem[p];
     int32_t gen_err = 0;
-    BKC(cudaMemcpy(&gen_err, c->err_flag, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    BKC(copy_sync(c, &gen_err, c->err_flag, sizeof(int32_t), cudaMemcpyDeviceToHost));
     if (gen_err) { b->err = "sketch generation: sample threshold search failed"; return RS_ECUDA; }
     if (!W_out || !W_out[p]) continue;
     const size_t v = (size_t)b->nrhs * c->m;

@@ -52,6 +52,9 @@ def test_null_arguments_are_rejected_without_a_device(L):
     assert st == rs.RS_EINVAL
     assert L.rs_iter_plan(None, None, None) == rs.RS_EINVAL
     L.rs_destroy(None)
+    # no pool exists before the first context: nothing to trim, no CUDA call
+    assert L.rs_trim_memory(-1) == rs.RS_EINVAL and L.rs_trim_memory(64) == rs.RS_EINVAL
+    assert L.rs_trim_memory(0) == rs.RS_OK
 
 
 def test_bad_enums_rejected(L):

@@ -424,3 +424,28 @@ def test_mixed_refresh_beyond_4096_columns(rs):
     # float-pair products carry about 48 bits: the residual relative to ||b|| to ~1e-14
     assert abs(got - ref) <= 1e-12
     assert ref <= 1e-6 * (1 + 1e-6)
+
+
+def test_pool_reuse_across_contexts(rs):
+    """Contexts created and destroyed back to back on one stream reuse the blocks of
+    the library's memory pool: every repetition gives bit-identical iterates (the
+    solves are deterministic), and the pool's unused memory can be trimmed."""
+    from synth import geometric_sigma, spectrum_problem
+
+    X, y, _ = spectrum_problem(2000, 300, geometric_sigma(300, 1e-1), seed=21, noise=0.01,
+                               dtype=np.float32)
+    first = {}
+    for rep in range(3):
+        for sketch, tau, prec in (("count", 32, "mixed"), ("subsample", 48, "fp64"),
+                                  ("count", 64, "mixed")):
+            with rs.Solver(X, y, 0.1, sketch=sketch, tau=tau, momentum="heuristic", seed=3,
+                           precision=prec) as s:
+                w, hist, iters, conv = s.solve(tol=1e-8, max_iters=400)
+            key = (sketch, tau, prec)
+            if rep == 0:
+                first[key] = (w.copy(), np.array(hist).copy(), iters)
+            else:
+                w0, h0, i0 = first[key]
+                assert iters == i0 and np.array_equal(w, w0) and np.array_equal(hist, h0), key
+        if rep == 1:
+            rs.trim_memory(0)
