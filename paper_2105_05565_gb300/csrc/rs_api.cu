@@ -1287,6 +1287,7 @@ rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int3
     h->max_iters = max_iters;
     h->r0 = c->r0;
     h->tol = tol;
+    h->checked_k = -1;
     if ((s = write_ctrl(c)) != RS_OK) return s;
     CKC(c, cudaEventRecord(c->ev0, st));
     const int64_t max_chunks = (max_iters + c->chunk - 1) / c->chunk + 2;
@@ -1305,7 +1306,10 @@ rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int3
       c->err = "rs_solve: NaN or Inf in the residual";
     } else {
       double last = 0.0;
-      if (c->mixed()) {  // final FP64 residual check through X
+      if (c->mixed() && h->checked_k == iters) {
+        // the last refresh already took the FP64 true residual of this iterate
+        CKC(c, copy_sync(c, &last, c->hist + iters, sizeof(double), cudaMemcpyDeviceToHost));
+      } else if (c->mixed()) {  // final FP64 residual check through X
         if ((s = true_rel(c, c->w, &last)) != RS_OK) return s;
         CKC(c, copy_sync(c, c->hist + iters, &last, sizeof(double), cudaMemcpyHostToDevice));
       } else {

@@ -61,6 +61,7 @@ struct Ctrl {
   int32_t pad;
   double r0;          // ||r^0|| = ||b||
   double tol;
+  int64_t checked_k;  // last k whose FP64 true residual (a refresh) is hist[k]; -1: none
 };
 
 __device__ __forceinline__ bool halted(const Ctrl* c) {

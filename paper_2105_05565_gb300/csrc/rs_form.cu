@@ -660,6 +660,7 @@ __global__ void __launch_bounds__(256) k_refresh_finish(Ctrl* __restrict__ ctrl,
     if (mode == 1) {
       const int64_t k = ctrl->k;
       hist[k] = rel;
+      ctrl->checked_k = k;
       if (!isfinite(rel)) {
         ctrl->status = 4;
         ctrl->stop = 1;

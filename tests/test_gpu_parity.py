@@ -449,3 +449,20 @@ def test_pool_reuse_across_contexts(rs):
                 assert iters == i0 and np.array_equal(w, w0) and np.array_equal(hist, h0), key
         if rep == 1:
             rs.trim_memory(0)
+
+
+@pytest.mark.parametrize("m,tau,kind", [(301, 16, "count"), (1000, 64, "count"),
+                                        (1000, 64, "subcount")])
+def test_mixed_sketched_system_matches_fp64(rs, m, tau, kind):
+    """Mixed path (FP32 A on the CUDA cores, S^T A and M = S^T A S in FP32 sums, m not
+    a multiple of 4): M equals the plain FP64 path's M of the same draw within FP32
+    rounding."""
+    g = np.random.default_rng(m + tau)
+    X = g.standard_normal((3 * m, m)).astype(np.float32)
+    y = g.standard_normal(3 * m)
+    with rs.Solver(X, y, 0.3, sketch=kind, tau=tau, seed=11, precision="mixed",
+                   setup_tc=False) as s:
+        M32, _, _ = s.probe_step()
+    with rs.Solver(X, y, 0.3, sketch=kind, tau=tau, seed=11, precision="fp64") as s:
+        M64, _, _ = s.probe_step()
+    assert np.linalg.norm(M32 - M64) <= 1e-5 * np.linalg.norm(M64)
