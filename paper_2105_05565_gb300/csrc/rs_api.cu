@@ -905,6 +905,66 @@ const char* rs_last_error(const rs_ctx* ctx) {
   return g_err.c_str();
 }
 
+constexpr int64_t kPipeMinRows = 16384;
+constexpr int kPipePieces = 4;
+
+// Setup of a mixed primal context from FP32 X in host memory: X is copied into c->X
+// in kPipePieces row ranges on a copy stream; on the context's stream, each range's
+// transposed copy, its part of X^T X + lambda I (tensor cores, added into A) and its
+// 512-row blocks of X^T y follow their range's copy event. c->X, y, A (zeroed), b and
+// the scratch are allocated on the context's stream before.
+rs_status setup_pipelined(rs_ctx* c, const float* Xh, double lambda) {
+  cudaStream_t st = c->stream;
+  const int64_t n = c->n, d = c->d;
+  float* Xf = static_cast<float*>(c->X);
+  float* Xt = nullptr;
+  CKC(c, pmalloc(c, (void**)&Xt, gram_tc_ws_floats(n, d) * sizeof(float)));
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev[kPipePieces + 1] = {};
+  auto cleanup = [&]() {
+    for (cudaEvent_t e : ev) if (e) cudaEventDestroy(e);  // (released once completed)
+    if (cs) cudaStreamDestroy(cs);
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  for (int i = 0; i <= kPipePieces && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+  // the copies start once the allocations are in place in the context's stream order
+  if (e == cudaSuccess) e = cudaEventRecord(ev[kPipePieces], st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[kPipePieces], 0);
+  if (e == cudaSuccess) e = xt_pairs_split(st, c->y, n, d, c->xt_part);
+  const int64_t rows = round_up((n + kPipePieces - 1) / kPipePieces, 512);
+  auto piece = [&](int i, int64_t& r0, int64_t& r1) {
+    r0 = std::min<int64_t>(n, (int64_t)i * rows);
+    r1 = std::min<int64_t>(n, r0 + rows);
+  };
+  // copy of range i, then the arithmetic of range i - 1 (a host staging a pageable
+  // source copies the next range while the device works on the previous one)
+  for (int i = 0; i <= kPipePieces && e == cudaSuccess; ++i) {
+    int64_t r0, r1;
+    if (i < kPipePieces) {
+      piece(i, r0, r1);
+      if (r1 > r0)
+        e = cudaMemcpyAsync(Xf + r0 * d, Xh + r0 * d, (size_t)(r1 - r0) * d * sizeof(float),
+                            cudaMemcpyHostToDevice, cs);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[i], cs);
+    }
+    if (i >= 1 && e == cudaSuccess) {
+      piece(i - 1, r0, r1);
+      e = cudaStreamWaitEvent(st, ev[i - 1], 0);
+      if (e == cudaSuccess && r1 > r0)
+        e = launch_gram_tc_rows(st, Xf, n, d, lambda, static_cast<float*>(c->A), c->ld, Xt,
+                                c->err_flag, r0, r1);
+      if (e == cudaSuccess && r1 > r0) e = xt_pairs_rows(st, Xf, n, d, c->xt_part, r0, r1);
+    }
+  }
+  if (e == cudaSuccess) e = launch_mirror_lower<float>(st, static_cast<float*>(c->A), d, c->ld);
+  if (e == cudaSuccess) e = xt_pairs_sum(st, n, d, c->xt_part, c->b);
+  pfree(c, Xt);  // in stream order, after the products
+  cleanup();
+  CKC(c, e);
+  return RS_OK;
+}
+
 rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, double lambda,
                     int32_t form, int32_t sketch, int64_t tau, const rs_mom* mom, uint64_t seed,
                     const rs_opts* opts, rs_ctx** out) {
@@ -1057,8 +1117,15 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   // X, y
   const size_t xel = X->dtype == RS_F32 ? 4 : 8;
   const size_t xbytes = (size_t)X->n * X->d * xel;
+  const int dual = (form == RS_DUAL);
+  // X from the host for the tensor-core Gram: uploaded in pieces, each piece's part of
+  // X^T X and X^T y formed as soon as it has landed (the upload, about 210 GB/s on this
+  // machine, overlaps the setup's arithmetic)
+  const bool pipe = !X->on_device && X->dtype == RS_F32 && c->mixed() && !dual && o.setup_tc &&
+                    c->n >= kPipeMinRows;
   TRYC(pmalloc(c, (void**)&c->X, xbytes));
-  TRYC(cudaMemcpyAsync(c->X, X->val, xbytes, X->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  if (!pipe)
+    TRYC(cudaMemcpyAsync(c->X, X->val, xbytes, X->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   TRY(dalloc(c, &c->y, c->n));
   TRYC(cudaMemcpyAsync(c->y, y, c->n * sizeof(double), y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   // scratch of the X products
@@ -1071,8 +1138,9 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   TRYC(cudaMemsetAsync(c->A, 0, (size_t)m * c->ld * c->elem(), st));
   TRY(dalloc(c, &c->b, m));
   TRYC(cudaEventRecord(c->ev0, st));
-  const int dual = (form == RS_DUAL);
-  if (X->dtype == RS_F32) {
+  if (pipe) {
+    TRY(setup_pipelined(c, static_cast<const float*>(X->val), lambda));
+  } else if (X->dtype == RS_F32) {
     const float* Xf = static_cast<const float*>(c->X);
     if (c->mixed() && !dual && o.setup_tc) {
       // X^T X on the tensor cores through a transposed, padded copy of X

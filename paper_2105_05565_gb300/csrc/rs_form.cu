@@ -463,14 +463,16 @@ __global__ void __launch_bounds__(kXtuCols) k_xtu_df(const float* __restrict__ X
                                                      int64_t d, int nv,
                                                      const float2* __restrict__ U,
                                                      double* __restrict__ part,
-                                                     const int32_t* __restrict__ skip) {
+                                                     const int32_t* __restrict__ skip,
+                                                     int64_t rb0 = 0) {
   if (skip != nullptr) {
     int all = 1;
     for (int q = 0; q < nv; ++q) all &= (skip[q] != 0);
     if (all) return;
   }
   __shared__ float2 su[kXtuRows * NV];
-  const int64_t r0 = (int64_t)blockIdx.y * kXtuRows;
+  const int64_t rb = rb0 + blockIdx.y;  // row block
+  const int64_t r0 = rb * kXtuRows;
   const int64_t r1 = min(n, r0 + kXtuRows);
   for (int64_t e = threadIdx.x; e < (r1 - r0) * NV; e += blockDim.x) su[e] = U[r0 * NV + e];
   __syncthreads();
@@ -495,7 +497,7 @@ __global__ void __launch_bounds__(kXtuCols) k_xtu_df(const float* __restrict__ X
   }
 #pragma unroll
   for (int q = 0; q < NV; ++q)
-    if (q < nv) part[((int64_t)blockIdx.y * nv + q) * d + c] = (double)ah[q] + (double)al[q];
+    if (q < nv) part[(rb * nv + q) * d + c] = (double)ah[q] + (double)al[q];
 }
 
 // U[i] = (hi, lo) float pair of v[i]
@@ -512,15 +514,38 @@ __global__ void k_split_pairs(const double* __restrict__ v, int64_t n, float2* _
 // X^T v for FP32 X in float-pair arithmetic (the FP64 pipe is too narrow on this GPU
 // for one FP64 FMA per entry of X): v split into float pairs, then the column sums
 // of pass 2 of the two-pass product, then the FP64 sum of the row blocks' sums.
-cudaError_t launch_xt_v_pairs(cudaStream_t st, const float* X, int64_t n, int64_t d,
-                              const double* v, double* out, double* part, const int32_t* stop) {
+// in three steps for row ranges: split v, the column sums of the 512-row blocks of
+// rows [r0, r1) (r0 a multiple of 512), the sum of all blocks
+cudaError_t xt_pairs_split(cudaStream_t st, const double* v, int64_t n, int64_t d, double* part,
+                           const int32_t* stop) {
   const int64_t nblk = (n + kXtuRows - 1) / kXtuRows;
   float2* U = reinterpret_cast<float2*>(part + nblk * d);  // after the row blocks' sums
   k_split_pairs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, n, U, stop);
-  const dim3 g2((unsigned)((d + kXtuCols - 1) / kXtuCols), (unsigned)nblk);
-  k_xtu_df<1><<<g2, kXtuCols, 0, st>>>(X, n, d, 1, U, part, stop);
+  return cudaGetLastError();
+}
+cudaError_t xt_pairs_rows(cudaStream_t st, const float* X, int64_t n, int64_t d, double* part,
+                          int64_t r0, int64_t r1, const int32_t* stop) {
+  if (r0 % kXtuRows != 0 || r1 <= r0) return cudaErrorInvalidValue;
+  const int64_t nblk = (n + kXtuRows - 1) / kXtuRows;
+  const float2* U = reinterpret_cast<const float2*>(part + nblk * d);
+  const int64_t b0 = r0 / kXtuRows, b1 = (std::min(r1, n) + kXtuRows - 1) / kXtuRows;
+  const dim3 g2((unsigned)((d + kXtuCols - 1) / kXtuCols), (unsigned)(b1 - b0));
+  k_xtu_df<1><<<g2, kXtuCols, 0, st>>>(X, n, d, 1, U, part, stop, b0);
+  return cudaGetLastError();
+}
+cudaError_t xt_pairs_sum(cudaStream_t st, int64_t n, int64_t d, double* part, double* out,
+                         const int32_t* stop) {
+  const int64_t nblk = (n + kXtuRows - 1) / kXtuRows;
   k_sum_parts<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(part, nblk, d, out, stop);
   return cudaGetLastError();
+}
+
+cudaError_t launch_xt_v_pairs(cudaStream_t st, const float* X, int64_t n, int64_t d,
+                              const double* v, double* out, double* part, const int32_t* stop) {
+  cudaError_t e = xt_pairs_split(st, v, n, d, part, stop);
+  if (e == cudaSuccess) e = xt_pairs_rows(st, X, n, d, part, 0, n, stop);
+  if (e == cudaSuccess) e = xt_pairs_sum(st, n, d, part, out, stop);
+  return e;
 }
 
 int64_t xtx_two_pass_part(int64_t n, int64_t d, int nv) {
@@ -541,7 +566,7 @@ cudaError_t launch_xtx_two_pass(cudaStream_t st, const float* X, int64_t n, int6
     e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return;
     k1<<<g1, 1024, smem, st>>>(X, n, d, nv, W, U, skip);
-    k2<<<g2, kXtuCols, 0, st>>>(X, n, d, nv, U, part, skip);
+    k2<<<g2, kXtuCols, 0, st>>>(X, n, d, nv, U, part, skip, (int64_t)0);
   };
   if (NV == 1) go(k_xw_df<1>, k_xtu_df<1>);
   else if (NV == 2) go(k_xw_df<2>, k_xtu_df<2>);

@@ -314,6 +314,11 @@ cudaError_t launch_chunk_begin(cudaStream_t st, Ctrl* ctrl);
 // A (lower triangle and diagonal, d x lda FP32) = X^T X + lambda I, TF32 inputs, FP32
 // accumulation; Xt_ws: gram_tc_ws_floats(n, d) floats; err set on a device timeout
 size_t gram_tc_ws_floats(int64_t n, int64_t d);
+// the part of rows [r0, r1) of X (r0 a multiple of 32; r1 too, or r1 = n): stored with
+// lambda I for r0 = 0, added to A otherwise (row ranges of an upload in pieces)
+cudaError_t launch_gram_tc_rows(cudaStream_t st, const float* X, int64_t n, int64_t d,
+                                double lambda, float* A, int64_t lda, float* Xt_ws, int32_t* err,
+                                int64_t r0, int64_t r1);
 cudaError_t launch_gram_tc(cudaStream_t st, const float* X, int64_t n, int64_t d, double lambda,
                            float* A, int64_t lda, float* Xt_ws, int32_t* err);
 template <typename T>
@@ -336,6 +341,14 @@ size_t xt_part_elems(int64_t n, int64_t d);
 cudaError_t launch_xt_v_pairs(cudaStream_t st, const float* X, int64_t n, int64_t d,
                               const double* v, double* out, double* part,
                               const int32_t* stop = nullptr);
+// its three steps, for row ranges of X: the float pairs of v, the sums of the 512-row
+// blocks of rows [r0, r1) (r0 a multiple of 512), the sum of all blocks into out
+cudaError_t xt_pairs_split(cudaStream_t st, const double* v, int64_t n, int64_t d, double* part,
+                           const int32_t* stop = nullptr);
+cudaError_t xt_pairs_rows(cudaStream_t st, const float* X, int64_t n, int64_t d, double* part,
+                          int64_t r0, int64_t r1, const int32_t* stop = nullptr);
+cudaError_t xt_pairs_sum(cudaStream_t st, int64_t n, int64_t d, double* part, double* out,
+                         const int32_t* stop = nullptr);
 // out[i] = sum_j X[i, j] v[j] (i < n), FP64 accumulate
 template <typename TI>
 cudaError_t launch_x_v(cudaStream_t st, const TI* X, int64_t n, int64_t d, const double* v,

@@ -140,8 +140,11 @@ __device__ __forceinline__ void cluster_sync() {
 
 }  // namespace
 
+// K steps [kb0, kb0 + nk); accumulate: add the tiles to A (a later range of rows of X),
+// else store them with lambda on the diagonal
 __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUtensorMap tmap,
-                                                   int64_t d, int64_t nk, double lambda,
+                                                   int64_t d, int64_t kb0, int64_t nk,
+                                                   double lambda, int accumulate,
                                                    float* __restrict__ A, int64_t lda,
                                                    int32_t* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -194,9 +197,9 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
       if (*(volatile int*)&s_abort) break;
       unsigned char* st = base + s * kStageBytes;
       mbar_arrive_expect_tx(&full_bar[s], kStageBytes);  // own A + both halves of B
-      tma_load_2d(st, &tmap, &full_bar[s], (int)(kb * kBK), row0);
-      tma_load_2d_mc(st + kABytes + crank * kBHalfBytes, &tmap, &full_bar[s], (int)(kb * kBK),
-                     col0 + (int)crank * (kBN / 2), kBoth);
+      tma_load_2d(st, &tmap, &full_bar[s], (int)((kb0 + kb) * kBK), row0);
+      tma_load_2d_mc(st + kABytes + crank * kBHalfBytes, &tmap, &full_bar[s],
+                     (int)((kb0 + kb) * kBK), col0 + (int)crank * (kBN / 2), kBoth);
     }
     // tail: every stage filled here has been released by both CTAs' MMAs, so no
     // commit of the peer is still on its way to these barriers
@@ -250,7 +253,8 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
           const int64_t cidx = col0 + c0 + q;
           if (cidx < d && cidx <= r) {
             float f = __uint_as_float(v[q]);
-            if (cidx == r) f = (float)((double)f + lambda);
+            if (accumulate) f += A[r * lda + cidx];
+            else if (cidx == r) f = (float)((double)f + lambda);
             A[r * lda + cidx] = f;
           }
         }
@@ -268,9 +272,9 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
 
 // Xt[i * ldk + k] = X[k * d + i] (zero for k >= n): 32 x 32 tiles through shared memory
 __global__ void k_transpose_pad(const float* __restrict__ X, int64_t n, int64_t d,
-                                float* __restrict__ Xt, int64_t ldk) {
+                                float* __restrict__ Xt, int64_t ldk, int64_t k_base) {
   __shared__ float tile[32][33];
-  const int64_t k0 = (int64_t)blockIdx.x * 32, i0 = (int64_t)blockIdx.y * 32;
+  const int64_t k0 = k_base + (int64_t)blockIdx.x * 32, i0 = (int64_t)blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int64_t k = k0 + r, i = i0 + threadIdx.x;
     tile[r][threadIdx.x] = (k < n && i < d) ? X[k * d + i] : 0.f;
@@ -302,12 +306,17 @@ static EncodeTiledFn encode_fn() {
 
 size_t gram_tc_ws_floats(int64_t n, int64_t d) { return (size_t)d * (size_t)round_up(n, 32); }
 
-// A (d x lda, lower triangle and diagonal; the caller mirrors) = X^T X + lambda I
-cudaError_t launch_gram_tc(cudaStream_t st, const float* X, int64_t n, int64_t d, double lambda,
-                           float* A, int64_t lda, float* Xt_ws, int32_t* err) {
+// the rows [r0, r1) of X (r0 a multiple of 32; r1 too, or r1 = n): their part of
+// X^T X into the lower triangle of A (d x lda; the caller mirrors), stored with lambda
+// on the diagonal for r0 = 0, else added to A
+cudaError_t launch_gram_tc_rows(cudaStream_t st, const float* X, int64_t n, int64_t d,
+                                double lambda, float* A, int64_t lda, float* Xt_ws, int32_t* err,
+                                int64_t r0, int64_t r1) {
   const int64_t ldk = round_up(n, 32);
-  dim3 tb(32, 8), tg((unsigned)(ldk / 32), (unsigned)((d + 31) / 32));
-  k_transpose_pad<<<tg, tb, 0, st>>>(X, n, d, Xt_ws, ldk);
+  const int64_t k1 = (r1 >= n) ? ldk : r1;  // the last range takes the zero padding
+  if (r0 % 32 != 0 || k1 % 32 != 0 || r0 >= k1) return cudaErrorInvalidValue;
+  dim3 tb(32, 8), tg((unsigned)((k1 - r0) / 32), (unsigned)((d + 31) / 32));
+  k_transpose_pad<<<tg, tb, 0, st>>>(X, n, d, Xt_ws, ldk, r0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   EncodeTiledFn enc = encode_fn();
@@ -339,7 +348,13 @@ cudaError_t launch_gram_tc(cudaStream_t st, const float* X, int64_t n, int64_t d
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_gram_tc, map, d, ldk / kBK, lambda, A, lda, err);
+  return cudaLaunchKernelEx(&cfg, k_gram_tc, map, d, r0 / kBK, (k1 - r0) / kBK, lambda,
+                            r0 > 0 ? 1 : 0, A, lda, err);
+}
+
+cudaError_t launch_gram_tc(cudaStream_t st, const float* X, int64_t n, int64_t d, double lambda,
+                           float* A, int64_t lda, float* Xt_ws, int32_t* err) {
+  return launch_gram_tc_rows(st, X, n, d, lambda, A, lda, Xt_ws, err, 0, n);
 }
 
 }  // namespace rs

@@ -466,3 +466,39 @@ def test_mixed_sketched_system_matches_fp64(rs, m, tau, kind):
     with rs.Solver(X, y, 0.3, sketch=kind, tau=tau, seed=11, precision="fp64") as s:
         M64, _, _ = s.probe_step()
     assert np.linalg.norm(M32 - M64) <= 1e-5 * np.linalg.norm(M64)
+
+
+def test_host_upload_in_pieces_matches_device_input(rs):
+    """FP32 X in host memory with n >= 16384: X is uploaded in four row ranges, each
+    range's part of X^T X (tensor cores, added into A) and of X^T y formed after its
+    copy. The system equals the one formed from the same X already on the device:
+    b to the bit (the same 512-row blocks summed in the same order), M = A[C, C] (S
+    the sample of all d columns) within the TF32 bound of the tensor-core Gram for both
+    (the range sums change only the FP32 rounding of the accumulation), and the mixed
+    solve reaches the FP64-checked tolerance."""
+    import torch
+
+    n, d = 40000 + 77, 256
+    g = np.random.default_rng(5)
+    X = g.standard_normal((n, d)).astype(np.float32)
+    y = g.standard_normal(n)
+    v = g.standard_normal(d)
+    Xd = torch.from_numpy(X).cuda()
+    out = {}
+    for name, Xin in (("host", X), ("device", Xd)):
+        with rs.Solver(Xin, y, 0.5, sketch="subsample", tau=d, seed=2, precision="mixed") as s:
+            M, _, _ = s.probe_step()
+            rel = s.true_residual(v)
+            w, hist, iters, conv = s.solve(tol=1e-8, max_iters=20000)
+        out[name] = (M, rel, w, conv)
+    Mh, rh, wh, ch = out["host"]
+    Md, rd, wd, cd = out["device"]
+    assert rh == rd
+    C = orng.subsample_indices(2, 0, d, d)
+    X64 = X.astype(np.float64)
+    ref = (X64.T @ X64 + 0.5 * np.eye(d))[np.ix_(C, C)]
+    bound = 2.0 ** -9 * (np.abs(X64).T @ np.abs(X64))[np.ix_(C, C)]
+    for M in (Mh, Md):
+        assert np.all(np.abs(M - ref) <= bound + 1e-6)
+    assert ch and cd
+    assert oracle.true_residual(X.astype(np.float64), y, 0.5, wh) <= 1e-8
