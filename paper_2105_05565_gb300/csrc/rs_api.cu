@@ -1356,6 +1356,8 @@ rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int3
     h->r0 = c->r0;
     h->tol = tol;
     h->checked_k = -1;
+    h->pk = -1;
+    h->predict = (c->mixed() && c->use_wide) ? 1 : 0;
     if ((s = write_ctrl(c)) != RS_OK) return s;
     CKC(c, cudaEventRecord(c->ev0, st));
     const int64_t max_chunks = (max_iters + c->chunk - 1) / c->chunk + 2;
@@ -1539,6 +1541,8 @@ rs_status rs_step(rs_ctx* c, int64_t n_iters, double* hist_out) {
   h->status = 0;
   h->ticket = 0;
   h->no_stop = 1;
+  h->predict = 0;  // every chunk runs to its end
+  h->kcap = 0;
   h->max_iters = k0 + n_iters;
   h->r0 = c->r0 > 0.0 ? c->r0 : 1.0;
   if ((s = write_ctrl(c)) != RS_OK) return s;
@@ -1590,6 +1594,7 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
   if ((s = ensure_schedule(c, k0 + reps + c->chunk + 2)) != RS_OK) return s;
   Ctrl* h = c->ctrl_h;
   h->stop = 0; h->pending = 0; h->status = 0; h->ticket = 0; h->no_stop = 1;
+  h->predict = 0; h->kcap = 0;
   // past the profiled iterations, so that no kernel of the last chunk sees the cap
   // (the refresh after it would return at once)
   h->max_iters = k0 + reps + c->chunk + 1;

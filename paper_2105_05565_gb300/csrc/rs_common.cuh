@@ -62,6 +62,15 @@ struct Ctrl {
   double r0;          // ||r^0|| = ||b||
   double tol;
   int64_t checked_k;  // last k whose FP64 true residual (a refresh) is hist[k]; -1: none
+  // convergence forecast of the mixed persistent path (predict = 1): after each
+  // refresh, kcap > 0 ends the next chunk at the iteration where the FP64 residual's
+  // decay over the last chunk reaches tol (with a margin), so that phase 1 forms no
+  // slot past it; pk, prel: iteration and FP64 residual of the previous refresh
+  int64_t kcap;
+  int64_t pk;
+  double prel;
+  int32_t predict;
+  int32_t pad2;
 };
 
 __device__ __forceinline__ bool halted(const Ctrl* c) {
@@ -79,7 +88,8 @@ __device__ __forceinline__ bool stopped(const Ctrl* c) {
 __device__ __forceinline__ int64_t active_slots(const Ctrl* c, int force, int nslots) {
   if (force) return nslots;
   if (stopped(c)) return 0;
-  const int64_t left = c->max_iters - c->k0;
+  int64_t left = c->max_iters - c->k0;
+  if (c->kcap > 0 && c->kcap - c->k0 < left) left = c->kcap - c->k0;
   return left < 0 ? 0 : (left < nslots ? left : (int64_t)nslots);
 }
 

@@ -694,6 +694,18 @@ __global__ void __launch_bounds__(256) k_refresh_finish(Ctrl* __restrict__ ctrl,
       }
       ctrl->pending = 0;
       if (k >= ctrl->max_iters) ctrl->stop = 1;
+      if (ctrl->predict) {
+        // forecast: the decay rate of the FP64 residual since the previous refresh
+        int64_t cap = 0;
+        if (ctrl->pk >= 0 && k > ctrl->pk && rel > ctrl->tol && ctrl->prel > rel && rel > 0.0) {
+          const double rate = log(rel / ctrl->prel) / (double)(k - ctrl->pk);  // < 0
+          const double left = log(ctrl->tol / rel) / rate;                      // > 0
+          if (left < 1e9) cap = k + (int64_t)ceil(1.25 * left) + 8;
+        }
+        ctrl->kcap = cap;
+        ctrl->pk = k;
+        ctrl->prel = rel;
+      }
     } else {
       *rel_out = rel;
     }

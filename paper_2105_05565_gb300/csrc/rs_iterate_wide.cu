@@ -310,7 +310,8 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   // exchange, so all CTAs take the same branches
   if (halted(ctrl)) return;
   const int64_t k0 = ctrl->k0, kstart = ctrl->k;
-  const int64_t kend = min(k0 + g.chunk, ctrl->max_iters);
+  int64_t kend = min(k0 + g.chunk, ctrl->max_iters);
+  if (ctrl->kcap > 0 && ctrl->kcap < kend) kend = ctrl->kcap;  // convergence forecast
   if (kstart >= kend) return;
   const double tol = ctrl->tol, r0 = ctrl->r0;
   const double thr2 = (tol * r0) * (tol * r0);
