@@ -625,37 +625,24 @@ __global__ void __maxnreg__(96) k_sweep_inv(const Ctrl* __restrict__ ctrl, int f
       for (int r = 0; r < kSwB; ++r)
 #pragma unroll
         for (int kk = 0; kk < kSwB; ++kk) Xs[kk][I * (kSwB + 1) + r] = a[r][kk];
-#pragma unroll
-      for (int c = 0; c < kSwB; ++c) {
-        float z[kSwB];
-#pragma unroll
-        for (int kk = 0; kk < kSwB; ++kk) z[kk] = Zs[kk][c];
-#pragma unroll
-        for (int r = 0; r < kSwB; ++r) {
-          float y = 0.f;
-#pragma unroll
-          for (int kk = 0; kk < kSwB; ++kk) y = fmaf(a[r][kk], z[kk], y);
-          Ys[c][I * (kSwB + 1) + r] = y;
-        }
-      }
     } else if (own && I == Pb && J < Pb) {
 #pragma unroll
       for (int kk = 0; kk < kSwB; ++kk)
 #pragma unroll
         for (int c = 0; c < kSwB; ++c) Xs[kk][J * (kSwB + 1) + c] = a[kk][c];
+    }
+    __syncthreads();
+    // Y = X Z by every thread (an entry each: 8 FMAs in the order of kk), instead of
+    // 512 FMAs by each panel block's owner
+    for (int e = tid; e < nb * kSwB * kSwB; e += blockDim.x) {
+      const int blk = e / (kSwB * kSwB);
+      if (blk == Pb) continue;
+      const int c = (e / kSwB) % kSwB, r = e % kSwB;
+      const int col = blk * (kSwB + 1) + r;
+      float y = 0.f;
 #pragma unroll
-      for (int cc = 0; cc < kSwB; ++cc) {
-        float z[kSwB];
-#pragma unroll
-        for (int kk = 0; kk < kSwB; ++kk) z[kk] = Zs[kk][cc];
-#pragma unroll
-        for (int c = 0; c < kSwB; ++c) {
-          float y = 0.f;
-#pragma unroll
-          for (int kk = 0; kk < kSwB; ++kk) y = fmaf(a[kk][c], z[kk], y);
-          Ys[cc][J * (kSwB + 1) + c] = y;
-        }
-      }
+      for (int kk = 0; kk < kSwB; ++kk) y = fmaf(Xs[kk][col], Zs[kk][c], y);
+      Ys[c][col] = y;
     }
     __syncthreads();
     // A_IJ -= X_I Y_J^T; A_IP = Y_I, A_PJ = Y_J^T; A_PP = -Z already
