@@ -198,7 +198,7 @@ class Solver:
     """
 
     def __init__(self, X, y, lam, form="primal", sketch="count", tau=0, momentum="none", seed=0,
-                 precision="fp64", refresh_every=150, sub_s=0, chol_fp64=False, chunk=0,
+                 precision="fp64", refresh_every=400, sub_s=0, chol_fp64=False, chunk=0,
                  eta=0.995, beta_switch=0.5, gamma_c=1.0, beta_c=0.5, uncapped=False,
                  device=0, stream=None, setup_tc=True, iter_ctas=0):
         L = lib()

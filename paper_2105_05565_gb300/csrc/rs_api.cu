@@ -77,7 +77,7 @@ struct rs_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   // problem
-  int form = 0, sketch = 0, precision = 0, chol_fp64 = 1, refresh_every = 150;
+  int form = 0, sketch = 0, precision = 0, chol_fp64 = 1, refresh_every = 400;
   int64_t n = 0, d = 0, m = 0, tau = 0, s = 0, kk = 0, mp = 0, ld = 0, chunk = 64;
   double lambda = 0.0;
   uint64_t seed = 0;
@@ -879,7 +879,7 @@ void rs_default_opts(rs_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
   o->precision = RS_PLAIN_FP64;
-  o->refresh_every = 150;
+  o->refresh_every = 400;
   o->sub_s = 0;
   o->cuda_stream = nullptr;
   o->device = 0;
@@ -1019,7 +1019,7 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     delete c;
     return RS_EUNSUPPORTED;
   }
-  c->refresh_every = o.refresh_every > 0 ? o.refresh_every : 150;
+  c->refresh_every = o.refresh_every > 0 ? o.refresh_every : 400;
   c->n = X->n;
   c->d = X->d;
   c->m = (form == RS_PRIMAL) ? X->d : X->n;
