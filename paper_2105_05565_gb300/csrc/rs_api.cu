@@ -1123,8 +1123,11 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   // machine, overlaps the setup's arithmetic)
   const bool pipe = !X->on_device && X->dtype == RS_F32 && c->mixed() && !dual && o.setup_tc &&
                     c->n >= kPipeMinRows;
+  // X on the device for the tensor-core Gram: the transposed copy's kernel also writes
+  // the context's copy of X, from one read of the caller's X
+  const bool fused_copy = X->on_device && X->dtype == RS_F32 && c->mixed() && !dual && o.setup_tc;
   TRYC(pmalloc(c, (void**)&c->X, xbytes));
-  if (!pipe)
+  if (!pipe && !fused_copy)
     TRYC(cudaMemcpyAsync(c->X, X->val, xbytes, X->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   TRY(dalloc(c, &c->y, c->n));
   TRYC(cudaMemcpyAsync(c->y, y, c->n * sizeof(double), y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
@@ -1146,7 +1149,11 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
       // X^T X on the tensor cores through a transposed, padded copy of X
       float* Xt = nullptr;
       TRYC(pmalloc(c, (void**)&Xt, gram_tc_ws_floats(c->n, c->d) * sizeof(float)));
-      cudaError_t e1 = launch_gram_tc(st, Xf, c->n, c->d, lambda, static_cast<float*>(c->A), c->ld,
+      cudaError_t e1 =
+          fused_copy ? launch_gram_tc(st, static_cast<const float*>(X->val), c->n, c->d, lambda,
+                                      static_cast<float*>(c->A), c->ld, Xt, c->err_flag,
+                                      static_cast<float*>(c->X))
+                     : launch_gram_tc(st, Xf, c->n, c->d, lambda, static_cast<float*>(c->A), c->ld,
                                       Xt, c->err_flag);
       if (e1 == cudaSuccess) e1 = launch_mirror_lower<float>(st, static_cast<float*>(c->A), c->d, c->ld);
       pfree(c, Xt);  // in stream order, after the product

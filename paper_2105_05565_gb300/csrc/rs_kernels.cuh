@@ -318,9 +318,11 @@ size_t gram_tc_ws_floats(int64_t n, int64_t d);
 // lambda I for r0 = 0, added to A otherwise (row ranges of an upload in pieces)
 cudaError_t launch_gram_tc_rows(cudaStream_t st, const float* X, int64_t n, int64_t d,
                                 double lambda, float* A, int64_t lda, float* Xt_ws, int32_t* err,
-                                int64_t r0, int64_t r1);
+                                int64_t r0, int64_t r1, float* Xcopy = nullptr);
+// (Xcopy != nullptr: X is also copied there, row-major, from the same read)
 cudaError_t launch_gram_tc(cudaStream_t st, const float* X, int64_t n, int64_t d, double lambda,
-                           float* A, int64_t lda, float* Xt_ws, int32_t* err);
+                           float* A, int64_t lda, float* Xt_ws, int32_t* err,
+                           float* Xcopy = nullptr);
 template <typename T>
 cudaError_t launch_mirror_lower(cudaStream_t st, T* A, int64_t m, int64_t lda);
 

@@ -270,14 +270,19 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
   cluster_sync();  // neither CTA leaves while the other may still reach its shared memory
 }
 
-// Xt[i * ldk + k] = X[k * d + i] (zero for k >= n): 32 x 32 tiles through shared memory
+// Xt[i * ldk + k] = X[k * d + i] (zero for k >= n): 32 x 32 tiles through shared memory;
+// with Xcopy != nullptr the tile is also stored to Xcopy (same layout as X), so that a
+// copy of X and its transpose come from one read of X
 __global__ void k_transpose_pad(const float* __restrict__ X, int64_t n, int64_t d,
-                                float* __restrict__ Xt, int64_t ldk, int64_t k_base) {
+                                float* __restrict__ Xt, int64_t ldk, int64_t k_base,
+                                float* __restrict__ Xcopy) {
   __shared__ float tile[32][33];
   const int64_t k0 = k_base + (int64_t)blockIdx.x * 32, i0 = (int64_t)blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int64_t k = k0 + r, i = i0 + threadIdx.x;
-    tile[r][threadIdx.x] = (k < n && i < d) ? X[k * d + i] : 0.f;
+    const float v = (k < n && i < d) ? X[k * d + i] : 0.f;
+    tile[r][threadIdx.x] = v;
+    if (Xcopy != nullptr && k < n && i < d) Xcopy[k * d + i] = v;
   }
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -311,12 +316,12 @@ size_t gram_tc_ws_floats(int64_t n, int64_t d) { return (size_t)d * (size_t)roun
 // on the diagonal for r0 = 0, else added to A
 cudaError_t launch_gram_tc_rows(cudaStream_t st, const float* X, int64_t n, int64_t d,
                                 double lambda, float* A, int64_t lda, float* Xt_ws, int32_t* err,
-                                int64_t r0, int64_t r1) {
+                                int64_t r0, int64_t r1, float* Xcopy) {
   const int64_t ldk = round_up(n, 32);
   const int64_t k1 = (r1 >= n) ? ldk : r1;  // the last range takes the zero padding
   if (r0 % 32 != 0 || k1 % 32 != 0 || r0 >= k1) return cudaErrorInvalidValue;
   dim3 tb(32, 8), tg((unsigned)((k1 - r0) / 32), (unsigned)((d + 31) / 32));
-  k_transpose_pad<<<tg, tb, 0, st>>>(X, n, d, Xt_ws, ldk, r0);
+  k_transpose_pad<<<tg, tb, 0, st>>>(X, n, d, Xt_ws, ldk, r0, Xcopy);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   EncodeTiledFn enc = encode_fn();
@@ -353,8 +358,8 @@ cudaError_t launch_gram_tc_rows(cudaStream_t st, const float* X, int64_t n, int6
 }
 
 cudaError_t launch_gram_tc(cudaStream_t st, const float* X, int64_t n, int64_t d, double lambda,
-                           float* A, int64_t lda, float* Xt_ws, int32_t* err) {
-  return launch_gram_tc_rows(st, X, n, d, lambda, A, lda, Xt_ws, err, 0, n);
+                           float* A, int64_t lda, float* Xt_ws, int32_t* err, float* Xcopy) {
+  return launch_gram_tc_rows(st, X, n, d, lambda, A, lda, Xt_ws, err, 0, n, Xcopy);
 }
 
 }  // namespace rs
