@@ -502,3 +502,24 @@ def test_host_upload_in_pieces_matches_device_input(rs):
         assert np.all(np.abs(M - ref) <= bound + 1e-6)
     assert ch and cd
     assert oracle.true_residual(X.astype(np.float64), y, 0.5, wh) <= 1e-8
+
+
+@pytest.mark.parametrize("refresh", [16, 48])
+def test_mixed_chunk_forecast_reaches_tolerance(rs, refresh):
+    """Mixed persistent path with short refresh periods, so that the convergence
+    forecast sets the end of many chunks (some forecasts fall short and cost one more
+    refresh): the solve still stops only on an FP64-checked residual below tol, with
+    the weights of the FP64 direct solution."""
+    from synth import geometric_sigma, spectrum_problem
+
+    X, y, _ = spectrum_problem(4000, 384, geometric_sigma(384, 1e-2), seed=17, noise=0.01,
+                               dtype=np.float32)
+    lam = 1e-3
+    with rs.Solver(X, y, lam, sketch="count", tau=32, momentum="heuristic", seed=5,
+                   precision="mixed", refresh_every=refresh) as s:
+        assert s.iter_ctas > 0
+        w, hist, iters, conv = s.solve(tol=1e-7, max_iters=100000)
+    Xd = X.astype(np.float64)
+    assert conv and hist[iters] <= 1e-7
+    assert oracle.true_residual(Xd, y, lam, w) <= 1e-7
+    assert rel(w, oracle.direct_solution(Xd, y, lam)) <= 1e-4
