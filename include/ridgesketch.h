@@ -122,7 +122,7 @@ typedef struct {
   int32_t precision;     /* rs_precision; default RS_PLAIN_FP64 */
   int32_t refresh_every; /* RS_MIXED: true-residual period in iterations (the chunk
                             length); default 400, shortened where the chunk's buffers
-                            would pass 4 GB (the Python batch binding passes 150) */
+                            would pass 4 GB (the Python batch binding passes 300) */
   int64_t sub_s;         /* SubCount sample size s (multiple of tau, <= m); 0 = rule of
                             Section 4.2: k = 10 if 10 tau <= m else floor(m/tau), s = k tau */
   void* cuda_stream;     /* cudaStream_t to issue work on; NULL = library-owned stream */

@@ -468,7 +468,7 @@ class Batch:
     """
 
     def __init__(self, Xs, Ys, lams, sketch="count", taus=None, momentum="none", seed=0,
-                 precision="fp64", refresh_every=150, sub_s=0, chunk=0, eta=0.995,
+                 precision="fp64", refresh_every=300, sub_s=0, chunk=0, eta=0.995,
                  beta_switch=0.5, gamma_c=1.0, beta_c=0.5, uncapped=False, device=0, stream=None,
                  setup_tc=True):
         L = lib()
