@@ -296,6 +296,54 @@ def bench_sparse(args, rs, dev):
     print(json.dumps(out), flush=True)
 
 
+def profile_case(workload, rs, dev):
+    """Short cases of the other workloads for ncu captures (mixed precision):
+    batched: the first 32 problems of the batched recipe, 50 iterations, 256 threads
+    per CTA, one phase-1 stream; sparse: the sparse recipe, 100 iterations in chunks
+    of 50; learned: X = U diag(i^-0.8) V^T at 16384 x 8192, lambda 1e-3, an untrained
+    network (synth.mlp_init(4) rounded to bfloat16), eps 0.1, 60 iterations in chunks
+    of 20. Prints one line with the iteration count."""
+    import torch
+
+    if workload == "batched":
+        from synth import batched_problem_torch, batched_specs
+
+        P = 32
+        d, n, lam = batched_specs(P, 4)
+        Xs, Ys = [], []
+        for p in range(P):
+            X, Y = batched_problem_torch(int(n[p]), int(d[p]), 4, 10000 + p, device=dev)
+            Xs.append(X)
+            Ys.append(Y)
+        torch.cuda.synchronize(dev)
+        taus = [min(128, int(v) // 8) for v in d]
+        with rs.Batch(Xs, Ys, list(lam), sketch="count", taus=taus, momentum="heuristic", seed=0,
+                      precision="mixed") as b:
+            b.set_launch(256, 1)
+            _, iters, _, _ = b.solve(tol=0.0, max_iters=50)
+        out = int(iters.max())
+    elif workload == "sparse":
+        from synth import sparse_problem
+
+        n, d = 1_000_000, 50_000
+        rowptr, colidx, vals, y, _ = sparse_problem(n, d, 5_000_000, 3000, bf16=True)
+        X = rs.CSR(rowptr, colidx, vals, (n, d), bf16=True)
+        with rs.Solver(X, y, 0.1, sketch="subcount", tau=512, momentum="heuristic", seed=0,
+                       precision="mixed", sub_s=4096, refresh_every=50) as s:
+            _, _, out, _ = s.solve(tol=0.0, max_iters=100)
+    else:
+        from synth import mlp_init, power_sigma, spectrum_problem_torch
+
+        X, y, _ = spectrum_problem_torch(16384, 8192, power_sigma(8192, 0.8), 999, device=dev)
+        f = np.ascontiguousarray(mlp_init(4), np.float32).view(np.uint32).astype(np.uint64)
+        wb = (((f + 0x7FFF + ((f >> 16) & 1)) >> 16) & 0xFFFF).astype(np.uint16)
+        with rs.Solver(X, y, 1e-3, sketch="subsample", tau=256, momentum="none", seed=5,
+                       precision="mixed", chunk=20, refresh_every=20) as s:
+            s.set_proposal(wb, 0.1)
+            _, _, out, _ = s.solve(tol=0.0, max_iters=60)
+    print(json.dumps({"profile_case": workload, "iters": out}), flush=True)
+
+
 def bench_learned(args, rs, dev):
     """X 65536 x 8192 = U diag(i^-0.8) V^T (Haar U, V), lambda 1e-3, subsample tau 256,
     no momentum, to 1e-6: uniform draws against the learned proposal (the network
@@ -360,8 +408,10 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--small", action="store_true",
-                    help="profiling case: X 20000 x 4096 (328 MB, larger than L2), same sketch and "
-                         "schedule; prints the line of that case (not the benchmark workload)")
+                    help="profiling case: dense X 20000 x 4096 (328 MB, larger than L2), same "
+                         "sketch and schedule, prints the line of that case; with --workload "
+                         "batched / sparse / learned the short case of that workload for ncu "
+                         "(profile_case)")
     ap.add_argument("--workload", default="dense", choices=["dense", "batched", "sparse", "learned"],
                     help="dense: the benchmark line; batched / sparse: measurement lines of the "
                          "256-problem batch and the Zipf-sparse matrix-free solve")
@@ -376,6 +426,8 @@ def main():
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
         rs.lib()
+        if args.small:
+            return profile_case(args.workload, rs, dev)
         fn = {"batched": bench_batched, "sparse": bench_sparse, "learned": bench_learned}[args.workload]
         return fn(args, rs, dev)
 
