@@ -803,6 +803,12 @@ bool wide_plan(int64_t m, int64_t tau, int max_ctas, int64_t chunk, WidePlan* ou
     const size_t smem = smem_of(q);
     // the staged block must fit one bulk copy's transaction count as well
     if (smem > (size_t)optin || (size_t)tau * round_up(q, 4) * sizeof(T) >= (1u << 20)) return false;
+    if (kWideCluster > 8 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
       cudaGetLastError();
@@ -844,6 +850,10 @@ cudaError_t launch_iterate_wide(cudaStream_t st, Ctrl* ctrl, const WideArgs<T, T
   auto kern = k_iterate_wide<T, TF>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  if (kWideCluster > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)g.nblk);
   cfg.blockDim = dim3(kWThreads);

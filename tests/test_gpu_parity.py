@@ -106,15 +106,15 @@ def test_plain_iterates_match_oracle(rs, kind, tau, s_, mom):
 
 @pytest.mark.parametrize("kind,tau,s_", KINDS[:3], ids=[k[0] for k in KINDS[:3]])
 def test_plain_iterates_one_cluster_of_ctas(rs, kind, tau, s_):
-    """The persistent iteration kernel with 8 CTAs of 16 rows (one cluster; the
-    last CTA idle) against the oracle."""
+    """The persistent iteration kernel as one cluster of 16 CTAs of 8 rows (the last
+    three CTAs idle) against the oracle."""
     X, y, _ = gaussian_problem(160, 97, 21)
     lam, K = 0.05, 40
     ref = oracle.solve_ridge(X, y, lam, "primal", kind, tau, seed=9, tol=0.0, max_iters=K,
                              mom={"kind": "heuristic"}, s=s_)
     with rs.Solver(X, y, lam, sketch=kind, tau=tau, momentum="heuristic", seed=9,
-                   sub_s=s_ or 0, iter_ctas=8) as s:
-        assert (s.iter_ctas, s.iter_rows) == (8, 16)
+                   sub_s=s_ or 0, iter_ctas=16) as s:
+        assert (s.iter_ctas, s.iter_rows) == (16, 8)
         w, hist, iters, _ = s.solve(tol=0.0, max_iters=K)
     assert iters == K
     assert rel(w, ref["w"]) <= W_TOL
