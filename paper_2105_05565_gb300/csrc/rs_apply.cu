@@ -270,8 +270,10 @@ __global__ void __launch_bounds__(256) k_sa_msys(const Ctrl* __restrict__ ctrl, 
         if (v >= nvec) continue;
         const int64_t c = v * VN;
         *reinterpret_cast<V*>(srow + r * mr + c) = acc[u];
+        // S^T A streams out marked evict-first, so that A stays in L2 for the other
+        // slots (read back by the iterations a chunk later, from DRAM in any case)
         if (bq == 0 ? c < ldsa : c < m)
-          *reinterpret_cast<V*>(SAs + sa_off(j, c, ldsa, bq, tau)) = acc[u];
+          __stcs(reinterpret_cast<V*>(SAs + sa_off(j, c, ldsa, bq, tau)), acc[u]);
       }
     }
   }
