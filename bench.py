@@ -538,12 +538,13 @@ def main():
         "wall_s_timed": wall,
     }
     line.update(extra)
-    # kernels launched in the timed region, per chunk of REFRESH iterations: chunk begin,
-    # sketch plans, inverse plan map, S^T A, S^T A S, factor + inverse, the fused
-    # iteration kernel, and the FP64 refresh (float-pair X^T X v, sum, finish);
-    # per step 10 more (forming A and b, ||b||, initial state, final FP64 check)
-    n_chunks = sum((r["iters"] + REFRESH - 1) // REFRESH for r in runs)
-    line["gpu_launches"] = int(n_chunks * 10 + args.steps * 10)
+    # kernels launched in the timed region: per chunk of REFRESH iterations 9 (chunk
+    # begin, sketch plans, row -> bucket map, S^T A with S^T A S, the sweep for M^+, the
+    # persistent iteration kernel, and the FP64 refresh: float-pair X^T X w, its sum,
+    # finish), chunks replayed four per CUDA graph; per step 7 more (transposed copy,
+    # tensor-core X^T X, mirror, b = X^T y in three launches, initial state)
+    n_chunks = sum(4 * ((((r["iters"] + REFRESH - 1) // REFRESH) + 3) // 4) for r in runs)
+    line["gpu_launches"] = int(n_chunks * 9 + args.steps * 7)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
