@@ -19,12 +19,13 @@
 // all-reduce.
 //
 // All-reduce, deterministic: (1) each CTA stores its tau + 1 partials to global
-// memory and publishes a flag with release semantics; (2) CTA rank r of a cluster
-// waits for every flag (acquire) and sums the entries [r E, (r + 1) E) over all
-// CTAs in a fixed order; (3) it stores those sums into the shared memory of every
-// CTA of its cluster with st.async, whose bytes complete on the destination's
-// mbarrier. Every wait is bounded (global timer); a CTA that gives up raises the
-// abort word, which ends the others' waits.
+// memory as self-validating words (payload and exchange tag in one 8-byte word);
+// (2) CTA rank r of a cluster reads the entries [r E, (r + 1) E) of every CTA,
+// re-reading the words whose tag is not current yet, and sums them over the CTAs in
+// a fixed order; (3) it stores those sums into the shared memory of every CTA of
+// its cluster with st.async, whose bytes complete on the destination's mbarrier.
+// Every wait is bounded (global timer); a CTA that gives up raises the abort word,
+// which ends the others' waits.
 //
 // Precision of the mixed form (T = TF = float): FP64 instructions take 64 cycles
 // (add, FMA) to about 100 (conversions) on this GPU, and every one of them on the
