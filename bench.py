@@ -214,10 +214,10 @@ def run_reference(args):
 
 # ncu DRAM traffic (read + write) per launch, taken on the X 20000 x 4096 profiling
 # case (profiles/): the iteration kernel does not touch X, so its bytes do not depend
-# on n (672.9 MB read + 3.3 MB written by a launch of 150 iterations, scaled to the
-# launch's iterations); the refresh product reads X once, so its
-# traffic scales with n (327.8 MB read + 2.9 MB written at n = 20000, times 5)
-PROFILED_TRAFFIC = {"iterate": lambda its_per_launch: 676.2e6 * its_per_launch / 150.0,
+# on n (1799.5 MB read + 3.3 MB written by a launch of 400 iterations, scaled to the
+# launch's iterations); the refresh product reads X once, so its traffic scales with
+# n (327.8 MB read + 2.9 MB written at n = 20000, times 5)
+PROFILED_TRAFFIC = {"iterate": lambda its_per_launch: 1802.8e6 * its_per_launch / 400.0,
                     "refresh": lambda its_per_launch: 330.7e6 * N_ROWS / 20000.0}
 
 
