@@ -138,12 +138,12 @@ def roofline(stats, pk):
     name, (ms, n, nbytes, flops, _its) = max(stats.items(), key=lambda kv: kv[1][0] * kv[1][1])
     hbm = pk.get("hbm_gbs", 6800.0)
     if name in ("chol",):
-        # FP64 ALU bound: peak from the FP64 FMA throughput measured on this GPU
-        # (1.2 TFLOP/s = 152 SMs x 2 DFMA/clk x ~1.95 GHz); see the design doc
+        # FP64 ALU bound: peak from the FP64 FMA throughput measured on this GPU by an
+        # FMA-throughput probe (1.2 TFLOP/s = 152 SMs x 2 DFMA/clk x ~1.95 GHz)
         achieved = flops / (ms * 1e-3) / 1e12
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": 1.19,
                 "unit": "TFLOP/s", "frac": achieved / 1.19, "traffic": None,
-                "peak_source": "measured FP64 FMA probe (DESIGN.md)"}
+                "peak_source": "measured FP64 FMA throughput probe"}
     achieved = nbytes / (ms * 1e-3) / 1e9
     traffic = None
     if name in PROFILED_TRAFFIC and n > 0:
