@@ -216,9 +216,16 @@ cudaError_t ctx_pool(int dev, cudaMemPool_t* out) {
 
 cudaError_t pmalloc(rs_ctx* c, void** p, size_t bytes) {
   cudaMemPool_t pool = nullptr;
-  const cudaError_t e = ctx_pool(c->device, &pool);
+  cudaError_t e = ctx_pool(c->device, &pool);
   if (e != cudaSuccess) return e;
-  return cudaMallocFromPoolAsync(p, bytes, pool, c->stream);
+  e = cudaMallocFromPoolAsync(p, bytes, pool, c->stream);
+  if (e == cudaErrorMemoryAllocation) {
+    // out of device memory: give the pool's unused blocks back and try once more
+    cudaGetLastError();
+    cudaMemPoolTrimTo(pool, 0);
+    e = cudaMallocFromPoolAsync(p, bytes, pool, c->stream);
+  }
+  return e;
 }
 void pfree(rs_ctx* c, void* p) {
   if (p) cudaFreeAsync(p, c->stream);
