@@ -247,7 +247,10 @@ rs_status rs_step(rs_ctx* ctx, int64_t n_iters, double* hist_out);
 rs_status rs_true_residual(rs_ctx* ctx, const double* v, double* rel_out);
 
 /* Device time of the last rs_solve (ms), split into setup (forming A, b in
- * rs_create) and iterations. Either pointer may be NULL. */
+ * rs_create; for FP32 X on the device it includes the context's copy of X, and for
+ * FP32 X in host memory with n >= 16384 on the mixed primal path it includes the
+ * upload of X, which that setup overlaps with its arithmetic) and iterations. Either
+ * pointer may be NULL. */
 rs_status rs_timings(const rs_ctx* ctx, double* setup_ms, double* solve_ms);
 
 /* Per-kernel device time of the iteration (measurement hook). */
