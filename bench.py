@@ -120,6 +120,19 @@ def one_solve(rs, X, y, precision, sketch, device, w_out, on_host=False, chol_fp
             "solve_ms": solve_ms, "final_rel": float(hist[-1]), "w": w}
 
 
+def aggregate_replicas(dist, solve_s, step_ms, iters, device):
+    """Replicas (one independent problem per rank): the slowest rank's solve and step
+    times, the iterations of all ranks."""
+    import torch
+
+    t = torch.tensor([solve_s, step_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    it = torch.tensor([float(iters)], device=device, dtype=torch.float64)
+    dist.all_reduce(it)
+    s, m = t.tolist()
+    return s, m, int(it.item())
+
+
 def profile_kernels(rs, X, y, device):
     """Per-kernel mean device time of the chosen form (CUDA events on the solver's
     stream), continuing from the converged state's first iterations."""
@@ -467,12 +480,7 @@ def main():
     solve_s = sum(r["solve_ms"] for r in runs) / 1e3
     step_ms = sum(r["ms"] for r in runs) / len(runs)
     if dist:
-        t = torch.tensor([solve_s, step_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        solve_s, step_ms = t.tolist()
-        it = torch.tensor([iters], device=dev, dtype=torch.float64)
-        dist.all_reduce(it)
-        iters = int(it.item())
+        solve_s, step_ms, iters = aggregate_replicas(dist, solve_s, step_ms, iters, dev)
     value = iters / solve_s
     if rank != 0:
         dist.destroy_process_group()
