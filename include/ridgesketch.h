@@ -292,8 +292,11 @@ rs_status rs_profile_iteration(rs_ctx* ctx, int64_t reps, rs_kernel_stat* out, i
  * device current), so make the first call before any stream capture. All calls share
  * the array: calls that overlap on the GPU (other streams, other host threads) race
  * and give wrong results; serialise them. Every entry the kernels read is written by
- * the same call, so no clearing is needed between calls. Runs asynchronously on
- * `stream`; returns RS_ECUDA if a launch fails.
+ * the same call, so no clearing is needed between calls. The array's address is
+ * cached per device for the life of the process: after cudaDeviceReset on a device,
+ * that address (like every other device state of the library on that device) is no
+ * longer valid, so do not call this entry point on that device again. Runs
+ * asynchronously on `stream`; returns RS_ECUDA if a launch fails.
  */
 rs_status rs_gram_apply_noalloc(const float* X, int64_t n, int64_t d, const double* v,
                                 double* out, void* stream);

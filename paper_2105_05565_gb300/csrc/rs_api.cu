@@ -220,8 +220,14 @@ cudaError_t pmalloc(rs_ctx* c, void** p, size_t bytes) {
   if (e != cudaSuccess) return e;
   e = cudaMallocFromPoolAsync(p, bytes, pool, c->stream);
   if (e == cudaErrorMemoryAllocation) {
-    // out of device memory: give the pool's unused blocks back and try once more
+    // out of device memory: let the stream-ordered frees of every context on this
+    // device complete (the pool is shared, and a block whose free is still pending
+    // is not released by a trim), give the pool's unused blocks back, try once more
     cudaGetLastError();
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cap) == cudaSuccess &&
+        cap == cudaStreamCaptureStatusNone)
+      cudaDeviceSynchronize();
     cudaMemPoolTrimTo(pool, 0);
     e = cudaMallocFromPoolAsync(p, bytes, pool, c->stream);
   }

@@ -3,21 +3,19 @@
 // TF32 operands, FP32 accumulation in tensor memory. X is first copied transposed
 // (Xt = X^T, d x ldk, K = n contiguous and zero padded) so that both operands of
 // C = Xt Xt^T are K-major. The lower triangle is cut into 128 x 256 tiles (128 rows
-// ti, 256 columns tj, tj <= ti / 2); the two tiles of the row blocks 2a and 2a + 1
-// with the same column block form a cluster of two CTAs, which share that column
-// block: each CTA loads one 128-row half of it and multicasts the half into both
-// CTAs' shared memory, so a CTA reads 16 KB of A rows and 16 KB of B rows from L2
-// per 128 x 256 x 32 step (the operand stream from L2 bounds this kernel).
-//   warp 0 (one lane)  TMA producer: its A box and its multicast B half into a ring
-//                      of kStages stages; a stage is refilled once the MMAs of both
-//                      CTAs have released it (two arrivals on its `empty` barrier);
+// ti, 256 columns tj, tj <= ti / 2), one CTA per tile. Consecutive CTAs take the row
+// blocks 2a and 2a + 1 of the same column block, so the second read of that B block
+// is served from L2. Per 128 x 256 x 32 step a CTA reads 16 KB of A rows and 32 KB
+// of B rows (two 128-row boxes) into its own shared memory.
+//   warp 0 (one lane)  TMA producer: its A box and both B boxes into a ring of
+//                      kStages stages; a stage is refilled once the MMAs that read
+//                      it have retired (one arrival on its `empty` barrier);
 //   warp 1 (one lane)  MMA issuer: 4 x tcgen05.mma (M 128, N 256, K 8) per stage,
-//                      tcgen05.commit (multicast to both CTAs) frees the stage;
+//                      tcgen05.commit frees the stage;
 //   warps 0-3          epilogue: tcgen05.ld of the 128 x 256 FP32 accumulator (each
 //                      warp its 32 TMEM lanes), + lambda on the diagonal, to global.
 // The upper triangle is mirrored afterwards. Every mbarrier wait is bounded; on a
-// timeout the CTA records an error and stops issuing; both CTAs meet at a cluster
-// barrier before either releases its shared memory.
+// timeout the CTA records an error, stops issuing, and frees its tensor memory.
 #include <cuda.h>
 
 #include "rs_kernels.cuh"
@@ -31,7 +29,7 @@ constexpr int kBN = 256;                            // columns (the pair's B blo
 constexpr int kBK = 32;                             // K step: 32 fp32 = one 128-byte row
 constexpr int kStages = 4;
 constexpr int kABytes = kBM * kBK * 4;              // 16 KB
-constexpr int kBHalfBytes = (kBN / 2) * kBK * 4;    // 16 KB, one CTA's half of B
+constexpr int kBHalfBytes = (kBN / 2) * kBK * 4;    // 16 KB, one 128-row box of B
 constexpr int kStageBytes = kABytes + 2 * kBHalfBytes;  // 48 KB
 constexpr uint32_t kTmemCols = 256;
 constexpr uint64_t kWaitNs = 4000000000ull;  // 4 s bound of every wait
@@ -53,9 +51,7 @@ __device__ __forceinline__ uint64_t now_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// wait on phase `parity` (acquire at cluster scope: the peer's multicast bytes and
-// commits arrive on these barriers), bounded by kWaitNs of the global timer; false
-// on timeout
+// wait on phase `parity`, bounded by kWaitNs of the global timer; false on timeout
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t a = smem_u32(bar);
   uint64_t t0 = 0;
@@ -84,17 +80,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
       : "memory");
 }
-// the same box written at the same offset into the shared memory of every CTA of
-// `mask`, completing on the mbarrier at the same offset in each
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                               int x, int y, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::"
-      "cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
-      : "memory");
-}
-
 // UMMA shared-memory descriptor, K-major operand in the 128-byte swizzled layout
 // written by TMA: 8-row groups of 128-byte rows, 1024 bytes apart.
 __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
@@ -125,19 +110,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
           smem_u32(bar))
       : "memory");
 }
-// the same on the barrier at this offset in every CTA of `mask`
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
-      "[%0], %1;" ::"r"(smem_u32(bar)),
-      "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::
-                   : "memory");
-}
-
 }  // namespace
 
 // K steps [kb0, kb0 + nk); accumulate: add the tiles to A (a later range of rows of X),
@@ -148,32 +120,31 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
                                                    float* __restrict__ A, int64_t lda,
                                                    int32_t* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte alignment for the swizzled stages (the same offset in both CTAs)
+  // 1024-byte alignment for the swizzled stages
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-  uint32_t crank;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
-  constexpr uint16_t kBoth = 0x3;
+  const uint32_t crank = blockIdx.x & 1;
 
-  // cluster p: row blocks 2a + crank, column block tj <= a
+  // CTAs 2p and 2p + 1: row blocks 2a + crank, column block tj <= a
   const int64_t p = blockIdx.x / 2;
   int64_t a = 0;
   while ((a + 1) * (a + 2) / 2 <= p) ++a;
   const int64_t tj = p - a * (a + 1) / 2;
   const int row0 = (int)((2 * a + (int64_t)crank) * kBM), col0 = (int)(tj * kBN);
+  if (row0 >= d) return;  // the odd row block past the last one (uniform over the CTA)
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 2);  // released by the MMAs of both CTAs
+      mbar_init(&empty_bar[s], 1);  // released by the commit of the MMAs that read it
     }
     mbar_init(&done_bar, 1);
     s_abort = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");  // visible to TMA
   }
   if (wid == 0) {  // tensor memory for the 128 x 256 accumulator
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -184,11 +155,10 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  cluster_sync();  // the peer's barriers are initialised before anything reaches them
   const uint32_t tmem = s_tmem;
 
   if (wid == 0 && lane == 0) {
-    // producer: the own A box, and the own half of the shared B block into both CTAs
+    // producer: the A box and the two 128-row boxes of the B block
     int64_t kb = 0;
     for (; kb < nk; ++kb) {
       const int s = (int)(kb % kStages);
@@ -196,19 +166,11 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
       if (!mbar_wait(&empty_bar[s], ph ^ 1)) { s_abort = 1; atomicExch(err, 1); break; }
       if (*(volatile int*)&s_abort) break;
       unsigned char* st = base + s * kStageBytes;
-      mbar_arrive_expect_tx(&full_bar[s], kStageBytes);  // own A + both halves of B
-      tma_load_2d(st, &tmap, &full_bar[s], (int)((kb0 + kb) * kBK), row0);
-      tma_load_2d_mc(st + kABytes + crank * kBHalfBytes, &tmap, &full_bar[s],
-                     (int)((kb0 + kb) * kBK), col0 + (int)crank * (kBN / 2), kBoth);
-    }
-    // tail: every stage filled here has been released by both CTAs' MMAs, so no
-    // commit of the peer is still on its way to these barriers
-    if (kb == nk) {
-      for (int64_t t = nk; t < nk + kStages; ++t) {
-        const int s = (int)(t % kStages);
-        const uint32_t ph = (uint32_t)((t / kStages) & 1);
-        if (!mbar_wait(&empty_bar[s], ph ^ 1)) { s_abort = 1; atomicExch(err, 1); break; }
-      }
+      mbar_arrive_expect_tx(&full_bar[s], kStageBytes);  // A + both boxes of B
+      const int kx = (int)((kb0 + kb) * kBK);
+      tma_load_2d(st, &tmap, &full_bar[s], kx, row0);
+      tma_load_2d(st + kABytes, &tmap, &full_bar[s], kx, col0);
+      tma_load_2d(st + kABytes + kBHalfBytes, &tmap, &full_bar[s], kx, col0 + kBN / 2);
     }
   } else if (wid == 1 && lane == 0) {
     // MMA issuer
@@ -224,7 +186,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
       for (int ks = 0; ks < kBK / 8; ++ks)  // K = 8 tf32 = 32 bytes per MMA
         mma_tf32(tmem, umma_desc_sw128(sa + ks * 32), umma_desc_sw128(sb + ks * 32),
                  (kb > 0 || ks > 0) ? 1u : 0u);
-      mma_commit_mc(&empty_bar[s], kBoth);  // the stage is free in both CTAs' rings
+      mma_commit(&empty_bar[s]);  // the stage is free once these MMAs retire
     }
     mma_commit(&done_bar);  // arrives once every MMA issued above has retired
   }
@@ -267,7 +229,6 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(kTmemCols)
                  : "memory");
-  cluster_sync();  // neither CTA leaves while the other may still reach its shared memory
 }
 
 // Xt[i * ldk + k] = X[k * d + i] (zero for k >= n): 32 x 32 tiles through shared memory;
@@ -337,22 +298,15 @@ cudaError_t launch_gram_tc_rows(cudaStream_t st, const float* X, int64_t n, int6
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const int64_t T = (d + kBM - 1) / kBM;  // row blocks
   const int64_t Tp = (T + 1) / 2;         // row-block pairs
-  const int64_t clusters = Tp * (Tp + 1) / 2;
+  const int64_t pairs = Tp * (Tp + 1) / 2;  // (pair, column block) with tj <= pair
   const size_t smem = (size_t)kStages * kStageBytes + 1024;
   e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(2 * clusters));
+  cfg.gridDim = dim3((unsigned)(2 * pairs));
   cfg.blockDim = dim3(128);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_gram_tc, map, d, r0 / kBK, (k1 - r0) / kBK, lambda,
                             r0 > 0 ? 1 : 0, A, lda, err);
 }

@@ -61,3 +61,31 @@ def test_noalloc_rejects_sizes_beyond_its_work_space():
                                  None)
     assert st == rs.RS_EINVAL
     assert b"4096" in L.rs_last_error(None)
+
+
+def test_noalloc_small_problems_after_a_large_one():
+    """A large call fills all 64 block slots of the shared work space; the smaller
+    calls after it (fewer rows than blocks, one row, a narrower d) must not pick up
+    any of its stale block sums."""
+    import torch
+
+    import paper_2105_05565_gb300 as rs
+
+    L = rs.lib()
+    g = np.random.default_rng(7)
+    stream = torch.cuda.current_stream().cuda_stream
+    for n, d in [(2500, 4096), (10, 300), (1, 4096), (63, 1025), (2500, 4096), (1, 1)]:
+        X = g.standard_normal((n, d)).astype(np.float32)
+        v = g.standard_normal(d)
+        Xd = torch.from_numpy(X).cuda()
+        vd = torch.from_numpy(v).cuda()
+        out = torch.full((d,), float("nan"), dtype=torch.float64, device="cuda")
+        st = L.rs_gram_apply_noalloc(ctypes.c_void_p(Xd.data_ptr()), n, d,
+                                     ctypes.c_void_p(vd.data_ptr()),
+                                     ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream))
+        assert st == rs.RS_OK, L.rs_last_error(None)
+        torch.cuda.synchronize()
+        X64 = X.astype(np.float64)
+        ref = X64.T @ (X64 @ v)
+        got = out.cpu().numpy()
+        assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref), (n, d)
