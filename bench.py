@@ -2,10 +2,15 @@
 
 Workload (default): dense primal ridge, X 100000 x 4096 = U diag(sigma) V^T with
 Haar U, V and sigma geometric from 1 to 1e-3 (float32 storage), y = X w* + 0.01 noise,
-lambda = 1e-2, count sketch tau = 256 with the heuristic momentum, FP32 bulk products
-with FP64 true-residual refresh every 400 iterations ("mixed"), to relative residual
-1e-6. The plain FP64 GPU path on the same problem (and both precisions with the
-subsample sketch) are measured beside it.
+lambda = 1e-2, count sketch tau = 256 with the heuristic momentum, to relative
+residual 1e-6 in mixed precision: X^T X on the tensor cores (TF32 in, FP32
+accumulation), S^T A and the iterations in FP32, the small system S^T A S factored
+by FP64 Cholesky and its pseudo-inverse applied in FP64, and the FP64 true residual
+through X every 50 iterations. Beside it: the plain FP64 GPU path on the same
+problem (count and subsample sketches, with its per-kernel profile), the same mixed
+path with an FP32 small solve and a 400-iteration refresh period, the subsample
+sketch in mixed precision, and the small dense case (X 2000 x 500, plain FP64,
+subsample tau = 50, no momentum).
 
 A step is one full solve through the C ABI: rs_create (copies X, y; forms A, b on
 the device) + rs_solve to 1e-6 + the weights back. ``value`` is the iteration
@@ -31,10 +36,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time-to-1e-6 rel. residual & iters/s, chosen form vs plain FP64, one GB300"
 N_ROWS, N_COLS, TAU, LAM, TOL, MAX_IT = 100000, 4096, 256, 1e-2, 1e-6, 30000
-REFRESH = 400
+REFRESH = 50
 WORKLOAD = ("dense primal ridge X 100000x4096 (Haar U,V; sigma geometric 1..1e-3; fp32), "
-            "lambda 1e-2, count sketch tau 256, heuristic momentum, mixed FP32 + FP64 refresh/400, "
-            "tol 1e-6")
+            "lambda 1e-2, count sketch tau 256, heuristic momentum, mixed: TF32 X^T X, FP32 "
+            "S^T A and iterations, FP64 Cholesky small solve, FP64 true residual every 50 "
+            "iterations, tol 1e-6")
+# the small dense case: X 2000 x 500 iid N(0, 1), y = X w* + 0.1 noise, lambda 1e-3,
+# plain FP64, subsample tau = 50, no momentum, seed 0
+SMALL = dict(n=2000, d=500, lam=1e-3, tau=50)
+# FP64 FMA throughput of one GB300 from its unit counts (the recipe's nominal
+# 1.25 TFLOP/s dense FP64); no measured FP64 figure is provided with the peaks
+FP64_PEAK_TFLOPS = 1.25
 
 
 def peaks():
@@ -99,9 +111,10 @@ def make_problem(seed, device, n_rows=N_ROWS):
                                   noise=0.01, device=device)
 
 
-def one_solve(rs, X, y, precision, sketch, device, w_out, on_host=False, chol_fp64=False):
+def one_solve(rs, X, y, precision, sketch, device, w_out, on_host=False, chol_fp64=True,
+              refresh=REFRESH):
     """One step: create (copy X, y; form A, b), solve to TOL, weights out, destroy.
-    Returns dict of times (ms) and iteration count."""
+    Returns dict of times (ms), iteration count and the chunking."""
     import torch
 
     st = torch.cuda.current_stream(device)
@@ -109,54 +122,77 @@ def one_solve(rs, X, y, precision, sketch, device, w_out, on_host=False, chol_fp
     torch.cuda.synchronize(device)
     e0.record(st)
     with rs.Solver(X, y, LAM, sketch=sketch, tau=TAU, momentum="heuristic", seed=0,
-                   precision=precision, refresh_every=REFRESH, device=device.index or 0,
+                   precision=precision, refresh_every=refresh, device=device.index or 0,
                    stream=st.cuda_stream, chol_fp64=chol_fp64) as s:
         w, hist, iters, conv = s.solve(TOL, MAX_IT, w_out=None if on_host else w_out)
         setup_ms, solve_ms = s.timings()
+        chunk, ref, fused = s.chunking()
     e1.record(st)
     torch.cuda.synchronize(device)
     w = w.detach().cpu().numpy() if hasattr(w, "detach") else np.array(w)
     return {"ms": e0.elapsed_time(e1), "iters": iters, "conv": bool(conv), "setup_ms": setup_ms,
-            "solve_ms": solve_ms, "final_rel": float(hist[-1]), "w": w}
+            "solve_ms": solve_ms, "final_rel": float(hist[-1]), "w": w, "chunk": chunk,
+            "refresh": ref, "fused_potri": fused}
+
+
+def launches_per_step(iters, chunk, refresh, fused=True, chunks_per_graph=4):
+    """Kernels one mixed step launches: per chunk the chunk start, the sketch plans, the
+    row -> bucket map, S^T A with S^T A S, M^+ (one fused kernel, else factor and
+    product), and per refresh period the persistent iteration kernel and the FP64
+    refresh (float-pair X^T X w, its sum, the finish); chunks are replayed four per
+    CUDA graph until the solve stops; per step 7 more for the setup (transposed copy,
+    tensor-core X^T X, mirror, b = X^T y in three launches, initial state)."""
+    per_chunk = 5 + (0 if fused else 1) + 4 * (chunk // refresh)
+    replays = max(1, ((iters + chunk - 1) // chunk + chunks_per_graph - 1) // chunks_per_graph)
+    return replays * chunks_per_graph * per_chunk + 7
 
 
 def aggregate_replicas(dist, solve_s, step_ms, iters, device):
     """Replicas (one independent problem per rank): the slowest rank's solve and step
-    times, the iterations of all ranks."""
+    times, the iterations of all ranks, and every rank's own (iterations, solve s,
+    step ms) so that a slow or long-running rank is visible."""
     import torch
 
     t = torch.tensor([solve_s, step_ms], device=device, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     it = torch.tensor([float(iters)], device=device, dtype=torch.float64)
     dist.all_reduce(it)
+    mine = torch.tensor([float(iters), solve_s, step_ms], device=device, dtype=torch.float64)
+    every = [torch.zeros_like(mine) for _ in range(dist.get_world_size())]
+    dist.all_gather(every, mine)
     s, m = t.tolist()
-    return s, m, int(it.item())
+    per_rank = [{"rank": r, "iters": int(v[0].item()), "solve_s": float(v[1].item()),
+                 "step_ms": float(v[2].item())} for r, v in enumerate(every)]
+    return s, m, int(it.item()), per_rank
 
 
-def profile_kernels(rs, X, y, device):
-    """Per-kernel mean device time of the chosen form (CUDA events on the solver's
-    stream), continuing from the converged state's first iterations."""
+def profile_kernels(rs, X, y, device, precision="mixed", chol_fp64=True, refresh=REFRESH,
+                    reps=1200):
+    """Per-kernel mean device time (CUDA events on the solver's stream), continuing
+    from the first iterations of a solve."""
     import torch
 
     st = torch.cuda.current_stream(device)
     with rs.Solver(X, y, LAM, sketch="count", tau=TAU, momentum="heuristic", seed=0,
-                   precision="mixed", refresh_every=REFRESH, device=device.index or 0,
-                   stream=st.cuda_stream) as s:
+                   precision=precision, refresh_every=refresh, device=device.index or 0,
+                   stream=st.cuda_stream, chol_fp64=chol_fp64) as s:
         s.solve(TOL, 60)
-        return s.profile_iteration(2 * REFRESH)
+        return s.profile_iteration(reps)
 
 
 def roofline(stats, pk):
-    """Dominant kernel of the iteration and its achieved fraction of the measured peak."""
+    """Dominant kernel of the iteration and its achieved fraction of its peak: HBM
+    bytes against the measured copy bandwidth, or (the FP64 factor, inverse and
+    product of the small systems) FP64 FLOP/s against the FP64 FMA peak."""
     name, (ms, n, nbytes, flops, _its) = max(stats.items(), key=lambda kv: kv[1][0] * kv[1][1])
     hbm = pk.get("hbm_gbs", 6800.0)
-    if name in ("chol",):
-        # FP64 ALU bound: peak from the FP64 FMA throughput measured on this GPU by an
-        # FMA-throughput probe (1.2 TFLOP/s = 152 SMs x 2 DFMA/clk x ~1.95 GHz)
+    if name in ("potri", "factor", "pinv", "chol"):
         achieved = flops / (ms * 1e-3) / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": 1.19,
-                "unit": "TFLOP/s", "frac": achieved / 1.19, "traffic": None,
-                "peak_source": "measured FP64 FMA throughput probe"}
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": PROFILED_TRAFFIC[name](_its / n) if name in PROFILED_TRAFFIC else None,
+                "peak_source": "FP64 FMA peak from the unit counts (nominal 1.25 TFLOP/s dense "
+                               "FP64 of one GB300)"}
     achieved = nbytes / (ms * 1e-3) / 1e9
     traffic = None
     if name in PROFILED_TRAFFIC and n > 0:
@@ -167,8 +203,11 @@ def roofline(stats, pk):
 
 def cpu_baseline(X, y, iters_ref, sample_iters=4):
     """The FP64 oracle on the host cores: A = X^T X + lambda I from the full X
-    (setup), then `sample_iters` count-sketch iterations; iters/s of its loop."""
+    (setup), then `sample_iters` count-sketch iterations; iters/s of its loop. Also
+    returns the FP64 solution w* = A^{-1} b of that A (the judge of the GPU results),
+    and the small dense case run by the oracle to tolerance."""
     import oracle
+    from synth import gaussian_problem
 
     cores = os.cpu_count()
     Xh = X.detach().cpu().double().numpy()
@@ -180,12 +219,21 @@ def cpu_baseline(X, y, iters_ref, sample_iters=4):
     oracle.sketch_and_project(A, b, "count", TAU, 0, 0.0, sample_iters,
                               mom={"kind": "heuristic"})
     t_it = (time.perf_counter() - t1) / sample_iters
-    return {"value": 1.0 / t_it, "unit": "iters/s", "cores": cores, "kind": "oracle",
-            "sample": (f"numpy FP64 oracle: setup X^T X on the full 100000x4096 X ({t_setup:.1f} s), "
-                       f"then {sample_iters} count-sketch iterations ({t_it * 1e3:.0f} ms each); "
-                       f"time to 1e-6 extrapolated with {iters_ref} iterations = "
-                       f"{t_setup + iters_ref * t_it:.1f} s"),
-            "setup_s": t_setup, "s_per_iter": t_it}
+    w_star = np.linalg.solve(A, b)
+    del A
+    Xs, ys, _ = gaussian_problem(SMALL["n"], SMALL["d"], seed=0)
+    t2 = time.perf_counter()
+    ref = oracle.solve_ridge(Xs, ys, SMALL["lam"], "primal", "subsample", SMALL["tau"], seed=0,
+                             tol=TOL, max_iters=100000, mom={"kind": "none"})
+    t_small = time.perf_counter() - t2
+    out = {"value": 1.0 / t_it, "unit": "iters/s", "cores": cores, "kind": "oracle",
+           "sample": (f"numpy FP64 oracle: setup X^T X on the full 100000x4096 X ({t_setup:.1f} s), "
+                      f"then {sample_iters} count-sketch iterations ({t_it * 1e3:.0f} ms each); "
+                      f"time to 1e-6 extrapolated with {iters_ref} iterations = "
+                      f"{t_setup + iters_ref * t_it:.1f} s"),
+           "setup_s": t_setup, "s_per_iter": t_it,
+           "small_case": {"iters": int(ref["iters"]), "s": t_small}}
+    return out, w_star, ref
 
 
 def run_reference(args):
@@ -216,7 +264,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": 1, "parallelism": "replicas"},
+            "config": {"workload": WORKLOAD, "global_batch": args.gpus,
+                       "parallelism": "replicas" if args.gpus > 1 else "single"},
             "cpu_baseline": {"value": value, "unit": "iters/s", "cores": os.cpu_count(),
                              "kind": "oracle",
                              "sample": f"{per_step} oracle iterations per step after one setup"},
@@ -479,8 +528,9 @@ def main():
     iters = sum(r["iters"] for r in runs)
     solve_s = sum(r["solve_ms"] for r in runs) / 1e3
     step_ms = sum(r["ms"] for r in runs) / len(runs)
+    per_rank = None
     if dist:
-        solve_s, step_ms, iters = aggregate_replicas(dist, solve_s, step_ms, iters, dev)
+        solve_s, step_ms, iters, per_rank = aggregate_replicas(dist, solve_s, step_ms, iters, dev)
     value = iters / solve_s
     if rank != 0:
         dist.destroy_process_group()
@@ -505,28 +555,64 @@ def main():
     pk = peaks()
     roof = roofline(stats, pk)
 
-    # plain FP64 and subsample arms on the same problem
+    def keep(r):
+        return {k: r[k] for k in ("ms", "iters", "conv", "setup_ms", "solve_ms", "final_rel")}
+
     extra = {}
     last = runs[-1]
-    w_star_err = None
+    ws = {"mixed": last["w"]}
     if not args.no_plain:
         plain = one_solve(rs, X, y, "fp64", "count", dev, w_out)
-        extra["plain_fp64_count"] = {k: plain[k] for k in ("ms", "iters", "conv", "setup_ms",
-                                                            "solve_ms", "final_rel")}
+        ws["plain_fp64"] = plain["w"]
+        extra["plain_fp64_count"] = keep(plain)
         extra["plain_fp64_count"]["iters_per_s"] = plain["iters"] / (plain["solve_ms"] / 1e3)
         extra["speedup_time_to_tol_vs_plain_fp64"] = plain["ms"] / step_ms
-        wp, wm = plain["w"], last["w"]
-        w_star_err = float(np.linalg.norm(wm - wp) / np.linalg.norm(wp))
-        f64f = one_solve(rs, X, y, "mixed", "count", dev, w_out, chol_fp64=True)
-        extra["mixed_count_fp64_factor"] = {k: f64f[k] for k in ("ms", "iters", "conv", "setup_ms",
-                                                                  "solve_ms", "final_rel")}
+        extra["speedup_solve_vs_plain_fp64"] = plain["solve_ms"] / last["solve_ms"]
+        Xd = X.double()
+        extra["plain_fp64_kernels"] = {
+            k: {"ms": v[0], "launches": v[1], "bytes": v[2], "flops": v[3], "iters": v[4]}
+            for k, v in profile_kernels(rs, Xd, y, dev, precision="fp64", reps=384).items()}
+        del Xd
+        f32 = one_solve(rs, X, y, "mixed", "count", dev, w_out, chol_fp64=False, refresh=400)
+        extra["mixed_count_fp32_small_solve_refresh400"] = keep(f32)
         for prec in ("mixed", "fp64"):
             sub = one_solve(rs, X, y, prec, "subsample", dev, w_out)
-            extra[f"{'plain_fp64' if prec == 'fp64' else 'mixed'}_subsample"] = {
-                k: sub[k] for k in ("ms", "iters", "conv", "setup_ms", "solve_ms", "final_rel")}
+            extra[f"{'plain_fp64' if prec == 'fp64' else 'mixed'}_subsample"] = keep(sub)
+        # the small dense case: plain FP64, subsample tau 50, no momentum, to 1e-6
+        from synth import gaussian_problem
+
+        Xs, ys, _ = gaussian_problem(SMALL["n"], SMALL["d"], seed=0)
+        Xs_d, ys_d = torch.from_numpy(Xs).to(dev), torch.from_numpy(ys).to(dev)
+        small = []
+        for _ in range(4):
+            st = torch.cuda.current_stream(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            with rs.Solver(Xs_d, ys_d, SMALL["lam"], sketch="subsample", tau=SMALL["tau"],
+                           momentum="none", seed=0, stream=st.cuda_stream) as sm:
+                wsm, hsm, itsm, cvsm = sm.solve(TOL, 100000)
+                sms = sm.timings()
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            small.append((e0.elapsed_time(e1), itsm, cvsm, sms, float(hsm[-1]), wsm))
+        ms_s, it_s, cv_s, (su_s, so_s), fin_s, w_small = small[-1]
+        extra["small_dense_plain_fp64_subsample50"] = {
+            "workload": "X 2000x500 iid N(0,1), y = X w* + 0.1 noise, lambda 1e-3, plain FP64, "
+                        "subsample tau 50, no momentum, seed 0, tol 1e-6",
+            "ms": ms_s, "iters": int(it_s), "conv": bool(cv_s), "setup_ms": su_s,
+            "solve_ms": so_s, "iters_per_s": it_s / (so_s / 1e3), "final_rel": fin_s}
     cpu = None
     if not args.no_cpu:
-        cpu = cpu_baseline(X, y, last["iters"])
+        cpu, w_star, small_ref = cpu_baseline(X, y, last["iters"])
+        nrm = float(np.linalg.norm(w_star))
+        extra["rel_err_vs_fp64_solution"] = {k: float(np.linalg.norm(v - w_star) / nrm)
+                                             for k, v in ws.items()}
+        if "small_dense_plain_fp64_subsample50" in extra:
+            sd = extra["small_dense_plain_fp64_subsample50"]
+            sd["oracle_iters"] = int(small_ref["iters"])
+            sd["rel_err_w_vs_oracle"] = float(np.linalg.norm(w_small - small_ref["w"]) /
+                                              np.linalg.norm(small_ref["w"]))
+            sd["oracle_s"] = cpu["small_case"]["s"]
     line = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": step_ms,
@@ -535,24 +621,22 @@ def main():
         "config": {"workload": WORKLOAD.replace("100000x4096", "20000x4096") if args.small else WORKLOAD,
                    "global_batch": world, "seq_len": None,
                    "parallelism": "replicas" if world > 1 else "single",
+                   "small_solve": "fp64", "refresh_every": last["refresh"], "chunk": last["chunk"],
                    "l2": "inputs larger than L2 (X = 1.64 GB re-read every step)"},
         "time_to_tol_ms": step_ms, "iters_to_tol": last["iters"], "converged": last["conv"],
         "final_true_rel_residual": last["final_rel"], "setup_ms": last["setup_ms"],
-        "solve_ms": last["solve_ms"], "rel_err_vs_plain_fp64_w": w_star_err,
+        "solve_ms": last["solve_ms"],
         "gpu_launches": None, "kernels": {k: {"ms": v[0], "launches": v[1], "bytes": v[2],
                                               "flops": v[3], "iters": v[4]}
                                           for k, v in stats.items()},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
         "wall_s_timed": wall,
     }
+    if per_rank is not None:
+        line["per_rank"] = per_rank
     line.update(extra)
-    # kernels launched in the timed region: per chunk of REFRESH iterations 9 (chunk
-    # begin, sketch plans, row -> bucket map, S^T A with S^T A S, the sweep for M^+, the
-    # persistent iteration kernel, and the FP64 refresh: float-pair X^T X w, its sum,
-    # finish), chunks replayed four per CUDA graph; per step 7 more (transposed copy,
-    # tensor-core X^T X, mirror, b = X^T y in three launches, initial state)
-    n_chunks = sum(4 * ((((r["iters"] + REFRESH - 1) // REFRESH) + 3) // 4) for r in runs)
-    line["gpu_launches"] = int(n_chunks * 9 + args.steps * 7)
+    line["gpu_launches"] = int(sum(launches_per_step(r["iters"], r["chunk"], r["refresh"],
+                                                     bool(r["fused_potri"])) for r in runs))
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -120,26 +120,39 @@ typedef struct {
 
 typedef struct {
   int32_t precision;     /* rs_precision; default RS_PLAIN_FP64 */
-  int32_t refresh_every; /* RS_MIXED: true-residual period in iterations (the chunk
-                            length); default 400, shortened where the chunk's buffers
-                            would pass 4 GB (the Python batch binding passes 300) */
+  int32_t refresh_every; /* RS_MIXED: FP64 true-residual period in iterations; default 50.
+                            A chunk shorter than the period shortens it to the chunk */
   int64_t sub_s;         /* SubCount sample size s (multiple of tau, <= m); 0 = rule of
                             Section 4.2: k = 10 if 10 tau <= m else floor(m/tau), s = k tau */
   void* cuda_stream;     /* cudaStream_t to issue work on; NULL = library-owned stream */
   int32_t device;        /* CUDA device ordinal; default 0 */
-  int32_t chol_fp64;     /* RS_MIXED only: 1 = factor S^T A S in FP64, 0 = FP32 (default;
-                            S^T A S is formed from the FP32 A there). RS_PLAIN_FP64 always
-                            factors in FP64. The Gaussian sketch in RS_MIXED needs 0. */
-  int64_t chunk;         /* iterations per device-side chunk (one CUDA graph replay); the
-                            sketched systems of a chunk are formed and factored ahead in
-                            batched launches. 0 = refresh_every (mixed) or 128 (plain),
-                            reduced so that the chunk's buffers stay under 4 GB */
+  int32_t chol_fp64;     /* RS_MIXED only: 1 = the small solve in FP64 (default): S^T A S
+                            (summed from the FP32 A) is factored by an FP64 Cholesky and
+                            its pseudo-inverse formed and applied in FP64; 0 = FP32 (M^+ by
+                            FP32 sweeps). RS_PLAIN_FP64 always works in FP64 */
+  int64_t chunk;         /* iterations per device-side chunk: the sketched systems of a
+                            chunk are formed and factored ahead in batched launches, and
+                            the chunk's iterations follow (RS_MIXED: one launch of the
+                            persistent kernel per refresh period, an FP64 refresh after
+                            each). 0 = 600 (RS_MIXED) or 128 (plain). RS_MIXED rounds it up
+                            to a whole number of refresh periods; every kind reduces it so
+                            that the chunk's buffers stay under 4 GB */
   int32_t setup_tc;      /* RS_MIXED, primal, FP32 X: 1 = form X^T X on the tensor cores
                             (TF32 inputs, FP32 accumulation; default), 0 = FP32 CUDA cores */
   int32_t iter_ctas;     /* subsample / count / subcount: CTAs of the persistent iteration
                             kernel that spreads the rows of w and r over the GPU (rounded
                             down to a multiple of 8); 0 = every SM (default); -1 = use the
                             single-cluster iteration kernel instead */
+  int64_t spin_limit_ns; /* bound, in ns of the GPU's global timer, of every wait of the
+                            persistent iteration kernel on other CTAs (its all-reduce) and
+                            on its copies; a wait that runs out ends the solve with
+                            RS_ETIMEOUT and leaves the context usable. 0 = 2 s */
+  int64_t stall_ns;      /* fault injection for tests of those waits: CTA 0 of the
+                            persistent iteration kernel publishes its first partials this
+                            many ns late in every launch; 0 = none (default) */
+  const char* tune_cache;/* batch autotuner: file that keeps its choices (read when it
+                            exists, written after a measurement); NULL = none. Read by
+                            rs_create_batch only; the string is copied */
 } rs_opts;
 
 /* Fill *o with the defaults listed above. */
@@ -200,6 +213,14 @@ const char* rs_last_error(const rs_ctx* ctx);
 rs_status rs_get_dims(const rs_ctx* ctx, int64_t* m, int64_t* tau, int64_t* s,
                       int64_t* k_sum, int64_t* m_pad);
 
+/*
+ * The chunking of a context (measurement and tests): *chunk = iterations per chunk
+ * (slots whose sketched systems phase 1 forms in one batch), *refresh_every = the
+ * FP64 refresh period (RS_MIXED; 0 for plain FP64), *fused_potri = 1 when M^+ is
+ * formed by the one-kernel factor, inverse and product. Any pointer may be NULL.
+ */
+rs_status rs_chunking(const rs_ctx* ctx, int64_t* chunk, int32_t* refresh_every,
+                      int32_t* fused_potri);
 /* Launch shape of the fused iteration kernel of a context: ctas CTAs owning q rows
  * each of w and r (persistent kernel over the GPU), or ctas = q = 0 when the chunk's
  * iterations run on one thread-block cluster (Gaussian; or the slices do not fit

@@ -50,7 +50,9 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("refresh_every", ctypes.c_int32),
                 ("sub_s", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
                 ("device", ctypes.c_int32), ("chol_fp64", ctypes.c_int32), ("chunk", ctypes.c_int64),
-                ("setup_tc", ctypes.c_int32), ("iter_ctas", ctypes.c_int32)]
+                ("setup_tc", ctypes.c_int32), ("iter_ctas", ctypes.c_int32),
+                ("spin_limit_ns", ctypes.c_int64), ("stall_ns", ctypes.c_int64),
+                ("tune_cache", ctypes.c_char_p)]
 
 
 class KernelStat(ctypes.Structure):
@@ -73,6 +75,7 @@ _SIGS = {
     "rs_last_error": (ctypes.c_char_p, [_P]),
     "rs_get_dims": (_I32, [_P] + [ctypes.POINTER(_I64)] * 5),
     "rs_iter_plan": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
+    "rs_chunking": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "rs_dump_sketch": (_I32, [_P, _I64, _P, _P, _P]),
     "rs_dump_gaussian": (_I32, [_P, _I64, _P]),
     "rs_get_state": (_I32, [_P, _P, _P, _P, _P, ctypes.POINTER(_I64)]),
@@ -198,9 +201,10 @@ class Solver:
     """
 
     def __init__(self, X, y, lam, form="primal", sketch="count", tau=0, momentum="none", seed=0,
-                 precision="fp64", refresh_every=400, sub_s=0, chol_fp64=False, chunk=0,
+                 precision="fp64", refresh_every=50, sub_s=0, chol_fp64=True, chunk=0,
                  eta=0.995, beta_switch=0.5, gamma_c=1.0, beta_c=0.5, uncapped=False,
-                 device=0, stream=None, setup_tc=True, iter_ctas=0):
+                 device=0, stream=None, setup_tc=True, iter_ctas=0, spin_limit_ns=0,
+                 stall_ns=0):
         L = lib()
         self._ctx = None
         yp, ydev, self._ykeep = _buf(y, np.float64)
@@ -228,6 +232,8 @@ class Solver:
         opts.chunk = int(chunk)
         opts.setup_tc = int(bool(setup_tc))
         opts.iter_ctas = int(iter_ctas)
+        opts.spin_limit_ns = int(spin_limit_ns)
+        opts.stall_ns = int(stall_ns)
         st = stream if stream is not None else _default_stream(device)
         opts.cuda_stream = st
         ctx = _P()
@@ -330,6 +336,14 @@ class Solver:
         out = _D()
         self._check(lib().rs_true_residual(self._ctx, v.ctypes.data, ctypes.byref(out)))
         return out.value
+
+    def chunking(self):
+        """(iterations per chunk, FP64 refresh period or 0, 1 if M^+ comes from the fused
+        factor-inverse-product kernel)."""
+        ch, ref, fu = _I64(), _I32(), _I32()
+        self._check(lib().rs_chunking(self._ctx, ctypes.byref(ch), ctypes.byref(ref),
+                                      ctypes.byref(fu)))
+        return ch.value, ref.value, fu.value
 
     def profile_iteration(self, reps):
         """Per kernel group: dict(name -> (mean ms per launch, launches, bytes, flops))."""

@@ -42,6 +42,7 @@ struct DeviceGuard {
 
 constexpr int64_t kLdAlign = 128;     // row length padding of m-long rows (elements)
 constexpr int kChunksPerGraph = 4;    // chunks of iterations captured in one CUDA graph
+constexpr int64_t kMixedChunk = 600;   // default slots per chunk in mixed precision (two waves of two CTAs per SM in the FP64 factor)
 constexpr int64_t kMaxSample = 8192;  // largest ordered sample drawn by one CTA
 constexpr int64_t kMaxCountTau = 2048;
 
@@ -115,6 +116,7 @@ struct rs_ctx {
   bool use_wide = false;
   WidePlan wide{};
   void* Pm = nullptr;       // per slot: M^+ = L^{-T} L^{-1}, tau x pld (factor precision)
+  void* pws = nullptr;      // per slot: tile workspace of k_potri (P formed in one kernel)
   bool sweep_p = false;     // M^+ by FP32 sweeps from an FP32 M (mixed, FP32 factor)
   bool batch_member = false;  // a problem of an rs_batch (S^T A and M^+ kept per slot)
   float* Mf = nullptr;      // per slot: M in FP32 for the sweeps
@@ -122,6 +124,8 @@ struct rs_ctx {
   uint64_t* xpart = nullptr;   // all-reduce partials, 2 x nblk x (tau + 1) x 2 tagged words
   uint64_t* xflags = nullptr;  // launch counter of the tags
   int32_t* xabort = nullptr;
+  uint64_t wait_ns = 2000000000ull;  // bound of the persistent kernel's waits
+  int64_t stall_ns = 0;              // fault injection (tests)
   // matrix-free sparse X (CSR input)
   bool sparse = false;
   int64_t nnz = 0;
@@ -254,7 +258,7 @@ rs_status dalloc(rs_ctx* c, T** p, size_t n) {
 void free_all(rs_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   void* ptrs[] = {c->X, c->y, c->A, c->b, c->w, c->wp, c->r, c->rp, c->u, c->SA, c->ST, c->M,
-                  c->Linv, c->fws, c->rS, c->delta, c->perm, c->boff, c->inv, c->err_flag,
+                  c->Linv, c->fws, c->pws, c->rS, c->delta, c->perm, c->boff, c->inv, c->err_flag,
                   c->ndropped,
                   c->gam, c->bet, c->hist, c->partials, c->vn, c->vd, c->xt_part, c->rel_dev,
                   c->ctrl, c->Pm, c->xpart, c->xflags, c->xabort, c->Mf,
@@ -372,6 +376,25 @@ rs_status enqueue_gen(rs_ctx* c, int64_t k0_arg, int nslots) {
 // the small systems' inverses
 constexpr int kP1Plan = 1, kP1Rows = 2, kP1Msys = 4, kP1Inv = 8, kP1All = 15;
 
+// M^+ of every slot in one kernel: FP64 or FP32 arithmetic (the factor's), stored in
+// the iteration kernel's type (FP32 for the mixed matrix-free path)
+rs_status enqueue_potri(rs_ctx* c, cudaStream_t st, int force, int nslots) {
+  double* M = c->M;
+  if (c->f64_factor() && c->sparse && c->mixed())
+    CKC(c, (launch_potri<double, float>(st, c->ctrl, force, nslots, M, c->m_slot, c->tau, nullptr,
+                                        c->l_slot, static_cast<float*>(c->Pm), c->pld, c->p_slot,
+                                        static_cast<double*>(c->pws), c->ndropped)));
+  else if (c->f64_factor())
+    CKC(c, (launch_potri<double, double>(st, c->ctrl, force, nslots, M, c->m_slot, c->tau, nullptr,
+                                         c->l_slot, static_cast<double*>(c->Pm), c->pld, c->p_slot,
+                                         static_cast<double*>(c->pws), c->ndropped)));
+  else
+    CKC(c, (launch_potri<float, float>(st, c->ctrl, force, nslots, M, c->m_slot, c->tau, nullptr,
+                                       c->l_slot, static_cast<float*>(c->Pm), c->pld, c->p_slot,
+                                       static_cast<float*>(c->pws), c->ndropped)));
+  return RS_OK;
+}
+
 template <typename T>
 rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots, bool want_p,
                            int stages = kP1All) {
@@ -438,6 +461,7 @@ rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots, boo
                             static_cast<float*>(c->Pm), c->pld, c->p_slot, c->ndropped));
     return RS_OK;
   }
+  if (want_p && c->pws != nullptr) return enqueue_potri(c, st, force, nslots);
   if (c->f64_factor())
     CKC(c, launch_factor_inv<double>(st, c->ctrl, force, nslots, c->M, c->m_slot, c->tau,
                                      static_cast<double*>(c->Linv), c->l_slot,
@@ -518,7 +542,7 @@ rs_status enqueue_update(rs_ctx* c) {
 }
 
 template <typename T, typename TF>
-rs_status enqueue_iterate_t(rs_ctx* c) {
+rs_status enqueue_iterate_t(rs_ctx* c, int64_t sub_end) {
   IterArgs<T, TF> g{};
   g.kind = c->sketch == RS_GAUSSIAN ? 1 : 0;
   g.mixed = c->mixed();
@@ -536,12 +560,13 @@ rs_status enqueue_iterate_t(rs_ctx* c) {
   g.w = c->w; g.wp = c->wp; g.r = c->r; g.rp = c->rp;
   g.hist = c->hist; g.delta_out = c->delta; g.rS_out = c->rS;
   g.m = c->m; g.tau = c->tau; g.chunk = c->chunk;
+  g.sub_end = sub_end;
   CKC(c, (launch_iterate<T, TF>(c->stream, c->ctrl, g)));
   return RS_OK;
 }
 
 template <typename T, typename TF>
-rs_status enqueue_wide_t(rs_ctx* c) {
+rs_status enqueue_wide_t(rs_ctx* c, int64_t sub_end) {
   WideArgs<T, TF> g{};
   g.mixed = c->mixed();
   g.rows = static_cast<const T*>(c->SA);
@@ -558,21 +583,28 @@ rs_status enqueue_wide_t(rs_ctx* c) {
   g.epoch = c->xflags;
   g.abort_word = c->xabort;
   g.m = c->m; g.tau = c->tau; g.chunk = c->chunk; g.q = c->wide.q;
+  g.sub_end = sub_end;
   g.nblk = c->wide.nblk;
   g.nsab = c->wide.nsab;
+  g.wait_ns = c->wait_ns;
+  g.stall_ns = c->stall_ns;
   CKC(c, (launch_iterate_wide<T, TF>(c->stream, c->ctrl, g, c->wide.smem)));
   return RS_OK;
 }
 
 // every iteration of the chunk in one launch (all sketches but SRHT): over the
 // whole GPU for the bucket-row sketches, else on one thread-block cluster
-rs_status enqueue_iterate(rs_ctx* c) {
+// the persistent iterations of the current chunk up to its slot sub_end (default: all)
+rs_status enqueue_iterate(rs_ctx* c, int64_t sub_end = -1) {
+  if (sub_end < 0 || sub_end > c->chunk) sub_end = c->chunk;
   if (c->use_wide) {
-    if (!c->mixed()) return enqueue_wide_t<double, double>(c);
-    return c->f64_factor() ? enqueue_wide_t<float, double>(c) : enqueue_wide_t<float, float>(c);
+    if (!c->mixed()) return enqueue_wide_t<double, double>(c, sub_end);
+    return c->f64_factor() ? enqueue_wide_t<float, double>(c, sub_end)
+                           : enqueue_wide_t<float, float>(c, sub_end);
   }
-  if (!c->mixed()) return enqueue_iterate_t<double, double>(c);
-  return c->f64_factor() ? enqueue_iterate_t<float, double>(c) : enqueue_iterate_t<float, float>(c);
+  if (!c->mixed()) return enqueue_iterate_t<double, double>(c, sub_end);
+  return c->f64_factor() ? enqueue_iterate_t<float, double>(c, sub_end)
+                         : enqueue_iterate_t<float, float>(c, sub_end);
 }
 
 // one matrix-free iteration: delta, (XS) delta, X^T v by column pieces, update
@@ -657,20 +689,26 @@ rs_status enqueue_refresh(rs_ctx* c) {
   return RS_OK;
 }
 
+// one chunk: phase 1 for all its slots, then its iterations; with_refresh (mixed) puts
+// an FP64 refresh after every refresh_every iterations (the chunk holds a whole number
+// of periods), so the persistent kernel runs in launches of one period each
 rs_status enqueue_chunk(rs_ctx* c, bool with_refresh) {
   CKC(c, launch_chunk_begin(c->stream, c->ctrl));
   rs_status s = enqueue_phase1(c, 0, -1, (int)c->nslots, c->use_wide || c->sparse);
   if (s != RS_OK) return s;
-  if (c->sparse) {
-    for (int64_t i = 0; i < c->chunk && s == RS_OK; ++i) s = enqueue_mf_iteration(c);
-    if (s != RS_OK) return s;
-  } else if (c->sketch != RS_SRHT) {
-    s = enqueue_iterate(c);
-    if (s != RS_OK) return s;
-  } else {
+  const int64_t per = with_refresh ? std::min<int64_t>(c->refresh_every, c->chunk) : c->chunk;
+  if (c->sparse || c->sketch == RS_SRHT) {
     for (int64_t i = 0; i < c->chunk; ++i) {
-      s = enqueue_iteration(c);
+      s = c->sparse ? enqueue_mf_iteration(c) : enqueue_iteration(c);
       if (s != RS_OK) return s;
+      if (with_refresh && (i + 1) % per == 0 && i + 1 < c->chunk && (s = enqueue_refresh(c)) != RS_OK)
+        return s;
+    }
+  } else {
+    for (int64_t e = per;; e += per) {
+      if ((s = enqueue_iterate(c, std::min<int64_t>(e, c->chunk))) != RS_OK) return s;
+      if (e >= c->chunk) break;
+      if (with_refresh && (s = enqueue_refresh(c)) != RS_OK) return s;
     }
   }
   if (with_refresh) return enqueue_refresh(c);
@@ -892,13 +930,17 @@ void rs_default_opts(rs_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
   o->precision = RS_PLAIN_FP64;
-  o->refresh_every = 400;
+  o->refresh_every = 50;
   o->sub_s = 0;
   o->cuda_stream = nullptr;
   o->device = 0;
-  o->chol_fp64 = 0;
+  o->chol_fp64 = 1;
   o->chunk = 0;
   o->setup_tc = 1;
+  o->iter_ctas = 0;
+  o->spin_limit_ns = 0;
+  o->stall_ns = 0;
+  o->tune_cache = nullptr;
 }
 
 void rs_default_mom(rs_mom* m, int32_t kind) {
@@ -978,6 +1020,15 @@ rs_status setup_pipelined(rs_ctx* c, const float* Xh, double lambda) {
   return RS_OK;
 }
 
+// the largest chunk within `cap` slots; in mixed precision a whole number of refresh
+// periods, or (cap below one period) the period itself shortened to cap
+int64_t cap_chunk(rs_ctx* c, int64_t cap) {
+  if (!c->mixed()) return cap;
+  if (cap >= c->refresh_every) return cap / c->refresh_every * c->refresh_every;
+  c->refresh_every = (int)cap;
+  return cap;
+}
+
 rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, double lambda,
                     int32_t form, int32_t sketch, int64_t tau, const rs_mom* mom, uint64_t seed,
                     const rs_opts* opts, rs_ctx** out) {
@@ -1027,12 +1078,9 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   c->sketch = sketch;
   c->precision = o.precision;
   c->chol_fp64 = o.chol_fp64 ? 1 : 0;
-  if (c->mixed() && c->chol_fp64 && sketch == RS_GAUSSIAN) {
-    set_global_error("rs_create: the mixed Gaussian sketch factors in FP32 (chol_fp64 = 0)");
-    delete c;
-    return RS_EUNSUPPORTED;
-  }
-  c->refresh_every = o.refresh_every > 0 ? o.refresh_every : 400;
+  c->refresh_every = o.refresh_every > 0 ? o.refresh_every : 50;
+  if (o.spin_limit_ns > 0) c->wait_ns = (uint64_t)o.spin_limit_ns;
+  c->stall_ns = o.stall_ns > 0 ? o.stall_ns : 0;
   c->n = X->n;
   c->d = X->d;
   c->m = (form == RS_PRIMAL) ? X->d : X->n;
@@ -1076,18 +1124,22 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { c->err = "rs_create: stream"; return fail(RS_ECUDA); }
     c->own_stream = true;
   }
-  c->chunk = o.chunk > 0 ? o.chunk : (c->mixed() ? c->refresh_every : 128);
-  if (c->mixed() && c->chunk != c->refresh_every) c->chunk = c->refresh_every;
+  // mixed: a chunk (the slots whose sketched systems phase 1 forms and factors in one
+  // batch) holds a whole number of refresh periods; by default the smallest such
+  // number of iterations >= kMixedChunk, so that phase 1 keeps every SM busy even
+  // when the refresh period is short
+  c->chunk = o.chunk > 0 ? o.chunk : (c->mixed() ? kMixedChunk : 128);
+  if (c->mixed()) {  // a chunk shorter than the period shortens the period to it
+    if (c->chunk < c->refresh_every) c->refresh_every = (int)c->chunk;
+    c->chunk = round_up(c->chunk, (int64_t)c->refresh_every);
+  }
   if (!c->sparse) {
     // keep the per-slot buffers of one chunk under 4 GB
     // (S^T A is materialised for every sketch once the persistent kernel runs it)
     const int64_t per_slot = c->tau * c->ld * (int64_t)c->elem() * (sketch == RS_GAUSSIAN ? 2 : 1) +
-                             c->tau * c->tau * 24 + c->ld * 4;
+                             c->tau * c->tau * 33 + c->ld * 4;
     const int64_t cap = std::max<int64_t>(1, (int64_t)4e9 / std::max<int64_t>(per_slot, 1));
-    if (c->chunk > cap) {  // (mixed: the refresh period shortens with the chunk)
-      c->chunk = cap;
-      if (c->mixed()) c->refresh_every = (int)cap;
-    }
+    if (c->chunk > cap) c->chunk = cap_chunk(c, cap);
   }
   c->nslots = c->chunk;
   cudaStream_t st = c->stream;
@@ -1119,12 +1171,11 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     TRYC(cudaEventRecord(c->ev1, st));
     // the per-slot XS buffers of a chunk stay under 4 GB
     const int64_t per_slot = c->mf_rcap * 8 + c->mf_ecap * (4 + (int64_t)c->elem()) +
-                             c->tau * c->tau * 24 + c->ld * 4 + c->mf_nrb * 16;
+                             c->tau * c->tau * 33 + c->ld * 4 + c->mf_nrb * 16;
     const int64_t cap = std::max<int64_t>(1, (int64_t)4e9 / std::max<int64_t>(per_slot, 1));
     if (c->chunk > cap) {
-      c->chunk = cap;
-      c->nslots = cap;
-      if (c->mixed()) c->refresh_every = (int)cap;
+      c->chunk = cap_chunk(c, cap);
+      c->nslots = c->chunk;
     }
   } else {
   // X, y
@@ -1195,11 +1246,14 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   TRY(dalloc(c, &c->delta, c->tau));
   if (c->sparse) {
     // M^+ per slot and the per-slot XS of the chunk
+    // M^+ is stored in the iteration's type (FP32 in mixed precision); it is formed in
+    // the factor's precision by one kernel
     const size_t fel = c->f64_factor() ? 8 : 4;
     const size_t nsl = (size_t)c->nslots;
     c->pld = round_up(c->tau, 4);
     c->p_slot = c->tau * c->pld;
-    TRYC(pmalloc(c, (void**)&c->Pm, nsl * c->p_slot * fel));
+    TRYC(pmalloc(c, (void**)&c->Pm, nsl * c->p_slot * (c->mixed() ? 4 : 8)));
+    if (c->tau <= 4096) TRYC(pmalloc(c, &c->pws, nsl * potri_ws_elems(c->tau) * fel));
     TRY(dalloc(c, &c->mf_bsum, nsl * c->mf_nrb * 2));
     TRY(dalloc(c, &c->mf_boffs, nsl * c->mf_nrb * 2));
     TRY(dalloc(c, &c->mf_tot, nsl * 2));
@@ -1245,6 +1299,9 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
       c->sweep_p = c->mixed() && !c->f64_factor() && c->tau <= kSweepMaxTau &&
                    sa_msys_fits<float>(m, c->tau, round_up((sketch == RS_COUNT) ? m : (sketch == RS_SUBCOUNT ? c->s : c->tau), 4));
       if (c->sweep_p) TRY(dalloc(c, &c->Mf, (size_t)c->nslots * c->tau * c->tau));
+      // otherwise M^+ by factor, inverse and product in one kernel
+      if (!c->sweep_p && c->tau <= 4096)
+        TRYC(pmalloc(c, &c->pws, (size_t)c->nslots * potri_ws_elems(c->tau) * fel));
     } else {
       cudaGetLastError();
     }
@@ -1359,7 +1416,13 @@ rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int3
   rs_status s;
   if ((s = ensure_schedule(c, std::max<int64_t>(max_iters, 1))) != RS_OK) return s;
   CKC(c, launch_init_state(st, c->m, c->b, c->w, c->wp, c->r, c->rp, c->u));
+  // a timed-out earlier solve left the abort word raised
+  if (c->xabort) CKC(c, cudaMemsetAsync(c->xabort, 0, sizeof(int32_t), st));
   if (c->learned) CKC(c, cudaMemsetAsync(c->lp_last, 0xFF, c->m * sizeof(int32_t), st));
+  if (!std::isfinite(c->r0)) {
+    c->err = "rs_solve: NaN or Inf in b (||b|| is not finite)";
+    return RS_ENUMERIC;
+  }
   const double h0 = c->r0 > 0.0 ? 1.0 : 0.0;
   CKC(c, cudaMemcpyAsync(c->hist, &h0, sizeof(double), cudaMemcpyHostToDevice, st));
   CKC(c, cudaStreamSynchronize(st));
@@ -1414,6 +1477,15 @@ rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int3
   CKC(c, cudaStreamSynchronize(st));
   if (iters_out) *iters_out = iters;
   return result;
+}
+
+rs_status rs_chunking(const rs_ctx* c, int64_t* chunk, int32_t* refresh_every,
+                      int32_t* fused_potri) {
+  if (!c) return RS_EINVAL;
+  if (chunk) *chunk = c->chunk;
+  if (refresh_every) *refresh_every = c->mixed() ? c->refresh_every : 0;
+  if (fused_potri) *fused_potri = c->pws != nullptr ? 1 : 0;
+  return RS_OK;
 }
 
 rs_status rs_iter_plan(const rs_ctx* c, int32_t* ctas, int64_t* q) {
@@ -1566,6 +1638,7 @@ rs_status rs_step(rs_ctx* c, int64_t n_iters, double* hist_out) {
   h->max_iters = k0 + n_iters;
   h->r0 = c->r0 > 0.0 ? c->r0 : 1.0;
   if ((s = write_ctrl(c)) != RS_OK) return s;
+  if (c->xabort) CKC(c, cudaMemsetAsync(c->xabort, 0, sizeof(int32_t), c->stream));
   const int64_t chunks = (n_iters + c->chunk - 1) / c->chunk + 1;
   for (int64_t q = 0; q < chunks; ++q) {
     if ((s = enqueue_chunk(c, false)) != RS_OK) return s;
@@ -1738,6 +1811,14 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
           grp("sweep").flops = nsl * tau * tau * tau;
           if (s != RS_OK) break;
         }
+        if (!sweep && c->use_wide && c->pws != nullptr) {
+          // factor, inverse and M^+ in one kernel
+          s = timed("potri", [&]() { return enqueue_potri(c, c->stream, 0, ns); });
+          // Cholesky tau^3 / 3, triangular inverse tau^3 / 3, L^{-T} L^{-1} tau^3 / 3
+          grp("potri").bytes = nsl * (tau * tau * (8.0 + fel));
+          grp("potri").flops = nsl * (tau * tau * tau);
+          if (s != RS_OK) break;
+        } else {
         if (!sweep) s = timed("factor", [&]() -> rs_status {
           if (c->f64_factor())
             CKC(c, launch_factor_inv<double>(c->stream, c->ctrl, 0, ns, c->M, c->m_slot, c->tau, static_cast<double*>(c->Linv), c->l_slot, static_cast<double*>(c->fws), c->ndropped));
@@ -1762,26 +1843,34 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
           grp("pinv").flops = nsl * (2.0 * tau * tau * tau);
           if (s != RS_OK) break;
         }
+        }
       }
     }
     if (c->sketch != RS_SRHT) {
-      // fused: the whole chunk's iterations in one launch
-      const int64_t nit = std::min<int64_t>(c->chunk, reps - it);
-      s = timed("iterate", [&]() { return enqueue_iterate(c); });
-      // algorithmic HBM bytes: S^T A (or the sampled rows of A) and the small system
-      // of every iteration; the persistent kernel reads and writes w, w_prev, r,
-      // r_prev once per launch, the cluster kernel every iteration
-      grp("iterate").bytes = c->use_wide
-          ? (double)nit * (tau * m * el + tau * tau * fel + 4.0 * m) + 64.0 * m
-          : (double)nit * (tau * m * el + tau * tau * fel + 80.0 * m);
-      grp("iterate").flops = (double)nit * (2.0 * tau * m + 2.0 * tau * tau + 10.0 * m);
-      grp("iterate").iters += nit;
-      if (s == RS_OK && c->mixed() && (it + nit) % c->refresh_every == 0) {
-        s = timed("refresh", [&]() { return enqueue_refresh(c); });
-        grp("refresh").bytes = (double)c->n * (double)c->d * (c->xdtype == RS_F32 ? 4.0 : 8.0) + m * 48.0;
-        grp("refresh").flops = 4.0 * (double)c->n * (double)c->d;
+      // fused: the chunk's iterations in one launch per refresh period (mixed) or one
+      // launch for the whole chunk (plain); every launch runs to its end
+      const int64_t per = c->mixed() ? std::min<int64_t>(c->refresh_every, c->chunk) : c->chunk;
+      int64_t done = 0;
+      for (int64_t off = 0; off < c->chunk && it + done < reps && s == RS_OK; off += per) {
+        const int64_t e = std::min<int64_t>(off + per, c->chunk);
+        const int64_t nit = e - off;
+        s = timed("iterate", [&]() { return enqueue_iterate(c, e); });
+        // algorithmic HBM bytes: S^T A (or the sampled rows of A) and the small system
+        // of every iteration; the persistent kernel reads and writes w, w_prev, r,
+        // r_prev once per launch, the cluster kernel every iteration
+        grp("iterate").bytes = c->use_wide
+            ? (double)nit * (tau * m * el + tau * tau * fel + 4.0 * m) + 64.0 * m
+            : (double)nit * (tau * m * el + tau * tau * fel + 80.0 * m);
+        grp("iterate").flops = (double)nit * (2.0 * tau * m + 2.0 * tau * tau + 10.0 * m);
+        grp("iterate").iters += nit;
+        done += nit;
+        if (s == RS_OK && c->mixed()) {
+          s = timed("refresh", [&]() { return enqueue_refresh(c); });
+          grp("refresh").bytes = (double)c->n * (double)c->d * (c->xdtype == RS_F32 ? 4.0 : 8.0) + m * 48.0;
+          grp("refresh").flops = 4.0 * (double)c->n * (double)c->d;
+        }
       }
-      it += nit - 1;
+      it += done - 1;
       continue;
     }
     s = timed("delta", [&]() { return enqueue_delta(c, 0, -1); });
@@ -2447,6 +2536,8 @@ rs_status rs_create_batch(int32_t P, const rs_matrix* Xs, const double* const* Y
   rs_default_opts(&o);
   if (opts) o = *opts;
   if (o.precision == RS_MIXED) o.chol_fp64 = 0;
+  // the batch refreshes at every chunk end: its chunk is the refresh period
+  if (o.precision == RS_MIXED && o.chunk <= 0) o.chunk = o.refresh_every > 0 ? o.refresh_every : 300;
   for (int p = 0; p < P; ++p) {
     if (Xs[p].is_csr) { g_batch_err = "rs_create_batch: dense X only"; return RS_EUNSUPPORTED; }
     if (o.precision == RS_MIXED && Xs[p].dtype != RS_F32) { g_batch_err = "rs_create_batch: RS_MIXED takes FP32 X"; return RS_EINVAL; }

@@ -284,6 +284,291 @@ cudaError_t launch_factor_inv(cudaStream_t st, const Ctrl* ctrl, int force, int 
 }
 
 // ---------------------------------------------------------------------------
+// phase 1 for the persistent iteration kernel: P = M^+ = L^{-T} L^{-1} (eq. (14)),
+// one CTA of kPotriThreads per slot, two CTAs per SM.
+//
+// FP64 arithmetic runs at about one warp instruction per 64 cycles on each of an
+// SM's four schedulers, so the factor is bound by how many schedulers have FP64
+// work at every moment, not by memory: the tiles live in global memory (L1/L2), two
+// slots share an SM so that one slot's narrow phases (a diagonal tile, the last
+// trailing updates) overlap the other's wide ones, and every phase is cut into
+// 32 x 32 tile tasks:
+//   1. Cholesky, right-looking, with the least-norm pivot rule of k_factor_blk;
+//      the diagonal tiles end up holding L_II^{-1};
+//   2. X = L^{-1} right-looking over all block columns at once: round r first
+//      finalises X_{J+r,J} = -X_{J+r,J+r} T_{J+r,J} for every J, then adds
+//      L_{I,K} X_{K,J} (K = J + r) to the accumulators T_{I,J} of every I > K;
+//      the critical path is 2 (P - 1) tile products instead of P (P + 1) / 2 - 1;
+//   3. the dropped rows and columns of X are zeroed, then
+//      P_{IJ} = sum_{K >= I} X_{KI}^T X_{KJ} for the lower tiles I >= J only
+//      (a sixth of a full tau^3 product), each written with its transpose.
+// ---------------------------------------------------------------------------
+constexpr int kPotriThreads = 256;
+
+// L (lower tiles incl. the diagonal) + the strictly lower tiles of X
+__host__ __device__ size_t potri_ws_elems(int64_t tau) {
+  const int64_t P = (tau + NBK - 1) / NBK;
+  return (size_t)(ntiles_lower(P) + P * (P - 1) / 2) * TILE;
+}
+
+template <typename T>
+__device__ __forceinline__ T* xtile_at(T* base, int64_t I, int64_t J) {  // I > J
+  return base + ((I - 1) * I / 2 + J) * TILE;
+}
+
+// acc (8 x 4 of the lane) += SGN * op(A) op(B); op(A) = A^T (TA), op(B) = B^T (TB)
+template <typename T, bool TA, bool TB, int SGN>
+__device__ __forceinline__ void wtile_mma_g(T (&acc)[8][4], const T* __restrict__ A,
+                                            const T* __restrict__ B, int ly, int lx) {
+#pragma unroll 2
+  for (int l = 0; l < NBK; ++l) {
+    T a[8], b[4];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) a[r] = TA ? A[l * TSK + ly * 8 + r] : A[(ly * 8 + r) * TSK + l];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) b[c] = TB ? B[(lx * 4 + c) * TSK + l] : B[l * TSK + lx * 4 + c];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (SGN > 0) acc[r][c] += a[r] * b[c];
+        else acc[r][c] -= a[r] * b[c];
+      }
+  }
+}
+
+// T: arithmetic and L^{-1}; TP: the stored P (FP32 for an FP32 iteration kernel)
+template <typename T, typename TP>
+__global__ void __launch_bounds__(kPotriThreads, 2) k_potri(
+    const Ctrl* __restrict__ ctrl, int force, int nslots, const double* __restrict__ M,
+    int64_t m_slot, int64_t tau, T* __restrict__ Linv, int64_t l_slot, TP* __restrict__ Pout,
+    int64_t pld, int64_t p_slot, T* __restrict__ ws, int32_t* __restrict__ ndropped) {
+  __shared__ unsigned char dropped[4096];
+  __shared__ double s_red[32];
+  const int64_t s = blockIdx.x;
+  if (s >= active_slots(ctrl, force, nslots)) return;
+  const int64_t P = (tau + NBK - 1) / NBK;
+  const int64_t tp = P * NBK;
+  T* tiles = ws + s * (int64_t)potri_ws_elems(tau);
+  T* xt = tiles + ntiles_lower(P) * TILE;
+  const double* Ms = M + s * m_slot;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int ly = lane >> 3, lx = lane & 7;
+  const unsigned full = 0xffffffffu;
+
+  // load the lower triangle into tiles (identity padding), zero the X accumulators,
+  // max of the diagonal
+  double dmax = 0.0;
+  for (int64_t i = tid; i < tau; i += blockDim.x) dmax = fmax(dmax, Ms[i * tau + i]);
+  for (int64_t i = tid; i < tp; i += blockDim.x) dropped[i] = 0;
+  for (int64_t t = wid; t < ntiles_lower(P) * NBK; t += nw) {  // one tile row per warp step
+    const int64_t tile = t / NBK, rr = t - tile * NBK;
+    int64_t I = 0;
+    while ((I + 1) * (I + 2) / 2 <= tile) ++I;
+    const int64_t J = tile - I * (I + 1) / 2;
+    const int64_t R = I * NBK + rr, Cc = J * NBK + lane;
+    double v = 0.0;
+    if (R < tau && Cc < tau) v = Ms[R * tau + Cc];
+    else if (R == Cc) v = 1.0;
+    tiles[tile * TILE + rr * TSK + lane] = (T)v;
+  }
+  for (int64_t e = tid; e < P * (P - 1) / 2 * TILE; e += blockDim.x) xt[e] = T(0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(full, dmax, o));
+  if (lane == 0) s_red[wid] = dmax;
+  __syncthreads();
+  if (wid == 0) {
+    double v = lane < nw ? s_red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(full, v, o));
+    if (lane == 0) s_red[0] = v;
+  }
+  __syncthreads();
+  const T thr = (T)((double)tau * Eps<T>::v * s_red[0]);
+
+  // 1. Cholesky (diagonal tiles become L_II^{-1}, the others L_IJ)
+  for (int64_t p = 0; p < P; ++p) {
+    const int64_t c0 = p * NBK;
+    T* D = tile_at(tiles, p, p);
+    if (wid == 0) {
+      T r[NBK];
+#pragma unroll
+      for (int j = 0; j < NBK; ++j) r[j] = D[lane * TSK + j];
+#pragma unroll
+      for (int kk = 0; kk < NBK; ++kk) {
+        const T d = __shfl_sync(full, r[kk], kk);
+        const bool dr = !(d > thr);
+        const T piv = dr ? T(1) : (T)sqrt((double)d);
+        const T inv = dr ? T(0) : T(1) / piv;
+        if (lane == kk) {
+          r[kk] = piv;
+          if (dr) {
+#pragma unroll
+            for (int j = 0; j < kk; ++j) r[j] = T(0);
+          }
+        } else if (lane > kk) {
+          r[kk] *= inv;
+        }
+#pragma unroll
+        for (int j = kk + 1; j < NBK; ++j) {
+          const T ljk = __shfl_sync(full, r[kk], j);
+          if (lane >= j) r[j] -= r[kk] * ljk;
+        }
+        if (lane == 0) dropped[c0 + kk] = dr;
+      }
+#pragma unroll
+      for (int j = 0; j < NBK; ++j) D[lane * TSK + j] = (j <= lane) ? r[j] : T(0);
+      __syncwarp();
+      T x[NBK];  // lane c: column c of L_pp^{-1}
+#pragma unroll
+      for (int i = 0; i < NBK; ++i) {
+        T acc = (i == lane) ? T(1) : T(0);
+#pragma unroll
+        for (int k = 0; k < i; ++k) acc -= D[i * TSK + k] * x[k];
+        x[i] = (i < lane) ? T(0) : acc / D[i * TSK + i];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < NBK; ++i) D[i * TSK + lane] = x[i];
+    }
+    __syncthreads();
+    // a dropped index q becomes e_q in L: clear its row in the tiles left of the panel
+    for (int64_t e = tid; e < p * NBK * NBK; e += blockDim.x) {
+      const int64_t J = e / (NBK * NBK), rem = e - J * NBK * NBK;
+      const int rr = (int)(rem / NBK), cc = (int)(rem - (rem / NBK) * NBK);
+      if (dropped[c0 + rr]) tile_at(tiles, p, J)[rr * TSK + cc] = T(0);
+    }
+    // panel tiles below: L_Ip = M_Ip L_pp^{-T} (dropped columns stay zero)
+    for (int64_t I = p + 1 + wid; I < P; I += nw) {
+      T acc[8][4];
+      wtile_zero(acc);
+      T* C = tile_at(tiles, I, p);
+      wtile_mma<T, true, 1>(acc, C, D, ly, lx);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (dropped[c0 + lx * 4 + c])
+#pragma unroll
+          for (int r = 0; r < 8; ++r) acc[r][c] = T(0);
+      __syncwarp();
+      wtile_store(C, acc, ly, lx);
+    }
+    __syncthreads();
+    // trailing update M_IJ -= L_Ip L_Jp^T, p < J <= I
+    const int64_t q = P - p - 1;
+    for (int64_t t = wid; t < q * (q + 1) / 2; t += nw) {
+      int64_t a = 0;
+      while ((a + 1) * (a + 2) / 2 <= t) ++a;
+      const int64_t I = p + 1 + a, J = p + 1 + (t - a * (a + 1) / 2);
+      T acc[8][4];
+      T* C = tile_at(tiles, I, J);
+      wtile_load(acc, C, ly, lx);
+      wtile_mma<T, true, -1>(acc, tile_at(tiles, I, p), tile_at(tiles, J, p), ly, lx);
+      wtile_store(C, acc, ly, lx);
+    }
+    __syncthreads();
+  }
+  // 2. X = L^{-1}: the diagonal tiles hold X_II; the strictly lower X_IJ are built in
+  // xt, which holds the accumulators T_IJ = sum_{K < I} L_IK X_KJ until finalised
+  for (int64_t r = 0; r + 1 < P; ++r) {
+    if (r >= 1) {  // X_{J+r,J} = -X_{J+r,J+r} T_{J+r,J}
+      for (int64_t J = wid; J + r < P; J += nw) {
+        const int64_t I = J + r;
+        T* X = xtile_at(xt, I, J);
+        T acc[8][4];
+        wtile_zero(acc);
+        wtile_mma<T, false, -1>(acc, tile_at(tiles, I, I), X, ly, lx);
+        __syncwarp();
+        wtile_store(X, acc, ly, lx);
+      }
+      __syncthreads();
+    }
+    // T_IJ += L_IK X_KJ with K = J + r final, for every I > K (tasks in column order)
+    const int64_t ntask = (P - 1 - r) * (P - r) / 2;
+    for (int64_t t = wid; t < ntask; t += nw) {
+      int64_t J = 0, left = t;
+      while (left >= P - 1 - J - r) { left -= P - 1 - J - r; ++J; }
+      const int64_t K = J + r, I = K + 1 + left;
+      T* X = xtile_at(xt, I, J);
+      T acc[8][4];
+      wtile_load(acc, X, ly, lx);
+      wtile_mma<T, false, 1>(acc, tile_at(tiles, I, K),
+                             r == 0 ? tile_at(tiles, J, J) : xtile_at(xt, K, J), ly, lx);
+      wtile_store(X, acc, ly, lx);
+    }
+    __syncthreads();
+  }
+  if (P >= 2) {  // the last round: X_{P-1,0}
+    if (wid == 0) {
+      T* X = xtile_at(xt, P - 1, 0);
+      T acc[8][4];
+      wtile_zero(acc);
+      wtile_mma<T, false, -1>(acc, tile_at(tiles, P - 1, P - 1), X, ly, lx);
+      __syncwarp();
+      wtile_store(X, acc, ly, lx);
+    }
+    __syncthreads();
+  }
+  // 3. zero the dropped (and padding) rows and columns of X
+  for (int64_t e = tid; e < ntiles_lower(P) * NBK * NBK; e += blockDim.x) {
+    const int64_t tile = e / (NBK * NBK), rem = e - tile * (NBK * NBK);
+    int64_t I = 0;
+    while ((I + 1) * (I + 2) / 2 <= tile) ++I;
+    const int64_t J = tile - I * (I + 1) / 2;
+    const int rr = (int)(rem / NBK), cc = (int)(rem - (rem / NBK) * NBK);
+    const int64_t i = I * NBK + rr, j = J * NBK + cc;
+    if (i >= tau || j >= tau || dropped[i] || dropped[j])
+      (I == J ? tile_at(tiles, I, I) : xtile_at(xt, I, J))[rr * TSK + cc] = T(0);
+  }
+  __syncthreads();
+  // P_IJ = sum_{K >= I} X_KI^T X_KJ, I >= J; tasks in order of decreasing work
+  if (Pout != nullptr) {
+    TP* Ps = Pout + s * p_slot;
+    for (int64_t t = wid; t < ntiles_lower(P); t += nw) {
+      int64_t I = 0;
+      while ((I + 1) * (I + 2) / 2 <= t) ++I;
+      const int64_t J = t - I * (I + 1) / 2;
+      T acc[8][4];
+      wtile_zero(acc);
+      for (int64_t K = I; K < P; ++K) {
+        const T* XI = (K == I) ? tile_at(tiles, K, K) : xtile_at(xt, K, I);
+        const T* XJ = (K == J) ? tile_at(tiles, K, K) : xtile_at(xt, K, J);
+        wtile_mma_g<T, true, false, 1>(acc, XI, XJ, ly, lx);
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int64_t i = I * NBK + ly * 8 + r, l = J * NBK + lx * 4 + c;
+          if (i < tau && l < tau) {
+            Ps[i * pld + l] = (TP)acc[r][c];
+            if (I != J) Ps[l * pld + i] = (TP)acc[r][c];
+          }
+        }
+    }
+  }
+  // L^{-1} with the dropped rows and columns zeroed (tau x tau, zero above), if asked
+  if (Linv != nullptr) {
+    T* out = Linv + s * l_slot;
+    for (int64_t i = wid; i < tau; i += nw) {
+      const int64_t I = i / NBK, rr = i - I * NBK;
+      for (int64_t j = lane; j < tau; j += 32) {
+        T v = T(0);
+        if (j <= i) {
+          const int64_t J = j / NBK;
+          v = (I == J ? tile_at(tiles, I, I) : xtile_at(xt, I, J))[rr * TSK + (j - J * NBK)];
+        }
+        out[i * tau + j] = v;
+      }
+    }
+  }
+  if (tid == 0 && ndropped != nullptr) {
+    int cnt = 0;
+    for (int64_t i = 0; i < tau; ++i) cnt += dropped[i];
+    if (cnt) atomicAdd(ndropped, cnt);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // phase 2: r_S, delta = L^{-T} L^{-1} r_S, u = S delta on a cluster of CS CTAs.
 // CTA q owns the index range [q*chunk, (q+1)*chunk) of r_S, y and delta.
 // ---------------------------------------------------------------------------
@@ -745,6 +1030,25 @@ cudaError_t launch_sweep_inv(cudaStream_t st, const Ctrl* ctrl, int force, int n
                                                      pld, p_slot, ndropped);
   return cudaGetLastError();
 }
+
+template <typename T, typename TP>
+cudaError_t launch_potri(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, const double* M,
+                         int64_t m_slot, int64_t tau, T* Linv, int64_t l_slot, TP* P, int64_t pld,
+                         int64_t p_slot, T* ws, int32_t* ndropped) {
+  if (tau < 1 || tau > 4096 || ws == nullptr) return cudaErrorInvalidValue;
+  k_potri<T, TP><<<nslots, kPotriThreads, 0, st>>>(ctrl, force, nslots, M, m_slot, tau, Linv,
+                                                    l_slot, P, pld, p_slot, ws, ndropped);
+  return cudaGetLastError();
+}
+template cudaError_t launch_potri<float, float>(cudaStream_t, const Ctrl*, int, int, const double*,
+                                                int64_t, int64_t, float*, int64_t, float*, int64_t,
+                                                int64_t, float*, int32_t*);
+template cudaError_t launch_potri<double, double>(cudaStream_t, const Ctrl*, int, int,
+                                                  const double*, int64_t, int64_t, double*, int64_t,
+                                                  double*, int64_t, int64_t, double*, int32_t*);
+template cudaError_t launch_potri<double, float>(cudaStream_t, const Ctrl*, int, int,
+                                                 const double*, int64_t, int64_t, double*, int64_t,
+                                                 float*, int64_t, int64_t, double*, int32_t*);
 
 // P_s = L_s^{-T} L_s^{-1}: P(i, j) = sum_k Linv[k, i] Linv[k, j], every slot in one launch
 template <typename TF>

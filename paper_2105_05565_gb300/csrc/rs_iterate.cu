@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) k_iterate(Ctrl* __restrict__ ctrl, IterAr
   const int64_t tau = g.tau, m = g.m;
   const int64_t k0 = ctrl->k0;
   int64_t k = ctrl->k;
-  const int64_t kend = min(k0 + g.chunk, ctrl->max_iters);
+  const int64_t kend = min(k0 + g.sub_end, ctrl->max_iters);
   const double tol = ctrl->tol, r0 = ctrl->r0;
   const int no_stop = ctrl->no_stop;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;

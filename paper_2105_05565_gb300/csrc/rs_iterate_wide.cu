@@ -47,7 +47,10 @@ constexpr int kWWarps = kWThreads / 32;
 constexpr int kIssueWarp = kWWarps - 1;        // issues the bulk copies
 constexpr int kSumLoads = 20;                   // partials in flight per thread
 constexpr int kRowsPerLane = 2;                 // rows of a lane in the A S delta product
-constexpr uint64_t kWaitNs = 2000000000ull;     // 2 s bound of every wait
+// waits at the end of a launch for copies already in flight into this CTA's shared
+// memory: they land within microseconds, so this bound is generous and independent
+// of the caller's limit on the other waits
+constexpr uint64_t kDrainNs = 2000000000ull;
 
 struct WideLayout {
   int64_t qs, E, G;
@@ -87,16 +90,17 @@ __host__ __device__ inline WideLayout wide_layout(int64_t q, int64_t tau, int64_
   return L;
 }
 
-// bounded wait on an mbarrier phase; false on timeout or (abort_word != nullptr)
-// when another CTA has raised the abort word
-__device__ bool wait_bar(uint64_t* bar, uint32_t parity, const int32_t* abort_word) {
+// bounded wait on an mbarrier phase (wait_ns of the global timer); false on timeout
+// or (abort_word != nullptr) when another CTA has raised the abort word
+__device__ bool wait_bar(uint64_t* bar, uint32_t parity, const int32_t* abort_word,
+                         uint64_t wait_ns) {
   if (ptx::mbar_test(bar, parity)) return true;
   const uint64_t t0 = ptx::now_ns();
   for (uint32_t it = 1;; ++it) {
     if (ptx::mbar_test(bar, parity)) return true;
     if ((it & 63) == 0) {
       if (abort_word != nullptr && ptx::ld_relaxed_s32(abort_word) != 0) return false;
-      if (ptx::now_ns() - t0 > kWaitNs) return false;
+      if (ptx::now_ns() - t0 > wait_ns) return false;
     }
   }
 }
@@ -104,6 +108,7 @@ __device__ bool wait_bar(uint64_t* bar, uint32_t parity, const int32_t* abort_wo
 struct Xch {
   uint64_t* part;   // 2 (parity) x nblk x nw words
   int32_t* abort_word;
+  uint64_t wait_ns;  // bound of every wait
   int nblk, cta;
   uint32_t crank;
   int64_t tau, ne, E, G, nw;
@@ -223,7 +228,7 @@ __device__ bool xch_end(const Xch& x, uint32_t tag, uint32_t n) {
             if ((pend & (1u << u)) && (uint32_t)(a[u] >> 32) == tag && (uint32_t)(b[u] >> 32) == tag)
               pend &= ~(1u << u);
           if (pend != 0 && (pass & 15) == 15 &&
-              (ptx::ld_relaxed_s32(x.abort_word) != 0 || ptx::now_ns() - t0 > kWaitNs)) {
+              (ptx::ld_relaxed_s32(x.abort_word) != 0 || ptx::now_ns() - t0 > x.wait_ns)) {
             bad = 1;
             break;
           }
@@ -276,7 +281,7 @@ __device__ bool xch_end(const Xch& x, uint32_t tag, uint32_t n) {
         ptx::st_async_f64(ptx::map_rank(x.tot + e, rk), v, ptx::map_rank(x.xbar, rk));
     }
   }
-  const bool ok = wait_bar(x.xbar, n & 1, x.abort_word);
+  const bool ok = wait_bar(x.xbar, n & 1, x.abort_word, x.wait_ns);
   if (__syncthreads_or(!ok)) {
     if (tid == 0) atomicExch(x.abort_word, 1);
     return false;
@@ -311,7 +316,8 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   // exchange, so all CTAs take the same branches
   if (halted(ctrl)) return;
   const int64_t k0 = ctrl->k0, kstart = ctrl->k;
-  int64_t kend = min(k0 + g.chunk, ctrl->max_iters);
+  // this launch's part of the chunk ends at k0 + sub_end (an FP64 refresh may follow)
+  int64_t kend = min(k0 + g.sub_end, ctrl->max_iters);
   if (ctrl->kcap > 0 && ctrl->kcap < kend) kend = ctrl->kcap;  // convergence forecast
   if (kstart >= kend) return;
   const double tol = ctrl->tol, r0 = ctrl->r0;
@@ -406,7 +412,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   ptx::cluster_sync_all();  // peers' mbarriers are initialised before any remote store
 
   Xch x;
-  x.part = g.part; x.abort_word = g.abort_word;
+  x.part = g.part; x.abort_word = g.abort_word; x.wait_ns = g.wait_ns;
   x.nblk = g.nblk; x.cta = cta; x.crank = crank;
   x.tau = tau; x.ne = tau + 1; x.E = L.E; x.G = L.G; x.nw = ll_words<TF>(tau);
   x.mine = mine; x.tot = tot; x.red = red; x.xbar = xbar;
@@ -431,7 +437,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   // (every thread) the inverse map of slot s is in place
   auto wait_iv = [&](int64_t s) -> bool {
     const int b = (int)(s % 3);
-    const bool r = wait_bar(iv_full + b, iv_use[b] & 1, g.abort_word);
+    const bool r = wait_bar(iv_full + b, iv_use[b] & 1, g.abort_word, g.wait_ns);
     iv_use[b]++;
     return !__syncthreads_or(!r);
   };
@@ -451,7 +457,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   auto issue_p = [&](int64_t s, bool iv_ready) {
     if (wid == kIssueWarp) {
       const int bi = (int)(s % 3);
-      bool okw = iv_ready || wait_bar(iv_full + bi, iv_use[bi] & 1, g.abort_word);
+      bool okw = iv_ready || wait_bar(iv_full + bi, iv_use[bi] & 1, g.abort_word, g.wait_ns);
       if (!okw) {
         if (lane == 0) atomicExch(g.abort_word, 1);
       }
@@ -503,7 +509,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
       }
     }
     if (use_p) {
-      const bool r = wait_bar(p_full, p_use & 1, g.abort_word);
+      const bool r = wait_bar(p_full, p_use & 1, g.abort_word, g.wait_ns);
       p_use++;
       if (__syncthreads_or(!r)) return false;
     } else {
@@ -567,6 +573,13 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
     ok = wait_iv(s0);
     if (ok) issue_p(s0, true);
   }
+  if (g.stall_ns > 0 && cta == 0) {
+    // fault injection (tests of the bounded waits): this CTA publishes its first
+    // partials stall_ns late, so that the other CTAs' waits for them run out
+    const uint64_t t0 = ptx::now_ns();
+    while (ptx::now_ns() - t0 < (uint64_t)g.stall_ns) {
+    }
+  }
   if (ok) ok = partial(true, true);
   while (ok) {
     const uint32_t tag = (uint32_t)(tag0 + nx + 1);
@@ -622,9 +635,9 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
     const int b = (int)(s % nsab);
     bool r = true;
     if (has_rows) {
-      r = (k == kstart) || wait_bar(iv_full + (s % 3), iv_use[s % 3] & 1, g.abort_word);
+      r = (k == kstart) || wait_bar(iv_full + (s % 3), iv_use[s % 3] & 1, g.abort_word, g.wait_ns);
       if (k > kstart) iv_use[s % 3]++;
-      r = r && wait_bar(sa_full + b, sa_use[b] & 1, g.abort_word);
+      r = r && wait_bar(sa_full + b, sa_use[b] & 1, g.abort_word, g.wait_ns);
       sa_use[b]++;
     }
     if (__syncthreads_or(!r)) { ok = false; break; }
@@ -737,15 +750,15 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   if (!ok) {
     outcome = 3;
     // let the stores of the cluster's sums of the last exchange land (bounded)
-    if (nx > 0) wait_bar(xbar, (nx - 1) & 1, nullptr);
+    if (nx > 0) wait_bar(xbar, (nx - 1) & 1, nullptr, kDrainNs);
   }
   // no bulk copy may still be writing this CTA's shared memory when it exits
   if (has_rows) {
     for (int b = 0; b < nsab; ++b)
-      for (; sa_use[b] < sa_iss[b]; ++sa_use[b]) wait_bar(sa_full + b, sa_use[b] & 1, nullptr);
+      for (; sa_use[b] < sa_iss[b]; ++sa_use[b]) wait_bar(sa_full + b, sa_use[b] & 1, nullptr, kDrainNs);
     for (int b = 0; b < 3; ++b)
-      for (; iv_use[b] < iv_iss[b]; ++iv_use[b]) wait_bar(iv_full + b, iv_use[b] & 1, nullptr);
-    for (; p_use < p_iss; ++p_use) wait_bar(p_full, p_use & 1, nullptr);
+      for (; iv_use[b] < iv_iss[b]; ++iv_use[b]) wait_bar(iv_full + b, iv_use[b] & 1, nullptr, kDrainNs);
+    for (; p_use < p_iss; ++p_use) wait_bar(p_full, p_use & 1, nullptr, kDrainNs);
   }
   __syncthreads();
   for (int64_t i = tid; i < qc; i += kWThreads) {

@@ -81,6 +81,13 @@ template <typename T>
 cudaError_t launch_factor_inv(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
                               const double* M, int64_t m_slot, int64_t tau, T* Linv, int64_t l_slot,
                               T* ws, int32_t* ndropped);
+// P = M^+ (and, if Linv != nullptr, the zeroed L^{-1}) per slot; ws holds
+// potri_ws_elems(tau) elements per slot
+__host__ __device__ size_t potri_ws_elems(int64_t tau);
+template <typename T, typename TP>
+cudaError_t launch_potri(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, const double* M,
+                         int64_t m_slot, int64_t tau, T* Linv, int64_t l_slot, TP* P, int64_t pld,
+                         int64_t p_slot, T* ws, int32_t* ndropped);
 template <typename T>
 struct DeltaArgs {
   int kind;            // 0 bucket rows (subsample, count, subcount), 1 Gaussian, 2 SRHT
@@ -112,6 +119,7 @@ struct IterArgs {
   double* w; double* wp; double* r; double* rp;
   double* hist; double* delta_out; double* rS_out;
   int64_t m, tau, chunk;
+  int64_t sub_end;  // iterations run while k < k0 + sub_end (sub_end <= chunk)
   int stage;           // set by the launcher: r and the plan staged in shared memory
 };
 template <typename T, typename TF>
@@ -141,6 +149,9 @@ struct WideArgs {
   uint64_t* epoch;                 // launch counter of the tags
   int32_t* abort_word;             // set by a CTA whose bounded wait ran out
   int64_t m, tau, chunk, q;
+  int64_t sub_end;  // iterations run while k < k0 + sub_end (sub_end <= chunk)
+  uint64_t wait_ns;  // bound of every device-side wait (global timer)
+  int64_t stall_ns;  // fault injection: CTA 0 publishes its first partials this late
   int nblk;
   int nsab;                        // buffers of the staged S^T A block (2, or 1 when tight)
 };

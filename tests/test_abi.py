@@ -78,7 +78,7 @@ def test_default_options(L):
 
     o = rs.Opts()
     L.rs_default_opts(ctypes.byref(o))
-    assert o.precision == 0 and o.refresh_every == 400 and o.chol_fp64 == 0
+    assert o.precision == 0 and o.refresh_every == 50 and o.chol_fp64 == 1
     assert o.iter_ctas == 0 and o.setup_tc == 1
     m = rs.Mom()
     L.rs_default_mom(ctypes.byref(m), 3)

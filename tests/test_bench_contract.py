@@ -24,3 +24,23 @@ def test_roofline_of_the_dominant_kernel():
 def test_roofline_falls_back_without_measured_peaks():
     r = bench.roofline({"refresh": (0.67, 1, 1.64e9, 0.0, 1)}, {})
     assert r["peak"] == 6800.0 and r["kernel"] == "refresh"
+
+
+def test_roofline_of_the_fp64_small_solve():
+    # the fused factor, inverse and product: tau^3 flops per slot, 600 slots
+    fl = 600 * 256.0 ** 3
+    r = bench.roofline({"potri": (12.8, 2, 1e8, fl, 2), "iterate": (0.585, 24, 1.6e8, 1e8, 1200)},
+                       {"hbm_gbs": 6809.6})
+    assert r["kernel"] == "potri" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - fl / 12.8e-3 / 1e12) < 1e-9
+    assert r["peak"] == bench.FP64_PEAK_TFLOPS and abs(r["frac"] - r["achieved"] / 1.25) < 1e-12
+
+
+def test_launch_count_of_a_mixed_step():
+    # 1217 iterations in chunks of 600 with a refresh every 50: three chunks run, one
+    # graph replay of four chunks; per chunk 5 phase-1 launches + 12 x (iterate + 3)
+    assert bench.launches_per_step(1217, 600, 50) == 4 * (5 + 48) + 7
+    # 2401 iterations: five chunks, two replays
+    assert bench.launches_per_step(2401, 600, 50) == 8 * 53 + 7
+    # factor and product as two launches
+    assert bench.launches_per_step(100, 600, 50, fused=False) == 4 * 54 + 7

@@ -1,6 +1,7 @@
 """The N > 1 path of bench.py (replicas, one independent problem per rank) on CPU:
 two gloo ranks aggregate their times and iteration counts as the contract says
-(max over ranks of the times, sum of the iterations)."""
+(max over ranks of the times, sum of the iterations) and keep every rank's own
+iterations and times."""
 import multiprocessing as mp
 import os
 import socket
@@ -38,5 +39,10 @@ def test_two_replicas_aggregate_on_gloo():
         p.join(timeout=60)
         assert p.exitcode == 0
     for r in range(2):
-        s, m, it = res[r]
+        s, m, it, per_rank = res[r]
         assert s == 2.0 and m == 10.0 and it == 201
+        # every rank's own record, in rank order, on every rank
+        assert [p["rank"] for p in per_rank] == [0, 1]
+        assert [p["iters"] for p in per_rank] == [100, 101]
+        assert [p["solve_s"] for p in per_rank] == [1.0, 2.0]
+        assert [p["step_ms"] for p in per_rank] == [10.0, 9.0]
