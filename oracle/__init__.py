@@ -16,6 +16,9 @@ What it computes follows the paper (arXiv 2105.05565, "RidgeSketch"):
   definition in Section 4 (Gaussian, Subsample, Count, SubCount, SRHT);
 * the momentum parameter rules of Sections 6.1-6.2 and 8.1 (eqs. (38), (40),
   (49)-(50), (66), (67));
+* importance-sampled coordinates p_j = A_jj / trace(A) and coordinate descent
+  with momentum (``oracle.importance``, Section 7, eqs. (mSdisccolCD), (CDmom)),
+  and the averaged iterates of the theorem of Section 5.2 (``average=True``);
 * the learned sketch proposal (``oracle.learned``): features, the scoring
   network and its gradient, the proposal, Gumbel-top-tau selection, the
   per-coordinate labels from the projection identity of Section 3, and Adam.
@@ -49,3 +52,4 @@ from .solver import (  # noqa: F401
     true_residual,
 )
 from . import learned  # noqa: F401,E402
+from . import importance  # noqa: F401,E402

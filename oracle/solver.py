@@ -68,13 +68,17 @@ def least_norm_solution(M, rS, rcond: float = LSTSQ_RCOND):
 
 
 def sketch_and_project(A, b, kind: str, tau: int, seed: int, tol: float, max_iters: int,
-                       mom=None, s=None, record_first: int = 0, apply_A=None):
+                       mom=None, s=None, record_first: int = 0, apply_A=None, sketch_fn=None,
+                       average: bool = False):
     """Algorithm 2 on A w = b. ``apply_A(V)`` (default ``A @ V``) gives A V for
     an m x tau block V, so that the matrix-free form can reuse the loop.
+    ``sketch_fn(k)``, if given, returns S_k in place of the sketch of ``kind``
+    (a sampler whose law depends on A, e.g. ``oracle.importance``).
 
     Returns dict(w, hist, iters, records): hist[k] = ||r^k|| / ||r^0|| for
     k = 0..iters; records holds (S, r_S, M, delta, w, r) of the first
-    ``record_first`` iterations.
+    ``record_first`` iterations. With ``average``, also w_avg, the mean of the
+    iterates w^0, ..., w^t (t = iters) of the theorem of Section 5.2.
     """
     mom = dict(mom or {"kind": "none"})
     mkind = mom.pop("kind", "none")
@@ -90,12 +94,16 @@ def sketch_and_project(A, b, kind: str, tau: int, seed: int, tol: float, max_ite
     r_prev = r.copy()
     r0 = np.linalg.norm(r)
     if r0 == 0.0:
-        return dict(w=w, hist=[0.0], iters=0, records=[])
+        out = dict(w=w, hist=[0.0], iters=0, records=[])
+        if average:
+            out["w_avg"] = w.copy()
+        return out
     hist = [1.0]
     records = []
+    w_sum = w.copy()  # sum of w^0 .. w^k
     k = 0
     while k < max_iters and np.linalg.norm(r) / r0 > tol:
-        S = sketch_matrix(kind, m, tau, seed, k, s)
+        S = sketch_fn(k) if sketch_fn is not None else sketch_matrix(kind, m, tau, seed, k, s)
         AS = apply_A(S)
         rS = S.T @ r
         M = S.T @ AS
@@ -108,8 +116,12 @@ def sketch_and_project(A, b, kind: str, tau: int, seed: int, tol: float, max_ite
         if k < record_first:
             records.append(dict(k=k, S=S, rS=rS, M=M, delta=delta, w=w.copy(), r=r.copy()))
         k += 1
+        w_sum = w_sum + w
         hist.append(np.linalg.norm(r) / r0)
-    return dict(w=w, hist=hist, iters=k, records=records)
+    out = dict(w=w, hist=hist, iters=k, records=records)
+    if average:
+        out["w_avg"] = w_sum / (k + 1)
+    return out
 
 
 def solve_ridge(X, y, lam: float, form: str, kind: str, tau: int, seed: int, tol: float,
