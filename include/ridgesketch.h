@@ -402,6 +402,56 @@ rs_status rs_batch_profile(rs_batch* b, int32_t chunks, double* ms_parts);
  * RS_EUNSUPPORTED for other sketches, matrix-free contexts or m > 16384.
  */
 rs_status rs_set_proposal(rs_ctx* c, const uint16_t* w_bf16, double eps);
+
+/*
+ * Training data for the learned proposal from this solver's own trajectory: from
+ * the current state, up to n_iters iterations (the proposal set by rs_set_proposal
+ * draws the rows), recording for every drawn row p of iteration k its features at
+ * k (the layout of rs_proposal_features) and the target
+ *   y_p = (1/2) ln(m max(a_p, 0) / e_k + 1e-3),  a_p = (r_C)_p delta_p,
+ *   e_k = ||w_k - w*||_A^2 = (w_k - w*) . r_k,
+ * where r_C . delta is the exact decrease of ||w - w*||_A^2 of a step without
+ * momentum (the projection identity of Section 3). Stops early once e_k <= 0 or
+ * ||r_k|| <= tol ||r_0||. Everything runs on the device; the host waits once.
+ *   w_star  m doubles (host): the solution the errors are measured against
+ *   Z_out   n_iters * tau * 4 floats (host), y_out n_iters * tau floats (host)
+ *   n_rows  rows written
+ * Needs RS_PLAIN_FP64, the subsample sketch with a proposal set, chunk = 1 and no
+ * momentum (RS_EINVAL otherwise). The state advances like rs_step.
+ */
+rs_status rs_collect(rs_ctx* ctx, const double* w_star, int64_t n_iters, double tol, float* Z_out,
+                     float* y_out, int64_t* n_rows);
+
+/*
+ * Importance-sampled subsample sketches (Section 7): with RS_SAMPLE_DIAG the tau
+ * rows of iteration k are drawn without replacement in proportion to the diagonal
+ * of A, p_j = A_jj / trace(A) (eq. (mSdisccolCD); for tau = 1 this is coordinate
+ * descent with the probabilities of that equation, and with momentum eq. (CDmom)),
+ * as the tau largest keys ln p_j + g_j with the Gumbel noise g_j of iteration k
+ * (the draws of the learned proposal with its scores fixed at ln A_jj and eps = 0).
+ * RS_SAMPLE_UNIFORM returns to the sketch's own uniform draws (also clears a
+ * learned proposal). RS_SUBSAMPLE sketches of dense A, m <= 16384 (RS_EUNSUPPORTED
+ * otherwise). Takes effect from the next rs_solve or rs_step.
+ */
+enum { RS_SAMPLE_UNIFORM = 0, RS_SAMPLE_DIAG = 1 };
+rs_status rs_set_sampling(rs_ctx* ctx, int32_t kind);
+
+/*
+ * Averaged iterates (the theorem of Section 5.2, eqs. (convsublinear) and
+ * (convressublinear)): with averaging on, rs_solve also keeps the running sum of
+ * its iterates w^0 = 0, w^1, ..., w^t inside the iteration kernel (FP64, one add
+ * per coordinate and iteration), and rs_get_average returns their mean
+ * wbar^t = (w^0 + ... + w^t) / (t + 1) of the last rs_solve (the paper writes the
+ * sum over t + 1 iterates with a factor 1 / t; the mean is read here). For RS_DUAL
+ * the result is X^T of the mean of the dual iterates, like w of rs_solve.
+ *   rs_set_averaging  on = 1 / 0; needs the persistent iteration kernel (subsample,
+ *                     count or subcount sketch of dense A): RS_EUNSUPPORTED otherwise.
+ *                     Takes effect from the next rs_solve.
+ *   rs_get_average    w_out: d doubles, caller-owned, device memory if w_on_device;
+ *                     RS_EINVAL when averaging is off.
+ */
+rs_status rs_set_averaging(rs_ctx* ctx, int32_t on);
+rs_status rs_get_average(rs_ctx* ctx, double* w_out, int32_t w_on_device);
 /* The m x 4 standardised feature rows (FP32, row-major, host pointer) at the
  * context's current state, as the proposal would see them at a chunk start. */
 rs_status rs_proposal_features(rs_ctx* c, float* Z_out);

@@ -76,6 +76,10 @@ _SIGS = {
     "rs_get_dims": (_I32, [_P] + [ctypes.POINTER(_I64)] * 5),
     "rs_iter_plan": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
     "rs_chunking": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "rs_set_sampling": (_I32, [_P, _I32]),
+    "rs_collect": (_I32, [_P, _P, _I64, _D, _P, _P, ctypes.POINTER(_I64)]),
+    "rs_set_averaging": (_I32, [_P, _I32]),
+    "rs_get_average": (_I32, [_P, _P, _I32]),
     "rs_dump_sketch": (_I32, [_P, _I64, _P, _P, _P]),
     "rs_dump_gaussian": (_I32, [_P, _I64, _P]),
     "rs_get_state": (_I32, [_P, _P, _P, _P, _P, ctypes.POINTER(_I64)]),
@@ -355,6 +359,32 @@ class Solver:
                                        arr[i].iters)
                 for i in range(n.value)}
 
+    def set_averaging(self, on=True):
+        """Keep the mean of the iterates of each solve (Section 5.2)."""
+        self._check(lib().rs_set_averaging(self._ctx, int(bool(on))))
+
+    def average(self):
+        """Mean of the iterates w^0..w^t of the last solve (host array)."""
+        out = np.empty(self.d)
+        self._check(lib().rs_get_average(self._ctx, out.ctypes.data, 0))
+        return out
+
+    def collect(self, w_star, n_iters, tol=1e-10):
+        """Features and targets of the rows drawn along up to n_iters iterations from the
+        current state (rs_collect): (Z (n, 4) float32, y (n,) float32)."""
+        ws = np.ascontiguousarray(w_star, dtype=np.float64)
+        Z = np.empty((int(n_iters) * self.tau, 4), np.float32)
+        y = np.empty(int(n_iters) * self.tau, np.float32)
+        n = _I64()
+        self._check(lib().rs_collect(self._ctx, ws.ctypes.data, int(n_iters), float(tol),
+                                     Z.ctypes.data, y.ctypes.data, ctypes.byref(n)))
+        return Z[:n.value].copy(), y[:n.value].copy()
+
+    def set_sampling(self, kind="diag"):
+        """Subsample rows drawn in proportion to A_jj ("diag", Section 7) or uniformly
+        ("uniform", the default)."""
+        self._check(lib().rs_set_sampling(self._ctx, {"uniform": 0, "diag": 1}[kind]))
+
     def set_proposal(self, weights_bf16=None, eps=0.1):
         """Draw the subsample rows from the learned proposal: ``weights_bf16`` (4545
         uint16 bfloat16 bit patterns) or None for the uniform proposal; eps < 0
@@ -484,7 +514,7 @@ class Batch:
     def __init__(self, Xs, Ys, lams, sketch="count", taus=None, momentum="none", seed=0,
                  precision="fp64", refresh_every=300, sub_s=0, chunk=0, eta=0.995,
                  beta_switch=0.5, gamma_c=1.0, beta_c=0.5, uncapped=False, device=0, stream=None,
-                 setup_tc=True):
+                 setup_tc=True, chol_fp64=True, tune_cache=None):
         L = lib()
         self._b = None
         P = len(Xs)
@@ -532,6 +562,9 @@ class Batch:
         opts.device = int(device)
         opts.chunk = int(chunk)
         opts.setup_tc = int(bool(setup_tc))
+        opts.chol_fp64 = int(bool(chol_fp64))
+        self._tune_cache = None if tune_cache is None else str(tune_cache).encode()
+        opts.tune_cache = self._tune_cache
         opts.cuda_stream = stream if stream is not None else _default_stream(device)
         b = _P()
         status = L.rs_create_batch(P, mats, yptrs, int(ydev), int(nrhs), lam_a, SKETCHES[sketch], tau_a,

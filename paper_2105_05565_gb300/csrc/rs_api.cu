@@ -102,6 +102,7 @@ struct rs_ctx {
   // learned proposal of the subsample rows (rs_set_proposal)
   bool learned = false;
   bool lp_uniform = false;     // no network: p_j = 1 / m
+  bool lp_fixed = false;       // scores fixed once (importance sampling, rs_set_sampling)
   float lp_eps = 0.1f;
   uint16_t* lp_w = nullptr;    // network weights, bfloat16
   float* lp_raw = nullptr;     // 2 m work space (raw static, then the dynamic features)
@@ -116,7 +117,8 @@ struct rs_ctx {
   bool use_wide = false;
   WidePlan wide{};
   void* Pm = nullptr;       // per slot: M^+ = L^{-T} L^{-1}, tau x pld (factor precision)
-  void* pws = nullptr;      // per slot: tile workspace of k_potri (P formed in one kernel)
+  void* pws = nullptr;      // per slot: tile workspace of k_potri when the tiles pass shared memory
+  bool potri = false;       // M^+ by the one-kernel factor, inverse and product
   bool sweep_p = false;     // M^+ by FP32 sweeps from an FP32 M (mixed, FP32 factor)
   bool batch_member = false;  // a problem of an rs_batch (S^T A and M^+ kept per slot)
   float* Mf = nullptr;      // per slot: M in FP32 for the sweeps
@@ -126,6 +128,9 @@ struct rs_ctx {
   int32_t* xabort = nullptr;
   uint64_t wait_ns = 2000000000ull;  // bound of the persistent kernel's waits
   int64_t stall_ns = 0;              // fault injection (tests)
+  bool avg = false;                  // keep the running sum of the iterates (rs_set_averaging)
+  double* wsum = nullptr;            // m: sum of w^0..w^k of the current solve
+  int64_t last_iters = 0;            // iterations of the last rs_solve
   // matrix-free sparse X (CSR input)
   bool sparse = false;
   int64_t nnz = 0;
@@ -266,7 +271,7 @@ void free_all(rs_ctx* c) {
                   c->sx_pcol, c->sx_pstart, c->sx_cpiece, c->mf_bsum, c->mf_boffs, c->mf_tot,
                   c->mf_crow, c->mf_cptr, c->mf_ebuck, c->mf_eval, c->mf_v, c->mf_pu, c->mf_pud,
                   c->mf_z, c->lp_w, c->lp_raw, c->lp_zstat, c->lp_stats, c->lp_score, c->lp_feat,
-                  c->lp_last};
+                  c->lp_last, c->wsum};
   for (void* p : ptrs) pfree(c, p);
   if (c->ctrl_h) {  // the stream may still read the pinned control block
     cudaStreamSynchronize(c->stream);
@@ -341,7 +346,8 @@ rs_status enqueue_gen(rs_ctx* c, int64_t k0_arg, int nslots) {
     CKC(c, launch_lp_plans(st, c->ctrl, k0_arg >= 0 ? 1 : 0, nslots, k0_arg, c->seed,
                            c->lp_uniform ? nullptr : c->lp_w, c->lp_eps, c->lp_zstat, c->lp_raw,
                            c->lp_stats, c->r, c->lp_last, c->m, c->tau, c->lp_score, c->perm,
-                           c->perm_stride, c->boff, c->boff_stride, k0_arg < 0));
+                           c->perm_stride, c->boff, c->boff_stride, k0_arg < 0 && !c->lp_fixed,
+                           c->lp_fixed));
     return RS_OK;
   }
   switch (c->sketch) {
@@ -377,10 +383,11 @@ rs_status enqueue_gen(rs_ctx* c, int64_t k0_arg, int nslots) {
 constexpr int kP1Plan = 1, kP1Rows = 2, kP1Msys = 4, kP1Inv = 8, kP1All = 15;
 
 // M^+ of every slot in one kernel: FP64 or FP32 arithmetic (the factor's), stored in
-// the iteration kernel's type (FP32 for the mixed matrix-free path)
+// the iteration kernel's type (FP32 in mixed precision: FP64 factor and inverse,
+// rounded once to FP32 for the FP32 iterations)
 rs_status enqueue_potri(rs_ctx* c, cudaStream_t st, int force, int nslots) {
   double* M = c->M;
-  if (c->f64_factor() && c->sparse && c->mixed())
+  if (c->f64_factor() && c->mixed() && (c->sparse || c->batch_member || c->use_wide))
     CKC(c, (launch_potri<double, float>(st, c->ctrl, force, nslots, M, c->m_slot, c->tau, nullptr,
                                         c->l_slot, static_cast<float*>(c->Pm), c->pld, c->p_slot,
                                         static_cast<double*>(c->pws), c->ndropped)));
@@ -461,7 +468,7 @@ rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots, boo
                             static_cast<float*>(c->Pm), c->pld, c->p_slot, c->ndropped));
     return RS_OK;
   }
-  if (want_p && c->pws != nullptr) return enqueue_potri(c, st, force, nslots);
+  if (want_p && c->potri) return enqueue_potri(c, st, force, nslots);
   if (c->f64_factor())
     CKC(c, launch_factor_inv<double>(st, c->ctrl, force, nslots, c->M, c->m_slot, c->tau,
                                      static_cast<double*>(c->Linv), c->l_slot,
@@ -588,6 +595,7 @@ rs_status enqueue_wide_t(rs_ctx* c, int64_t sub_end) {
   g.nsab = c->wide.nsab;
   g.wait_ns = c->wait_ns;
   g.stall_ns = c->stall_ns;
+  g.wsum = c->avg ? c->wsum : nullptr;
   CKC(c, (launch_iterate_wide<T, TF>(c->stream, c->ctrl, g, c->wide.smem)));
   return RS_OK;
 }
@@ -598,9 +606,9 @@ rs_status enqueue_wide_t(rs_ctx* c, int64_t sub_end) {
 rs_status enqueue_iterate(rs_ctx* c, int64_t sub_end = -1) {
   if (sub_end < 0 || sub_end > c->chunk) sub_end = c->chunk;
   if (c->use_wide) {
+    // mixed: M^+ (FP64-formed or by FP32 sweeps) is stored in FP32 for the FP32 iterations
     if (!c->mixed()) return enqueue_wide_t<double, double>(c, sub_end);
-    return c->f64_factor() ? enqueue_wide_t<float, double>(c, sub_end)
-                           : enqueue_wide_t<float, float>(c, sub_end);
+    return enqueue_wide_t<float, float>(c, sub_end);
   }
   if (!c->mixed()) return enqueue_iterate_t<double, double>(c, sub_end);
   return c->f64_factor() ? enqueue_iterate_t<float, double>(c, sub_end)
@@ -1253,7 +1261,10 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     c->pld = round_up(c->tau, 4);
     c->p_slot = c->tau * c->pld;
     TRYC(pmalloc(c, (void**)&c->Pm, nsl * c->p_slot * (c->mixed() ? 4 : 8)));
-    if (c->tau <= 4096) TRYC(pmalloc(c, &c->pws, nsl * potri_ws_elems(c->tau) * fel));
+    if (c->tau <= 4096) {
+      c->potri = true;
+      if (potri_needs_ws(c->tau, fel)) TRYC(pmalloc(c, &c->pws, nsl * potri_ws_elems(c->tau) * fel));
+    }
     TRY(dalloc(c, &c->mf_bsum, nsl * c->mf_nrb * 2));
     TRY(dalloc(c, &c->mf_boffs, nsl * c->mf_nrb * 2));
     TRY(dalloc(c, &c->mf_tot, nsl * 2));
@@ -1267,26 +1278,32 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     TRYC(pmalloc(c, (void**)&c->mf_pu, std::max<int64_t>(c->sx_npieces, 1) * c->elem()));
   }
   if (t_batch_member && !c->sparse) {
+    // M^+ in the batch iteration kernel's type (FP32 in mixed precision), formed in
+    // the factor's precision
     const size_t fel = c->f64_factor() ? 8 : 4;
     c->pld = round_up(c->tau, 4);
     c->p_slot = c->tau * c->pld;
-    TRYC(pmalloc(c, (void**)&c->Pm, (size_t)c->nslots * c->p_slot * fel));
+    TRYC(pmalloc(c, (void**)&c->Pm, (size_t)c->nslots * c->p_slot * (c->mixed() ? 4 : 8)));
     // FP32 M^+ by sweeps (every phase-1 path of a member writes the FP32 M they read)
     c->sweep_p = c->mixed() && !c->f64_factor() && c->tau <= kSweepMaxTau;
     if (c->sweep_p) TRY(dalloc(c, &c->Mf, (size_t)c->nslots * c->tau * c->tau));
+    else if (c->tau <= 4096) {
+      c->potri = true;
+      if (potri_needs_ws(c->tau, fel))
+        TRYC(pmalloc(c, &c->pws, (size_t)c->nslots * potri_ws_elems(c->tau) * fel));
+    }
   }
   if (!t_batch_member && !c->sparse && (sketch == RS_SUBSAMPLE || sketch == RS_COUNT || sketch == RS_SUBCOUNT) && o.iter_ctas >= 0) {
     // persistent iteration kernel over the whole GPU: S^T A blocked by CTA, M^+ per
     // slot and the all-reduce buffers
     bool fits = false;
     if (!c->mixed()) fits = wide_plan<double, double>(m, c->tau, o.iter_ctas, c->chunk, &c->wide);
-    else if (c->f64_factor()) fits = wide_plan<float, double>(m, c->tau, o.iter_ctas, c->chunk, &c->wide);
     else fits = wide_plan<float, float>(m, c->tau, o.iter_ctas, c->chunk, &c->wide);
     if (fits) {
       const size_t fel = c->f64_factor() ? 8 : 4;
       c->pld = round_up(c->tau, 4);
       c->p_slot = c->tau * c->pld;
-      TRYC(pmalloc(c, (void**)&c->Pm, (size_t)c->nslots * c->p_slot * fel));
+      TRYC(pmalloc(c, (void**)&c->Pm, (size_t)c->nslots * c->p_slot * (c->mixed() ? 4 : 8)));
       const size_t nwords = (size_t)2 * c->wide.nblk * (c->tau + 1) * 2;
       TRY(dalloc(c, &c->xpart, nwords));
       TRY(dalloc(c, &c->xflags, 1));
@@ -1300,8 +1317,11 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
                    sa_msys_fits<float>(m, c->tau, round_up((sketch == RS_COUNT) ? m : (sketch == RS_SUBCOUNT ? c->s : c->tau), 4));
       if (c->sweep_p) TRY(dalloc(c, &c->Mf, (size_t)c->nslots * c->tau * c->tau));
       // otherwise M^+ by factor, inverse and product in one kernel
-      if (!c->sweep_p && c->tau <= 4096)
-        TRYC(pmalloc(c, &c->pws, (size_t)c->nslots * potri_ws_elems(c->tau) * fel));
+      if (!c->sweep_p && c->tau <= 4096) {
+        c->potri = true;
+        if (potri_needs_ws(c->tau, fel))
+          TRYC(pmalloc(c, &c->pws, (size_t)c->nslots * potri_ws_elems(c->tau) * fel));
+      }
     } else {
       cudaGetLastError();
     }
@@ -1418,6 +1438,7 @@ rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int3
   CKC(c, launch_init_state(st, c->m, c->b, c->w, c->wp, c->r, c->rp, c->u));
   // a timed-out earlier solve left the abort word raised
   if (c->xabort) CKC(c, cudaMemsetAsync(c->xabort, 0, sizeof(int32_t), st));
+  if (c->avg) CKC(c, cudaMemsetAsync(c->wsum, 0, c->m * sizeof(double), st));  // w^0 = 0
   if (c->learned) CKC(c, cudaMemsetAsync(c->lp_last, 0xFF, c->m * sizeof(int32_t), st));
   if (!std::isfinite(c->r0)) {
     c->err = "rs_solve: NaN or Inf in b (||b|| is not finite)";
@@ -1472,6 +1493,7 @@ rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int3
     }
   }
   c->solve_ms = ms;
+  c->last_iters = iters;
   if ((s = copy_out_w(c, w_out, w_on_device)) != RS_OK) return s;
   if (hist_out) CKC(c, cudaMemcpyAsync(hist_out, c->hist, (iters + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
   CKC(c, cudaStreamSynchronize(st));
@@ -1479,12 +1501,45 @@ rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int3
   return result;
 }
 
+rs_status rs_set_averaging(rs_ctx* c, int32_t on) {
+  if (!c) { set_global_error("rs_set_averaging: null context"); return RS_EINVAL; }
+  DeviceGuard dg(c->device);
+  if (!on) { c->avg = false; return RS_OK; }
+  if (!c->use_wide)
+    FAILC(c, RS_EUNSUPPORTED, "rs_set_averaging: needs the persistent iteration kernel "
+                              "(subsample, count or subcount sketch of dense A)");
+  if (!c->wsum) {
+    rs_status s = dalloc(c, &c->wsum, c->m);
+    if (s != RS_OK) return s;
+  }
+  c->avg = true;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }  // kernels read wsum
+  return RS_OK;
+}
+
+rs_status rs_get_average(rs_ctx* c, double* w_out, int32_t w_on_device) {
+  if (!c || !w_out) { set_global_error("rs_get_average: null argument"); return RS_EINVAL; }
+  if (!c->avg) FAILC(c, RS_EINVAL, "rs_get_average: averaging is off (rs_set_averaging)");
+  DeviceGuard dg(c->device);
+  // mean of w^0..w^t (t iterations) into u, then out as w (dual: X^T of the mean)
+  CKC(c, launch_scale(c->stream, c->wsum, 1.0 / (double)(c->last_iters + 1), c->m, c->u));
+  double* keep = c->w;
+  c->w = c->u;
+  rs_status s = copy_out_w(c, w_out, w_on_device);
+  c->w = keep;
+  if (s != RS_OK) return s;
+  CKC(c, cudaStreamSynchronize(c->stream));
+  CKC(c, cudaMemsetAsync(c->u, 0, c->m * sizeof(double), c->stream));
+  CKC(c, cudaStreamSynchronize(c->stream));
+  return RS_OK;
+}
+
 rs_status rs_chunking(const rs_ctx* c, int64_t* chunk, int32_t* refresh_every,
                       int32_t* fused_potri) {
   if (!c) return RS_EINVAL;
   if (chunk) *chunk = c->chunk;
   if (refresh_every) *refresh_every = c->mixed() ? c->refresh_every : 0;
-  if (fused_potri) *fused_potri = c->pws != nullptr ? 1 : 0;
+  if (fused_potri) *fused_potri = c->potri ? 1 : 0;
   return RS_OK;
 }
 
@@ -1720,6 +1775,7 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
   };
   const double el = (double)c->elem();
   const double fel = c->f64_factor() ? 8.0 : 4.0;
+  const double pel = (c->use_wide && c->mixed()) ? 4.0 : fel;  // M^+ as the iterations read it
   const double m = (double)c->m, tau = (double)c->tau;
   const int ns = (int)c->nslots;
   const double rows = c->sketch == RS_COUNT ? m : (c->sketch == RS_SUBCOUNT ? (double)c->s : tau);
@@ -1811,7 +1867,7 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
           grp("sweep").flops = nsl * tau * tau * tau;
           if (s != RS_OK) break;
         }
-        if (!sweep && c->use_wide && c->pws != nullptr) {
+        if (!sweep && c->use_wide && c->potri) {
           // factor, inverse and M^+ in one kernel
           s = timed("potri", [&]() { return enqueue_potri(c, c->stream, 0, ns); });
           // Cholesky tau^3 / 3, triangular inverse tau^3 / 3, L^{-T} L^{-1} tau^3 / 3
@@ -1859,7 +1915,7 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
         // of every iteration; the persistent kernel reads and writes w, w_prev, r,
         // r_prev once per launch, the cluster kernel every iteration
         grp("iterate").bytes = c->use_wide
-            ? (double)nit * (tau * m * el + tau * tau * fel + 4.0 * m) + 64.0 * m
+            ? (double)nit * (tau * m * el + tau * tau * pel + 4.0 * m) + 64.0 * m
             : (double)nit * (tau * m * el + tau * tau * fel + 80.0 * m);
         grp("iterate").flops = (double)nit * (2.0 * tau * m + 2.0 * tau * tau + 10.0 * m);
         grp("iterate").iters += nit;
@@ -1909,6 +1965,8 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
   return RS_OK;
 }
 
+static rs_status lp_alloc(rs_ctx* c);
+
 rs_status rs_set_proposal(rs_ctx* c, const uint16_t* w_bf16, double eps) {
   if (!c) { set_global_error("rs_set_proposal: null context"); return RS_EINVAL; }
   DeviceGuard dg(c->device);
@@ -1923,6 +1981,21 @@ rs_status rs_set_proposal(rs_ctx* c, const uint16_t* w_bf16, double eps) {
   int64_t np2 = 1;
   while (np2 < c->m) np2 <<= 1;
   if (np2 * 8 > 200 * 1024) FAILC(c, RS_EUNSUPPORTED, "rs_set_proposal: m > 16384");
+  rs_status s0 = lp_alloc(c);
+  if (s0 != RS_OK) return s0;
+  cudaStream_t st = c->stream;
+  c->lp_uniform = (w_bf16 == nullptr);
+  if (w_bf16) CKC(c, cudaMemcpyAsync(c->lp_w, w_bf16, kMlpParams * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
+  c->lp_eps = (float)eps;
+  c->lp_fixed = false;
+  c->learned = true;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  CKC(c, cudaStreamSynchronize(st));
+  return RS_OK;
+}
+
+// buffers of the scored proposal and the static features (once per context)
+static rs_status lp_alloc(rs_ctx* c) {
   cudaStream_t st = c->stream;
   const size_t m = (size_t)c->m;
   if (!c->lp_w) {
@@ -1941,18 +2014,127 @@ rs_status rs_set_proposal(rs_ctx* c, const uint16_t* w_bf16, double eps) {
       CKC(c, launch_lp_static<double>(st, static_cast<const double*>(c->A), c->ld, c->m, c->lp_raw,
                                       c->lp_zstat));
   }
-  c->lp_uniform = (w_bf16 == nullptr);
-  if (w_bf16) CKC(c, cudaMemcpyAsync(c->lp_w, w_bf16, kMlpParams * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
-  c->lp_eps = (float)eps;
+  return RS_OK;
+}
+
+rs_status rs_collect(rs_ctx* c, const double* w_star, int64_t n_iters, double tol, float* Z_out,
+                     float* y_out, int64_t* n_rows) {
+  if (!c || !w_star || !Z_out || !y_out || !n_rows || n_iters < 0 || !(tol >= 0.0)) {
+    set_global_error("rs_collect: bad arguments");
+    return RS_EINVAL;
+  }
+  *n_rows = 0;
+  if (!c->learned || c->lp_fixed)
+    FAILC(c, RS_EINVAL, "rs_collect: needs a proposal (rs_set_proposal, weights or uniform)");
+  if (c->mixed() || c->chunk != 1 || c->mom.kind != RS_MOM_NONE)
+    FAILC(c, RS_EINVAL, "rs_collect: needs plain FP64, chunk = 1 and no momentum (the "
+                        "projection identity of the labels)");
+  if (n_iters == 0) return RS_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t st = c->stream;
+  rs_status s = read_ctrl(c);
+  if (s != RS_OK) return s;
+  const int64_t k0 = c->ctrl_h->k;
+  if ((s = ensure_schedule(c, k0 + n_iters + 2)) != RS_OK) return s;
+  const int64_t cap = n_iters * c->tau;
+  double *ws = nullptr, *e2 = nullptr;
+  float *Zd = nullptr, *yd = nullptr;
+  int64_t* cnt = nullptr;
+  auto release = [&]() { pfree(c, ws); pfree(c, e2); pfree(c, Zd); pfree(c, yd); pfree(c, cnt); };
+  if ((s = dalloc(c, &ws, c->m)) != RS_OK || (s = dalloc(c, &e2, 1)) != RS_OK ||
+      (s = dalloc(c, &Zd, cap * 4)) != RS_OK || (s = dalloc(c, &yd, cap)) != RS_OK ||
+      (s = dalloc(c, &cnt, 1)) != RS_OK) {
+    release();
+    return s;
+  }
+  // the same control state as rs_step: every iteration runs until the collection stops
+  Ctrl* h = c->ctrl_h;
+  h->stop = 0; h->pending = 0; h->status = 0; h->ticket = 0; h->no_stop = 1;
+  h->predict = 0; h->kcap = 0;
+  h->max_iters = k0 + n_iters;
+  h->r0 = c->r0 > 0.0 ? c->r0 : 1.0;
+  cudaError_t e = cudaMemcpyAsync(ws, w_star, c->m * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int64_t), st);
+  if (e != cudaSuccess) { release(); FAILC(c, RS_ECUDA, std::string("rs_collect: ") + cudaGetErrorString(e)); }
+  if ((s = write_ctrl(c)) != RS_OK) { release(); return s; }
+  for (int64_t it = 0; it < n_iters && s == RS_OK; ++it) {
+    const int64_t k = k0 + it;
+    // ||e_k||_A^2 and the stop test; the features and the rows drawn at k; the step's
+    // r_C and delta; the labels; then the iteration itself
+    e = launch_collect_pre(st, c->ctrl, c->w, ws, c->r, c->m, tol, e2);
+    if (e == cudaSuccess)
+      e = launch_lp_features(st, c->ctrl, k, c->lp_zstat, c->lp_raw, c->lp_stats, c->r, c->lp_last,
+                             c->m, c->lp_score, c->lp_feat);
+    if (e != cudaSuccess) break;
+    if ((s = enqueue_phase1(c, 1, k, 1)) != RS_OK) break;
+    if ((s = enqueue_delta(c, 1, k)) != RS_OK) break;
+    e = cudaMemsetAsync(c->u, 0, c->m * sizeof(double), st);
+    if (e == cudaSuccess)
+      e = launch_collect_rows(st, c->ctrl, c->perm, c->boff, c->tau, c->lp_feat, c->rS, c->delta,
+                              e2, c->m, cap, Zd, yd, cnt);
+    if (e != cudaSuccess) break;
+    s = enqueue_chunk(c, false);
+    if (s == RS_OK && it % 64 == 63) {  // stop enqueueing once the device has stopped
+      if ((s = read_ctrl(c)) != RS_OK) break;
+      if (h->stop) break;
+    }
+  }
+  if (s != RS_OK) { release(); return s; }
+  if (e != cudaSuccess) { release(); FAILC(c, RS_ECUDA, std::string("rs_collect: ") + cudaGetErrorString(e)); }
+  int64_t n = 0;
+  e = cudaMemcpyAsync(&n, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(Z_out, Zd, n * 4 * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(y_out, yd, n * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  release();
+  if (e != cudaSuccess) FAILC(c, RS_ECUDA, std::string("rs_collect: ") + cudaGetErrorString(e));
+  if ((s = read_ctrl(c)) != RS_OK) return s;
+  if (h->status == RS_ETIMEOUT) FAILC(c, RS_ETIMEOUT, "rs_collect: a bounded device-side wait gave up");
+  *n_rows = n;
+  // leave the context ready for further steps or probes
+  h->stop = 0;
+  h->max_iters = INT64_MAX;
+  if ((s = write_ctrl(c)) != RS_OK) return s;
+  CKC(c, cudaStreamSynchronize(st));
+  return RS_OK;
+}
+
+rs_status rs_set_sampling(rs_ctx* c, int32_t kind) {
+  if (!c) { set_global_error("rs_set_sampling: null context"); return RS_EINVAL; }
+  DeviceGuard dg(c->device);
+  if (kind == RS_SAMPLE_UNIFORM) {  // the sketch's own uniform draws
+    c->learned = false;
+    c->lp_fixed = false;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    return RS_OK;
+  }
+  if (kind != RS_SAMPLE_DIAG) FAILC(c, RS_EINVAL, "rs_set_sampling: unknown sampling");
+  if (c->sketch != RS_SUBSAMPLE || c->sparse)
+    FAILC(c, RS_EUNSUPPORTED, "rs_set_sampling: importance sampling draws subsample sketches of dense A");
+  int64_t np2 = 1;
+  while (np2 < c->m) np2 <<= 1;
+  if (np2 * 8 > 200 * 1024) FAILC(c, RS_EUNSUPPORTED, "rs_set_sampling: m > 16384");
+  rs_status s = lp_alloc(c);
+  if (s != RS_OK) return s;
+  if (c->mixed())
+    CKC(c, launch_lp_diag_score<float>(c->stream, static_cast<const float*>(c->A), c->ld, c->m,
+                                       c->lp_score));
+  else
+    CKC(c, launch_lp_diag_score<double>(c->stream, static_cast<const double*>(c->A), c->ld, c->m,
+                                        c->lp_score));
+  c->lp_uniform = true;  // no network: the scores stay ln A_jj
+  c->lp_eps = 0.0f;
+  c->lp_fixed = true;
   c->learned = true;
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
-  CKC(c, cudaStreamSynchronize(st));
+  CKC(c, cudaStreamSynchronize(c->stream));
   return RS_OK;
 }
 
 rs_status rs_proposal_features(rs_ctx* c, float* Z_out) {
   if (!c || !Z_out) return RS_EINVAL;
-  if (!c->learned) FAILC(c, RS_EINVAL, "rs_proposal_features: no proposal set");
+  if (!c->learned || c->lp_fixed) FAILC(c, RS_EINVAL, "rs_proposal_features: no learned proposal set");
   DeviceGuard dg(c->device);
   rs_status s = read_ctrl(c);
   if (s != RS_OK) return s;
@@ -2023,6 +2205,9 @@ struct rs_batch {
   int nstreams = 1;                    // side streams of phase 1 (tuned)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double setup_ms = 0.0, solve_ms = 0.0, tune_ms = 0.0;
+  std::string tune_cache;              // file of the autotuner's choices ("" = none)
+  bool tune_cached = false;            // the choice of this batch came from that file
+  int sketch = 0;
   std::string err;
   bool mixed() const { return precision == RS_MIXED; }
 };
@@ -2338,9 +2523,73 @@ bool batch_fits(const rs_batch* b, int threads) {
                                                             b->perm_max, b->pld_max, threads)) > 0;
 }
 
+// The autotuner's cache: one line per batch shape, "<key> <threads> <streams>". The
+// key holds everything the choice depends on (problem count and sizes, right-hand
+// sides, precision, sketch, chunk, and the GPU's SM count).
+std::string batch_tune_key(const rs_batch* b) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "v1:P=%d:nrhs=%d:prec=%d:sketch=%d:chunk=%lld:tau=%lld:bq=%lld:"
+                "d=%lld:perm=%lld:pld=%lld:sms=%d", b->P, b->nrhs, b->precision, b->sketch,
+                (long long)b->chunk, (long long)b->tau_max, (long long)b->bq_max,
+                (long long)b->d_max, (long long)b->perm_max, (long long)b->pld_max, nsm);
+  return buf;
+}
+
+bool tune_cache_read(const std::string& path, const std::string& key, int* threads, int* streams) {
+  std::FILE* f = std::fopen(path.c_str(), "r");
+  if (!f) return false;
+  char k[256];
+  int t = 0, n = 0;
+  bool found = false;
+  while (std::fscanf(f, "%255s %d %d", k, &t, &n) == 3)
+    if (key == k) { *threads = t; *streams = n; found = true; }  // the last line wins
+  std::fclose(f);
+  return found;
+}
+
+// rewrites the file with this key's line replaced (best effort: a failure to write
+// leaves the tuning in effect for this batch only)
+void tune_cache_write(const std::string& path, const std::string& key, int threads, int streams) {
+  std::vector<std::string> keep;
+  if (std::FILE* f = std::fopen(path.c_str(), "r")) {
+    char k[256];
+    int t = 0, n = 0;
+    while (std::fscanf(f, "%255s %d %d", k, &t, &n) == 3)
+      if (key != k) keep.push_back(std::string(k) + " " + std::to_string(t) + " " + std::to_string(n));
+    std::fclose(f);
+  }
+  keep.push_back(key + " " + std::to_string(threads) + " " + std::to_string(streams));
+  const std::string tmp = path + ".tmp";
+  std::FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  bool ok = true;
+  for (const std::string& l : keep) ok = ok && std::fprintf(f, "%s\n", l.c_str()) > 0;
+  ok = (std::fclose(f) == 0) && ok;
+  if (ok) std::rename(tmp.c_str(), path.c_str());
+  else std::remove(tmp.c_str());
+}
+
 // autotuner: one steady-state chunk (tol = 0, no pair stops) per candidate CTA size
-// of the iteration kernel and number of phase-1 streams; keeps the fastest
+// of the iteration kernel and number of phase-1 streams; keeps the fastest. With a
+// cache file, a shape tuned before is taken from it (if it still fits) and a new
+// choice is written to it.
 rs_status batch_tune(rs_batch* b) {
+  const std::string key = b->tune_cache.empty() ? std::string() : batch_tune_key(b);
+  if (!key.empty()) {
+    int t = 0, ns = 0;
+    if (tune_cache_read(b->tune_cache, key, &t, &ns) && (t == 128 || t == 256 || t == 512) &&
+        ns >= 1 && ns <= kBatchMaxStreams && (ns == 1 || ns <= b->P) && b->bq_max <= 4 * t &&
+        batch_fits(b, t)) {
+      b->threads = t;
+      b->nstreams = ns;
+      b->tuned = true;
+      b->tune_cached = true;
+      return RS_OK;
+    }
+  }
   const int thr[] = {128, 256, 512};
   const int nss[] = {1, 2, kBatchMaxStreams};
   float best = -1.f;
@@ -2381,6 +2630,8 @@ rs_status batch_tune(rs_batch* b) {
   b->threads = bt;
   b->nstreams = bs;
   b->tuned = true;
+  b->tune_cached = false;
+  if (!key.empty()) tune_cache_write(b->tune_cache, key, bt, bs);
   return done(RS_OK);
 }
 
@@ -2535,7 +2786,6 @@ rs_status rs_create_batch(int32_t P, const rs_matrix* Xs, const double* const* Y
   rs_opts o;
   rs_default_opts(&o);
   if (opts) o = *opts;
-  if (o.precision == RS_MIXED) o.chol_fp64 = 0;
   // the batch refreshes at every chunk end: its chunk is the refresh period
   if (o.precision == RS_MIXED && o.chunk <= 0) o.chunk = o.refresh_every > 0 ? o.refresh_every : 300;
   for (int p = 0; p < P; ++p) {
@@ -2549,6 +2799,8 @@ rs_status rs_create_batch(int32_t P, const rs_matrix* Xs, const double* const* Y
   b->P = P;
   b->nrhs = nrhs;
   b->precision = o.precision;
+  b->sketch = sketch;
+  if (o.tune_cache != nullptr) b->tune_cache = o.tune_cache;
   const rs_status s = batch_init(b, Xs, Ys, y_on_device, lambdas, sketch, taus, mom, seed, o);
   if (s != RS_OK) {
     g_batch_err = b->err;

@@ -285,13 +285,14 @@ cudaError_t launch_factor_inv(cudaStream_t st, const Ctrl* ctrl, int force, int 
 
 // ---------------------------------------------------------------------------
 // phase 1 for the persistent iteration kernel: P = M^+ = L^{-T} L^{-1} (eq. (14)),
-// one CTA of kPotriThreads per slot, two CTAs per SM.
+// one CTA of kPotriThreads (four warps) per slot, four CTAs per SM.
 //
 // FP64 arithmetic runs at about one warp instruction per 64 cycles on each of an
 // SM's four schedulers, so the factor is bound by how many schedulers have FP64
-// work at every moment, not by memory: the tiles live in global memory (L1/L2), two
-// slots share an SM so that one slot's narrow phases (a diagonal tile, the last
-// trailing updates) overlap the other's wide ones, and every phase is cut into
+// work at every moment, not by memory: the tiles live in global memory (L1/L2), four
+// slots share an SM (one warp of each per scheduler) so that one slot's narrow phases
+// (a diagonal tile, the last trailing updates) overlap the others' wide ones, and a
+// chunk of 600 slots runs in one wave on 152 SMs; every phase is cut into
 // 32 x 32 tile tasks:
 //   1. Cholesky, right-looking, with the least-norm pivot rule of k_factor_blk;
 //      the diagonal tiles end up holding L_II^{-1};
@@ -303,13 +304,17 @@ cudaError_t launch_factor_inv(cudaStream_t st, const Ctrl* ctrl, int force, int 
 //      P_{IJ} = sum_{K >= I} X_{KI}^T X_{KJ} for the lower tiles I >= J only
 //      (a sixth of a full tau^3 product), each written with its transpose.
 // ---------------------------------------------------------------------------
-constexpr int kPotriThreads = 256;
+constexpr int kPotriThreads = 128;
 
 // L (lower tiles incl. the diagonal) + the strictly lower tiles of X
 __host__ __device__ size_t potri_ws_elems(int64_t tau) {
   const int64_t P = (tau + NBK - 1) / NBK;
   return (size_t)(ntiles_lower(P) + P * (P - 1) / 2) * TILE;
 }
+// the tiles stay in shared memory up to this size (tau <= 128 in FP64), else they
+// live in a global work space of potri_ws_elems(tau) elements per slot
+constexpr size_t kPotriSmemMax = 200 * 1024;
+bool potri_needs_ws(int64_t tau, size_t elem) { return potri_ws_elems(tau) * elem > kPotriSmemMax; }
 
 template <typename T>
 __device__ __forceinline__ T* xtile_at(T* base, int64_t I, int64_t J) {  // I > J
@@ -339,17 +344,18 @@ __device__ __forceinline__ void wtile_mma_g(T (&acc)[8][4], const T* __restrict_
 
 // T: arithmetic and L^{-1}; TP: the stored P (FP32 for an FP32 iteration kernel)
 template <typename T, typename TP>
-__global__ void __launch_bounds__(kPotriThreads, 2) k_potri(
+__global__ void __launch_bounds__(kPotriThreads, 4) k_potri(
     const Ctrl* __restrict__ ctrl, int force, int nslots, const double* __restrict__ M,
     int64_t m_slot, int64_t tau, T* __restrict__ Linv, int64_t l_slot, TP* __restrict__ Pout,
-    int64_t pld, int64_t p_slot, T* __restrict__ ws, int32_t* __restrict__ ndropped) {
+    int64_t pld, int64_t p_slot, T* __restrict__ ws, int use_smem, int32_t* __restrict__ ndropped) {
+  extern __shared__ __align__(16) unsigned char potri_smem[];
   __shared__ unsigned char dropped[4096];
   __shared__ double s_red[32];
   const int64_t s = blockIdx.x;
   if (s >= active_slots(ctrl, force, nslots)) return;
   const int64_t P = (tau + NBK - 1) / NBK;
   const int64_t tp = P * NBK;
-  T* tiles = ws + s * (int64_t)potri_ws_elems(tau);
+  T* tiles = use_smem ? reinterpret_cast<T*>(potri_smem) : ws + s * (int64_t)potri_ws_elems(tau);
   T* xt = tiles + ntiles_lower(P) * TILE;
   const double* Ms = M + s * m_slot;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
@@ -1035,9 +1041,17 @@ template <typename T, typename TP>
 cudaError_t launch_potri(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, const double* M,
                          int64_t m_slot, int64_t tau, T* Linv, int64_t l_slot, TP* P, int64_t pld,
                          int64_t p_slot, T* ws, int32_t* ndropped) {
-  if (tau < 1 || tau > 4096 || ws == nullptr) return cudaErrorInvalidValue;
-  k_potri<T, TP><<<nslots, kPotriThreads, 0, st>>>(ctrl, force, nslots, M, m_slot, tau, Linv,
-                                                    l_slot, P, pld, p_slot, ws, ndropped);
+  const int use_smem = potri_needs_ws(tau, sizeof(T)) ? 0 : 1;
+  if (tau < 1 || tau > 4096 || (!use_smem && ws == nullptr)) return cudaErrorInvalidValue;
+  const size_t smem = use_smem ? potri_ws_elems(tau) * sizeof(T) : 0;
+  if (use_smem) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        k_potri<T, TP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPotriSmemMax);
+    if (e != cudaSuccess) return e;
+  }
+  k_potri<T, TP><<<nslots, kPotriThreads, smem, st>>>(ctrl, force, nslots, M, m_slot, tau, Linv,
+                                                       l_slot, P, pld, p_slot, ws, use_smem,
+                                                       ndropped);
   return cudaGetLastError();
 }
 template cudaError_t launch_potri<float, float>(cudaStream_t, const Ctrl*, int, int, const double*,

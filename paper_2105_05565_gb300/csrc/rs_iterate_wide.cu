@@ -54,7 +54,7 @@ constexpr uint64_t kDrainNs = 2000000000ull;
 
 struct WideLayout {
   int64_t qs, E, G;
-  size_t sa, pb, iv, mine, tot, dT, red, st, coef, prow, pinv, hn2, bars, gb, total;
+  size_t sa, pb, iv, mine, tot, dT, red, st, coef, prow, pinv, hn2, bars, gb, sum, total;
 };
 
 __host__ __device__ inline size_t wl_take(size_t& o, size_t bytes) {
@@ -86,6 +86,7 @@ __host__ __device__ inline WideLayout wide_layout(int64_t q, int64_t tau, int64_
   L.hn2 = wl_take(o, (size_t)(chunk + 1) * 8);      // ||r_k||^2 of the tested iterations
   L.bars = wl_take(o, 8 * 8);                       // mbarriers
   L.gb = wl_take(o, (size_t)2 * chunk * 8);         // gamma_k, beta_k of the chunk
+  L.sum = wl_take(o, (size_t)L.qs * 8);             // running sums of the own w rows
   L.total = o;
   return L;
 }
@@ -370,6 +371,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   uint64_t* iv_full = bars + 2;    // 3
   uint64_t* p_full = bars + 5;     // 1
   uint64_t* xbar = bars + 6;       // 1
+  double* ssum = reinterpret_cast<double*>(smem + L.sum);  // sum of w^0..w^k (averaging)
   double* sgam = reinterpret_cast<double*>(smem + L.gb);
   double* sbet = sgam + g.chunk;
   float* sgamf = reinterpret_cast<float*>(sgam);  // kFP: gamma_k, beta_k in FP32
@@ -396,6 +398,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
     }
   }
   for (int64_t i = tid; i < qc; i += kWThreads) {
+    ssum[i] = g.wsum != nullptr ? g.wsum[ilo + i] : 0.0;
     if constexpr (kFP) {
       fr[i] = split2(g.r[ilo + i]);
       frp[i] = split2(g.rp[ilo + i]);
@@ -704,8 +707,10 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
           const float2 rn = add_pf(ri, fmaf(bk, dr, -gk * (float)asum));
           fr[i] = rn;
           frp[i] = ri;
-          fw[i] = add_pf(wi, fmaf(bk, dw, -gk * ui));
+          const float2 wn = add_pf(wi, fmaf(bk, dw, -gk * ui));
+          fw[i] = wn;
           fwp[i] = wi;
+          if (g.wsum != nullptr) ssum[i] += (double)wn.x + (double)wn.y;
           const int32_t t = pinv[i];  // staged row of slot k + 1
           if (t >= 0) coef[t] = prow[t] < 0 ? -rn.x : rn.x;
           const float v = rn.x * inv_r0f;
@@ -730,8 +735,10 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
           const int32_t t = pinv[i];  // staged row of slot k + 1
           if (t >= 0) coef[t] = (TF)(prow[t] < 0 ? -rn : rn);
           srp[i] = ri;
-          sw[i] = (1.0 + bk) * wi - bk * wpi - gk * ui;
+          const double wn = (1.0 + bk) * wi - bk * wpi - gk * ui;
+          sw[i] = wn;
           swp[i] = wi;
+          if (g.wsum != nullptr) ssum[i] += wn;
           sq += rn * rn;
         }
         if (wid * 32 < qc) sq = warp_sum(sq);
@@ -762,6 +769,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   }
   __syncthreads();
   for (int64_t i = tid; i < qc; i += kWThreads) {
+    if (g.wsum != nullptr) g.wsum[ilo + i] = ssum[i];
     if constexpr (kFP) {
       g.r[ilo + i] = join2(fr[i]);
       g.rp[ilo + i] = join2(frp[i]);

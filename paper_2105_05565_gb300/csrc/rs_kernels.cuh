@@ -84,6 +84,7 @@ cudaError_t launch_factor_inv(cudaStream_t st, const Ctrl* ctrl, int force, int 
 // P = M^+ (and, if Linv != nullptr, the zeroed L^{-1}) per slot; ws holds
 // potri_ws_elems(tau) elements per slot
 __host__ __device__ size_t potri_ws_elems(int64_t tau);
+bool potri_needs_ws(int64_t tau, size_t elem);  // false: the tiles fit shared memory
 template <typename T, typename TP>
 cudaError_t launch_potri(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, const double* M,
                          int64_t m_slot, int64_t tau, T* Linv, int64_t l_slot, TP* P, int64_t pld,
@@ -152,6 +153,7 @@ struct WideArgs {
   int64_t sub_end;  // iterations run while k < k0 + sub_end (sub_end <= chunk)
   uint64_t wait_ns;  // bound of every device-side wait (global timer)
   int64_t stall_ns;  // fault injection: CTA 0 publishes its first partials this late
+  double* wsum;      // nullptr, or the running sum of the iterates w^0..w^k (m)
   int nblk;
   int nsab;                        // buffers of the staged S^T A block (2, or 1 when tight)
 };
@@ -285,11 +287,21 @@ cudaError_t launch_lp_static(cudaStream_t st, const T* A, int64_t lda, int64_t m
 // plans of the chunk's slots drawn from the proposal (w null: uniform); stats: 5
 // doubles, score: m floats of work space; last: last visit per row (updated when
 // update_age)
+cudaError_t launch_collect_pre(cudaStream_t st, Ctrl* ctrl, const double* w, const double* wstar,
+                               const double* r, int64_t m, double tol, double* e2_out);
+cudaError_t launch_collect_rows(cudaStream_t st, const Ctrl* ctrl, const int32_t* perm,
+                                const int32_t* boff, int64_t tau, const float* feat,
+                                const double* rS, const double* delta, const double* e2,
+                                int64_t m, int64_t cap, float* Z, float* y, int64_t* count);
+template <typename T>
+cudaError_t launch_lp_diag_score(cudaStream_t st, const T* A, int64_t lda, int64_t m,
+                                 float* score);
 cudaError_t launch_lp_plans(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, int64_t k0_arg,
                             uint64_t seed, const uint16_t* w, float eps, const float* zstat,
                             float* dyn, double* stats, const double* r, int32_t* last, int64_t m,
                             int64_t tau, float* score, int32_t* perm, int64_t perm_stride,
-                            int32_t* boff, int64_t boff_stride, bool update_age);
+                            int32_t* boff, int64_t boff_stride, bool update_age,
+                            bool fixed_score);
 // the m x 4 feature rows at iteration k0 (the network's inputs); dyn: 2 m floats
 cudaError_t launch_lp_features(cudaStream_t st, const Ctrl* ctrl, int64_t k0, const float* zstat,
                                float* dyn, double* stats, const double* r, const int32_t* last,
@@ -324,6 +336,7 @@ cudaError_t launch_init_state(cudaStream_t st, int64_t m, const double* b, doubl
                               double* r, double* rp, double* u);
 // ctrl->k0 = ctrl->k (first iteration of a chunk)
 cudaError_t launch_chunk_begin(cudaStream_t st, Ctrl* ctrl);
+cudaError_t launch_scale(cudaStream_t st, const double* in, double s, int64_t m, double* out);
 
 // ---- X^T X on the tensor cores (rs_tc_gemm.cu) ----
 // A (lower triangle and diagonal, d x lda FP32) = X^T X + lambda I, TF32 inputs, FP32

@@ -124,6 +124,92 @@ cudaError_t launch_lp_static(cudaStream_t st, const T* A, int64_t lda, int64_t m
   return cudaGetLastError();
 }
 
+// ---- training data from a solver trajectory (rs_collect) ----
+// Before iteration k: e2 = ||w_k - w*||_A^2 = (w_k - w*) . r_k (r_k = A w_k - b) and
+// ||r_k||; the collection stops (ctrl->stop) once e2 <= 0 or ||r_k|| <= tol ||r_0||.
+// One block; FP64 sums in a fixed order.
+__global__ void __launch_bounds__(1024) k_collect_pre(Ctrl* __restrict__ ctrl,
+                                                      const double* __restrict__ w,
+                                                      const double* __restrict__ wstar,
+                                                      const double* __restrict__ r, int64_t m,
+                                                      double tol, double* __restrict__ e2_out) {
+  __shared__ double s_red[32];
+  if (stopped(ctrl)) return;
+  double e2 = 0.0, n2 = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+    e2 += (w[i] - wstar[i]) * r[i];
+    n2 += r[i] * r[i];
+  }
+  e2 = block_sum(e2, s_red);
+  n2 = block_sum(n2, s_red);
+  if (threadIdx.x == 0) {
+    *e2_out = e2;
+    if (!(e2 > 0.0) || sqrt(n2) <= tol * ctrl->r0) ctrl->stop = 1;
+    __threadfence();
+  }
+}
+
+// The rows drawn at iteration k (bucket p of the slot-0 plan holds one row for the
+// subsample sketch) with their chunk-start features and the targets
+//   y_p = (1/2) ln(m max(a_p, 0) / e2 + 1e-3),   a_p = (r_C)_p delta_p,
+// where r_C . delta is the exact decrease of ||w - w*||_A^2 of the step without
+// momentum (the projection identity of Section 3). Appended at *count (one block).
+__global__ void k_collect_rows(const Ctrl* __restrict__ ctrl, const int32_t* __restrict__ perm,
+                               const int32_t* __restrict__ boff, int64_t tau,
+                               const float* __restrict__ feat, const double* __restrict__ rS,
+                               const double* __restrict__ delta, const double* __restrict__ e2p,
+                               int64_t m, int64_t cap, float* __restrict__ Z,
+                               float* __restrict__ y, int64_t* __restrict__ count) {
+  if (stopped(ctrl)) return;
+  const int64_t base = *count;
+  const double e2 = *e2p;
+  for (int64_t p = threadIdx.x; p < tau; p += blockDim.x) {
+    if (base + p >= cap) continue;
+    const int64_t row = entry_row(perm[boff[p]]);
+#pragma unroll
+    for (int f = 0; f < kNF; ++f) Z[(base + p) * kNF + f] = feat[row * kNF + f];
+    const double a = rS[p] * delta[p];
+    y[base + p] = (float)(0.5 * log((double)m * fmax(a, 0.0) / e2 + 1e-3));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *count = base + tau < cap ? base + tau : cap;
+}
+
+cudaError_t launch_collect_pre(cudaStream_t st, Ctrl* ctrl, const double* w, const double* wstar,
+                               const double* r, int64_t m, double tol, double* e2_out) {
+  k_collect_pre<<<1, 1024, 0, st>>>(ctrl, w, wstar, r, m, tol, e2_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_collect_rows(cudaStream_t st, const Ctrl* ctrl, const int32_t* perm,
+                                const int32_t* boff, int64_t tau, const float* feat,
+                                const double* rS, const double* delta, const double* e2,
+                                int64_t m, int64_t cap, float* Z, float* y, int64_t* count) {
+  k_collect_rows<<<1, 256, 0, st>>>(ctrl, perm, boff, tau, feat, rS, delta, e2, m, cap, Z, y,
+                                    count);
+  return cudaGetLastError();
+}
+
+// ---- importance sampling (Section 7): fixed scores s_j = ln A_jj, so that the
+// proposal with eps = 0 is p_j = exp(s_j) / sum_l exp(s_l) = A_jj / trace(A) ----
+template <typename T>
+__global__ void k_lp_diag_score(const T* __restrict__ A, int64_t lda, int64_t m,
+                                float* __restrict__ score) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < m) score[j] = (float)log((double)A[j * lda + j]);
+}
+
+template <typename T>
+cudaError_t launch_lp_diag_score(cudaStream_t st, const T* A, int64_t lda, int64_t m,
+                                 float* score) {
+  k_lp_diag_score<T><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(A, lda, m, score);
+  return cudaGetLastError();
+}
+template cudaError_t launch_lp_diag_score<float>(cudaStream_t, const float*, int64_t, int64_t,
+                                                 float*);
+template cudaError_t launch_lp_diag_score<double>(cudaStream_t, const double*, int64_t, int64_t,
+                                                  float*);
+
 // ---- per chunk: the dynamic features and their statistics (one block) ----
 // dyn: x1_j = ln(1 + |r_j| / rms(r)) and x3_j = ln(1 + age_j), age_j = k0 - last_j,
 // in FP32 (2 m floats); stats: 1 / rms(r), mean and 1 / (std + 1e-6) of x1 and x3
@@ -316,13 +402,17 @@ cudaError_t launch_lp_plans(cudaStream_t st, const Ctrl* ctrl, int force, int ns
                             uint64_t seed, const uint16_t* w, float eps, const float* zstat,
                             float* dyn, double* stats, const double* r, int32_t* last, int64_t m,
                             int64_t tau, float* score, int32_t* perm, int64_t perm_stride,
-                            int32_t* boff, int64_t boff_stride, bool update_age) {
+                            int32_t* boff, int64_t boff_stride, bool update_age,
+                            bool fixed_score) {
   int64_t npow2 = 1;
   while (npow2 < m) npow2 <<= 1;
   const size_t smem = (size_t)npow2 * 8;
   if (smem > 200 * 1024 || tau > m) return cudaErrorInvalidValue;
-  k_lp_stats<<<1, 1024, 0, st>>>(ctrl, k0_arg, r, m, last, dyn, stats);
-  k_lp_score<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(w, zstat, stats, dyn, m, score, nullptr);
+  if (!fixed_score) {  // the network's scores of this chunk's features
+    k_lp_stats<<<1, 1024, 0, st>>>(ctrl, k0_arg, r, m, last, dyn, stats);
+    k_lp_score<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(w, zstat, stats, dyn, m, score,
+                                                            nullptr);
+  }
   cudaError_t e = cudaFuncSetAttribute(k_lp_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

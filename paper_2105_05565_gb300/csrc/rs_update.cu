@@ -139,6 +139,17 @@ cudaError_t launch_init_state(cudaStream_t st, int64_t m, const double* b, doubl
   return cudaGetLastError();
 }
 
+// out = s * in (the mean of the iterates from their running sum)
+__global__ void k_scale(const double* __restrict__ in, double s, int64_t m, double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) out[i] = s * in[i];
+}
+
+cudaError_t launch_scale(cudaStream_t st, const double* in, double s, int64_t m, double* out) {
+  k_scale<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(in, s, m, out);
+  return cudaGetLastError();
+}
+
 __global__ void k_chunk_begin(Ctrl* ctrl) { ctrl->k0 = ctrl->k; }
 
 cudaError_t launch_chunk_begin(cudaStream_t st, Ctrl* ctrl) {

@@ -1,16 +1,15 @@
 """Training the learned sketch proposal (offline, on solver trajectories).
 
-``collect`` walks a solver (subsample sketch, no momentum, a proposal set with
-``Solver.set_proposal``) one iteration at a time and records, for every drawn
-row, its standardised features and the target
+``collect`` runs a solver (subsample sketch, no momentum, a proposal set with
+``Solver.set_proposal``) through the library's rs_collect, which records on the
+device, for every drawn row, its standardised features and the target
 
     y_p = (1/2) ln(m max(a_p, 0) / ||e_k||_A^2 + 1e-3),   a_p = (r_C)_p delta_p,
 
 where r_C . delta is the exact decrease of ||w - w*||_A^2 of the step (the
 projection identity of Section 3) and ||e_k||_A^2 = (w_k - w*) . r_k. ``train``
-fits the network to those pairs with the library's Adam kernels. The product
-path (the proposal inside the solver) runs in the CUDA library; this module only
-drives it.
+fits the network to those pairs with the library's Adam kernels. The arithmetic
+of both runs in the CUDA library; this module only drives it.
 """
 from __future__ import annotations
 
@@ -32,31 +31,9 @@ def init_params(seed: int) -> np.ndarray:
 def collect(solver, w_star, n_iters: int, tol: float = 1e-10):
     """(features (n, 4) float32, targets (n,) float32) of the rows drawn along
     n_iters iterations of ``solver`` from its current state (stops early once the
-    relative residual is below tol)."""
-    w_star = np.asarray(w_star, dtype=np.float64)
-    m, tau = solver.m, solver.tau
-    feats, targets = [], []
-    w, _, r, _, k = solver.get_state()
-    r0 = None
-    for _ in range(int(n_iters)):
-        e2 = float((w - w_star) @ r)
-        nr = float(np.linalg.norm(r))
-        r0 = nr if r0 is None else r0
-        if e2 <= 0.0 or nr <= tol * r0:
-            break
-        Z = solver.proposal_features()
-        idx, _, _ = solver.dump_sketch(k)
-        C = idx[:tau].astype(np.int64)
-        _, rS, delta = solver.probe_step()
-        a = rS * delta
-        feats.append(Z[C])
-        targets.append(0.5 * np.log(m * np.maximum(a, 0.0) / e2 + 1e-3))
-        solver.step(1)
-        w, _, r, _, k = solver.get_state()
-    if not feats:
-        return np.zeros((0, 4), np.float32), np.zeros(0, np.float32)
-    return (np.concatenate(feats).astype(np.float32),
-            np.concatenate(targets).astype(np.float32))
+    relative residual is below tol); the library forms both on the device
+    (rs_collect)."""
+    return solver.collect(w_star, n_iters, tol)
 
 
 def train(Z, y, steps: int = 2000, batch: int = 512, lr: float = 3e-3, seed: int = 0,

@@ -166,3 +166,38 @@ def test_uneven_batch_mixed_sampled_pairs(rs):
     for p, r in [(0, 0), (7, 3), (13, 1), (23, 2)]:
         t = oracle.true_residual(Xs[p].astype(np.float64), Ys[p][r], float(lam[p]), W[p][r])
         assert t <= 1e-6 * (1 + 1e-9) and abs(t - resid[p, r]) <= 1e-12
+
+
+def test_tune_cache_keeps_the_autotuners_choice(rs, tmp_path):
+    """rs_opts.tune_cache: the first batch tunes and writes its choice under a key of
+    its shape; a second batch of the same shape takes the choice from the file. The
+    file is then edited to another valid launch shape, which a third batch must use
+    (so the file is really read), with the same iterates."""
+    dims, nrhs = [64, 100, 37], 2
+    lams, taus = [0.1, 0.5, 1e-3], [8, 12, 4]
+    Xs, Ys = make_batch(dims, nrhs, 90)
+    path = tmp_path / "tune.txt"
+
+    def run():
+        with rs.Batch(Xs, Ys, lams, sketch="count", taus=taus, momentum="heuristic", seed=2,
+                      tune_cache=str(path)) as b:
+            W, iters, resid, conv = b.solve(tol=0.0, max_iters=30)
+            return W, b.info()
+
+    W1, info1 = run()
+    lines = path.read_text().split("\n")
+    lines = [l for l in lines if l.strip()]
+    assert len(lines) == 1
+    key, t, ns = lines[0].split()
+    assert (int(t), int(ns)) == (info1["iter_threads"], info1["phase1_streams"])
+    W2, info2 = run()
+    assert (info2["iter_threads"], info2["phase1_streams"]) == (int(t), int(ns))
+    # another valid shape in the file: the next batch must take it
+    other = 256 if int(t) != 256 else 128
+    path.write_text(f"{key} {other} 1\n")
+    W3, info3 = run()
+    assert (info3["iter_threads"], info3["phase1_streams"]) == (other, 1)
+    for p in range(len(dims)):
+        for r in range(nrhs):
+            assert rel(W3[p][r], W1[p][r]) <= 1e-12
+            assert rel(W2[p][r], W1[p][r]) <= 1e-12

@@ -157,3 +157,34 @@ def test_trained_proposal_beats_uniform_on_held_out_problems(rs):
                 out.append(iters)
             assert oracle.true_residual(X, y, lam, w) <= 1.01e-6
     assert np.mean(its_l) <= 0.85 * np.mean(its_u), (its_l, its_u)
+
+
+def test_collected_training_pairs_match_oracle(rs):
+    """rs_collect (features and targets formed on the device along the trajectory)
+    against the oracle's collected pairs on the same seeded problem, network and
+    draws: features within 1e-4, targets (1/2) ln(m a / e + 1e-3) within FP32
+    rounding of the FP64 values."""
+    m, n, tau, seed, eps, K = 96, 400, 6, 3, 0.2, 25
+    X, y, A, b, lam = problem(m, n, 41)
+    theta = mlp_init(5)
+    w_star = np.linalg.solve(A, b)
+    with rs.Solver(X, y, lam, sketch="subsample", tau=tau, momentum="none", seed=seed,
+                   chunk=1) as s:
+        s.set_proposal(bf16_bits(theta), eps)
+        s.set_state(np.zeros(m), np.zeros(m), -b, -b, 0)
+        Z, t = s.collect(w_star, K, tol=1e-12)
+    ref = OL.solve_learned(A, b, OL.bf16(theta), tau, seed, tol=0.0, max_iters=K, eps=eps,
+                           chunk=1, bf16_mode=True, w_star=w_star, collect=True)
+    Zr, tr = ref["data"]
+    assert Z.shape == (K * tau, 4) and t.shape == (K * tau,)
+    assert np.abs(Z - Zr).max() <= 1e-4
+    assert np.all(np.abs(t - tr) <= 1e-5 * (1 + np.abs(tr)))
+
+
+def test_collect_needs_its_setting(rs):
+    X, y, A, b, lam = problem(64, 256, 42)
+    with rs.Solver(X, y, lam, sketch="subsample", tau=4, momentum="heuristic", chunk=1) as s:
+        s.set_proposal(None, 0.1)
+        with pytest.raises(rs.RSError) as e:
+            s.collect(np.zeros(64), 10)
+        assert e.value.status == rs.RS_EINVAL

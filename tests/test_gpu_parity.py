@@ -337,6 +337,19 @@ def test_cholesky_fp32_factor(rs, tau):
     assert rel(delta, ref) <= 1e-4
 
 
+@pytest.mark.parametrize("tau", [7, 64, 256])
+def test_cholesky_fp64_factor_mixed(rs, tau):
+    """Mixed path with the FP64 factorisation of S^T A S (the default): delta solves
+    the sketched system of the FP32 A to FP64 accuracy."""
+    m = 700
+    X, y, _ = gaussian_problem(900, m, 73)
+    with rs.Solver(X.astype(np.float32), y, 0.5, sketch="subsample", tau=tau, seed=3,
+                   precision="mixed") as s:
+        M, rS, delta = s.probe_step()
+    ref = np.linalg.solve(M, rS)
+    assert rel(delta, ref) <= 1e-10
+
+
 def test_mixed_fp32_factor_reaches_tolerance(rs):
     from synth import geometric_sigma, spectrum_problem
 
@@ -348,15 +361,15 @@ def test_mixed_fp32_factor_reaches_tolerance(rs):
     assert conv and oracle.true_residual(X.astype(np.float64), y, lam, w) <= 1e-6
 
 
-@pytest.mark.parametrize("kind", ["count", "subsample", "gaussian"])
-def test_mixed_fp64_factor_and_kinds(rs, kind):
-    """Mixed path: FP64 factor of S^T A S (count, subsample) and the Gaussian sketch
-    with the FP32 factor, both to the FP64-checked tolerance."""
+@pytest.mark.parametrize("f64", [True, False])
+@pytest.mark.parametrize("kind", ["count", "subsample", "gaussian", "subcount"])
+def test_mixed_fp64_factor_and_kinds(rs, kind, f64):
+    """Mixed path with the FP64 factor of S^T A S (the default) and with the FP32
+    factor, every dense sketch kind, to the FP64-checked tolerance."""
     from synth import geometric_sigma, spectrum_problem
 
     X, y, _ = spectrum_problem(2000, 192, geometric_sigma(192), seed=9, noise=0.01, dtype=np.float32)
     lam = 1e-2
-    f64 = kind != "gaussian"
     with rs.Solver(X, y, lam, sketch=kind, tau=24, momentum="heuristic", seed=4,
                    precision="mixed", chol_fp64=f64) as s:
         w, hist, iters, conv = s.solve(tol=1e-6, max_iters=50000)
