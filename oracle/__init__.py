@@ -19,6 +19,8 @@ What it computes follows the paper (arXiv 2105.05565, "RidgeSketch"):
 * importance-sampled coordinates p_j = A_jj / trace(A) and coordinate descent
   with momentum (``oracle.importance``, Section 7, eqs. (mSdisccolCD), (CDmom)),
   and the averaged iterates of the theorem of Section 5.2 (``average=True``);
+* Conjugate Gradients on the same system (``oracle.cg``, the competitor of
+  Section 8.3);
 * the learned sketch proposal (``oracle.learned``): features, the scoring
   network and its gradient, the proposal, Gumbel-top-tau selection, the
   per-coordinate labels from the projection identity of Section 3, and Adam.
@@ -53,3 +55,4 @@ from .solver import (  # noqa: F401
 )
 from . import learned  # noqa: F401,E402
 from . import importance  # noqa: F401,E402
+from . import cg  # noqa: F401,E402
