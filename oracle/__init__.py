@@ -20,6 +20,7 @@ What it computes follows the paper (arXiv 2105.05565, "RidgeSketch"):
   with momentum (``oracle.importance``, Section 7, eqs. (mSdisccolCD), (CDmom)),
   and the averaged iterates of the theorem of Section 5.2 (``average=True``);
 * accelerated sketch-and-project (``oracle.accel``, Algorithm 3 of Section 9);
+* kernel ridge regression with the RBF kernel (``oracle.kernel``, Section 2.2);
 * Conjugate Gradients on the same system (``oracle.cg``, the competitor of
   Section 8.3);
 * the learned sketch proposal (``oracle.learned``): features, the scoring
@@ -58,3 +59,4 @@ from . import learned  # noqa: F401,E402
 from . import importance  # noqa: F401,E402
 from . import cg  # noqa: F401,E402
 from . import accel  # noqa: F401,E402
+from . import kernel  # noqa: F401,E402
