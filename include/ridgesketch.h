@@ -195,6 +195,40 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
 rs_status rs_solve(rs_ctx* ctx, double tol, int64_t max_iters, double* w_out,
                    int32_t w_on_device, double* hist_out, int64_t* iters_out);
 
+/*
+ * Kernel ridge regression with the Gaussian kernel (Section 2.2): the n x n kernel
+ * matrix K_ij = exp(-||p_i - p_j||^2 / (2 sigma^2)) (eq. (Gausskernel)) of the rows of
+ * P, and the system K (K + lambda I) alpha = K y (eq. (kernelridge)), A = K^T (K +
+ * lambda I), b = K^T y, solved like any other (rs_solve: w_out receives alpha, n
+ * entries; predictions are K alpha).
+ *   P       n x d points, dense row-major, RS_F64 or RS_F32 (host or device, copied)
+ *   y       n targets (FP64); sigma > 0, lambda > 0; the rest as for rs_create
+ * RS_PLAIN_FP64: K from the differences of the points in FP64, A by an FP64 product.
+ * RS_MIXED: K on the tensor cores (TF32 products of the points, FP32 accumulation in
+ * tensor memory, the exponential in the epilogue), FP32 K taken as the problem's data;
+ * A = K^T K on the tensor cores; the FP64 refresh forms K^T (K w) + lambda K w - b with
+ * FP64 sums over that K. Errors as rs_create.
+ */
+rs_status rs_create_kernel(const rs_matrix* P, const double* y, int32_t y_on_device, double lambda,
+                           double sigma, int32_t sketch, int64_t tau, const rs_mom* mom,
+                           uint64_t seed, const rs_opts* opts, rs_ctx** out);
+/* The kernel matrix of a kernel ridge context (n x n doubles, host, row-major). */
+rs_status rs_get_kernel(rs_ctx* ctx, double* K_out);
+
+/*
+ * Conjugate Gradients (Hestenes and Stiefel, 1952) on the same system A w = b: the
+ * direct competitor of the paper's Experiment 3 (Section 8.3), for time-to-tolerance
+ * comparisons on the same context. The sketch settings are not used. Dense A: the
+ * formed A (FP64; RS_MIXED: the FP32 A with float-pair products and the FP64 true
+ * residual through X every refresh_every iterations, which also decides convergence);
+ * CSR X: A p = X^T (X p) + lambda p with FP64 sums over the stored values. Starts
+ * from w = 0. Arguments, outputs and status codes as for rs_solve (hist_out: the
+ * relative residual of every iteration, FP64-checked ones at the refreshes);
+ * rs_timings reports its solve time.
+ */
+rs_status rs_solve_cg(rs_ctx* ctx, double tol, int64_t max_iters, double* w_out,
+                      int32_t w_on_device, double* hist_out, int64_t* iters_out);
+
 /* Free every resource of the context. NULL is accepted. The device memory of the
  * contexts comes from one stream-ordered pool per device that keeps freed blocks
  * for the next context (no cudaMalloc / cudaFree per context once warm). */
@@ -435,6 +469,20 @@ rs_status rs_collect(rs_ctx* ctx, const double* w_star, int64_t n_iters, double 
  */
 enum { RS_SAMPLE_UNIFORM = 0, RS_SAMPLE_DIAG = 1 };
 rs_status rs_set_sampling(rs_ctx* ctx, int32_t kind);
+
+/*
+ * Accelerated sketch-and-project (Algorithm 3, Section 9) with parameters
+ * 0 < mu <= 1 <= nu <= 1 / mu: beta = 1 - sqrt(mu / nu), gamma = sqrt(1 / (mu nu)),
+ * alpha = 1 / (1 + sqrt(nu / mu)); three iterates w, v, z = alpha v + (1 - alpha) w
+ * and the residuals r_w, r_v (r_z = alpha r_v + (1 - alpha) r_w), the sketched
+ * system solved for S^T r_z. The momentum parameters of rs_create are not used while
+ * it is on. mu = nu = 1 is Algorithm 1 (z = v = w). The stopping test is on
+ * ||r_w|| / ||r_w^0||, the residual of the returned w (the printed listing monitors
+ * r_v). mu = nu = 0 returns to Algorithm 2. Needs the persistent iteration kernel
+ * (subsample, count or subcount sketch of dense A), else RS_EUNSUPPORTED; bad
+ * parameters give RS_EINVAL. Takes effect from the next rs_solve or rs_step.
+ */
+rs_status rs_set_acceleration(rs_ctx* ctx, double mu, double nu);
 
 /*
  * Averaged iterates (the theorem of Section 5.2, eqs. (convsublinear) and

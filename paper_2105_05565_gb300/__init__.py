@@ -77,6 +77,12 @@ _SIGS = {
     "rs_iter_plan": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
     "rs_chunking": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "rs_set_sampling": (_I32, [_P, _I32]),
+    "rs_create_kernel": (_I32, [ctypes.POINTER(Matrix), _P, _I32, _D, _D, _I32, _I64,
+                                ctypes.POINTER(Mom), ctypes.c_uint64, ctypes.POINTER(Opts),
+                                ctypes.POINTER(_P)]),
+    "rs_get_kernel": (_I32, [_P, _P]),
+    "rs_set_acceleration": (_I32, [_P, _D, _D]),
+    "rs_solve_cg": (_I32, [_P, _D, _I64, _P, _I32, _P, ctypes.POINTER(_I64)]),
     "rs_collect": (_I32, [_P, _P, _I64, _D, _P, _P, ctypes.POINTER(_I64)]),
     "rs_set_averaging": (_I32, [_P, _I32]),
     "rs_get_average": (_I32, [_P, _P, _I32]),
@@ -208,7 +214,7 @@ class Solver:
                  precision="fp64", refresh_every=50, sub_s=0, chol_fp64=True, chunk=0,
                  eta=0.995, beta_switch=0.5, gamma_c=1.0, beta_c=0.5, uncapped=False,
                  device=0, stream=None, setup_tc=True, iter_ctas=0, spin_limit_ns=0,
-                 stall_ns=0):
+                 stall_ns=0, kernel_sigma=None):
         L = lib()
         self._ctx = None
         yp, ydev, self._ykeep = _buf(y, np.float64)
@@ -241,9 +247,18 @@ class Solver:
         st = stream if stream is not None else _default_stream(device)
         opts.cuda_stream = st
         ctx = _P()
-        status = L.rs_create(ctypes.byref(mat), yp, ydev, float(lam), FORMS[form], SKETCHES[sketch],
-                             int(tau), ctypes.byref(mom), ctypes.c_uint64(int(seed)),
-                             ctypes.byref(opts), ctypes.byref(ctx))
+        if kernel_sigma is not None:
+            # kernel ridge (Section 2.2): X holds the n points; the system is n x n
+            status = L.rs_create_kernel(ctypes.byref(mat), yp, ydev, float(lam),
+                                        float(kernel_sigma), SKETCHES[sketch], int(tau),
+                                        ctypes.byref(mom), ctypes.c_uint64(int(seed)),
+                                        ctypes.byref(opts), ctypes.byref(ctx))
+            d = n
+        else:
+            status = L.rs_create(ctypes.byref(mat), yp, ydev, float(lam), FORMS[form],
+                                 SKETCHES[sketch], int(tau), ctypes.byref(mom),
+                                 ctypes.c_uint64(int(seed)), ctypes.byref(opts),
+                                 ctypes.byref(ctx))
         if status != RS_OK:
             raise RSError(status, L.rs_last_error(None).decode())
         self._ctx = ctx
@@ -295,6 +310,22 @@ class Solver:
                          allow=(RS_OK, RS_ENOTCONV))
         k = iters.value
         return w_ret, hist[: k + 1].copy(), k, st == RS_OK
+
+    def solve_cg(self, tol=1e-6, max_iters=10000, w_out=None):
+        """Conjugate Gradients on the same system from w = 0 (rs_solve_cg). Returns
+        (w, hist, iters, converged) like solve."""
+        hist = np.empty(int(max_iters) + 1)
+        iters = _I64()
+        if w_out is not None:
+            wp, wdev, _keep = w_out.data_ptr(), int(w_out.is_cuda), w_out
+            w_ret = w_out
+        else:
+            w_ret = np.empty(self.d)
+            wp, wdev = w_ret.ctypes.data, 0
+        st = self._check(lib().rs_solve_cg(self._ctx, float(tol), int(max_iters), wp, wdev,
+                                           hist.ctypes.data, ctypes.byref(iters)),
+                         allow=(RS_OK, RS_ENOTCONV))
+        return w_ret, hist[: iters.value + 1], iters.value, st == RS_OK
 
     def dump_sketch(self, k):
         cap = max(self.m, self.s, self.tau, 1)
@@ -358,6 +389,17 @@ class Solver:
         return {arr[i].name.decode(): (arr[i].ms, arr[i].launches, arr[i].bytes, arr[i].flops,
                                        arr[i].iters)
                 for i in range(n.value)}
+
+    def set_acceleration(self, mu, nu):
+        """Accelerated sketch-and-project (Algorithm 3) with parameters mu, nu; (0, 0)
+        returns to the momentum form."""
+        self._check(lib().rs_set_acceleration(self._ctx, float(mu), float(nu)))
+
+    def kernel_matrix(self):
+        """The n x n kernel matrix of a kernel ridge solver (host array)."""
+        K = np.empty((self.n, self.n))
+        self._check(lib().rs_get_kernel(self._ctx, K.ctypes.data))
+        return K
 
     def set_averaging(self, on=True):
         """Keep the mean of the iterates of each solve (Section 5.2)."""

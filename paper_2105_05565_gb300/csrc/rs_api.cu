@@ -128,6 +128,14 @@ struct rs_ctx {
   int32_t* xabort = nullptr;
   uint64_t wait_ns = 2000000000ull;  // bound of the persistent kernel's waits
   int64_t stall_ns = 0;              // fault injection (tests)
+  // Conjugate Gradients on the same system (rs_solve_cg)
+  double *cg_p = nullptr, *cg_v = nullptr, *cg_part = nullptr;
+  float2* cg_p2 = nullptr;  // p as float pairs (mixed, dense A)
+  CgScal* cg_s = nullptr;
+  cudaGraphExec_t cg_graph = nullptr;
+  bool kernel = false;               // kernel ridge: X holds K, A = K^T (K + lambda I)
+  bool accel = false;                // Algorithm 3 (rs_set_acceleration)
+  double acc_a = 0.5, acc_b = 0.0, acc_g = 1.0;
   bool avg = false;                  // keep the running sum of the iterates (rs_set_averaging)
   double* wsum = nullptr;            // m: sum of w^0..w^k of the current solve
   int64_t last_iters = 0;            // iterations of the last rs_solve
@@ -172,6 +180,8 @@ struct rs_ctx {
   bool mixed() const { return precision == RS_MIXED; }
   size_t elem() const { return mixed() ? sizeof(float) : sizeof(double); }
   bool f64_factor() const { return !mixed() || chol_fp64 == 1; }
+  // CG in mixed precision with dense A: the FP32 A needs the FP64 refresh through X
+  bool cg_refresh() const { return mixed() && !sparse; }
 };
 
 #define CKC(ctx, call)                                                                      \
@@ -262,6 +272,7 @@ rs_status dalloc(rs_ctx* c, T** p, size_t n) {
 
 void free_all(rs_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->cg_graph) cudaGraphExecDestroy(c->cg_graph);
   void* ptrs[] = {c->X, c->y, c->A, c->b, c->w, c->wp, c->r, c->rp, c->u, c->SA, c->ST, c->M,
                   c->Linv, c->fws, c->pws, c->rS, c->delta, c->perm, c->boff, c->inv, c->err_flag,
                   c->ndropped,
@@ -271,7 +282,7 @@ void free_all(rs_ctx* c) {
                   c->sx_pcol, c->sx_pstart, c->sx_cpiece, c->mf_bsum, c->mf_boffs, c->mf_tot,
                   c->mf_crow, c->mf_cptr, c->mf_ebuck, c->mf_eval, c->mf_v, c->mf_pu, c->mf_pud,
                   c->mf_z, c->lp_w, c->lp_raw, c->lp_zstat, c->lp_stats, c->lp_score, c->lp_feat,
-                  c->lp_last, c->wsum};
+                  c->lp_last, c->wsum, c->cg_p, c->cg_v, c->cg_part, c->cg_s, c->cg_p2};
   for (void* p : ptrs) pfree(c, p);
   if (c->ctrl_h) {  // the stream may still read the pinned control block
     cudaStreamSynchronize(c->stream);
@@ -596,6 +607,10 @@ rs_status enqueue_wide_t(rs_ctx* c, int64_t sub_end) {
   g.wait_ns = c->wait_ns;
   g.stall_ns = c->stall_ns;
   g.wsum = c->avg ? c->wsum : nullptr;
+  g.accel = c->accel ? 1 : 0;
+  g.acc_a = c->acc_a;
+  g.acc_b = c->acc_b;
+  g.acc_g = c->acc_g;
   CKC(c, (launch_iterate_wide<T, TF>(c->stream, c->ctrl, g, c->wide.smem)));
   return RS_OK;
 }
@@ -659,6 +674,18 @@ rs_status enqueue_true_av(rs_ctx* c, const double* v, const int32_t* stop) {
       return RS_OK;
     });
   // primal: A w = X^T (X w) + lambda w; dual: A a = X (X^T a) + lambda a
+  if (c->kernel) {  // K w into vn (for the lambda K w term), K^T (K w) into vd, FP64 sums
+    if (c->xdtype == RS_F32) {
+      CKC(c, launch_x_v<float>(st, static_cast<const float*>(c->X), c->n, c->d, v, c->vn, stop));
+      CKC(c, launch_xt_v<float>(st, static_cast<const float*>(c->X), c->n, c->d, c->vn, c->vd,
+                                c->xt_part, stop));
+    } else {
+      CKC(c, launch_x_v<double>(st, static_cast<const double*>(c->X), c->n, c->d, v, c->vn, stop));
+      CKC(c, launch_xt_v<double>(st, static_cast<const double*>(c->X), c->n, c->d, c->vn, c->vd,
+                                 c->xt_part, stop));
+    }
+    return RS_OK;
+  }
   if (c->xdtype == RS_F32) {
     const float* X = static_cast<const float*>(c->X);
     if (c->form == RS_PRIMAL && c->d <= 4096 && c->xtx_df) {
@@ -692,8 +719,9 @@ const double* av_out(const rs_ctx* c) { return c->form == RS_PRIMAL ? c->vd : c-
 rs_status enqueue_refresh(rs_ctx* c) {
   rs_status s = enqueue_true_av(c, c->w, &c->ctrl->stop);
   if (s != RS_OK) return s;
-  CKC(c, launch_refresh_finish(c->stream, c->ctrl, 1, c->m, av_out(c), c->w, c->b, c->lambda, c->r,
-                               c->rp, c->partials, c->hist, nullptr));
+  // A w = K^T K w + lambda K w (kernel ridge) or X^T X w + lambda w
+  CKC(c, launch_refresh_finish(c->stream, c->ctrl, 1, c->m, av_out(c), c->kernel ? c->vn : c->w,
+                               c->b, c->lambda, c->r, c->rp, c->partials, c->hist, nullptr));
   return RS_OK;
 }
 
@@ -758,6 +786,10 @@ rs_status ensure_schedule(rs_ctx* c, int64_t K) {
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
+  }
+  if (c->cg_graph) {  // captured the history buffer too
+    cudaGraphExecDestroy(c->cg_graph);
+    c->cg_graph = nullptr;
   }
   rs_status s;
   if ((s = dalloc(c, &c->gam, L)) != RS_OK) return s;
@@ -839,8 +871,8 @@ rs_status copy_out_w(rs_ctx* c, double* w_out, int32_t on_device) {
 rs_status true_rel(rs_ctx* c, const double* v_dev, double* rel) {
   rs_status s = enqueue_true_av(c, v_dev, nullptr);
   if (s != RS_OK) return s;
-  CKC(c, launch_refresh_finish(c->stream, c->ctrl, 0, c->m, av_out(c), v_dev, c->b, c->lambda,
-                               nullptr, nullptr, c->partials, nullptr, c->rel_dev));
+  CKC(c, launch_refresh_finish(c->stream, c->ctrl, 0, c->m, av_out(c), c->kernel ? c->vn : v_dev,
+                               c->b, c->lambda, nullptr, nullptr, c->partials, nullptr, c->rel_dev));
   CKC(c, cudaMemcpyAsync(c->scal_h, c->rel_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CKC(c, cudaStreamSynchronize(c->stream));
   *rel = *c->scal_h;
@@ -1499,6 +1531,290 @@ rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int3
   CKC(c, cudaStreamSynchronize(st));
   if (iters_out) *iters_out = iters;
   return result;
+}
+
+// ---- Conjugate Gradients on the same system (the competitor of Section 8.3) ----
+namespace {
+constexpr int kCgPlainSeg = 64;  // plain: iterations per captured segment
+constexpr int kCgSegs = 4;       // segments per graph replay
+
+// one CG iteration: direction, product with p . v, update with r . r and the stop test
+rs_status enqueue_cg_iter(rs_ctx* c) {
+  cudaStream_t st = c->stream;
+  const int64_t m = c->m;
+  float2* p2 = (c->mixed() && !c->sparse) ? c->cg_p2 : nullptr;
+  CKC(c, launch_cg_dir(st, c->ctrl, c->cg_s, m, c->r, c->cg_p, p2));
+  if (c->sparse) {  // A p = X^T (X p) + lambda p through the stored entries, FP64 sums
+    rs_status s = with_vt(c, [&](auto tag) -> rs_status {
+      using VT = std::remove_pointer_t<decltype(tag)>;
+      const SparseX<VT> X = sparse_view<VT>(c);
+      CKC(c, sparse_xv_d<VT>(st, X, c->cg_p, c->mf_z, &c->ctrl->stop));
+      CKC(c, sparse_xtv_d<VT>(st, X, c->mf_z, c->cg_v, c->mf_pud, &c->ctrl->stop));
+      return RS_OK;
+    });
+    if (s != RS_OK) return s;
+    CKC(c, launch_cg_lam_dot(st, c->ctrl, m, c->lambda, c->cg_p, c->cg_v, c->cg_s, c->cg_part));
+  } else if (c->mixed()) {
+    CKC(c, launch_cg_matvec<float>(st, c->ctrl, static_cast<const float*>(c->A), c->ld, m, c->cg_p,
+                                   p2, c->cg_v, c->cg_s, c->cg_part));
+  } else {
+    CKC(c, launch_cg_matvec<double>(st, c->ctrl, static_cast<const double*>(c->A), c->ld, m,
+                                    c->cg_p, nullptr, c->cg_v, c->cg_s, c->cg_part));
+  }
+  CKC(c, launch_cg_update(st, c->ctrl, c->cg_s, m, c->cg_p, c->cg_v, c->w, c->r, c->cg_part,
+                          c->hist, c->cg_refresh() ? 1 : 0));
+  return RS_OK;
+}
+
+// a graph of kCgSegs segments; a segment is one refresh period followed by the FP64
+// refresh (dense mixed) or kCgPlainSeg iterations (FP64 products)
+rs_status build_cg_graph(rs_ctx* c) {
+  if (c->cg_graph) return RS_OK;
+  const int per = c->cg_refresh() ? c->refresh_every : kCgPlainSeg;
+  CKC(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+  rs_status s = RS_OK;
+  for (int q = 0; q < kCgSegs && s == RS_OK; ++q) {
+    for (int i = 0; i < per && s == RS_OK; ++i) s = enqueue_cg_iter(c);
+    if (s == RS_OK && c->cg_refresh()) {
+      s = enqueue_refresh(c);  // r = A w - b through X in FP64; decides convergence
+      if (s == RS_OK) {
+        const cudaError_t e = launch_cg_rr(c->stream, c->ctrl, c->cg_s, c->m, c->r, 0);
+        if (e != cudaSuccess) s = (c->err = std::string("cg: ") + cudaGetErrorString(e), RS_ECUDA);
+      }
+    }
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (s != RS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) FAILC(c, RS_ECUDA, std::string("cg graph capture: ") + cudaGetErrorString(e));
+  const cudaError_t e2 = cudaGraphInstantiate(&c->cg_graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) FAILC(c, RS_ECUDA, std::string("cg graph: ") + cudaGetErrorString(e2));
+  return RS_OK;
+}
+}  // namespace
+
+rs_status rs_create_kernel(const rs_matrix* P, const double* y, int32_t y_on_device, double lambda,
+                           double sigma, int32_t sketch, int64_t tau, const rs_mom* mom,
+                           uint64_t seed, const rs_opts* opts, rs_ctx** out) {
+  if (out) *out = nullptr;
+  if (!P || !y || !out || P->is_csr || !P->val) {
+    set_global_error("rs_create_kernel: need dense points, y and out");
+    return RS_EINVAL;
+  }
+  if (!(sigma > 0.0) || !(lambda > 0.0) || P->n < 1 || P->d < 1) {
+    set_global_error("rs_create_kernel: need sigma > 0, lambda > 0, n, d >= 1");
+    return RS_EINVAL;
+  }
+  if (P->dtype != RS_F64 && P->dtype != RS_F32) {
+    set_global_error("rs_create_kernel: points must be FP64 or FP32");
+    return RS_EINVAL;
+  }
+  rs_opts o;
+  rs_default_opts(&o);
+  if (opts) o = *opts;
+  const bool mixed = o.precision == RS_MIXED;
+  const int64_t n = P->n, d = P->d;
+  DeviceGuard dg(o.device);
+  cudaStream_t st = static_cast<cudaStream_t>(o.cuda_stream);
+  // temporary buffers of the set-up (the context copies K)
+  const size_t pel = P->dtype == RS_F32 ? 4 : 8;
+  const size_t kel = mixed ? 4 : 8;
+  void *Pd = nullptr, *K = nullptr, *ws = nullptr;
+  int32_t* err = nullptr;
+  auto release = [&]() {
+    if (Pd && !P->on_device) cudaFree(Pd);
+    if (K) cudaFree(K);
+    if (ws) cudaFree(ws);
+    if (err) cudaFree(err);
+  };
+  cudaError_t e = cudaSuccess;
+  const void* Pv = P->val;
+  if (!P->on_device) {
+    e = cudaMalloc(&Pd, (size_t)n * d * pel);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Pd, P->val, (size_t)n * d * pel, cudaMemcpyHostToDevice, st);
+    Pv = Pd;
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&K, (size_t)n * n * kel);
+  if (e == cudaSuccess && mixed) {
+    // FP32 points (a converted copy when given FP64), the tensor-core kernel matrix
+    const float* Pf = static_cast<const float*>(Pv);
+    float* conv = nullptr;
+    if (P->dtype == RS_F64) {
+      e = cudaMalloc((void**)&conv, (size_t)n * d * 4);
+      if (e == cudaSuccess) e = launch_cast_f64_f32(st, static_cast<const double*>(Pv), (int64_t)n * d, conv);
+      Pf = conv;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&ws, rbf_tc_ws_floats(n, d) * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&err, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess)
+      e = launch_rbf_tc(st, Pf, n, d, sigma, static_cast<float*>(K), n, static_cast<float*>(ws), err);
+    if (e == cudaSuccess) e = launch_mirror_lower<float>(st, static_cast<float*>(K), n, n);
+    int32_t bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (conv) cudaFree(conv);
+    if (e == cudaSuccess && bad) e = cudaErrorLaunchTimeout;
+  } else if (e == cudaSuccess) {
+    e = P->dtype == RS_F64
+            ? launch_rbf_f64<double>(st, static_cast<const double*>(Pv), n, d, sigma,
+                                     static_cast<double*>(K), n)
+            : launch_rbf_f64<float>(st, static_cast<const float*>(Pv), n, d, sigma,
+                                    static_cast<double*>(K), n);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) {
+    release();
+    set_global_error(std::string("rs_create_kernel: kernel matrix: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? RS_ENOMEM : RS_ECUDA;
+  }
+  // the ridge system with X = K (primal): A = K^T K + lambda I, b = K^T y; then
+  // A += lambda (K - I) for A = K^T (K + lambda I) (eq. (kernelridge))
+  rs_matrix Km{};
+  Km.is_csr = 0;
+  Km.dtype = mixed ? RS_F32 : RS_F64;
+  Km.n = n;
+  Km.d = n;
+  Km.val = K;
+  Km.on_device = 1;
+  rs_ctx* c = nullptr;
+  rs_status s = rs_create(&Km, y, y_on_device, lambda, RS_PRIMAL, sketch, tau, mom, seed, &o, &c);
+  release();
+  if (s != RS_OK) return s;
+  c->kernel = true;
+  cudaError_t e2 = mixed ? launch_add_offdiag<float>(c->stream, static_cast<float*>(c->A), c->ld,
+                                                     static_cast<const float*>(c->X), n, n, lambda)
+                         : launch_add_offdiag<double>(c->stream, static_cast<double*>(c->A), c->ld,
+                                                      static_cast<const double*>(c->X), n, n, lambda);
+  if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(c->stream);
+  if (e2 != cudaSuccess) {
+    set_global_error(std::string("rs_create_kernel: ") + cudaGetErrorString(e2));
+    rs_destroy(c);
+    return RS_ECUDA;
+  }
+  *out = c;
+  return RS_OK;
+}
+
+rs_status rs_get_kernel(rs_ctx* c, double* K_out) {
+  if (!c || !K_out) { set_global_error("rs_get_kernel: null argument"); return RS_EINVAL; }
+  if (!c->kernel) FAILC(c, RS_EINVAL, "rs_get_kernel: not a kernel ridge context");
+  DeviceGuard dg(c->device);
+  const size_t nn = (size_t)c->n * c->n;
+  if (c->xdtype == RS_F64) {
+    CKC(c, copy_sync(c, K_out, c->X, nn * 8, cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float> tmp(nn);
+    CKC(c, copy_sync(c, tmp.data(), c->X, nn * 4, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < nn; ++i) K_out[i] = (double)tmp[i];
+  }
+  return RS_OK;
+}
+
+rs_status rs_solve_cg(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int32_t w_on_device,
+                      double* hist_out, int64_t* iters_out) {
+  if (!c) { set_global_error("rs_solve_cg: null context"); return RS_EINVAL; }
+  if (max_iters < 0 || !(tol >= 0.0)) FAILC(c, RS_EINVAL, "rs_solve_cg: bad tol or max_iters");
+  if (!c->sparse && c->A == nullptr) FAILC(c, RS_EUNSUPPORTED, "rs_solve_cg: no formed A");
+  DeviceGuard dg(c->device);
+  cudaStream_t st = c->stream;
+  const int64_t m = c->m;
+  rs_status s;
+  if (!c->cg_p) {
+    const int64_t np = std::max<int64_t>(cg_matvec_blocks(m), cg_blocks(m));
+    if ((s = dalloc(c, &c->cg_p, m)) != RS_OK) return s;
+    if ((s = dalloc(c, &c->cg_v, m)) != RS_OK) return s;
+    if ((s = dalloc(c, &c->cg_part, np)) != RS_OK) return s;
+    CKC(c, pmalloc(c, (void**)&c->cg_s, sizeof(CgScal)));
+    CKC(c, pmalloc(c, (void**)&c->cg_p2, m * sizeof(float2)));
+  }
+  if ((s = ensure_schedule(c, std::max<int64_t>(max_iters, 1))) != RS_OK) return s;
+  if (c->xabort) CKC(c, cudaMemsetAsync(c->xabort, 0, sizeof(int32_t), st));
+  CKC(c, launch_init_state(st, m, c->b, c->w, c->wp, c->r, c->rp, c->u));  // w = 0, r = -b
+  CKC(c, cudaMemsetAsync(c->cg_p, 0, m * sizeof(double), st));
+  const double h0 = c->r0 > 0.0 ? 1.0 : 0.0;
+  CKC(c, cudaMemcpyAsync(c->hist, &h0, sizeof(double), cudaMemcpyHostToDevice, st));
+  Ctrl* h = c->ctrl_h;
+  std::memset(h, 0, sizeof(Ctrl));
+  h->max_iters = max_iters;
+  h->r0 = c->r0 > 0.0 ? c->r0 : 1.0;
+  h->tol = tol;
+  h->checked_k = -1;
+  h->pk = -1;
+  if ((s = write_ctrl(c)) != RS_OK) return s;
+  CKC(c, launch_cg_rr(st, c->ctrl, c->cg_s, m, c->r, 1));
+  CKC(c, cudaStreamSynchronize(st));
+  if (!std::isfinite(c->r0)) {
+    c->err = "rs_solve_cg: NaN or Inf in b (||b|| is not finite)";
+    return RS_ENUMERIC;
+  }
+  int64_t iters = 0;
+  rs_status result = RS_OK;
+  float ms = 0.f;
+  if (c->r0 == 0.0 || max_iters == 0) {
+    if (c->r0 != 0.0 && tol < 1.0) result = RS_ENOTCONV;
+  } else {
+    if ((s = build_cg_graph(c)) != RS_OK) return s;
+    const int per = c->cg_refresh() ? c->refresh_every : kCgPlainSeg;
+    const int64_t per_graph = (int64_t)per * kCgSegs;
+    CKC(c, cudaEventRecord(c->ev0, st));
+    for (int64_t q = 0; q < max_iters / per_graph + 2; ++q) {
+      CKC(c, cudaGraphLaunch(c->cg_graph, st));
+      if ((s = read_ctrl(c)) != RS_OK) return s;
+      if (h->stop) break;
+    }
+    CKC(c, cudaEventRecord(c->ev1, st));
+    CKC(c, cudaEventSynchronize(c->ev1));
+    CKC(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    iters = h->k;
+    if (h->status == RS_ENUMERIC) {
+      result = RS_ENUMERIC;
+      c->err = "rs_solve_cg: NaN or Inf in the residual";
+    } else {
+      double last = 0.0;
+      if (c->cg_refresh() && h->checked_k != iters) {  // final FP64 residual through X
+        if ((s = true_rel(c, c->w, &last)) != RS_OK) return s;
+        CKC(c, copy_sync(c, c->hist + iters, &last, sizeof(double), cudaMemcpyHostToDevice));
+      } else {
+        CKC(c, copy_sync(c, &last, c->hist + iters, sizeof(double), cudaMemcpyDeviceToHost));
+      }
+      if (!(last <= tol)) result = RS_ENOTCONV;
+    }
+  }
+  c->solve_ms = ms;
+  c->last_iters = iters;
+  if ((s = copy_out_w(c, w_out, w_on_device)) != RS_OK) return s;
+  if (hist_out) CKC(c, cudaMemcpyAsync(hist_out, c->hist, (iters + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CKC(c, cudaStreamSynchronize(st));
+  if (iters_out) *iters_out = iters;
+  return result;
+}
+
+rs_status rs_set_acceleration(rs_ctx* c, double mu, double nu) {
+  if (!c) { set_global_error("rs_set_acceleration: null context"); return RS_EINVAL; }
+  DeviceGuard dg(c->device);
+  if (mu == 0.0 && nu == 0.0) {  // back to Algorithm 2
+    c->accel = false;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    return RS_OK;
+  }
+  if (!(mu > 0.0 && mu <= 1.0 && nu >= 1.0 && nu * mu <= 1.0 + 1e-12))
+    FAILC(c, RS_EINVAL, "rs_set_acceleration: need 0 < mu <= 1 <= nu <= 1 / mu");
+  if (!c->use_wide)
+    FAILC(c, RS_EUNSUPPORTED, "rs_set_acceleration: needs the persistent iteration kernel "
+                              "(subsample, count or subcount sketch of dense A)");
+  // Algorithm 3: beta = 1 - sqrt(mu / nu), gamma = sqrt(1 / (mu nu)),
+  // alpha = 1 / (1 + sqrt(nu / mu))
+  c->acc_b = 1.0 - std::sqrt(mu / nu);
+  c->acc_g = std::sqrt(1.0 / (mu * nu));
+  c->acc_a = 1.0 / (1.0 + std::sqrt(nu / mu));
+  c->accel = true;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  return RS_OK;
 }
 
 rs_status rs_set_averaging(rs_ctx* c, int32_t on) {

@@ -170,8 +170,7 @@ cudaError_t launch_msys_batched(cudaStream_t st, const Ctrl* ctrl, int force, in
     if (!staged) smem = 0;
   }
   if (smem > 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_msys_batched<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_smem_max((const void*)k_msys_batched<T>, (size_t)((int)smem));
     if (e != cudaSuccess) return e;
   }
   k_msys_batched<T><<<(unsigned)(nslots * tau), 512, smem, st>>>(ctrl, force, nslots, plan, rows, m,
@@ -315,8 +314,7 @@ cudaError_t launch_sa_msys(cudaStream_t st, const Ctrl* ctrl, int force, int nsl
   const int64_t nperm = plan.perm_stride;
   const size_t smem = sa_msys_smem<T>(m, tau, nperm);
   if (smem > 200 * 1024 || bq % 4 != 0) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_sa_msys<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = set_smem_max((const void*)k_sa_msys<T>, (size_t)((int)smem));
   if (e != cudaSuccess) return e;
   const int64_t nj = (tau + kJB - 1) / kJB;
   k_sa_msys<T><<<(unsigned)(nslots * nj), 256, smem, st>>>(ctrl, force, nslots, plan, A, lda, m, tau,
@@ -414,13 +412,12 @@ cudaError_t launch_srht_system(cudaStream_t st, const Ctrl* ctrl, int force, int
                                int64_t lda, int64_t m, int64_t mp, int64_t tau, T* SA, int64_t ldsa,
                                int64_t sa_slot, double* M, int64_t m_slot) {
   size_t smem = (size_t)mp * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(k_srht_sa<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = set_smem_max((const void*)k_srht_sa<T>, (size_t)((int)smem));
   if (e != cudaSuccess) return e;
   k_srht_sa<T><<<dim3((unsigned)m, (unsigned)nslots), 1024, smem, st>>>(
       ctrl, force, nslots, k0_arg, seed, plan, A, lda, m, mp, tau, SA, ldsa, sa_slot);
   smem = (size_t)mp * sizeof(double);
-  e = cudaFuncSetAttribute(k_srht_msys<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = set_smem_max((const void*)k_srht_msys<T>, (size_t)((int)smem));
   if (e != cudaSuccess) return e;
   k_srht_msys<T><<<dim3((unsigned)tau, (unsigned)nslots), 1024, smem, st>>>(
       ctrl, force, nslots, k0_arg, seed, plan, SA, ldsa, sa_slot, m, mp, tau, M, m_slot);

@@ -569,7 +569,7 @@ cudaError_t launch_nr(cudaStream_t st, const BatchProbC<T>* probs, const int32_t
   const ClSmem L = cl_plan<T, NR>(tau_max, bq_max, perm_max, pld_max, &stage);
   if (L.total > 227u * 1024u) return cudaErrorInvalidValue;
   auto kern = k_batch_cluster<T, kMixed, NR>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  cudaError_t e = set_smem_max((const void*)kern, (size_t)((int)L.total));
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(std::max(nprob, 1) * kBatchCluster));

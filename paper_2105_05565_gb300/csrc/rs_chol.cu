@@ -275,8 +275,7 @@ cudaError_t launch_factor_inv(cudaStream_t st, const Ctrl* ctrl, int force, int 
   const int use_smem = need <= 220 * 1024 && tau <= 4096;
   const size_t smem = use_smem ? need : 4096;
   if (!use_smem && ws == nullptr) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_factor_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = set_smem_max((const void*)k_factor_blk<T>, (size_t)((int)smem));
   if (e != cudaSuccess) return e;
   k_factor_blk<T><<<nslots, 512, smem, st>>>(ctrl, force, nslots, M, m_slot, tau, Linv, l_slot, ws,
                                               use_smem, ndropped);
@@ -730,7 +729,7 @@ cudaError_t launch_delta(cudaStream_t st, const Ctrl* ctrl, int force, int64_t k
     last_tau = g.tau;
     last_mp = g.mp;
     cs = delta_cluster_size<T>(g.tau);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_smem_max((const void*)kern, (size_t)((int)smem));
     if (e != cudaSuccess) return e;
     if (cs > 8) {
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

@@ -371,7 +371,7 @@ cudaError_t launch_xtx_multi_df(cudaStream_t st, const float* X, int64_t n, int6
   const size_t smem = (size_t)nv * d * sizeof(float2);
   cudaError_t e = cudaSuccess;
   auto go = [&](auto kern) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = set_smem_max((const void*)kern, (size_t)((int)smem));
     if (e == cudaSuccess) kern<<<G, 512, smem, st>>>(X, n, d, nv, V, part, skip);
   };
   if (d <= 1024) go(k_xtx_multi_df<2, 2>);
@@ -563,7 +563,7 @@ cudaError_t launch_xtx_two_pass(cudaStream_t st, const float* X, int64_t n, int6
   const dim3 g2((unsigned)((d + kXtuCols - 1) / kXtuCols), (unsigned)((n + kXtuRows - 1) / kXtuRows));
   cudaError_t e = cudaSuccess;
   auto go = [&](auto k1, auto k2) {
-    e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = set_smem_max((const void*)k1, (size_t)((int)smem));
     if (e != cudaSuccess) return;
     k1<<<g1, 1024, smem, st>>>(X, n, d, nv, W, U, skip);
     k2<<<g2, kXtuCols, 0, st>>>(X, n, d, nv, U, part, skip, (int64_t)0);
@@ -576,6 +576,76 @@ cudaError_t launch_xtx_two_pass(cudaStream_t st, const float* X, int64_t n, int6
       part, (int)g2.y, nv, d, out, skip);
   return cudaGetLastError();
 }
+
+// ---- kernel ridge (Section 2.2) ----
+// K_ij = exp(-||p_i - p_j||^2 / (2 sigma^2)) (eq. (Gausskernel)) in FP64 from the
+// differences of the points (no norm expansion): 32 x 32 output tiles, the two row
+// blocks of points staged in shared memory in chunks of 32 features
+template <typename TP>
+__global__ void __launch_bounds__(256) k_rbf_f64(const TP* __restrict__ P, int64_t n, int64_t d,
+                                                 double inv2s2, double* __restrict__ K,
+                                                 int64_t ldK) {
+  __shared__ double si[32][33], sj[32][33];
+  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows of 32
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t k0 = 0; k0 < d; k0 += 32) {
+    for (int r = ty; r < 32; r += 8) {
+      const int64_t k = k0 + tx;
+      si[r][tx] = (i0 + r < n && k < d) ? (double)P[(i0 + r) * d + k] : 0.0;
+      sj[r][tx] = (j0 + r < n && k < d) ? (double)P[(j0 + r) * d + k] : 0.0;
+    }
+    __syncthreads();
+    const int kn = (int)((d - k0) < 32 ? (d - k0) : 32);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = ty + 8 * q;
+      for (int k = 0; k < kn; ++k) {
+        const double df = si[r][k] - sj[tx][k];
+        acc[q] = fma(df, df, acc[q]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t i = i0 + ty + 8 * q, j = j0 + tx;
+    if (i < n && j < n) K[i * ldK + j] = (i == j) ? 1.0 : exp(-acc[q] * inv2s2);
+  }
+}
+
+template <typename TP>
+cudaError_t launch_rbf_f64(cudaStream_t st, const TP* P, int64_t n, int64_t d, double sigma,
+                           double* K, int64_t ldK) {
+  const dim3 g((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
+  k_rbf_f64<TP><<<g, 256, 0, st>>>(P, n, d, 1.0 / (2.0 * sigma * sigma), K, ldK);
+  return cudaGetLastError();
+}
+template cudaError_t launch_rbf_f64<double>(cudaStream_t, const double*, int64_t, int64_t, double,
+                                            double*, int64_t);
+template cudaError_t launch_rbf_f64<float>(cudaStream_t, const float*, int64_t, int64_t, double,
+                                           double*, int64_t);
+
+// A += lambda (K - I): from K^T K + lambda I to K^T (K + lambda I) (eq. (kernelridge));
+// the diagonal of the Gaussian kernel is 1, so only the off-diagonal entries change
+template <typename T>
+__global__ void k_add_offdiag(T* __restrict__ A, int64_t lda, const T* __restrict__ K, int64_t ldK,
+                              int64_t n, double lambda) {
+  const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && j < n && i != j) A[i * lda + j] = (T)((double)A[i * lda + j] + lambda * (double)K[i * ldK + j]);
+}
+
+template <typename T>
+cudaError_t launch_add_offdiag(cudaStream_t st, T* A, int64_t lda, const T* K, int64_t ldK,
+                               int64_t n, double lambda) {
+  k_add_offdiag<T><<<dim3((unsigned)((n + 255) / 256), (unsigned)n), 256, 0, st>>>(A, lda, K, ldK,
+                                                                                    n, lambda);
+  return cudaGetLastError();
+}
+template cudaError_t launch_add_offdiag<float>(cudaStream_t, float*, int64_t, const float*, int64_t,
+                                               int64_t, double);
+template cudaError_t launch_add_offdiag<double>(cudaStream_t, double*, int64_t, const double*,
+                                                int64_t, int64_t, double);
 
 // ---- variant of the one-pass X^T X v that allocates nothing (rs_gram_apply_noalloc) ----
 // The per-block column sums live in a fixed device array of this file instead of a

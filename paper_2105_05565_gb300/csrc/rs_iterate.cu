@@ -342,7 +342,7 @@ cudaError_t launch_iterate(cudaStream_t st, Ctrl* ctrl, IterArgs<T, TF> g) {
     cs = 16;
     for (;;) {
       const size_t smem = iterate_smem<T, TF>(g.tau, cs, sb);
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      set_smem_max((const void*)kern, (size_t)((int)smem));
       if (cs > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3((unsigned)cs);

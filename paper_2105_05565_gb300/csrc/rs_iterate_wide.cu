@@ -330,6 +330,9 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   const float thr2f = (float)(tol * tol);
   const int no_stop = ctrl->no_stop;
   const uint64_t tag0 = (*g.epoch) << 24;
+  // Algorithm 3 coefficients in FP32 (mixed form): alpha, (1 - beta)(1 - alpha), gamma
+  const float aaf = (float)g.acc_a, cvf = (float)((1.0 - g.acc_b) * (1.0 - g.acc_a)),
+              agf = (float)g.acc_g;
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int cta = blockIdx.x;
@@ -524,11 +527,14 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
     if (fresh) {  // else the row update has written them
       for (int t = tid; t < nrows; t += kWThreads) {
         const int32_t pr = prow[t];
+        // r_S of r (Algorithm 2) or of r_z = r_w - alpha (r_w - r_v) (Algorithm 3)
         if constexpr (kFP) {
-          const float v = fr[pr & 0x7FFFFFFF].x;
+          float v = fr[pr & 0x7FFFFFFF].x;
+          if (g.accel) v -= aaf * (v - frp[pr & 0x7FFFFFFF].x);
           coef[t] = pr < 0 ? -v : v;
         } else {
-          const double v = sr[pr & 0x7FFFFFFF];
+          double v = sr[pr & 0x7FFFFFFF];
+          if (g.accel) v = g.acc_a * srp[pr & 0x7FFFFFFF] + (1.0 - g.acc_a) * v;
           coef[t] = (TF)(pr < 0 ? -v : v);
         }
       }
@@ -704,15 +710,30 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
           const float2 ri = fr[i], rpi = frp[i], wi = fw[i], wpi = fwp[i];
           const float dr = (ri.x - rpi.x) + (ri.y - rpi.y);
           const float dw = (wi.x - wpi.x) + (wi.y - wpi.y);
-          const float2 rn = add_pf(ri, fmaf(bk, dr, -gk * (float)asum));
+          float2 rn, wn;
+          float cz;  // r_S coefficient of the next iteration (hi part)
+          if (g.accel) {
+            // Algorithm 3 as increments: with z = w - alpha (w - v),
+            // w+ = z - S delta, v+ = v + (1 - beta)(1 - alpha)(w - v) - gamma S delta,
+            // and the same for r_w, r_v with A S delta
+            const float2 rvn = add_pf(rpi, fmaf(cvf, dr, -agf * (float)asum));
+            rn = add_pf(ri, fmaf(-aaf, dr, -(float)asum));
+            wn = add_pf(wi, fmaf(-aaf, dw, -ui));
+            fwp[i] = add_pf(wpi, fmaf(cvf, dw, -agf * ui));
+            frp[i] = rvn;
+            cz = rn.x - aaf * (rn.x - rvn.x);
+          } else {
+            rn = add_pf(ri, fmaf(bk, dr, -gk * (float)asum));
+            wn = add_pf(wi, fmaf(bk, dw, -gk * ui));
+            frp[i] = ri;
+            fwp[i] = wi;
+            cz = rn.x;
+          }
           fr[i] = rn;
-          frp[i] = ri;
-          const float2 wn = add_pf(wi, fmaf(bk, dw, -gk * ui));
           fw[i] = wn;
-          fwp[i] = wi;
           if (g.wsum != nullptr) ssum[i] += (double)wn.x + (double)wn.y;
           const int32_t t = pinv[i];  // staged row of slot k + 1
-          if (t >= 0) coef[t] = prow[t] < 0 ? -rn.x : rn.x;
+          if (t >= 0) coef[t] = prow[t] < 0 ? -cz : cz;
           const float v = rn.x * inv_r0f;
           sq = fmaf(v, v, sq);
         }
@@ -730,14 +751,27 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
           const double ui = (e == kNotSketched) ? 0.0
                             : (entry_neg(e) ? -tot[e & 0x7FFFFFFF] : tot[e & 0x7FFFFFFF]);
           const double ri = sr[i], rpi = srp[i], wi = sw[i], wpi = swp[i];
-          const double rn = (1.0 + bk) * ri - bk * rpi - gk * asd;
+          double rn, wn, cz;
+          if (g.accel) {  // Algorithm 3: (w, v, r_w, r_v) in (w, w_prev, r, r_prev)
+            const double z = g.acc_a * wpi + (1.0 - g.acc_a) * wi;
+            const double rz = g.acc_a * rpi + (1.0 - g.acc_a) * ri;
+            rn = rz - asd;
+            wn = z - ui;
+            const double rvn = g.acc_b * rpi + (1.0 - g.acc_b) * rz - g.acc_g * asd;
+            srp[i] = rvn;
+            swp[i] = g.acc_b * wpi + (1.0 - g.acc_b) * z - g.acc_g * ui;
+            cz = g.acc_a * rvn + (1.0 - g.acc_a) * rn;
+          } else {
+            rn = (1.0 + bk) * ri - bk * rpi - gk * asd;
+            wn = (1.0 + bk) * wi - bk * wpi - gk * ui;
+            srp[i] = ri;
+            swp[i] = wi;
+            cz = rn;
+          }
           sr[i] = rn;
           const int32_t t = pinv[i];  // staged row of slot k + 1
-          if (t >= 0) coef[t] = (TF)(prow[t] < 0 ? -rn : rn);
-          srp[i] = ri;
-          const double wn = (1.0 + bk) * wi - bk * wpi - gk * ui;
+          if (t >= 0) coef[t] = (TF)(prow[t] < 0 ? -cz : cz);
           sw[i] = wn;
-          swp[i] = wi;
           if (g.wsum != nullptr) ssum[i] += wn;
           sq += rn * rn;
         }
@@ -831,7 +865,7 @@ bool wide_plan(int64_t m, int64_t tau, int max_ctas, int64_t chunk, WidePlan* ou
       cudaGetLastError();
       return false;
     }
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (set_smem_max((const void*)kern, (size_t)((int)smem)) !=
         cudaSuccess) {
       cudaGetLastError();
       return false;
@@ -870,7 +904,7 @@ bool wide_plan(int64_t m, int64_t tau, int max_ctas, int64_t chunk, WidePlan* ou
 template <typename T, typename TF>
 cudaError_t launch_iterate_wide(cudaStream_t st, Ctrl* ctrl, const WideArgs<T, TF>& g, size_t smem) {
   auto kern = k_iterate_wide<T, TF>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem_max((const void*)kern, (size_t)((int)smem));
   if (e != cudaSuccess) return e;
   if (kWideCluster > 8) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

@@ -154,6 +154,8 @@ struct WideArgs {
   uint64_t wait_ns;  // bound of every device-side wait (global timer)
   int64_t stall_ns;  // fault injection: CTA 0 publishes its first partials this late
   double* wsum;      // nullptr, or the running sum of the iterates w^0..w^k (m)
+  int accel;         // 1: Algorithm 3 with (w, v, r_w, r_v) in (w, w_prev, r, r_prev)
+  double acc_a, acc_b, acc_g;  // its alpha, beta, gamma
   int nblk;
   int nsab;                        // buffers of the staged S^T A block (2, or 1 when tight)
 };
@@ -337,6 +339,33 @@ cudaError_t launch_init_state(cudaStream_t st, int64_t m, const double* b, doubl
 // ctrl->k0 = ctrl->k (first iteration of a chunk)
 cudaError_t launch_chunk_begin(cudaStream_t st, Ctrl* ctrl);
 cudaError_t launch_scale(cudaStream_t st, const double* in, double s, int64_t m, double* out);
+cudaError_t launch_cast_f64_f32(cudaStream_t st, const double* in, int64_t n, float* out);
+// raise (never lower) a kernel's maximum dynamic shared memory on the current device
+cudaError_t set_smem_max(const void* func, size_t bytes);
+
+// ---- Conjugate Gradients (rs_cg.cu) ----
+struct CgScal {
+  double rr;        // r . r of the current residual
+  double pv;        // p . A p of the current direction
+  double beta;      // coefficient of the next direction update
+  uint32_t ticket;  // last-block counter of the grid reductions
+  int32_t pad;
+};
+int cg_blocks(int64_t m);
+int cg_matvec_blocks(int64_t m);
+cudaError_t launch_cg_dir(cudaStream_t st, const Ctrl* ctrl, const CgScal* cs, int64_t m,
+                          const double* r, double* p, float2* p2);
+template <typename TA>
+cudaError_t launch_cg_matvec(cudaStream_t st, const Ctrl* ctrl, const TA* A, int64_t lda, int64_t m,
+                             const double* p, const float2* p2, double* v, CgScal* cs,
+                             double* part);
+cudaError_t launch_cg_lam_dot(cudaStream_t st, const Ctrl* ctrl, int64_t m, double lambda,
+                              const double* p, double* v, CgScal* cs, double* part);
+cudaError_t launch_cg_update(cudaStream_t st, Ctrl* ctrl, CgScal* cs, int64_t m, const double* p,
+                             const double* v, double* w, double* r, double* part, double* hist,
+                             int mixed);
+cudaError_t launch_cg_rr(cudaStream_t st, const Ctrl* ctrl, CgScal* cs, int64_t m, const double* r,
+                         int init);
 
 // ---- X^T X on the tensor cores (rs_tc_gemm.cu) ----
 // A (lower triangle and diagonal, d x lda FP32) = X^T X + lambda I, TF32 inputs, FP32
@@ -348,6 +377,17 @@ cudaError_t launch_gram_tc_rows(cudaStream_t st, const float* X, int64_t n, int6
                                 double lambda, float* A, int64_t lda, float* Xt_ws, int32_t* err,
                                 int64_t r0, int64_t r1, float* Xcopy = nullptr);
 // (Xcopy != nullptr: X is also copied there, row-major, from the same read)
+// kernel ridge: the Gaussian kernel matrix on the tensor cores (FP32) or in FP64, and
+// A = K^T K + lambda I turned into K^T (K + lambda I)
+size_t rbf_tc_ws_floats(int64_t n, int64_t d);
+cudaError_t launch_rbf_tc(cudaStream_t st, const float* P, int64_t n, int64_t d, double sigma,
+                          float* K, int64_t ldK, float* ws, int32_t* err);
+template <typename TP>
+cudaError_t launch_rbf_f64(cudaStream_t st, const TP* P, int64_t n, int64_t d, double sigma,
+                           double* K, int64_t ldK);
+template <typename T>
+cudaError_t launch_add_offdiag(cudaStream_t st, T* A, int64_t lda, const T* K, int64_t ldK,
+                               int64_t n, double lambda);
 cudaError_t launch_gram_tc(cudaStream_t st, const float* X, int64_t n, int64_t d, double lambda,
                            float* A, int64_t lda, float* Xt_ws, int32_t* err,
                            float* Xcopy = nullptr);

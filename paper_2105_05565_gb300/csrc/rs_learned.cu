@@ -413,8 +413,7 @@ cudaError_t launch_lp_plans(cudaStream_t st, const Ctrl* ctrl, int force, int ns
     k_lp_score<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(w, zstat, stats, dyn, m, score,
                                                             nullptr);
   }
-  cudaError_t e = cudaFuncSetAttribute(k_lp_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = set_smem_max((const void*)k_lp_select, (size_t)((int)smem));
   if (e != cudaSuccess) return e;
   k_lp_select<<<(unsigned)nslots, 1024, smem, st>>>(ctrl, force, nslots, k0_arg, seed, score, m, tau,
                                                     eps, npow2, perm, perm_stride, boff, boff_stride);
@@ -599,8 +598,7 @@ cudaError_t launch_mlp_grad(cudaStream_t st, const float* theta, const float* Z,
   if (n <= 0) return cudaErrorInvalidValue;
   const int nblk = mlp_grad_blocks(n);
   const size_t smem = sizeof(GradSmem);
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = set_smem_max((const void*)k_mlp_grad, (size_t)((int)smem));
   if (e != cudaSuccess) return e;
   k_mlp_grad<<<nblk, kGB, smem, st>>>(theta, Z, y, n, part, loss_part);
   k_mlp_sum<<<(kMlpParams + 255) / 256, 256, 0, st>>>(part, loss_part, nblk, n, grad, loss);

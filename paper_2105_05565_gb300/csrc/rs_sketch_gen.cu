@@ -246,8 +246,7 @@ cudaError_t launch_gen_sample(cudaStream_t st, const Ctrl* ctrl, int64_t k0_arg,
                               int64_t boff_stride, int32_t* err) {
   const int cap = sample_cap(n, cnt);
   const size_t smem = (size_t)cap * 12;
-  cudaError_t e = cudaFuncSetAttribute(k_gen_sample, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = set_smem_max((const void*)k_gen_sample, (size_t)((int)smem));
   if (e != cudaSuccess) return e;
   k_gen_sample<<<nslots, 1024, smem, st>>>(ctrl, k0_arg, seed, n, cnt, cap, mode, kk, tau, perm,
                                            perm_stride, boff, boff_stride, err);
@@ -258,8 +257,7 @@ cudaError_t launch_gen_count(cudaStream_t st, const Ctrl* ctrl, int64_t k0_arg, 
                              uint64_t seed, int64_t m, int64_t tau, int32_t* perm,
                              int64_t perm_stride, int32_t* boff, int64_t boff_stride) {
   const size_t smem = (size_t)tau * 8 + (size_t)tau * 32 * 2;
-  cudaError_t e = cudaFuncSetAttribute(k_gen_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = set_smem_max((const void*)k_gen_count, (size_t)((int)smem));
   if (e != cudaSuccess) return e;
   k_gen_count<<<nslots, 1024, smem, st>>>(ctrl, k0_arg, seed, m, tau, perm, perm_stride, boff,
                                           boff_stride);

@@ -112,13 +112,17 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 }
 }  // namespace
 
-// K steps [kb0, kb0 + nk); accumulate: add the tiles to A (a later range of rows of X),
-// else store them with lambda on the diagonal
+// K steps [kb0, kb0 + nk); mode 1 (accumulate): add the tiles to A (a later range of
+// rows of X); mode 0: store them with lambda on the diagonal; mode 2 (the Gaussian
+// kernel of eq. (Gausskernel) on the rows of the operand, C = P P^T): store
+// exp(-max(sq_r + sq_c - 2 C_rc, 0) * rbf_scale), rbf_scale = 1 / (2 sigma^2)
 __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUtensorMap tmap,
                                                    int64_t d, int64_t kb0, int64_t nk,
                                                    double lambda, int accumulate,
                                                    float* __restrict__ A, int64_t lda,
-                                                   int32_t* __restrict__ err) {
+                                                   int32_t* __restrict__ err,
+                                                   const float* __restrict__ sqn,
+                                                   float rbf_scale) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzled stages
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -215,8 +219,14 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
           const int64_t cidx = col0 + c0 + q;
           if (cidx < d && cidx <= r) {
             float f = __uint_as_float(v[q]);
-            if (accumulate) f += A[r * lda + cidx];
-            else if (cidx == r) f = (float)((double)f + lambda);
+            if (accumulate == 2) {
+              const float d2 = fmaxf(sqn[r] + sqn[cidx] - 2.f * f, 0.f);
+              f = (cidx == r) ? 1.f : expf(-d2 * rbf_scale);
+            } else if (accumulate) {
+              f += A[r * lda + cidx];
+            } else if (cidx == r) {
+              f = (float)((double)f + lambda);
+            }
             A[r * lda + cidx] = f;
           }
         }
@@ -300,7 +310,7 @@ cudaError_t launch_gram_tc_rows(cudaStream_t st, const float* X, int64_t n, int6
   const int64_t Tp = (T + 1) / 2;         // row-block pairs
   const int64_t pairs = Tp * (Tp + 1) / 2;  // (pair, column block) with tj <= pair
   const size_t smem = (size_t)kStages * kStageBytes + 1024;
-  e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = set_smem_max((const void*)k_gram_tc, (size_t)((int)smem));
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(2 * pairs));
@@ -308,7 +318,65 @@ cudaError_t launch_gram_tc_rows(cudaStream_t st, const float* X, int64_t n, int6
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   return cudaLaunchKernelEx(&cfg, k_gram_tc, map, d, r0 / kBK, (k1 - r0) / kBK, lambda,
-                            r0 > 0 ? 1 : 0, A, lda, err);
+                            r0 > 0 ? 1 : 0, A, lda, err, (const float*)nullptr, 0.f);
+}
+
+// the rows of P (n x d) zero-padded to ldk = round_up(d, 32) columns (the K-major
+// operand of C = P P^T), and their squared norms in FP32 (summed in FP64)
+__global__ void k_pad_rows(const float* __restrict__ P, int64_t n, int64_t d, int64_t ldk,
+                           float* __restrict__ out, float* __restrict__ sqn) {
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int64_t k = lane; k < ldk; k += 32) {
+    const float v = k < d ? P[i * d + k] : 0.f;
+    out[i * ldk + k] = v;
+    s += (double)v * (double)v;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) sqn[i] = (float)s;
+}
+
+size_t rbf_tc_ws_floats(int64_t n, int64_t d) { return (size_t)n * round_up(d, 32) + (size_t)n; }
+
+// K = exp(-||p_i - p_j||^2 / (2 sigma^2)) of the rows of P (n x d, FP32, device), the
+// lower triangle on the tensor cores (TF32 products, FP32 accumulation in tensor
+// memory, the kernel's exponential in the epilogue), into K (n x ldK); the caller
+// mirrors the upper triangle. ws: rbf_tc_ws_floats(n, d) floats.
+cudaError_t launch_rbf_tc(cudaStream_t st, const float* P, int64_t n, int64_t d, double sigma,
+                          float* K, int64_t ldK, float* ws, int32_t* err) {
+  const int64_t ldk = round_up(d, 32);
+  float* Pp = ws;
+  float* sqn = ws + (size_t)n * ldk;
+  k_pad_rows<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(P, n, d, ldk, Pp, sqn);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)n};
+  const cuuint64_t strides[1] = {(cuuint64_t)ldk * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, Pp, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const int64_t T = (n + kBM - 1) / kBM;
+  const int64_t Tp = (T + 1) / 2;
+  const int64_t pairs = Tp * (Tp + 1) / 2;
+  const size_t smem = (size_t)kStages * kStageBytes + 1024;
+  e = set_smem_max((const void*)k_gram_tc, (size_t)((int)smem));
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * pairs));
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  const float scale = (float)(1.0 / (2.0 * sigma * sigma));
+  return cudaLaunchKernelEx(&cfg, k_gram_tc, map, n, (int64_t)0, ldk / kBK, 0.0, 2, K, ldK, err,
+                            (const float*)sqn, scale);
 }
 
 cudaError_t launch_gram_tc(cudaStream_t st, const float* X, int64_t n, int64_t d, double lambda,

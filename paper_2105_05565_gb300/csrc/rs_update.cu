@@ -4,6 +4,10 @@
 //   r^{k+1} = (1 + beta_k) r^k - beta_k r^{k-1} - gamma_k (A S delta)
 // with (A S delta)_i = sum_j (S^T A)[j, i] delta_j (A symmetric), fused with the
 // squared norm of r^{k+1}, the history entry and the stopping test.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "rs_kernels.cuh"
 
 namespace rs {
@@ -136,6 +140,36 @@ cudaError_t launch_init_state(cudaStream_t st, int64_t m, const double* b, doubl
                               double* r, double* rp, double* u) {
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 1024));
   k_init_state<<<blocks, 256, 0, st>>>(m, b, w, wp, r, rp, u);
+  return cudaGetLastError();
+}
+
+// The maximum dynamic shared memory of a kernel is a per-function attribute: a launcher
+// that set it to its own launch's size would lower it for other launches of the same
+// function already captured in a CUDA graph (the batch captures one launch per
+// problem, of uneven sizes). Raised only, per function and device.
+cudaError_t set_smem_max(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = done[std::make_pair(func, dev)];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+
+__global__ void k_cast_f64_f32(const double* __restrict__ in, int64_t n, float* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+cudaError_t launch_cast_f64_f32(cudaStream_t st, const double* in, int64_t n, float* out) {
+  const int64_t b = (n + 255) / 256;
+  k_cast_f64_f32<<<(unsigned)(b < 4096 ? b : 4096), 256, 0, st>>>(in, n, out);
   return cudaGetLastError();
 }
 
