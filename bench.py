@@ -369,11 +369,46 @@ def bench_sparse(args, rs, dev):
     print(json.dumps(out), flush=True)
 
 
+def bench_kernel(args, rs, dev):
+    """Kernel ridge with the Gaussian kernel (Section 2.2), California-Housing-shaped
+    synthetic data: n = 20640 points in d = 8 standardised features (a mixture of
+    three Gaussian clusters), y = sin(x_1) + x_2 x_3 / 2 + 0.1 noise, sigma = 1,
+    lambda = 1e-2; count sketch tau = 256 with the heuristic momentum, plain FP64 and
+    mixed (kernel matrix and A on the tensor cores), and CG on the same system; time to
+    1e-4 (the tolerance of the paper's Experiment 1) and to 1e-6."""
+    n, d, sigma, lam = 20640, 8, 1.0, 1e-2
+    g = np.random.default_rng(4321)
+    centers = g.standard_normal((3, d)) * 1.5
+    P = centers[g.integers(0, 3, n)] + g.standard_normal((n, d))
+    P = (P - P.mean(axis=0)) / P.std(axis=0)
+    y = np.sin(P[:, 0]) + 0.5 * P[:, 1] * P[:, 2] + 0.1 * g.standard_normal(n)
+    out = {"workload": "kernel ridge RBF", "n": n, "d": d, "sigma": sigma, "lambda": lam}
+    for prec in ("mixed", "fp64"):
+        Pp = P.astype(np.float32) if prec == "mixed" else P
+        with rs.Solver(Pp, y, lam, sketch="count", tau=256, momentum="heuristic", seed=0,
+                       precision=prec, kernel_sigma=sigma) as s:
+            setup_ms, _ = s.timings()
+            row = {"setup_ms": setup_ms}
+            for tol in (1e-4, 1e-6):
+                _, hist, iters, conv = s.solve(tol=tol, max_iters=60000)
+                _, solve_ms = s.timings()
+                _, hc, itc, cvc = s.solve_cg(tol=tol, max_iters=60000)
+                _, cg_ms = s.timings()
+                row[f"snp_{tol:g}"] = {"iters": iters, "converged": bool(conv), "solve_ms": solve_ms,
+                                       "final_rel": float(hist[-1])}
+                row[f"cg_{tol:g}"] = {"iters": itc, "converged": bool(cvc), "solve_ms": cg_ms,
+                                      "final_rel": float(hc[-1])}
+            out[prec] = row
+    print(json.dumps(out), flush=True)
+
+
 def profile_case(workload, rs, dev):
     """Short cases of the other workloads for ncu captures (mixed precision):
     batched: the first 32 problems of the batched recipe, 50 iterations, 256 threads
     per CTA, one phase-1 stream; sparse: the sparse recipe, 100 iterations in chunks
-    of 50; learned: X = U diag(i^-0.8) V^T at 16384 x 8192, lambda 1e-3, an untrained
+    of 50; kernel: kernel ridge on 8192 random points in 8 dimensions (mixed: the
+    tensor-core kernel matrix, then K^T K), 50 iterations; learned: X = U diag(i^-0.8)
+    V^T at 16384 x 8192, lambda 1e-3, an untrained
     network (synth.mlp_init(4) rounded to bfloat16), eps 0.1, 60 iterations in chunks
     of 20. Prints one line with the iteration count."""
     import torch
@@ -404,6 +439,13 @@ def profile_case(workload, rs, dev):
         with rs.Solver(X, y, 0.1, sketch="subcount", tau=512, momentum="heuristic", seed=0,
                        precision="mixed", sub_s=4096, refresh_every=50) as s:
             _, _, out, _ = s.solve(tol=0.0, max_iters=100)
+    elif workload == "kernel":
+        g = np.random.default_rng(4321)
+        P = g.standard_normal((8192, 8)).astype(np.float32)
+        y = np.sin(P[:, 0].astype(np.float64))
+        with rs.Solver(P, y, 1e-2, sketch="count", tau=256, momentum="heuristic", seed=0,
+                       precision="mixed", kernel_sigma=1.0) as s:
+            _, _, out, _ = s.solve(tol=0.0, max_iters=50)
     else:
         from synth import mlp_init, power_sigma, spectrum_problem_torch
 
@@ -512,7 +554,8 @@ def main():
                          "sketch and schedule, prints the line of that case; with --workload "
                          "batched / sparse / learned the short case of that workload for ncu "
                          "(profile_case)")
-    ap.add_argument("--workload", default="dense", choices=["dense", "batched", "sparse", "learned"],
+    ap.add_argument("--workload", default="dense",
+                    choices=["dense", "batched", "sparse", "learned", "kernel"],
                     help="dense: the benchmark line; batched / sparse: measurement lines of the "
                          "256-problem batch and the Zipf-sparse matrix-free solve")
     args = ap.parse_args()
@@ -528,7 +571,8 @@ def main():
         rs.lib()
         if args.small:
             return profile_case(args.workload, rs, dev)
-        fn = {"batched": bench_batched, "sparse": bench_sparse, "learned": bench_learned}[args.workload]
+        fn = {"batched": bench_batched, "sparse": bench_sparse, "learned": bench_learned,
+              "kernel": bench_kernel}[args.workload]
         return fn(args, rs, dev)
 
     import torch
