@@ -221,6 +221,7 @@ def cpu_baseline(X, y, iters_ref, sample_iters=4):
     oracle.sketch_and_project(A, b, "count", TAU, 0, 0.0, sample_iters,
                               mom={"kind": "heuristic"})
     t_it = (time.perf_counter() - t1) / sample_iters
+    one = single_thread_iters(A, b)
     w_star = np.linalg.solve(A, b)
     del A
     Xs, ys, _ = gaussian_problem(SMALL["n"], SMALL["d"], seed=0)
@@ -232,10 +233,35 @@ def cpu_baseline(X, y, iters_ref, sample_iters=4):
            "sample": (f"numpy FP64 oracle: setup X^T X on the full 100000x4096 X ({t_setup:.1f} s), "
                       f"then {sample_iters} count-sketch iterations ({t_it * 1e3:.0f} ms each); "
                       f"time to 1e-6 extrapolated with {iters_ref} iterations = "
-                      f"{t_setup + iters_ref * t_it:.1f} s"),
-           "setup_s": t_setup, "s_per_iter": t_it,
+                      f"{t_setup + iters_ref * t_it:.1f} s; on one thread the iterations take "
+                      f"{one if one is None else round(one * 1e3)} ms each"),
+           "setup_s": t_setup, "s_per_iter": t_it, "s_per_iter_1_thread": one,
            "small_case": {"iters": int(ref["iters"]), "s": t_small}}
     return out, w_star, ref
+
+
+def single_thread_iters(A, b, iters=2):
+    """Seconds per iteration of the oracle's count-sketch loop on one host thread: a
+    child process with the BLAS thread pools set to one thread (they are fixed when
+    numpy loads) runs `iters` iterations on the same A, b."""
+    import tempfile
+
+    with tempfile.TemporaryDirectory() as d:
+        np.save(os.path.join(d, "A.npy"), A)
+        np.save(os.path.join(d, "b.npy"), b)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+                   MKL_NUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+        code = ("import sys, time, numpy as np; sys.path.insert(0, sys.argv[1]); import oracle; "
+                "A = np.load(sys.argv[2]); b = np.load(sys.argv[3]); t = time.perf_counter(); "
+                f"oracle.sketch_and_project(A, b, 'count', {TAU}, 0, 0.0, {iters}, "
+                "mom={'kind': 'heuristic'}); print((time.perf_counter() - t) / " + str(iters) + ")")
+        try:
+            out = subprocess.run([sys.executable, "-c", code, ROOT, os.path.join(d, "A.npy"),
+                                  os.path.join(d, "b.npy")], env=env, capture_output=True,
+                                 text=True, timeout=600)
+            return float(out.stdout.strip().splitlines()[-1])
+        except Exception:
+            return None
 
 
 def run_reference(args):
@@ -406,11 +432,16 @@ def profile_case(workload, rs, dev):
     """Short cases of the other workloads for ncu captures (mixed precision):
     batched: the first 32 problems of the batched recipe, 50 iterations, 256 threads
     per CTA, one phase-1 stream; sparse: the sparse recipe, 100 iterations in chunks
-    of 50; kernel: kernel ridge on 8192 random points in 8 dimensions (mixed: the
+    of 50; plain: the dense recipe at 20000 x 4096 in plain FP64 (count sketch tau = 256,
+    heuristic momentum) to 1e-6; gaussian: the dense recipe at 20000 x 4096 with the
+    Gaussian sketch tau = 256
+    in mixed precision (S^T A on the tensor cores), one chunk of 64 slots;
+    kernel: kernel ridge on 8192 random points in 256 dimensions (mixed: the
     tensor-core kernel matrix, then K^T K), 50 iterations; learned: X = U diag(i^-0.8)
-    V^T at 16384 x 8192, lambda 1e-3, an untrained
-    network (synth.mlp_init(4) rounded to bfloat16), eps 0.1, 60 iterations in chunks
-    of 20. Prints one line with the iteration count."""
+    V^T at 16384 x 8192, lambda 1e-3, an untrained network (synth.mlp_init(4) rounded
+    to bfloat16), eps 0.1, 60 iterations in chunks of 20, then three training steps of
+    the network on 65536 random rows (the gradient kernel). Prints one line with the
+    iteration count."""
     import torch
 
     if workload == "batched":
@@ -439,12 +470,25 @@ def profile_case(workload, rs, dev):
         with rs.Solver(X, y, 0.1, sketch="subcount", tau=512, momentum="heuristic", seed=0,
                        precision="mixed", sub_s=4096, refresh_every=50) as s:
             _, _, out, _ = s.solve(tol=0.0, max_iters=100)
+    elif workload == "plain":
+        X, y, _ = make_problem(1234, dev, 20000)
+        with rs.Solver(X.double(), y, LAM, sketch="count", tau=TAU, momentum="heuristic", seed=0,
+                       precision="fp64") as s:
+            _, _, out, _ = s.solve(tol=TOL, max_iters=MAX_IT)
+    elif workload == "gaussian":
+        from synth import geometric_sigma, spectrum_problem_torch
+
+        X, y, _ = spectrum_problem_torch(20000, 4096, geometric_sigma(4096, 1e-3), seed=1234,
+                                         noise=0.01, device=dev)
+        with rs.Solver(X, y, LAM, sketch="gaussian", tau=TAU, momentum="heuristic", seed=0,
+                       precision="mixed", chunk=64) as s:
+            _, _, out, _ = s.solve(tol=0.0, max_iters=64)
     elif workload == "kernel":
         g = np.random.default_rng(4321)
-        P = g.standard_normal((8192, 8)).astype(np.float32)
+        P = g.standard_normal((8192, 256)).astype(np.float32)
         y = np.sin(P[:, 0].astype(np.float64))
         with rs.Solver(P, y, 1e-2, sketch="count", tau=256, momentum="heuristic", seed=0,
-                       precision="mixed", kernel_sigma=1.0) as s:
+                       precision="mixed", kernel_sigma=16.0) as s:
             _, _, out, _ = s.solve(tol=0.0, max_iters=50)
     else:
         from synth import mlp_init, power_sigma, spectrum_problem_torch
@@ -456,6 +500,13 @@ def profile_case(workload, rs, dev):
                        precision="mixed", chunk=20, refresh_every=20) as s:
             s.set_proposal(wb, 0.1)
             _, _, out, _ = s.solve(tol=0.0, max_iters=60)
+        # training steps of the network (the gradient kernel's tensor-core products)
+        g = np.random.default_rng(0)
+        Z = torch.as_tensor(g.standard_normal((65536, 4)), dtype=torch.float32, device=dev)
+        t = torch.as_tensor(g.standard_normal(65536), dtype=torch.float32, device=dev)
+        with rs.MLP(mlp_init(4)) as net:
+            for _ in range(3):
+                net.step(Z, t, 1e-3)
     print(json.dumps({"profile_case": workload, "iters": out}), flush=True)
 
 
@@ -487,9 +538,11 @@ def bench_learned(args, rs, dev):
             w_star, _, _, _ = s.solve(tol=1e-11, max_iters=200000)
         Xd = X.double()
         del X
+        b = (Xd.T @ y.double()).cpu().numpy()  # the collection starts from w = 0, r = -b
         with rs.Solver(Xd, y, lam, sketch="subsample", tau=tau, momentum="none", seed=sd,
                        chunk=1) as s:
             s.set_proposal(None, 0.1)
+            s.set_state(np.zeros(m), np.zeros(m), -b, -b, 0)
             Z, t = learned.collect(s, w_star, 1500, tol=1e-6)
         del Xd
         Zs.append(Z)
@@ -555,7 +608,8 @@ def main():
                          "batched / sparse / learned the short case of that workload for ncu "
                          "(profile_case)")
     ap.add_argument("--workload", default="dense",
-                    choices=["dense", "batched", "sparse", "learned", "kernel"],
+                    choices=["dense", "batched", "sparse", "learned", "kernel", "gaussian",
+                             "plain"],
                     help="dense: the benchmark line; batched / sparse: measurement lines of the "
                          "256-problem batch and the Zipf-sparse matrix-free solve")
     args = ap.parse_args()
@@ -571,6 +625,8 @@ def main():
         rs.lib()
         if args.small:
             return profile_case(args.workload, rs, dev)
+        if args.workload in ("gaussian", "plain"):
+            raise SystemExit(f"--workload {args.workload} is a profiling case: use it with --small")
         fn = {"batched": bench_batched, "sparse": bench_sparse, "learned": bench_learned,
               "kernel": bench_kernel}[args.workload]
         return fn(args, rs, dev)

@@ -134,7 +134,7 @@ typedef struct {
                             chunk are formed and factored ahead in batched launches, and
                             the chunk's iterations follow (RS_MIXED: one launch of the
                             persistent kernel per refresh period, an FP64 refresh after
-                            each). 0 = 600 (RS_MIXED) or 128 (plain). RS_MIXED rounds it up
+                            each). 0 = 600 (128 for plain FP64 CSR X). RS_MIXED rounds it up
                             to a whole number of refresh periods; every kind reduces it so
                             that the chunk's buffers stay under 4 GB */
   int32_t setup_tc;      /* RS_MIXED, primal, FP32 X: 1 = form X^T X on the tensor cores
@@ -220,7 +220,8 @@ rs_status rs_get_kernel(rs_ctx* ctx, double* K_out);
  * direct competitor of the paper's Experiment 3 (Section 8.3), for time-to-tolerance
  * comparisons on the same context. The sketch settings are not used. Dense A: the
  * formed A (FP64; RS_MIXED: the FP32 A with float-pair products and the FP64 true
- * residual through X every refresh_every iterations, which also decides convergence);
+ * residual through X every refresh_every iterations, which also decides convergence,
+ * and CG restarts from it: iterative refinement with an inner CG on the FP32 A);
  * CSR X: A p = X^T (X p) + lambda p with FP64 sums over the stored values. Starts
  * from w = 0. Arguments, outputs and status codes as for rs_solve (hist_out: the
  * relative residual of every iteration, FP64-checked ones at the refreshes);

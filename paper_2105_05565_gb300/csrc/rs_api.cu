@@ -117,6 +117,7 @@ struct rs_ctx {
   bool use_wide = false;
   WidePlan wide{};
   void* Pm = nullptr;       // per slot: M^+ = L^{-T} L^{-1}, tau x pld (factor precision)
+  int32_t* tc_err = nullptr;  // a tensor-core GEMM of phase 1 gave up a bounded wait
   void* pws = nullptr;      // per slot: tile workspace of k_potri when the tiles pass shared memory
   bool potri = false;       // M^+ by the one-kernel factor, inverse and product
   bool sweep_p = false;     // M^+ by FP32 sweeps from an FP32 M (mixed, FP32 factor)
@@ -282,7 +283,8 @@ void free_all(rs_ctx* c) {
                   c->sx_pcol, c->sx_pstart, c->sx_cpiece, c->mf_bsum, c->mf_boffs, c->mf_tot,
                   c->mf_crow, c->mf_cptr, c->mf_ebuck, c->mf_eval, c->mf_v, c->mf_pu, c->mf_pud,
                   c->mf_z, c->lp_w, c->lp_raw, c->lp_zstat, c->lp_stats, c->lp_score, c->lp_feat,
-                  c->lp_last, c->wsum, c->cg_p, c->cg_v, c->cg_part, c->cg_s, c->cg_p2};
+                  c->lp_last, c->wsum, c->cg_p, c->cg_v, c->cg_part, c->cg_s, c->cg_p2,
+                  c->tc_err};
   for (void* p : ptrs) pfree(c, p);
   if (c->ctrl_h) {  // the stream may still read the pinned control block
     cudaStreamSynchronize(c->stream);
@@ -463,6 +465,16 @@ rs_status enqueue_phase1_t(rs_ctx* c, int force, int64_t k0_arg, int nslots, boo
       T* ST = static_cast<T*>(c->ST);
       CKC(c, launch_gen_gauss<T>(st, c->ctrl, force, nslots, k0_arg, c->seed, c->m, c->tau, ST,
                                  c->ld, c->sa_slot));
+      if constexpr (sizeof(T) == 4) {
+        if (c->tc_err != nullptr && c->sa_slot == c->tau * c->ld) {
+          // S^T A of all slots as one TF32 tensor-core product, then M = S^T A S
+          CKC(c, launch_gauss_sa_tc(st, c->ctrl, force, nslots, ST, c->ld, c->m, c->tau, A, c->ld,
+                                    SA, c->tc_err));
+          CKC(c, launch_gauss_msys<T>(st, c->ctrl, force, nslots, ST, c->sa_slot, c->m, c->tau,
+                                      SA, c->ld, c->sa_slot, c->M, c->m_slot, c->ld));
+          break;
+        }
+      }
       CKC(c, launch_gauss_system<T>(st, c->ctrl, force, nslots, ST, c->sa_slot, A, c->ld, c->m,
                                     c->tau, SA, c->ld, c->sa_slot, c->M, c->m_slot));
       break;
@@ -1168,7 +1180,9 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   // batch) holds a whole number of refresh periods; by default the smallest such
   // number of iterations >= kMixedChunk, so that phase 1 keeps every SM busy even
   // when the refresh period is short
-  c->chunk = o.chunk > 0 ? o.chunk : (c->mixed() ? kMixedChunk : 128);
+  // default chunks: 600 slots for dense A in either precision (the FP64 factor's
+  // four CTAs per SM then fill the GPU), 128 for the matrix-free path
+  c->chunk = o.chunk > 0 ? o.chunk : ((c->mixed() || !c->sparse) ? kMixedChunk : 128);
   if (c->mixed()) {  // a chunk shorter than the period shortens the period to it
     if (c->chunk < c->refresh_every) c->refresh_every = (int)c->chunk;
     c->chunk = round_up(c->chunk, (int64_t)c->refresh_every);
@@ -1383,6 +1397,10 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     if (sketch == RS_GAUSSIAN) {
       TRYC(pmalloc(c, (void**)&c->ST, nsl * c->sa_slot * c->elem()));
       TRYC(cudaMemsetAsync(c->ST, 0, nsl * c->sa_slot * c->elem(), st));
+      if (c->mixed()) {  // S^T A on the tensor cores
+        TRY(dalloc(c, &c->tc_err, 1));
+        TRYC(cudaMemsetAsync(c->tc_err, 0, sizeof(int32_t), st));
+      }
     }
   }
   if (sketch != RS_GAUSSIAN) {
@@ -1505,6 +1523,14 @@ rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int3
     int32_t gen_err = 0;
     CKC(c, copy_sync(c, &gen_err, c->err_flag, sizeof(int32_t), cudaMemcpyDeviceToHost));
     if (gen_err) FAILC(c, RS_ECUDA, "sketch generation: sample threshold search failed");
+    if (c->tc_err != nullptr) {
+      int32_t te = 0;
+      CKC(c, copy_sync(c, &te, c->tc_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+      if (te) {
+        CKC(c, cudaMemsetAsync(c->tc_err, 0, sizeof(int32_t), c->stream));
+        FAILC(c, RS_ETIMEOUT, "rs_solve: a bounded wait of the tensor-core S^T A gave up");
+      }
+    }
     if (h->status == RS_ETIMEOUT) {
       FAILC(c, RS_ETIMEOUT, "rs_solve: a bounded device-side wait of the iteration kernel gave up");
     } else if (h->status == RS_ENUMERIC) {
@@ -2107,7 +2133,7 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
       s = timed("mf_iter", [&]() { return enqueue_mf_iteration(c); });
       // per iteration: X restricted to the sampled columns' rows is touched through
       // the compact rows; X^T v reads every stored entry once
-      grp("mf_iter").bytes = (double)c->nnz * (4.0 + (c->xdtype == RS_BF16 ? 2.0 : (c->xdtype == RS_F32 ? 4.0 : 8.0))) + m * 48.0;
+      grp("mf_iter").bytes += (double)c->nnz * (4.0 + (c->xdtype == RS_BF16 ? 2.0 : (c->xdtype == RS_F32 ? 4.0 : 8.0))) + m * 48.0;
       grp("mf_iter").iters += 1;
       if (s == RS_OK && c->mixed() && (it + 1) % c->refresh_every == 0)
         s = timed("refresh", [&]() { return enqueue_refresh(c); });
@@ -2148,8 +2174,8 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
               CKC(c, launch_sa_msys<double>(c->stream, c->ctrl, 0, ns, plan, static_cast<const double*>(c->A), c->ld, c->m, c->tau, static_cast<double*>(c->SA), c->ld, c->sa_slot, bq, c->M, c->m_slot));
             return RS_OK;
           });
-          grp("sa_msys").bytes = nsl * (rows * m * el + tau * m * el + rows * 4.0 + tau * tau * 8.0);
-          grp("sa_msys").flops = nsl * (rows * m + tau * rows);
+          grp("sa_msys").bytes += nsl * (rows * m * el + tau * m * el + rows * 4.0 + tau * tau * 8.0);
+          grp("sa_msys").flops += nsl * (rows * m + tau * rows);
           if (s != RS_OK) break;
         } else {
           if (has_sa) {
@@ -2160,8 +2186,8 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
                 CKC(c, launch_sa_batched<double>(c->stream, c->ctrl, 0, ns, plan, static_cast<const double*>(c->A), c->ld, c->m, c->tau, static_cast<double*>(c->SA), c->ld, c->sa_slot, bq));
               return RS_OK;
             });
-            grp("sa").bytes = nsl * (rows * m * el + tau * m * el + rows * 4.0);
-            grp("sa").flops = nsl * rows * m;
+            grp("sa").bytes += nsl * (rows * m * el + tau * m * el + rows * 4.0);
+            grp("sa").flops += nsl * rows * m;
             if (s != RS_OK) break;
           }
           s = timed("msys", [&]() -> rs_status {
@@ -2169,8 +2195,8 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
             else CKC(c, launch_msys_batched<double>(c->stream, c->ctrl, 0, ns, plan, rows_view<double>(c), c->m, c->tau, c->M, c->m_slot));
             return RS_OK;
           });
-          grp("msys").bytes = nsl * ((c->sketch == RS_SUBSAMPLE ? tau * tau * el : tau * m * el + rows * 4.0) + tau * tau * 8.0);
-          grp("msys").flops = nsl * (c->sketch == RS_SUBSAMPLE ? 0.0 : tau * rows);
+          grp("msys").bytes += nsl * ((c->sketch == RS_SUBSAMPLE ? tau * tau * el : tau * m * el + rows * 4.0) + tau * tau * 8.0);
+          grp("msys").flops += nsl * (c->sketch == RS_SUBSAMPLE ? 0.0 : tau * rows);
           if (s != RS_OK) break;
         }
         const bool sweep = c->sweep_p;
@@ -2179,16 +2205,16 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
             CKC(c, launch_sweep_inv(c->stream, c->ctrl, 0, ns, c->Mf, c->m_slot, c->tau, static_cast<float*>(c->Pm), c->pld, c->p_slot, c->ndropped));
             return RS_OK;
           });
-          grp("sweep").bytes = nsl * tau * tau * (8.0 + 4.0);
-          grp("sweep").flops = nsl * tau * tau * tau;
+          grp("sweep").bytes += nsl * tau * tau * (8.0 + 4.0);
+          grp("sweep").flops += nsl * tau * tau * tau;
           if (s != RS_OK) break;
         }
         if (!sweep && c->use_wide && c->potri) {
           // factor, inverse and M^+ in one kernel
           s = timed("potri", [&]() { return enqueue_potri(c, c->stream, 0, ns); });
           // Cholesky tau^3 / 3, triangular inverse tau^3 / 3, L^{-T} L^{-1} tau^3 / 3
-          grp("potri").bytes = nsl * (tau * tau * (8.0 + fel));
-          grp("potri").flops = nsl * (tau * tau * tau);
+          grp("potri").bytes += nsl * (tau * tau * (8.0 + fel));
+          grp("potri").flops += nsl * (tau * tau * tau);
           if (s != RS_OK) break;
         } else {
         if (!sweep) s = timed("factor", [&]() -> rs_status {
@@ -2199,8 +2225,8 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
           return RS_OK;
         });
         if (!sweep) {
-          grp("factor").bytes = nsl * (tau * tau * (8.0 + fel));
-          grp("factor").flops = nsl * (2.0 * tau * tau * tau / 3.0);
+          grp("factor").bytes += nsl * (tau * tau * (8.0 + fel));
+          grp("factor").flops += nsl * (2.0 * tau * tau * tau / 3.0);
         }
         if (s != RS_OK) break;
         if (c->use_wide && !sweep) {
@@ -2211,8 +2237,8 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
               CKC(c, launch_pinv<float>(c->stream, c->ctrl, 0, ns, static_cast<const float*>(c->Linv), c->l_slot, c->tau, static_cast<float*>(c->Pm), c->pld, c->p_slot));
             return RS_OK;
           });
-          grp("pinv").bytes = nsl * (tau * tau * 2.0 * fel);
-          grp("pinv").flops = nsl * (2.0 * tau * tau * tau);
+          grp("pinv").bytes += nsl * (tau * tau * 2.0 * fel);
+          grp("pinv").flops += nsl * (2.0 * tau * tau * tau);
           if (s != RS_OK) break;
         }
         }
@@ -2230,32 +2256,32 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
         // algorithmic HBM bytes: S^T A (or the sampled rows of A) and the small system
         // of every iteration; the persistent kernel reads and writes w, w_prev, r,
         // r_prev once per launch, the cluster kernel every iteration
-        grp("iterate").bytes = c->use_wide
+        grp("iterate").bytes += c->use_wide
             ? (double)nit * (tau * m * el + tau * tau * pel + 4.0 * m) + 64.0 * m
             : (double)nit * (tau * m * el + tau * tau * fel + 80.0 * m);
-        grp("iterate").flops = (double)nit * (2.0 * tau * m + 2.0 * tau * tau + 10.0 * m);
+        grp("iterate").flops += (double)nit * (2.0 * tau * m + 2.0 * tau * tau + 10.0 * m);
         grp("iterate").iters += nit;
         done += nit;
         if (s == RS_OK && c->mixed()) {
           s = timed("refresh", [&]() { return enqueue_refresh(c); });
-          grp("refresh").bytes = (double)c->n * (double)c->d * (c->xdtype == RS_F32 ? 4.0 : 8.0) + m * 48.0;
-          grp("refresh").flops = 4.0 * (double)c->n * (double)c->d;
+          grp("refresh").bytes += (double)c->n * (double)c->d * (c->xdtype == RS_F32 ? 4.0 : 8.0) + m * 48.0;
+          grp("refresh").flops += 4.0 * (double)c->n * (double)c->d;
         }
       }
       it += done - 1;
       continue;
     }
     s = timed("delta", [&]() { return enqueue_delta(c, 0, -1); });
-    grp("delta").bytes = tau * tau * fel / 2.0 + rows * 12.0 + m * 8.0;
-    grp("delta").flops = 2.0 * tau * tau;
+    grp("delta").bytes += tau * tau * fel / 2.0 + rows * 12.0 + m * 8.0;
+    grp("delta").flops += 2.0 * tau * tau;
     if (s != RS_OK) break;
     s = timed("update", [&]() { return enqueue_update(c); });
-    grp("update").bytes = (c->sketch == RS_SUBSAMPLE ? tau * m * el : tau * m * el) + m * 8.0 * 9.0;
-    grp("update").flops = 2.0 * tau * m + 10.0 * m;
+    grp("update").bytes += (c->sketch == RS_SUBSAMPLE ? tau * m * el : tau * m * el) + m * 8.0 * 9.0;
+    grp("update").flops += 2.0 * tau * m + 10.0 * m;
     if (s == RS_OK && c->mixed() && (it + 1) % c->refresh_every == 0) {
       s = timed("refresh", [&]() { return enqueue_refresh(c); });
-      grp("refresh").bytes = 2.0 * (double)c->n * (double)c->d * (c->xdtype == RS_F32 ? 4.0 : 8.0) + m * 48.0;
-      grp("refresh").flops = 4.0 * (double)c->n * (double)c->d;
+      grp("refresh").bytes += 2.0 * (double)c->n * (double)c->d * (c->xdtype == RS_F32 ? 4.0 : 8.0) + m * 48.0;
+      grp("refresh").flops += 4.0 * (double)c->n * (double)c->d;
     }
   }
   cudaEventDestroy(e0);
@@ -2269,8 +2295,9 @@ rs_status rs_profile_iteration(rs_ctx* c, int64_t reps, rs_kernel_stat* out, int
     std::strncpy(o.name, x.name, sizeof(o.name) - 1);
     o.launches = x.n;
     o.ms = x.n ? x.ms / x.n : 0.0;
-    o.bytes = x.bytes;
-    o.flops = x.flops;
+    // per launch, averaged like the times (a chunk's last launch may be shorter)
+    o.bytes = x.n ? x.bytes / x.n : 0.0;
+    o.flops = x.n ? x.flops / x.n : 0.0;
     o.iters = x.iters > 0 ? x.iters : x.n;
   }
   *n_out = n;

@@ -343,6 +343,18 @@ cudaError_t launch_gauss_system(cudaStream_t st, const Ctrl* ctrl, int force, in
                                     nslots, sa_slot, st_slot, m_slot);
 }
 
+// M = S^T A S of every slot from S^T A formed elsewhere (the tensor-core product)
+template <typename T>
+cudaError_t launch_gauss_msys(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
+                              const T* ST, int64_t st_slot, int64_t m, int64_t tau, const T* SA,
+                              int64_t ldsa, int64_t sa_slot, double* M, int64_t m_slot,
+                              int64_t lda) {
+  const Ctrl* c = force ? nullptr : ctrl;
+  // M[j, l] = sum_c SA[j, c] ST[l, c]
+  return gemm_strided<T, T, double>(st, tau, tau, m, SA, ldsa, 1, ST, 1, lda, M, tau, 0.0, 0, c,
+                                    nslots, sa_slot, st_slot, m_slot);
+}
+
 // ---------------------------------------------------------------------------
 // SRHT (Section 4.3): S = (tau m')^{-1/2} D H_{m'}[0:m, C]. Products with S are
 // fast Walsh-Hadamard transforms (Sylvester order, eq. (18)) of length m' in
@@ -435,6 +447,9 @@ cudaError_t launch_srht_system(cudaStream_t st, const Ctrl* ctrl, int force, int
   template cudaError_t launch_msys_batched<T>(cudaStream_t, const Ctrl*, int, int, PlanView,       \
                                               RowsView<T>, int64_t, int64_t, double*, int64_t,     \
                                               float*);                                             \
+  template cudaError_t launch_gauss_msys<T>(cudaStream_t, const Ctrl*, int, int, const T*,        \
+                                           int64_t, int64_t, int64_t, const T*, int64_t, int64_t,   \
+                                           double*, int64_t, int64_t);                              \
   template cudaError_t launch_gauss_system<T>(cudaStream_t, const Ctrl*, int, int, const T*,       \
                                               int64_t, const T*, int64_t, int64_t, int64_t, T*,    \
                                               int64_t, int64_t, double*, int64_t);                 \

@@ -11,7 +11,8 @@
 // the last block (ticket in CgScal) in a fixed order. Every kernel returns at once
 // when the control block says stop or pending; in mixed precision an FP64 refresh
 // of r through X (the one of the sketch-and-project path) follows every refresh
-// period and decides convergence, and k_cg_rr re-forms r . r after it.
+// period and decides convergence, and k_cg_rr re-forms r . r after it and restarts
+// the directions (iterative refinement with an inner CG on the FP32 A).
 #include <algorithm>
 
 #include "rs_kernels.cuh"
@@ -201,7 +202,10 @@ __global__ void __launch_bounds__(256) k_cg_update(Ctrl* __restrict__ ctrl, CgSc
   }
 }
 
-// r . r (after a refresh replaced r; also the start of a solve), one block
+// r . r at the start of a solve, and after a refresh replaced r by the FP64 true
+// residual: CG then restarts from it (beta = 0, p = -r), iterative refinement with an
+// inner CG on the FP32 operator (continuing the old directions with the replaced
+// residual loses conjugacy when the FP32 A differs much from the exact one), one block
 __global__ void __launch_bounds__(1024) k_cg_rr(const Ctrl* __restrict__ ctrl, CgScal* __restrict__ cs,
                                                 int64_t m, const double* __restrict__ r, int init) {
   __shared__ double s_red[32];
@@ -211,8 +215,8 @@ __global__ void __launch_bounds__(1024) k_cg_rr(const Ctrl* __restrict__ ctrl, C
   rr = block_sum(rr, s_red);
   if (threadIdx.x == 0) {
     cs->rr = rr;
+    cs->beta = 0.0;
     if (init) {
-      cs->beta = 0.0;
       cs->pv = 0.0;
       cs->ticket = 0u;
     }

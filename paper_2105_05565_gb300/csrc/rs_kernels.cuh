@@ -64,6 +64,11 @@ cudaError_t launch_msys_batched(cudaStream_t st, const Ctrl* ctrl, int force, in
                                 double* M, int64_t m_slot, float* Mf = nullptr);
 
 template <typename T>
+cudaError_t launch_gauss_msys(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
+                              const T* ST, int64_t st_slot, int64_t m, int64_t tau, const T* SA,
+                              int64_t ldsa, int64_t sa_slot, double* M, int64_t m_slot,
+                              int64_t lda);
+template <typename T>
 cudaError_t launch_gauss_system(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
                                 const T* ST, int64_t st_slot, const T* A, int64_t lda, int64_t m,
                                 int64_t tau, T* SA, int64_t ldsa, int64_t sa_slot, double* M,
@@ -379,6 +384,9 @@ cudaError_t launch_gram_tc_rows(cudaStream_t st, const float* X, int64_t n, int6
 // (Xcopy != nullptr: X is also copied there, row-major, from the same read)
 // kernel ridge: the Gaussian kernel matrix on the tensor cores (FP32) or in FP64, and
 // A = K^T K + lambda I turned into K^T (K + lambda I)
+cudaError_t launch_gauss_sa_tc(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
+                               const float* ST, int64_t ld, int64_t m, int64_t tau,
+                               const float* A, int64_t lda, float* SA, int32_t* err);
 size_t rbf_tc_ws_floats(int64_t n, int64_t d);
 cudaError_t launch_rbf_tc(cudaStream_t st, const float* P, int64_t n, int64_t d, double sigma,
                           float* K, int64_t ldK, float* ws, int32_t* err);

@@ -40,41 +40,99 @@ __device__ __forceinline__ uint16_t to_bf16(float x) {
   return (uint16_t)(__float_as_uint(round_bf16(x)) >> 16);
 }
 
-// network weights (bfloat16 values as FP32) in shared memory
+// network weights in shared memory: all of them as FP32 (bfloat16 values), and W2
+// again as bfloat16 bits, row-major W2[o][i], the B operand of the tensor-core layer
 struct MlpSmem {
   float p[kMlpParams + 3];
+  __align__(16) uint16_t w2h[kH * kH];
 };
 
 __device__ __forceinline__ void load_weights_bf16(MlpSmem& s, const uint16_t* w) {
   for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) s.p[i] = bf16_to_f(w[i]);
+  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) s.w2h[i] = w[kOffW2 + i];
 }
 
-// forward of one feature row; h1 rounded to bfloat16 on the way
-__device__ __forceinline__ float mlp_forward(const MlpSmem& s, const float z[kNF]) {
-  float h1[kH];
-#pragma unroll
-  for (int o = 0; o < kH; ++o) {
-    float a = s.p[kOffB1 + o];
-#pragma unroll
-    for (int i = 0; i < kNF; ++i) a = fmaf(s.p[o * kNF + i], z[i], a);
-    h1[o] = round_bf16(fmaxf(a, 0.f));
-  }
-  float out = s.p[kOffB3];
-  for (int o = 0; o < kH; ++o) {
-    const float4* w2 = reinterpret_cast<const float4*>(s.p + kOffW2 + o * kH);
-    float a = s.p[kOffB2 + o];
-#pragma unroll
-    for (int i4 = 0; i4 < kH / 4; ++i4) {
-      const float4 w = w2[i4];
-      a = fmaf(w.x, h1[4 * i4], a);
-      a = fmaf(w.y, h1[4 * i4 + 1], a);
-      a = fmaf(w.z, h1[4 * i4 + 2], a);
-      a = fmaf(w.w, h1[4 * i4 + 3], a);
-    }
-    out = fmaf(s.p[kOffW3 + o], round_bf16(fmaxf(a, 0.f)), out);
-  }
-  return out;
+// D (16 x 8, FP32) += A (16 x 16, bfloat16, row-major) B (16 x 8, bfloat16, column-major)
+// on the tensor cores (warp-wide mma). Fragments, with g = lane / 4 and t = lane % 4:
+// A: a[0] = (row g, cols 2t, 2t+1), a[1] = (row g+8, same), a[2] = (row g, cols 2t+8,
+// 2t+9), a[3] = (row g+8, same); B: b[0] = (rows 2t, 2t+1, col g), b[1] = (rows 2t+8,
+// 2t+9, col g); D: d[0..1] = (row g, cols 2t, 2t+1), d[2..3] = (row g+8, same). In a
+// packed register the lower-indexed element sits in the low 16 bits.
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4],
+                                         const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  return (uint32_t)to_bf16(lo) | ((uint32_t)to_bf16(hi) << 16);
+}
+__device__ __forceinline__ uint32_t ld_b32(const uint16_t* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
+}
+
+// layer 1 of the two rows (g, g + 8) of a warp's 16-row tile, as the A fragments of
+// layer 2: h1 = bfloat16(relu(W1 z + b1)), fragment kc covers h1 columns 16 kc..16 kc+15
+__device__ __forceinline__ void mlp_layer1_frag(const float* w, const float zg[kNF],
+                                                const float zg8[kNF], uint32_t (&afr)[4][4]) {
+  const int t = threadIdx.x & 3;
+#pragma unroll
+  for (int kc = 0; kc < 4; ++kc)
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int o0 = 16 * kc + 8 * half + 2 * t;
+      float h[2][2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int o = o0 + q;
+        float a0 = w[kOffB1 + o], a1 = a0;
+#pragma unroll
+        for (int f = 0; f < kNF; ++f) {
+          a0 = fmaf(w[o * kNF + f], zg[f], a0);
+          a1 = fmaf(w[o * kNF + f], zg8[f], a1);
+        }
+        h[0][q] = fmaxf(a0, 0.f);
+        h[1][q] = fmaxf(a1, 0.f);
+      }
+      afr[kc][2 * half] = pack_bf16(h[0][0], h[0][1]);
+      afr[kc][2 * half + 1] = pack_bf16(h[1][0], h[1][1]);
+    }
+}
+
+// scores of the warp's 16 rows: lane (g, t) returns those of rows g and g + 8 (the four
+// lanes of a group agree). Layer 2 on the tensor cores (bfloat16 operands, FP32
+// accumulation); h2 rounded to bfloat16; the output layer in FP32.
+__device__ __forceinline__ void mlp_forward_warp(const MlpSmem& s, const float zg[kNF],
+                                                 const float zg8[kNF], float& out_g,
+                                                 float& out_g8) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  uint32_t afr[4][4];
+  mlp_layer1_frag(s.p, zg, zg8, afr);
+  float og = 0.f, og8 = 0.f;
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int o0 = 8 * nt + 2 * t;
+    float c[4] = {s.p[kOffB2 + o0], s.p[kOffB2 + o0 + 1], s.p[kOffB2 + o0], s.p[kOffB2 + o0 + 1]};
+    const uint16_t* wrow = s.w2h + (8 * nt + g) * kH;
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      const uint32_t b[2] = {ld_b32(wrow + 16 * kc + 2 * t), ld_b32(wrow + 16 * kc + 2 * t + 8)};
+      mma_bf16(c, afr[kc], b);
+    }
+    const float w0 = s.p[kOffW3 + o0], w1 = s.p[kOffW3 + o0 + 1];
+    og = fmaf(w0, round_bf16(fmaxf(c[0], 0.f)), fmaf(w1, round_bf16(fmaxf(c[1], 0.f)), og));
+    og8 = fmaf(w0, round_bf16(fmaxf(c[2], 0.f)), fmaf(w1, round_bf16(fmaxf(c[3], 0.f)), og8));
+  }
+  og += __shfl_xor_sync(0xffffffffu, og, 1);
+  og += __shfl_xor_sync(0xffffffffu, og, 2);
+  og8 += __shfl_xor_sync(0xffffffffu, og8, 1);
+  og8 += __shfl_xor_sync(0xffffffffu, og8, 2);
+  out_g = og + s.p[kOffB3];
+  out_g8 = og8 + s.p[kOffB3];
+}
+
 }  // namespace
 
 // ---- static features: standardised ln A_jj and ln ||A[:, j]|| (A symmetric) ----
@@ -268,6 +326,8 @@ __device__ __forceinline__ void lp_feature_row(const float* zstat, const double*
 }
 
 // ---- per chunk: scores s_j (uniform proposal: s = 0) ----
+constexpr int kScoreRows = 128;  // rows of a 256-thread block: 8 warp tiles of 16
+
 __global__ void __launch_bounds__(256) k_lp_score(const uint16_t* __restrict__ w, const float* zstat,
                                                   const double* stats, const float* __restrict__ dyn,
                                                   int64_t m, float* __restrict__ score,
@@ -275,14 +335,27 @@ __global__ void __launch_bounds__(256) k_lp_score(const uint16_t* __restrict__ w
   __shared__ __align__(16) MlpSmem s;
   if (w != nullptr) load_weights_bf16(s, w);
   __syncthreads();
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= m) return;
-  float z[kNF];
-  lp_feature_row(zstat, stats, dyn, m, j, z);
-  if (feat_out != nullptr)
+  // warp tiles of 16 rows: lane (g, t) holds rows g and g + 8 of its warp's tile
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int64_t j0 = (int64_t)blockIdx.x * kScoreRows + (threadIdx.x >> 5) * 16;
+  if (j0 >= m) return;  // whole warp (the tile's first row is past m)
+  const int64_t jg = j0 + g, jg8 = jg + 8;
+  float zg[kNF] = {0.f, 0.f, 0.f, 0.f}, zg8[kNF] = {0.f, 0.f, 0.f, 0.f};
+  if (jg < m) lp_feature_row(zstat, stats, dyn, m, jg, zg);
+  if (jg8 < m) lp_feature_row(zstat, stats, dyn, m, jg8, zg8);
+  if (feat_out != nullptr && t == 0) {
 #pragma unroll
-    for (int i = 0; i < kNF; ++i) feat_out[j * kNF + i] = z[i];
-  score[j] = w != nullptr ? mlp_forward(s, z) : 0.f;
+    for (int i = 0; i < kNF; ++i) {
+      if (jg < m) feat_out[jg * kNF + i] = zg[i];
+      if (jg8 < m) feat_out[jg8 * kNF + i] = zg8[i];
+    }
+  }
+  float sg = 0.f, sg8 = 0.f;
+  if (w != nullptr) mlp_forward_warp(s, zg, zg8, sg, sg8);
+  if (t == 0) {
+    if (jg < m) score[jg] = sg;
+    if (jg8 < m) score[jg8] = sg8;
+  }
 }
 
 // ---- per slot: proposal, Gumbel keys, top tau (one block per slot) ----
@@ -410,7 +483,7 @@ cudaError_t launch_lp_plans(cudaStream_t st, const Ctrl* ctrl, int force, int ns
   if (smem > 200 * 1024 || tau > m) return cudaErrorInvalidValue;
   if (!fixed_score) {  // the network's scores of this chunk's features
     k_lp_stats<<<1, 1024, 0, st>>>(ctrl, k0_arg, r, m, last, dyn, stats);
-    k_lp_score<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(w, zstat, stats, dyn, m, score,
+    k_lp_score<<<(unsigned)((m + kScoreRows - 1) / kScoreRows), 256, 0, st>>>(w, zstat, stats, dyn, m, score,
                                                             nullptr);
   }
   cudaError_t e = set_smem_max((const void*)k_lp_select, (size_t)((int)smem));
@@ -427,7 +500,7 @@ cudaError_t launch_lp_features(cudaStream_t st, const Ctrl* ctrl, int64_t k0, co
                                float* dyn, double* stats, const double* r, const int32_t* last,
                                int64_t m, float* score, float* feat_out) {
   k_lp_stats<<<1, 1024, 0, st>>>(ctrl, k0, r, m, last, dyn, stats);
-  k_lp_score<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(nullptr, zstat, stats, dyn, m, score,
+  k_lp_score<<<(unsigned)((m + kScoreRows - 1) / kScoreRows), 256, 0, st>>>(nullptr, zstat, stats, dyn, m, score,
                                                           feat_out);
   return cudaGetLastError();
 }
@@ -439,114 +512,221 @@ __global__ void __launch_bounds__(256) k_mlp_forward(const uint16_t* __restrict_
   __shared__ __align__(16) MlpSmem s;
   load_weights_bf16(s, w);
   __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  float z[kNF];
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int64_t i0 = (int64_t)blockIdx.x * kScoreRows + (threadIdx.x >> 5) * 16;
+  if (i0 >= n) return;
+  const int64_t ig = i0 + g, ig8 = ig + 8;
+  float zg[kNF], zg8[kNF];
 #pragma unroll
-  for (int f = 0; f < kNF; ++f) z[f] = Z[i * kNF + f];
-  s_out[i] = mlp_forward(s, z);
+  for (int f = 0; f < kNF; ++f) {
+    zg[f] = ig < n ? Z[ig * kNF + f] : 0.f;
+    zg8[f] = ig8 < n ? Z[ig8 * kNF + f] : 0.f;
+  }
+  float sg, sg8;
+  mlp_forward_warp(s, zg, zg8, sg, sg8);
+  if (t == 0) {
+    if (ig < n) s_out[ig] = sg;
+    if (ig8 < n) s_out[ig8] = sg8;
+  }
 }
 
 cudaError_t launch_mlp_forward(cudaStream_t st, const uint16_t* w, const float* Z, int64_t n,
                                float* s_out) {
   if (n <= 0) return cudaSuccess;
-  k_mlp_forward<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w, Z, n, s_out);
+  k_mlp_forward<<<(unsigned)((n + kScoreRows - 1) / kScoreRows), 256, 0, st>>>(w, Z, n, s_out);
   return cudaGetLastError();
 }
 
 // ---- training: gradient of the mean loss (s - y)^2 / 2 over n rows ----
-// A block takes kGB rows (a thread per row): the forward with bfloat16-rounded
-// weights and activations (kept in shared memory column-major by row), the
-// backward in FP32 (the roundings pass gradients straight through), then the
-// block's weight gradients as sums over its rows in row order; per-block sums go
-// to part (blocks x kMlpParams) and are added in block order.
+// A block takes kGB rows, a warp tile of 16 rows per warp. The forward as in the
+// scores (layer 2 on the tensor cores: bfloat16 operands, FP32 accumulation;
+// bfloat16-rounded activations); the backward: dL/da2 = ds w3 [a2 > 0], rounded to
+// bfloat16 for the two 64 x 64 contractions, dL/dh1 = dL/da2 W2 (the C fragments of
+// dL/da2 are the A fragments of that product) and the block's W2 gradient
+// sum_r dL/da2[r, o] h1[r, i] (tensor cores over the rows, from transposed bfloat16
+// copies in shared memory); the other parameters' gradients as FP32 sums over the
+// block's rows in row order. Per-block sums go to part (blocks x kMlpParams) and are
+// added in block order. The roundings pass gradients straight through.
 namespace {
-constexpr int kGB = 128;
+constexpr int kGB = 128;  // rows per block
+constexpr int kGT = 256;  // threads per block: 8 warp tiles of 16 rows
 
 struct GradSmem {
-  float w[kMlpParams + 3];
+  float w[kMlpParams + 3];              // bfloat16-rounded weights as FP32
+  __align__(16) uint16_t w2h[kH * kH];  // W2[o][i] as bfloat16 bits
+  __align__(16) uint16_t w2th[kH * kH]; // W2^T[i][o]
+  __align__(16) uint16_t d2t[kH][kGB];  // dL/da2 transposed [o][r], bfloat16
+  __align__(16) uint16_t h1t[kH][kGB];  // h1 transposed [i][r], bfloat16
   float z[kNF][kGB];
-  float h1[kH][kGB];
   float h2[kH][kGB];
-  float d2[kH][kGB];   // dL / da2
-  float d1[kH][kGB];   // dL / da1
+  float d2[kH][kGB];   // dL/da2 in FP32 (b2)
+  float d1[kH][kGB];   // dL/da1 (W1, b1)
   float ds[kGB];
   float loss[kGB];
 };
+
+__device__ __forceinline__ float bf_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
 }  // namespace
 
-__global__ void __launch_bounds__(kGB, 1) k_mlp_grad(const float* __restrict__ theta,
+__global__ void __launch_bounds__(kGT, 1) k_mlp_grad(const float* __restrict__ theta,
                                                      const float* __restrict__ Z,
                                                      const float* __restrict__ y, int64_t n,
                                                      float* __restrict__ part,
                                                      float* __restrict__ loss_part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   GradSmem& s = *reinterpret_cast<GradSmem*>(smem_raw);
-  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) s.w[i] = round_bf16(theta[i]);
-  const int tid = threadIdx.x;
-  const int64_t row = (int64_t)blockIdx.x * kGB + tid;
-  const bool live = row < n;
-  float z[kNF];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, g = lane >> 2, t = lane & 3;
+  for (int i = tid; i < kMlpParams; i += kGT) s.w[i] = round_bf16(theta[i]);
+  for (int i = tid; i < kH * kH; i += kGT) {
+    const uint16_t h = to_bf16(theta[kOffW2 + i]);
+    s.w2h[i] = h;
+    s.w2th[(i % kH) * kH + i / kH] = h;
+  }
+  const int64_t base = (int64_t)blockIdx.x * kGB;
+  const int rg = wid * 16 + g, rg8 = rg + 8;  // block-local rows of this lane
+  const bool live_g = base + rg < n, live_g8 = base + rg8 < n;
+  float zg[kNF], zg8[kNF];
 #pragma unroll
   for (int f = 0; f < kNF; ++f) {
-    z[f] = live ? Z[row * kNF + f] : 0.f;
-    s.z[f][tid] = z[f];
-  }
-  __syncthreads();
-  // forward
-  float h1[kH];
-#pragma unroll
-  for (int o = 0; o < kH; ++o) {
-    float a = s.w[kOffB1 + o];
-#pragma unroll
-    for (int i = 0; i < kNF; ++i) a = fmaf(s.w[o * kNF + i], z[i], a);
-    h1[o] = round_bf16(fmaxf(a, 0.f));
-    s.h1[o][tid] = h1[o];
-  }
-  float out = s.w[kOffB3];
-  for (int o = 0; o < kH; ++o) {
-    const float4* w2 = reinterpret_cast<const float4*>(s.w + kOffW2 + o * kH);
-    float a = s.w[kOffB2 + o];
-#pragma unroll
-    for (int i4 = 0; i4 < kH / 4; ++i4) {
-      const float4 w = w2[i4];
-      a = fmaf(w.x, h1[4 * i4], a);
-      a = fmaf(w.y, h1[4 * i4 + 1], a);
-      a = fmaf(w.z, h1[4 * i4 + 2], a);
-      a = fmaf(w.w, h1[4 * i4 + 3], a);
-    }
-    const float h2 = round_bf16(fmaxf(a, 0.f));
-    s.h2[o][tid] = h2;
-    s.d2[o][tid] = a > 0.f ? 1.f : 0.f;  // relu mask for now
-    out = fmaf(s.w[kOffW3 + o], h2, out);
-  }
-  const float err = live ? out - y[row] : 0.f;
-  const float ds = err / (float)n;
-  s.ds[tid] = ds;
-  s.loss[tid] = 0.5f * err * err;
-  // backward through the rows of this thread
-  float g1[kH];
-#pragma unroll
-  for (int i = 0; i < kH; ++i) g1[i] = 0.f;
-  for (int o = 0; o < kH; ++o) {
-    const float d = ds * s.w[kOffW3 + o] * s.d2[o][tid];
-    s.d2[o][tid] = d;
-    const float4* w2 = reinterpret_cast<const float4*>(s.w + kOffW2 + o * kH);
-#pragma unroll
-    for (int i4 = 0; i4 < kH / 4; ++i4) {
-      const float4 w = w2[i4];
-      g1[4 * i4] = fmaf(d, w.x, g1[4 * i4]);
-      g1[4 * i4 + 1] = fmaf(d, w.y, g1[4 * i4 + 1]);
-      g1[4 * i4 + 2] = fmaf(d, w.z, g1[4 * i4 + 2]);
-      g1[4 * i4 + 3] = fmaf(d, w.w, g1[4 * i4 + 3]);
+    zg[f] = live_g ? Z[(base + rg) * kNF + f] : 0.f;
+    zg8[f] = live_g8 ? Z[(base + rg8) * kNF + f] : 0.f;
+    if (t == 0) {
+      s.z[f][rg] = zg[f];
+      s.z[f][rg8] = zg8[f];
     }
   }
-#pragma unroll
-  for (int i = 0; i < kH; ++i) s.d1[i][tid] = h1[i] > 0.f ? g1[i] : 0.f;
   __syncthreads();
-  // the block's parameter gradients (sums over its rows in row order)
+  // forward: layer 1 as A fragments (also kept transposed for the W2 gradient)
+  uint32_t afr[4][4];
+  mlp_layer1_frag(s.w, zg, zg8, afr);
+#pragma unroll
+  for (int kc = 0; kc < 4; ++kc)
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int o0 = 16 * kc + 8 * half + 2 * t;
+      const uint32_t a = afr[kc][2 * half], b = afr[kc][2 * half + 1];
+      s.h1t[o0][rg] = (uint16_t)(a & 0xFFFFu);
+      s.h1t[o0 + 1][rg] = (uint16_t)(a >> 16);
+      s.h1t[o0][rg8] = (uint16_t)(b & 0xFFFFu);
+      s.h1t[o0 + 1][rg8] = (uint16_t)(b >> 16);
+    }
+  // layer 2 on the tensor cores
+  float c2[8][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int o0 = 8 * nt + 2 * t;
+    c2[nt][0] = s.w[kOffB2 + o0];
+    c2[nt][1] = s.w[kOffB2 + o0 + 1];
+    c2[nt][2] = c2[nt][0];
+    c2[nt][3] = c2[nt][1];
+    const uint16_t* wrow = s.w2h + (8 * nt + g) * kH;
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      const uint32_t b[2] = {ld_b32(wrow + 16 * kc + 2 * t), ld_b32(wrow + 16 * kc + 2 * t + 8)};
+      mma_bf16(c2[nt], afr[kc], b);
+    }
+  }
+  // output layer, loss, ds
+  float og = 0.f, og8 = 0.f;
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int o0 = 8 * nt + 2 * t;
+    const float h[4] = {round_bf16(fmaxf(c2[nt][0], 0.f)), round_bf16(fmaxf(c2[nt][1], 0.f)),
+                        round_bf16(fmaxf(c2[nt][2], 0.f)), round_bf16(fmaxf(c2[nt][3], 0.f))};
+    s.h2[o0][rg] = h[0];
+    s.h2[o0 + 1][rg] = h[1];
+    s.h2[o0][rg8] = h[2];
+    s.h2[o0 + 1][rg8] = h[3];
+    og = fmaf(s.w[kOffW3 + o0], h[0], fmaf(s.w[kOffW3 + o0 + 1], h[1], og));
+    og8 = fmaf(s.w[kOffW3 + o0], h[2], fmaf(s.w[kOffW3 + o0 + 1], h[3], og8));
+  }
+  og += __shfl_xor_sync(0xffffffffu, og, 1);
+  og += __shfl_xor_sync(0xffffffffu, og, 2);
+  og8 += __shfl_xor_sync(0xffffffffu, og8, 1);
+  og8 += __shfl_xor_sync(0xffffffffu, og8, 2);
+  const float err_g = live_g ? og + s.w[kOffB3] - y[base + rg] : 0.f;
+  const float err_g8 = live_g8 ? og8 + s.w[kOffB3] - y[base + rg8] : 0.f;
+  const float ds_g = err_g / (float)n, ds_g8 = err_g8 / (float)n;
+  if (t == 0) {
+    s.ds[rg] = ds_g;
+    s.ds[rg8] = ds_g8;
+    s.loss[rg] = 0.5f * err_g * err_g;
+    s.loss[rg8] = 0.5f * err_g8 * err_g8;
+  }
+  // dL/da2 = ds w3 [a2 > 0]: FP32 for b2, bfloat16 for the products (A fragments)
+  uint32_t dA[4][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int o0 = 8 * nt + 2 * t;
+    const float w0 = s.w[kOffW3 + o0], w1 = s.w[kOffW3 + o0 + 1];
+    const float d[4] = {c2[nt][0] > 0.f ? ds_g * w0 : 0.f, c2[nt][1] > 0.f ? ds_g * w1 : 0.f,
+                        c2[nt][2] > 0.f ? ds_g8 * w0 : 0.f, c2[nt][3] > 0.f ? ds_g8 * w1 : 0.f};
+    s.d2[o0][rg] = d[0];
+    s.d2[o0 + 1][rg] = d[1];
+    s.d2[o0][rg8] = d[2];
+    s.d2[o0 + 1][rg8] = d[3];
+    const uint32_t pg = pack_bf16(d[0], d[1]), pg8 = pack_bf16(d[2], d[3]);
+    s.d2t[o0][rg] = (uint16_t)(pg & 0xFFFFu);
+    s.d2t[o0 + 1][rg] = (uint16_t)(pg >> 16);
+    s.d2t[o0][rg8] = (uint16_t)(pg8 & 0xFFFFu);
+    s.d2t[o0 + 1][rg8] = (uint16_t)(pg8 >> 16);
+    dA[nt >> 1][2 * (nt & 1)] = pg;
+    dA[nt >> 1][2 * (nt & 1) + 1] = pg8;
+  }
+  // dL/dh1 = dL/da2 W2 (tensor cores), dL/da1 = dL/dh1 [h1 > 0]
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const uint16_t* wrow = s.w2th + (8 * nt + g) * kH;
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      const uint32_t b[2] = {ld_b32(wrow + 16 * kc + 2 * t), ld_b32(wrow + 16 * kc + 2 * t + 8)};
+      mma_bf16(acc, dA[kc], b);
+    }
+    const int i0 = 8 * nt + 2 * t;
+    const uint32_t hg = afr[nt >> 1][2 * (nt & 1)], hg8 = afr[nt >> 1][2 * (nt & 1) + 1];
+    s.d1[i0][rg] = bf_lo(hg) > 0.f ? acc[0] : 0.f;
+    s.d1[i0 + 1][rg] = bf_hi(hg) > 0.f ? acc[1] : 0.f;
+    s.d1[i0][rg8] = bf_lo(hg8) > 0.f ? acc[2] : 0.f;
+    s.d1[i0 + 1][rg8] = bf_hi(hg8) > 0.f ? acc[3] : 0.f;
+  }
+  __syncthreads();
   float* pb = part + (int64_t)blockIdx.x * kMlpParams;
-  for (int e = tid; e < kMlpParams; e += blockDim.x) {
+  // W2 gradient: sum over the block's rows of dL/da2[r, o] h1[r, i] on the tensor cores;
+  // warp w: o tile 16 (w / 2) .. + 15, i tiles 4 (w % 2) .. + 3 of 8
+  {
+    const int mt = wid >> 1, nt0 = (wid & 1) * 4;
+    float acc[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[q][e] = 0.f;
+#pragma unroll
+    for (int kc = 0; kc < kGB / 16; ++kc) {
+      const int r0 = 16 * kc + 2 * t;
+      const uint32_t a[4] = {ld_b32(&s.d2t[16 * mt + g][r0]), ld_b32(&s.d2t[16 * mt + g + 8][r0]),
+                             ld_b32(&s.d2t[16 * mt + g][r0 + 8]),
+                             ld_b32(&s.d2t[16 * mt + g + 8][r0 + 8])};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int ii = 8 * (nt0 + q) + g;
+        const uint32_t b[2] = {ld_b32(&s.h1t[ii][r0]), ld_b32(&s.h1t[ii][r0 + 8])};
+        mma_bf16(acc[q], a, b);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i0 = 8 * (nt0 + q) + 2 * t, o = 16 * mt + g;
+      pb[kOffW2 + o * kH + i0] = acc[q][0];
+      pb[kOffW2 + o * kH + i0 + 1] = acc[q][1];
+      pb[kOffW2 + (o + 8) * kH + i0] = acc[q][2];
+      pb[kOffW2 + (o + 8) * kH + i0 + 1] = acc[q][3];
+    }
+  }
+  // the other parameters' gradients (sums over the block's rows in row order)
+  for (int e = tid; e < kMlpParams; e += kGT) {
+    if (e >= kOffW2 && e < kOffB2) continue;  // W2: above
     float acc = 0.f;
     if (e < kOffB1) {                      // W1[o][i]
       const int o = e / kNF, i = e % kNF;
@@ -554,9 +734,6 @@ __global__ void __launch_bounds__(kGB, 1) k_mlp_grad(const float* __restrict__ t
     } else if (e < kOffW2) {               // b1[o]
       const int o = e - kOffB1;
       for (int r = 0; r < kGB; ++r) acc += s.d1[o][r];
-    } else if (e < kOffB2) {               // W2[o][i]
-      const int o = (e - kOffW2) / kH, i = (e - kOffW2) % kH;
-      for (int r = 0; r < kGB; ++r) acc = fmaf(s.d2[o][r], s.h1[i][r], acc);
     } else if (e < kOffW3) {               // b2[o]
       const int o = e - kOffB2;
       for (int r = 0; r < kGB; ++r) acc += s.d2[o][r];
@@ -600,7 +777,7 @@ cudaError_t launch_mlp_grad(cudaStream_t st, const float* theta, const float* Z,
   const size_t smem = sizeof(GradSmem);
   cudaError_t e = set_smem_max((const void*)k_mlp_grad, (size_t)((int)smem));
   if (e != cudaSuccess) return e;
-  k_mlp_grad<<<nblk, kGB, smem, st>>>(theta, Z, y, n, part, loss_part);
+  k_mlp_grad<<<nblk, kGT, smem, st>>>(theta, Z, y, n, part, loss_part);
   k_mlp_sum<<<(kMlpParams + 255) / 256, 256, 0, st>>>(part, loss_part, nblk, n, grad, loss);
   return cudaGetLastError();
 }

@@ -241,6 +241,115 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
                  : "memory");
 }
 
+// C = P Q^T for K-major P (Mr x K, map ta) and Q (N x K, map tb), FP32 out, on the same
+// pipeline as k_gram_tc (128 x 256 tiles, one CTA each, 4 stages of TMA loads, TF32
+// MMAs into tensor memory). Used for S^T A of the Gaussian sketch: P = the chunk's S^T
+// blocks stacked (rows slot * tau + j), Q = A (symmetric, so A^T = A). Row blocks of
+// slots past the active ones (convergence forecast, iteration cap) are skipped.
+__global__ void __launch_bounds__(128, 1) k_gemm_tc_nt(const __grid_constant__ CUtensorMap ta,
+                                                      const __grid_constant__ CUtensorMap tb,
+                                                      int64_t Mr, int64_t N, int64_t nk,
+                                                      float* __restrict__ C, int64_t ldc,
+                                                      const Ctrl* __restrict__ ctrl, int force,
+                                                      int nslots, int64_t rows_per_slot,
+                                                      int32_t* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const int64_t rows_live = (ctrl != nullptr || force)
+                                ? active_slots(ctrl, force, nslots) * rows_per_slot
+                                : Mr;
+  const int64_t rmax = rows_live < Mr ? rows_live : Mr;
+  const int row0 = (int)((int64_t)blockIdx.y * kBM), col0 = (int)((int64_t)blockIdx.x * kBN);
+  if (row0 >= rmax) return;  // uniform over the CTA
+  if (tid == 0) {
+    for (int q = 0; q < kStages; ++q) {
+      mbar_init(&full_bar[q], 1);
+      mbar_init(&empty_bar[q], 1);
+    }
+    mbar_init(&done_bar, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (wid == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  if (wid == 0 && lane == 0) {  // producer
+    for (int64_t kb = 0; kb < nk; ++kb) {
+      const int q = (int)(kb % kStages);
+      const uint32_t ph = (uint32_t)((kb / kStages) & 1);
+      if (!mbar_wait(&empty_bar[q], ph ^ 1)) { s_abort = 1; atomicExch(err, 1); break; }
+      if (*(volatile int*)&s_abort) break;
+      unsigned char* stg = base + q * kStageBytes;
+      mbar_arrive_expect_tx(&full_bar[q], kStageBytes);
+      const int kx = (int)(kb * kBK);
+      tma_load_2d(stg, &ta, &full_bar[q], kx, row0);
+      tma_load_2d(stg + kABytes, &tb, &full_bar[q], kx, col0);
+      tma_load_2d(stg + kABytes + kBHalfBytes, &tb, &full_bar[q], kx, col0 + kBN / 2);
+    }
+  } else if (wid == 1 && lane == 0) {  // MMA issuer
+    for (int64_t kb = 0; kb < nk; ++kb) {
+      const int q = (int)(kb % kStages);
+      const uint32_t ph = (uint32_t)((kb / kStages) & 1);
+      if (!mbar_wait(&full_bar[q], ph)) { s_abort = 1; atomicExch(err, 1); break; }
+      if (*(volatile int*)&s_abort) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(base + q * kStageBytes);
+      const uint32_t sb = sa + kABytes;
+#pragma unroll
+      for (int ks = 0; ks < kBK / 8; ++ks)
+        mma_tf32(tmem, umma_desc_sw128(sa + ks * 32), umma_desc_sw128(sb + ks * 32),
+                 (kb > 0 || ks > 0) ? 1u : 0u);
+      mma_commit(&empty_bar[q]);
+    }
+    mma_commit(&done_bar);
+  }
+  __syncwarp();
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0));
+  if (!ok && lane == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok && !*(volatile int*)&s_abort) {
+    const int64_t r = row0 + wid * 32 + lane;
+    for (int c0 = 0; c0 < kBN; c0 += 16) {
+      if (col0 + c0 >= N) break;  // uniform
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(wid * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+          "%11, %12, %13, %14, %15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (r < rmax) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int64_t cidx = col0 + c0 + q;
+          if (cidx < N) C[r * ldc + cidx] = __uint_as_float(v[q]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (wid == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+}
+
 // Xt[i * ldk + k] = X[k * d + i] (zero for k >= n): 32 x 32 tiles through shared memory;
 // with Xcopy != nullptr the tile is also stored to Xcopy (same layout as X), so that a
 // copy of X and its transpose come from one read of X
@@ -377,6 +486,41 @@ cudaError_t launch_rbf_tc(cudaStream_t st, const float* P, int64_t n, int64_t d,
   const float scale = (float)(1.0 / (2.0 * sigma * sigma));
   return cudaLaunchKernelEx(&cfg, k_gram_tc, map, n, (int64_t)0, ldk / kBK, 0.0, 2, K, ldK, err,
                             (const float*)sqn, scale);
+}
+
+// S^T A of every slot of a chunk for the Gaussian sketch on the tensor cores:
+// SA[s tau + j, c] = sum_i ST[s tau + j, i] A[c, i] (A symmetric). ST and SA hold the
+// slots' tau x ld blocks back to back (row stride ld, zero beyond column m); lda and ld
+// multiples of 4 (16-byte row strides for the tensor maps)
+cudaError_t launch_gauss_sa_tc(cudaStream_t st, const Ctrl* ctrl, int force, int nslots,
+                               const float* ST, int64_t ld, int64_t m, int64_t tau,
+                               const float* A, int64_t lda, float* SA, int32_t* err) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  if (ld % 32 != 0 || lda % 4 != 0) return cudaErrorInvalidValue;
+  const int64_t rows = (int64_t)nslots * tau;
+  CUtensorMap ma, mb;
+  const cuuint64_t da[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+  const cuuint64_t sta[1] = {(cuuint64_t)ld * 4};
+  const cuuint64_t db[2] = {(cuuint64_t)ld, (cuuint64_t)m};
+  const cuuint64_t stb[1] = {(cuuint64_t)lda * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(&ma, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ST), da, sta, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  r = enc(&mb, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), db, stb, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)kStages * kStageBytes + 1024;
+  cudaError_t e = set_smem_max((const void*)k_gemm_tc_nt, smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((unsigned)((m + kBN - 1) / kBN), (unsigned)((rows + kBM - 1) / kBM));
+  k_gemm_tc_nt<<<grid, 128, smem, st>>>(ma, mb, rows, m, ld / kBK, SA, ld, ctrl, force, nslots,
+                                         tau, err);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gram_tc(cudaStream_t st, const float* X, int64_t n, int64_t d, double lambda,

@@ -536,3 +536,25 @@ def test_mixed_chunk_forecast_reaches_tolerance(rs, refresh):
     assert conv and hist[iters] <= 1e-7
     assert oracle.true_residual(Xd, y, lam, w) <= 1e-7
     assert rel(w, oracle.direct_solution(Xd, y, lam)) <= 1e-4
+
+
+def test_gaussian_sketched_system_on_tensor_cores(rs):
+    """Mixed Gaussian sketch: S^T A of the chunk's slots is one TF32 tensor-core product
+    (and A the TF32 Gram), then M = S^T A S. Against S^T (X^T X + lambda I) S in FP64
+    from the library's own S: each TF32 product perturbs a term by at most 2^-10 of
+    its magnitude, so |dM| <= 4 * 2^-10 |S|^T (|X|^T |X| + lambda I) |S| (two
+    products, FP32 sums), checked with that bound."""
+    n, m, tau, lam = 700, 300, 24, 0.5
+    X, y, _ = gaussian_problem(n, m, 74)
+    X32 = X.astype(np.float32)
+    with rs.Solver(X32, y, lam, sketch="gaussian", tau=tau, seed=3, precision="mixed",
+                   chol_fp64=False) as s:
+        S = s.dump_gaussian(0)
+        M, rS, delta = s.probe_step()
+    Xf = X32.astype(np.float64)
+    A = Xf.T @ Xf + lam * np.eye(m)
+    M_ref = S.T @ A @ S
+    Aabs = np.abs(Xf).T @ np.abs(Xf) + lam * np.eye(m)
+    bound = 4 * 2.0 ** -10 * (np.abs(S).T @ Aabs @ np.abs(S))
+    assert np.all(np.abs(M - M_ref) <= bound)
+    assert np.abs(M - M_ref).max() > 0  # the tensor-core path ran (not an FP64 product)
