@@ -18,14 +18,18 @@
 // and issued after the CTA has published its partials, so that they overlap the
 // all-reduce.
 //
-// All-reduce, deterministic: (1) each CTA stores its tau + 1 partials to global
-// memory as self-validating words (payload and exchange tag in one 8-byte word);
-// (2) CTA rank r of a cluster reads the entries [r E, (r + 1) E) of every CTA,
-// re-reading the words whose tag is not current yet, and sums them over the CTAs in
-// a fixed order; (3) it stores those sums into the shared memory of every CTA of
-// its cluster with st.async, whose bytes complete on the destination's mbarrier.
-// Every wait is bounded (global timer); a CTA that gives up raises the abort word,
-// which ends the others' waits.
+// All-reduce, deterministic, in two stages. CTA rank r of a cluster owns the entries
+// [r E, (r + 1) E) of the tau + 1. (1) Inside the cluster: every CTA stores its
+// partials of those entries into rank r's shared memory with st.async (the bytes
+// complete on r's gather mbarrier), and r adds them over the 16 CTAs in rank order.
+// (2) Across clusters: r publishes its cluster sums to global memory as
+// self-validating words (payload and exchange tag in one 8-byte word), reads the
+// sums of every cluster, re-reading the words whose tag is not current yet, and adds
+// them in cluster order (one cluster: no global memory at all). (3) r stores the
+// totals into the shared memory of every CTA of its cluster with st.async. Each
+// global word is thus read by one CTA per cluster instead of every CTA polling the
+// partials of every other one. Every wait is bounded (global timer); a CTA that
+// gives up raises the abort word, which ends the others' waits.
 //
 // Precision of the mixed form (T = TF = float): FP64 instructions take 64 cycles
 // (add, FMA) to about 100 (conversions) on this GPU, and every one of them on the
@@ -45,16 +49,18 @@ namespace {
 constexpr int kWThreads = 256;
 constexpr int kWWarps = kWThreads / 32;
 constexpr int kIssueWarp = kWWarps - 1;        // issues the bulk copies
-constexpr int kSumLoads = 20;                   // partials in flight per thread
 constexpr int kRowsPerLane = 2;                 // rows of a lane in the A S delta product
 // waits at the end of a launch for copies already in flight into this CTA's shared
 // memory: they land within microseconds, so this bound is generous and independent
 // of the caller's limit on the other waits
 constexpr uint64_t kDrainNs = 2000000000ull;
 
+// clusters of one launch at most (the stage-2 sums of the all-reduce)
+constexpr int kMaxClusters = 16;
+
 struct WideLayout {
-  int64_t qs, E, G;
-  size_t sa, pb, iv, mine, tot, dT, red, st, coef, prow, pinv, hn2, bars, gb, sum, total;
+  int64_t qs, E;
+  size_t sa, pb, iv, mine, tot, dT, red, gat, st, coef, prow, pinv, hn2, bars, gb, sum, total;
 };
 
 __host__ __device__ inline size_t wl_take(size_t& o, size_t bytes) {
@@ -69,7 +75,6 @@ __host__ __device__ inline WideLayout wide_layout(int64_t q, int64_t tau, int64_
   WideLayout L;
   L.qs = (q + 3) / 4 * 4;
   L.E = (tau + 1 + kWideCluster - 1) / kWideCluster;  // all-reduce entries per cluster rank
-  L.G = kWThreads / L.E > 0 ? kWThreads / L.E : 1;     // thread groups of the sums
   size_t o = 0;
   L.sa = wl_take(o, (size_t)nsab * tau * L.qs * se);  // S^T A block, 1 or 2 buffers
   L.pb = wl_take(o, (size_t)L.qs * pld * sf);       // rows of P for the own rows
@@ -77,8 +82,9 @@ __host__ __device__ inline WideLayout wide_layout(int64_t q, int64_t tau, int64_
   L.mine = wl_take(o, (size_t)tau * 8);             // own partials of delta
   L.tot = wl_take(o, (size_t)(tau + 1) * 8);        // all-reduced totals
   L.dT = wl_take(o, (size_t)tau * se);              // delta in the product type
-  const int64_t rw = kWWarps * L.qs > L.G * L.E ? kWWarps * L.qs : L.G * L.E;
-  L.red = wl_take(o, (size_t)rw * 8);               // cross-warp / cross-group partial sums
+  const int64_t rw = kWWarps * L.qs > kMaxClusters * L.E ? kWWarps * L.qs : kMaxClusters * L.E;
+  L.red = wl_take(o, (size_t)rw * 8);               // cross-warp / cross-cluster partial sums
+  L.gat = wl_take(o, (size_t)2 * kWideCluster * L.E * 8);  // cluster's partials of own entries
   L.st = wl_take(o, (size_t)4 * L.qs * 8);          // r, r_prev, w, w_prev
   L.coef = wl_take(o, (size_t)L.qs * 8);            // sigma_i r_i of the staged rows
   L.prow = wl_take(o, (size_t)L.qs * 4);            // staged row -> own row | sign
@@ -107,32 +113,30 @@ __device__ bool wait_bar(uint64_t* bar, uint32_t parity, const int32_t* abort_wo
 }
 
 struct Xch {
-  uint64_t* part;   // 2 (parity) x nblk x nw words
+  uint64_t* part;   // 2 (parity) x nclu x 2 ne words: the clusters' sums
   int32_t* abort_word;
   uint64_t wait_ns;  // bound of every wait
-  int nblk, cta;
+  int nclu, clu;     // clusters of the launch, this CTA's cluster
   uint32_t crank;
-  int64_t tau, ne, E, G, nw;
+  int64_t tau, ne, E;
   void* mine;       // PT[tau]: own partials of delta
   const void* mine_nrm;  // own partial of ||r||^2 (float for PT = float, else double)
   double* tot;      // ne all-reduced totals (delta, then ||r||^2)
-  void* red;        // per-group sums of the reducer
-  uint64_t* xbar;
+  void* red;        // per-cluster sums of the own entries
+  void* gat;        // PT[2][kWideCluster][E]: the cluster's partials of the own entries
+  uint64_t* xbar;   // the totals have arrived
+  uint64_t* gbar;   // the cluster's partials of the own entries have arrived
 };
 
-// The partials travel as self-validating words: a 32-bit payload and the exchange's
-// 32-bit tag in one 8-byte word (single-copy atomic), so a reader that sees the tag
-// has the payload and no separate flag, fence or release is needed. Tags increase
-// from exchange to exchange and from launch to launch and the buffer alternates by
-// parity, so a stale word never carries the current tag. Payloads: PT = float,
-// one word per delta entry and two for the norm (the value, then zero); PT =
-// double, two words (low and high halves) per entry.
+// The clusters' sums travel as self-validating words: a 32-bit payload and the
+// exchange's 32-bit tag in one 8-byte word (single-copy atomic), so a reader that
+// sees the tag has the payload and no separate flag, fence or release is needed.
+// Tags increase from exchange to exchange and from launch to launch and the buffer
+// alternates by parity, so a stale word never carries the current tag. Two words
+// per entry: PT = float, the sum as a float pair (hi, lo); PT = double, the low and
+// high halves of the sum.
 __device__ __forceinline__ uint64_t ll_word(uint32_t payload, uint32_t tag) {
   return (uint64_t)payload | ((uint64_t)tag << 32);
-}
-template <typename PT>
-__host__ __device__ constexpr int64_t ll_words(int64_t tau) {
-  return sizeof(PT) == 4 ? tau + 2 : 2 * tau + 2;
 }
 
 // error-free sum of two floats (Knuth): s + e == a + b exactly
@@ -142,131 +146,146 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - t)) + (b - t);
 }
 
+// entries of the all-reduce owned by cluster rank crank
+__device__ __forceinline__ int64_t xch_own(int64_t ne, int64_t E, uint32_t crank) {
+  const int64_t e0 = (int64_t)crank * E;
+  return e0 < ne ? (ne - e0 < E ? ne - e0 : E) : 0;
+}
+
+// arm the gather mbarrier for the next exchange: the bytes of the own entries from
+// every CTA of the cluster. It is armed before the launch's first exchange and right
+// after each wait on it, so always before a peer can store into it: a peer sends
+// exchange n + 1 only once it has the totals of exchange n, which include this
+// CTA's, stored after this CTA's wait.
+template <typename PT>
+__device__ __forceinline__ void arm_gather(uint64_t* gbar, int64_t ne, int64_t E, uint32_t crank) {
+  ptx::mbar_arrive_expect_tx(gbar, (uint32_t)(xch_own(ne, E, crank) * kWideCluster * sizeof(PT)));
+}
+
 // All-reduce of the partials over every CTA into `tot`, first half: arm the own
-// mbarrier for the ne * 8 bytes the cluster will store, then publish the partials.
-// `n` counts this launch's exchanges.
+// mbarrier of the totals, then store every partial into the gather buffer of the
+// cluster rank that owns its entry. `n` counts this launch's exchanges.
 template <typename PT>
 __device__ void xch_begin(const Xch& x, uint32_t tag, uint32_t n) {
   const int tid = threadIdx.x;
-  uint64_t* pb = x.part + ((size_t)(n & 1) * x.nblk + x.cta) * x.nw;
   __syncthreads();  // the partials written; `tot` of the previous exchange read
   if (tid == 0) ptx::mbar_arrive_expect_tx(x.xbar, (uint32_t)(x.ne * 8));
   const PT* mine = static_cast<const PT*>(x.mine);
-  if constexpr (sizeof(PT) == 4) {
-    for (int64_t e = tid; e < x.tau; e += kWThreads)
-      ptx::st_relaxed_u64(pb + e, ll_word(__float_as_uint(mine[e]), tag));
-    if (tid == 0) {
-      const float v = *static_cast<const float*>(x.mine_nrm);
-      ptx::st_relaxed_u64(pb + x.tau, ll_word(__float_as_uint(v), tag));
-      ptx::st_relaxed_u64(pb + x.tau + 1, ll_word(0u, tag));
-    }
-  } else {
-    for (int64_t e = tid; e < x.ne; e += kWThreads) {
-      const uint64_t b = (uint64_t)__double_as_longlong(
-          e < x.tau ? (double)mine[e] : *static_cast<const double*>(x.mine_nrm));
-      ptx::st_relaxed_u64(pb + 2 * e, ll_word((uint32_t)b, tag));
-      ptx::st_relaxed_u64(pb + 2 * e + 1, ll_word((uint32_t)(b >> 32), tag));
-    }
+  PT* gat = static_cast<PT*>(x.gat) + (size_t)(n & 1) * kWideCluster * x.E + x.crank * x.E;
+  for (int64_t e = tid; e < x.ne; e += kWThreads) {
+    const PT v = e < x.tau ? mine[e] : *static_cast<const PT*>(x.mine_nrm);
+    const uint32_t rk = (uint32_t)(e / x.E);
+    const uint32_t dst = ptx::map_rank(gat + (e - (int64_t)rk * x.E), rk);
+    if constexpr (sizeof(PT) == 4) ptx::st_async_b32(dst, __float_as_uint(v), ptx::map_rank(x.gbar, rk));
+    else ptx::st_async_f64(dst, v, ptx::map_rank(x.gbar, rk));
   }
 }
 
-// word(s) of entry e in a CTA's block
-template <typename PT>
-__device__ __forceinline__ void ll_pos(int64_t e, int64_t tau, int64_t& w0, int& nwords) {
-  if constexpr (sizeof(PT) == 4) {
-    w0 = e;
-    nwords = (e < tau) ? 1 : 2;
-  } else {
-    w0 = 2 * e;
-    nwords = 2;
-  }
-}
-
-// second half: gather the own entries of every CTA (re-reading words whose tag is
-// not current yet), sum them in a fixed order (float pairs for PT = float, so the
-// sum is as accurate as in FP64 without FP64 arithmetic), scatter the sums to the
-// cluster (PT = float: each total as a normalised float pair (hi, lo) in the 8
-// bytes of its `tot` entry) and wait for the cluster's sums; false on abort or
-// timeout
+// second half: wait for the cluster's partials of the own entries and add them in
+// rank order; with more than one cluster, publish those sums, gather every
+// cluster's (re-reading words whose tag is not current yet) and add them in cluster
+// order (PT = float: float pairs throughout, so the sums are as accurate as in
+// FP64 without FP64 arithmetic); store the totals into the `tot` of every CTA of
+// the cluster (PT = float: a normalised float pair (hi, lo) in each 8-byte entry)
+// and wait for the cluster's totals; false on abort or timeout
 template <typename PT>
 __device__ bool xch_end(const Xch& x, uint32_t tag, uint32_t n) {
   constexpr bool F = sizeof(PT) == 4;
   const int tid = threadIdx.x;
-  const uint64_t* pb = x.part + (size_t)(n & 1) * x.nblk * x.nw;
-  // own entries [e0, e1): thread (g, el) adds CTAs g, g + G, ... in that order,
-  // then the G group sums are added in group order (fixed order, deterministic)
   const int64_t e0 = (int64_t)x.crank * x.E;
-  const int64_t e1 = (e0 + x.E < x.ne) ? e0 + x.E : x.ne;
-  int bad = 0;
-  for (int64_t idx = tid; idx < x.G * x.E; idx += kWThreads) {
-    const int64_t g = idx / x.E, el = idx - g * x.E, e = e0 + el;
-    float S = 0.f, C = 0.f;   // PT = float
-    double acc = 0.0;         // PT = double
-    if (e < e1) {
-      int64_t w0;
-      int nwd;
-      ll_pos<PT>(e, x.tau, w0, nwd);
-      for (int c0 = (int)g; c0 < x.nblk && !bad; c0 += (int)x.G * kSumLoads) {
-        uint64_t a[kSumLoads], b[kSumLoads];
-        // every pass re-reads, all at once, the words whose tag is not current yet;
-        // the first pass reads them all
-        uint32_t pend = 0;
-#pragma unroll
-        for (int u = 0; u < kSumLoads; ++u)
-          if (c0 + u * (int)x.G < x.nblk) pend |= 1u << u;
-        const uint64_t t0 = ptx::now_ns();
-        for (uint32_t pass = 0; pend != 0; ++pass) {
-#pragma unroll
-          for (int u = 0; u < kSumLoads; ++u) {
-            if (pend & (1u << u)) {
-              const uint64_t* w = pb + (size_t)(c0 + u * (int)x.G) * x.nw + w0;
-              a[u] = ptx::ld_relaxed_u64(w);
-              b[u] = nwd > 1 ? ptx::ld_relaxed_u64(w + 1) : ll_word(0u, tag);
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < kSumLoads; ++u)
-            if ((pend & (1u << u)) && (uint32_t)(a[u] >> 32) == tag && (uint32_t)(b[u] >> 32) == tag)
-              pend &= ~(1u << u);
-          if (pend != 0 && (pass & 15) == 15 &&
-              (ptx::ld_relaxed_s32(x.abort_word) != 0 || ptx::now_ns() - t0 > x.wait_ns)) {
-            bad = 1;
-            break;
-          }
-        }
-        if (bad) break;
-#pragma unroll
-        for (int u = 0; u < kSumLoads; ++u) {
-          if (c0 + u * (int)x.G >= x.nblk) continue;
-          if constexpr (F) {
-            float t, err;
-            two_sum(S, __uint_as_float((uint32_t)a[u]), t, err);
-            S = t;
-            C += err + __uint_as_float((uint32_t)b[u]);  // lo of the norm, else 0
-          } else {
-            acc += __longlong_as_double((long long)((a[u] & 0xFFFFFFFFull) | (b[u] << 32)));
-          }
-        }
-      }
-    }
-    if constexpr (F) static_cast<float2*>(x.red)[idx] = make_float2(S, C);
-    else static_cast<double*>(x.red)[idx] = acc;
-  }
-  if (__syncthreads_or(bad)) {
+  const int64_t nown = xch_own(x.ne, x.E, x.crank);
+  bool ok = wait_bar(x.gbar, n & 1, x.abort_word, x.wait_ns);
+  if (__syncthreads_or(!ok)) {
     if (tid == 0) atomicExch(x.abort_word, 1);
     return false;
   }
-  for (int64_t e = e0 + tid; e < e1; e += kWThreads) {
-    if constexpr (F) {
-      const float2* r = static_cast<const float2*>(x.red);
-      float S = 0.f, C = 0.f;
-      for (int64_t g = 0; g < x.G; ++g) {
-        const float2 p = r[g * x.E + (e - e0)];
+  // every thread has seen phase n complete: arm phase n + 1 (its buffer is the other)
+  if (tid == 0) arm_gather<PT>(x.gbar, x.ne, x.E, x.crank);
+  // stage 1: this cluster's sum of own entry el, in rank order
+  float S = 0.f, C = 0.f;  // PT = float
+  double acc = 0.0;        // PT = double
+  if (tid < nown) {
+    const PT* gat = static_cast<const PT*>(x.gat) + (size_t)(n & 1) * kWideCluster * x.E + tid;
+#pragma unroll
+    for (int c = 0; c < kWideCluster; ++c) {
+      if constexpr (F) {
         float t, err;
-        two_sum(S, p.x, t, err);
+        two_sum(S, gat[c * x.E], t, err);
         S = t;
-        C += err + p.y;
+        C += err;
+      } else {
+        acc += gat[c * x.E];
       }
+    }
+  }
+  if (x.nclu > 1) {
+    // stage 2: publish, then gather the clusters' sums (thread (g, el) reads
+    // cluster g's words of own entry el)
+    uint64_t* pb = x.part + (size_t)(n & 1) * x.nclu * 2 * x.ne;
+    if (tid < nown) {
+      uint32_t lo, hi;
+      if constexpr (F) {
+        lo = __float_as_uint(S);
+        hi = __float_as_uint(C);
+      } else {
+        const uint64_t b = (uint64_t)__double_as_longlong(acc);
+        lo = (uint32_t)b;
+        hi = (uint32_t)(b >> 32);
+      }
+      uint64_t* w = pb + ((size_t)x.clu * x.ne + e0 + tid) * 2;
+      ptx::st_relaxed_u64(w, ll_word(lo, tag));
+      ptx::st_relaxed_u64(w + 1, ll_word(hi, tag));
+    }
+    int bad = 0;
+    for (int64_t idx = tid; idx < (int64_t)x.nclu * x.E && !bad; idx += kWThreads) {
+      const int64_t g = idx / x.E, el = idx - g * x.E;
+      if (el >= nown) continue;
+      const uint64_t* w = pb + ((size_t)g * x.ne + e0 + el) * 2;
+      uint64_t a = 0, b = 0;
+      const uint64_t t0 = ptx::now_ns();
+      for (uint32_t pass = 0;; ++pass) {
+        a = ptx::ld_relaxed_u64(w);
+        b = ptx::ld_relaxed_u64(w + 1);
+        if ((uint32_t)(a >> 32) == tag && (uint32_t)(b >> 32) == tag) break;
+        if ((pass & 15) == 15 &&
+            (ptx::ld_relaxed_s32(x.abort_word) != 0 || ptx::now_ns() - t0 > x.wait_ns)) {
+          bad = 1;
+          break;
+        }
+      }
+      if constexpr (F)
+        static_cast<float2*>(x.red)[idx] =
+            make_float2(__uint_as_float((uint32_t)a), __uint_as_float((uint32_t)b));
+      else
+        static_cast<double*>(x.red)[idx] =
+            __longlong_as_double((long long)((a & 0xFFFFFFFFull) | (b << 32)));
+    }
+    if (__syncthreads_or(bad)) {
+      if (tid == 0) atomicExch(x.abort_word, 1);
+      return false;
+    }
+    if (tid < nown) {
+      if constexpr (F) {
+        const float2* r = static_cast<const float2*>(x.red);
+        S = 0.f;
+        C = 0.f;
+        for (int g = 0; g < x.nclu; ++g) {
+          const float2 p = r[g * x.E + tid];
+          float t, err;
+          two_sum(S, p.x, t, err);
+          S = t;
+          C += err + p.y;
+        }
+      } else {
+        const double* r = static_cast<const double*>(x.red);
+        acc = 0.0;
+        for (int g = 0; g < x.nclu; ++g) acc += r[g * x.E + tid];
+      }
+    }
+  }
+  if (tid < nown) {
+    const int64_t e = e0 + tid;
+    if constexpr (F) {
       float hi, lo;
       two_sum(S, C, hi, lo);
       const uint64_t v = (uint64_t)__float_as_uint(hi) | ((uint64_t)__float_as_uint(lo) << 32);
@@ -274,15 +293,12 @@ __device__ bool xch_end(const Xch& x, uint32_t tag, uint32_t n) {
       for (uint32_t rk = 0; rk < (uint32_t)kWideCluster; ++rk)
         ptx::st_async_b64(ptx::map_rank(x.tot + e, rk), v, ptx::map_rank(x.xbar, rk));
     } else {
-      const double* r = static_cast<const double*>(x.red);
-      double v = 0.0;
-      for (int64_t g = 0; g < x.G; ++g) v += r[g * x.E + (e - e0)];
 #pragma unroll
       for (uint32_t rk = 0; rk < (uint32_t)kWideCluster; ++rk)
-        ptx::st_async_f64(ptx::map_rank(x.tot + e, rk), v, ptx::map_rank(x.xbar, rk));
+        ptx::st_async_f64(ptx::map_rank(x.tot + e, rk), acc, ptx::map_rank(x.xbar, rk));
     }
   }
-  const bool ok = wait_bar(x.xbar, n & 1, x.abort_word, x.wait_ns);
+  ok = wait_bar(x.xbar, n & 1, x.abort_word, x.wait_ns);
   if (__syncthreads_or(!ok)) {
     if (tid == 0) atomicExch(x.abort_word, 1);
     return false;
@@ -374,6 +390,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   uint64_t* iv_full = bars + 2;    // 3
   uint64_t* p_full = bars + 5;     // 1
   uint64_t* xbar = bars + 6;       // 1
+  uint64_t* gbar = bars + 7;       // 1
   double* ssum = reinterpret_cast<double*>(smem + L.sum);  // sum of w^0..w^k (averaging)
   double* sgam = reinterpret_cast<double*>(smem + L.gb);
   double* sbet = sgam + g.chunk;
@@ -388,7 +405,8 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   __shared__ int s_dec;     // stopping decision of the current iteration
 
   if (tid == 0) {
-    for (int b = 0; b < 7; ++b) ptx::mbar_init(bars + b, 1);
+    for (int b = 0; b < 8; ++b) ptx::mbar_init(bars + b, 1);
+    arm_gather<TF>(bars + 7, tau + 1, L.E, crank);  // the first exchange
     ptx::fence_mbar_init();
   }
   for (int64_t k = kstart + tid; k < kend; k += kWThreads) {
@@ -419,9 +437,9 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
 
   Xch x;
   x.part = g.part; x.abort_word = g.abort_word; x.wait_ns = g.wait_ns;
-  x.nblk = g.nblk; x.cta = cta; x.crank = crank;
-  x.tau = tau; x.ne = tau + 1; x.E = L.E; x.G = L.G; x.nw = ll_words<TF>(tau);
-  x.mine = mine; x.tot = tot; x.red = red; x.xbar = xbar;
+  x.nclu = g.nblk / kWideCluster; x.clu = cta / kWideCluster; x.crank = crank;
+  x.tau = tau; x.ne = tau + 1; x.E = L.E;
+  x.mine = mine; x.tot = tot; x.red = red; x.gat = smem + L.gat; x.xbar = xbar; x.gbar = gbar;
   if constexpr (kFP) x.mine_nrm = &s_nrmf; else x.mine_nrm = &s_nrm;
 
   // copy bookkeeping, identical in every thread: issued / consumed phases per buffer
@@ -790,8 +808,11 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   }
   if (!ok) {
     outcome = 3;
-    // let the stores of the cluster's sums of the last exchange land (bounded)
-    if (nx > 0) wait_bar(xbar, (nx - 1) & 1, nullptr, kDrainNs);
+    // let the peers' stores of the last exchange land (bounded)
+    if (nx > 0) {
+      wait_bar(gbar, (nx - 1) & 1, nullptr, kDrainNs);
+      wait_bar(xbar, (nx - 1) & 1, nullptr, kDrainNs);
+    }
   }
   // no bulk copy may still be writing this CTA's shared memory when it exits
   if (has_rows) {
@@ -871,6 +892,7 @@ bool wide_plan(int64_t m, int64_t tau, int max_ctas, int64_t chunk, WidePlan* ou
       return false;
     }
     const int64_t nblk = round_up((m + q - 1) / q, kWideCluster);
+    if (nblk > (int64_t)kMaxClusters * kWideCluster) return false;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)nblk);
     cfg.blockDim = dim3(kWThreads);

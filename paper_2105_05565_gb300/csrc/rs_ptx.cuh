@@ -83,6 +83,15 @@ __device__ __forceinline__ void st_async_b64(uint32_t cluster_addr, uint64_t v, 
       "l"(v), "r"(cluster_bar)
       : "memory");
 }
+// store of 4 bytes into (possibly another CTA's) shared memory of the cluster, counted
+// as 4 transaction bytes on the destination's mbarrier `cluster_bar`
+__device__ __forceinline__ void st_async_b32(uint32_t cluster_addr, uint32_t v, uint32_t cluster_bar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(
+          cluster_addr),
+      "r"(v), "r"(cluster_bar)
+      : "memory");
+}
 __device__ __forceinline__ void fence_cluster() {
   asm volatile("fence.acq_rel.cluster;" ::: "memory");
 }
