@@ -18,6 +18,8 @@
 // timeout the CTA records an error, stops issuing, and frees its tensor memory.
 #include <cuda.h>
 
+#include <cstring>
+
 #include "rs_kernels.cuh"
 
 namespace rs {
@@ -110,19 +112,111 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
           smem_u32(bar))
       : "memory");
 }
+
+// ---- epilogue through shared memory and TMA stores ----
+constexpr int kOutCols = 32;                        // columns of one output box (128 bytes)
+constexpr int kOutBoxBytes = kBM * kOutCols * 4;    // 16 KB
+
+// 32 consecutive accumulator columns of the warp's 32 TMEM lanes (one row per lane)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(smem_u32(src)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, const void* src, int x,
+                                                  int y) {
+  asm volatile(
+      "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(smem_u32(src)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// at most N bulk groups of this thread still reading shared memory / still in flight
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+template <int N>
+__device__ __forceinline__ void bulk_wait() {
+  asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
+}
+// generic-proxy writes of shared memory visible to the bulk copies that follow
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// The first ncb 32-column boxes of the CTA's 128-row accumulator, one after the
+// other: TMEM -> registers (op(row, column, bits) gives each stored value) -> a
+// 128 x 32 box in the 128-byte swizzled layout of the output tensor map (16-byte
+// chunk j of row r at chunk j ^ (r % 8), so that the lanes' stores hit distinct
+// banks) -> one TMA store (or reduce-add) of the box at (x0 + 32 cb, y0). Two boxes
+// alternate in `stage` (1024-byte aligned, 32 KB free); the store of box cb - 2 must
+// have read its buffer before box cb is written there. Every thread of the CTA calls
+// this; thread 0 issues and waits for the bulk copies.
+template <typename Op>
+__device__ __forceinline__ void epilogue_tma(uint32_t tmem, unsigned char* stage,
+                                             const CUtensorMap* tout, int x0, int y0, int ncb,
+                                             bool reduce, Op op) {
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const int rl = wid * 32 + lane;
+  for (int cb = 0; cb < ncb; ++cb) {
+    unsigned char* buf = stage + (cb & 1) * kOutBoxBytes;
+    if (cb >= 2) {
+      if (tid == 0) bulk_wait_read<1>();
+      __syncthreads();
+    }
+    uint32_t v[32];
+    tmem_ld32(tmem + ((uint32_t)(wid * 32) << 16) + (uint32_t)(cb * kOutCols), v);
+    float4* row = reinterpret_cast<float4*>(buf + rl * 128);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = cb * kOutCols + 4 * j;
+      row[j ^ (rl & 7)] = make_float4(op(rl, c, v[4 * j]), op(rl, c + 1, v[4 * j + 1]),
+                                      op(rl, c + 2, v[4 * j + 2]), op(rl, c + 3, v[4 * j + 3]));
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      if (reduce) tma_reduce_add_2d(tout, buf, x0 + cb * kOutCols, y0);
+      else tma_store_2d(tout, buf, x0 + cb * kOutCols, y0);
+      bulk_commit();
+    }
+  }
+  if (tid == 0) bulk_wait<0>();
+}
 }  // namespace
 
 // K steps [kb0, kb0 + nk); mode 1 (accumulate): add the tiles to A (a later range of
 // rows of X); mode 0: store them with lambda on the diagonal; mode 2 (the Gaussian
 // kernel of eq. (Gausskernel) on the rows of the operand, C = P P^T): store
 // exp(-max(sq_r + sq_c - 2 C_rc, 0) * rbf_scale), rbf_scale = 1 / (2 sigma^2)
+// With tma_out, tout maps A (d x d, row stride lda) for the TMA-store epilogue: the
+// tile's boxes are written whole, so a diagonal tile also writes (or adds to) its
+// part above the diagonal, which the caller's mirror overwrites.
 __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUtensorMap tmap,
+                                                   const __grid_constant__ CUtensorMap tout,
                                                    int64_t d, int64_t kb0, int64_t nk,
                                                    double lambda, int accumulate,
                                                    float* __restrict__ A, int64_t lda,
                                                    int32_t* __restrict__ err,
                                                    const float* __restrict__ sqn,
-                                                   float rbf_scale) {
+                                                   float rbf_scale, int tma_out) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzled stages
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -199,7 +293,25 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
   const bool ok = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0));
   if (!ok && lane == 0) atomicExch(err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok && !*(volatile int*)&s_abort) {
+  if (ok && !*(volatile int*)&s_abort && tma_out) {
+    // boxes not entirely above the tile's last row, nor past column d
+    const int64_t lim = min((int64_t)row0 + kBM - col0, d - col0);
+    const int64_t nbox = (lim + kOutCols - 1) / kOutCols;
+    const int ncb = (int)(nbox < kBN / kOutCols ? nbox : kBN / kOutCols);
+    const int mode = accumulate;
+    epilogue_tma(tmem, base, &tout, col0, row0, ncb, mode == 1,
+                 [&](int rl, int c, uint32_t bits) -> float {
+                   const int64_t r = row0 + rl, cidx = col0 + c;
+                   float f = __uint_as_float(bits);
+                   if (mode == 2) {
+                     if (r >= d || cidx >= d) return 0.f;  // clipped by the store
+                     const float d2 = fmaxf(sqn[r] + sqn[cidx] - 2.f * f, 0.f);
+                     return (cidx == r) ? 1.f : expf(-d2 * rbf_scale);
+                   }
+                   if (mode == 0 && cidx == r) f = (float)((double)f + lambda);
+                   return f;
+                 });
+  } else if (ok && !*(volatile int*)&s_abort) {
     const int64_t r = row0 + wid * 32 + lane;
     for (int c0 = 0; c0 < kBN; c0 += 16) {
       if (col0 + c0 > row0 + kBM - 1) break;  // above every row of the tile (uniform)
@@ -246,13 +358,17 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
 // MMAs into tensor memory). Used for S^T A of the Gaussian sketch: P = the chunk's S^T
 // blocks stacked (rows slot * tau + j), Q = A (symmetric, so A^T = A). Row blocks of
 // slots past the active ones (convergence forecast, iteration cap) are skipped.
+// With tma_out, tc maps C (Mr x N, row stride ldc) for the TMA-store epilogue; a tile
+// that reaches past the active rows writes its rows past them too (rows of slots that
+// no iteration reads).
 __global__ void __launch_bounds__(128, 1) k_gemm_tc_nt(const __grid_constant__ CUtensorMap ta,
                                                       const __grid_constant__ CUtensorMap tb,
+                                                      const __grid_constant__ CUtensorMap tc,
                                                       int64_t Mr, int64_t N, int64_t nk,
                                                       float* __restrict__ C, int64_t ldc,
                                                       const Ctrl* __restrict__ ctrl, int force,
                                                       int nslots, int64_t rows_per_slot,
-                                                      int32_t* __restrict__ err) {
+                                                      int32_t* __restrict__ err, int tma_out) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -319,7 +435,13 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc_nt(const __grid_constant__ C
   const bool ok = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0));
   if (!ok && lane == 0) atomicExch(err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok && !*(volatile int*)&s_abort) {
+  if (ok && !*(volatile int*)&s_abort && tma_out) {
+    const int64_t lim = N - col0;
+    const int64_t nbox = (lim + kOutCols - 1) / kOutCols;
+    const int ncb = (int)(nbox < kBN / kOutCols ? nbox : kBN / kOutCols);
+    epilogue_tma(tmem, base, &tc, col0, row0, ncb, false,
+                 [](int, int, uint32_t bits) -> float { return __uint_as_float(bits); });
+  } else if (ok && !*(volatile int*)&s_abort) {
     const int64_t r = row0 + wid * 32 + lane;
     for (int c0 = 0; c0 < kBN; c0 += 16) {
       if (col0 + c0 >= N) break;  // uniform
@@ -391,6 +513,23 @@ static EncodeTiledFn encode_fn() {
 
 size_t gram_tc_ws_floats(int64_t n, int64_t d) { return (size_t)d * (size_t)round_up(n, 32); }
 
+// tensor map of an FP32 output (rows x cols, row stride ld floats) in 128-row x 32-column
+// boxes, 128-byte swizzled, for the TMA-store epilogue; false (the kernel then stores
+// directly) when the base or the row stride is not 16-byte aligned
+static bool out_map(EncodeTiledFn enc, CUtensorMap* map, float* base, int64_t rows, int64_t cols,
+                    int64_t ld) {
+  std::memset(map, 0, sizeof(*map));
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld * 4) % 16 != 0 || rows <= 0 || cols <= 0)
+    return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)kOutCols, (cuuint32_t)kBM};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // the rows [r0, r1) of X (r0 a multiple of 32; r1 too, or r1 = n): their part of
 // X^T X into the lower triangle of A (d x lda; the caller mirrors), stored with lambda
 // on the diagonal for r0 = 0, else added to A
@@ -415,6 +554,8 @@ cudaError_t launch_gram_tc_rows(cudaStream_t st, const float* X, int64_t n, int6
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  CUtensorMap omap;
+  const int tma_out = out_map(enc, &omap, A, d, d, lda) ? 1 : 0;
   const int64_t T = (d + kBM - 1) / kBM;  // row blocks
   const int64_t Tp = (T + 1) / 2;         // row-block pairs
   const int64_t pairs = Tp * (Tp + 1) / 2;  // (pair, column block) with tj <= pair
@@ -426,8 +567,8 @@ cudaError_t launch_gram_tc_rows(cudaStream_t st, const float* X, int64_t n, int6
   cfg.blockDim = dim3(128);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  return cudaLaunchKernelEx(&cfg, k_gram_tc, map, d, r0 / kBK, (k1 - r0) / kBK, lambda,
-                            r0 > 0 ? 1 : 0, A, lda, err, (const float*)nullptr, 0.f);
+  return cudaLaunchKernelEx(&cfg, k_gram_tc, map, omap, d, r0 / kBK, (k1 - r0) / kBK, lambda,
+                            r0 > 0 ? 1 : 0, A, lda, err, (const float*)nullptr, 0.f, tma_out);
 }
 
 // the rows of P (n x d) zero-padded to ldk = round_up(d, 32) columns (the K-major
@@ -472,6 +613,8 @@ cudaError_t launch_rbf_tc(cudaStream_t st, const float* P, int64_t n, int64_t d,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  CUtensorMap omap;
+  const int tma_out = out_map(enc, &omap, K, n, n, ldK) ? 1 : 0;
   const int64_t T = (n + kBM - 1) / kBM;
   const int64_t Tp = (T + 1) / 2;
   const int64_t pairs = Tp * (Tp + 1) / 2;
@@ -484,8 +627,8 @@ cudaError_t launch_rbf_tc(cudaStream_t st, const float* P, int64_t n, int64_t d,
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   const float scale = (float)(1.0 / (2.0 * sigma * sigma));
-  return cudaLaunchKernelEx(&cfg, k_gram_tc, map, n, (int64_t)0, ldk / kBK, 0.0, 2, K, ldK, err,
-                            (const float*)sqn, scale);
+  return cudaLaunchKernelEx(&cfg, k_gram_tc, map, omap, n, (int64_t)0, ldk / kBK, 0.0, 2, K, ldK,
+                            err, (const float*)sqn, scale, tma_out);
 }
 
 // S^T A of every slot of a chunk for the Gaussian sketch on the tensor cores:
@@ -514,12 +657,14 @@ cudaError_t launch_gauss_sa_tc(cudaStream_t st, const Ctrl* ctrl, int force, int
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  CUtensorMap mc;
+  const int tma_out = out_map(enc, &mc, SA, rows, m, ld) ? 1 : 0;
   const size_t smem = (size_t)kStages * kStageBytes + 1024;
   cudaError_t e = set_smem_max((const void*)k_gemm_tc_nt, smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)((m + kBN - 1) / kBN), (unsigned)((rows + kBM - 1) / kBM));
-  k_gemm_tc_nt<<<grid, 128, smem, st>>>(ma, mb, rows, m, ld / kBK, SA, ld, ctrl, force, nslots,
-                                         tau, err);
+  k_gemm_tc_nt<<<grid, 128, smem, st>>>(ma, mb, mc, rows, m, ld / kBK, SA, ld, ctrl, force, nslots,
+                                         tau, err, tma_out);
   return cudaGetLastError();
 }
 
