@@ -162,147 +162,149 @@ __device__ __forceinline__ void arm_gather(uint64_t* gbar, int64_t ne, int64_t E
   ptx::mbar_arrive_expect_tx(gbar, (uint32_t)(xch_own(ne, E, crank) * kWideCluster * sizeof(PT)));
 }
 
-// All-reduce of the partials over every CTA into `tot`, first half: arm the own
-// mbarrier of the totals, then store every partial into the gather buffer of the
-// cluster rank that owns its entry. `n` counts this launch's exchanges.
+// All-reduce of the partials over every CTA into `tot`, first half: store every
+// partial into the gather buffer of the cluster rank that owns its entry. `n` counts
+// this launch's exchanges. No block barrier is needed for the exchange: thread t
+// stores the partials mine[t + 256 u] it wrote itself, thread 0 the norm it summed
+// itself, and every thread read `tot` of the previous exchange before the block
+// barrier that precedes the partials. The totals' mbarrier was armed for this exchange at the end
+// of the previous one (or before the first), so before any total can arrive: a total
+// needs every CTA's partials, sent after the next block barrier.
 template <typename PT>
 __device__ void xch_begin(const Xch& x, uint32_t tag, uint32_t n) {
   const int tid = threadIdx.x;
-  __syncthreads();  // the partials written; `tot` of the previous exchange read
-  if (tid == 0) ptx::mbar_arrive_expect_tx(x.xbar, (uint32_t)(x.ne * 8));
   const PT* mine = static_cast<const PT*>(x.mine);
   PT* gat = static_cast<PT*>(x.gat) + (size_t)(n & 1) * kWideCluster * x.E + x.crank * x.E;
-  for (int64_t e = tid; e < x.ne; e += kWThreads) {
-    const PT v = e < x.tau ? mine[e] : *static_cast<const PT*>(x.mine_nrm);
+  auto send = [&](int64_t e, PT v) {
     const uint32_t rk = (uint32_t)(e / x.E);
     const uint32_t dst = ptx::map_rank(gat + (e - (int64_t)rk * x.E), rk);
     if constexpr (sizeof(PT) == 4) ptx::st_async_b32(dst, __float_as_uint(v), ptx::map_rank(x.gbar, rk));
     else ptx::st_async_f64(dst, v, ptx::map_rank(x.gbar, rk));
-  }
+  };
+  for (int64_t e = tid; e < x.tau; e += kWThreads) send(e, mine[e]);
+  if (tid == 0) send(x.tau, *static_cast<const PT*>(x.mine_nrm));
 }
 
-// second half: wait for the cluster's partials of the own entries and add them in
-// rank order; with more than one cluster, publish those sums, gather every
-// cluster's (re-reading words whose tag is not current yet) and add them in cluster
-// order (PT = float: float pairs throughout, so the sums are as accurate as in
-// FP64 without FP64 arithmetic); store the totals into the `tot` of every CTA of
-// the cluster (PT = float: a normalised float pair (hi, lo) in each 8-byte entry)
-// and wait for the cluster's totals; false on abort or timeout
+// second half, by the thread that owns each entry of this cluster rank: wait for
+// the cluster's partials of the entry and add them in rank order; with more than
+// one cluster, publish the sum, read every cluster's sum of the entry (re-reading
+// words whose tag is not current yet) and add them in cluster order (PT = float:
+// float pairs throughout, so the sums are as accurate as in FP64 without FP64
+// arithmetic); store the total into the `tot` of every CTA of the cluster (PT =
+// float: a normalised float pair (hi, lo) in each 8-byte entry). Then every thread
+// waits for the cluster's totals; one block barrier at the end agrees on failure
+// (abort or timeout anywhere), after which the call returns false everywhere.
 template <typename PT>
 __device__ bool xch_end(const Xch& x, uint32_t tag, uint32_t n) {
   constexpr bool F = sizeof(PT) == 4;
   const int tid = threadIdx.x;
   const int64_t e0 = (int64_t)x.crank * x.E;
   const int64_t nown = xch_own(x.ne, x.E, x.crank);
-  bool ok = wait_bar(x.gbar, n & 1, x.abort_word, x.wait_ns);
-  if (__syncthreads_or(!ok)) {
-    if (tid == 0) atomicExch(x.abort_word, 1);
-    return false;
-  }
-  // every thread has seen phase n complete: arm phase n + 1 (its buffer is the other)
-  if (tid == 0) arm_gather<PT>(x.gbar, x.ne, x.E, x.crank);
-  // stage 1: this cluster's sum of own entry el, in rank order
-  float S = 0.f, C = 0.f;  // PT = float
-  double acc = 0.0;        // PT = double
+  bool ok = true;
   if (tid < nown) {
-    const PT* gat = static_cast<const PT*>(x.gat) + (size_t)(n & 1) * kWideCluster * x.E + tid;
+    ok = wait_bar(x.gbar, n & 1, x.abort_word, x.wait_ns);
+    // phase n is complete for this thread; the peers' stores of exchange n + 1 come
+    // only after the totals of exchange n, which wait for every owner thread here
+    if (ok && tid == 0) arm_gather<PT>(x.gbar, x.ne, x.E, x.crank);
+    float S = 0.f, C = 0.f;  // PT = float
+    double acc = 0.0;        // PT = double
+    if (ok) {
+      const PT* gat = static_cast<const PT*>(x.gat) + (size_t)(n & 1) * kWideCluster * x.E + tid;
 #pragma unroll
-    for (int c = 0; c < kWideCluster; ++c) {
-      if constexpr (F) {
-        float t, err;
-        two_sum(S, gat[c * x.E], t, err);
-        S = t;
-        C += err;
-      } else {
-        acc += gat[c * x.E];
+      for (int c = 0; c < kWideCluster; ++c) {
+        if constexpr (F) {
+          float t, err;
+          two_sum(S, gat[c * x.E], t, err);
+          S = t;
+          C += err;
+        } else {
+          acc += gat[c * x.E];
+        }
       }
     }
-  }
-  if (x.nclu > 1) {
-    // stage 2: publish, then gather the clusters' sums (thread (g, el) reads
-    // cluster g's words of own entry el)
-    uint64_t* pb = x.part + (size_t)(n & 1) * x.nclu * 2 * x.ne;
-    if (tid < nown) {
-      uint32_t lo, hi;
-      if constexpr (F) {
-        lo = __float_as_uint(S);
-        hi = __float_as_uint(C);
-      } else {
-        const uint64_t b = (uint64_t)__double_as_longlong(acc);
-        lo = (uint32_t)b;
-        hi = (uint32_t)(b >> 32);
+    if (ok && x.nclu > 1) {
+      uint64_t* pb = x.part + (size_t)(n & 1) * x.nclu * 2 * x.ne;
+      {
+        uint32_t lo, hi;
+        if constexpr (F) {
+          lo = __float_as_uint(S);
+          hi = __float_as_uint(C);
+        } else {
+          const uint64_t b = (uint64_t)__double_as_longlong(acc);
+          lo = (uint32_t)b;
+          hi = (uint32_t)(b >> 32);
+        }
+        uint64_t* w = pb + ((size_t)x.clu * x.ne + e0 + tid) * 2;
+        ptx::st_relaxed_u64(w, ll_word(lo, tag));
+        ptx::st_relaxed_u64(w + 1, ll_word(hi, tag));
       }
-      uint64_t* w = pb + ((size_t)x.clu * x.ne + e0 + tid) * 2;
-      ptx::st_relaxed_u64(w, ll_word(lo, tag));
-      ptx::st_relaxed_u64(w + 1, ll_word(hi, tag));
-    }
-    int bad = 0;
-    for (int64_t idx = tid; idx < (int64_t)x.nclu * x.E && !bad; idx += kWThreads) {
-      const int64_t g = idx / x.E, el = idx - g * x.E;
-      if (el >= nown) continue;
-      const uint64_t* w = pb + ((size_t)g * x.ne + e0 + el) * 2;
-      uint64_t a = 0, b = 0;
+      // every cluster's words of this entry, all loads of a pass in flight at once
+      uint64_t a[kMaxClusters], b[kMaxClusters];
+      uint32_t pend = (x.nclu >= 32) ? 0xffffffffu : ((1u << x.nclu) - 1u);
       const uint64_t t0 = ptx::now_ns();
-      for (uint32_t pass = 0;; ++pass) {
-        a = ptx::ld_relaxed_u64(w);
-        b = ptx::ld_relaxed_u64(w + 1);
-        if ((uint32_t)(a >> 32) == tag && (uint32_t)(b >> 32) == tag) break;
-        if ((pass & 15) == 15 &&
+      for (uint32_t pass = 0; pend != 0; ++pass) {
+#pragma unroll
+        for (int g = 0; g < kMaxClusters; ++g) {
+          if (pend & (1u << g)) {
+            const uint64_t* w = pb + ((size_t)g * x.ne + e0 + tid) * 2;
+            a[g] = ptx::ld_relaxed_u64(w);
+            b[g] = ptx::ld_relaxed_u64(w + 1);
+          }
+        }
+#pragma unroll
+        for (int g = 0; g < kMaxClusters; ++g)
+          if ((pend & (1u << g)) && (uint32_t)(a[g] >> 32) == tag && (uint32_t)(b[g] >> 32) == tag)
+            pend &= ~(1u << g);
+        if (pend != 0 && (pass & 15) == 15 &&
             (ptx::ld_relaxed_s32(x.abort_word) != 0 || ptx::now_ns() - t0 > x.wait_ns)) {
-          bad = 1;
+          ok = false;
           break;
         }
       }
-      if constexpr (F)
-        static_cast<float2*>(x.red)[idx] =
-            make_float2(__uint_as_float((uint32_t)a), __uint_as_float((uint32_t)b));
-      else
-        static_cast<double*>(x.red)[idx] =
-            __longlong_as_double((long long)((a & 0xFFFFFFFFull) | (b << 32)));
-    }
-    if (__syncthreads_or(bad)) {
-      if (tid == 0) atomicExch(x.abort_word, 1);
-      return false;
-    }
-    if (tid < nown) {
-      if constexpr (F) {
-        const float2* r = static_cast<const float2*>(x.red);
+      if (ok) {
         S = 0.f;
         C = 0.f;
-        for (int g = 0; g < x.nclu; ++g) {
-          const float2 p = r[g * x.E + tid];
-          float t, err;
-          two_sum(S, p.x, t, err);
-          S = t;
-          C += err + p.y;
-        }
-      } else {
-        const double* r = static_cast<const double*>(x.red);
         acc = 0.0;
-        for (int g = 0; g < x.nclu; ++g) acc += r[g * x.E + tid];
+#pragma unroll
+        for (int g = 0; g < kMaxClusters; ++g) {
+          if (g >= x.nclu) break;
+          if constexpr (F) {
+            float t, err;
+            two_sum(S, __uint_as_float((uint32_t)a[g]), t, err);
+            S = t;
+            C += err + __uint_as_float((uint32_t)b[g]);
+          } else {
+            acc += __longlong_as_double((long long)((a[g] & 0xFFFFFFFFull) | (b[g] << 32)));
+          }
+        }
       }
     }
-  }
-  if (tid < nown) {
-    const int64_t e = e0 + tid;
-    if constexpr (F) {
-      float hi, lo;
-      two_sum(S, C, hi, lo);
-      const uint64_t v = (uint64_t)__float_as_uint(hi) | ((uint64_t)__float_as_uint(lo) << 32);
+    if (ok) {
+      const int64_t e = e0 + tid;
+      if constexpr (F) {
+        float hi, lo;
+        two_sum(S, C, hi, lo);
+        const uint64_t v = (uint64_t)__float_as_uint(hi) | ((uint64_t)__float_as_uint(lo) << 32);
 #pragma unroll
-      for (uint32_t rk = 0; rk < (uint32_t)kWideCluster; ++rk)
-        ptx::st_async_b64(ptx::map_rank(x.tot + e, rk), v, ptx::map_rank(x.xbar, rk));
+        for (uint32_t rk = 0; rk < (uint32_t)kWideCluster; ++rk)
+          ptx::st_async_b64(ptx::map_rank(x.tot + e, rk), v, ptx::map_rank(x.xbar, rk));
+      } else {
+#pragma unroll
+        for (uint32_t rk = 0; rk < (uint32_t)kWideCluster; ++rk)
+          ptx::st_async_f64(ptx::map_rank(x.tot + e, rk), acc, ptx::map_rank(x.xbar, rk));
+      }
     } else {
-#pragma unroll
-      for (uint32_t rk = 0; rk < (uint32_t)kWideCluster; ++rk)
-        ptx::st_async_f64(ptx::map_rank(x.tot + e, rk), acc, ptx::map_rank(x.xbar, rk));
+      atomicExch(x.abort_word, 1);
     }
+  } else if (tid == 0) {
+    arm_gather<PT>(x.gbar, x.ne, x.E, x.crank);  // no own entries: zero bytes
   }
-  ok = wait_bar(x.xbar, n & 1, x.abort_word, x.wait_ns);
+  ok = ok && wait_bar(x.xbar, n & 1, x.abort_word, x.wait_ns);
   if (__syncthreads_or(!ok)) {
     if (tid == 0) atomicExch(x.abort_word, 1);
     return false;
   }
+  if (tid == 0) ptx::mbar_arrive_expect_tx(x.xbar, (uint32_t)(x.ne * 8));  // exchange n + 1
   return true;
 }
 
@@ -402,11 +404,12 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
   __shared__ double s_nrm;  // own partial of ||r||^2
   __shared__ float s_redf[32];
   __shared__ float s_nrmf;  // kFP: own partial of ||r||^2 / ||r_0||^2
-  __shared__ int s_dec;     // stopping decision of the current iteration
 
   if (tid == 0) {
     for (int b = 0; b < 8; ++b) ptx::mbar_init(bars + b, 1);
-    arm_gather<TF>(bars + 7, tau + 1, L.E, crank);  // the first exchange
+    // the first exchange: the cluster's partials of the own entries, the totals
+    arm_gather<TF>(bars + 7, tau + 1, L.E, crank);
+    ptx::mbar_arrive_expect_tx(bars + 6, (uint32_t)((tau + 1) * 8));
     ptx::fence_mbar_init();
   }
   for (int64_t k = kstart + tid; k < kend; k += kWThreads) {
@@ -612,8 +615,12 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
     const uint32_t tag = (uint32_t)(tag0 + nx + 1);
     xch_begin<TF>(x, tag, nx);
     // prefetch, after the partials are out: S^T A and P rows of the next slot,
-    // the inverse map of the one after
+    // the inverse map of the one after. The P rows, their row maps and count replace
+    // the ones the partials just read: the issue warp waits on named barrier 1 until
+    // every other warp has passed it (after its partials), the others do not wait
     if (has_rows && k + 1 < kend) {
+      if (wid == kIssueWarp) ptx::named_bar_sync(1, kWThreads);
+      else ptx::named_bar_arrive(1, kWThreads);
       const int64_t s1 = slot_of(k + 1);
       if (nsab == 2) issue_sa(s1);  // one buffer: issued once iteration k has read it
       issue_p(s1, false);
@@ -622,43 +629,44 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
     ok = xch_end<TF>(x, tag, nx);
     ++nx;
     if (!ok) break;
-    // stopping test on ||r_k|| (k = kstart was tested before this launch), taken by
-    // one thread (the FP64 square root and division are slow here) and broadcast
-    if (tid == 0) {
-      int dec = 0;
-      if (k > kstart) {
-        if constexpr (kFP) {
-          // relative ||r_k||^2 in FP32; the FP64 refresh confirms a convergence
-          const float2 n2 = tot2[tau];
-          hn2f[k - k0] = n2;
-          const float nf = n2.x + n2.y;
-          if (!isfinite(nf)) dec = 2;
-          else if (!no_stop && nf <= thr2f) dec = 1;
-        } else {
-          const double n2 = tot[tau];
-          hn2[k - k0] = n2;
-          if (!isfinite(n2)) {
-            dec = 2;
-          } else if (!no_stop) {
-            // rel = sqrt(n2) / r0 <= tol, decided on n2 away from the boundary
-            if (n2 <= thr2_lo) dec = 1;
-            else if (n2 <= thr2_hi) dec = (sqrt(n2) / r0 <= tol) ? 1 : 0;
-          }
+    // stopping test on ||r_k|| (k = kstart was tested before this launch): every
+    // thread takes the same decision from the same total (thread 0 records the
+    // norm); FP64 square root and division only within 1e-9 of the boundary
+    int dec = 0;
+    if (k > kstart) {
+      if constexpr (kFP) {
+        // relative ||r_k||^2 in FP32; the FP64 refresh confirms a convergence
+        const float2 n2 = tot2[tau];
+        if (tid == 0) hn2f[k - k0] = n2;
+        const float nf = n2.x + n2.y;
+        if (!isfinite(nf)) dec = 2;
+        else if (!no_stop && nf <= thr2f) dec = 1;
+      } else {
+        const double n2 = tot[tau];
+        if (tid == 0) hn2[k - k0] = n2;
+        if (!isfinite(n2)) {
+          dec = 2;
+        } else if (!no_stop) {
+          if (n2 <= thr2_lo) dec = 1;
+          else if (n2 <= thr2_hi) dec = (sqrt(n2) / r0 <= tol) ? 1 : 0;
         }
       }
-      s_dec = dec;
     }
     if (k >= kend) {
       __syncthreads();
-      outcome = s_dec;
+      outcome = dec;
       break;
     }
-    // iteration k on the own rows
+    // iteration k on the own rows; delta in the product's type, each warp converting
+    // the entries of its own columns of the product below (no block barrier)
     const int64_t s = slot_of(k);
-    for (int64_t j = tid; j < tau; j += kWThreads) {
+    const int64_t jc = (tau + kWWarps - 1) / kWWarps;
+    const int64_t j0 = wid * jc, j1 = (j0 + jc < tau) ? j0 + jc : tau;
+    for (int64_t j = j0 + lane; j < j1; j += 32) {
       if constexpr (kFP) dT[j] = tot2[j].x + tot2[j].y;
       else dT[j] = (T)tot[j];
     }
+    __syncwarp();
     const int b = (int)(s % nsab);
     bool r = true;
     if (has_rows) {
@@ -667,14 +675,16 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
       r = r && wait_bar(sa_full + b, sa_use[b] & 1, g.abort_word, g.wait_ns);
       sa_use[b]++;
     }
-    if (__syncthreads_or(!r)) { ok = false; break; }
-    if (s_dec != 0) { outcome = s_dec; break; }
+    if (dec != 0) {  // uniform: stop, unless a wait gave up somewhere
+      if (__syncthreads_or(!r)) ok = false;
+      else outcome = dec;
+      break;
+    }
     if (has_rows) {
       // (A S delta)_i: warp w takes the columns [w jc, (w + 1) jc), lane the rows
-      // lane + 32 u, kRowsPerLane at a time
+      // lane + 32 u, kRowsPerLane at a time; a failed wait is agreed on at the block
+      // barrier after the product (the product only reads this CTA's shared memory)
       const T* sb = sab + (size_t)b * tau * qs;
-      const int64_t jc = (tau + kWWarps - 1) / kWWarps;
-      const int64_t j0 = wid * jc, j1 = (j0 + jc < tau) ? j0 + jc : tau;
       for (int64_t i0 = 0; i0 < qc; i0 += 32 * kRowsPerLane) {
         T acc[kRowsPerLane][4];  // 4 independent chains over j
 #pragma unroll
@@ -707,7 +717,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_iterate_wide(Ctrl* __restrict_
           if (i < qs) red[wid * qs + i] = (acc[u][0] + acc[u][1]) + (acc[u][2] + acc[u][3]);
         }
       }
-      __syncthreads();
+      if (__syncthreads_or(!r)) { ok = false; break; }
       if (nsab == 1 && k + 1 < kend) issue_sa(s + 1);
       const int32_t* iv = ivb + (s % 3) * qs;
       if constexpr (kFP) {

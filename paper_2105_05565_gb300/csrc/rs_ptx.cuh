@@ -92,6 +92,14 @@ __device__ __forceinline__ void st_async_b32(uint32_t cluster_addr, uint32_t v, 
       "r"(v), "r"(cluster_bar)
       : "memory");
 }
+// named CTA barrier `id` (1..15) of `n` threads: sync waits for all n, arrive counts
+// this thread without waiting
+__device__ __forceinline__ void named_bar_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_bar_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
 __device__ __forceinline__ void fence_cluster() {
   asm volatile("fence.acq_rel.cluster;" ::: "memory");
 }
