@@ -341,6 +341,139 @@ __device__ __forceinline__ void wtile_mma_g(T (&acc)[8][4], const T* __restrict_
   }
 }
 
+// ---- tile products of k_potri on a mirrored lane mapping ----
+// FP64 runs at one warp-wide DFMA per 64 cycles per scheduler here, so the small
+// solve is bound by its count of DFMAs; loads, selects and moves go to other pipes.
+// Several of its tile products have a triangular operand, whose zero half a plain
+// 32 x 32 product multiplies too. Here lane (ly, lx) owns the rows p, 31 - p for
+// p = ly + 4k (k < 4) and the columns b, 31 - b for b = lx, lx + 8: in a product
+// whose column c needs the terms l <= c (or l >= c), the pair (b, 31 - b) needs 33
+// terms in all, the same in every lane, so the loops below stay uniform across the
+// warp and skip the zeros (528 DFMAs per lane instead of 1024). Each output sums its
+// terms in ascending l, as the full product does.
+__device__ __forceinline__ int prow_of(int ly, int i) {
+  const int p = ly + 4 * (i >> 1);
+  return (i & 1) ? NBK - 1 - p : p;
+}
+__device__ __forceinline__ int pcol_of(int lx, int j) {
+  const int b = lx + 8 * (j >> 1);
+  return (j & 1) ? NBK - 1 - b : b;
+}
+template <typename T, bool TA>
+__device__ __forceinline__ T opa(const T* A, int r, int l) { return TA ? A[l * TSK + r] : A[r * TSK + l]; }
+template <typename T, bool TB>
+__device__ __forceinline__ T opb(const T* B, int l, int c) { return TB ? B[c * TSK + l] : B[l * TSK + c]; }
+
+template <typename T>
+__device__ __forceinline__ void ptile_zero(T (&acc)[8][4]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+}
+template <typename T>
+__device__ __forceinline__ void ptile_load(T (&acc)[8][4], const T* C, int ly, int lx) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = C[prow_of(ly, i) * TSK + pcol_of(lx, j)];
+}
+template <typename T>
+__device__ __forceinline__ void ptile_store(T* C, const T (&acc)[8][4], int ly, int lx) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) C[prow_of(ly, i) * TSK + pcol_of(lx, j)] = acc[i][j];
+}
+
+// acc += SGN op(A) op(B), full operands
+template <typename T, bool TA, bool TB, int SGN>
+__device__ __forceinline__ void ptile_mma(T (&acc)[8][4], const T* __restrict__ A,
+                                          const T* __restrict__ B, int ly, int lx) {
+#pragma unroll 1  // FP64-pipe bound: ILP comes from the other warps
+  for (int l = 0; l < NBK; ++l) {
+    T a[8], b[4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = opa<T, TA>(A, prow_of(ly, i), l);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = opb<T, TB>(B, l, pcol_of(lx, j));
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fma(SGN > 0 ? a[i] : -a[i], b[j], acc[i][j]);
+  }
+}
+
+// acc += SGN op(A) op(B) where op(B)[l][c] = 0 for l > c (UP) or for l < c (!UP):
+// column c takes the terms l in [0, c] (UP) or [c, 31]
+template <typename T, bool TA, bool TB, int SGN, bool UP>
+__device__ __forceinline__ void ptile_mma_tri_b(T (&acc)[8][4], const T* __restrict__ A,
+                                                const T* __restrict__ B, int ly, int lx) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int b = lx + 8 * q;  // columns b (j = 2q), then 31 - b (j = 2q + 1)
+    const int n1 = UP ? b + 1 : NBK - b;  // terms of column b
+    T v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = acc[i][2 * q];
+    int col = b;
+#pragma unroll 1
+    for (int t = 0; t < NBK + 1; ++t) {
+      if (t == n1) {  // column b done: column 31 - b
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          acc[i][2 * q] = v[i];
+          v[i] = acc[i][2 * q + 1];
+        }
+        col = NBK - 1 - b;
+      }
+      const int l = UP ? (t < n1 ? t : t - n1) : (t < n1 ? b + t : t - 1);
+      const T bv = opb<T, TB>(B, l, col);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const T a = opa<T, TA>(A, prow_of(ly, i), l);
+        v[i] = fma(SGN > 0 ? a : -a, bv, v[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i][2 * q + 1] = v[i];
+  }
+}
+
+// acc += SGN op(A) op(B) where op(A)[r][l] = 0 for l > r (LO) or for l < r (!LO):
+// row r takes the terms l in [0, r] (LO) or [r, 31]
+template <typename T, bool TA, bool TB, int SGN, bool LO>
+__device__ __forceinline__ void ptile_mma_tri_a(T (&acc)[8][4], const T* __restrict__ A,
+                                                const T* __restrict__ B, int ly, int lx) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int p = ly + 4 * k;  // rows p (i = 2k), then 31 - p (i = 2k + 1)
+    const int n1 = LO ? p + 1 : NBK - p;  // terms of row p
+    T v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = acc[2 * k][j];
+    int row = p;
+#pragma unroll 1
+    for (int t = 0; t < NBK + 1; ++t) {
+      if (t == n1) {  // row p done: row 31 - p
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[2 * k][j] = v[j];
+          v[j] = acc[2 * k + 1][j];
+        }
+        row = NBK - 1 - p;
+      }
+      const int l = LO ? (t < n1 ? t : t - n1) : (t < n1 ? p + t : t - 1);
+      const T a = opa<T, TA>(A, row, l);
+      const T as = SGN > 0 ? a : -a;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = fma(as, opb<T, TB>(B, l, pcol_of(lx, j)), v[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[2 * k + 1][j] = v[j];
+  }
+}
+
 // T: arithmetic and L^{-1}; TP: the stored P (FP32 for an FP32 iteration kernel)
 template <typename T, typename TP>
 __global__ void __launch_bounds__(kPotriThreads, 4) k_potri(
@@ -446,16 +579,17 @@ __global__ void __launch_bounds__(kPotriThreads, 4) k_potri(
     // panel tiles below: L_Ip = M_Ip L_pp^{-T} (dropped columns stay zero)
     for (int64_t I = p + 1 + wid; I < P; I += nw) {
       T acc[8][4];
-      wtile_zero(acc);
+      ptile_zero(acc);
       T* C = tile_at(tiles, I, p);
-      wtile_mma<T, true, 1>(acc, C, D, ly, lx);
+      // C L_pp^{-T}: column c of L_pp^{-T} is zero below row c
+      ptile_mma_tri_b<T, false, true, 1, true>(acc, C, D, ly, lx);
 #pragma unroll
       for (int c = 0; c < 4; ++c)
-        if (dropped[c0 + lx * 4 + c])
+        if (dropped[c0 + pcol_of(lx, c)])
 #pragma unroll
           for (int r = 0; r < 8; ++r) acc[r][c] = T(0);
       __syncwarp();
-      wtile_store(C, acc, ly, lx);
+      ptile_store(C, acc, ly, lx);
     }
     __syncthreads();
     // trailing update M_IJ -= L_Ip L_Jp^T, p < J <= I
@@ -466,9 +600,9 @@ __global__ void __launch_bounds__(kPotriThreads, 4) k_potri(
       const int64_t I = p + 1 + a, J = p + 1 + (t - a * (a + 1) / 2);
       T acc[8][4];
       T* C = tile_at(tiles, I, J);
-      wtile_load(acc, C, ly, lx);
-      wtile_mma<T, true, -1>(acc, tile_at(tiles, I, p), tile_at(tiles, J, p), ly, lx);
-      wtile_store(C, acc, ly, lx);
+      ptile_load(acc, C, ly, lx);
+      ptile_mma<T, false, true, -1>(acc, tile_at(tiles, I, p), tile_at(tiles, J, p), ly, lx);
+      ptile_store(C, acc, ly, lx);
     }
     __syncthreads();
   }
@@ -480,10 +614,11 @@ __global__ void __launch_bounds__(kPotriThreads, 4) k_potri(
         const int64_t I = J + r;
         T* X = xtile_at(xt, I, J);
         T acc[8][4];
-        wtile_zero(acc);
-        wtile_mma<T, false, -1>(acc, tile_at(tiles, I, I), X, ly, lx);
+        ptile_zero(acc);
+        // X_II is lower triangular: row r takes the terms l <= r
+        ptile_mma_tri_a<T, false, false, -1, true>(acc, tile_at(tiles, I, I), X, ly, lx);
         __syncwarp();
-        wtile_store(X, acc, ly, lx);
+        ptile_store(X, acc, ly, lx);
       }
       __syncthreads();
     }
@@ -495,10 +630,13 @@ __global__ void __launch_bounds__(kPotriThreads, 4) k_potri(
       const int64_t K = J + r, I = K + 1 + left;
       T* X = xtile_at(xt, I, J);
       T acc[8][4];
-      wtile_load(acc, X, ly, lx);
-      wtile_mma<T, false, 1>(acc, tile_at(tiles, I, K),
-                             r == 0 ? tile_at(tiles, J, J) : xtile_at(xt, K, J), ly, lx);
-      wtile_store(X, acc, ly, lx);
+      ptile_load(acc, X, ly, lx);
+      if (r == 0)  // X_JJ is lower triangular: column c takes the terms l >= c
+        ptile_mma_tri_b<T, false, false, 1, false>(acc, tile_at(tiles, I, K), tile_at(tiles, J, J),
+                                                   ly, lx);
+      else
+        ptile_mma<T, false, false, 1>(acc, tile_at(tiles, I, K), xtile_at(xt, K, J), ly, lx);
+      ptile_store(X, acc, ly, lx);
     }
     __syncthreads();
   }
@@ -506,10 +644,10 @@ __global__ void __launch_bounds__(kPotriThreads, 4) k_potri(
     if (wid == 0) {
       T* X = xtile_at(xt, P - 1, 0);
       T acc[8][4];
-      wtile_zero(acc);
-      wtile_mma<T, false, -1>(acc, tile_at(tiles, P - 1, P - 1), X, ly, lx);
+      ptile_zero(acc);
+      ptile_mma_tri_a<T, false, false, -1, true>(acc, tile_at(tiles, P - 1, P - 1), X, ly, lx);
       __syncwarp();
-      wtile_store(X, acc, ly, lx);
+      ptile_store(X, acc, ly, lx);
     }
     __syncthreads();
   }
@@ -533,17 +671,21 @@ __global__ void __launch_bounds__(kPotriThreads, 4) k_potri(
       while ((I + 1) * (I + 2) / 2 <= t) ++I;
       const int64_t J = t - I * (I + 1) / 2;
       T acc[8][4];
-      wtile_zero(acc);
-      for (int64_t K = I; K < P; ++K) {
-        const T* XI = (K == I) ? tile_at(tiles, K, K) : xtile_at(xt, K, I);
+      ptile_zero(acc);
+      // K = I: X_II^T is upper triangular, row r takes the terms l >= r
+      ptile_mma_tri_a<T, true, false, 1, false>(acc, tile_at(tiles, I, I),
+                                                I == J ? tile_at(tiles, I, I) : xtile_at(xt, I, J),
+                                                ly, lx);
+      for (int64_t K = I + 1; K < P; ++K) {
+        const T* XI = xtile_at(xt, K, I);
         const T* XJ = (K == J) ? tile_at(tiles, K, K) : xtile_at(xt, K, J);
-        wtile_mma_g<T, true, false, 1>(acc, XI, XJ, ly, lx);
+        ptile_mma<T, true, false, 1>(acc, XI, XJ, ly, lx);
       }
 #pragma unroll
       for (int r = 0; r < 8; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const int64_t i = I * NBK + ly * 8 + r, l = J * NBK + lx * 4 + c;
+          const int64_t i = I * NBK + prow_of(ly, r), l = J * NBK + pcol_of(lx, c);
           if (i < tau && l < tau) {
             Ps[i * pld + l] = (TP)acc[r][c];
             if (I != J) Ps[l * pld + i] = (TP)acc[r][c];
