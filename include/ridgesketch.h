@@ -372,7 +372,9 @@ rs_status rs_gram_apply_noalloc(const float* X, int64_t n, int64_t d, const doub
  *   sketch   RS_SUBSAMPLE, RS_COUNT or RS_SUBCOUNT
  *   taus     P sketch sizes (0 = the rule of rs_create), or NULL for all 0
  *   mom, opts as for rs_create (opts.cuda_stream: the stream of the whole batch);
- *            problem p draws its sketches with seed + p
+ *            problem p draws its sketches with seed + p; opts.chunk = 0 takes the
+ *            refresh period for RS_MIXED (an FP64 refresh ends every chunk) and
+ *            128 slots for plain FP64 (every problem holds one chunk's S^T A)
  *   out      receives the batch; NULL on failure
  * On failure the message is rs_batch_last_error(NULL).
  */

@@ -234,6 +234,19 @@ cudaError_t ctx_pool(int dev, cudaMemPool_t* out) {
   return cudaSuccess;
 }
 
+// " (device memory: F GiB free of T GiB)" for out-of-memory messages
+std::string mem_note() {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return std::string();
+  }
+  char buf[96];
+  std::snprintf(buf, sizeof(buf), " (device memory: %.1f GiB free of %.1f GiB)",
+                (double)fr / (1 << 30), (double)tot / (1 << 30));
+  return std::string(buf);
+}
+
 cudaError_t pmalloc(rs_ctx* c, void** p, size_t bytes) {
   cudaMemPool_t pool = nullptr;
   cudaError_t e = ctx_pool(c->device, &pool);
@@ -1199,7 +1212,7 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   cudaStream_t st = c->stream;
   rs_status s;
 #define TRY(expr) do { if ((s = (expr)) != RS_OK) return fail(s); } while (0)
-#define TRYC(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { c->err = std::string(#call) + ": " + cudaGetErrorString(e_); return fail(e_ == cudaErrorMemoryAllocation ? RS_ENOMEM : RS_ECUDA); } } while (0)
+#define TRYC(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { c->err = std::string(#call) + ": " + cudaGetErrorString(e_) + (e_ == cudaErrorMemoryAllocation ? mem_note() : std::string()); return fail(e_ == cudaErrorMemoryAllocation ? RS_ENOMEM : RS_ECUDA); } } while (0)
   TRYC(cudaEventCreate(&c->ev0));
   TRYC(cudaEventCreate(&c->ev1));
   TRYC(cudaMallocHost((void**)&c->ctrl_h, sizeof(Ctrl)));
@@ -1386,7 +1399,10 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     c->l_slot = c->tau * c->tau;
     const size_t nsl = (size_t)c->nslots;
     TRY(dalloc(c, &c->M, nsl * c->m_slot));
-    TRYC(pmalloc(c, (void**)&c->Linv, nsl * c->l_slot * fel));
+    // L^{-1} per slot: for the factor-then-inverse paths and single-slot probes; a
+    // batch member forms M^+ in one kernel (or by sweeps) and is never probed
+    if (!(c->batch_member && (c->potri || c->sweep_p)))
+      TRYC(pmalloc(c, (void**)&c->Linv, nsl * c->l_slot * fel));
     const size_t need_smem = (size_t)factor_ws_elems(c->tau) * fel + 4096;
     if (need_smem > 220 * 1024 || c->tau > 4096)
       TRYC(pmalloc(c, (void**)&c->fws, nsl * factor_ws_elems(c->tau) * fel));
@@ -3129,8 +3145,11 @@ rs_status rs_create_batch(int32_t P, const rs_matrix* Xs, const double* const* Y
   rs_opts o;
   rs_default_opts(&o);
   if (opts) o = *opts;
-  // the batch refreshes at every chunk end: its chunk is the refresh period
-  if (o.precision == RS_MIXED && o.chunk <= 0) o.chunk = o.refresh_every > 0 ? o.refresh_every : 300;
+  // the batch refreshes at every chunk end: its chunk is the refresh period. A plain
+  // FP64 batch keeps 128 slots per problem: its S^T A is FP64, and hundreds of
+  // problems hold one chunk each at once
+  if (o.chunk <= 0)
+    o.chunk = o.precision == RS_MIXED ? (o.refresh_every > 0 ? o.refresh_every : 300) : 128;
   for (int p = 0; p < P; ++p) {
     if (Xs[p].is_csr) { g_batch_err = "rs_create_batch: dense X only"; return RS_EUNSUPPORTED; }
     if (o.precision == RS_MIXED && Xs[p].dtype != RS_F32) { g_batch_err = "rs_create_batch: RS_MIXED takes FP32 X"; return RS_EINVAL; }

@@ -558,3 +558,27 @@ def test_gaussian_sketched_system_on_tensor_cores(rs):
     bound = 4 * 2.0 ** -10 * (np.abs(S).T @ Aabs @ np.abs(S))
     assert np.all(np.abs(M - M_ref) <= bound)
     assert np.abs(M - M_ref).max() > 0  # the tensor-core path ran (not an FP64 product)
+
+
+@pytest.mark.parametrize("m,prec,kind", [(8192, "fp64", "count"), (8192, "mixed", "count"),
+                                         (4100, "fp64", "subcount"), (6000, "mixed", "subsample")])
+def test_sketched_system_large_and_ragged_m(rs, m, prec, kind):
+    """S^T A and M = S^T A S of the bucket-row sketches where A exceeds L2 (m = 8192 in
+    FP64 and FP32, m = 6000 in FP32) or m is ragged (4100 in FP64): M of slot 0 against
+    S^T (X^T X + lambda I) S in FP64 from X S."""
+    n, tau, lam = 48, 256, 0.3
+    g = np.random.default_rng(m)
+    X = g.standard_normal((n, m))
+    y = g.standard_normal(n)
+    s_ = 1024 if kind == "subcount" else None
+    Xin = X.astype(np.float32) if prec == "mixed" else X
+    kw = {"sub_s": s_} if s_ else {}
+    with rs.Solver(Xin, y, lam, sketch=kind, tau=tau, seed=5, precision=prec, setup_tc=False,
+                   **kw) as s:
+        M, _, _ = s.probe_step()
+    Xr = Xin.astype(np.float64)
+    S = oracle.sketch_matrix(kind, m, tau, 5, 0, s=s_)
+    XS = Xr @ S
+    ref = XS.T @ XS + lam * (S.T @ S)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert np.linalg.norm(M - ref) <= tol * np.linalg.norm(ref)
