@@ -343,10 +343,10 @@ def run_reference(args):
 # on n (1799.5 MB read + 3.3 MB written by a launch of 400 iterations, scaled to the
 # launch's iterations); the refresh product reads X once, so its traffic scales with
 # n (327.8 MB read + 2.9 MB written at n = 20000, times 5)
-PROFILED_TRAFFIC = {"iterate": lambda its_per_launch: 1802.8e6 * its_per_launch / 400.0,
-                    # the tile work space of k_potri: 1558.9 MB read + 1341.9 MB written
+PROFILED_TRAFFIC = {"iterate": lambda its_per_launch: 228.7e6 * its_per_launch / 50.0,
+                    # the tile work space of k_potri: 1831.8 MB read + 1450.4 MB written
                     # per launch of 600 slots (the bench's chunk), independent of n
-                    "potri": lambda _unused: 2900.9e6,
+                    "potri": lambda _unused: 3282.2e6,
                     "refresh": lambda its_per_launch: 330.7e6 * N_ROWS / 20000.0}
 
 

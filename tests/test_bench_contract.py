@@ -16,9 +16,10 @@ def test_roofline_of_the_dominant_kernel():
     assert r["kernel"] == "iterate" and r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert abs(r["achieved"] - 1.790e9 / 2.87e-3 / 1e9) < 1e-9
     assert abs(r["frac"] - r["achieved"] / 6788.3) < 1e-12
-    # ncu traffic scaled to the iterations of one launch (400 here)
+    # ncu traffic (228.7 MB per 50 iterations) scaled to the iterations of one launch
+    # (400 here)
     assert abs(r["traffic"] - bench.PROFILED_TRAFFIC["iterate"](400)) < 1.0
-    assert abs(r["traffic"] - 1802.8e6) < 1e3
+    assert abs(r["traffic"] - 8 * 228.7e6) < 1e3
 
 
 def test_roofline_falls_back_without_measured_peaks():
