@@ -2554,6 +2554,11 @@ struct rs_batch {
   std::vector<double*> xpart;          // per phase-1 stream: X^T X W partial sums (mixed)
   std::vector<float2*> xu;             // per phase-1 stream: X W as float pairs (mixed)
   int64_t bq_max = 0, d_max = 0, perm_max = 0, pld_max = 0;
+  // the small solves of all running problems in one launch (every member forms M^+ by
+  // factor, inverse and product): the members' jobs and the launch's tile work space
+  bool potri_batch = false;
+  rs::PotriJob* pjobs = nullptr;
+  void* pbws = nullptr;
   std::vector<cudaStream_t> side;      // phase-1 fan-out streams
   std::vector<cudaEvent_t> evs;        // fork / join events (timing disabled)
   cudaGraphExec_t graph = nullptr;
@@ -2588,7 +2593,7 @@ void batch_free(rs_batch* b) {
   for (rs_ctx* c : b->mem) rs_destroy(c);
   for (unsigned char* p : b->state) if (p) cudaFree(p);
   void* ptrs[] = {b->probs, b->refs, b->ctrls, b->flag, b->skip, b->iters, b->r0, b->resid,
-                  b->tol, b->fin, b->alive, b->order, b->err_word};
+                  b->tol, b->fin, b->alive, b->order, b->err_word, b->pjobs, b->pbws};
   for (void* p : ptrs) if (p) cudaFree(p);
   for (double* p : b->xpart) if (p) cudaFree(p);
   for (float2* p : b->xu) if (p) cudaFree(p);
@@ -2678,6 +2683,39 @@ rs_status batch_upload(rs_batch* b) {
     BKC(cudaMalloc(&b->refs, f.size() * sizeof(f[0])));
     BKC(cudaMemcpy(b->refs, f.data(), f.size() * sizeof(f[0]), cudaMemcpyHostToDevice));
   }
+  // one launch for the small solves of all members (each with the same chunk)
+  bool all_potri = true;
+  for (const rs_ctx* c : b->mem) all_potri = all_potri && c->potri && !c->sweep_p && !c->sparse;
+  if (all_potri) {
+    std::vector<rs::PotriJob> j(b->P);
+    for (int p = 0; p < b->P; ++p) {
+      const rs_ctx* c = b->mem[p];
+      j[p] = rs::PotriJob{c->M, c->m_slot, c->tau, c->Pm, c->pld, c->p_slot, c->ndropped, c->ctrl};
+    }
+    BKC(cudaMalloc(&b->pjobs, j.size() * sizeof(j[0])));
+    BKC(cudaMemcpy(b->pjobs, j.data(), j.size() * sizeof(j[0]), cudaMemcpyHostToDevice));
+    const size_t fel = b->mem[0]->f64_factor() ? 8 : 4;
+    BKC(cudaMalloc(&b->pbws, (size_t)rs::potri_batch_ctas() * rs::potri_ws_elems(b->tau_max) * fel));
+    b->potri_batch = true;
+  }
+  return RS_OK;
+}
+
+// the small solves of the running problems of a chunk, one launch (potri_batch)
+rs_status batch_enqueue_potri(rs_batch* b) {
+  const rs_ctx* c0 = b->mem[0];
+  if (c0->f64_factor() && b->mixed())
+    BKC((rs::launch_potri_batch<double, float>(b->stream, b->pjobs, b->order, b->nrun,
+                                               (int)b->chunk, b->tau_max,
+                                               static_cast<double*>(b->pbws))));
+  else if (c0->f64_factor())
+    BKC((rs::launch_potri_batch<double, double>(b->stream, b->pjobs, b->order, b->nrun,
+                                                (int)b->chunk, b->tau_max,
+                                                static_cast<double*>(b->pbws))));
+  else
+    BKC((rs::launch_potri_batch<float, float>(b->stream, b->pjobs, b->order, b->nrun,
+                                              (int)b->chunk, b->tau_max,
+                                              static_cast<float*>(b->pbws))));
   return RS_OK;
 }
 
@@ -2759,18 +2797,24 @@ rs_status batch_enqueue_chunk(rs_batch* b, int threads, int ns, int parts = kPar
   const int np = b->P * b->nrhs;
   rs_status s;
   if (parts & kPartPhase1) {
-  if ((s = batch_fork(b, ns, 0)) != RS_OK) return s;
-  for (int t = 0; t < b->nrun; ++t) {
-    const int p = b->order_h[t];
-    rs_ctx* c = b->mem[p];
-    cudaStream_t st = stream_of(p);
-    if (p1_stages & kP1Plan) BKC(launch_chunk_begin(st, c->ctrl));
-    c->stream = st;
-    s = enqueue_phase1(c, 0, -1, (int)c->nslots, true, p1_stages);
-    c->stream = b->stream;
-    if (s != RS_OK) { b->err = c->err; return s; }
+  // with potri_batch the members stop before their small solves, which then run for
+  // all of them in one launch on the batch's stream
+  const int mstages = b->potri_batch ? (p1_stages & ~kP1Inv) : p1_stages;
+  if (mstages != 0) {
+    if ((s = batch_fork(b, ns, 0)) != RS_OK) return s;
+    for (int t = 0; t < b->nrun; ++t) {
+      const int p = b->order_h[t];
+      rs_ctx* c = b->mem[p];
+      cudaStream_t st = stream_of(p);
+      if (p1_stages & kP1Plan) BKC(launch_chunk_begin(st, c->ctrl));
+      c->stream = st;
+      s = enqueue_phase1(c, 0, -1, (int)c->nslots, true, mstages);
+      c->stream = b->stream;
+      if (s != RS_OK) { b->err = c->err; return s; }
+    }
+    if ((s = batch_join(b, ns, 0)) != RS_OK) return s;
   }
-  if ((s = batch_join(b, ns, 0)) != RS_OK) return s;
+  if (b->potri_batch && (p1_stages & kP1Inv) && (s = batch_enqueue_potri(b)) != RS_OK) return s;
   }
   const double* gam = b->mem[0]->gam;
   const double* bet = b->mem[0]->bet;

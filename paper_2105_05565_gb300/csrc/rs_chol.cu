@@ -17,6 +17,8 @@
 #include <cooperative_groups.h>
 
 #include "rs_gemm.cuh"
+#include <algorithm>
+
 #include "rs_kernels.cuh"
 
 namespace rs {
@@ -474,22 +476,20 @@ __device__ __forceinline__ void ptile_mma_tri_a(T (&acc)[8][4], const T* __restr
   }
 }
 
-// T: arithmetic and L^{-1}; TP: the stored P (FP32 for an FP32 iteration kernel)
+// M^+ of one slot, by every thread of the CTA. T: arithmetic and L^{-1}; TP: the
+// stored P (FP32 for an FP32 iteration kernel). Ms: the slot's tau x tau M; Ps: its
+// P (row stride pld) or null; LinvS: its L^{-1} or null; tiles: potri_ws_elems(tau)
+// elements of shared or global memory
 template <typename T, typename TP>
-__global__ void __launch_bounds__(kPotriThreads, 4) k_potri(
-    const Ctrl* __restrict__ ctrl, int force, int nslots, const double* __restrict__ M,
-    int64_t m_slot, int64_t tau, T* __restrict__ Linv, int64_t l_slot, TP* __restrict__ Pout,
-    int64_t pld, int64_t p_slot, T* __restrict__ ws, int use_smem, int32_t* __restrict__ ndropped) {
-  extern __shared__ __align__(16) unsigned char potri_smem[];
+__device__ __forceinline__ void potri_slot(const double* __restrict__ Ms, int64_t tau,
+                                           T* __restrict__ LinvS, TP* __restrict__ Ps,
+                                           int64_t pld, T* __restrict__ tiles,
+                                           int32_t* __restrict__ ndropped) {
   __shared__ unsigned char dropped[4096];
   __shared__ double s_red[32];
-  const int64_t s = blockIdx.x;
-  if (s >= active_slots(ctrl, force, nslots)) return;
   const int64_t P = (tau + NBK - 1) / NBK;
   const int64_t tp = P * NBK;
-  T* tiles = use_smem ? reinterpret_cast<T*>(potri_smem) : ws + s * (int64_t)potri_ws_elems(tau);
   T* xt = tiles + ntiles_lower(P) * TILE;
-  const double* Ms = M + s * m_slot;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const int ly = lane >> 3, lx = lane & 7;
   const unsigned full = 0xffffffffu;
@@ -664,8 +664,7 @@ __global__ void __launch_bounds__(kPotriThreads, 4) k_potri(
   }
   __syncthreads();
   // P_IJ = sum_{K >= I} X_KI^T X_KJ, I >= J; tasks in order of decreasing work
-  if (Pout != nullptr) {
-    TP* Ps = Pout + s * p_slot;
+  if (Ps != nullptr) {
     for (int64_t t = wid; t < ntiles_lower(P); t += nw) {
       int64_t I = 0;
       while ((I + 1) * (I + 2) / 2 <= t) ++I;
@@ -694,8 +693,8 @@ __global__ void __launch_bounds__(kPotriThreads, 4) k_potri(
     }
   }
   // L^{-1} with the dropped rows and columns zeroed (tau x tau, zero above), if asked
-  if (Linv != nullptr) {
-    T* out = Linv + s * l_slot;
+  if (LinvS != nullptr) {
+    T* out = LinvS;
     for (int64_t i = wid; i < tau; i += nw) {
       const int64_t I = i / NBK, rr = i - I * NBK;
       for (int64_t j = lane; j < tau; j += 32) {
@@ -712,6 +711,40 @@ __global__ void __launch_bounds__(kPotriThreads, 4) k_potri(
     int cnt = 0;
     for (int64_t i = 0; i < tau; ++i) cnt += dropped[i];
     if (cnt) atomicAdd(ndropped, cnt);
+  }
+}
+
+template <typename T, typename TP>
+__global__ void __launch_bounds__(kPotriThreads, 4) k_potri(
+    const Ctrl* __restrict__ ctrl, int force, int nslots, const double* __restrict__ M,
+    int64_t m_slot, int64_t tau, T* __restrict__ Linv, int64_t l_slot, TP* __restrict__ Pout,
+    int64_t pld, int64_t p_slot, T* __restrict__ ws, int use_smem, int32_t* __restrict__ ndropped) {
+  extern __shared__ __align__(16) unsigned char potri_smem[];
+  const int64_t s = blockIdx.x;
+  if (s >= active_slots(ctrl, force, nslots)) return;
+  T* tiles = use_smem ? reinterpret_cast<T*>(potri_smem) : ws + s * (int64_t)potri_ws_elems(tau);
+  potri_slot<T, TP>(M + s * m_slot, tau, Linv != nullptr ? Linv + s * l_slot : nullptr,
+                    Pout != nullptr ? Pout + s * p_slot : nullptr, pld, tiles, ndropped);
+}
+
+// M^+ of the running problems of a batch in one launch: a grid of at most four CTAs
+// per SM walks the (problem, slot) pairs, problem order[t] taking the pairs
+// [t chunk, (t + 1) chunk), each CTA in its own tile work space of ws_elems elements
+// (the problems come largest first, so the large systems start first)
+template <typename T, typename TP>
+__global__ void __launch_bounds__(kPotriThreads, 4) k_potri_batch(
+    const PotriJob* __restrict__ jobs, const int32_t* __restrict__ order, int nrun, int chunk,
+    T* __restrict__ ws, int64_t ws_elems) {
+  const int64_t total = (int64_t)nrun * chunk;
+  T* tiles = ws + (int64_t)blockIdx.x * ws_elems;
+  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+    const int t = (int)(g / chunk), s = (int)(g - (int64_t)t * chunk);
+    const PotriJob j = jobs[order[t]];
+    if (s >= active_slots(j.ctrl, 0, chunk)) continue;  // uniform over the CTA
+    potri_slot<T, TP>(j.M + s * j.m_slot, j.tau, nullptr,
+                      j.P != nullptr ? static_cast<TP*>(j.P) + s * j.p_slot : nullptr, j.pld,
+                      tiles, j.ndropped);
+    __syncthreads();  // the tiles (and the drop flags) serve the next slot
   }
 }
 
@@ -1204,6 +1237,31 @@ template cudaError_t launch_potri<double, double>(cudaStream_t, const Ctrl*, int
 template cudaError_t launch_potri<double, float>(cudaStream_t, const Ctrl*, int, int,
                                                  const double*, int64_t, int64_t, double*, int64_t,
                                                  float*, int64_t, int64_t, double*, int32_t*);
+
+int potri_batch_ctas() {
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return 4 * nsm;
+}
+
+template <typename T, typename TP>
+cudaError_t launch_potri_batch(cudaStream_t st, const PotriJob* jobs, const int32_t* order,
+                               int nrun, int chunk, int64_t tau_max, T* ws) {
+  if (nrun <= 0) return cudaSuccess;
+  if (tau_max < 1 || tau_max > 4096 || ws == nullptr || chunk < 1) return cudaErrorInvalidValue;
+  const int64_t total = (int64_t)nrun * chunk;
+  const int grid = (int)std::min<int64_t>(total, potri_batch_ctas());
+  k_potri_batch<T, TP><<<grid, kPotriThreads, 0, st>>>(jobs, order, nrun, chunk, ws,
+                                                        (int64_t)potri_ws_elems(tau_max));
+  return cudaGetLastError();
+}
+template cudaError_t launch_potri_batch<float, float>(cudaStream_t, const PotriJob*, const int32_t*,
+                                                      int, int, int64_t, float*);
+template cudaError_t launch_potri_batch<double, double>(cudaStream_t, const PotriJob*,
+                                                        const int32_t*, int, int, int64_t, double*);
+template cudaError_t launch_potri_batch<double, float>(cudaStream_t, const PotriJob*,
+                                                       const int32_t*, int, int, int64_t, double*);
 
 // P_s = L_s^{-T} L_s^{-1}: P(i, j) = sum_k Linv[k, i] Linv[k, j], every slot in one launch
 template <typename TF>

@@ -94,6 +94,22 @@ template <typename T, typename TP>
 cudaError_t launch_potri(cudaStream_t st, const Ctrl* ctrl, int force, int nslots, const double* M,
                          int64_t m_slot, int64_t tau, T* Linv, int64_t l_slot, TP* P, int64_t pld,
                          int64_t p_slot, T* ws, int32_t* ndropped);
+// one problem of a batched small solve: its M per slot, the stored P (type TP of the
+// launch) per slot, its drop counter and control block (active slots)
+struct PotriJob {
+  const double* M;
+  int64_t m_slot, tau;
+  void* P;
+  int64_t pld, p_slot;
+  int32_t* ndropped;
+  const Ctrl* ctrl;
+};
+// M^+ of every active slot of the running problems order[0..nrun) of jobs, chunk slots
+// each, in one launch; ws holds potri_batch_ctas() x potri_ws_elems(tau_max) elements
+int potri_batch_ctas();
+template <typename T, typename TP>
+cudaError_t launch_potri_batch(cudaStream_t st, const PotriJob* jobs, const int32_t* order,
+                               int nrun, int chunk, int64_t tau_max, T* ws);
 template <typename T>
 struct DeltaArgs {
   int kind;            // 0 bucket rows (subsample, count, subcount), 1 Gaussian, 2 SRHT
