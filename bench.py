@@ -557,9 +557,11 @@ def profile_case(workload, rs, dev):
 def bench_learned(args, rs, dev):
     """X 65536 x 8192 = U diag(i^-0.8) V^T (Haar U, V), lambda 1e-3, subsample tau 256,
     no momentum, to 1e-6. Training: plain FP64 trajectories of the uniform proposal on
-    64 seeds of the same recipe (700..763, 1500 iterations each, labels formed on the
-    device by rs_collect; w* of each seed from a mixed solve to 1e-11), 3000 Adam steps
-    of the library's kernels. Evaluation on 16 held-out seeds (900..915): uniform
+    64 seeds of the same recipe (700..763): trajectories of 60 of them (1500 iterations
+    each, labels formed on the device by rs_collect; w* of each seed from a mixed solve
+    to 1e-11), 3000 Adam steps of the library's kernels; the uniform mixture weight eps
+    of the proposal chosen among 0.1, 0.25, 0.5, 0.75 by the mean plain FP64 iteration
+    count on the other 4 seeds. Evaluation on 16 held-out seeds (900..915): uniform
     draws, the learned proposal and the A_jj proposal of Section 7, plain FP64 (one
     context per seed, the samplers switched on it) and mixed; the mean and quartiles of
     the iteration and time ratios against uniform."""
@@ -569,20 +571,25 @@ def bench_learned(args, rs, dev):
     from synth import power_sigma, spectrum_problem_torch
 
     n, m, tau, lam, chunk = 65536, 8192, 256, 1e-3, 20
-    n_train = 4 if args.small else 64
+    n_pool = 6 if args.small else 64
+    n_val = 2 if args.small else 4
+    n_train = n_pool - n_val
     n_eval = 2 if args.small else 16
+    eps_grid = (0.1, 0.25, 0.5, 0.75)
     out = {"workload": "learned", "n": n, "m": m, "tau": tau, "chunk": chunk,
-           "train_seeds": n_train, "eval_seeds": n_eval}
+           "train_seeds": n_train, "validation_seeds": n_val, "eval_seeds": n_eval}
     t0 = time.perf_counter()
     Zs, Ys = [], []
     for sd in range(n_train):
         X, y, _ = spectrum_problem_torch(n, m, power_sigma(m, 0.8), 700 + sd, device=dev)
+        torch.cuda.synchronize(dev)
         with rs.Solver(X, y, lam, sketch="subsample", tau=tau, momentum="heuristic", seed=sd,
                        precision="mixed") as s:
             w_star, _, _, _ = s.solve(tol=1e-11, max_iters=200000)
         Xd = X.double()
         del X
         b = (Xd.T @ y.double()).cpu().numpy()  # the collection starts from w = 0, r = -b
+        torch.cuda.synchronize(dev)
         with rs.Solver(Xd, y, lam, sketch="subsample", tau=tau, momentum="none", seed=sd,
                        chunk=1) as s:
             s.set_proposal(None, 0.1)
@@ -599,14 +606,32 @@ def bench_learned(args, rs, dev):
     out["train_rows"] = int(sum(len(t) for t in Ys))
     out["train_loss_first_last"] = [float(losses[:50].mean()), float(losses[-200:].mean())]
     del Zs, Ys
+    # eps on the validation seeds (plain FP64 iterations to tolerance)
+    val = {e: [] for e in eps_grid}
+    for sd in range(n_train, n_pool):
+        X, y, _ = spectrum_problem_torch(n, m, power_sigma(m, 0.8), 700 + sd, device=dev)
+        Xd = X.double()
+        del X
+        torch.cuda.synchronize(dev)
+        with rs.Solver(Xd, y, lam, sketch="subsample", tau=tau, momentum="none", seed=5 + sd,
+                       chunk=chunk) as s:
+            for e in eps_grid:
+                s.set_proposal(wb, e)
+                _, _, iters, _ = s.solve(tol=TOL, max_iters=100000)
+                val[e].append(iters)
+        del Xd
+    eps = min(eps_grid, key=lambda e: float(np.mean(val[e])))
+    out["validation_iters_by_eps"] = {str(e): float(np.mean(v)) for e, v in val.items()}
+    out["eps"] = eps
     arms = {"uniform": lambda s: s.set_sampling("uniform"),
-            "learned": lambda s: s.set_proposal(wb, 0.1),
+            "learned": lambda s: s.set_proposal(wb, eps),
             "diag": lambda s: s.set_sampling("diag")}
     res = {f"{p}_{a}": [] for p in ("fp64", "mixed") for a in arms}
     for sd in range(n_eval):
         X, y, _ = spectrum_problem_torch(n, m, power_sigma(m, 0.8), 900 + sd, device=dev)
         for prec in ("fp64", "mixed"):
             Xp = X.double() if prec == "fp64" else X
+            torch.cuda.synchronize(dev)
             with rs.Solver(Xp, y, lam, sketch="subsample", tau=tau, momentum="none", seed=5 + sd,
                            precision=prec, chunk=chunk) as s:
                 for name, setter in arms.items():

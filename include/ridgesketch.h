@@ -30,7 +30,10 @@
  *    written during the call.
  *  - Row-major dense layouts; sizes are element counts.
  *  - All work of a context is issued on the context's stream (rs_opts.cuda_stream,
- *    or a stream the library creates). Calls on one context must not overlap.
+ *    or a blocking stream the library creates, whose work orders after the work
+ *    issued before it on the legacy default stream). Device inputs written on any
+ *    other stream must be complete, or that stream ordered before the context's
+ *    stream, when the call starts. Calls on one context must not overlap.
  */
 #ifndef RIDGESKETCH_H
 #define RIDGESKETCH_H

@@ -1186,7 +1186,10 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
   if (o.cuda_stream) {
     c->stream = static_cast<cudaStream_t>(o.cuda_stream);
   } else {
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { c->err = "rs_create: stream"; return fail(RS_ECUDA); }
+    // a blocking stream: its work orders after the work issued before it on the
+    // legacy default stream, where device inputs are often produced (a non-blocking
+    // stream could read them half-written)
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamDefault) != cudaSuccess) { c->err = "rs_create: stream"; return fail(RS_ECUDA); }
     c->own_stream = true;
   }
   // mixed: a chunk (the slots whose sketched systems phase 1 forms and factors in one
@@ -3050,7 +3053,7 @@ rs_status batch_init(rs_batch* b, const rs_matrix* Xs, const double* const* Ys,
   if (o.cuda_stream) {
     b->stream = static_cast<cudaStream_t>(o.cuda_stream);
   } else {
-    BKC(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    BKC(cudaStreamCreateWithFlags(&b->stream, cudaStreamDefault));  // as rs_create's own stream
     b->own_stream = true;
   }
   BKC(cudaEventCreate(&b->ev0));

@@ -582,3 +582,31 @@ def test_sketched_system_large_and_ragged_m(rs, m, prec, kind):
     ref = XS.T @ XS + lam * (S.T @ S)
     tol = 1e-12 if prec == "fp64" else 1e-5
     assert np.linalg.norm(M - ref) <= tol * np.linalg.norm(ref)
+
+
+def test_inputs_produced_on_the_default_stream_just_before(rs):
+    """Device inputs that torch is still writing on its default stream when the context
+    is made (no synchronize between): the library's own stream orders after that work,
+    so the setup reads complete inputs and the solve equals the one from inputs that
+    were complete."""
+    torch = pytest.importorskip("torch")
+    n, m = 32768, 2048
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    Xf = torch.randn(n, m, device="cuda", generator=gen)
+    y = torch.randn(n, device="cuda", dtype=torch.float64, generator=gen)
+    torch.cuda.synchronize()
+
+    def make():  # several kernels on torch's stream, the last one writing X
+        return ((Xf.double() * 2.0 + 1.0) - 1.0) * 0.5
+
+    Xd = make()
+    torch.cuda.synchronize()
+    with rs.Solver(Xd, y, 0.1, sketch="subsample", tau=64, seed=2) as s:
+        w_ref, h_ref, _, _ = s.solve(tol=0.0, max_iters=10)
+    w_ref = np.asarray(w_ref)
+    for _ in range(3):
+        Xd = make()
+        with rs.Solver(Xd, y, 0.1, sketch="subsample", tau=64, seed=2) as s:
+            w, h, _, _ = s.solve(tol=0.0, max_iters=10)
+        assert np.array_equal(np.asarray(h), np.asarray(h_ref))
+        assert np.array_equal(np.asarray(w), w_ref)
