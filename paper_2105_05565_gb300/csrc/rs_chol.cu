@@ -476,6 +476,83 @@ __device__ __forceinline__ void ptile_mma_tri_a(T (&acc)[8][4], const T* __restr
   }
 }
 
+// Lower-triangle outputs (c <= r) of a diagonal tile, with 18 accumulators per lane:
+// for each (k, q), p = ly + 4k and b = lx + 8q, the output (31 - p, b) (always below
+// the diagonal) and (p, b) if b <= p, else (31 - p, 31 - b); the outputs (p, 31 - b)
+// lie above it. A lane with b = p for two (k, q) (lx = ly or ly + 4) also owns the
+// diagonal outputs (31 - p, 31 - p) of those two: 16 regular outputs per lane, two
+// more in a quarter of the lanes, 18 DFMAs per term in every lane instead of 32.
+// v[2 (2k + q)] is (31 - p, b), v[2 (2k + q) + 1] the second, v[16], v[17] the ties.
+__device__ __forceinline__ bool syrk_low(int ly, int lx, int k, int q) {
+  return lx + 8 * q <= ly + 4 * k;
+}
+__device__ __forceinline__ void syrk_pos(int ly, int lx, int v, int& r, int& c, bool& valid) {
+  valid = true;
+  if (v < 16) {
+    const int k = v >> 2, q = (v >> 1) & 1;
+    const int p = ly + 4 * k, b = lx + 8 * q;
+    if ((v & 1) == 0) { r = NBK - 1 - p; c = b; }
+    else if (b <= p) { r = p; c = b; }
+    else { r = NBK - 1 - p; c = NBK - 1 - b; }
+  } else {
+    valid = (lx == ly) || (lx == ly + 4);
+    const int kt = (lx == ly ? 0 : 1) + (v == 17 ? 2 : 0);
+    r = c = NBK - 1 - (ly + 4 * kt);
+  }
+}
+template <typename T>
+__device__ __forceinline__ void syrk_load(T (&v)[18], const T* C, int ly, int lx) {
+#pragma unroll
+  for (int i = 0; i < 18; ++i) {
+    int r, c;
+    bool ok;
+    syrk_pos(ly, lx, i, r, c, ok);
+    v[i] = ok ? C[r * TSK + c] : T(0);
+  }
+}
+template <typename T>
+__device__ __forceinline__ void syrk_store(T* C, const T (&v)[18], int ly, int lx) {
+#pragma unroll
+  for (int i = 0; i < 18; ++i) {
+    int r, c;
+    bool ok;
+    syrk_pos(ly, lx, i, r, c, ok);
+    if (ok) C[r * TSK + c] = v[i];
+  }
+}
+// v += SGN op(A) op(B) on the lower-triangle outputs of a diagonal tile
+template <typename T, bool TA, bool TB, int SGN>
+__device__ __forceinline__ void ptile_syrk_lower(T (&v)[18], const T* __restrict__ A,
+                                                 const T* __restrict__ B, int ly, int lx) {
+  bool low[4][2];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) low[k][q] = syrk_low(ly, lx, k, q);
+  const bool t0 = (lx == ly);  // ties at (k, q) = (0, 0), (2, 1); else (1, 0), (3, 1)
+#pragma unroll 1
+  for (int l = 0; l < NBK; ++l) {
+    T a[8], b[4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = opa<T, TA>(A, prow_of(ly, i), l);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = opb<T, TB>(B, l, pcol_of(lx, j));
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int o = 2 * (2 * k + q);
+        const T ra = low[k][q] ? a[2 * k] : a[2 * k + 1];
+        const T cb = low[k][q] ? b[2 * q] : b[2 * q + 1];
+        v[o] = fma(SGN > 0 ? a[2 * k + 1] : -a[2 * k + 1], b[2 * q], v[o]);
+        v[o + 1] = fma(SGN > 0 ? ra : -ra, cb, v[o + 1]);
+      }
+    const T x16 = t0 ? a[1] : a[3], x17 = t0 ? a[5] : a[7];
+    v[16] = fma(SGN > 0 ? x16 : -x16, b[1], v[16]);
+    v[17] = fma(SGN > 0 ? x17 : -x17, b[3], v[17]);
+  }
+}
+
 // M^+ of one slot, by every thread of the CTA. T: arithmetic and L^{-1}; TP: the
 // stored P (FP32 for an FP32 iteration kernel). Ms: the slot's tau x tau M; Ps: its
 // P (row stride pld) or null; LinvS: its L^{-1} or null; tiles: potri_ws_elems(tau)
@@ -598,11 +675,18 @@ __device__ __forceinline__ void potri_slot(const double* __restrict__ Ms, int64_
       int64_t a = 0;
       while ((a + 1) * (a + 2) / 2 <= t) ++a;
       const int64_t I = p + 1 + a, J = p + 1 + (t - a * (a + 1) / 2);
-      T acc[8][4];
       T* C = tile_at(tiles, I, J);
-      ptile_load(acc, C, ly, lx);
-      ptile_mma<T, false, true, -1>(acc, tile_at(tiles, I, p), tile_at(tiles, J, p), ly, lx);
-      ptile_store(C, acc, ly, lx);
+      if (I == J) {  // only the lower half of a diagonal tile is used
+        T v[18];
+        syrk_load(v, C, ly, lx);
+        ptile_syrk_lower<T, false, true, -1>(v, tile_at(tiles, I, p), tile_at(tiles, I, p), ly, lx);
+        syrk_store(C, v, ly, lx);
+      } else {
+        T acc[8][4];
+        ptile_load(acc, C, ly, lx);
+        ptile_mma<T, false, true, -1>(acc, tile_at(tiles, I, p), tile_at(tiles, J, p), ly, lx);
+        ptile_store(C, acc, ly, lx);
+      }
     }
     __syncthreads();
   }
@@ -669,17 +753,34 @@ __device__ __forceinline__ void potri_slot(const double* __restrict__ Ms, int64_
       int64_t I = 0;
       while ((I + 1) * (I + 2) / 2 <= t) ++I;
       const int64_t J = t - I * (I + 1) / 2;
+      if (I == J) {  // a diagonal tile of the symmetric P: its lower half, then mirrored
+        T v[18];
+#pragma unroll
+        for (int i = 0; i < 18; ++i) v[i] = T(0);
+        for (int64_t K = I; K < P; ++K) {
+          const T* XK = (K == I) ? tile_at(tiles, I, I) : xtile_at(xt, K, I);
+          ptile_syrk_lower<T, true, false, 1>(v, XK, XK, ly, lx);
+        }
+#pragma unroll
+        for (int e = 0; e < 18; ++e) {
+          int r, c;
+          bool ok;
+          syrk_pos(ly, lx, e, r, c, ok);
+          const int64_t i = I * NBK + r, l = I * NBK + c;
+          if (ok && i < tau && l < tau) {
+            Ps[i * pld + l] = (TP)v[e];
+            if (i != l) Ps[l * pld + i] = (TP)v[e];
+          }
+        }
+        continue;
+      }
       T acc[8][4];
       ptile_zero(acc);
       // K = I: X_II^T is upper triangular, row r takes the terms l >= r
-      ptile_mma_tri_a<T, true, false, 1, false>(acc, tile_at(tiles, I, I),
-                                                I == J ? tile_at(tiles, I, I) : xtile_at(xt, I, J),
+      ptile_mma_tri_a<T, true, false, 1, false>(acc, tile_at(tiles, I, I), xtile_at(xt, I, J),
                                                 ly, lx);
-      for (int64_t K = I + 1; K < P; ++K) {
-        const T* XI = xtile_at(xt, K, I);
-        const T* XJ = (K == J) ? tile_at(tiles, K, K) : xtile_at(xt, K, J);
-        ptile_mma<T, true, false, 1>(acc, XI, XJ, ly, lx);
-      }
+      for (int64_t K = I + 1; K < P; ++K)
+        ptile_mma<T, true, false, 1>(acc, xtile_at(xt, K, I), xtile_at(xt, K, J), ly, lx);
 #pragma unroll
       for (int r = 0; r < 8; ++r)
 #pragma unroll
@@ -687,7 +788,7 @@ __device__ __forceinline__ void potri_slot(const double* __restrict__ Ms, int64_
           const int64_t i = I * NBK + prow_of(ly, r), l = J * NBK + pcol_of(lx, c);
           if (i < tau && l < tau) {
             Ps[i * pld + l] = (TP)acc[r][c];
-            if (I != J) Ps[l * pld + i] = (TP)acc[r][c];
+            Ps[l * pld + i] = (TP)acc[r][c];
           }
         }
     }
