@@ -344,9 +344,9 @@ def run_reference(args):
 # launch's iterations); the refresh product reads X once, so its traffic scales with
 # n (327.8 MB read + 2.9 MB written at n = 20000, times 5)
 PROFILED_TRAFFIC = {"iterate": lambda its_per_launch: 228.7e6 * its_per_launch / 50.0,
-                    # the tile work space of k_potri: 1831.8 MB read + 1450.4 MB written
+                    # the tile work space of k_potri: 1814.7 MB read + 1411.7 MB written
                     # per launch of 600 slots (the bench's chunk), independent of n
-                    "potri": lambda _unused: 3282.2e6,
+                    "potri": lambda _unused: 3226.4e6,
                     "refresh": lambda its_per_launch: 330.7e6 * N_ROWS / 20000.0}
 
 
@@ -433,6 +433,9 @@ def bench_sparse(args, rs, dev):
                 _, cg_ms = s.timings()
                 out["cg"] = {"iters": itc, "converged": bool(cvc), "solve_ms": cg_ms,
                              "final_rel": float(hc[-1]), "true_rel": s.true_residual(wc)}
+                # per-group device time of the mixed iterations (CUDA events)
+                out["mixed_kernels"] = {
+                    k: {"ms": v[0], "launches": v[1]} for k, v in s.profile_iteration(600).items()}
     out["iters_per_s_mixed_vs_plain_fp64"] = out["mixed"]["iters_per_s"] / out["fp64"]["iters_per_s"]
     print(json.dumps(out), flush=True)
 
