@@ -1239,10 +1239,18 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     });
     if (s != RS_OK) return fail(s);
     TRYC(cudaEventRecord(c->ev1, st));
-    // the per-slot XS buffers of a chunk stay under 4 GB
+    // the per-slot XS buffers of a chunk, sized for the heaviest sampled columns, stay
+    // under a quarter of the free device memory and 16 GB: a chunk of a few dozen slots
+    // would leave most SMs idle in its small solves (one CTA per slot)
     const int64_t per_slot = c->mf_rcap * 8 + c->mf_ecap * (4 + (int64_t)c->elem()) +
                              c->tau * c->tau * 33 + c->ld * 4 + c->mf_nrb * 16;
-    const int64_t cap = std::max<int64_t>(1, (int64_t)4e9 / std::max<int64_t>(per_slot, 1));
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      cudaGetLastError();
+      fr = (size_t)16e9;
+    }
+    const int64_t budget = std::max<int64_t>((int64_t)4e9, std::min<int64_t>((int64_t)16e9, (int64_t)(fr / 4)));
+    const int64_t cap = std::max<int64_t>(1, budget / std::max<int64_t>(per_slot, 1));
     if (c->chunk > cap) {
       c->chunk = cap_chunk(c, cap);
       c->nslots = c->chunk;
