@@ -139,12 +139,13 @@ def one_solve(rs, X, y, precision, sketch, device, w_out, on_host=False, chol_fp
 
 def launches_per_step(iters, chunk, refresh, fused=True, chunks_per_graph=4):
     """Kernels one mixed step launches: per chunk the chunk start, the sketch plans, the
-    row -> bucket map, S^T A with S^T A S, M^+ (one fused kernel, else factor and
-    product), and per refresh period the persistent iteration kernel and the FP64
+    row -> bucket map, S^T A with S^T A S, M^+ (the fused kernel in its two forms, of
+    which the active slot count runs one; else factor and product), and per refresh
+    period the persistent iteration kernel and the FP64
     refresh (float-pair X^T X w, its sum, the finish); chunks are replayed four per
     CUDA graph until the solve stops; per step 7 more for the setup (transposed copy,
     tensor-core X^T X, mirror, b = X^T y in three launches, initial state)."""
-    per_chunk = 5 + (0 if fused else 1) + 4 * (chunk // refresh)
+    per_chunk = 6 + 4 * (chunk // refresh)  # M^+: two launches either way
     replays = max(1, ((iters + chunk - 1) // chunk + chunks_per_graph - 1) // chunks_per_graph)
     return replays * chunks_per_graph * per_chunk + 7
 

@@ -815,14 +815,22 @@ __device__ __forceinline__ void potri_slot(const double* __restrict__ Ms, int64_
   }
 }
 
-template <typename T, typename TP>
-__global__ void __launch_bounds__(kPotriThreads, 4) k_potri(
+// NT threads per slot. A chunk launches both forms; the active slot count (known on
+// the device) picks one: above `few` (the SM count), four 128-thread CTAs per SM keep
+// the FP64 pipes busy across slots; up to it, one 512-thread CTA per slot gives every
+// scheduler four warps of that slot, so that the few slots of a chunk cut short by
+// the convergence forecast take a fraction of one slot's single-warp latency.
+template <typename T, typename TP, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_potri(
     const Ctrl* __restrict__ ctrl, int force, int nslots, const double* __restrict__ M,
     int64_t m_slot, int64_t tau, T* __restrict__ Linv, int64_t l_slot, TP* __restrict__ Pout,
-    int64_t pld, int64_t p_slot, T* __restrict__ ws, int use_smem, int32_t* __restrict__ ndropped) {
+    int64_t pld, int64_t p_slot, T* __restrict__ ws, int use_smem, int32_t* __restrict__ ndropped,
+    int64_t few) {
   extern __shared__ __align__(16) unsigned char potri_smem[];
   const int64_t s = blockIdx.x;
-  if (s >= active_slots(ctrl, force, nslots)) return;
+  const int64_t nact = active_slots(ctrl, force, nslots);
+  if ((NT == kPotriThreads) == (nact <= few)) return;  // the other form runs this chunk
+  if (s >= nact) return;
   T* tiles = use_smem ? reinterpret_cast<T*>(potri_smem) : ws + s * (int64_t)potri_ws_elems(tau);
   potri_slot<T, TP>(M + s * m_slot, tau, Linv != nullptr ? Linv + s * l_slot : nullptr,
                     Pout != nullptr ? Pout + s * p_slot : nullptr, pld, tiles, ndropped);
@@ -1320,13 +1328,26 @@ cudaError_t launch_potri(cudaStream_t st, const Ctrl* ctrl, int force, int nslot
   if (tau < 1 || tau > 4096 || (!use_smem && ws == nullptr)) return cudaErrorInvalidValue;
   const size_t smem = use_smem ? potri_ws_elems(tau) * sizeof(T) : 0;
   if (use_smem) {
-    const cudaError_t e = cudaFuncSetAttribute(
-        k_potri<T, TP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPotriSmemMax);
+    cudaError_t e = cudaFuncSetAttribute(k_potri<T, TP, kPotriThreads>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kPotriSmemMax);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_potri<T, TP, 4 * kPotriThreads>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPotriSmemMax);
     if (e != cudaSuccess) return e;
   }
-  k_potri<T, TP><<<nslots, kPotriThreads, smem, st>>>(ctrl, force, nslots, M, m_slot, tau, Linv,
-                                                       l_slot, P, pld, p_slot, ws, use_smem,
-                                                       ndropped);
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  k_potri<T, TP, kPotriThreads><<<nslots, kPotriThreads, smem, st>>>(
+      ctrl, force, nslots, M, m_slot, tau, Linv, l_slot, P, pld, p_slot, ws, use_smem, ndropped,
+      (int64_t)nsm);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_potri<T, TP, 4 * kPotriThreads><<<(unsigned)std::min<int64_t>(nslots, nsm),
+                                      4 * kPotriThreads, smem, st>>>(
+      ctrl, force, nslots, M, m_slot, tau, Linv, l_slot, P, pld, p_slot, ws, use_smem, ndropped,
+      (int64_t)nsm);
   return cudaGetLastError();
 }
 template cudaError_t launch_potri<float, float>(cudaStream_t, const Ctrl*, int, int, const double*,

@@ -39,9 +39,10 @@ def test_roofline_of_the_fp64_small_solve():
 
 def test_launch_count_of_a_mixed_step():
     # 1217 iterations in chunks of 600 with a refresh every 50: three chunks run, one
-    # graph replay of four chunks; per chunk 5 phase-1 launches + 12 x (iterate + 3)
-    assert bench.launches_per_step(1217, 600, 50) == 4 * (5 + 48) + 7
+    # graph replay of four chunks; per chunk 6 phase-1 launches (M^+ in its two forms)
+    # + 12 x (iterate + 3)
+    assert bench.launches_per_step(1217, 600, 50) == 4 * (6 + 48) + 7
     # 2401 iterations: five chunks, two replays
-    assert bench.launches_per_step(2401, 600, 50) == 8 * 53 + 7
+    assert bench.launches_per_step(2401, 600, 50) == 8 * 54 + 7
     # factor and product as two launches
     assert bench.launches_per_step(100, 600, 50, fused=False) == 4 * 54 + 7
