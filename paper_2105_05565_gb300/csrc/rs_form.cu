@@ -109,11 +109,15 @@ cudaError_t launch_x_v(cudaStream_t st, const TI* X, int64_t n, int64_t d, const
 // X holds exact FP32 data; v is FP64. Products x * v_hi are split exactly with a fused
 // multiply-add (x * v = p + e, e = fma(x, v_hi, -p)), sums are carried as unevaluated
 // float pairs with the error-free two-sum (Knuth); v_lo = fp32(v - v_hi) adds its small
-// product directly. Each block takes a range of rows: for every row i it forms
-// u_i = x_i . v (block reduction of pairs), then adds u_i x_i to its per-column
-// pairs; per-block column sums go to `part` (blocks x d) and are added in block order.
-// X is read with evict-first loads so that its stream does not push A (read again
-// by the next chunk's phase 1) out of L2.
+// product directly. Each block takes a range of rows, two at a time: for every row i
+// it forms u_i = x_i . v (block reduction of pairs), then adds u_i x_i to its
+// per-column pairs; per-block column sums go to `part` (blocks x d) and are added in
+// block order. Inside a warp the two row dots are reduced by a reduce-scatter: the
+// first exchange leaves each half-warp one row, so later exchanges carry one pair
+// instead of two (the same pairing tree, so the same sums). Two blocks of 128
+// registers per thread share an SM. X is read with evict-first loads, as float4 when
+// its rows are 16-byte aligned, so that its stream does not push A (read again by
+// the next chunk's phase 1) out of L2.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);
@@ -128,20 +132,29 @@ __device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl)
   al = __fsub_rn(e, __fsub_rn(ah, s));
 }
 
-template <int NC, int R, int NT = 256>
-__global__ void __launch_bounds__(NT) k_xtx_v_df(const float* __restrict__ X, int64_t n, int64_t d,
-                                                  const double* __restrict__ v,
-                                                  double* __restrict__ part,
-                                                  const int32_t* __restrict__ stop) {
+// column of the c-th value of thread tid: strided singly, or four consecutive (V4)
+template <int NT, bool V4>
+__device__ __forceinline__ int64_t df_col(int tid, int c) {
+  if constexpr (V4) return 4 * ((int64_t)tid + (int64_t)NT * (c >> 2)) + (c & 3);
+  else return tid + (int64_t)NT * c;
+}
+
+template <int NC, bool V4, int NT = 256>
+__global__ void __launch_bounds__(NT, 2) k_xtx_v_df(const float* __restrict__ X, int64_t n, int64_t d,
+                                                     const double* __restrict__ v,
+                                                     double* __restrict__ part,
+                                                     const int32_t* __restrict__ stop) {
   if (stop != nullptr && *(volatile const int32_t*)stop) return;
+  constexpr int R = 2;  // rows per step
   constexpr int NW = NT / 32;
   __shared__ float s_h[NW][R], s_l[NW][R];
   __shared__ float u_h[R], u_l[R];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const unsigned full = 0xffffffffu;
   float vh[NC], vl[NC], ah[NC], al[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    const int64_t col = tid + NT * c;
+    const int64_t col = df_col<NT, V4>(tid, c);
     const double vv = col < d ? v[col] : 0.0;
     vh[c] = (float)vv;
     vl[c] = (float)(vv - (double)vh[c]);
@@ -158,10 +171,23 @@ __global__ void __launch_bounds__(NT) k_xtx_v_df(const float* __restrict__ X, in
       dh[r] = 0.f;
       dl[r] = 0.f;
       const int64_t i = ib + r;
+      if constexpr (V4) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const int64_t col = tid + NT * c;
-        x[r][c] = (i < i1 && col < d) ? __ldcs(X + i * d + col) : 0.f;
+        for (int g = 0; g < NC / 4; ++g) {
+          const int64_t col = df_col<NT, true>(tid, 4 * g);
+          float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (i < i1 && col < d) q = __ldcs(reinterpret_cast<const float4*>(X + i * d + col));
+          x[r][4 * g] = q.x;
+          x[r][4 * g + 1] = q.y;
+          x[r][4 * g + 2] = q.z;
+          x[r][4 * g + 3] = q.w;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int64_t col = df_col<NT, false>(tid, c);
+          x[r][c] = (i < i1 && col < d) ? __ldcs(X + i * d + col) : 0.f;
+        }
       }
     }
 #pragma unroll
@@ -175,16 +201,24 @@ __global__ void __launch_bounds__(NT) k_xtx_v_df(const float* __restrict__ X, in
         dh[r] = s;
         dl[r] = __fmaf_rn(x[r][c], vl[c], __fadd_rn(dl[r], __fadd_rn(er, e)));
       }
-    // block reduction of the R row dots (fixed tree)
+    // warp reduction of the two row dots: after the exchange across half-warps, lanes
+    // 0-15 carry row 0 and lanes 16-31 row 1
+    {
+      const bool up = (lane & 16) != 0;
+      float kh = up ? dh[1] : dh[0], kl = up ? dl[1] : dl[0];
+      const float oh = __shfl_xor_sync(full, up ? dh[0] : dh[1], 16);
+      const float ol = __shfl_xor_sync(full, up ? dl[0] : dl[1], 16);
+      df_add(kh, kl, oh, ol);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float oh = __shfl_xor_sync(0xffffffffu, dh[r], o);
-        const float ol = __shfl_xor_sync(0xffffffffu, dl[r], o);
-        df_add(dh[r], dl[r], oh, ol);
+      for (int o = 8; o > 0; o >>= 1) {
+        const float ph = __shfl_xor_sync(full, kh, o);
+        const float pl = __shfl_xor_sync(full, kl, o);
+        df_add(kh, kl, ph, pl);
       }
-      if (lane == 0) { s_h[wid][r] = dh[r]; s_l[wid][r] = dl[r]; }
+      if ((lane & 15) == 0) {
+        s_h[wid][lane >> 4] = kh;
+        s_l[wid][lane >> 4] = kl;
+      }
     }
     __syncthreads();
     if (tid < R) {
@@ -194,7 +228,9 @@ __global__ void __launch_bounds__(NT) k_xtx_v_df(const float* __restrict__ X, in
       u_l[tid] = l;
     }
     __syncthreads();
-    // column pairs += u_i x_i
+    // column pairs += u_i x_i. No barrier after this: the next step writes s_h before
+    // its first barrier, which follows every thread's reads of u_h here, and u_h only
+    // after that barrier.
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const float uh = u_h[r], ul = u_l[r];
@@ -208,24 +244,40 @@ __global__ void __launch_bounds__(NT) k_xtx_v_df(const float* __restrict__ X, in
         al[c] = __fmaf_rn(x[r][c], ul, __fadd_rn(al[c], __fadd_rn(er, e)));
       }
     }
-    __syncthreads();
   }
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    const int64_t col = tid + NT * c;
+    const int64_t col = df_col<NT, V4>(tid, c);
     if (col < d) part[blockIdx.x * d + col] = (double)ah[c] + (double)al[c];
   }
 }
 
-int xtx_df_blocks() { return 152; }
+// the kernel for d <= 4096: float4 loads when every row of X starts on 16 bytes
+cudaError_t launch_xtx_df_kernel(cudaStream_t st, int G, const float* X, int64_t n, int64_t d,
+                                 const double* v, double* part, const int32_t* stop) {
+  const bool v4 = (d % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+  if (d <= 1024) {
+    if (v4) k_xtx_v_df<4, true><<<G, 256, 0, st>>>(X, n, d, v, part, stop);
+    else k_xtx_v_df<4, false><<<G, 256, 0, st>>>(X, n, d, v, part, stop);
+  } else if (d <= 2048) {
+    if (v4) k_xtx_v_df<8, true><<<G, 256, 0, st>>>(X, n, d, v, part, stop);
+    else k_xtx_v_df<8, false><<<G, 256, 0, st>>>(X, n, d, v, part, stop);
+  } else if (d <= 4096) {
+    if (v4) k_xtx_v_df<16, true><<<G, 256, 0, st>>>(X, n, d, v, part, stop);
+    else k_xtx_v_df<16, false><<<G, 256, 0, st>>>(X, n, d, v, part, stop);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int xtx_df_blocks() { return 2 * 152; }  // two per SM
 
 cudaError_t launch_xtx_v_df(cudaStream_t st, const float* X, int64_t n, int64_t d, const double* v,
                             double* out, double* part, const int32_t* stop) {
   const int G = xtx_df_blocks();
-  if (d <= 1024) k_xtx_v_df<4, 4><<<G, 256, 0, st>>>(X, n, d, v, part, stop);
-  else if (d <= 2048) k_xtx_v_df<8, 4><<<G, 256, 0, st>>>(X, n, d, v, part, stop);
-  else if (d <= 4096) k_xtx_v_df<16, 4><<<G, 256, 0, st>>>(X, n, d, v, part, stop);
-  else return cudaErrorInvalidValue;
+  const cudaError_t e = launch_xtx_df_kernel(st, G, X, n, d, v, part, stop);
+  if (e != cudaSuccess) return e;
   k_sum_parts<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(part, G, d, out, stop);
   return cudaGetLastError();
 }
@@ -698,11 +750,11 @@ extern "C" rs_status rs_gram_apply_noalloc(const float* X, int64_t n, int64_t d,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   double* pp = static_cast<double*>(part);
   // every block writes all d of its column sums, so nothing needs clearing first
-  if (d <= 1024) k_xtx_v_df<4, 4><<<kNoAllocBlocks, 256, 0, st>>>(X, n, d, v, pp, nullptr);
-  else if (d <= 2048) k_xtx_v_df<8, 4><<<kNoAllocBlocks, 256, 0, st>>>(X, n, d, v, pp, nullptr);
-  else k_xtx_v_df<16, 4><<<kNoAllocBlocks, 256, 0, st>>>(X, n, d, v, pp, nullptr);
-  k_sum_parts<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(pp, kNoAllocBlocks, d, out, nullptr);
-  const cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_xtx_df_kernel(st, kNoAllocBlocks, X, n, d, v, pp, nullptr);
+  if (e == cudaSuccess) {
+    k_sum_parts<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(pp, kNoAllocBlocks, d, out, nullptr);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) {
     set_global_error_msg((std::string("rs_gram_apply_noalloc: ") + cudaGetErrorString(e)).c_str());
     return RS_ECUDA;
