@@ -62,14 +62,33 @@ __global__ void __launch_bounds__(256) k_xt_v_part(const TI* __restrict__ X, int
   part[c * d + j] = acc;
 }
 
-__global__ void k_sum_parts(const double* __restrict__ part, int64_t nchunk, int64_t d,
-                            double* __restrict__ out, const int32_t* __restrict__ stop) {
+// out[j] = sum over c of part[c * d + j], in a fixed order: a block takes 32 columns,
+// warp q sums the parts c = q, q + 8, q + 16, ... in order, and the eight warps' sums
+// are added in q order
+constexpr int kSumWarps = 8;
+__global__ void __launch_bounds__(32 * kSumWarps) k_sum_parts(const double* __restrict__ part,
+                                                              int64_t nchunk, int64_t d,
+                                                              double* __restrict__ out,
+                                                              const int32_t* __restrict__ stop) {
   if (stop != nullptr && *(volatile const int32_t*)stop) return;
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= d) return;
+  __shared__ double s[kSumWarps][32];
+  const int lx = threadIdx.x & 31, q = threadIdx.x >> 5;
+  const int64_t j = (int64_t)blockIdx.x * 32 + lx;
   double acc = 0.0;
-  for (int64_t c = 0; c < nchunk; ++c) acc += part[c * d + j];
-  out[j] = acc;
+  if (j < d)
+    for (int64_t c = q; c < nchunk; c += kSumWarps) acc += part[c * d + j];
+  s[q][lx] = acc;
+  __syncthreads();
+  if (q == 0 && j < d) {
+    double t = s[0][lx];
+#pragma unroll
+    for (int k = 1; k < kSumWarps; ++k) t += s[k][lx];
+    out[j] = t;
+  }
+}
+void launch_sum_parts(cudaStream_t st, const double* part, int64_t nchunk, int64_t d, double* out,
+                      const int32_t* stop) {
+  k_sum_parts<<<(unsigned)((d + 31) / 32), 32 * kSumWarps, 0, st>>>(part, nchunk, d, out, stop);
 }
 
 template <typename TI>
@@ -78,7 +97,7 @@ cudaError_t launch_xt_v(cudaStream_t st, const TI* X, int64_t n, int64_t d, cons
   const int64_t nchunk = (n + kXtRows - 1) / kXtRows;
   dim3 g((unsigned)((d + 255) / 256), (unsigned)nchunk);
   k_xt_v_part<TI><<<g, 256, 0, st>>>(X, n, d, v, part, stop);
-  k_sum_parts<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(part, nchunk, d, out, stop);
+  launch_sum_parts(st, part, nchunk, d, out, stop);
   return cudaGetLastError();
 }
 
@@ -278,7 +297,7 @@ cudaError_t launch_xtx_v_df(cudaStream_t st, const float* X, int64_t n, int64_t 
   const int G = xtx_df_blocks();
   const cudaError_t e = launch_xtx_df_kernel(st, G, X, n, d, v, part, stop);
   if (e != cudaSuccess) return e;
-  k_sum_parts<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(part, G, d, out, stop);
+  launch_sum_parts(st, part, G, d, out, stop);
   return cudaGetLastError();
 }
 
@@ -588,7 +607,7 @@ cudaError_t xt_pairs_rows(cudaStream_t st, const float* X, int64_t n, int64_t d,
 cudaError_t xt_pairs_sum(cudaStream_t st, int64_t n, int64_t d, double* part, double* out,
                          const int32_t* stop) {
   const int64_t nblk = (n + kXtuRows - 1) / kXtuRows;
-  k_sum_parts<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(part, nblk, d, out, stop);
+  launch_sum_parts(st, part, nblk, d, out, stop);
   return cudaGetLastError();
 }
 
@@ -752,7 +771,7 @@ extern "C" rs_status rs_gram_apply_noalloc(const float* X, int64_t n, int64_t d,
   // every block writes all d of its column sums, so nothing needs clearing first
   cudaError_t e = launch_xtx_df_kernel(st, kNoAllocBlocks, X, n, d, v, pp, nullptr);
   if (e == cudaSuccess) {
-    k_sum_parts<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(pp, kNoAllocBlocks, d, out, nullptr);
+    launch_sum_parts(st, pp, kNoAllocBlocks, d, out, nullptr);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {
