@@ -761,7 +761,10 @@ def main():
            "d2h_bytes_per_step": int(N_COLS * 8 + (MAX_IT + 1) * 8),
            "ms_per_step": e2e_ms / len(e2e_runs),
            # this box's pinned host -> device rate for the same bytes (one copy of X)
-           "h2d_gbs_measured": h2d_gbs(Xh, dev)}
+           "h2d_gbs_measured": h2d_gbs(Xh, dev),
+           # each timed run: step, setup (upload overlapped with the Gram) and solve
+           "runs_ms": [[round(r["ms"], 3), round(r["setup_ms"], 3), round(r["solve_ms"], 3)]
+                       for r in e2e_runs]}
 
     # roofline of the dominant kernel (CUDA events inside the library, same stream)
     stats = profile_kernels(rs, X, y, dev)

@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(512, 1)
               T v;
               if constexpr (kMixed) v = pr.r2[(int64_t)q * d + row].x;
               else v = pr.r[(int64_t)q * d + row];
-              acc[q] += neg ? -v : v;
+              acc[q] = sadd(acc[q], v, neg);
             }
           }
         }

@@ -897,7 +897,7 @@ __global__ void __launch_bounds__(256) k_delta(const Ctrl* __restrict__ ctrl, in
       for (int32_t t = boff[l] + lane; t < t1; t += 32) {
         const int32_t e = perm[t];
         const double v = g.r[entry_row(e)];
-        acc += entry_neg(e) ? -v : v;
+        acc = sadd(acc, v, entry_neg(e));
       }
       acc = warp_sum(acc);
       if (lane == 0) rsv[l] = (TA)acc;

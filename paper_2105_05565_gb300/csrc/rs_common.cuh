@@ -37,6 +37,13 @@ __host__ __device__ __forceinline__ int32_t pack_entry(int32_t row, bool neg) {
 }
 __host__ __device__ __forceinline__ int32_t entry_row(int32_t e) { return e & 0x7FFFFFFF; }
 __host__ __device__ __forceinline__ bool entry_neg(int32_t e) { return e < 0; }
+// acc + (neg ? -v : v) as one fused multiply-add by +-1: the product is exact, so the
+// result is the correctly rounded sum or difference. A branch on the sign is
+// predicated both ways and issues both adds.
+template <typename T>
+__device__ __forceinline__ T sadd(T acc, T v, bool neg) {
+  return fma(v, neg ? T(-1) : T(1), acc);
+}
 
 // inverse map of a sketch plan: inv[i] = bucket | sign bit for rows in the sketch,
 // kNotSketched otherwise

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(256) k_iterate(Ctrl* __restrict__ ctrl, IterAr
           for (int32_t t = sb[l]; t < t1; ++t) {
             const int32_t e = sp[t];
             const double v = sr[entry_row(e)];
-            acc += entry_neg(e) ? -v : v;
+            acc = sadd(acc, v, entry_neg(e));
           }
           rsf[l] = (TF)acc;
         }
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256) k_iterate(Ctrl* __restrict__ ctrl, IterAr
           for (int32_t t = boff[l]; t < t1; ++t) {
             const int32_t e = perm[t];
             const double v = g.r[entry_row(e)];
-            acc += entry_neg(e) ? -v : v;
+            acc = sadd(acc, v, entry_neg(e));
           }
           rsf[l] = (TF)acc;
         }

@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(256) k_mf_delta(Ctrl* __restrict__ ctrl, PlanV
     for (int32_t t = boff[j]; t < boff[j + 1]; ++t) {
       const int32_t e = perm[t];
       const double v = r[entry_row(e)];
-      acc += entry_neg(e) ? -v : v;
+      acc = sadd(acc, v, entry_neg(e));
     }
     rs[j] = (TF)acc;
     if (blockIdx.x == 0 && rS_out != nullptr) rS_out[j] = acc;
