@@ -139,7 +139,8 @@ typedef struct {
                             persistent kernel per refresh period, an FP64 refresh after
                             each). 0 = 600 (128 for plain FP64 CSR X). RS_MIXED rounds it up
                             to a whole number of refresh periods; every kind reduces it so
-                            that the chunk's buffers stay under 4 GB */
+                            that the chunk's buffers stay within a quarter of the
+                            free device memory, at least 4 GB and at most 16 GB */
   int32_t setup_tc;      /* RS_MIXED, primal, FP32 X: 1 = form X^T X on the tensor cores
                             (TF32 inputs, FP32 accumulation; default), 0 = FP32 CUDA cores */
   int32_t iter_ctas;     /* subsample / count / subcount: CTAs of the persistent iteration

@@ -754,7 +754,7 @@ rs_status enqueue_refresh(rs_ctx* c) {
 // an FP64 refresh after every refresh_every iterations (the chunk holds a whole number
 // of periods), so the persistent kernel runs in launches of one period each
 rs_status enqueue_chunk(rs_ctx* c, bool with_refresh) {
-  CKC(c, launch_chunk_begin(c->stream, c->ctrl));
+  CKC(c, launch_chunk_begin(c->stream, c->ctrl, c->hist));
   rs_status s = enqueue_phase1(c, 0, -1, (int)c->nslots, c->use_wide || c->sparse);
   if (s != RS_OK) return s;
   const int64_t per = with_refresh ? std::min<int64_t>(c->refresh_every, c->chunk) : c->chunk;
@@ -1085,6 +1085,17 @@ rs_status setup_pipelined(rs_ctx* c, const float* Xh, double lambda) {
   return RS_OK;
 }
 
+// bytes the per-slot buffers of one chunk may take: a quarter of the free device
+// memory, at least 4 GB and at most 16 GB
+int64_t slot_budget() {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    fr = (size_t)16e9;
+  }
+  return std::max<int64_t>((int64_t)4e9, std::min<int64_t>((int64_t)16e9, (int64_t)(fr / 4)));
+}
+
 // the largest chunk within `cap` slots; in mixed precision a whole number of refresh
 // periods, or (cap below one period) the period itself shortened to cap
 int64_t cap_chunk(rs_ctx* c, int64_t cap) {
@@ -1204,11 +1215,13 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     c->chunk = round_up(c->chunk, (int64_t)c->refresh_every);
   }
   if (!c->sparse) {
-    // keep the per-slot buffers of one chunk under 4 GB
-    // (S^T A is materialised for every sketch once the persistent kernel runs it)
+    // keep the per-slot buffers of one chunk within the slot budget (S^T A is
+    // materialised for every sketch once the persistent kernel runs it): in FP64 a
+    // 4 GB cap held 379 slots of tau = 256 at m = 4096, a partial wave of the small
+    // solve's four CTAs per SM
     const int64_t per_slot = c->tau * c->ld * (int64_t)c->elem() * (sketch == RS_GAUSSIAN ? 2 : 1) +
                              c->tau * c->tau * 33 + c->ld * 4;
-    const int64_t cap = std::max<int64_t>(1, (int64_t)4e9 / std::max<int64_t>(per_slot, 1));
+    const int64_t cap = std::max<int64_t>(1, slot_budget() / std::max<int64_t>(per_slot, 1));
     if (c->chunk > cap) c->chunk = cap_chunk(c, cap);
   }
   c->nslots = c->chunk;
@@ -1240,17 +1253,11 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     if (s != RS_OK) return fail(s);
     TRYC(cudaEventRecord(c->ev1, st));
     // the per-slot XS buffers of a chunk, sized for the heaviest sampled columns, stay
-    // under a quarter of the free device memory and 16 GB: a chunk of a few dozen slots
-    // would leave most SMs idle in its small solves (one CTA per slot)
+    // within the slot budget: a chunk of a few dozen slots would leave most SMs idle in
+    // its small solves (one CTA per slot)
     const int64_t per_slot = c->mf_rcap * 8 + c->mf_ecap * (4 + (int64_t)c->elem()) +
                              c->tau * c->tau * 33 + c->ld * 4 + c->mf_nrb * 16;
-    size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
-      cudaGetLastError();
-      fr = (size_t)16e9;
-    }
-    const int64_t budget = std::max<int64_t>((int64_t)4e9, std::min<int64_t>((int64_t)16e9, (int64_t)(fr / 4)));
-    const int64_t cap = std::max<int64_t>(1, budget / std::max<int64_t>(per_slot, 1));
+    const int64_t cap = std::max<int64_t>(1, slot_budget() / std::max<int64_t>(per_slot, 1));
     if (c->chunk > cap) {
       c->chunk = cap_chunk(c, cap);
       c->nslots = c->chunk;
@@ -1538,7 +1545,7 @@ rs_status rs_solve(rs_ctx* c, double tol, int64_t max_iters, double* w_out, int3
     h->tol = tol;
     h->checked_k = -1;
     h->pk = -1;
-    h->predict = (c->mixed() && c->use_wide) ? 1 : 0;
+    h->predict = !c->use_wide ? 0 : (c->mixed() ? 1 : 2);
     if ((s = write_ctrl(c)) != RS_OK) return s;
     CKC(c, cudaEventRecord(c->ev0, st));
     const int64_t max_chunks = (max_iters + c->chunk - 1) / c->chunk + 2;

@@ -69,10 +69,12 @@ struct Ctrl {
   double r0;          // ||r^0|| = ||b||
   double tol;
   int64_t checked_k;  // last k whose FP64 true residual (a refresh) is hist[k]; -1: none
-  // convergence forecast of the mixed persistent path (predict = 1): after each
-  // refresh, kcap > 0 ends the next chunk at the iteration where the FP64 residual's
-  // decay over the last chunk reaches tol (with a margin), so that phase 1 forms no
-  // slot past it; pk, prel: iteration and FP64 residual of the previous refresh
+  // convergence forecast of the persistent paths: kcap > 0 ends the next chunk at the
+  // iteration where the FP64 residual's decay reaches tol (with a margin), so that
+  // phase 1 forms no slot past it. predict = 1 (mixed): set after each FP64 refresh,
+  // from the decay since the previous one; predict = 2 (plain): set at each chunk's
+  // start, from the decay of the recursive residual since the previous chunk's start.
+  // pk, prel: iteration and relative residual of that previous point
   int64_t kcap;
   int64_t pk;
   double prel;

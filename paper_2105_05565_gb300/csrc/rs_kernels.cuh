@@ -358,7 +358,7 @@ int update_blocks(int64_t m);
 cudaError_t launch_init_state(cudaStream_t st, int64_t m, const double* b, double* w, double* wp,
                               double* r, double* rp, double* u);
 // ctrl->k0 = ctrl->k (first iteration of a chunk)
-cudaError_t launch_chunk_begin(cudaStream_t st, Ctrl* ctrl);
+cudaError_t launch_chunk_begin(cudaStream_t st, Ctrl* ctrl, const double* hist = nullptr);
 cudaError_t launch_scale(cudaStream_t st, const double* in, double s, int64_t m, double* out);
 cudaError_t launch_cast_f64_f32(cudaStream_t st, const double* in, int64_t n, float* out);
 // raise (never lower) a kernel's maximum dynamic shared memory on the current device

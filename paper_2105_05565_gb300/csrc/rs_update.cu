@@ -184,10 +184,31 @@ cudaError_t launch_scale(cudaStream_t st, const double* in, double s, int64_t m,
   return cudaGetLastError();
 }
 
-__global__ void k_chunk_begin(Ctrl* ctrl) { ctrl->k0 = ctrl->k; }
+// start of a chunk: k0 = k. With predict = 2 (plain persistent path, whose FP64
+// recursive residual is exact up to rounding and tested every iteration) it also
+// sets the convergence forecast: kcap ends the chunk where the decay rate of the
+// relative residual since the previous chunk's start reaches tol, with a margin, so
+// that phase 1 forms no slot past it. (The mixed path sets kcap after each FP64
+// refresh instead.)
+__global__ void k_chunk_begin(Ctrl* ctrl, const double* __restrict__ hist) {
+  const int64_t k = ctrl->k;
+  if (ctrl->predict == 2 && hist != nullptr && !ctrl->stop) {
+    const double rel = (k == 0) ? 1.0 : hist[k];
+    int64_t cap = 0;
+    if (ctrl->pk >= 0 && k > ctrl->pk && rel > ctrl->tol && ctrl->prel > rel && rel > 0.0) {
+      const double rate = log(rel / ctrl->prel) / (double)(k - ctrl->pk);  // < 0
+      const double left = log(ctrl->tol / rel) / rate;                      // > 0
+      if (left < 1e9) cap = k + (int64_t)ceil(1.25 * left) + 8;
+    }
+    ctrl->kcap = cap;
+    ctrl->pk = k;
+    ctrl->prel = rel;
+  }
+  ctrl->k0 = k;
+}
 
-cudaError_t launch_chunk_begin(cudaStream_t st, Ctrl* ctrl) {
-  k_chunk_begin<<<1, 1, 0, st>>>(ctrl);
+cudaError_t launch_chunk_begin(cudaStream_t st, Ctrl* ctrl, const double* hist) {
+  k_chunk_begin<<<1, 1, 0, st>>>(ctrl, hist);
   return cudaGetLastError();
 }
 
