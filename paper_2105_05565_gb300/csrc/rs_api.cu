@@ -1215,13 +1215,22 @@ rs_status rs_create(const rs_matrix* X, const double* y, int32_t y_on_device, do
     c->chunk = round_up(c->chunk, (int64_t)c->refresh_every);
   }
   if (!c->sparse) {
-    // keep the per-slot buffers of one chunk within the slot budget (S^T A is
-    // materialised for every sketch once the persistent kernel runs it): in FP64 a
-    // 4 GB cap held 379 slots of tau = 256 at m = 4096, a partial wave of the small
-    // solve's four CTAs per SM
+    // keep the per-slot buffers of one chunk (S^T A is materialised for every sketch
+    // once the persistent kernel runs it) within the slot budget where S^T A and M
+    // are formed in one pass (bucket-row sketches whose rows fit shared memory): there
+    // a full chunk fills the FP64 factor's wave (in FP64 a 4 GB cap held 379 slots of
+    // tau = 256 at m = 4096). The other phase-1 paths share reads of A and the
+    // factors' work space in L2 between the slots in flight and run faster on smaller
+    // chunks (kernel ridge at m = 20640: 2x per slot at 600 slots against 150), so
+    // they keep 4 GB.
+    const int64_t nperm = round_up(sketch == RS_COUNT ? m : (sketch == RS_SUBCOUNT ? c->s : c->tau), 4);
+    const bool one_pass =
+        (sketch == RS_SUBSAMPLE || sketch == RS_COUNT || sketch == RS_SUBCOUNT) &&
+        (c->mixed() ? sa_msys_fits<float>(m, c->tau, nperm) : sa_msys_fits<double>(m, c->tau, nperm));
     const int64_t per_slot = c->tau * c->ld * (int64_t)c->elem() * (sketch == RS_GAUSSIAN ? 2 : 1) +
                              c->tau * c->tau * 33 + c->ld * 4;
-    const int64_t cap = std::max<int64_t>(1, slot_budget() / std::max<int64_t>(per_slot, 1));
+    const int64_t budget = one_pass ? slot_budget() : (int64_t)4e9;
+    const int64_t cap = std::max<int64_t>(1, budget / std::max<int64_t>(per_slot, 1));
     if (c->chunk > cap) c->chunk = cap_chunk(c, cap);
   }
   c->nslots = c->chunk;
