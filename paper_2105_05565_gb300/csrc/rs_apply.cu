@@ -193,7 +193,12 @@ cudaError_t launch_msys_batched(cudaStream_t st, const Ctrl* ctrl, int force, in
 // them out, and then M_s[j, l] = sum over bucket l of sign * SA_s[j, row] from
 // shared memory, so S^T A is not read back.
 // ---------------------------------------------------------------------------
-constexpr int kJB = 2;  // buckets per block
+// one bucket per block, two vectors of each of two rows in flight per thread, four
+// 256-thread blocks per SM (64 registers): the reads of A come from L2, and more
+// resident warps hide their latency better than more loads per thread (FP32: 2.87
+// against 3.26 ms per 600 slots at m = 4096 for two buckets per block, four vectors
+// and two blocks per SM; FP64 runs at the FP64 add rate either way)
+constexpr int kJB = 1;  // buckets per block
 
 template <typename T>
 size_t sa_msys_smem(int64_t m, int64_t tau, int64_t nperm) {
@@ -201,7 +206,7 @@ size_t sa_msys_smem(int64_t m, int64_t tau, int64_t nperm) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_sa_msys(const Ctrl* __restrict__ ctrl, int force, int nslots,
+__global__ void __launch_bounds__(256, 4) k_sa_msys(const Ctrl* __restrict__ ctrl, int force, int nslots,
                                                  PlanView plan, const T* __restrict__ A, int64_t lda,
                                                  int64_t m, int64_t tau, int64_t nperm,
                                                  T* __restrict__ SA, int64_t ldsa, int64_t sa_slot,
@@ -230,7 +235,7 @@ __global__ void __launch_bounds__(256) k_sa_msys(const Ctrl* __restrict__ ctrl, 
   // rows SA[j, :], j = jb .. jb + nrow - 1: each thread kVU vectors of VN columns at
   // once (kVU x 2 row loads in flight), rows summed in bucket order
   const int64_t nvec = (m + VN - 1) / VN;
-  constexpr int kVU = 4;
+  constexpr int kVU = 2;
   for (int r = 0; r < nrow; ++r) {
     const int64_t j = jb + r;
     const int32_t t0 = sboff[j], t1 = sboff[j + 1];
@@ -312,7 +317,11 @@ __global__ void __launch_bounds__(256) k_sa_msys(const Ctrl* __restrict__ ctrl, 
 // false when the block's buffers do not fit shared memory (two-kernel path)
 template <typename T>
 bool sa_msys_fits(int64_t m, int64_t tau, int64_t nperm) {
-  return sa_msys_smem<T>(m, tau, nperm) <= 200 * 1024;
+  // the problems this path takes: the plan and the rows of two buckets fit 200 KB (a
+  // fixed rule, independent of the block's shape, so that larger m keep the paths
+  // that share reads of A between slots in L2)
+  return ((size_t)(nperm + tau + 1) * 4 + 15) / 16 * 16 + (size_t)2 * round_up(m, 4) * sizeof(T) <=
+         200 * 1024;
 }
 
 template <typename T>
