@@ -243,7 +243,7 @@ def dgemm_tflops(device, n=4096, reps=5):
 def cpu_baseline(X, y, iters_ref, sample_iters=4):
     """The FP64 oracle on the host cores: A = X^T X + lambda I from the full X
     (setup), then `sample_iters` count-sketch iterations; iters/s of its loop. Also
-    returns the FP64 solution w* = A^{-1} b of that A (the judge of the GPU results),
+    returns the FP64 solution w* = A^{-1} b of that A (the reference the GPU results are checked against),
     and the small dense case run by the oracle to tolerance."""
     import oracle
     from synth import gaussian_problem
