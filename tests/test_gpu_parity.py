@@ -155,6 +155,28 @@ def test_cfg_small_to_tolerance(rs):
     assert rel(w, oracle.direct_solution(X, y, lam)) <= 1e-4
 
 
+def test_plain_chunking_and_forecast_leave_iterates_unchanged(rs):
+    """Plain FP64 persistent path (count sketch, heuristic momentum) to tolerance in
+    chunks of 50, 128 and the default: each chunk's start sets a convergence forecast
+    that can end the chunk early, but the sketches are drawn by iteration index and
+    the state carries over in FP64, so every chunking stops at the oracle's iteration
+    with the same w."""
+    X, y, _ = gaussian_problem(3000, 700, 1)
+    lam = 1e-2
+    ref = oracle.solve_ridge(X, y, lam, "primal", "count", 64, seed=3, tol=1e-6, max_iters=5000,
+                             mom={"kind": "heuristic"})
+    ws = []
+    for ch in (50, 128, 0):
+        with rs.Solver(X, y, lam, sketch="count", tau=64, momentum="heuristic", seed=3,
+                       chunk=ch) as s:
+            w, hist, iters, conv = s.solve(tol=1e-6, max_iters=5000)
+        assert conv and iters == ref["iters"], (ch, iters, ref["iters"])
+        assert rel(w, ref["w"]) <= W_TOL
+        ws.append(w)
+    for w in ws[1:]:
+        assert rel(w, ws[0]) <= 1e-13
+
+
 @pytest.mark.parametrize("kind", ["subsample", "count", "subcount", "gaussian", "srht"])
 def test_probe_sketched_system(rs, kind):
     """M = S^T A S, r_S = S^T r and delta of one iteration, from the oracle's state."""
