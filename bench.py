@@ -345,9 +345,9 @@ def run_reference(args):
 # launch's iterations); the refresh product reads X once, so its traffic scales with
 # n (327.8 MB read + 2.9 MB written at n = 20000, times 5)
 PROFILED_TRAFFIC = {"iterate": lambda its_per_launch: 228.7e6 * its_per_launch / 50.0,
-                    # the tile work space of k_potri: 1814.7 MB read + 1411.7 MB written
+                    # the tile work space of k_potri: 1819.1 MB read + 1415.4 MB written
                     # per launch of 600 slots (the bench's chunk), independent of n
-                    "potri": lambda _unused: 3226.4e6,
+                    "potri": lambda _unused: 3234.5e6,
                     "refresh": lambda its_per_launch: 330.7e6 * N_ROWS / 20000.0}
 
 
